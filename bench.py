@@ -1,0 +1,472 @@
+"""Benchmark: nonzero-amplitude updates/s of the sparse-state gate path.
+
+Workload (default ``adder67``): 67 qubits with 128-bit labels; H on the low
+16 bits of register a (65,536 nonzeros), X gates loading a seeded 32-bit
+constant into b, a 32-bit ripple-carry adder, 32 controlled-phase gates on
+seeded pairs of a/b qubits, then the inverse adder; FP64 amplitudes, prune
+eps 1e-14. Other workloads: ``adder67-w24`` (a over 24 bits, 16.8 M nonzeros),
+``givens64`` (64 qubits, 4 occupied modes, 500 Givens/CZ layers).
+
+A step = reset to |0...0>, apply the whole gate stream (every branching pass
+and fused phase/permutation pass), read the probability of one register value
+back (the readout kernels). Updates per step U = sum over gates of the nonzero
+count before the gate. ``value`` = U * steps / (sum of per-step device times);
+L2 is flushed (a 512 MB write) between timed steps, outside the timed events.
+
+``--impl reference`` times the CPU oracle (the only reference this method has)
+on a bounded sample of the same workload on the host cores.
+
+Prints one JSON line on rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2105_01533_gb300 import workloads as W  # noqa: E402
+
+METRIC = "nonzero-amplitude updates/s"
+UNIT = "updates/s"
+EPS = 1e-14
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ---- workloads -------------------------------------------------------------------
+def make_workload(name: str):
+    if name == "adder67":
+        wl = W.adder_workload(seed=1, width=16)
+        return dict(name=name, gates=wl.gates, nqubits=wl.layout.nqubits, capacity=1 << 17,
+                    readout=((0xFFFF, 0), (0, 0)),
+                    desc="adder67: 67 qubits, 128-bit labels, H on a[0..15] (65,536 nonzeros), "
+                         "32-bit ripple-carry adder, 32 CP gates, inverse adder; FP64, eps 1e-14")
+    if name == "adder67-w24":
+        wl = W.adder_workload(seed=1, width=24)
+        return dict(name=name, gates=wl.gates, nqubits=wl.layout.nqubits, capacity=1 << 25,
+                    readout=((0xFFFF, 0), (0, 0)),
+                    desc="adder67-w24: as adder67 with a over 24 bits (16,777,216 nonzeros, "
+                         "537 MB state)")
+    if name == "givens64":
+        g = W.givens_workload(seed=2, nqubits=64, modes=4, layers=500)
+        return dict(name=name, gates=g, nqubits=64, capacity=700_000,
+                    readout=((0xFF, 0), (0x0F, 0)),
+                    desc="givens64: 64 qubits, 4 occupied modes (<= 635,376 nonzeros), 500 layers "
+                         "of 32 Givens + 32 CZ; FP64, eps 1e-14")
+    raise SystemExit("unknown workload %s" % name)
+
+
+# ---- distributed plumbing --------------------------------------------------------
+def dist_init(ngpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, int(os.environ.get("RANK", "0")), world, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---- clocks ----------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for_smi() -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        u = u if u.startswith("GPU-") else "GPU-" + u
+        out = subprocess.run(["nvidia-smi", "--query-gpu=uuid", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout
+        if u in out:
+            return u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    return vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device())
+
+
+# ---- roofline ----------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact"}
+
+
+def algorithmic_bytes(r) -> float:
+    """Bytes a launch must move at minimum: a fused pass reads
+    every label, writes it back if the pass permutes, and reads and writes the
+    amplitude if the pass has phases; a branching pass reads the old state
+    (emit) and writes the new one (compaction)."""
+    lb = r["label_bytes"]
+    if r["kind"] == 1:
+        per = lb + (lb if r["flags"] & 1 else 0) + (32 if r["flags"] & 2 else 0)
+        return per * r["n_in"]
+    if r["kind"] == 2:
+        return (lb + 16) * r["n_in"]
+    return (lb + 16) * r["n_out"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2105_01533_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2105_01533_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str, n_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    launch size, or None if the summary is missing or the kernels changed."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel, {}).get(workload)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_entry"] * n_per_launch
+
+
+def roofline(records, workload: str):
+    peak, which = measured_peaks()
+    by = {}
+    for r in records:
+        b = by.setdefault(r["kind"], {"ms": 0.0, "bytes": 0.0, "n": 0, "entries": 0})
+        b["ms"] += r["ms"]
+        b["bytes"] += algorithmic_bytes(r)
+        b["n"] += 1
+        b["entries"] += r["n_in"] if r["kind"] != 3 else r["n_out"]
+    total = sum(b["ms"] for b in by.values()) or 1.0
+    kind = max(by, key=lambda k: by[k]["ms"])
+    b = by[kind]
+    avg_ms = b["ms"] / b["n"]
+    avg_bytes = b["bytes"] / b["n"]
+    achieved = avg_bytes / (avg_ms * 1e-3) / 1e9
+    share = {KIND_NAMES[k]: round(v["ms"] / total, 4) for k, v in by.items()}
+    traffic = ncu_traffic(KIND_NAMES[kind], workload, b["entries"] / b["n"])
+    return {"bound": "hbm", "kernel": KIND_NAMES[kind], "achieved": round(achieved, 2),
+            "peak": peak, "peak_source": which + " (MEASURED_PEAKS.json hbm_gbs)" if which == "measured"
+            else "fallback 6800 GB/s", "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic, "algorithmic_bytes_per_launch": round(avg_bytes),
+            "avg_launch_ms": round(avg_ms, 5), "launches_per_step": None,
+            "time_share": share}
+
+
+# ---- our arm ---------------------------------------------------------------------
+def updates_per_step(sps, wl, st) -> tuple:
+    """Untimed: nonzeros before every gate, from the product path itself."""
+    plan = sps.sps_plan(wl["gates"], wl["nqubits"])
+    bounds = [p[1] for p in plan] + [len(wl["gates"])]
+    st.reset()
+    u = 0
+    nnz = 1
+    for j, (kind, first, _) in enumerate(plan):
+        u += nnz * (bounds[j + 1] - first)
+        st.apply(wl["gates"][first:bounds[j + 1]], EPS)
+        nnz = st.nnz()
+    return u, nnz
+
+
+def run_ours(args, dist, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2105_01533_gb300 import sps
+
+    wl = make_workload(args.workload)
+    st = sps.SparseState(wl["nqubits"], wl["capacity"])
+    stream = torch.cuda.current_stream()
+    U, nnz_final = updates_per_step(sps, wl, st)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    mask, val = wl["readout"]
+
+    def step():
+        st.reset()
+        st.apply(wl["gates"], EPS)
+        return st.probability(mask, val)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st.set_option(sps.SPS_OPT_PROFILE, 1)
+    st.profile_read()
+    sampler = ClockSampler(gpu_id_for_smi()) if rank == 0 else None
+    barrier(dist)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    c0 = st.counters().kernel_launches
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    records = []
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        if (i + 1) % 64 == 0:
+            records += st.profile_read()
+    torch.cuda.synchronize()
+    launches = st.counters().kernel_launches - c0
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    records += st.profile_read()
+    st.set_option(sps.SPS_OPT_PROFILE, 0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(dist, sum(step_ms))
+    units = sum_over_ranks(dist, float(U) * args.steps)
+    value = units / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(args, sps, torch, wl, st, flush, U, dist)
+
+    rl = roofline(records, wl["name"])
+    rl["launches_per_step"] = round(launches / args.steps, 2)
+    res = None
+    if rank == 0:
+        res = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": wl["desc"], "nqubits": wl["nqubits"],
+                          "gates": int(len(wl["gates"])), "nnz_final": int(nnz_final),
+                          "updates_per_step": int(U), "prune_eps": EPS,
+                          "l2": "flushed between timed steps (512 MB write)",
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "roofline": rl, "e2e": e2e, "gpu_launches": int(launches * world),
+               "clocks": clocks, "p50_step_ms": round(float(np.median(step_ms)), 5),
+               "p99_step_ms": round(float(np.percentile(step_ms, 99)), 5)}
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
+    st.close()
+    return res
+
+
+def run_e2e(args, sps, torch, wl, st, flush, U, dist):
+    """Same metric through the public calls with host buffers: every step
+    copies the gate records from host memory (inside sps_apply) and reads the
+    whole final state back into pinned host arrays."""
+    n = st.nnz()
+    pin = lambda dt: torch.empty(max(n, 1), dtype=dt, pin_memory=True).numpy()  # noqa: E731
+    hi, lo, re, im = pin(torch.int64).view(np.uint64), pin(torch.int64).view(np.uint64), \
+        pin(torch.float64), pin(torch.float64)
+    k = max(3, args.steps // 4)
+    for _ in range(2):
+        st.reset()
+        st.apply(wl["gates"], EPS)
+        sps.sps_get_amplitudes(st.handle, hi, lo, re, im, len(lo))
+    total = 0.0
+    for _ in range(k):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.reset()
+        st.apply(wl["gates"], EPS)
+        got = sps.sps_get_amplitudes(st.handle, hi, lo, re, im, len(lo))
+        total += time.perf_counter() - t0
+    total = max_over_ranks(dist, total)
+    units = sum_over_ranks(dist, float(U) * k)
+    return {"value": round(units / total, 1), "unit": UNIT,
+            "h2d_bytes_per_step": int(wl["gates"].nbytes), "d2h_bytes_per_step": int(got * 32 + 64),
+            "steps": k}
+
+
+# ---- the oracle on the host ------------------------------------------------------------
+def oracle_rate(wl, budget_s: float, prefix_cache={}):
+    """Run the oracle over the gate stream (gate by gate, single thread) until
+    the budget is used; returns (updates, seconds, gates_done)."""
+    from oracle import OracleState
+    gates = wl["gates"]
+    orc = OracleState(wl["nqubits"])
+    u, done, t = 0, 0, 0.0
+    while done < len(gates) and t < budget_s:
+        nnz = orc.nnz()
+        t0 = time.perf_counter()
+        orc.apply(gates[done:done + 1], eps=EPS)
+        t += time.perf_counter() - t0
+        u += nnz
+        done += 1
+    return u, t, done
+
+
+def cpu_baseline(wl, budget_s: float):
+    u, t, done = oracle_rate(wl, budget_s)
+    return {"value": round(u / t, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d gates of %s, gate by gate, one host thread (%.1f s)" % (
+                done, len(wl["gates"]), wl["name"], t),
+            "cpu": cpu_model(), "nproc": os.cpu_count()}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_reference(args, dist, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    wl = make_workload(args.workload)
+    per_step = max(0.05, min(5.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_rate(wl, per_step)
+    us, ts, gates = 0, 0.0, 0
+    times = []
+    for _ in range(args.steps):
+        u, t, g = oracle_rate(wl, per_step)
+        us += u
+        ts += t
+        gates = g
+        times.append(t)
+    value = us / ts
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * ts / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "nqubits": wl["nqubits"],
+                       "parallelism": "single host thread"},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: the first %d gates of %s from |0..0>, gate by "
+                                       "gate" % (gates, wl["name"]), "cpu": cpu_model()},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="adder67",
+                    choices=["adder67", "adder67-w24", "givens64"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        # rank 0 alone times the host oracle; other ranks exit without work
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        res = run_reference(args, None, rank, world)
+        if rank == 0 and res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    dist, rank, world, local_rank = dist_init(args.gpus)
+    if True:
+        res = run_ours(args, dist, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

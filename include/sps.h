@@ -1,0 +1,217 @@
+/*
+ * sps.h - C ABI of libsps, a GB300 (sm_103a) library that applies quantum gate
+ * streams to a state held only as its nonzero (basis label, amplitude) pairs.
+ *
+ * Method: arXiv 2105.01533, "Leveraging state sparsity for more efficient
+ * quantum simulations".
+ *   Sec. 3    the state sum_b alpha_b |b> is stored as unordered (label b,
+ *             amplitude alpha_b) pairs with alpha_b != 0.
+ *   Sec. 2.1  |i> = |i_{n-1}> (x) ... (x) |i_0>: qubit k is bit k of a label;
+ *             gate matrices; CU = |0><0| (x) 1 + |1><1| (x) U.
+ *   Sec. 3.1  gates with two nonzeros per row act on a label pair (b, b') by a
+ *             2x2 matrix (Eq. 2); the result goes to a new container.
+ *   Sec. 3.2  runs of gates with one nonzero per row (phases, permutations)
+ *             compose as f1(b) f2(g1(b)) |g2(g1(b))> and are applied in one pass.
+ *
+ * Conventions for every entry point:
+ *   - Labels are 128-bit: key_lo holds qubits 0..63, key_hi qubits 64..127.
+ *     States of <= 63 qubits are stored with 64-bit labels; key_hi reads as 0.
+ *   - Amplitudes are IEEE binary64 (re, im) pairs.
+ *   - Pointers named "host or device" may point to pageable host memory,
+ *     pinned host memory or device memory of the state's device (unified
+ *     addressing decides); all others are host pointers unless stated.
+ *   - The library owns all device memory it allocates (see sps_set_allocator).
+ *   - Entry points return an sps_status; SPS_OK is 0. They never abort the
+ *     process and never leave a kernel spinning: every wait inside a kernel is
+ *     bounded and turns into an error code.
+ *   - A state is bound to the CUDA stream given at creation; all its work is
+ *     ordered on that stream. One state must not be used from two host threads
+ *     at once; distinct states are independent.
+ */
+#ifndef SPS_H
+#define SPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sps_status {
+  SPS_OK = 0,
+  SPS_ERR_ARG = 1,         /* bad argument or gate record (nothing was enqueued) */
+  SPS_ERR_CAPACITY = 2,    /* the state would exceed its capacity, or an output
+                              buffer is too small */
+  SPS_ERR_TABLE_FULL = 3,  /* the branching hash table hit its probe limit */
+  SPS_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  SPS_ERR_OOM = 5,         /* device allocation failed */
+  SPS_ERR_NO_DEVICE = 6    /* no usable CUDA device */
+} sps_status;
+
+/* Gate codes (sps_gate.op). Every gate takes any number of controls in
+ * sps_gate.cmask (Sec. 2.1 controlled gates); a control must not coincide with
+ * a target. Matrices are given in the basis (|0>, |1>) of the target.
+ *   one nonzero per row (Sec. 3.2 phase/permutation gates):
+ *     X [[0,1],[1,0]]   Y [[0,-i],[i,0]]   Z diag(1,-1)   S diag(1,i)
+ *     SDG diag(1,-i)    T diag(1,e^{i pi/4})   TDG diag(1,e^{-i pi/4})
+ *     P(theta) diag(1,e^{i theta})  (one control: controlled phase CP)
+ *     RZ(theta) = exp(-i theta Z/2) = diag(e^{-i theta/2}, e^{i theta/2})
+ *   two nonzeros per row (Sec. 3.1, Eq. 2):
+ *     H sqrt(0.5)[[1,1],[1,-1]]
+ *     RX(theta) = exp(-i theta X/2), RY(theta) = exp(-i theta Y/2)
+ *     GIVENS(theta) on qubits (p = t0, q = t1): on the span of the label with
+ *       bit p = 0, bit q = 1 (first) and the label with bit p = 1, bit q = 0
+ *       (second) it acts by [[cos theta, -sin theta], [sin theta, cos theta]];
+ *       labels with bit p == bit q are unchanged (number conserving).
+ */
+typedef enum sps_op {
+  SPS_OP_X = 1, SPS_OP_Y = 2, SPS_OP_Z = 3, SPS_OP_S = 4, SPS_OP_SDG = 5,
+  SPS_OP_T = 6, SPS_OP_TDG = 7, SPS_OP_P = 8, SPS_OP_RZ = 9,
+  SPS_OP_H = 10, SPS_OP_RX = 11, SPS_OP_RY = 12, SPS_OP_GIVENS = 13
+} sps_op;
+
+/* One gate, 32 bytes, little-endian. */
+typedef struct sps_gate {
+  uint8_t op;          /* sps_op */
+  uint8_t reserved0;   /* must be 0 */
+  uint16_t t0;         /* target qubit (GIVENS: p) */
+  uint16_t t1;         /* GIVENS: q; otherwise ignored */
+  uint16_t reserved1;  /* must be 0 */
+  uint64_t cmask[2];   /* control qubits: bit k of cmask[0] = qubit k,
+                          bit k of cmask[1] = qubit 64 + k */
+  double theta;        /* angle in radians (P, RZ, RX, RY, GIVENS) */
+} sps_gate;
+
+typedef struct sps_state sps_state; /* opaque, owned by the library */
+
+/* Device memory hook. alloc(ctx, bytes, stream) returns a device pointer
+ * aligned to >= 256 bytes or NULL; release(ctx, ptr, bytes, stream) frees it.
+ * Both are called on the thread that calls into the library, with the
+ * state's stream. Passing NULL for both restores the built-in allocator
+ * (cudaMallocAsync on the state's stream). Affects states created afterwards. */
+typedef void* (*sps_alloc_fn)(void* ctx, size_t bytes, void* stream);
+typedef void (*sps_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
+sps_status sps_set_allocator(sps_alloc_fn alloc, sps_free_fn release, void* ctx);
+
+/* Creates |0...0> on nqubits qubits (1..127) with room for `capacity`
+ * nonzeros (>= 1) on the current CUDA device. `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream). The state keeps two label/amplitude
+ * buffers of `capacity` entries (32 bytes each, 24 with 64-bit labels) and a
+ * branching table of 32-byte slots (see sps_set_option). *out receives the
+ * handle. Errors: SPS_ERR_ARG, SPS_ERR_OOM, SPS_ERR_CUDA, SPS_ERR_NO_DEVICE. */
+sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream,
+                      sps_state** out);
+
+/* Enqueues a reset to |0...0> on the state's stream (no host wait). Also
+ * clears a pending device-side error. */
+sps_status sps_reset(sps_state* s);
+
+/* Frees the state's device memory (after its stream's pending work). NULL ok. */
+void sps_destroy(sps_state* s);
+
+/* Applies `ngates` gates (host array, copied before return) in order, as one
+ * batch: each maximal run of one-nonzero-per-row gates becomes one in-place
+ * per-element pass (Sec. 3.2), each two-nonzero gate one branching pass
+ * (Sec. 3.1) after which entries with re*re + im*im < prune_eps^2 (strict) or
+ * exactly zero are dropped. prune_eps >= 0.
+ * The call only enqueues work on the state's stream. Records are validated on
+ * the host first: on a bad record it returns SPS_ERR_ARG, sets *failed_gate
+ * (if not NULL) to its index and enqueues nothing. Errors found on the device
+ * (SPS_ERR_CAPACITY, SPS_ERR_TABLE_FULL) are reported by the next sps_sync /
+ * sps_nnz / sps_get_amplitudes / sps_probability; passes after the failing one
+ * are skipped and the state is left exactly as it was before the failing pass. */
+sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates,
+                     double prune_eps, size_t* failed_gate);
+
+/* Waits for the state's stream. Returns the first device-side error since the
+ * last sync (and clears it, so the state is usable again, holding the result
+ * of the last pass that succeeded). If failed_gate is not NULL and an error is
+ * returned, it receives the index of the first gate of the failing pass within
+ * the gate array of the sps_apply call that enqueued it. */
+sps_status sps_sync(sps_state* s, size_t* failed_gate);
+
+/* Synchronises like sps_sync and writes the number of stored nonzeros. */
+sps_status sps_nnz(sps_state* s, uint64_t* nnz);
+
+/* Synchronises, then copies the state out in unspecified order: entry i is
+ * (key_hi[i], key_lo[i], re[i], im[i]). Each pointer is host or device memory
+ * of at least `cap` elements; key_hi may be NULL. *nnz_out receives the count;
+ * if it exceeds cap nothing is copied and SPS_ERR_CAPACITY is returned. */
+sps_status sps_get_amplitudes(sps_state* s, uint64_t* key_hi, uint64_t* key_lo,
+                              double* re, double* im, uint64_t cap, uint64_t* nnz_out);
+
+/* Replaces the state by n entries (host or device arrays; key_hi may be NULL
+ * for all-zero high words). Labels must be distinct and use only qubits below
+ * nqubits; amplitudes are taken as given. Errors: SPS_ERR_CAPACITY if
+ * n > capacity, SPS_ERR_ARG on a label outside the qubit range. */
+sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64_t* key_lo,
+                              const double* re, const double* im, uint64_t n);
+
+/* Synchronises, then writes *p = sum of |alpha_k|^2 over stored labels k with
+ * (k & mask) == value (mask/value: two words as in sps_gate.cmask). The sum is
+ * formed in a fixed order for a given state layout, so it is reproducible. */
+sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
+                           double* p);
+
+/* Tuning options (see sps_set_option). */
+typedef enum sps_option {
+  SPS_OPT_LOAD_FACTOR_PCT = 1, /* target branching-table load, 10..90 (default 50) */
+  SPS_OPT_PROBE_LIMIT = 2,     /* max slots probed per insert, >= 1 (default: table size) */
+  SPS_OPT_BLOCK_THREADS = 3,   /* threads per block of the per-element kernels: 128..1024 */
+  SPS_OPT_MAX_FUSED_OPS = 4,   /* longest op list of one fused pass, >= 1 (default 4096) */
+  SPS_OPT_COOP_WIDTH = 5,      /* lanes probing one insert together: 1, 2, 4 or 8 */
+  SPS_OPT_PROFILE = 6          /* 1: time every kernel launch with CUDA events on the
+                                  state's stream and log its entry counts; 0: off */
+} sps_option;
+
+/* Sets an option for subsequent sps_apply calls on this state. Errors:
+ * SPS_ERR_ARG for an unknown option or out-of-range value. */
+sps_status sps_set_option(sps_state* s, sps_option opt, int64_t value);
+
+/* Per-state counters since creation (host-side bookkeeping, no sync). */
+typedef struct sps_counters {
+  uint64_t gates;            /* gates accepted by sps_apply */
+  uint64_t fused_passes;     /* per-element phase/permutation passes enqueued */
+  uint64_t branch_passes;    /* branching passes enqueued */
+  uint64_t kernel_launches;  /* kernels enqueued by this state */
+} sps_counters;
+sps_status sps_get_counters(sps_state* s, sps_counters* out);
+
+/* One profiled kernel launch (SPS_OPT_PROFILE). kind: 1 fused phase /
+ * permutation pass, 2 branching emit, 3 branching compaction. n_in: entries
+ * the kernel read; n_out: entries in the state after it. flags: bit 0 the
+ * pass permutes labels, bit 1 it changes amplitudes. label_bytes: 8 or 16. */
+typedef struct sps_kernel_record {
+  uint32_t kind;
+  uint32_t pass_serial;
+  float ms;
+  uint32_t nops;
+  uint64_t n_in;
+  uint64_t n_out;
+  uint32_t flags;
+  uint32_t label_bytes;
+} sps_kernel_record;
+
+/* Synchronises, then moves up to `cap` records of profiled launches (oldest
+ * first) into out[] and *n; records that do not fit stay queued. */
+sps_status sps_profile_read(sps_state* s, sps_kernel_record* out, size_t cap, size_t* n);
+
+/* Host-only: compiles a gate list for an nqubits-qubit state and describes the
+ * passes without touching a GPU. For pass i: kind[i] = 1 (fused phase /
+ * permutation run) or 2 (branching gate), first_gate[i] = index of its first
+ * gate, ops[i] = number of device ops in the pass. At most `cap` passes are
+ * written; *npasses receives the total. max_fused_ops as in SPS_OPT_MAX_FUSED_OPS
+ * (0 = default). Errors: SPS_ERR_ARG with *failed_gate on a bad record. */
+sps_status sps_plan(const sps_gate* gates, size_t ngates, uint32_t nqubits,
+                    uint32_t max_fused_ops, uint32_t* kind, uint64_t* first_gate,
+                    uint32_t* ops, size_t cap, size_t* npasses, size_t* failed_gate);
+
+/* Static text for a status code. */
+const char* sps_status_str(sps_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPS_H */

@@ -1,0 +1,613 @@
+// C ABI of libsps (see include/sps.h). Host orchestration only: validation,
+// compilation into passes, buffer management and kernel enqueue. Every step of
+// the gate application runs in the kernels of sps_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "sps.h"
+#include "sps_internal.h"
+
+using namespace sps;
+
+namespace {
+
+std::mutex g_alloc_mu;
+sps_alloc_fn g_alloc = nullptr;
+sps_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+constexpr size_t kProfileCap = 1 << 16;   // profiled launches kept between reads
+
+struct Allocation {
+  void* ptr;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct sps_state {
+  uint32_t nqubits = 0;
+  int kw = 1;                 // label words: 1 (<= 63 qubits) or 2
+  uint64_t capacity = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+  // memory
+  sps_alloc_fn alloc = nullptr;
+  sps_free_fn release = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<Allocation> allocs;
+  Ctl* ctl = nullptr;
+  Ctl* ctl_host = nullptr;    // pinned mirror
+  Bufs bufs{};
+  Slot* table = nullptr;
+  uint32_t max_log2 = 8;
+  uint64_t table_slots = 0;
+  double* partials = nullptr;
+  double* dresult = nullptr;
+  double* hresult = nullptr;  // pinned
+  unsigned* dflag = nullptr;
+  unsigned* hflag = nullptr;  // pinned
+  int prob_blocks = 0;
+  // options
+  uint32_t load_pct = 50;
+  uint32_t probe_limit = 0;   // 0 = table size
+  int threads = 256;
+  uint32_t max_fused_ops = kDefaultMaxFusedOps;
+  int coop = 1;
+  // profiling (SPS_OPT_PROFILE)
+  bool profile = false;
+  unsigned long long* dlog = nullptr;      // 2 words per profiled launch
+  unsigned long long* hlog = nullptr;      // pinned copy
+  struct Pending {
+    cudaEvent_t start, stop;
+    uint32_t kind, pass_serial, nops, flags;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  // bookkeeping
+  uint64_t nnz_bound = 1;
+  uint32_t pass_serial = 0;
+  uint32_t apply_serial = 0;
+  sps_counters counters{};
+};
+
+namespace {
+
+void* default_alloc(void*, size_t bytes, void* stream) {
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void default_free(void*, void* p, size_t, void* stream) {
+  cudaFreeAsync(p, (cudaStream_t)stream);
+}
+
+sps_status dev_alloc(sps_state* s, size_t bytes, void** out) {
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = s->alloc(s->alloc_ctx, bytes, s->stream);
+  if (!p) return SPS_ERR_OOM;
+  s->allocs.push_back({p, bytes});
+  *out = p;
+  return SPS_OK;
+}
+
+void release_all(sps_state* s) {
+  cudaStreamSynchronize(s->stream);
+  for (auto& a : s->allocs) s->release(s->alloc_ctx, a.ptr, a.bytes, s->stream);
+  s->allocs.clear();
+  cudaStreamSynchronize(s->stream);
+  if (s->ctl_host) cudaFreeHost(s->ctl_host);
+  if (s->hresult) cudaFreeHost(s->hresult);
+  if (s->hflag) cudaFreeHost(s->hflag);
+  if (s->hlog) cudaFreeHost(s->hlog);
+  s->hlog = nullptr;
+  for (auto& p : s->pending) {
+    cudaEventDestroy(p.start);
+    cudaEventDestroy(p.stop);
+  }
+  s->pending.clear();
+  for (auto e : s->event_pool) cudaEventDestroy(e);
+  s->event_pool.clear();
+  s->ctl_host = nullptr;
+  s->hresult = nullptr;
+  s->hflag = nullptr;
+  cudaGetLastError();
+}
+
+LaunchCfg cfg_of(const sps_state* s) {
+  LaunchCfg lc;
+  lc.threads = s->threads;
+  lc.max_blocks = s->sms * (2048 / s->threads);
+  lc.stream = s->stream;
+  return lc;
+}
+
+sps_status cuda_ok(cudaError_t e) {
+  if (e == cudaSuccess) return SPS_OK;
+  cudaGetLastError();
+  return SPS_ERR_CUDA;
+}
+
+// Reads the control block after the stream drains.
+sps_status read_ctl(sps_state* s) {
+  if (cudaMemcpyAsync(s->ctl_host, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream) !=
+      cudaSuccess)
+    return cuda_ok(cudaGetLastError());
+  return cuda_ok(cudaStreamSynchronize(s->stream));
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void label_limits(uint32_t nq, uint64_t* lim0, uint64_t* lim1) {
+  *lim0 = nq >= 64 ? ~0ull : ((1ull << nq) - 1);
+  *lim1 = nq <= 64 ? 0ull : (nq >= 128 ? ~0ull : ((1ull << (nq - 64)) - 1));
+}
+
+cudaEvent_t take_event(sps_state* s) {
+  if (!s->event_pool.empty()) {
+    cudaEvent_t e = s->event_pool.back();
+    s->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Brackets one launch with events when profiling; returns the log slot or null.
+struct ProfScope {
+  sps_state* s;
+  sps_state::Pending rec{};
+  unsigned long long* slot = nullptr;
+  bool on = false;
+  ProfScope(sps_state* st, uint32_t kind, uint32_t serial, uint32_t nops, uint32_t flags) : s(st) {
+    if (!s->profile || s->pending.size() >= kProfileCap) return;
+    rec.start = take_event(s);
+    rec.stop = take_event(s);
+    if (!rec.start || !rec.stop) return;
+    rec.kind = kind;
+    rec.pass_serial = serial;
+    rec.nops = nops;
+    rec.flags = flags;
+    slot = s->dlog + 2 * s->pending.size();
+    on = cudaEventRecord(rec.start, s->stream) == cudaSuccess;
+  }
+  void done() {
+    if (!on) return;
+    if (cudaEventRecord(rec.stop, s->stream) == cudaSuccess) s->pending.push_back(rec);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* sps_status_str(sps_status st) {
+  switch (st) {
+    case SPS_OK: return "ok";
+    case SPS_ERR_ARG: return "invalid argument";
+    case SPS_ERR_CAPACITY: return "capacity exceeded";
+    case SPS_ERR_TABLE_FULL: return "hash table probe limit reached";
+    case SPS_ERR_CUDA: return "CUDA error";
+    case SPS_ERR_OOM: return "out of device memory";
+    case SPS_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+sps_status sps_set_allocator(sps_alloc_fn alloc, sps_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) return SPS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = release;
+  g_alloc_ctx = ctx;
+  return SPS_OK;
+}
+
+sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sps_state** out) {
+  if (!out) return SPS_ERR_ARG;
+  *out = nullptr;
+  if (nqubits < 1 || nqubits > 127 || capacity < 1 || capacity > (1ull << 34)) return SPS_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return SPS_ERR_NO_DEVICE;
+  }
+  sps_state* s = new (std::nothrow) sps_state;
+  if (!s) return SPS_ERR_OOM;
+  s->nqubits = nqubits;
+  s->kw = nqubits <= 63 ? 1 : 2;
+  s->capacity = capacity;
+  s->stream = (cudaStream_t)cuda_stream;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    s->alloc = g_alloc ? g_alloc : default_alloc;
+    s->release = g_alloc ? g_free : default_free;
+    s->alloc_ctx = g_alloc ? g_alloc_ctx : nullptr;
+  }
+  sps_status st = SPS_OK;
+  auto fail = [&](sps_status e) {
+    release_all(s);
+    delete s;
+    return e;
+  };
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SPS_ERR_CUDA);
+  }
+  // table: 2 * capacity labels at the default 50% load, power of two
+  s->max_log2 = table_log2_for(capacity, 50, 40);
+  s->table_slots = 1ull << s->max_log2;
+  s->prob_blocks = s->sms * 2 < 1024 ? s->sms * 2 : 1024;
+  void* p = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = dev_alloc(s, capacity * 8, &p)) != SPS_OK) return fail(st);
+    s->bufs.b[b].lo = (uint64_t*)p;
+    if (s->kw == 2) {
+      if ((st = dev_alloc(s, capacity * 8, &p)) != SPS_OK) return fail(st);
+      s->bufs.b[b].hi = (uint64_t*)p;
+    }
+    if ((st = dev_alloc(s, capacity * 8, &p)) != SPS_OK) return fail(st);
+    s->bufs.b[b].re = (double*)p;
+    if ((st = dev_alloc(s, capacity * 8, &p)) != SPS_OK) return fail(st);
+    s->bufs.b[b].im = (double*)p;
+  }
+  if ((st = dev_alloc(s, s->table_slots * sizeof(Slot), &p)) != SPS_OK) return fail(st);
+  s->table = (Slot*)p;
+  if ((st = dev_alloc(s, sizeof(Ctl), &p)) != SPS_OK) return fail(st);
+  s->ctl = (Ctl*)p;
+  if ((st = dev_alloc(s, sizeof(double) * (s->prob_blocks + 1), &p)) != SPS_OK) return fail(st);
+  s->partials = (double*)p;
+  s->dresult = s->partials + s->prob_blocks;
+  if ((st = dev_alloc(s, 256, &p)) != SPS_OK) return fail(st);
+  s->dflag = (unsigned*)p;
+  if ((st = dev_alloc(s, 2 * sizeof(unsigned long long) * kProfileCap, &p)) != SPS_OK) return fail(st);
+  s->dlog = (unsigned long long*)p;
+  if (cudaMallocHost((void**)&s->ctl_host, sizeof(Ctl)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->hresult, sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->hflag, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->hlog, 2 * sizeof(unsigned long long) * kProfileCap) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SPS_ERR_OOM);
+  }
+  // |0...0>: one entry (label 0, amplitude 1)
+  static const double kOne = 1.0;
+  SoA b0 = s->bufs.b[0];
+  bool ok = cudaMemsetAsync(b0.lo, 0, 8, s->stream) == cudaSuccess &&
+            (s->kw == 1 || cudaMemsetAsync(b0.hi, 0, 8, s->stream) == cudaSuccess) &&
+            cudaMemcpyAsync(b0.re, &kOne, 8, cudaMemcpyHostToDevice, s->stream) == cudaSuccess &&
+            cudaMemsetAsync(b0.im, 0, 8, s->stream) == cudaSuccess &&
+            cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), s->stream) == cudaSuccess;
+  if (!ok) return fail(SPS_ERR_CUDA);
+  LaunchCfg lc = cfg_of(s);
+  if (launch_table_clear(lc, s->table, s->table_slots) < 0 || launch_set_nnz(s->stream, s->ctl, 1) < 0)
+    return fail(SPS_ERR_CUDA);
+  s->counters.kernel_launches += 2;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(cuda_ok(cudaGetLastError()));
+  s->nnz_bound = 1;
+  *out = s;
+  return SPS_OK;
+}
+
+sps_status sps_reset(sps_state* s) {
+  if (!s) return SPS_ERR_ARG;
+  if (launch_reset_state(s->stream, s->kw, s->ctl, s->bufs) < 0) return cuda_ok(cudaGetLastError());
+  s->counters.kernel_launches += 1;
+  s->nnz_bound = 1;
+  return SPS_OK;
+}
+
+sps_status sps_profile_read(sps_state* s, sps_kernel_record* out, size_t cap, size_t* n) {
+  if (!s || !n || (cap && !out)) return SPS_ERR_ARG;
+  sps_status st = cuda_ok(cudaStreamSynchronize(s->stream));
+  if (st != SPS_OK) return st;
+  const size_t have = s->pending.size();
+  if (have &&
+      cudaMemcpy(s->hlog, s->dlog, 2 * sizeof(unsigned long long) * have, cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+    return cuda_ok(cudaGetLastError());
+  const size_t take = have < cap ? have : cap;
+  for (size_t i = 0; i < take; ++i) {
+    const auto& p = s->pending[i];
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.start, p.stop) != cudaSuccess) {
+      cudaGetLastError();
+      ms = -1.0f;
+    }
+    out[i].kind = p.kind;
+    out[i].pass_serial = p.pass_serial;
+    out[i].ms = ms;
+    out[i].nops = p.nops;
+    out[i].n_in = s->hlog[2 * i];
+    out[i].n_out = s->hlog[2 * i + 1];
+    out[i].flags = p.flags;
+    out[i].label_bytes = 8u * (uint32_t)s->kw;
+    s->event_pool.push_back(p.start);
+    s->event_pool.push_back(p.stop);
+  }
+  // keep the rest queued, with their log words moved to the front
+  if (take < have) {
+    const size_t rest = have - take;
+    if (cudaMemcpy(s->dlog, s->hlog + 2 * take, 2 * sizeof(unsigned long long) * rest,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return cuda_ok(cudaGetLastError());
+  }
+  s->pending.erase(s->pending.begin(), s->pending.begin() + take);
+  *n = take;
+  return SPS_OK;
+}
+
+void sps_destroy(sps_state* s) {
+  if (!s) return;
+  release_all(s);
+  delete s;
+}
+
+sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
+                     size_t* failed_gate) {
+  if (!s || (ngates && !gates) || !(prune_eps >= 0.0)) return SPS_ERR_ARG;
+  std::vector<Pass> passes;
+  size_t bad = 0;
+  const sps_status cs = compile(gates, ngates, s->nqubits, s->max_fused_ops, &passes, &bad);
+  if (cs != SPS_OK) {
+    if (failed_gate) *failed_gate = bad;
+    return cs;
+  }
+  const LaunchCfg lc = cfg_of(s);
+  const uint32_t limit = s->probe_limit ? s->probe_limit : (uint32_t)(s->table_slots > 0xFFFFFFFFull ? 0xFFFFFFFFu : s->table_slots);
+  ++s->apply_serial;
+  for (const Pass& p : passes) {
+    const uint32_t serial = ++s->pass_serial;
+    const uint64_t tag = ((uint64_t)s->apply_serial << 32) | (p.first_gate & 0xFFFFFFFFull);
+    if (p.kind == PASS_FUSED) {
+      const uint32_t flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
+      ProfScope ps(s, 1, serial, (uint32_t)p.ops.size(), flags);
+      const int n = launch_fused(lc, s->kw, s->ctl, s->bufs, p, s->nnz_bound, ps.slot);
+      ps.done();
+      if (n < 0) return cuda_ok(cudaGetLastError());
+      s->counters.fused_passes++;
+      s->counters.kernel_launches += (uint64_t)n;
+    } else {
+      BranchLaunch b;
+      b.op = p.br;
+      b.eps = prune_eps;
+      b.load_pct = s->load_pct;
+      b.max_log2 = s->max_log2;
+      b.probe_limit = limit;
+      b.pass_serial = serial;
+      b.coop = s->coop;
+      b.capacity = s->capacity;
+      b.fail_tag = tag;
+      {
+        ProfScope ps(s, 2, serial, 1, 3u);
+        const int n = launch_branch_emit(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
+        ps.done();
+        if (n < 0) return cuda_ok(cudaGetLastError());
+      }
+      {
+        ProfScope ps(s, 3, serial, 1, 3u);
+        const int n = launch_branch_compact(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
+        ps.done();
+        if (n < 0) return cuda_ok(cudaGetLastError());
+      }
+      s->counters.branch_passes++;
+      s->counters.kernel_launches += 2;
+      const uint64_t nb = s->nnz_bound * 2;
+      s->nnz_bound = nb < s->capacity ? nb : s->capacity;
+    }
+  }
+  s->counters.gates += ngates;
+  return SPS_OK;
+}
+
+sps_status sps_sync(sps_state* s, size_t* failed_gate) {
+  if (!s) return SPS_ERR_ARG;
+  sps_status st = read_ctl(s);
+  if (st != SPS_OK) return st;
+  const Ctl c = *s->ctl_host;
+  s->nnz_bound = c.nnz > 0 ? c.nnz : 1;
+  if (c.status == 0u) return SPS_OK;
+  if (failed_gate) *failed_gate = (size_t)(c.fail_gate & 0xFFFFFFFFull);
+  // recover: clear the error and the table; the state is the last good one
+  const LaunchCfg lc = cfg_of(s);
+  if (launch_reset_status(s->stream, s->ctl) < 0 ||
+      launch_table_clear(lc, s->table, s->table_slots) < 0)
+    return cuda_ok(cudaGetLastError());
+  s->counters.kernel_launches += 2;
+  st = cuda_ok(cudaStreamSynchronize(s->stream));
+  if (st != SPS_OK) return st;
+  return (sps_status)c.status;
+}
+
+sps_status sps_nnz(sps_state* s, uint64_t* nnz) {
+  if (!s || !nnz) return SPS_ERR_ARG;
+  const sps_status st = sps_sync(s, nullptr);
+  if (st != SPS_OK) return st;
+  *nnz = s->ctl_host->nnz;
+  return SPS_OK;
+}
+
+sps_status sps_get_amplitudes(sps_state* s, uint64_t* key_hi, uint64_t* key_lo, double* re,
+                              double* im, uint64_t cap, uint64_t* nnz_out) {
+  if (!s || !key_lo || !re || !im || !nnz_out) return SPS_ERR_ARG;
+  sps_status st = sps_sync(s, nullptr);
+  if (st != SPS_OK) return st;
+  const uint64_t n = s->ctl_host->nnz;
+  *nnz_out = n;
+  if (n > cap) return SPS_ERR_CAPACITY;
+  if (n == 0) return SPS_OK;
+  const SoA b = s->bufs.b[s->ctl_host->cur];
+  bool ok = cudaMemcpyAsync(key_lo, b.lo, n * 8, cudaMemcpyDefault, s->stream) == cudaSuccess &&
+            cudaMemcpyAsync(re, b.re, n * 8, cudaMemcpyDefault, s->stream) == cudaSuccess &&
+            cudaMemcpyAsync(im, b.im, n * 8, cudaMemcpyDefault, s->stream) == cudaSuccess;
+  if (ok && key_hi) {
+    if (s->kw == 2) {
+      ok = cudaMemcpyAsync(key_hi, b.hi, n * 8, cudaMemcpyDefault, s->stream) == cudaSuccess;
+    } else if (is_device_pointer(key_hi)) {
+      ok = cudaMemsetAsync(key_hi, 0, n * 8, s->stream) == cudaSuccess;
+    } else {
+      std::memset(key_hi, 0, n * 8);
+    }
+  }
+  if (!ok) return cuda_ok(cudaGetLastError());
+  return cuda_ok(cudaStreamSynchronize(s->stream));
+}
+
+sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64_t* key_lo,
+                              const double* re, const double* im, uint64_t n) {
+  if (!s || (n && (!key_lo || !re || !im))) return SPS_ERR_ARG;
+  if (n > s->capacity) return SPS_ERR_CAPACITY;
+  sps_status st = sps_sync(s, nullptr);
+  if (st != SPS_OK) return st;
+  const SoA b = s->bufs.b[0];
+  bool ok = true;
+  if (n) {
+    ok = cudaMemcpyAsync(b.lo, key_lo, n * 8, cudaMemcpyDefault, s->stream) == cudaSuccess &&
+         cudaMemcpyAsync(b.re, re, n * 8, cudaMemcpyDefault, s->stream) == cudaSuccess &&
+         cudaMemcpyAsync(b.im, im, n * 8, cudaMemcpyDefault, s->stream) == cudaSuccess;
+    if (ok && s->kw == 2) {
+      ok = key_hi ? cudaMemcpyAsync(b.hi, key_hi, n * 8, cudaMemcpyDefault, s->stream) == cudaSuccess
+                  : cudaMemsetAsync(b.hi, 0, n * 8, s->stream) == cudaSuccess;
+    }
+  }
+  if (!ok) return cuda_ok(cudaGetLastError());
+  uint64_t lim0, lim1;
+  label_limits(s->nqubits, &lim0, &lim1);
+  // For 64-bit labels the high words must be zero: check them from the spare buffer.
+  Bufs chk = s->bufs;
+  if (s->kw == 1 && key_hi && n) {
+    if (cudaMemcpyAsync(s->bufs.b[1].lo, key_hi, n * 8, cudaMemcpyDefault, s->stream) != cudaSuccess)
+      return cuda_ok(cudaGetLastError());
+  }
+  if (launch_set_nnz(s->stream, s->ctl, n) < 0 ||
+      cudaMemsetAsync(s->dflag, 0, sizeof(unsigned), s->stream) != cudaSuccess ||
+      launch_check_labels(s->stream, s->kw, s->ctl, chk, lim0, lim1, s->dflag, n) < 0)
+    return cuda_ok(cudaGetLastError());
+  int launched = 2;
+  if (s->kw == 1 && key_hi && n) {
+    // labels in bufs[1].lo are the high words; every one must be zero
+    Bufs hib = s->bufs;
+    hib.b[0].lo = s->bufs.b[1].lo;
+    if (launch_check_labels(s->stream, 1, s->ctl, hib, 0ull, 0ull, s->dflag, n) < 0)
+      return cuda_ok(cudaGetLastError());
+    ++launched;
+  }
+  s->counters.kernel_launches += launched;
+  if (cudaMemcpyAsync(s->hflag, s->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream) !=
+      cudaSuccess)
+    return cuda_ok(cudaGetLastError());
+  st = cuda_ok(cudaStreamSynchronize(s->stream));
+  if (st != SPS_OK) return st;
+  s->nnz_bound = n ? n : 1;
+  if (*s->hflag) {
+    // reject: fall back to |0...0>
+    static const double kOne = 1.0;
+    ok = cudaMemsetAsync(b.lo, 0, 8, s->stream) == cudaSuccess &&
+         (s->kw == 1 || cudaMemsetAsync(b.hi, 0, 8, s->stream) == cudaSuccess) &&
+         cudaMemcpyAsync(b.re, &kOne, 8, cudaMemcpyHostToDevice, s->stream) == cudaSuccess &&
+         cudaMemsetAsync(b.im, 0, 8, s->stream) == cudaSuccess && launch_set_nnz(s->stream, s->ctl, 1) >= 0 &&
+         cudaStreamSynchronize(s->stream) == cudaSuccess;
+    s->nnz_bound = 1;
+    s->counters.kernel_launches += 1;
+    return ok ? SPS_ERR_ARG : cuda_ok(cudaGetLastError());
+  }
+  return SPS_OK;
+}
+
+sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t value[2], double* p) {
+  if (!s || !mask || !value || !p) return SPS_ERR_ARG;
+  sps_status st = sps_sync(s, nullptr);
+  if (st != SPS_OK) return st;
+  const LaunchCfg lc = cfg_of(s);
+  if (launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0], value[1],
+                         s->partials, s->prob_blocks, s->dresult) < 0)
+    return cuda_ok(cudaGetLastError());
+  s->counters.kernel_launches += 2;
+  if (cudaMemcpyAsync(s->hresult, s->dresult, sizeof(double), cudaMemcpyDeviceToHost, s->stream) !=
+      cudaSuccess)
+    return cuda_ok(cudaGetLastError());
+  st = cuda_ok(cudaStreamSynchronize(s->stream));
+  if (st != SPS_OK) return st;
+  *p = *s->hresult;
+  return SPS_OK;
+}
+
+sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
+  if (!s) return SPS_ERR_ARG;
+  switch (opt) {
+    case SPS_OPT_LOAD_FACTOR_PCT:
+      if (v < 10 || v > 90) return SPS_ERR_ARG;
+      s->load_pct = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_PROBE_LIMIT:
+      if (v < 0 || v > 0xFFFFFFFFll) return SPS_ERR_ARG;
+      s->probe_limit = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_BLOCK_THREADS:
+      if (v != 128 && v != 256) return SPS_ERR_ARG;
+      s->threads = (int)v;
+      return SPS_OK;
+    case SPS_OPT_MAX_FUSED_OPS:
+      if (v < 1 || v > (int64_t)kMaxFusedOps) return SPS_ERR_ARG;
+      s->max_fused_ops = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_PROFILE:
+      if (v != 0 && v != 1) return SPS_ERR_ARG;
+      s->profile = v == 1;
+      return SPS_OK;
+    case SPS_OPT_COOP_WIDTH:
+      if (v != 1 && v != 2 && v != 4 && v != 8) return SPS_ERR_ARG;
+      s->coop = (int)v;
+      return SPS_OK;
+  }
+  return SPS_ERR_ARG;
+}
+
+sps_status sps_get_counters(sps_state* s, sps_counters* out) {
+  if (!s || !out) return SPS_ERR_ARG;
+  *out = s->counters;
+  return SPS_OK;
+}
+
+sps_status sps_plan(const sps_gate* gates, size_t ngates, uint32_t nqubits, uint32_t max_fused_ops,
+                    uint32_t* kind, uint64_t* first_gate, uint32_t* ops, size_t cap,
+                    size_t* npasses, size_t* failed_gate) {
+  if ((ngates && !gates) || !npasses || nqubits < 1 || nqubits > 127) return SPS_ERR_ARG;
+  std::vector<Pass> passes;
+  size_t bad = 0;
+  const sps_status st = compile(gates, ngates, nqubits, max_fused_ops, &passes, &bad);
+  if (st != SPS_OK) {
+    if (failed_gate) *failed_gate = bad;
+    return st;
+  }
+  *npasses = passes.size();
+  for (size_t i = 0; i < passes.size() && i < cap; ++i) {
+    if (kind) kind[i] = passes[i].kind;
+    if (first_gate) first_gate[i] = passes[i].first_gate;
+    if (ops) ops[i] = passes[i].kind == PASS_FUSED ? (uint32_t)passes[i].ops.size() : 1u;
+  }
+  return SPS_OK;
+}
+
+}  // extern "C"

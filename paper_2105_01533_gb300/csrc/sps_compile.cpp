@@ -1,0 +1,180 @@
+// Gate-batch compiler (host). Splits a gate stream at every two-nonzero gate
+// (Sec. 3.1) and turns each maximal run of one-nonzero gates into one op list
+// applied per element in a single pass (Sec. 3.2, composition of (f, g) pairs).
+// Angles are turned into cos/sin here, once, with the host libm, so the device
+// evaluates no transcendental function.
+#include <cmath>
+#include <cstring>
+
+#include "sps_internal.h"
+
+namespace sps {
+namespace {
+
+struct Mask128 {
+  uint64_t w[2] = {0, 0};
+  void set(uint32_t q) { w[q >> 6] |= 1ull << (q & 63); }
+  bool has(uint32_t q) const { return (w[q >> 6] >> (q & 63)) & 1ull; }
+};
+
+bool in_range(const uint64_t m[2], uint32_t nq) {
+  const uint64_t lim0 = nq >= 64 ? ~0ull : ((1ull << nq) - 1);
+  const uint64_t lim1 = nq <= 64 ? 0ull : (nq >= 128 ? ~0ull : ((1ull << (nq - 64)) - 1));
+  return (m[0] & ~lim0) == 0 && (m[1] & ~lim1) == 0;
+}
+
+bool is_branch(uint8_t op) {
+  return op == SPS_OP_H || op == SPS_OP_RX || op == SPS_OP_RY || op == SPS_OP_GIVENS;
+}
+
+bool check(const sps_gate& g, uint32_t nq) {
+  if (g.op < SPS_OP_X || g.op > SPS_OP_GIVENS) return false;
+  if (g.reserved0 != 0 || g.reserved1 != 0) return false;
+  if (g.t0 >= nq || !in_range(g.cmask, nq)) return false;
+  if ((g.cmask[g.t0 >> 6] >> (g.t0 & 63)) & 1ull) return false;
+  if (g.op == SPS_OP_GIVENS) {
+    if (g.t1 >= nq || g.t1 == g.t0) return false;
+    if ((g.cmask[g.t1 >> 6] >> (g.t1 & 63)) & 1ull) return false;
+  }
+  if (!std::isfinite(g.theta)) return false;
+  return true;
+}
+
+FOp make_op(const uint64_t cmask[2]) {
+  FOp o;
+  std::memset(&o, 0, sizeof(o));
+  o.c[0] = cmask[0];
+  o.c[1] = cmask[1];
+  o.sbit = NO_SEL;
+  o.ph = NO_PH;
+  return o;
+}
+
+// Appends the ops of one phase/permutation gate to the pass.
+void lower_perm_diag(const sps_gate& g, Pass* p) {
+  Mask128 tgt;
+  tgt.set(g.t0);
+  FOp o = make_op(g.cmask);
+  switch (g.op) {
+    case SPS_OP_X:   // flip the target
+      o.t[0] = tgt.w[0]; o.t[1] = tgt.w[1];
+      p->has_perm = true;
+      break;
+    case SPS_OP_Y:   // |0> -> i|1>, |1> -> -i|0>: phase by the old bit, then flip
+      o.t[0] = tgt.w[0]; o.t[1] = tgt.w[1];
+      o.sbit = static_cast<uint8_t>(g.t0);
+      o.a0 = 2; o.a1 = 6;
+      p->has_perm = p->has_phase = true;
+      break;
+    case SPS_OP_Z: case SPS_OP_S: case SPS_OP_SDG: case SPS_OP_T: case SPS_OP_TDG: {
+      // diag(1, e^{i pi a / 4}): condition = controls and the target bit
+      o.c[0] |= tgt.w[0]; o.c[1] |= tgt.w[1];
+      const uint8_t steps[] = {0, 0, 0, 4, 2, 6, 1, 7};
+      o.a0 = steps[g.op];
+      p->has_phase = true;
+      break;
+    }
+    case SPS_OP_P: {  // diag(1, e^{i theta})
+      o.c[0] |= tgt.w[0]; o.c[1] |= tgt.w[1];
+      PhasePair pp{std::cos(g.theta), std::sin(g.theta), 1.0, 0.0};
+      o.ph = static_cast<uint16_t>(p->phases.size());
+      p->phases.push_back(pp);
+      p->has_phase = true;
+      break;
+    }
+    case SPS_OP_RZ: {  // diag(e^{-i theta/2}, e^{i theta/2}) selected by the target bit
+      const double c = std::cos(0.5 * g.theta), s = std::sin(0.5 * g.theta);
+      PhasePair pp{c, -s, c, s};
+      o.sbit = static_cast<uint8_t>(g.t0);
+      o.ph = static_cast<uint16_t>(p->phases.size());
+      p->phases.push_back(pp);
+      p->has_phase = true;
+      break;
+    }
+    default:
+      break;
+  }
+  p->ops.push_back(o);
+}
+
+void lower_branch(const sps_gate& g, Pass* p) {
+  BranchOp& b = p->br;
+  std::memset(&b, 0, sizeof(b));
+  b.c[0] = g.cmask[0];
+  b.c[1] = g.cmask[1];
+  Mask128 m;
+  m.set(g.t0);
+  b.sbit = g.t0;
+  if (g.op == SPS_OP_GIVENS) {
+    m.set(g.t1);
+    b.qbit = g.t1;
+    b.givens = 1;
+  }
+  b.m[0] = m.w[0];
+  b.m[1] = m.w[1];
+  const double r = std::sqrt(0.5);
+  const double c = std::cos(0.5 * g.theta), s = std::sin(0.5 * g.theta);
+  double mr[2][2] = {{1, 0}, {0, 1}}, mi[2][2] = {{0, 0}, {0, 0}};
+  b.real_m = 1;
+  switch (g.op) {
+    case SPS_OP_H:
+      mr[0][0] = r; mr[0][1] = r; mr[1][0] = r; mr[1][1] = -r;
+      break;
+    case SPS_OP_RX:   // [[c, -i s], [-i s, c]]
+      mr[0][0] = c; mr[1][1] = c; mr[0][1] = 0; mr[1][0] = 0;
+      mi[0][1] = -s; mi[1][0] = -s;
+      b.real_m = 0;
+      break;
+    case SPS_OP_RY:   // [[c, -s], [s, c]]
+      mr[0][0] = c; mr[0][1] = -s; mr[1][0] = s; mr[1][1] = c;
+      break;
+    case SPS_OP_GIVENS: {
+      const double cg = std::cos(g.theta), sg = std::sin(g.theta);
+      mr[0][0] = cg; mr[0][1] = -sg; mr[1][0] = sg; mr[1][1] = cg;
+      break;
+    }
+    default:
+      break;
+  }
+  std::memcpy(b.m_re, mr, sizeof(mr));
+  std::memcpy(b.m_im, mi, sizeof(mi));
+}
+
+}  // namespace
+
+sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
+                   uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad) {
+  if (max_fused_ops == 0 || max_fused_ops > kMaxFusedOps) max_fused_ops = kDefaultMaxFusedOps;
+  out->clear();
+  for (size_t i = 0; i < ngates; ++i) {
+    if (!check(gates[i], nqubits)) {
+      if (bad) *bad = i;
+      out->clear();
+      return SPS_ERR_ARG;
+    }
+  }
+  Pass* run = nullptr;
+  for (size_t i = 0; i < ngates; ++i) {
+    const sps_gate& g = gates[i];
+    if (is_branch(g.op)) {
+      run = nullptr;
+      Pass p;
+      p.kind = PASS_BRANCH;
+      p.first_gate = i;
+      lower_branch(g, &p);
+      out->push_back(std::move(p));
+      continue;
+    }
+    if (run == nullptr || run->ops.size() >= max_fused_ops || run->phases.size() >= kMaxFusedPhases) {
+      Pass p;
+      p.kind = PASS_FUSED;
+      p.first_gate = i;
+      out->push_back(std::move(p));
+      run = &out->back();
+    }
+    lower_perm_diag(g, run);
+  }
+  return SPS_OK;
+}
+
+}  // namespace sps

@@ -1,0 +1,156 @@
+// Internal types shared by the host compiler, the kernels and the C ABI layer
+// of libsps. Nothing here is part of the public interface (include/sps.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "sps.h"
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __align__(n) alignas(n)
+#endif
+
+namespace sps {
+
+// ---- compiled per-element op (Sec. 3.2) --------------------------------------
+// A run of one-nonzero-per-row gates maps alpha_b |b> to f(b) alpha_b |g(b)>;
+// composing gates is applying their ops in order to the running label:
+//   if ((k & c) == c) {
+//     sel  = (sbit == NO_SEL) ? 0 : bit sbit of k
+//     cnt += sel ? a1 : a0                      // phase e^{i pi cnt / 4}
+//     if (ph != NO_PH) acc *= phase[ph][sel]    // arbitrary-angle phase
+//     k   ^= t                                  // permutation
+//   }
+// Phases are read before the flip, i.e. from the label the gate acts on.
+constexpr uint8_t NO_SEL = 0xFF;
+constexpr uint16_t NO_PH = 0xFFFF;
+
+struct FOp {            // 48 bytes
+  uint64_t c[2];        // condition mask: all these bits must be 1
+  uint64_t t[2];        // xor mask applied when the condition holds
+  uint8_t a0, a1;       // pi/4 steps added when sel = 0 / 1 (mod 8)
+  uint8_t sbit;         // selector qubit or NO_SEL
+  uint8_t reserved;
+  uint16_t ph;          // index into the pass's phase pairs or NO_PH
+  uint16_t reserved2;
+  uint64_t reserved3;
+};
+static_assert(sizeof(FOp) == 48, "FOp layout");
+
+struct PhasePair { double re0, im0, re1, im1; };   // phase for sel = 0, sel = 1
+
+// ---- branching gate (Sec. 3.1, Eq. 2) ----------------------------------------
+// For a label k with controls satisfied (and, for Givens, bit p != bit q) the
+// pair is k0 = (x ? k ^ m : k), k1 = (x ? k : k ^ m) with x = bit sbit of k;
+// k contributes M[0][x] a to k0 and M[1][x] a to k1. Otherwise k keeps a.
+struct BranchOp {
+  uint64_t c[2];        // controls
+  uint64_t m[2];        // flip mask: one bit, or bits p and q for Givens
+  uint32_t sbit;        // selector qubit (target, or p for Givens)
+  uint32_t qbit;        // Givens: q; otherwise unused
+  uint32_t givens;      // 1: also require bit p != bit q
+  uint32_t real_m;      // 1: every entry of M is real
+  double m_re[2][2];
+  double m_im[2][2];
+};
+
+// ---- a compiled pass -----------------------------------------------------------
+enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2 };
+
+struct Pass {
+  PassKind kind;
+  uint64_t first_gate;
+  // fused
+  std::vector<FOp> ops;
+  std::vector<PhasePair> phases;
+  bool has_perm = false;    // some op flips label bits
+  bool has_phase = false;   // some op changes amplitudes
+  // branch
+  BranchOp br{};
+};
+
+// Op lists travel as kernel parameters (<= 32 KB), which bounds one fused pass.
+constexpr uint32_t kMaxFusedOps = 512;
+constexpr uint32_t kMaxFusedPhases = 96;
+constexpr uint32_t kDefaultMaxFusedOps = kMaxFusedOps;
+
+// Validates and compiles; on a bad record returns SPS_ERR_ARG with *bad set.
+sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
+                   uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad);
+
+// ---- device-side control block -------------------------------------------------
+struct Ctl {
+  unsigned long long nnz;        // entries in the current buffer
+  unsigned long long out_count;  // compaction output counter of the running pass
+  unsigned int cur;              // which of the two buffers holds the state
+  unsigned int status;           // first device-side error (sps_status), 0 = none
+  unsigned int fail_pass;        // pass serial of the failing pass
+  unsigned int blocks_done;      // last-block detection in the compaction
+  unsigned long long fail_gate;  // (apply serial << 32) | first gate of failing pass
+  unsigned long long reserved[3];
+};
+
+struct SoA {
+  uint64_t* lo;
+  uint64_t* hi;   // unused (may be null) for 64-bit labels
+  double* re;
+  double* im;
+};
+
+struct Bufs { SoA b[2]; };
+
+struct __align__(32) Slot {
+  uint64_t lo, hi;
+  double re, im;
+};
+
+constexpr uint64_t EMPTY = ~0ull;   // label bit 127 (or 63) is never set
+
+// Table size for a branching pass with n_in input entries (both kernels of the
+// pass compute it from the same n_in, so they agree without a host round trip).
+__host__ __device__ inline uint32_t table_log2_for(unsigned long long n_in, uint32_t load_pct,
+                                                   uint32_t max_log2) {
+  const unsigned long long need = (2ull * n_in * 100ull + load_pct - 1) / load_pct;
+  uint32_t lg = 8;
+  while (lg < max_log2 && (1ull << lg) < need) ++lg;
+  return lg;
+}
+
+// ---- kernel launchers (sps_kernels.cu) -----------------------------------------
+struct LaunchCfg {
+  int threads;
+  int max_blocks;
+  void* stream;
+};
+
+// All launchers return the number of kernels enqueued, or -1 on a launch error.
+// `plog` (nullable) receives two words per launch for profiling: entries read
+// and entries in the state afterwards.
+int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots);
+int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
+                 uint64_t nnz_bound, unsigned long long* plog);
+struct BranchLaunch {
+  BranchOp op;
+  double eps;
+  uint32_t load_pct, max_log2, probe_limit, pass_serial;
+  int coop;
+  uint64_t capacity, fail_tag;
+};
+int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,
+                       const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog);
+int launch_branch_compact(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,
+                          const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog);
+int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
+                       uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
+                       double* partials, int nblocks, double* result);
+int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz);
+int launch_reset_state(void* stream, int key_words, Ctl* ctl, Bufs bufs);
+int launch_check_labels(void* stream, int key_words, const Ctl* ctl, Bufs bufs,
+                        uint64_t lim_lo, uint64_t lim_hi, unsigned int* bad_flag, uint64_t n);
+int launch_reset_status(void* stream, Ctl* ctl);
+
+}  // namespace sps

@@ -1,0 +1,585 @@
+// CUDA kernels of libsps (sm_103a). No tensor cores: nothing on this path is a
+// dense contraction. Every kernel is a grid-stride loop over a count it reads
+// from the device control block, so the host never waits for a count.
+//
+//   k_fused          one pass per run of phase/permutation gates (Sec. 3.2):
+//                    per element, run the op list on the label in registers,
+//                    accumulate the phase, write back in place (a bijection
+//                    keeps labels distinct, so no table is needed).
+//   k_table_clear    sets table slots to EMPTY (creation and error recovery;
+//                    the compaction leaves the table clean otherwise).
+//   k_branch_emit    one two-nonzero gate (Sec. 3.1, Eq. 2): every element
+//                    scatters its one or two contributions into an
+//                    open-addressing table with 128-bit labels (claim by CAS,
+//                    accumulate with FP64 atomic adds).
+//   k_branch_compact walks the table, drops exact zeros and entries with
+//                    re^2 + im^2 < eps^2, writes survivors to the other buffer
+//                    (warp ballot + block scan + one atomic per block), cleans
+//                    the slots it read and, in the last block, publishes the new
+//                    count and flips the buffers.
+//   k_probability    sum of |a|^2 over labels matching (mask, value) with a
+//                    fixed-order two-level reduction.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sps_internal.h"
+
+namespace sps {
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+struct K128 {
+  uint64_t lo, hi;
+};
+struct __align__(16) K128a {
+  uint64_t lo, hi;
+};
+
+// Buffer selection without indexing the parameter struct dynamically (which
+// would copy it to local memory).
+__device__ __forceinline__ SoA pick(const Bufs& b, unsigned cur) {
+  SoA s;
+  s.lo = cur ? b.b[1].lo : b.b[0].lo;
+  s.hi = cur ? b.b[1].hi : b.b[0].hi;
+  s.re = cur ? b.b[1].re : b.b[0].re;
+  s.im = cur ? b.b[1].im : b.b[0].im;
+  return s;
+}
+
+__device__ __forceinline__ bool label_bit(uint64_t k0, uint64_t k1, uint32_t q) {
+  return q < 64 ? ((k0 >> q) & 1ull) : ((k1 >> (q - 64)) & 1ull);
+}
+
+__device__ __forceinline__ void fail(Ctl* ctl, unsigned code, uint32_t pass_serial,
+                                     uint64_t fail_tag) {
+  if (atomicCAS(&ctl->status, 0u, code) == 0u) {
+    ctl->fail_pass = pass_serial;
+    ctl->fail_gate = fail_tag;
+  }
+}
+
+// murmur3 64-bit finaliser
+__device__ __forceinline__ uint64_t fmix64(uint64_t z) {
+  z ^= z >> 33;
+  z *= 0xff51afd7ed558ccdull;
+  z ^= z >> 33;
+  z *= 0xc4ceb9fe1a85ec53ull;
+  z ^= z >> 33;
+  return z;
+}
+
+template <int KW>
+__device__ __forceinline__ uint64_t hash_label(uint64_t lo, uint64_t hi) {
+  if (KW == 1) return fmix64(lo);
+  return fmix64(lo ^ fmix64(hi + 0x9E3779B97F4A7C15ull));
+}
+
+// ---------------------------------------------------------------------------
+// Fused phase/permutation pass.
+template <int MAXOPS, int MAXPH>
+struct FusedArgs {
+  uint32_t nops, nph, has_perm, has_phase;
+  FOp ops[MAXOPS];
+  PhasePair ph[MAXPH];
+};
+
+template <int KW, int MAXOPS, int MAXPH>
+__global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
+                                               const __grid_constant__ FusedArgs<MAXOPS, MAXPH> a,
+                                               unsigned long long* plog) {
+  const uint64_t n = ctl->nnz;
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+    plog[0] = n;
+    plog[1] = n;
+  }
+  if (ctl->status != 0u) return;
+  const SoA s = pick(bufs, ctl->cur);
+  const double r = 0.70710678118654752440;  // sqrt(0.5)
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t k0 = s.lo[i];
+    uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    uint32_t cnt = 0;
+    bool any_ph = false;
+    double acc_re = 1.0, acc_im = 0.0;
+    for (uint32_t j = 0; j < a.nops; ++j) {
+      const FOp& o = a.ops[j];
+      bool cond = (k0 & o.c[0]) == o.c[0];
+      if (KW == 2) cond = cond && ((k1 & o.c[1]) == o.c[1]);
+      const bool sel = o.sbit != NO_SEL && label_bit(k0, k1, o.sbit);
+      const uint32_t step = sel ? o.a1 : o.a0;
+      cnt += cond ? step : 0u;
+      if (o.ph != NO_PH && cond) {
+        const PhasePair& pp = a.ph[o.ph];
+        const double pr = sel ? pp.re1 : pp.re0;
+        const double pi = sel ? pp.im1 : pp.im0;
+        const double nr = acc_re * pr - acc_im * pi;
+        const double ni = acc_re * pi + acc_im * pr;
+        acc_re = nr;
+        acc_im = ni;
+        any_ph = true;
+      }
+      const uint64_t m = cond ? ~0ull : 0ull;
+      k0 ^= o.t[0] & m;
+      if (KW == 2) k1 ^= o.t[1] & m;
+    }
+    if (a.has_perm) {
+      s.lo[i] = k0;
+      if (KW == 2) s.hi[i] = k1;
+    }
+    cnt &= 7u;
+    if (a.has_phase && (cnt != 0u || any_ph)) {
+      double re = s.re[i], im = s.im[i];
+      if (any_ph) {
+        const double nr = re * acc_re - im * acc_im;
+        const double ni = re * acc_im + im * acc_re;
+        re = nr;
+        im = ni;
+      }
+      if (cnt & 1u) {  // times e^{i pi/4} = sqrt(0.5) (1 + i)
+        const double nr = r * (re - im);
+        const double ni = r * (re + im);
+        re = nr;
+        im = ni;
+      }
+      switch (cnt >> 1) {  // times i^(cnt/2)
+        case 1: { const double t = re; re = -im; im = t; break; }
+        case 2: re = -re; im = -im; break;
+        case 3: { const double t = re; re = im; im = -t; break; }
+        default: break;
+      }
+      s.re[i] = re;
+      s.im[i] = im;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_table_clear(Slot* table, uint64_t nslots) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nslots;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(table + i);
+    p[0] = make_ulonglong2(EMPTY, EMPTY);
+    p[1] = make_ulonglong2(0ull, 0ull);
+  }
+}
+
+struct BranchArgs {
+  BranchOp op;
+  double eps2;
+  uint64_t capacity;
+  uint64_t fail_tag;
+  uint32_t load_pct, max_log2, probe_limit, pass_serial;
+};
+
+// Inserts (lo, hi) -> (re, im): claims a slot for the label if it is not in
+// the table yet and adds the amplitude. Returns false if `limit` slots were
+// probed without finding the label or a free slot.
+template <int KW>
+__device__ __forceinline__ bool table_add(Slot* table, uint64_t mask, uint32_t limit,
+                                          uint64_t lo, uint64_t hi, double re, double im) {
+  uint64_t h = hash_label<KW>(lo, hi) & mask;
+  for (uint32_t p = 0; p < limit; ++p, h = (h + 1) & mask) {
+    Slot* sl = table + h;
+    bool mine;
+    if (KW == 1) {
+      const uint64_t cur = __ldcg(&sl->lo);
+      mine = cur == lo;
+      if (!mine) {
+        if (cur != EMPTY) continue;
+        const unsigned long long old =
+            atomicCAS(reinterpret_cast<unsigned long long*>(&sl->lo), EMPTY, lo);
+        mine = old == EMPTY || old == lo;
+        if (!mine) continue;
+      }
+    } else {
+      // A slot changes once, from (EMPTY, EMPTY) to a label. A read that sees
+      // both words different from EMPTY therefore saw a whole label (a torn read
+      // has one EMPTY word); anything else is settled by the CAS.
+      // A label whose low word is all ones always takes the CAS path.
+      const ulonglong2 cur = __ldcg(reinterpret_cast<const ulonglong2*>(sl));
+      if (cur.x != EMPTY && cur.y != EMPTY) {
+        if (cur.x != lo || cur.y != hi) continue;
+      } else {
+        K128a expect{EMPTY, EMPTY}, want{lo, hi};
+        const K128a old = atomicCAS(reinterpret_cast<K128a*>(sl), expect, want);
+        mine = (old.lo == EMPTY && old.hi == EMPTY) || (old.lo == lo && old.hi == hi);
+        if (!mine) continue;
+      }
+    }
+    atomicAdd(&sl->re, re);
+    atomicAdd(&sl->im, im);
+    return true;
+  }
+  return false;
+}
+
+// contribution M[row][x] * (re, im), rounded like the plain formula
+// (re*mr - im*mi, re*mi + im*mr) with every product and sum rounded once.
+__device__ __forceinline__ void mat_times(const BranchOp& op, int row, int x, double re,
+                                          double im, double* o_re, double* o_im) {
+  const double mr = op.m_re[row][x];
+  if (op.real_m) {
+    *o_re = __dmul_rn(mr, re);
+    *o_im = __dmul_rn(mr, im);
+  } else {
+    const double mi = op.m_im[row][x];
+    *o_re = __dsub_rn(__dmul_rn(mr, re), __dmul_rn(mi, im));
+    *o_im = __dadd_rn(__dmul_rn(mr, im), __dmul_rn(mi, re));
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_branch_emit(Ctl* ctl, Bufs bufs, Slot* table,
+                                                     const __grid_constant__ BranchArgs a,
+                                                     unsigned long long* plog) {
+  const uint64_t n = ctl->nnz;
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+    plog[0] = n;
+    plog[1] = 0ull;
+  }
+  if (ctl->status != 0u) return;
+  const uint64_t mask = (1ull << table_log2_for(n, a.load_pct, a.max_log2)) - 1;
+  const SoA s = pick(bufs, ctl->cur);
+  const BranchOp& op = a.op;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k0 = s.lo[i];
+    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    const double re = s.re[i], im = s.im[i];
+    bool active = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
+    const bool x = label_bit(k0, k1, op.sbit);
+    if (op.givens) active = active && (x != label_bit(k0, k1, op.qbit));
+    bool ok = true;
+    if (!active) {
+      ok = table_add<KW>(table, mask, a.probe_limit, k0, k1, re, im);
+    } else {
+      const int xi = x ? 1 : 0;
+      const uint64_t f0 = k0 ^ op.m[0], f1 = k1 ^ op.m[1];
+      // k0 side: the label whose selector bit is 0
+      const uint64_t a0 = x ? f0 : k0, a1 = x ? f1 : k1;
+      const uint64_t b0 = x ? k0 : f0, b1 = x ? k1 : f1;
+      if (op.m_re[0][xi] != 0.0 || op.m_im[0][xi] != 0.0) {
+        double vr, vi;
+        mat_times(op, 0, xi, re, im, &vr, &vi);
+        ok = table_add<KW>(table, mask, a.probe_limit, a0, a1, vr, vi);
+      }
+      if (ok && (op.m_re[1][xi] != 0.0 || op.m_im[1][xi] != 0.0)) {
+        double vr, vi;
+        mat_times(op, 1, xi, re, im, &vr, &vi);
+        ok = table_add<KW>(table, mask, a.probe_limit, b0, b1, vr, vi);
+      }
+    }
+    if (!ok) {
+      fail(ctl, SPS_ERR_TABLE_FULL, a.pass_serial, a.fail_tag);
+      return;
+    }
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slot* table,
+                                                        const __grid_constant__ BranchArgs a,
+                                                        unsigned long long* plog) {
+  __shared__ unsigned warp_cnt[32];
+  __shared__ unsigned long long block_base;
+  const unsigned status0 = ctl->status;
+  // An error from an earlier pass means this pass never filled the table.
+  if (status0 != 0u && ctl->fail_pass != a.pass_serial) return;
+  const bool write_ok = status0 == 0u;
+  const uint64_t n_in = ctl->nnz;
+  const uint64_t size = 1ull << table_log2_for(n_in, a.load_pct, a.max_log2);
+  const unsigned cur = ctl->cur;
+  const SoA out = pick(bufs, cur ^ 1u);
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned nwarps = blockDim.x >> 5;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < size;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    bool keep = false;
+    uint64_t lo = 0, hi = 0;
+    double re = 0.0, im = 0.0;
+    if (i < size) {
+      const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2*>(table + i));
+      const bool occ = KW == 2 ? kk.y != EMPTY : kk.x != EMPTY;
+      if (occ) {
+        const double2 aa = __ldcs(reinterpret_cast<const double2*>(table + i) + 1);
+        lo = kk.x;
+        hi = kk.y;
+        re = aa.x;
+        im = aa.y;
+        const double mag2 = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+        keep = !(re == 0.0 && im == 0.0) && !(mag2 < a.eps2);
+        ulonglong2* p = reinterpret_cast<ulonglong2*>(table + i);
+        p[0] = make_ulonglong2(EMPTY, EMPTY);
+        p[1] = make_ulonglong2(0ull, 0ull);
+      }
+    }
+    const unsigned ballot = __ballot_sync(FULL, keep);
+    if (lane == 0) warp_cnt[warp] = __popc(ballot);
+    __syncthreads();
+    if (warp == 0) {
+      // exclusive scan of the per-warp counts in warp 0
+      unsigned v = lane < nwarps ? warp_cnt[lane] : 0u;
+      unsigned incl = v;
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= (unsigned)d) incl += t;
+      }
+      const unsigned total = __shfl_sync(FULL, incl, 31);
+      if (lane < nwarps) warp_cnt[lane] = incl - v;
+      if (lane == 0) block_base = total ? atomicAdd(&ctl->out_count, (unsigned long long)total) : 0ull;
+    }
+    __syncthreads();
+    if (keep) {
+      const uint64_t pos = block_base + warp_cnt[warp] + __popc(ballot & ((1u << lane) - 1u));
+      if (write_ok && pos < a.capacity) {
+        out.lo[pos] = lo;
+        if (KW == 2) out.hi[pos] = hi;
+        out.re[pos] = re;
+        out.im[pos] = im;
+      }
+    }
+    __syncthreads();
+  }
+  // The last block to finish publishes the pass result.
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long total = atomicAdd(&ctl->out_count, 0ull);
+      bool published = false;
+      if (write_ok) {
+        if (total > a.capacity) {
+          fail(ctl, SPS_ERR_CAPACITY, a.pass_serial, a.fail_tag);
+        } else {
+          ctl->nnz = total;
+          ctl->cur = cur ^ 1u;
+          published = true;
+        }
+      }
+      if (plog) {
+        plog[0] = n_in;
+        plog[1] = published ? total : n_in;
+      }
+      ctl->out_count = 0ull;
+      ctl->blocks_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(FULL, v, d);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < (blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(FULL, t, d);
+  }
+  return t;  // valid in thread 0
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_probability(const Ctl* ctl, Bufs bufs, uint64_t m0,
+                                                     uint64_t m1, uint64_t v0, uint64_t v1,
+                                                     double* partials) {
+  __shared__ double sh[32];
+  const uint64_t n = ctl->nnz;
+  const SoA s = pick(bufs, ctl->cur);
+  double acc = 0.0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k0 = s.lo[i];
+    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    if ((k0 & m0) == v0 && (k1 & m1) == v1) {
+      const double re = s.re[i], im = s.im[i];
+      acc += re * re + im * im;
+    }
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void k_sum_partials(const double* partials, int n, double* out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = t;
+}
+
+__global__ void k_set_nnz(Ctl* ctl, unsigned long long nnz) {
+  ctl->nnz = nnz;
+  ctl->cur = 0u;
+  ctl->status = 0u;
+  ctl->out_count = 0ull;
+  ctl->blocks_done = 0u;
+}
+
+// |0...0>: one entry (label 0, amplitude 1) in buffer 0.
+__global__ void k_reset_state(Ctl* ctl, Bufs bufs, int key_words) {
+  bufs.b[0].lo[0] = 0ull;
+  if (key_words == 2) bufs.b[0].hi[0] = 0ull;
+  bufs.b[0].re[0] = 1.0;
+  bufs.b[0].im[0] = 0.0;
+  ctl->nnz = 1ull;
+  ctl->cur = 0u;
+  ctl->status = 0u;
+  ctl->fail_pass = 0u;
+  ctl->fail_gate = 0ull;
+  ctl->out_count = 0ull;
+  ctl->blocks_done = 0u;
+}
+
+__global__ void k_reset_status(Ctl* ctl) {
+  ctl->status = 0u;
+  ctl->fail_pass = 0u;
+  ctl->fail_gate = 0ull;
+  ctl->out_count = 0ull;
+  ctl->blocks_done = 0u;
+}
+
+template <int KW>
+__global__ void k_check_labels(const Ctl* ctl, Bufs bufs, uint64_t lim0, uint64_t lim1,
+                               unsigned* bad) {
+  const uint64_t n = ctl->nnz;
+  const SoA s = pick(bufs, ctl->cur);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    if ((s.lo[i] & ~lim0) != 0ull || (k1 & ~lim1) != 0ull) atomicOr(bad, 1u);
+  }
+}
+
+int grid_for(uint64_t work, int threads, int max_blocks) {
+  uint64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > (uint64_t)max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+template <int KW, int MAXOPS, int MAXPH>
+int fused_impl(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const Pass& p, uint64_t nnz_bound,
+               unsigned long long* plog) {
+  static_assert(sizeof(FusedArgs<MAXOPS, MAXPH>) <= 32000, "kernel parameter limit");
+  FusedArgs<MAXOPS, MAXPH> a;
+  a.nops = (uint32_t)p.ops.size();
+  a.nph = (uint32_t)p.phases.size();
+  a.has_perm = p.has_perm;
+  a.has_phase = p.has_phase;
+  for (uint32_t j = 0; j < a.nops; ++j) a.ops[j] = p.ops[j];
+  for (uint32_t j = 0; j < a.nph; ++j) a.ph[j] = p.phases[j];
+  const int blocks = grid_for(nnz_bound, lc.threads, lc.max_blocks);
+  k_fused<KW, MAXOPS, MAXPH><<<blocks, lc.threads, 0, (cudaStream_t)lc.stream>>>(ctl, bufs, a, plog);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+template <int KW>
+int fused_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const Pass& p, uint64_t nnz_bound,
+             unsigned long long* plog) {
+  const size_t no = p.ops.size(), np = p.phases.size();
+  if (no <= 16 && np <= 8) return fused_impl<KW, 16, 8>(lc, ctl, bufs, p, nnz_bound, plog);
+  if (no <= 128 && np <= 32) return fused_impl<KW, 128, 32>(lc, ctl, bufs, p, nnz_bound, plog);
+  if (no <= kMaxFusedOps && np <= kMaxFusedPhases)
+    return fused_impl<KW, kMaxFusedOps, kMaxFusedPhases>(lc, ctl, bufs, p, nnz_bound, plog);
+  return -1;
+}
+
+BranchArgs branch_args(const BranchLaunch& b) {
+  BranchArgs a;
+  a.op = b.op;
+  a.eps2 = b.eps * b.eps;
+  a.capacity = b.capacity;
+  a.fail_tag = b.fail_tag;
+  a.load_pct = b.load_pct;
+  a.max_log2 = b.max_log2;
+  a.probe_limit = b.probe_limit;
+  a.pass_serial = b.pass_serial;
+  return a;
+}
+
+}  // namespace
+
+int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots) {
+  const int blocks = grid_for(nslots, lc.threads, lc.max_blocks);
+  k_table_clear<<<blocks, lc.threads, 0, (cudaStream_t)lc.stream>>>(table, nslots);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
+                 uint64_t nnz_bound, unsigned long long* plog) {
+  if (p.ops.empty()) return 0;
+  return key_words == 1 ? fused_kw<1>(lc, ctl, bufs, p, nnz_bound, plog)
+                        : fused_kw<2>(lc, ctl, bufs, p, nnz_bound, plog);
+}
+
+int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,
+                       const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog) {
+  const BranchArgs a = branch_args(b);
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  const int blocks = grid_for(nnz_bound, lc.threads, lc.max_blocks);
+  if (key_words == 1)
+    k_branch_emit<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, table, a, plog);
+  else
+    k_branch_emit<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, table, a, plog);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_branch_compact(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,
+                          const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog) {
+  const BranchArgs a = branch_args(b);
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  const uint64_t tsize = 1ull << table_log2_for(nnz_bound, b.load_pct, b.max_log2);
+  const int blocks = grid_for(tsize, lc.threads, lc.max_blocks);
+  if (key_words == 1)
+    k_branch_compact<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, table, a, plog);
+  else
+    k_branch_compact<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, table, a, plog);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
+                       uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
+                       double* partials, int nblocks, double* result) {
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  if (key_words == 1)
+    k_probability<1><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi, partials);
+  else
+    k_probability<2><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi, partials);
+  k_sum_partials<<<1, 256, 0, st>>>(partials, nblocks, result);
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
+}
+
+int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz) {
+  k_set_nnz<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, nnz);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_reset_state(void* stream, int key_words, Ctl* ctl, Bufs bufs) {
+  k_reset_state<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, bufs, key_words);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_reset_status(void* stream, Ctl* ctl) {
+  k_reset_status<<<1, 1, 0, (cudaStream_t)stream>>>(ctl);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_check_labels(void* stream, int key_words, const Ctl* ctl, Bufs bufs, uint64_t lim_lo,
+                        uint64_t lim_hi, unsigned int* bad_flag, uint64_t n) {
+  const int blocks = grid_for(n, 256, 1024);
+  if (key_words == 1)
+    k_check_labels<1><<<blocks, 256, 0, (cudaStream_t)stream>>>(ctl, bufs, lim_lo, lim_hi, bad_flag);
+  else
+    k_check_labels<2><<<blocks, 256, 0, (cudaStream_t)stream>>>(ctl, bufs, lim_lo, lim_hi, bad_flag);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace sps

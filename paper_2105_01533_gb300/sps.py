@@ -1,0 +1,357 @@
+"""Thin ctypes binding of ``libsps.so`` (C ABI in ``include/sps.h``).
+
+Argument marshalling only: every step of gate application runs in the CUDA
+kernels of the library. The functions keep the C names (``sps_create``,
+``sps_apply``, ...); :class:`SparseState` wraps them for convenience.
+
+PyTorch supplies device memory (its caching allocator is installed as the
+library's allocator hook) and streams (the current torch stream by default).
+If ``libsps.so`` is missing this module raises: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import workloads
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsps.so")
+
+SPS_OK, SPS_ERR_ARG, SPS_ERR_CAPACITY, SPS_ERR_TABLE_FULL = 0, 1, 2, 3
+SPS_ERR_CUDA, SPS_ERR_OOM, SPS_ERR_NO_DEVICE = 4, 5, 6
+SPS_OPT_LOAD_FACTOR_PCT, SPS_OPT_PROBE_LIMIT, SPS_OPT_BLOCK_THREADS = 1, 2, 3
+SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
+KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
+
+EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_apply", "sps_sync",
+           "sps_nnz", "sps_get_amplitudes", "sps_set_amplitudes", "sps_probability",
+           "sps_set_option", "sps_get_counters", "sps_profile_read", "sps_plan", "sps_status_str")
+
+
+class SpsError(RuntimeError):
+    def __init__(self, status: int, what: str, failed_gate: Optional[int] = None):
+        self.status = status
+        self.failed_gate = failed_gate
+        msg = "%s: %s" % (what, _status_str(status))
+        if failed_gate is not None:
+            msg += " (gate %d)" % failed_gate
+        super().__init__(msg)
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("gates", ctypes.c_uint64), ("fused_passes", ctypes.c_uint64),
+                ("branch_passes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+
+
+class KernelRecord(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("pass_serial", ctypes.c_uint32),
+                ("ms", ctypes.c_float), ("nops", ctypes.c_uint32), ("n_in", ctypes.c_uint64),
+                ("n_out", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("label_bytes", ctypes.c_uint32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                           ctypes.c_void_p)
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libsps.so. Raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libsps.so is not built (%s); run paper_2105_01533_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, sz, dbl, i64 = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                  ctypes.c_size_t, ctypes.c_double, ctypes.c_int64)
+    st = ctypes.c_int
+    psz = ctypes.POINTER(ctypes.c_size_t)
+    pu64 = ctypes.POINTER(ctypes.c_uint64)
+    lib.sps_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+    lib.sps_set_allocator.restype = st
+    lib.sps_create.argtypes = [u32, u64, vp, ctypes.POINTER(vp)]
+    lib.sps_create.restype = st
+    lib.sps_reset.argtypes = [vp]
+    lib.sps_reset.restype = st
+    lib.sps_profile_read.argtypes = [vp, ctypes.POINTER(KernelRecord), sz, psz]
+    lib.sps_profile_read.restype = st
+    lib.sps_destroy.argtypes = [vp]
+    lib.sps_destroy.restype = None
+    lib.sps_apply.argtypes = [vp, vp, sz, dbl, psz]
+    lib.sps_apply.restype = st
+    lib.sps_sync.argtypes = [vp, psz]
+    lib.sps_sync.restype = st
+    lib.sps_nnz.argtypes = [vp, pu64]
+    lib.sps_nnz.restype = st
+    lib.sps_get_amplitudes.argtypes = [vp, vp, vp, vp, vp, u64, pu64]
+    lib.sps_get_amplitudes.restype = st
+    lib.sps_set_amplitudes.argtypes = [vp, vp, vp, vp, vp, u64]
+    lib.sps_set_amplitudes.restype = st
+    lib.sps_probability.argtypes = [vp, vp, vp, ctypes.POINTER(dbl)]
+    lib.sps_probability.restype = st
+    lib.sps_set_option.argtypes = [vp, ctypes.c_int, i64]
+    lib.sps_set_option.restype = st
+    lib.sps_get_counters.argtypes = [vp, ctypes.POINTER(Counters)]
+    lib.sps_get_counters.restype = st
+    lib.sps_plan.argtypes = [vp, sz, u32, u32, vp, vp, vp, sz, psz, psz]
+    lib.sps_plan.restype = st
+    lib.sps_status_str.argtypes = [st]
+    lib.sps_status_str.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _status_str(code: int) -> str:
+    try:
+        return load_library().sps_status_str(code).decode()
+    except Exception:  # pragma: no cover - only when the library is absent
+        return "status %d" % code
+
+
+def _check(code: int, what: str, failed_gate: Optional[int] = None) -> None:
+    if code != SPS_OK:
+        raise SpsError(code, what, failed_gate)
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data if a.size else None
+    return a.data_ptr()  # torch.Tensor
+
+
+def gate_array(gates) -> np.ndarray:
+    g = np.ascontiguousarray(gates)
+    if g.dtype != workloads.GATE_DTYPE:
+        g = np.ascontiguousarray(g.astype(workloads.GATE_DTYPE))
+    return g
+
+
+# ---- torch as memory provider ---------------------------------------------------
+_torch_hooks = None
+
+
+def use_torch_allocator() -> bool:
+    """Install torch's CUDA caching allocator as the device memory hook."""
+    global _torch_hooks
+    if _torch_hooks is not None:
+        return True
+    import torch
+    if not torch.cuda.is_available():
+        return False
+    lib = load_library()
+
+    def _alloc(ctx, nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ctx, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib.sps_set_allocator(hooks[0], hooks[1], None), "sps_set_allocator")
+    _torch_hooks = hooks
+    return True
+
+
+def current_stream_handle() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+# ---- C-named wrappers -------------------------------------------------------------
+def sps_create(nqubits: int, capacity: int, stream: Optional[int] = None) -> int:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.sps_create(nqubits, capacity, stream, ctypes.byref(h)), "sps_create")
+    return h.value
+
+
+def sps_reset(h: int) -> None:
+    _check(load_library().sps_reset(h), "sps_reset")
+
+
+def sps_profile_read(h: int, cap: int = 1 << 16):
+    """Profiled launches since the last read, as a list of dicts."""
+    recs = (KernelRecord * cap)()
+    n = ctypes.c_size_t(0)
+    _check(load_library().sps_profile_read(h, recs, cap, ctypes.byref(n)), "sps_profile_read")
+    out = []
+    for i in range(n.value):
+        r = recs[i]
+        out.append({"kind": r.kind, "pass": r.pass_serial, "ms": r.ms, "nops": r.nops,
+                    "n_in": r.n_in, "n_out": r.n_out, "flags": r.flags,
+                    "label_bytes": r.label_bytes})
+    return out
+
+
+def sps_destroy(h: int) -> None:
+    load_library().sps_destroy(h)
+
+
+def sps_apply(h: int, gates, prune_eps: float = 0.0) -> None:
+    g = gate_array(gates)
+    bad = ctypes.c_size_t(0)
+    rc = load_library().sps_apply(h, _ptr(g), g.size, float(prune_eps), ctypes.byref(bad))
+    _check(rc, "sps_apply", bad.value if rc == SPS_ERR_ARG else None)
+
+
+def sps_sync(h: int) -> None:
+    bad = ctypes.c_size_t(0)
+    rc = load_library().sps_sync(h, ctypes.byref(bad))
+    _check(rc, "sps_sync", bad.value if rc in (SPS_ERR_CAPACITY, SPS_ERR_TABLE_FULL) else None)
+
+
+def sps_nnz(h: int) -> int:
+    n = ctypes.c_uint64(0)
+    _check(load_library().sps_nnz(h, ctypes.byref(n)), "sps_nnz")
+    return n.value
+
+
+def sps_get_amplitudes(h: int, key_hi, key_lo, re, im, cap: int) -> int:
+    n = ctypes.c_uint64(0)
+    rc = load_library().sps_get_amplitudes(h, _ptr(key_hi), _ptr(key_lo), _ptr(re), _ptr(im),
+                                          cap, ctypes.byref(n))
+    _check(rc, "sps_get_amplitudes")
+    return n.value
+
+
+def sps_set_amplitudes(h: int, key_hi, key_lo, re, im, n: int) -> None:
+    _check(load_library().sps_set_amplitudes(h, _ptr(key_hi), _ptr(key_lo), _ptr(re), _ptr(im), n),
+           "sps_set_amplitudes")
+
+
+def sps_probability(h: int, mask: Sequence[int], value: Sequence[int]) -> float:
+    m = np.array([int(mask[0]), int(mask[1])], np.uint64)
+    v = np.array([int(value[0]), int(value[1])], np.uint64)
+    p = ctypes.c_double(0.0)
+    _check(load_library().sps_probability(h, _ptr(m), _ptr(v), ctypes.byref(p)), "sps_probability")
+    return p.value
+
+
+def sps_set_option(h: int, opt: int, value: int) -> None:
+    _check(load_library().sps_set_option(h, opt, int(value)), "sps_set_option")
+
+
+def sps_get_counters(h: int) -> Counters:
+    c = Counters()
+    _check(load_library().sps_get_counters(h, ctypes.byref(c)), "sps_get_counters")
+    return c
+
+
+def sps_plan(gates, nqubits: int, max_fused_ops: int = 0):
+    """Host-only compilation: list of (kind, first_gate, nops); kind 1 = fused
+    phase/permutation pass, 2 = branching pass."""
+    lib = load_library()
+    g = gate_array(gates)
+    cap = max(len(g), 1)
+    kind = np.zeros(cap, np.uint32)
+    first = np.zeros(cap, np.uint64)
+    ops = np.zeros(cap, np.uint32)
+    npass = ctypes.c_size_t(0)
+    bad = ctypes.c_size_t(0)
+    rc = lib.sps_plan(_ptr(g), g.size, nqubits, max_fused_ops, _ptr(kind), _ptr(first), _ptr(ops),
+                      cap, ctypes.byref(npass), ctypes.byref(bad))
+    _check(rc, "sps_plan", bad.value if rc == SPS_ERR_ARG else None)
+    n = npass.value
+    return [(int(kind[i]), int(first[i]), int(ops[i])) for i in range(n)]
+
+
+def sps_status_str(code: int) -> str:
+    return _status_str(code)
+
+
+# ---- convenience class ----------------------------------------------------------
+class SparseState:
+    """A device-resident sparse state. ``stream`` is a cudaStream_t handle
+    (int); by default the current torch stream."""
+
+    def __init__(self, nqubits: int, capacity: int, stream: Optional[int] = None,
+                 torch_memory: bool = True):
+        if torch_memory:
+            use_torch_allocator()
+        if stream is None:
+            stream = current_stream_handle()
+        self.nqubits = nqubits
+        self.capacity = capacity
+        self.stream = stream
+        self._h = sps_create(nqubits, capacity, stream)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def close(self) -> None:
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            sps_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def apply(self, gates, eps: float = 0.0) -> None:
+        sps_apply(self._h, gates, eps)
+
+    def sync(self) -> None:
+        sps_sync(self._h)
+
+    def reset(self) -> None:
+        sps_reset(self._h)
+
+    def profile_read(self):
+        return sps_profile_read(self._h)
+
+    def nnz(self) -> int:
+        return sps_nnz(self._h)
+
+    def set_option(self, opt: int, value: int) -> None:
+        sps_set_option(self._h, opt, value)
+
+    def counters(self) -> Counters:
+        return sps_get_counters(self._h)
+
+    def probability(self, mask, value) -> float:
+        return sps_probability(self._h, mask, value)
+
+    def get_amplitudes(self, sort: bool = True):
+        """(hi, lo, re, im) numpy arrays, sorted by (hi, lo) unless sort=False."""
+        n = self.nnz()
+        hi = np.empty(n, np.uint64)
+        lo = np.empty(n, np.uint64)
+        re = np.empty(n, np.float64)
+        im = np.empty(n, np.float64)
+        if n:
+            sps_get_amplitudes(self._h, hi, lo, re, im, n)
+        if sort and n:
+            order = np.lexsort((lo, hi))
+            hi, lo, re, im = hi[order], lo[order], re[order], im[order]
+        return hi, lo, re, im
+
+    def set_amplitudes(self, hi, lo, re, im) -> None:
+        lo = np.ascontiguousarray(lo, np.uint64)
+        hi = None if hi is None else np.ascontiguousarray(hi, np.uint64)
+        re = np.ascontiguousarray(re, np.float64)
+        im = np.ascontiguousarray(im, np.float64)
+        sps_set_amplitudes(self._h, hi, lo, re, im, len(lo))

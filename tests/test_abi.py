@@ -1,0 +1,121 @@
+"""CPU-side checks of the C ABI: the library loads, exports every entry point
+the header declares, rejects bad input on the host, and compiles gate streams
+into passes as the batching rule says (no GPU needed)."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2105_01533_gb300 import build as B
+from paper_2105_01533_gb300 import sps
+from paper_2105_01533_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return sps.load_library()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "sps.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(sps_[a-z_]+)\s*\(", text))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert "sps_create" in names and "sps_apply" in names and "sps_probability" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(sps.EXPORTS)
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert sps.sps_status_str(code)
+    assert sps.sps_status_str(3) == "hash table probe limit reached"
+
+
+def test_gate_record_layout():
+    assert W.GATE_DTYPE.itemsize == 32
+    text = open(os.path.join(ROOT, "include", "sps.h")).read()
+    for name, code in [("SPS_OP_X", 1), ("SPS_OP_H", 10), ("SPS_OP_GIVENS", 13)]:
+        assert re.search(r"%s = %d\b" % (name, code), text)
+    assert W.OP_X == 1 and W.OP_H == 10 and W.OP_GIVENS == 13
+
+
+def test_create_rejects_bad_arguments_on_host(lib):
+    for nq, cap in [(0, 10), (128, 10), (10, 0)]:
+        with pytest.raises(sps.SpsError) as e:
+            sps.sps_create(nq, cap, None)
+        assert e.value.status == sps.SPS_ERR_ARG
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(sps.SpsError) as e:
+        sps.sps_create(10, 16, None)
+    assert e.value.status == sps.SPS_ERR_NO_DEVICE
+
+
+def classify(op):
+    return 2 if op in W.BRANCH_OPS else 1
+
+
+def test_plan_splits_at_every_branching_gate(lib):
+    gates = W.random_mix(3, 24, 400, keep_branch=W.CountingBound(4096), p_perm=0.5, p_diag=0.3)
+    plan = sps.sps_plan(gates, 24)
+    kinds = [classify(int(op)) for op in gates["op"]]
+    # rebuild the expected plan: maximal runs of kind 1, single passes of kind 2
+    want = []
+    for i, k in enumerate(kinds):
+        if k == 2:
+            want.append((2, i))
+        elif not want or want[-1][0] == 2:
+            want.append((1, i))
+    assert [(k, f) for k, f, _ in plan] == want
+    # op count of a fused pass = number of gates in the run
+    bounds = [f for _, f, _ in plan] + [len(gates)]
+    for j, (k, f, nops) in enumerate(plan):
+        assert nops == (bounds[j + 1] - f if k == 1 else 1)
+
+
+def test_plan_respects_max_fused_ops(lib):
+    lay = W.AdderLayout(32)
+    add = W.cuccaro_adder(lay)
+    plan = sps.sps_plan(add, lay.nqubits, max_fused_ops=50)
+    assert [p[2] for p in plan] == [50, 50, 50, 43]
+    assert [p[1] for p in plan] == [0, 50, 100, 150]
+    plan = sps.sps_plan(add, lay.nqubits)
+    assert plan == [(1, 0, len(add))]
+
+
+def test_plan_rejects_bad_records(lib):
+    good = W.to_array([W.H(0), W.X(3, 1)])
+    cases = [
+        W.to_array([W.H(0), W.X(5)]),                 # target out of range (n = 5)
+        W.to_array([W.H(0), W.X(2, 2)]),              # control on the target
+        W.to_array([W.H(0), W.Givens(1, 1, 0.3)]),    # p == q
+        W.to_array([W.H(0), W.gate(99, 0)]),          # unknown code
+        W.to_array([W.H(0), W.X(1, 70)]),             # control beyond n
+    ]
+    assert len(sps.sps_plan(good, 5)) == 2
+    for c in cases:
+        with pytest.raises(sps.SpsError) as e:
+            sps.sps_plan(c, 5)
+        assert e.value.status == sps.SPS_ERR_ARG and e.value.failed_gate == 1
+    nan = W.to_array([W.Ry(0, float("nan"))])
+    with pytest.raises(sps.SpsError):
+        sps.sps_plan(nan, 2)
+
+
+def test_plan_of_empty_stream(lib):
+    assert sps.sps_plan(np.zeros(0, W.GATE_DTYPE), 10) == []

@@ -1,0 +1,305 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs. Labels must match bit for bit (except labels within 10x eps
+of the prune threshold on one side), amplitudes to 1e-12 max abs error.
+
+Branching passes compute every product and sum exactly as the oracle does, so
+for circuits of branching gates alone the GPU result is bit-identical; fused
+phase passes reorder the phase products and stay within the tolerance."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import OracleState
+from paper_2105_01533_gb300 import sps
+from paper_2105_01533_gb300 import workloads as W
+
+from helpers import compare_states, plain24_gates
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2105_01533_gb300 import build as B
+    B.build()
+    sps.load_library()
+    yield
+
+
+def run_both(n, gates, eps, capacity=1 << 16, chunks=1, options=()):
+    st = sps.SparseState(n, capacity)
+    for opt, val in options:
+        st.set_option(opt, val)
+    parts = np.array_split(gates, chunks) if chunks > 1 else [gates]
+    for p in parts:
+        st.apply(p, eps)
+    got = st.get_amplitudes()
+    st.close()
+    orc = OracleState(n)
+    orc.apply(gates, eps=eps)
+    return got, orc.get()
+
+
+@pytest.mark.parametrize("n", [20, 64, 100, 127])
+@pytest.mark.parametrize("op", sorted(W.OP_NAMES))
+def test_each_gate_type(n, op):
+    rng = W.SplitMix64(1000 * n + op)
+    prep = [W.H(q) for q in rng.distinct(n, 6)] + [W.X(q) for q in rng.distinct(n, 4)]
+    prep += [W.Ry(rng.below(n), rng.angle()), W.T(rng.below(n))]
+    gates = list(prep)
+    for nctl in range(3):
+        ntarg = 2 if op == W.OP_GIVENS else 1
+        qs = rng.distinct(n, ntarg + nctl)
+        if op == W.OP_GIVENS:
+            gates.append(W.Givens(qs[0], qs[1], rng.angle(), *qs[2:]))
+        else:
+            gates.append(W.gate(op, qs[0], qs[1:], rng.angle()))
+    gates = W.to_array(gates)
+    got, want = run_both(n, gates, eps=1e-14)
+    compare_states(got, want, 1e-14)
+
+
+@pytest.mark.parametrize("n,seed", [(12, 1), (40, 2), (63, 3), (64, 4), (90, 5), (127, 6)])
+def test_random_circuits_all_gates(n, seed):
+    gates = W.random_all_gates(seed, n, 400, max_controls=3, branch_frac=0.2)
+    got, want = run_both(n, gates, eps=1e-14, capacity=1 << 18)
+    compare_states(got, want, 1e-14)
+
+
+def test_branching_only_is_bit_identical():
+    n = 30
+    rng = W.SplitMix64(5)
+    recs = []
+    for _ in range(14):
+        kind = rng.below(3)
+        q = rng.distinct(n, 3)
+        if kind == 0:
+            recs.append(W.H(q[0]))
+        elif kind == 1:
+            recs.append(W.Ry(q[0], rng.angle(), q[1]))
+        else:
+            recs.append(W.Givens(q[0], q[1], rng.angle()))
+    gates = W.to_array(recs)
+    got, want = run_both(n, gates, eps=0.0)
+    for a, b in zip(got, want):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_plain24_workload_full():
+    """24 qubits, H on 8 qubits then 2000 gates (70% X/CNOT/Toffoli, 20%
+    Z/S/T/CRz, 10% H kept only while the oracle reports <= 4096 nonzeros)."""
+    gates = plain24_gates(seed=0)
+    assert len(gates) == 2008
+    got, want = run_both(24, gates, eps=1e-14, capacity=8192)
+    stats = compare_states(got, want, 1e-14)
+    assert stats["common"] >= 256
+    # same stream applied in several calls gives the same result
+    got2, _ = run_both(24, gates, eps=1e-14, capacity=8192, chunks=7)
+    compare_states(got2, want, 1e-14)
+
+
+def test_adder_workload_full_and_closed_form():
+    wl = W.adder_workload(seed=1, width=16)
+    got, want = run_both(wl.layout.nqubits, wl.gates, eps=1e-14, capacity=1 << 17)
+    stats = compare_states(got, want, 1e-14)
+    assert stats["common"] == 1 << 16
+    hi, lo, re, im = got
+    n = wl.layout.nbits
+    a = lo & np.uint64(0xFFFFFFFF)
+    assert np.all(hi == 0) and np.all((lo >> np.uint64(n)) == np.uint64(wl.b_const))
+    bsum = (a + np.uint64(wl.b_const)) & np.uint64(0xFFFFFFFF)
+    reg = a | (bsum << np.uint64(n))
+    phase = np.zeros(len(a))
+    for q1, q2, phi in wl.cp_pairs:
+        both = ((reg >> np.uint64(q1)) & np.uint64(1)) & ((reg >> np.uint64(q2)) & np.uint64(1))
+        phase += phi * both.astype(float)
+    amp = 2.0 ** -8 * np.exp(1j * phase)
+    assert np.max(np.abs(re + 1j * im - amp)) < 1e-12
+
+
+def test_givens_workload_few_layers():
+    gates = W.givens_workload(seed=2, nqubits=64, modes=4, layers=3)
+    got, want = run_both(64, gates, eps=1e-14, capacity=700_000)
+    compare_states(got, want, 1e-14)
+
+
+def test_givens_workload_full_properties():
+    """All 500 layers: the oracle is too slow here, so check what holds at any
+    size: Hamming weight 4, nnz <= C(64,4), unit norm, and that the inverse
+    circuit brings the state back to the start label."""
+    gates = W.givens_workload(seed=2, nqubits=64, modes=4, layers=500)
+    st = sps.SparseState(64, 700_000)
+    st.apply(gates, 1e-14)
+    hi, lo, re, im = st.get_amplitudes(sort=False)
+    assert len(lo) <= math.comb(64, 4)
+    w = np.zeros(len(lo), np.int64)
+    x = lo.copy()
+    while np.any(x):
+        w += (x & np.uint64(1)).astype(np.int64)
+        x >>= np.uint64(1)
+    assert np.all(w == 4) and np.all(hi == 0)
+    assert abs(np.sum(re * re + im * im) - 1.0) < 1e-10
+    st.apply(W.inverse(gates), 1e-14)
+    hi, lo, re, im = st.get_amplitudes()
+    assert lo.tolist() == [0xF]
+    assert abs(re[0] - 1.0) < 1e-9 and abs(im[0]) < 1e-9
+    st.close()
+
+
+def test_probability_matches_oracle():
+    gates = W.random_all_gates(8, 70, 300, max_controls=2, branch_frac=0.2)
+    st = sps.SparseState(70, 1 << 16)
+    st.apply(gates, 1e-14)
+    orc = OracleState(70)
+    orc.apply(gates, eps=1e-14)
+    for mask, val in [((0, 0), (0, 0)), ((1, 0), (1, 0)), ((0xF0, 1 << 3), (0x30, 1 << 3)),
+                      ((~0 & 0xFFFFFFFFFFFFFFFF, 0x3F), (0, 0))]:
+        p_gpu = st.probability(mask, val)
+        p_orc = orc.probability(mask, val)
+        assert abs(p_gpu - p_orc) < 1e-12
+    p1 = st.probability((1, 0), (1, 0))
+    p2 = st.probability((1, 0), (1, 0))
+    assert p1 == p2
+    st.close()
+
+
+# ---- edge cases -------------------------------------------------------------
+def test_empty_gate_list_and_identity():
+    st = sps.SparseState(10, 16)
+    st.apply(np.zeros(0, W.GATE_DTYPE), 0.0)
+    hi, lo, re, im = st.get_amplitudes()
+    assert lo.tolist() == [0] and re.tolist() == [1.0] and im.tolist() == [0.0]
+    st.close()
+
+
+def test_everything_pruned_then_continue():
+    st = sps.SparseState(10, 64)
+    st.apply(W.to_array([W.H(0), W.H(1)]), 0.0)
+    st.apply(W.to_array([W.H(2)]), 1.0)        # |a| = 0.35 < 1: all pruned
+    assert st.nnz() == 0
+    st.apply(W.to_array([W.X(3), W.H(4), W.Ry(5, 0.3)]), 0.0)
+    assert st.nnz() == 0
+    st.close()
+
+
+def test_ragged_sizes_span_tiles():
+    """nnz not a multiple of any block size, across several grid tiles."""
+    n = 40
+    for k in (9, 13, 17):
+        qs = list(range(k))
+        gates = W.to_array([W.H(q) for q in qs] + [W.Ry(k, 0.4, 0), W.X(k + 1, 1)] +
+                           [W.Givens(k + 2, 0, 0.7)] + [W.CRz(3, k + 3, 1.1)])
+        got, want = run_both(n, gates, eps=0.0, capacity=1 << 19)
+        compare_states(got, want, 0.0)
+        assert len(got[1]) > (1 << k)
+
+
+def test_capacity_overflow_leaves_last_good_state():
+    st = sps.SparseState(20, 100)
+    st.apply(W.to_array([W.H(q) for q in range(6)]), 0.0)       # 64 entries
+    before = st.get_amplitudes()
+    st.apply(W.to_array([W.X(10), W.H(7), W.Z(3)]), 0.0)        # H would make 128
+    with pytest.raises(sps.SpsError) as e:
+        st.sync()
+    assert e.value.status == sps.SPS_ERR_CAPACITY and e.value.failed_gate == 1
+    hi, lo, re, im = st.get_amplitudes()
+    # the X pass ran, the H pass failed, the Z pass was skipped
+    np.testing.assert_array_equal(np.sort(before[1] ^ np.uint64(1 << 10)), lo)
+    np.testing.assert_array_equal(re, np.full(64, 0.125))
+    # the state is usable again
+    st.apply(W.to_array([W.H(0)]), 0.0)
+    assert st.nnz() == 32
+    st.close()
+
+
+def test_probe_limit_reports_table_full_without_hanging():
+    st = sps.SparseState(30, 1 << 12)
+    st.apply(W.to_array([W.H(q) for q in range(8)]), 0.0)
+    st.sync()
+    st.set_option(sps.SPS_OPT_PROBE_LIMIT, 1)
+    st.set_option(sps.SPS_OPT_LOAD_FACTOR_PCT, 90)
+    st.apply(W.to_array([W.H(q) for q in range(8, 12)]), 0.0)
+    with pytest.raises(sps.SpsError) as e:
+        st.sync()
+    assert e.value.status == sps.SPS_ERR_TABLE_FULL
+    assert st.nnz() == 256                       # unchanged
+    st.set_option(sps.SPS_OPT_PROBE_LIMIT, 0)     # back to unbounded
+    st.apply(W.to_array([W.H(q) for q in range(8, 12)]), 0.0)
+    assert st.nnz() == 4096
+    st.close()
+
+
+def test_high_load_factor_collisions():
+    n = 50
+    gates = W.to_array([W.H(q) for q in range(12)] + [W.Ry(q, 0.3 * q) for q in range(12, 16)])
+    got, want = run_both(n, gates, eps=0.0, capacity=1 << 16,
+                         options=[(sps.SPS_OPT_LOAD_FACTOR_PCT, 90)])
+    compare_states(got, want, 0.0)
+
+
+def test_labels_with_all_ones_low_word():
+    """128-bit labels whose low 64 bits are all set go through the CAS-only
+    probe path; results must still match."""
+    n = 70
+    gates = W.to_array([W.X(q) for q in range(64)] + [W.H(q) for q in (0, 64, 65, 3)] +
+                       [W.Givens(1, 66, 0.9), W.Ry(2, 1.3, 64)] + [W.H(q) for q in (0, 64)])
+    got, want = run_both(n, gates, eps=1e-14)
+    compare_states(got, want, 1e-14)
+    assert np.any(got[1] == np.uint64(0xFFFFFFFFFFFFFFFF))
+
+
+def test_bad_gate_rejected_before_enqueue():
+    st = sps.SparseState(8, 16)
+    with pytest.raises(sps.SpsError) as e:
+        st.apply(W.to_array([W.H(0), W.X(9)]), 0.0)
+    assert e.value.status == sps.SPS_ERR_ARG and e.value.failed_gate == 1
+    hi, lo, re, im = st.get_amplitudes()
+    assert lo.tolist() == [0]
+    st.close()
+
+
+def test_set_get_roundtrip_and_rejects_out_of_range():
+    rng = np.random.default_rng(3)
+    for n in (30, 100):
+        st = sps.SparseState(n, 1000)
+        m = 777
+        lo = np.unique(rng.integers(0, 2 ** 30, m * 2, dtype=np.uint64))[:m]
+        hi = rng.integers(0, 2 ** (n - 64), m, dtype=np.uint64) if n > 64 else np.zeros(m, np.uint64)
+        re, im = rng.normal(size=m), rng.normal(size=m)
+        st.set_amplitudes(hi, lo, re, im)
+        g = st.get_amplitudes()
+        order = np.lexsort((lo, hi))
+        for a, b in zip(g, (hi[order], lo[order], re[order], im[order])):
+            np.testing.assert_array_equal(a, b)
+        bad_lo = lo.copy()
+        bad_lo[5] = np.uint64(1) << np.uint64(min(n, 63))
+        if n <= 63:
+            with pytest.raises(sps.SpsError):
+                st.set_amplitudes(hi, bad_lo, re, im)
+            assert st.nnz() == 1
+        st.close()
+
+
+def test_options_give_identical_results():
+    gates = plain24_gates(seed=3, ngates=600)
+    base, want = run_both(24, gates, eps=1e-14, capacity=8192)
+    compare_states(base, want, 1e-14)
+    for opts in ([(sps.SPS_OPT_BLOCK_THREADS, 128)], [(sps.SPS_OPT_MAX_FUSED_OPS, 3)],
+                 [(sps.SPS_OPT_LOAD_FACTOR_PCT, 25)]):
+        got, _ = run_both(24, gates, eps=1e-14, capacity=8192, options=opts)
+        compare_states(got, want, 1e-14)
+
+
+def test_counters_count_launches():
+    st = sps.SparseState(24, 4096)
+    c0 = st.counters().kernel_launches
+    st.apply(W.to_array([W.X(0), W.Z(1), W.H(2), W.CX(2, 3), W.H(4)]), 0.0)
+    c = st.counters()
+    assert c.fused_passes == 2 and c.branch_passes == 2
+    assert c.kernel_launches - c0 == 2 * 1 + 2 * 2
+    st.close()
