@@ -59,6 +59,12 @@ def make_workload(name: str):
                     readout=((0xFFFF, 0), (0, 0)),
                     desc="adder67-w24: as adder67 with a over 24 bits (16,777,216 nonzeros, "
                          "537 MB state)")
+    if name == "adder67-w22":
+        wl = W.adder_workload(seed=1, width=22)
+        return dict(name=name, gates=wl.gates, nqubits=wl.layout.nqubits, capacity=1 << 22,
+                    readout=((0xFFFF, 0), (0, 0)),
+                    desc="adder67-w22: as adder67 with a over 22 bits (4,194,304 nonzeros, "
+                         "134 MB state); profiling size")
     if name == "givens64":
         g = W.givens_workload(seed=2, nqubits=64, modes=4, layers=500)
         return dict(name=name, gates=g, nqubits=64, capacity=700_000,
@@ -285,8 +291,6 @@ def run_ours(args, dist, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    st.set_option(sps.SPS_OPT_PROFILE, 1)
-    st.profile_read()
     sampler = ClockSampler(gpu_id_for_smi()) if rank == 0 else None
     barrier(dist)
     torch.cuda.synchronize()
@@ -296,22 +300,35 @@ def run_ours(args, dist, rank, world, local_rank):
     c0 = st.counters().kernel_launches
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    records = []
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
-        if (i + 1) % 64 == 0:
-            records += st.profile_read()
     torch.cuda.synchronize()
     launches = st.counters().kernel_launches - c0
     barrier(dist)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
-    records += st.profile_read()
-    st.set_option(sps.SPS_OPT_PROFILE, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
+
+    # per-kernel times: the same steps again with every launch bracketed by
+    # CUDA events on the state's stream (kept out of the headline timing)
+    st.set_option(sps.SPS_OPT_PROFILE, 1)
+    st.profile_read()
+    records = []
+    prof_steps = min(args.steps, 20)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(prof_steps)]
+    for i in range(prof_steps):
+        flush.zero_()
+        pev[i][0].record(stream)
+        step()
+        pev[i][1].record(stream)
+        records += st.profile_read()
+    torch.cuda.synchronize()
+    st.set_option(sps.SPS_OPT_PROFILE, 0)
+    prof_ms = sum(a.elapsed_time(b) for a, b in pev) / prof_steps
     total_ms = max_over_ranks(dist, sum(step_ms))
     units = sum_over_ranks(dist, float(U) * args.steps)
     value = units / (total_ms * 1e-3)
@@ -321,6 +338,8 @@ def run_ours(args, dist, rank, world, local_rank):
 
     rl = roofline(records, wl["name"])
     rl["launches_per_step"] = round(launches / args.steps, 2)
+    rl["profiled_steps"] = prof_steps
+    rl["profiled_ms_per_step"] = round(prof_ms, 5)
     res = None
     if rank == 0:
         res = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -445,7 +464,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="adder67",
-                    choices=["adder67", "adder67-w24", "givens64"])
+                    choices=["adder67", "adder67-w22", "adder67-w24", "givens64"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

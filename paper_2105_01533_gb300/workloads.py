@@ -205,14 +205,19 @@ def random_mix(seed: int, nqubits: int, ngates: int, n_initial_h: int = 8,
 
 
 def random_all_gates(seed: int, nqubits: int, ngates: int, max_controls: int = 2,
-                     branch_frac: float = 0.3) -> np.ndarray:
+                     branch_frac: float = 0.3,
+                     keep_branch: Optional[KeepBranch] = None) -> np.ndarray:
     """Random circuit drawing every gate code, with 0..max_controls controls.
-    For small-n parity and pin tests."""
+    A branching candidate rejected by ``keep_branch`` becomes a
+    phase/permutation gate. For parity and pin tests."""
     rng = SplitMix64(seed)
     perm_diag = list(PERM_OPS + DIAG_OPS)
     out: List[tuple] = []
     for _ in range(ngates):
-        if rng.uniform() < branch_frac:
+        branch = rng.uniform() < branch_frac
+        if branch and keep_branch is not None and not keep_branch(out, None):
+            branch = False
+        if branch:
             op = BRANCH_OPS[rng.below(len(BRANCH_OPS))]
         else:
             op = perm_diag[rng.below(len(perm_diag))]

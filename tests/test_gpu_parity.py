@@ -66,8 +66,9 @@ def test_each_gate_type(n, op):
 
 @pytest.mark.parametrize("n,seed", [(12, 1), (40, 2), (63, 3), (64, 4), (90, 5), (127, 6)])
 def test_random_circuits_all_gates(n, seed):
-    gates = W.random_all_gates(seed, n, 400, max_controls=3, branch_frac=0.2)
-    got, want = run_both(n, gates, eps=1e-14, capacity=1 << 18)
+    gates = W.random_all_gates(seed, n, 400, max_controls=3, branch_frac=0.2,
+                               keep_branch=W.CountingBound(1 << 16))
+    got, want = run_both(n, gates, eps=1e-14, capacity=1 << 16)
     compare_states(got, want, 1e-14)
 
 
@@ -152,7 +153,8 @@ def test_givens_workload_full_properties():
 
 
 def test_probability_matches_oracle():
-    gates = W.random_all_gates(8, 70, 300, max_controls=2, branch_frac=0.2)
+    gates = W.random_all_gates(8, 70, 300, max_controls=2, branch_frac=0.2,
+                               keep_branch=W.CountingBound(1 << 16))
     st = sps.SparseState(70, 1 << 16)
     st.apply(gates, 1e-14)
     orc = OracleState(70)
