@@ -207,6 +207,40 @@ sps_status sps_plan(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                     uint32_t max_fused_ops, uint32_t* kind, uint64_t* first_gate,
                     uint32_t* ops, size_t cap, size_t* npasses, size_t* failed_gate);
 
+/* Allocation-free variant of one branching pass, for callers that must not
+ * allocate device memory (a host framework that owns all device memory and
+ * forbids library allocations, a service whose device footprint is fixed at
+ * start-up, or code running inside an allocator callback). The paper has no
+ * counterpart; it is an interface convenience.
+ * Applies ONE two-nonzero gate (`gate`: SPS_OP_H, RX, RY or GIVENS, host
+ * pointer) to the n_in entries in the caller's device arrays in_*, prunes as
+ * sps_apply does (prune_eps), and writes the result to the caller's device
+ * arrays out_* (out_cap entries each, not aliasing the inputs); *n_out (host)
+ * receives the count. nqubits (1..127) fixes the label width: for <= 63
+ * qubits in_hi/out_hi are ignored and may be NULL. Input labels must be
+ * distinct and use only qubits below nqubits.
+ * Scratch: a fixed 8 MiB + 64 B array inside the library image (262,144
+ * table slots and a control block), held by every GPU that loads the library
+ * until the process exits. It allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library call. Limit: n_in <= 65,536, else SPS_ERR_CAPACITY
+ * before anything is launched.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array and it keeps the last call's contents; each
+ * call clears the part it needs first. Calls that overlap on the GPU (on
+ * different streams, host threads or processes sharing a context) race on the
+ * array and give wrong results: serialise them. The call synchronises
+ * `cuda_stream` before returning.
+ * Errors: SPS_ERR_ARG (bad gate or pointers), SPS_ERR_CAPACITY (n_in too
+ * large, or more than out_cap entries result; *n_out = 0),
+ * SPS_ERR_TABLE_FULL, SPS_ERR_CUDA, SPS_ERR_NO_DEVICE. */
+sps_status sps_branch_apply_static(const sps_gate* gate, uint32_t nqubits,
+                                   const uint64_t* in_hi, const uint64_t* in_lo,
+                                   const double* in_re, const double* in_im, uint64_t n_in,
+                                   double prune_eps, uint64_t* out_hi, uint64_t* out_lo,
+                                   double* out_re, double* out_im, uint64_t out_cap,
+                                   uint64_t* n_out, void* cuda_stream);
+
 /* Static text for a status code. */
 const char* sps_status_str(sps_status st);
 

@@ -30,7 +30,8 @@ KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 
 EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_apply", "sps_sync",
            "sps_nnz", "sps_get_amplitudes", "sps_set_amplitudes", "sps_probability",
-           "sps_set_option", "sps_get_counters", "sps_profile_read", "sps_plan", "sps_status_str")
+           "sps_set_option", "sps_get_counters", "sps_profile_read", "sps_plan", "sps_status_str",
+           "sps_branch_apply_static")
 
 
 class SpsError(RuntimeError):
@@ -103,6 +104,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_get_counters.restype = st
     lib.sps_plan.argtypes = [vp, sz, u32, u32, vp, vp, vp, sz, psz, psz]
     lib.sps_plan.restype = st
+    lib.sps_branch_apply_static.argtypes = [vp, u32, vp, vp, vp, vp, u64, dbl, vp, vp, vp, vp,
+                                            u64, pu64, vp]
+    lib.sps_branch_apply_static.restype = st
     lib.sps_status_str.argtypes = [st]
     lib.sps_status_str.restype = ctypes.c_char_p
     _lib = lib
@@ -268,6 +272,24 @@ def sps_plan(gates, nqubits: int, max_fused_ops: int = 0):
     _check(rc, "sps_plan", bad.value if rc == SPS_ERR_ARG else None)
     n = npass.value
     return [(int(kind[i]), int(first[i]), int(ops[i])) for i in range(n)]
+
+
+def sps_branch_apply_static(gate, nqubits: int, in_arrays, n_in: int, prune_eps: float,
+                            out_arrays, out_cap: int, stream: Optional[int] = None) -> int:
+    """One branching gate on caller-owned device arrays, without allocating.
+    in_arrays / out_arrays: (hi, lo, re, im) device tensors (hi may be None
+    below 64 qubits). Returns the output count."""
+    g = gate_array(gate)
+    if g.size != 1:
+        raise ValueError("exactly one gate record")
+    n = ctypes.c_uint64(0)
+    ih, il, ir, ii = in_arrays
+    oh, ol, orr, oi = out_arrays
+    rc = load_library().sps_branch_apply_static(
+        _ptr(g), nqubits, _ptr(ih), _ptr(il), _ptr(ir), _ptr(ii), n_in, float(prune_eps),
+        _ptr(oh), _ptr(ol), _ptr(orr), _ptr(oi), out_cap, ctypes.byref(n), stream)
+    _check(rc, "sps_branch_apply_static")
+    return n.value
 
 
 def sps_status_str(code: int) -> str:
