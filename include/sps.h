@@ -112,7 +112,9 @@ void sps_destroy(sps_state* s);
 
 /* Applies `ngates` gates (host array, copied before return) in order, as one
  * batch: each maximal run of one-nonzero-per-row gates becomes one in-place
- * per-element pass (Sec. 3.2), each two-nonzero gate one branching pass
+ * per-element pass (Sec. 3.2; a run is cut after SPS_OPT_MAX_FUSED_OPS gates or
+ * when its P / RZ gates would need more than 61 phase slots, P taking one and
+ * RZ two), each two-nonzero gate one branching pass
  * (Sec. 3.1) after which entries with re*re + im*im < prune_eps^2 (strict) or
  * exactly zero are dropped. prune_eps >= 0.
  * The call only enqueues work on the state's stream. Records are validated on
@@ -161,8 +163,11 @@ typedef enum sps_option {
   SPS_OPT_BLOCK_THREADS = 3,   /* threads per block of the per-element kernels: 128..1024 */
   SPS_OPT_MAX_FUSED_OPS = 4,   /* longest op list of one fused pass, >= 1 (default 4096) */
   SPS_OPT_COOP_WIDTH = 5,      /* lanes probing one insert together: 1, 2, 4 or 8 */
-  SPS_OPT_PROFILE = 6          /* 1: time every kernel launch with CUDA events on the
+  SPS_OPT_PROFILE = 6,         /* 1: time every kernel launch with CUDA events on the
                                   state's stream and log its entry counts; 0: off */
+  SPS_OPT_BITSLICE_MIN_OPS = 7 /* fused passes with at least this many ops run
+                                  bit-sliced (labels as bit-planes, 32 entries per
+                                  logic op); 0 = never (default 8) */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:

@@ -60,6 +60,18 @@ struct sps_state {
   int threads = 256;
   uint32_t max_fused_ops = kDefaultMaxFusedOps;
   int coop = 1;
+  uint32_t bitslice_min_ops = 8;
+  // plan arena: bit-sliced op lists and phase tables of the current sps_apply
+  unsigned char* arena = nullptr;
+  size_t arena_cap = 0;
+  struct Staging {
+    unsigned char* host = nullptr;   // pinned
+    size_t cap = 0;
+    cudaEvent_t copied = nullptr;    // recorded after the copy out of `host`
+    bool pending = false;
+  };
+  Staging staging[4];
+  unsigned staging_next = 0;
   // profiling (SPS_OPT_PROFILE)
   bool profile = false;
   unsigned long long* dlog = nullptr;      // 2 words per profiled launch
@@ -118,6 +130,11 @@ void release_all(sps_state* s) {
   s->pending.clear();
   for (auto e : s->event_pool) cudaEventDestroy(e);
   s->event_pool.clear();
+  for (auto& st : s->staging) {
+    if (st.host) cudaFreeHost(st.host);
+    if (st.copied) cudaEventDestroy(st.copied);
+    st = sps_state::Staging();
+  }
   s->ctl_host = nullptr;
   s->hresult = nullptr;
   s->hflag = nullptr;
@@ -172,6 +189,58 @@ cudaEvent_t take_event(sps_state* s) {
     return nullptr;
   }
   return e;
+}
+
+// Makes the device plan arena at least `bytes` long. The old arena is released
+// in stream order, after the kernels already enqueued that read it.
+sps_status ensure_arena(sps_state* s, size_t bytes) {
+  if (bytes <= s->arena_cap) return SPS_OK;
+  size_t cap = s->arena_cap ? s->arena_cap : (1u << 20);
+  while (cap < bytes) cap *= 2;
+  void* p = s->alloc(s->alloc_ctx, cap, s->stream);
+  if (!p) return SPS_ERR_OOM;
+  if (s->arena) {
+    for (auto it = s->allocs.begin(); it != s->allocs.end(); ++it) {
+      if (it->ptr == s->arena) {
+        s->release(s->alloc_ctx, it->ptr, it->bytes, s->stream);
+        s->allocs.erase(it);
+        break;
+      }
+    }
+  }
+  s->allocs.push_back({p, cap});
+  s->arena = (unsigned char*)p;
+  s->arena_cap = cap;
+  return SPS_OK;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Next pinned staging buffer of at least `bytes`; waits only if the copy that
+// last used it has not finished (the ring lets the host run ahead of the GPU).
+sps_status take_staging(sps_state* s, size_t bytes, sps_state::Staging** out) {
+  sps_state::Staging& st = s->staging[s->staging_next];
+  s->staging_next = (s->staging_next + 1) % 4;
+  if (st.pending) {
+    if (cudaEventSynchronize(st.copied) != cudaSuccess) return cuda_ok(cudaGetLastError());
+    st.pending = false;
+  }
+  if (!st.copied && cudaEventCreateWithFlags(&st.copied, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_ok(cudaGetLastError());
+  if (st.cap < bytes) {
+    if (st.host) cudaFreeHost(st.host);
+    st.host = nullptr;
+    st.cap = 0;
+    size_t cap = 1u << 16;
+    while (cap < bytes) cap *= 2;
+    if (cudaMallocHost((void**)&st.host, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return SPS_ERR_OOM;
+    }
+    st.cap = cap;
+  }
+  *out = &st;
+  return SPS_OK;
 }
 
 // Brackets one launch with events when profiling; returns the log slot or null.
@@ -376,14 +445,71 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   }
   const LaunchCfg lc = cfg_of(s);
   const uint32_t limit = s->probe_limit ? s->probe_limit : (uint32_t)(s->table_slots > 0xFFFFFFFFull ? 0xFFFFFFFFu : s->table_slots);
+  // bit-sliced plans of long fused runs go to the device in one copy
+  std::vector<BsPass> bs(passes.size());
+  std::vector<size_t> bs_off(passes.size(), 0);
+  size_t arena_bytes = 0;
+  for (size_t i = 0; i < passes.size(); ++i) {
+    const Pass& p = passes[i];
+    if (p.kind != PASS_FUSED || s->bitslice_min_ops == 0 || p.ops.size() < s->bitslice_min_ops)
+      continue;
+    build_bitslice(p, s->nqubits, &bs[i]);
+    bs_off[i] = arena_bytes;
+    arena_bytes += align16(bs[i].ops.size() * sizeof(SOp)) + align16(bs[i].tables.size() * 8) +
+                   align16(bs[i].list.size());
+  }
+  if (arena_bytes) {
+    const sps_status as = ensure_arena(s, arena_bytes);
+    if (as != SPS_OK) return as;
+    sps_state::Staging* stg = nullptr;
+    const sps_status ss = take_staging(s, arena_bytes, &stg);
+    if (ss != SPS_OK) return ss;
+    for (size_t i = 0; i < passes.size(); ++i) {
+      if (bs[i].ops.empty()) continue;
+      unsigned char* dst = stg->host + bs_off[i];
+      std::memcpy(dst, bs[i].ops.data(), bs[i].ops.size() * sizeof(SOp));
+      dst += align16(bs[i].ops.size() * sizeof(SOp));
+      std::memcpy(dst, bs[i].tables.data(), bs[i].tables.size() * 8);
+      dst += align16(bs[i].tables.size() * 8);
+      if (!bs[i].list.empty()) std::memcpy(dst, bs[i].list.data(), bs[i].list.size());
+    }
+    // runs in stream order after earlier kernels that read the arena
+    if (cudaMemcpyAsync(s->arena, stg->host, arena_bytes, cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess ||
+        cudaEventRecord(stg->copied, s->stream) != cudaSuccess)
+      return cuda_ok(cudaGetLastError());
+    stg->pending = true;
+  }
   ++s->apply_serial;
-  for (const Pass& p : passes) {
+  for (size_t pi = 0; pi < passes.size(); ++pi) {
+    const Pass& p = passes[pi];
     const uint32_t serial = ++s->pass_serial;
     const uint64_t tag = ((uint64_t)s->apply_serial << 32) | (p.first_gate & 0xFFFFFFFFull);
     if (p.kind == PASS_FUSED) {
       const uint32_t flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
       ProfScope ps(s, 1, serial, (uint32_t)p.ops.size(), flags);
-      const int n = launch_fused(lc, s->kw, s->ctl, s->bufs, p, s->nnz_bound, ps.slot);
+      int n;
+      if (!bs[pi].ops.empty()) {
+        const BsPass& b = bs[pi];
+        BsLaunch bl;
+        const unsigned char* base = s->arena + bs_off[pi];
+        bl.ops = reinterpret_cast<const SOp*>(base);
+        base += align16(b.ops.size() * sizeof(SOp));
+        bl.tables = reinterpret_cast<const double*>(base);
+        base += align16(b.tables.size() * 8);
+        bl.list = base;
+        bl.nops = (uint32_t)b.ops.size();
+        bl.nw = b.nw;
+        bl.na = b.na;
+        bl.nchunks = b.nchunks();
+        bl.has_perm = p.has_perm;
+        bl.has_phase = p.has_phase;
+        bl.has_cnt = b.has_cnt;
+        bl.list_len = (uint32_t)b.list.size();
+        n = launch_fused_bs(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
+      } else {
+        n = launch_fused(lc, s->kw, s->ctl, s->bufs, p, s->nnz_bound, ps.slot);
+      }
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
       s->counters.fused_passes++;
@@ -571,6 +697,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_MAX_FUSED_OPS:
       if (v < 1 || v > (int64_t)kMaxFusedOps) return SPS_ERR_ARG;
       s->max_fused_ops = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_BITSLICE_MIN_OPS:
+      if (v < 0 || v > 1000000) return SPS_ERR_ARG;
+      s->bitslice_min_ops = (uint32_t)v;
       return SPS_OK;
     case SPS_OPT_PROFILE:
       if (v != 0 && v != 1) return SPS_ERR_ARG;

@@ -80,6 +80,7 @@ void lower_perm_diag(const sps_gate& g, Pass* p) {
       o.ph = static_cast<uint16_t>(p->phases.size());
       p->phases.push_back(pp);
       p->has_phase = true;
+      p->fire_slots += 1;
       break;
     }
     case SPS_OP_RZ: {  // diag(e^{-i theta/2}, e^{i theta/2}) selected by the target bit
@@ -89,6 +90,7 @@ void lower_perm_diag(const sps_gate& g, Pass* p) {
       o.ph = static_cast<uint16_t>(p->phases.size());
       p->phases.push_back(pp);
       p->has_phase = true;
+      p->fire_slots += 2;
       break;
     }
     default:
@@ -165,7 +167,9 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
       out->push_back(std::move(p));
       continue;
     }
-    if (run == nullptr || run->ops.size() >= max_fused_ops || run->phases.size() >= kMaxFusedPhases) {
+    const uint32_t slots = g.op == SPS_OP_P ? 1u : (g.op == SPS_OP_RZ ? 2u : 0u);
+    if (run == nullptr || run->ops.size() >= max_fused_ops || run->phases.size() >= kMaxFusedPhases ||
+        run->fire_slots + slots > kMaxFireSlots) {
       Pass p;
       p.kind = PASS_FUSED;
       p.first_gate = i;
@@ -175,6 +179,91 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
     lower_perm_diag(g, run);
   }
   return SPS_OK;
+}
+
+// ---- bit-sliced form ------------------------------------------------------------
+namespace {
+
+using cld = long double;
+struct CL { cld re, im; };
+CL cl_mul(CL a, CL b) { return CL{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+}  // namespace
+
+void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
+  *out = BsPass();
+  out->nw = (nqubits + 31) / 32;
+  bool cnt = false;
+  for (const FOp& o : p.ops) cnt = cnt || o.a0 != 0 || o.a1 != 0;
+  out->has_cnt = cnt;
+  const uint32_t label_rows = 32 * out->nw;
+  uint32_t aux = cnt ? 3u : 0u;
+  // factor of every aux bit, for the chunk tables
+  std::vector<CL> factor;
+  if (cnt) {
+    const cld r = std::sqrt((cld)0.5);
+    factor.push_back(CL{r, r});      // counter bit 0: e^{i pi/4}
+    factor.push_back(CL{0, 1});      // counter bit 1: e^{i pi/2}
+    factor.push_back(CL{-1, 0});     // counter bit 2: e^{i pi}
+  }
+  for (const FOp& o : p.ops) {
+    SOp so;
+    std::memset(&so, 0, sizeof(so));
+    std::vector<uint8_t> conds;
+    for (int w = 0; w < 2; ++w)
+      for (int b = 0; b < 64; ++b)
+        if ((o.c[w] >> b) & 1ull) conds.push_back((uint8_t)(64 * w + b));
+    if (conds.size() <= 3) {
+      so.nc = (uint8_t)conds.size();
+      for (size_t k = 0; k < conds.size(); ++k) so.c[k] = conds[k];
+    } else {
+      so.nc = SOP_LIST;
+      so.list_off = (uint16_t)out->list.size();
+      so.list_n = (uint16_t)conds.size();
+      out->list.insert(out->list.end(), conds.begin(), conds.end());
+    }
+    if (o.t[0] | o.t[1]) {
+      so.kind |= SOP_FLIP;
+      for (int w = 0; w < 2; ++w)
+        for (int b = 0; b < 64; ++b)
+          if ((o.t[w] >> b) & 1ull) so.t = (uint8_t)(64 * w + b);
+    }
+    if (o.sbit != NO_SEL) {
+      so.kind |= SOP_SEL;
+      so.s = o.sbit;
+    }
+    if (o.a0 || o.a1) {
+      so.kind |= SOP_CNT;
+      so.a0 = o.a0;
+      so.a1 = o.a1;
+    }
+    if (o.ph != NO_PH) {
+      const PhasePair& pp = p.phases[o.ph];
+      so.kind |= SOP_FIRE;
+      so.f0 = (uint8_t)(label_rows + aux++);
+      factor.push_back(CL{pp.re0, pp.im0});
+      if (o.sbit != NO_SEL) {
+        so.f1 = (uint8_t)(label_rows + aux++);
+        factor.push_back(CL{pp.re1, pp.im1});
+      }
+    }
+    out->ops.push_back(so);
+  }
+  out->aux_bits = aux;
+  out->na = (aux + 31) / 32;
+  const uint32_t nch = out->nchunks();
+  out->tables.assign((size_t)nch * 256 * 2, 0.0);
+  for (uint32_t c = 0; c < nch; ++c) {
+    for (uint32_t idx = 0; idx < 256; ++idx) {
+      CL acc{1, 0};
+      for (uint32_t b = 0; b < 8; ++b) {
+        const uint32_t bit = 8 * c + b;
+        if (((idx >> b) & 1u) && bit < aux) acc = cl_mul(acc, factor[bit]);
+      }
+      out->tables[((size_t)c * 256 + idx) * 2] = (double)acc.re;
+      out->tables[((size_t)c * 256 + idx) * 2 + 1] = (double)acc.im;
+    }
+  }
 }
 
 }  // namespace sps

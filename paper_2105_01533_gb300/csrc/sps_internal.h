@@ -58,6 +58,45 @@ struct BranchOp {
   double m_im[2][2];
 };
 
+// ---- bit-sliced form of a fused pass ------------------------------------------
+// Labels of 32 entries are transposed into bit-planes (one 32-bit word per
+// label bit, bit i = entry i). A gate then acts on 32 entries with a few logic
+// ops: X with controls c is P[t] ^= AND(P[c]); pi/4 phases add a constant to a
+// 3-plane counter; arbitrary phases record the planes on which they fire.
+// Plane rows 0 .. 32*nw-1 hold label bits (row = qubit), rows 32*nw .. hold
+// "aux" bits: 0..2 the counter (if any), then one fire plane per arbitrary
+// phase slot. After the op walk every entry gets its aux word back, and its
+// phase is the product over 8-bit chunks of precomputed tables.
+enum SOpKind : uint8_t { SOP_FLIP = 1, SOP_CNT = 2, SOP_FIRE = 4, SOP_SEL = 8 };
+constexpr uint8_t SOP_LIST = 0xFF;   // conditions come from the list
+
+struct SOp {                // 16 bytes
+  uint8_t kind;
+  uint8_t nc;               // 0..3 inline conditions, or SOP_LIST
+  uint8_t c[3];             // condition rows
+  uint8_t t;                // flip row
+  uint8_t s;                // selector row
+  uint8_t a0, a1;           // counter steps for sel = 0 / 1
+  uint8_t f0, f1;           // aux rows written for sel = 0 / sel = 1 (f1 only with SEL)
+  uint8_t reserved;
+  uint16_t list_off, list_n;
+};
+static_assert(sizeof(SOp) == 16, "SOp layout");
+
+constexpr uint32_t kMaxAuxBits = 64;     // counter (3) + fire slots
+constexpr uint32_t kMaxFireSlots = kMaxAuxBits - 3;
+
+struct BsPass {
+  uint32_t nw = 0;          // label words of 32 bits transposed
+  uint32_t na = 0;          // aux words
+  uint32_t aux_bits = 0;
+  bool has_cnt = false;
+  std::vector<SOp> ops;
+  std::vector<uint8_t> list;
+  std::vector<double> tables;   // nchunks * 256 * (re, im)
+  uint32_t nchunks() const { return (aux_bits + 7) / 8; }
+};
+
 // ---- a compiled pass -----------------------------------------------------------
 enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2 };
 
@@ -69,9 +108,13 @@ struct Pass {
   std::vector<PhasePair> phases;
   bool has_perm = false;    // some op flips label bits
   bool has_phase = false;   // some op changes amplitudes
+  uint32_t fire_slots = 0;  // aux bits its arbitrary phases need in bit-sliced form
   // branch
   BranchOp br{};
 };
+
+// Builds the bit-sliced form of a fused pass for an nqubits-qubit state.
+void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out);
 
 // Op lists travel as kernel parameters (<= 32 KB), which bounds one fused pass.
 constexpr uint32_t kMaxFusedOps = 512;
@@ -144,6 +187,15 @@ int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, 
                        const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog);
 int launch_branch_compact(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,
                           const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog);
+struct BsLaunch {
+  const SOp* ops;           // device copies (plan arena)
+  const uint8_t* list;
+  const double* tables;
+  uint32_t nops, nw, na, nchunks;
+  uint32_t has_perm, has_phase, has_cnt, list_len;
+};
+int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
+                    uint64_t nnz_bound, unsigned long long* plog);
 int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
                        double* partials, int nblocks, double* result);

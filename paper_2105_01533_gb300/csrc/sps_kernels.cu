@@ -157,6 +157,187 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
 }
 
 // ---------------------------------------------------------------------------
+// Bit-sliced fused pass. A warp owns a tile of `groups` x 32 entries:
+//   1. load: 32 entries at a time, each 32-bit label word is transposed across
+//      the warp (shuffle butterfly), so lane j holds bit-plane j of the group;
+//      planes go to shared memory, row = plane, column = group (stride 33 keeps
+//      every access bank-conflict free);
+//   2. walk: lane g runs the op list on group g's planes (one logic op handles
+//      32 entries), keeping the pi/4 counter in three registers and writing the
+//      fire planes of arbitrary phases to aux rows;
+//   3. store: planes are transposed back; labels are written if the pass
+//      permutes; the aux word selects precomputed chunk phases, multiplied
+//      into the amplitude only where it is not 1.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, unsigned lane) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const uint32_t mk = m == 16 ? 0x0000FFFFu : m == 8 ? 0x00FF00FFu : m == 4 ? 0x0F0F0F0Fu
+                      : m == 2 ? 0x33333333u : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(FULL, x, m);
+    x = (lane & m) == 0 ? ((x & mk) | ((y & mk) << m)) : ((x & ~mk) | ((y >> m) & mk));
+  }
+  return x;
+}
+
+// adds the constant k (0..7) to the 3-plane counter where f is set
+__device__ __forceinline__ void cnt_add(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t k,
+                                        uint32_t f) {
+  if (k & 1u) {
+    const uint32_t carry0 = c0 & f;
+    c0 ^= f;
+    const uint32_t carry1 = c1 & carry0;
+    c1 ^= carry0;
+    c2 ^= carry1;
+  }
+  if (k & 2u) {
+    const uint32_t carry1 = c1 & f;
+    c1 ^= f;
+    c2 ^= carry1;
+  }
+  if (k & 4u) c2 ^= f;
+}
+
+struct BsArgs {
+  const SOp* ops;
+  const uint8_t* list;
+  const double* tables;
+  uint32_t nops, nw, na, nchunks;
+  uint32_t has_perm, has_phase, has_cnt, list_len;
+  uint32_t groups;   // groups of 32 entries per warp tile (1..32)
+};
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_fused_bs(Ctl* ctl, Bufs bufs,
+                                                  const __grid_constant__ BsArgs a,
+                                                  unsigned long long* plog) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SOp* sops = reinterpret_cast<SOp*>(smem);
+  double2* stab = reinterpret_cast<double2*>(smem + 16 * a.nops);
+  uint8_t* slist = reinterpret_cast<uint8_t*>(stab + 256 * a.nchunks);
+  uint32_t* splanes =
+      reinterpret_cast<uint32_t*>(smem + ((16 * a.nops + 4096 * a.nchunks + a.list_len + 15) & ~15u));
+  const uint64_t n = ctl->nnz;
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+    plog[0] = n;
+    plog[1] = n;
+  }
+  if (ctl->status != 0u) return;
+  // stage the op list, the phase tables and the condition list
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.ops);
+    uint4* dst = reinterpret_cast<uint4*>(sops);
+    for (uint32_t i = threadIdx.x; i < a.nops; i += blockDim.x) dst[i] = src[i];
+    const double2* ts = reinterpret_cast<const double2*>(a.tables);
+    for (uint32_t i = threadIdx.x; i < 256 * a.nchunks; i += blockDim.x) stab[i] = ts[i];
+    for (uint32_t i = threadIdx.x; i < a.list_len; i += blockDim.x) slist[i] = a.list[i];
+  }
+  __syncthreads();
+  const SoA s = pick(bufs, ctl->cur);
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned warp = threadIdx.x >> 5;
+  const uint32_t rows = 32u * (a.nw + a.na);
+  uint32_t* pl = splanes + (size_t)warp * rows * 33u;
+  const uint32_t G = a.groups;
+  const uint64_t tile_entries = 32ull * G;
+  const uint64_t ntiles = (n + tile_entries - 1) / tile_entries;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < ntiles;
+       tile += nwarps) {
+    const uint64_t base = tile * tile_entries;
+    // 1. load and transpose
+    for (uint32_t g = 0; g < G; ++g) {
+      const uint64_t e = base + 32ull * g + lane;
+      const bool valid = e < n;
+      const uint64_t lo = valid ? s.lo[e] : 0ull;
+      const uint64_t hi = (KW == 2 && valid) ? s.hi[e] : 0ull;
+      for (uint32_t w = 0; w < a.nw; ++w) {
+        const uint64_t src = w < 2 ? lo : hi;
+        const uint32_t x = (uint32_t)(src >> (32 * (w & 1u)));
+        pl[(32u * w + lane) * 33u + g] = transpose32(x, lane);
+      }
+    }
+    for (uint32_t r = 32u * a.nw; r < rows; ++r) pl[r * 33u + lane] = 0u;
+    __syncwarp();
+    // 2. op walk, lane g on group g
+    if (lane < G) {
+      uint32_t* col = pl + lane;
+      uint32_t c0 = 0u, c1 = 0u, c2 = 0u;
+      for (uint32_t j = 0; j < a.nops; ++j) {
+        const SOp o = sops[j];
+        uint32_t f = 0xFFFFFFFFu;
+        if (o.nc != SOP_LIST) {
+          if (o.nc > 0) f &= col[o.c[0] * 33u];
+          if (o.nc > 1) f &= col[o.c[1] * 33u];
+          if (o.nc > 2) f &= col[o.c[2] * 33u];
+        } else {
+          for (uint32_t k = 0; k < o.list_n; ++k) f &= col[slist[o.list_off + k] * 33u];
+        }
+        const uint32_t sel = (o.kind & SOP_SEL) ? col[o.s * 33u] : 0u;
+        if (o.kind & SOP_CNT) {
+          cnt_add(c0, c1, c2, o.a0, f & ~sel);
+          if (o.kind & SOP_SEL) cnt_add(c0, c1, c2, o.a1, f & sel);
+        }
+        if (o.kind & SOP_FIRE) {
+          col[o.f0 * 33u] = f & ~sel;
+          if (o.kind & SOP_SEL) col[o.f1 * 33u] = f & sel;
+        }
+        if (o.kind & SOP_FLIP) col[o.t * 33u] ^= f;
+      }
+      if (a.has_cnt) {
+        const uint32_t r0 = 32u * a.nw;
+        col[r0 * 33u] = c0;
+        col[(r0 + 1u) * 33u] = c1;
+        col[(r0 + 2u) * 33u] = c2;
+      }
+    }
+    __syncwarp();
+    // 3. transpose back and store
+    for (uint32_t g = 0; g < G; ++g) {
+      const uint64_t e = base + 32ull * g + lane;
+      const bool valid = e < n;
+      uint64_t lo = 0ull, hi = 0ull;
+      for (uint32_t w = 0; w < a.nw; ++w) {
+        const uint64_t x = transpose32(pl[(32u * w + lane) * 33u + g], lane);
+        if (w < 2) lo |= x << (32 * w); else hi |= x << (32 * (w - 2));
+      }
+      uint32_t aux0 = 0u, aux1 = 0u;
+      if (a.na > 0) aux0 = transpose32(pl[(32u * a.nw + lane) * 33u + g], lane);
+      if (a.na > 1) aux1 = transpose32(pl[(32u * (a.nw + 1u) + lane) * 33u + g], lane);
+      if (valid) {
+        if (a.has_perm) {
+          s.lo[e] = lo;
+          if (KW == 2) s.hi[e] = hi;
+        }
+        if (a.has_phase && (aux0 | aux1)) {
+          double pr = 1.0, pi = 0.0;
+          bool any = false;
+          for (uint32_t c = 0; c < a.nchunks; ++c) {
+            const uint32_t word = c < 4 ? aux0 : aux1;
+            const uint32_t idx = (word >> (8 * (c & 3u))) & 0xFFu;
+            if (idx == 0u) continue;
+            const double2 t = stab[c * 256u + idx];
+            if (!any) {
+              pr = t.x;
+              pi = t.y;
+              any = true;
+            } else {
+              const double nr = pr * t.x - pi * t.y;
+              const double ni = pr * t.y + pi * t.x;
+              pr = nr;
+              pi = ni;
+            }
+          }
+          const double re = s.re[e], im = s.im[e];
+          s.re[e] = re * pr - im * pi;
+          s.im[e] = re * pi + im * pr;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 __global__ void k_table_clear(Slot* table, uint64_t nslots) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nslots;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -492,6 +673,50 @@ int fused_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const Pass& p, uint64_t n
   return -1;
 }
 
+size_t bs_smem_fixed(const BsLaunch& b) {
+  return ((16 * (size_t)b.nops + 4096 * (size_t)b.nchunks + b.list_len + 15) & ~(size_t)15);
+}
+
+template <int KW>
+int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uint64_t nnz_bound,
+                unsigned long long* plog) {
+  BsArgs a;
+  a.ops = b.ops;
+  a.list = b.list;
+  a.tables = b.tables;
+  a.nops = b.nops;
+  a.nw = b.nw;
+  a.na = b.na;
+  a.nchunks = b.nchunks;
+  a.has_perm = b.has_perm;
+  a.has_phase = b.has_phase;
+  a.has_cnt = b.has_cnt;
+  a.list_len = b.list_len;
+  const size_t fixed = bs_smem_fixed(b);
+  const size_t per_warp = (size_t)32 * (b.nw + b.na) * 33 * 4;
+  const size_t budget = 200 * 1024;
+  int warps = 8;
+  while (warps > 1 && fixed + warps * per_warp > budget) warps >>= 1;
+  if (fixed + warps * per_warp > budget) return -1;
+  const size_t smem = fixed + warps * per_warp;
+  // enough warps to fill the GPU: tiles of 32 x G entries
+  const uint64_t want_warps = (uint64_t)(lc.max_blocks > 0 ? lc.max_blocks : 1) * 4;
+  uint64_t g = (nnz_bound + 32 * want_warps - 1) / (32 * want_warps);
+  if (g < 1) g = 1;
+  if (g > 32) g = 32;
+  a.groups = (uint32_t)g;
+  const uint64_t tiles = (nnz_bound + 32 * g - 1) / (32 * g);
+  uint64_t blocks = (tiles + warps - 1) / warps;
+  const int per_sm_blocks = (int)((227 * 1024) / (smem + 1024));
+  const uint64_t max_blocks = (uint64_t)(lc.max_blocks / 8 > 0 ? lc.max_blocks / 8 : 1) *
+                              (per_sm_blocks > 0 ? per_sm_blocks : 1);
+  if (blocks > max_blocks) blocks = max_blocks;
+  if (blocks < 1) blocks = 1;
+  cudaFuncSetAttribute(k_fused_bs<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_fused_bs<KW><<<(int)blocks, warps * 32, smem, (cudaStream_t)lc.stream>>>(ctl, bufs, a, plog);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 BranchArgs branch_args(const BranchLaunch& b) {
   BranchArgs a;
   a.op = b.op;
@@ -518,6 +743,13 @@ int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const 
   if (p.ops.empty()) return 0;
   return key_words == 1 ? fused_kw<1>(lc, ctl, bufs, p, nnz_bound, plog)
                         : fused_kw<2>(lc, ctl, bufs, p, nnz_bound, plog);
+}
+
+int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
+                    uint64_t nnz_bound, unsigned long long* plog) {
+  if (b.nops == 0) return 0;
+  return key_words == 1 ? fused_bs_kw<1>(lc, ctl, bufs, b, nnz_bound, plog)
+                        : fused_bs_kw<2>(lc, ctl, bufs, b, nnz_bound, plog);
 }
 
 int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,

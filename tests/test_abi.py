@@ -74,13 +74,20 @@ def test_plan_splits_at_every_branching_gate(lib):
     gates = W.random_mix(3, 24, 400, keep_branch=W.CountingBound(4096), p_perm=0.5, p_diag=0.3)
     plan = sps.sps_plan(gates, 24)
     kinds = [classify(int(op)) for op in gates["op"]]
-    # rebuild the expected plan: maximal runs of kind 1, single passes of kind 2
+    # expected plan: runs of kind 1, cut where a run would pass 61 arbitrary-
+    # phase slots (P takes 1, Rz 2); single passes of kind 2
     want = []
+    slots = 0
     for i, k in enumerate(kinds):
+        op = int(gates["op"][i])
+        need = 1 if op == W.OP_P else (2 if op == W.OP_RZ else 0)
         if k == 2:
             want.append((2, i))
-        elif not want or want[-1][0] == 2:
+        elif not want or want[-1][0] == 2 or slots + need > 61:
             want.append((1, i))
+            slots = need
+        else:
+            slots += need
     assert [(k, f) for k, f, _ in plan] == want
     # op count of a fused pass = number of gates in the run
     bounds = [f for _, f, _ in plan] + [len(gates)]

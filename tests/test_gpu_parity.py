@@ -305,3 +305,61 @@ def test_counters_count_launches():
     assert c.fused_passes == 2 and c.branch_passes == 2
     assert c.kernel_launches - c0 == 2 * 1 + 2 * 2
     st.close()
+
+
+# ---- bit-sliced fused passes ------------------------------------------------------
+def perm_diag_run(seed, n, ngates, max_controls=5, p_arbitrary=0.15):
+    """A long phase/permutation run drawing X, Y, Z, S, Sdg, T, Tdg, P, Rz with
+    0..max_controls controls."""
+    rng = W.SplitMix64(seed)
+    codes = [W.OP_X, W.OP_Y, W.OP_Z, W.OP_S, W.OP_SDG, W.OP_T, W.OP_TDG]
+    recs = []
+    for _ in range(ngates):
+        if rng.uniform() < p_arbitrary:
+            op = (W.OP_P, W.OP_RZ)[rng.below(2)]
+        else:
+            op = codes[rng.below(len(codes))]
+        qs = rng.distinct(n, 1 + rng.below(max_controls + 1))
+        recs.append(W.gate(op, qs[0], qs[1:], rng.angle()))
+    return W.to_array(recs)
+
+
+@pytest.mark.parametrize("n", [9, 24, 40, 64, 100, 127])
+@pytest.mark.parametrize("min_ops", [1, 0])
+def test_bitslice_and_direct_long_runs(n, min_ops):
+    rng = W.SplitMix64(n)
+    k = min(n, 12)
+    prep = W.to_array([W.H(q) for q in rng.distinct(n, k)] + [W.Ry(rng.below(n), 0.77)])
+    gates = np.concatenate([prep, perm_diag_run(100 + n, n, 300)])
+    got, want = run_both(n, gates, eps=1e-14, capacity=1 << 14,
+                         options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, min_ops)])
+    compare_states(got, want, 1e-14)
+
+
+def test_bitslice_many_phase_slots_and_split():
+    """More arbitrary phases than one pass holds: 70 Rz (140 fire slots) plus
+    40 P; the compiler splits the run, each part uses two aux words."""
+    n = 30
+    rng = W.SplitMix64(77)
+    prep = [W.H(q) for q in range(10)]
+    run = [W.Rz(rng.below(n), rng.angle(), *([rng.below(10)] if rng.below(2) else []))
+           for _ in range(70)]
+    run += [W.CP(rng.below(10), 10 + rng.below(20), rng.angle()) for _ in range(40)]
+    run = [g for g in run if g[5][0] & (1 << g[2]) == 0]   # control never on the target
+    gates = W.to_array(prep + run + [W.X(q, (q + 1) % 10) for q in range(10)])
+    plan = sps.sps_plan(gates, n)
+    assert sum(1 for k, _, _ in plan if k == 1) >= 2
+    got, want = run_both(n, gates, eps=1e-14, options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1)])
+    compare_states(got, want, 1e-14)
+
+
+@pytest.mark.parametrize("nnz_log2", [5, 10, 15, 17])
+def test_bitslice_sizes(nnz_log2):
+    """Tiles of 1..32 groups and a ragged tail: 2^k entries plus a few."""
+    n = 70
+    prep = [W.H(q) for q in range(nnz_log2)] + [W.Ry(40, 0.3, 0)] + [W.H(41, 1)]
+    gates = np.concatenate([W.to_array(prep), perm_diag_run(9, n, 200, max_controls=3)])
+    got, want = run_both(n, gates, eps=1e-14, capacity=1 << 19,
+                         options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1)])
+    compare_states(got, want, 1e-14)
+    assert len(got[1]) > (1 << nnz_log2)
