@@ -189,7 +189,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact"}
+KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact", 4: "k_small_run"}
 
 
 def algorithmic_bytes(r) -> float:
@@ -203,6 +203,8 @@ def algorithmic_bytes(r) -> float:
         return per * r["n_in"]
     if r["kind"] == 2:
         return (lb + 16) * r["n_in"]
+    if r["kind"] == 4:   # a run of passes in shared memory: read the state once, write it once
+        return (lb + 16) * (r["n_in"] + r["n_out"])
     return (lb + 16) * r["n_out"]
 
 
@@ -237,7 +239,7 @@ def roofline(records, workload: str):
         b["ms"] += r["ms"]
         b["bytes"] += algorithmic_bytes(r)
         b["n"] += 1
-        b["entries"] += r["n_in"] if r["kind"] != 3 else r["n_out"]
+        b["entries"] += r["n_out"] if r["kind"] == 3 else r["n_in"]
     total = sum(b["ms"] for b in by.values()) or 1.0
     kind = max(by, key=lambda k: by[k]["ms"])
     b = by[kind]

@@ -165,9 +165,13 @@ typedef enum sps_option {
   SPS_OPT_COOP_WIDTH = 5,      /* lanes probing one insert together: 1, 2, 4 or 8 */
   SPS_OPT_PROFILE = 6,         /* 1: time every kernel launch with CUDA events on the
                                   state's stream and log its entry counts; 0: off */
-  SPS_OPT_BITSLICE_MIN_OPS = 7 /* fused passes with at least this many ops run
+  SPS_OPT_BITSLICE_MIN_OPS = 7, /* fused passes with at least this many ops run
                                   bit-sliced (labels as bit-planes, 32 entries per
                                   logic op); 0 = never (default 8) */
+  SPS_OPT_SMALL_RUN_CAP = 8    /* consecutive passes whose nonzero bound stays at
+                                  most this (<= 2048, default 2048) run in one
+                                  single-block launch with the state in shared
+                                  memory; 0 = never */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:

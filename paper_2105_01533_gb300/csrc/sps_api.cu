@@ -61,6 +61,7 @@ struct sps_state {
   uint32_t max_fused_ops = kDefaultMaxFusedOps;
   int coop = 1;
   uint32_t bitslice_min_ops = 8;
+  uint32_t small_cap = kSmallCap;   // 0 disables small-state runs
   // plan arena: bit-sliced op lists and phase tables of the current sps_apply
   unsigned char* arena = nullptr;
   size_t arena_cap = 0;
@@ -445,19 +446,99 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   }
   const LaunchCfg lc = cfg_of(s);
   const uint32_t limit = s->probe_limit ? s->probe_limit : (uint32_t)(s->table_slots > 0xFFFFFFFFull ? 0xFFFFFFFFu : s->table_slots);
-  // bit-sliced plans of long fused runs go to the device in one copy
+  // 1. segments of consecutive passes that a small-state run can take: the
+  //    nonzero bound (doubling per branching pass) stays within small_cap
+  std::vector<size_t> seg_end(passes.size(), 0);   // > 0: a run starts here, ends there
+  {
+    uint64_t b = s->nnz_bound;
+    for (size_t i = 0; i < passes.size();) {
+      if (s->small_cap && b <= s->small_cap) {
+        size_t j = i;
+        uint64_t bb = b;
+        while (j < passes.size()) {
+          const uint64_t after =
+              passes[j].kind == PASS_BRANCH ? (2 * bb < s->capacity ? 2 * bb : s->capacity) : bb;
+          if (after > s->small_cap) break;
+          bb = after;
+          ++j;
+        }
+        if (j > i) {
+          seg_end[i] = j;
+          b = bb;
+          i = j;
+          continue;
+        }
+      }
+      if (passes[i].kind == PASS_BRANCH) b = 2 * b < s->capacity ? 2 * b : s->capacity;
+      ++i;
+    }
+  }
+  // 2. device data: bit-sliced plans of long fused runs outside small runs, and
+  //    the records of the small runs, packed into one upload
   std::vector<BsPass> bs(passes.size());
   std::vector<size_t> bs_off(passes.size(), 0);
+  std::vector<size_t> run_off(passes.size(), 0);
   size_t arena_bytes = 0;
-  for (size_t i = 0; i < passes.size(); ++i) {
-    const Pass& p = passes[i];
-    if (p.kind != PASS_FUSED || s->bitslice_min_ops == 0 || p.ops.size() < s->bitslice_min_ops)
-      continue;
-    build_bitslice(p, s->nqubits, &bs[i]);
-    bs_off[i] = arena_bytes;
-    arena_bytes += align16(bs[i].ops.size() * sizeof(SOp)) + align16(bs[i].tables.size() * 8) +
-                   align16(bs[i].list.size());
+  std::vector<unsigned char> blob;   // small-run payloads, appended after the bit-sliced plans
+  {
+    size_t i = 0;
+    while (i < passes.size()) {
+      if (seg_end[i]) {
+        i = seg_end[i];
+        continue;
+      }
+      const Pass& p = passes[i];
+      if (p.kind == PASS_FUSED && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops) {
+        build_bitslice(p, s->nqubits, &bs[i]);
+        bs_off[i] = arena_bytes;
+        arena_bytes += align16(bs[i].ops.size() * sizeof(SOp)) + align16(bs[i].tables.size() * 8) +
+                       align16(bs[i].list.size());
+      }
+      ++i;
+    }
   }
+  {
+    uint32_t serial = s->pass_serial;
+    const uint64_t next_apply = (uint64_t)s->apply_serial + 1;
+    size_t i = 0;
+    auto put = [&](const void* src, size_t bytes) {
+      const size_t at = blob.size();
+      blob.resize(align16(at + bytes), 0);
+      std::memcpy(blob.data() + at, src, bytes);
+      return at;
+    };
+    while (i < passes.size()) {
+      if (!seg_end[i]) {
+        ++serial;
+        ++i;
+        continue;
+      }
+      const size_t j = seg_end[i];
+      std::vector<RunPass> recs(j - i);
+      std::vector<size_t> payload(j - i, 0);
+      for (size_t k = i; k < j; ++k) {
+        const Pass& p = passes[k];
+        RunPass& r = recs[k - i];
+        std::memset(&r, 0, sizeof(r));
+        r.kind = p.kind;
+        r.pass_serial = ++serial;
+        r.fail_tag = (next_apply << 32) | (p.first_gate & 0xFFFFFFFFull);
+        r.eps2 = prune_eps * prune_eps;
+        if (p.kind == PASS_FUSED) {
+          r.nops = (uint32_t)p.ops.size();
+          r.flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
+          r.ops_off = (uint32_t)put(p.ops.data(), p.ops.size() * sizeof(FOp));
+          r.ph_off = p.phases.empty() ? 0u : (uint32_t)put(p.phases.data(), p.phases.size() * sizeof(PhasePair));
+        } else {
+          r.br_off = (uint32_t)put(&p.br, sizeof(BranchOp));
+        }
+      }
+      run_off[i] = put(recs.data(), recs.size() * sizeof(RunPass));
+      i = j;
+    }
+  }
+  const size_t blob_base = arena_bytes;
+  arena_bytes += blob.size();
   if (arena_bytes) {
     const sps_status as = ensure_arena(s, arena_bytes);
     if (as != SPS_OK) return as;
@@ -473,6 +554,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       dst += align16(bs[i].tables.size() * 8);
       if (!bs[i].list.empty()) std::memcpy(dst, bs[i].list.data(), bs[i].list.size());
     }
+    if (!blob.empty()) std::memcpy(stg->host + blob_base, blob.data(), blob.size());
     // runs in stream order after earlier kernels that read the arena
     if (cudaMemcpyAsync(s->arena, stg->host, arena_bytes, cudaMemcpyHostToDevice, s->stream) !=
             cudaSuccess ||
@@ -483,6 +565,27 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   ++s->apply_serial;
   for (size_t pi = 0; pi < passes.size(); ++pi) {
     const Pass& p = passes[pi];
+    if (seg_end[pi]) {
+      const size_t j = seg_end[pi];
+      uint32_t nbranch = 0;
+      for (size_t k = pi; k < j; ++k) nbranch += passes[k].kind == PASS_BRANCH ? 1u : 0u;
+      ProfScope ps(s, 4, s->pass_serial + 1, (uint32_t)(j - pi), 3u);
+      const int n = launch_small_run(s->stream, s->kw, s->ctl, s->bufs, s->arena,
+                                     (uint32_t)(blob_base + run_off[pi]), (uint32_t)(j - pi),
+                                     s->capacity, ps.slot);
+      ps.done();
+      if (n < 0) return cuda_ok(cudaGetLastError());
+      s->pass_serial += (uint32_t)(j - pi);
+      s->counters.branch_passes += nbranch;
+      s->counters.fused_passes += (j - pi) - nbranch;
+      s->counters.kernel_launches += 1;
+      for (uint32_t k = 0; k < nbranch; ++k) {
+        const uint64_t nb = s->nnz_bound * 2;
+        s->nnz_bound = nb < s->capacity ? nb : s->capacity;
+      }
+      pi = j - 1;
+      continue;
+    }
     const uint32_t serial = ++s->pass_serial;
     const uint64_t tag = ((uint64_t)s->apply_serial << 32) | (p.first_gate & 0xFFFFFFFFull);
     if (p.kind == PASS_FUSED) {
@@ -697,6 +800,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_MAX_FUSED_OPS:
       if (v < 1 || v > (int64_t)kMaxFusedOps) return SPS_ERR_ARG;
       s->max_fused_ops = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_SMALL_RUN_CAP:
+      if (v < 0 || v > (int64_t)kSmallCap) return SPS_ERR_ARG;
+      s->small_cap = (uint32_t)v;
       return SPS_OK;
     case SPS_OPT_BITSLICE_MIN_OPS:
       if (v < 0 || v > 1000000) return SPS_ERR_ARG;

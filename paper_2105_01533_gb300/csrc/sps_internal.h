@@ -113,6 +113,25 @@ struct Pass {
   BranchOp br{};
 };
 
+// One pass of a small-state run (k_small_run), stored in the plan arena.
+struct RunPass {            // 48 bytes
+  uint32_t kind;            // PASS_FUSED or PASS_BRANCH
+  uint32_t nops;            // fused: ops
+  uint32_t ops_off;         // byte offset of the FOp array in the arena
+  uint32_t ph_off;          // byte offset of the PhasePair array
+  uint32_t br_off;          // byte offset of the BranchOp
+  uint32_t flags;           // bit 0: permutes, bit 1: changes amplitudes
+  uint32_t pass_serial;
+  uint32_t reserved;
+  uint64_t fail_tag;
+  double eps2;
+};
+static_assert(sizeof(RunPass) == 48, "RunPass layout");
+
+constexpr uint32_t kSmallCap = 2048;          // entries a small-state run holds
+constexpr uint32_t kSmallThreads = 1024;
+constexpr uint32_t kSmallTableSlots = 8192;   // input index table, load <= 25%
+
 // Builds the bit-sliced form of a fused pass for an nqubits-qubit state.
 void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out);
 
@@ -196,6 +215,11 @@ struct BsLaunch {
 };
 int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
                     uint64_t nnz_bound, unsigned long long* plog);
+// Runs npasses consecutive passes (RunPass records at arena + pass_off) in one
+// CTA with the state in shared memory; the host guarantees nnz <= kSmallCap.
+int launch_small_run(void* stream, int key_words, Ctl* ctl, Bufs bufs, const unsigned char* arena,
+                     uint32_t pass_off, uint32_t npasses, uint64_t capacity,
+                     unsigned long long* plog);
 int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
                        double* partials, int nblocks, double* result);

@@ -72,7 +72,8 @@ def test_random_circuits_all_gates(n, seed):
     compare_states(got, want, 1e-14)
 
 
-def test_branching_only_is_bit_identical():
+@pytest.mark.parametrize("small_cap", [2048, 0])
+def test_branching_only_is_bit_identical(small_cap):
     n = 30
     rng = W.SplitMix64(5)
     recs = []
@@ -86,7 +87,7 @@ def test_branching_only_is_bit_identical():
         else:
             recs.append(W.Givens(q[0], q[1], rng.angle()))
     gates = W.to_array(recs)
-    got, want = run_both(n, gates, eps=0.0)
+    got, want = run_both(n, gates, eps=0.0, options=[(sps.SPS_OPT_SMALL_RUN_CAP, small_cap)])
     for a, b in zip(got, want):
         np.testing.assert_array_equal(a, b)
 
@@ -221,6 +222,7 @@ def test_capacity_overflow_leaves_last_good_state():
 
 def test_probe_limit_reports_table_full_without_hanging():
     st = sps.SparseState(30, 1 << 12)
+    st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)      # exercise the global table
     st.apply(W.to_array([W.H(q) for q in range(8)]), 0.0)
     st.sync()
     st.set_option(sps.SPS_OPT_PROBE_LIMIT, 1)
@@ -240,7 +242,8 @@ def test_high_load_factor_collisions():
     n = 50
     gates = W.to_array([W.H(q) for q in range(12)] + [W.Ry(q, 0.3 * q) for q in range(12, 16)])
     got, want = run_both(n, gates, eps=0.0, capacity=1 << 16,
-                         options=[(sps.SPS_OPT_LOAD_FACTOR_PCT, 90)])
+                         options=[(sps.SPS_OPT_LOAD_FACTOR_PCT, 90),
+                                  (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
     compare_states(got, want, 0.0)
 
 
@@ -292,18 +295,49 @@ def test_options_give_identical_results():
     base, want = run_both(24, gates, eps=1e-14, capacity=8192)
     compare_states(base, want, 1e-14)
     for opts in ([(sps.SPS_OPT_BLOCK_THREADS, 128)], [(sps.SPS_OPT_MAX_FUSED_OPS, 3)],
-                 [(sps.SPS_OPT_LOAD_FACTOR_PCT, 25)]):
+                 [(sps.SPS_OPT_LOAD_FACTOR_PCT, 25)], [(sps.SPS_OPT_SMALL_RUN_CAP, 0)],
+                 [(sps.SPS_OPT_SMALL_RUN_CAP, 64)], [(sps.SPS_OPT_BITSLICE_MIN_OPS, 0)]):
         got, _ = run_both(24, gates, eps=1e-14, capacity=8192, options=opts)
         compare_states(got, want, 1e-14)
 
 
 def test_counters_count_launches():
+    gates = W.to_array([W.X(0), W.Z(1), W.H(2), W.CX(2, 3), W.H(4)])
     st = sps.SparseState(24, 4096)
+    st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)
     c0 = st.counters().kernel_launches
-    st.apply(W.to_array([W.X(0), W.Z(1), W.H(2), W.CX(2, 3), W.H(4)]), 0.0)
+    st.apply(gates, 0.0)
     c = st.counters()
     assert c.fused_passes == 2 and c.branch_passes == 2
     assert c.kernel_launches - c0 == 2 * 1 + 2 * 2
+    st.close()
+    st = sps.SparseState(24, 4096)        # all five passes fit one small-state run
+    c0 = st.counters().kernel_launches
+    st.apply(gates, 0.0)
+    c = st.counters()
+    assert c.fused_passes == 2 and c.branch_passes == 2
+    assert c.kernel_launches - c0 == 1
+    st.close()
+
+
+@pytest.mark.parametrize("small_cap", [0, 16, 2048])
+def test_small_run_boundaries(small_cap):
+    """Runs that end exactly at the cap, errors inside a run, and a run that
+    starts from a state loaded with set_amplitudes."""
+    n = 50
+    gates = W.to_array([W.H(q) for q in range(12)] + [W.T(3), W.CX(1, 40)] +
+                       [W.Givens(2, 41, 0.8), W.Ry(42, 1.1, 5)])
+    got, want = run_both(n, gates, eps=1e-14, capacity=1 << 15,
+                         options=[(sps.SPS_OPT_SMALL_RUN_CAP, small_cap)])
+    compare_states(got, want, 1e-14)
+    st = sps.SparseState(n, 300)
+    st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, small_cap)
+    st.set_amplitudes(None, np.arange(100, dtype=np.uint64) * 2, np.full(100, 0.1), np.zeros(100))
+    st.apply(W.to_array([W.H(0), W.X(9), W.H(20), W.Z(1)]), 0.0)   # 100 -> 200 -> 200 -> 400
+    with pytest.raises(sps.SpsError) as e:
+        st.sync()
+    assert e.value.status == sps.SPS_ERR_CAPACITY and e.value.failed_gate == 2
+    assert st.nnz() == 200
     st.close()
 
 
