@@ -501,11 +501,13 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
     uint32_t serial = s->pass_serial;
     const uint64_t next_apply = (uint64_t)s->apply_serial + 1;
     size_t i = 0;
+    // offsets are from the arena base: the blob follows the bit-sliced plans
+    const size_t base = arena_bytes;
     auto put = [&](const void* src, size_t bytes) {
       const size_t at = blob.size();
       blob.resize(align16(at + bytes), 0);
       std::memcpy(blob.data() + at, src, bytes);
-      return at;
+      return base + at;
     };
     while (i < passes.size()) {
       if (!seg_end[i]) {
@@ -571,7 +573,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       for (size_t k = pi; k < j; ++k) nbranch += passes[k].kind == PASS_BRANCH ? 1u : 0u;
       ProfScope ps(s, 4, s->pass_serial + 1, (uint32_t)(j - pi), 3u);
       const int n = launch_small_run(s->stream, s->kw, s->ctl, s->bufs, s->arena,
-                                     (uint32_t)(blob_base + run_off[pi]), (uint32_t)(j - pi),
+                                     (uint32_t)run_off[pi], (uint32_t)(j - pi),
                                      s->capacity, ps.slot);
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
