@@ -280,6 +280,9 @@ def run_ours(args, dist, rank, world, local_rank):
 
     wl = make_workload(args.workload)
     st = sps.SparseState(wl["nqubits"], wl["capacity"])
+    for kv in args.opt:
+        name, val = kv.split("=")
+        st.set_option(getattr(sps, "SPS_OPT_" + name.upper()), int(val))
     stream = torch.cuda.current_stream()
     U, nnz_final = updates_per_step(sps, wl, st)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -331,6 +334,11 @@ def run_ours(args, dist, rank, world, local_rank):
     torch.cuda.synchronize()
     st.set_option(sps.SPS_OPT_PROFILE, 0)
     prof_ms = sum(a.elapsed_time(b) for a, b in pev) / prof_steps
+    if args.dump_profile and rank == 0:
+        per_step = len(records) // prof_steps
+        with open(args.dump_profile, "w") as f:
+            json.dump({"workload": wl["name"], "options": args.opt,
+                       "step_records": records[-per_step:] if per_step else []}, f, indent=1)
     total_ms = max_over_ranks(dist, sum(step_ms))
     units = sum_over_ranks(dist, float(U) * args.steps)
     value = units / (total_ms * 1e-3)
@@ -469,6 +477,10 @@ def main():
                     choices=["adder67", "adder67-w22", "adder67-w24", "givens64"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--opt", action="append", default=[],
+                    help="library option NAME=VALUE (e.g. bitslice_min_ops=0), repeatable")
+    ap.add_argument("--dump-profile", default=None,
+                    help="write the per-launch records of one profiled step to this JSON file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
