@@ -168,10 +168,12 @@ typedef enum sps_option {
   SPS_OPT_BITSLICE_MIN_OPS = 7, /* fused passes with at least this many ops run
                                   bit-sliced (labels as bit-planes, 32 entries per
                                   logic op); 0 = never (default 8) */
-  SPS_OPT_SMALL_RUN_CAP = 8    /* consecutive passes whose nonzero bound stays at
+  SPS_OPT_SMALL_RUN_CAP = 8,   /* consecutive passes whose nonzero bound stays at
                                   most this (<= 2048, default 2048) run in one
                                   single-block launch with the state in shared
                                   memory; 0 = never */
+  SPS_OPT_BITSLICE_MIN_NNZ = 9 /* ... and only when the nonzero bound before the
+                                  pass is at least this (default 262,144) */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:

@@ -61,6 +61,7 @@ struct sps_state {
   uint32_t max_fused_ops = kDefaultMaxFusedOps;
   int coop = 1;
   uint32_t bitslice_min_ops = 8;
+  uint64_t bitslice_min_nnz = 1u << 18;   // below this the direct kernel is faster
   uint32_t small_cap = kSmallCap;   // 0 disables small-state runs
   // plan arena: bit-sliced op lists and phase tables of the current sps_apply
   unsigned char* arena = nullptr;
@@ -449,8 +450,14 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   // 1. segments of consecutive passes that a small-state run can take: the
   //    nonzero bound (doubling per branching pass) stays within small_cap
   std::vector<size_t> seg_end(passes.size(), 0);   // > 0: a run starts here, ends there
+  std::vector<uint64_t> bound_at(passes.size(), 0);  // nonzero bound before each pass
   {
     uint64_t b = s->nnz_bound;
+    for (size_t i = 0; i < passes.size(); ++i) {
+      bound_at[i] = b;
+      if (passes[i].kind == PASS_BRANCH) b = 2 * b < s->capacity ? 2 * b : s->capacity;
+    }
+    b = s->nnz_bound;
     for (size_t i = 0; i < passes.size();) {
       if (s->small_cap && b <= s->small_cap) {
         size_t j = i;
@@ -488,7 +495,8 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         continue;
       }
       const Pass& p = passes[i];
-      if (p.kind == PASS_FUSED && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops) {
+      if (p.kind == PASS_FUSED && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops &&
+          bound_at[i] >= s->bitslice_min_nnz) {
         build_bitslice(p, s->nqubits, &bs[i]);
         bs_off[i] = arena_bytes;
         arena_bytes += align16(bs[i].ops.size() * sizeof(SOp)) + align16(bs[i].tables.size() * 8) +
@@ -810,6 +818,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_BITSLICE_MIN_OPS:
       if (v < 0 || v > 1000000) return SPS_ERR_ARG;
       s->bitslice_min_ops = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_BITSLICE_MIN_NNZ:
+      if (v < 0) return SPS_ERR_ARG;
+      s->bitslice_min_nnz = (uint64_t)v;
       return SPS_OK;
     case SPS_OPT_PROFILE:
       if (v != 0 && v != 1) return SPS_ERR_ARG;

@@ -26,7 +26,7 @@ SPS_OK, SPS_ERR_ARG, SPS_ERR_CAPACITY, SPS_ERR_TABLE_FULL = 0, 1, 2, 3
 SPS_ERR_CUDA, SPS_ERR_OOM, SPS_ERR_NO_DEVICE = 4, 5, 6
 SPS_OPT_LOAD_FACTOR_PCT, SPS_OPT_PROBE_LIMIT, SPS_OPT_BLOCK_THREADS = 1, 2, 3
 SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
-SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP = 7, 8
+SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP, SPS_OPT_BITSLICE_MIN_NNZ = 7, 8, 9
 KIND_SMALL_RUN = 4
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 

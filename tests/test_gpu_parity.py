@@ -366,7 +366,8 @@ def test_bitslice_and_direct_long_runs(n, min_ops):
     prep = W.to_array([W.H(q) for q in rng.distinct(n, k)] + [W.Ry(rng.below(n), 0.77)])
     gates = np.concatenate([prep, perm_diag_run(100 + n, n, 300)])
     got, want = run_both(n, gates, eps=1e-14, capacity=1 << 14,
-                         options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, min_ops)])
+                         options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, min_ops),
+                                  (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
     compare_states(got, want, 1e-14)
 
 
@@ -383,7 +384,8 @@ def test_bitslice_many_phase_slots_and_split():
     gates = W.to_array(prep + run + [W.X(q, (q + 1) % 10) for q in range(10)])
     plan = sps.sps_plan(gates, n)
     assert sum(1 for k, _, _ in plan if k == 1) >= 2
-    got, want = run_both(n, gates, eps=1e-14, options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1)])
+    got, want = run_both(n, gates, eps=1e-14, options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1),
+                                                       (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
     compare_states(got, want, 1e-14)
 
 
@@ -394,6 +396,7 @@ def test_bitslice_sizes(nnz_log2):
     prep = [W.H(q) for q in range(nnz_log2)] + [W.Ry(40, 0.3, 0)] + [W.H(41, 1)]
     gates = np.concatenate([W.to_array(prep), perm_diag_run(9, n, 200, max_controls=3)])
     got, want = run_both(n, gates, eps=1e-14, capacity=1 << 19,
-                         options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1)])
+                         options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1),
+                                  (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
     compare_states(got, want, 1e-14)
     assert len(got[1]) > (1 << nnz_log2)
