@@ -189,7 +189,8 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact", 4: "k_small_run"}
+KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact", 4: "k_small_run",
+              5: "k_gather_build", 6: "k_gather_emit"}
 
 
 def algorithmic_bytes(r) -> float:
@@ -203,8 +204,10 @@ def algorithmic_bytes(r) -> float:
         return per * r["n_in"]
     if r["kind"] == 2:
         return (lb + 16) * r["n_in"]
-    if r["kind"] == 4:   # a run of passes in shared memory: read the state once, write it once
+    if r["kind"] in (4, 6):   # read the old state once, write the new one once
         return (lb + 16) * (r["n_in"] + r["n_out"])
+    if r["kind"] == 5:        # index the input labels
+        return lb * r["n_in"]
     return (lb + 16) * r["n_out"]
 
 

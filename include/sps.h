@@ -172,8 +172,14 @@ typedef enum sps_option {
                                   most this (<= 2048, default 2048) run in one
                                   single-block launch with the state in shared
                                   memory; 0 = never */
-  SPS_OPT_BITSLICE_MIN_NNZ = 9 /* ... and only when the nonzero bound before the
+  SPS_OPT_BITSLICE_MIN_NNZ = 9, /* ... and only when the nonzero bound before the
                                   pass is at least this (default 262,144) */
+  SPS_OPT_BRANCH_FORM = 10     /* branching passes on the whole GPU: 0 default
+                                  (gather), 1 scatter (labels emitted into a
+                                  32-byte-slot table, FP64 atomic accumulation,
+                                  separate prune/compact walk), 2 gather (each
+                                  pair written once after a partner lookup in an
+                                  index table; the insert-once rule of Sec. 3.1) */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:
@@ -190,7 +196,8 @@ typedef struct sps_counters {
 sps_status sps_get_counters(sps_state* s, sps_counters* out);
 
 /* One profiled kernel launch (SPS_OPT_PROFILE). kind: 1 fused phase /
- * permutation pass, 2 branching emit, 3 branching compaction. n_in: entries
+ * permutation pass, 2 scatter emit, 3 scatter compaction, 4 small-state run
+ * (several passes in one block), 5 gather index build, 6 gather emit. n_in: entries
  * the kernel read; n_out: entries in the state after it. flags: bit 0 the
  * pass permutes labels, bit 1 it changes amplitudes. label_bytes: 8 or 16. */
 typedef struct sps_kernel_record {

@@ -45,9 +45,13 @@ struct sps_state {
   Ctl* ctl = nullptr;
   Ctl* ctl_host = nullptr;    // pinned mirror
   Bufs bufs{};
-  Slot* table = nullptr;
+  Slot* table = nullptr;            // scatter-form table, allocated on first use
   uint32_t max_log2 = 8;
   uint64_t table_slots = 0;
+  unsigned long long* itab = nullptr;  // gather-form index table
+  uint32_t itab_log2 = 8;
+  uint32_t epoch = 0;
+  int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
   double* hresult = nullptr;  // pinned
@@ -218,6 +222,19 @@ sps_status ensure_arena(sps_state* s, size_t bytes) {
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// The scatter-form table (32-byte slots for 2 * capacity labels at 50% load)
+// is large, so it is only allocated when that form is first used.
+sps_status ensure_scatter_table(sps_state* s) {
+  if (s->table) return SPS_OK;
+  void* p = nullptr;
+  const sps_status st = dev_alloc(s, s->table_slots * sizeof(Slot), &p);
+  if (st != SPS_OK) return st;
+  s->table = (Slot*)p;
+  if (launch_table_clear(cfg_of(s), s->table, s->table_slots) < 0) return cuda_ok(cudaGetLastError());
+  s->counters.kernel_launches += 1;
+  return SPS_OK;
+}
+
 // Next pinned staging buffer of at least `bytes`; waits only if the copy that
 // last used it has not finished (the ring lets the host run ahead of the GPU).
 sps_status take_staging(sps_state* s, size_t bytes, sps_state::Staging** out) {
@@ -344,8 +361,9 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
     if ((st = dev_alloc(s, capacity * 8, &p)) != SPS_OK) return fail(st);
     s->bufs.b[b].im = (double*)p;
   }
-  if ((st = dev_alloc(s, s->table_slots * sizeof(Slot), &p)) != SPS_OK) return fail(st);
-  s->table = (Slot*)p;
+  s->itab_log2 = table_log2_for((capacity + 1) / 2, 50, 40);
+  if ((st = dev_alloc(s, (sizeof(unsigned long long) << s->itab_log2), &p)) != SPS_OK) return fail(st);
+  s->itab = (unsigned long long*)p;
   if ((st = dev_alloc(s, sizeof(Ctl), &p)) != SPS_OK) return fail(st);
   s->ctl = (Ctl*)p;
   if ((st = dev_alloc(s, sizeof(double) * (s->prob_blocks + 1), &p)) != SPS_OK) return fail(st);
@@ -372,7 +390,8 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
             cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), s->stream) == cudaSuccess;
   if (!ok) return fail(SPS_ERR_CUDA);
   LaunchCfg lc = cfg_of(s);
-  if (launch_table_clear(lc, s->table, s->table_slots) < 0 || launch_set_nnz(s->stream, s->ctl, 1) < 0)
+  if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0 ||
+      launch_set_nnz(s->stream, s->ctl, 1) < 0)
     return fail(SPS_ERR_CUDA);
   s->counters.kernel_launches += 2;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(cuda_ok(cudaGetLastError()));
@@ -638,16 +657,36 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       b.coop = s->coop;
       b.capacity = s->capacity;
       b.fail_tag = tag;
-      {
-        ProfScope ps(s, 2, serial, 1, 3u);
-        const int n = launch_branch_emit(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
-        ps.done();
+      const bool scatter = s->branch_form == 1 || s->capacity >= (1ull << 32);
+      if (scatter) {
+        const sps_status ts = ensure_scatter_table(s);
+        if (ts != SPS_OK) return ts;
+        {
+          ProfScope ps(s, 2, serial, 1, 3u);
+          const int n = launch_branch_emit(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
+          ps.done();
+          if (n < 0) return cuda_ok(cudaGetLastError());
+        }
+        {
+          ProfScope ps(s, 3, serial, 1, 3u);
+          const int n = launch_branch_compact(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
+          ps.done();
+          if (n < 0) return cuda_ok(cudaGetLastError());
+        }
+      } else {
+        if (++s->epoch == 0) {  // epochs wrapped: make every slot free again
+          if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0) return cuda_ok(cudaGetLastError());
+          s->counters.kernel_launches += 1;
+          s->epoch = 1;
+        }
+        b.max_log2 = s->itab_log2;
+        ProfScope pb(s, 5, serial, 1, 3u);
+        int n = launch_gather_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, b, s->nnz_bound, 0, pb.slot);
+        pb.done();
         if (n < 0) return cuda_ok(cudaGetLastError());
-      }
-      {
-        ProfScope ps(s, 3, serial, 1, 3u);
-        const int n = launch_branch_compact(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
-        ps.done();
+        ProfScope pe(s, 6, serial, 1, 3u);
+        n = launch_gather_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, b, s->nnz_bound, 1, pe.slot);
+        pe.done();
         if (n < 0) return cuda_ok(cudaGetLastError());
       }
       s->counters.branch_passes++;
@@ -671,7 +710,7 @@ sps_status sps_sync(sps_state* s, size_t* failed_gate) {
   // recover: clear the error and the table; the state is the last good one
   const LaunchCfg lc = cfg_of(s);
   if (launch_reset_status(s->stream, s->ctl) < 0 ||
-      launch_table_clear(lc, s->table, s->table_slots) < 0)
+      (s->table && launch_table_clear(lc, s->table, s->table_slots) < 0))
     return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 2;
   st = cuda_ok(cudaStreamSynchronize(s->stream));
@@ -810,6 +849,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_MAX_FUSED_OPS:
       if (v < 1 || v > (int64_t)kMaxFusedOps) return SPS_ERR_ARG;
       s->max_fused_ops = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_BRANCH_FORM:
+      if (v < 0 || v > 2) return SPS_ERR_ARG;
+      s->branch_form = (int)v;
       return SPS_OK;
     case SPS_OPT_SMALL_RUN_CAP:
       if (v < 0 || v > (int64_t)kSmallCap) return SPS_ERR_ARG;

@@ -1,0 +1,261 @@
+// Gather-form branching pass on the whole GPU (the insert-once rule of Sec. 3.1).
+//
+//   k_gather_build  every input label claims one slot of an open-addressing
+//                   index table: slot = (epoch << 32) | index, claimed with a
+//                   64-bit CAS. Labels are distinct, so no label comparison is
+//                   needed here. A slot whose epoch differs from the pass's is
+//                   free, so the table never needs clearing between passes.
+//   k_gather_emit   every entry: inactive -> itself; active -> look up the
+//                   partner label (flip mask applied); if the partner exists
+//                   and this entry's selector bit is 0, the partner writes the
+//                   pair; else this entry writes both outputs of the 2x2 action
+//                   (each product and sum rounded once). Outputs are pruned and
+//                   compacted (warp ballot, block scan, one atomic per block);
+//                   the last block publishes the count and flips the buffers.
+//
+// No amplitude atomics: every output is computed once, so the result equals the
+// scatter form bit for bit.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sps_device.cuh"
+#include "sps_internal.h"
+
+namespace sps {
+namespace {
+
+using namespace dev;
+
+struct GatherArgs {
+  BranchOp op;
+  double eps2;
+  uint64_t capacity;
+  uint64_t fail_tag;
+  uint32_t load_pct, max_log2, pass_serial, epoch;
+};
+
+// The table holds n_in labels at the load factor: size for n_in, not 2 n_in.
+__device__ __forceinline__ uint64_t itab_mask(uint64_t n, uint32_t load_pct, uint32_t max_log2) {
+  return (1ull << table_log2_for((n + 1) / 2, load_pct, max_log2)) - 1;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsigned long long* itab,
+                                                      const __grid_constant__ GatherArgs a,
+                                                      unsigned long long* plog) {
+  const uint64_t n = ctl->nnz;
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+    plog[0] = n;
+    plog[1] = 0ull;
+  }
+  if (ctl->status != 0u) return;
+  const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
+  const SoA s = pick(bufs, ctl->cur);
+  const unsigned long long tag = (unsigned long long)a.epoch << 32;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k0 = s.lo[i];
+    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    uint64_t h = hash_label<KW>(k0, k1) & mask;
+    bool ok = false;
+    for (uint64_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
+      const unsigned long long v = __ldcg(itab + h);
+      if ((v & 0xFFFFFFFF00000000ull) == tag) continue;   // taken in this pass
+      if (atomicCAS(itab + h, v, tag | i) == v) {
+        ok = true;
+        break;
+      }
+      // lost the race: the slot now belongs to this pass, go on
+    }
+    if (!ok) {
+      fail(ctl, SPS_ERR_TABLE_FULL, a.pass_serial, a.fail_tag);
+      return;
+    }
+  }
+}
+
+template <int KW>
+__device__ __forceinline__ uint64_t find_label(const unsigned long long* itab, uint64_t mask,
+                                               unsigned long long tag, const SoA& s, uint64_t lo,
+                                               uint64_t hi) {
+  uint64_t h = hash_label<KW>(lo, hi) & mask;
+  for (uint64_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
+    const unsigned long long v = __ldcg(itab + h);
+    if ((v & 0xFFFFFFFF00000000ull) != tag) return ~0ull;
+    const uint64_t j = v & 0xFFFFFFFFull;
+    if (s.lo[j] == lo && (KW == 1 || s.hi[j] == hi)) return j;
+  }
+  return ~0ull;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
+                                                     const unsigned long long* itab,
+                                                     const __grid_constant__ GatherArgs a,
+                                                     unsigned long long* plog) {
+  __shared__ unsigned warp_cnt[32];
+  __shared__ unsigned long long block_base;
+  const unsigned status0 = ctl->status;
+  if (status0 != 0u) return;
+  const uint64_t n = ctl->nnz;
+  const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
+  const unsigned cur = ctl->cur;
+  const SoA s = pick(bufs, cur);
+  const SoA out = pick(bufs, cur ^ 1u);
+  const unsigned long long tag = (unsigned long long)a.epoch << 32;
+  const BranchOp& op = a.op;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned nwarps = blockDim.x >> 5;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+    double v0r = 0, v0i = 0, v1r = 0, v1i = 0;
+    bool w0 = false, w1 = false;
+    if (i < n) {
+      const uint64_t k0 = s.lo[i];
+      const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+      const double re = s.re[i], im = s.im[i];
+      bool active = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
+      const bool x = label_bit(k0, k1, op.sbit);
+      if (op.givens) active = active && (x != label_bit(k0, k1, op.qbit));
+      if (!active) {
+        l0 = k0; h0 = k1; v0r = re; v0i = im;
+        w0 = keep_amp(re, im, a.eps2);
+      } else {
+        const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
+        const uint64_t j = find_label<KW>(itab, mask, tag, s, p0, p1);
+        if (j == ~0ull || x) {   // else the partner with selector bit 1 writes the pair
+          const double pre = j != ~0ull ? s.re[j] : 0.0;
+          const double pim = j != ~0ull ? s.im[j] : 0.0;
+          const double a0r = x ? pre : re, a0i = x ? pim : im;
+          const double a1r = x ? re : pre, a1i = x ? im : pim;
+          l0 = x ? p0 : k0; h0 = x ? p1 : k1;
+          l1 = x ? k0 : p0; h1 = x ? k1 : p1;
+          double t0r, t0i, t1r, t1i;
+          mat_times(op, 0, 0, a0r, a0i, &t0r, &t0i);
+          mat_times(op, 0, 1, a1r, a1i, &t1r, &t1i);
+          v0r = __dadd_rn(t0r, t1r);
+          v0i = __dadd_rn(t0i, t1i);
+          mat_times(op, 1, 0, a0r, a0i, &t0r, &t0i);
+          mat_times(op, 1, 1, a1r, a1i, &t1r, &t1i);
+          v1r = __dadd_rn(t0r, t1r);
+          v1i = __dadd_rn(t0i, t1i);
+          w0 = keep_amp(v0r, v0i, a.eps2);
+          w1 = keep_amp(v1r, v1i, a.eps2);
+        }
+      }
+    }
+    const unsigned b0 = __ballot_sync(FULL, w0), b1 = __ballot_sync(FULL, w1);
+    if (lane == 0) warp_cnt[warp] = __popc(b0) + __popc(b1);
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned v = lane < nwarps ? warp_cnt[lane] : 0u;
+      unsigned incl = v;
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= (unsigned)d) incl += t;
+      }
+      const unsigned total = __shfl_sync(FULL, incl, 31);
+      if (lane < nwarps) warp_cnt[lane] = incl - v;
+      if (lane == 0)
+        block_base = total ? atomicAdd(&ctl->out_count, (unsigned long long)total) : 0ull;
+    }
+    __syncthreads();
+    const unsigned below = (1u << lane) - 1u;
+    uint64_t pos = block_base + warp_cnt[warp] + __popc(b0 & below) + __popc(b1 & below);
+    if (w0) {
+      if (pos < a.capacity) {
+        out.lo[pos] = l0;
+        if (KW == 2) out.hi[pos] = h0;
+        out.re[pos] = v0r;
+        out.im[pos] = v0i;
+      }
+      ++pos;
+    }
+    if (w1 && pos < a.capacity) {
+      out.lo[pos] = l1;
+      if (KW == 2) out.hi[pos] = h1;
+      out.re[pos] = v1r;
+      out.im[pos] = v1i;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long total = atomicAdd(&ctl->out_count, 0ull);
+      bool published = false;
+      if (ctl->status == 0u) {
+        if (total > a.capacity) {
+          fail(ctl, SPS_ERR_CAPACITY, a.pass_serial, a.fail_tag);
+        } else {
+          ctl->nnz = total;
+          ctl->cur = cur ^ 1u;
+          published = true;
+        }
+      }
+      if (plog) {
+        plog[0] = n;
+        plog[1] = published ? total : n;
+      }
+      ctl->out_count = 0ull;
+      ctl->blocks_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+__global__ void k_itab_clear(unsigned long long* itab, uint64_t nslots) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nslots;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    itab[i] = 0ull;
+}
+
+int grid_of(uint64_t work, int threads, int max_blocks) {
+  uint64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > (uint64_t)max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+}  // namespace
+
+int launch_itab_clear(const LaunchCfg& lc, unsigned long long* itab, uint64_t nslots) {
+  k_itab_clear<<<grid_of(nslots, lc.threads, lc.max_blocks), lc.threads, 0,
+                 (cudaStream_t)lc.stream>>>(itab, nslots);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                       unsigned long long* itab, uint32_t epoch, const BranchLaunch& b,
+                       uint64_t nnz_bound, int part, unsigned long long* plog) {
+  GatherArgs a;
+  a.op = b.op;
+  a.eps2 = b.eps * b.eps;
+  a.capacity = b.capacity;
+  a.fail_tag = b.fail_tag;
+  a.load_pct = b.load_pct;
+  a.max_log2 = b.max_log2;
+  a.pass_serial = b.pass_serial;
+  a.epoch = epoch;
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
+  if (part == 0) {
+    if (key_words == 1)
+      k_gather_build<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    else
+      k_gather_build<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+  } else {
+    if (key_words == 1)
+      k_gather_emit<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    else
+      k_gather_emit<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace sps

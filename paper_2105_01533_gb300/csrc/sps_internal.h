@@ -220,6 +220,16 @@ int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, con
 int launch_small_run(void* stream, int key_words, Ctl* ctl, Bufs bufs, const unsigned char* arena,
                      uint32_t pass_off, uint32_t npasses, uint64_t capacity,
                      unsigned long long* plog);
+// Gather form of a branching pass (insert-once rule, Sec. 3.1) on the whole GPU:
+// k_gather_build claims one slot per input label in an index table whose
+// 64-bit slots hold (epoch << 32 | input index), so a new epoch per pass makes
+// the table empty without clearing it; k_gather_emit looks up each active
+// entry's partner, writes the pair once, prunes and compacts.
+// part 0 launches k_gather_build, part 1 k_gather_emit.
+int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                       unsigned long long* itab, uint32_t epoch, const BranchLaunch& b,
+                       uint64_t nnz_bound, int part, unsigned long long* plog);
+int launch_itab_clear(const LaunchCfg& lc, unsigned long long* itab, uint64_t nslots);
 int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
                        double* partials, int nblocks, double* result);

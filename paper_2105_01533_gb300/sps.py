@@ -27,7 +27,8 @@ SPS_ERR_CUDA, SPS_ERR_OOM, SPS_ERR_NO_DEVICE = 4, 5, 6
 SPS_OPT_LOAD_FACTOR_PCT, SPS_OPT_PROBE_LIMIT, SPS_OPT_BLOCK_THREADS = 1, 2, 3
 SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
 SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP, SPS_OPT_BITSLICE_MIN_NNZ = 7, 8, 9
-KIND_SMALL_RUN = 4
+SPS_OPT_BRANCH_FORM = 10
+KIND_SMALL_RUN, KIND_GATHER_BUILD, KIND_GATHER_EMIT = 4, 5, 6
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 
 EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_apply", "sps_sync",

@@ -64,16 +64,18 @@ def test_each_gate_type(n, op):
     compare_states(got, want, 1e-14)
 
 
+@pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("n,seed", [(12, 1), (40, 2), (63, 3), (64, 4), (90, 5), (127, 6)])
-def test_random_circuits_all_gates(n, seed):
+def test_random_circuits_all_gates(n, seed, form):
     gates = W.random_all_gates(seed, n, 400, max_controls=3, branch_frac=0.2,
                                keep_branch=W.CountingBound(1 << 16))
-    got, want = run_both(n, gates, eps=1e-14, capacity=1 << 16)
+    got, want = run_both(n, gates, eps=1e-14, capacity=1 << 16,
+                         options=[(sps.SPS_OPT_BRANCH_FORM, form)])
     compare_states(got, want, 1e-14)
 
 
-@pytest.mark.parametrize("small_cap", [2048, 0])
-def test_branching_only_is_bit_identical(small_cap):
+@pytest.mark.parametrize("small_cap,form", [(2048, 0), (0, 1), (0, 2)])
+def test_branching_only_is_bit_identical(small_cap, form):
     n = 30
     rng = W.SplitMix64(5)
     recs = []
@@ -87,17 +89,20 @@ def test_branching_only_is_bit_identical(small_cap):
         else:
             recs.append(W.Givens(q[0], q[1], rng.angle()))
     gates = W.to_array(recs)
-    got, want = run_both(n, gates, eps=0.0, options=[(sps.SPS_OPT_SMALL_RUN_CAP, small_cap)])
+    got, want = run_both(n, gates, eps=0.0, options=[(sps.SPS_OPT_SMALL_RUN_CAP, small_cap),
+                                                     (sps.SPS_OPT_BRANCH_FORM, form)])
     for a, b in zip(got, want):
         np.testing.assert_array_equal(a, b)
 
 
-def test_plain24_workload_full():
+@pytest.mark.parametrize("form", [0, 1])
+def test_plain24_workload_full(form):
     """24 qubits, H on 8 qubits then 2000 gates (70% X/CNOT/Toffoli, 20%
     Z/S/T/CRz, 10% H kept only while the oracle reports <= 4096 nonzeros)."""
     gates = plain24_gates(seed=0)
     assert len(gates) == 2008
-    got, want = run_both(24, gates, eps=1e-14, capacity=8192)
+    got, want = run_both(24, gates, eps=1e-14, capacity=8192,
+                         options=[(sps.SPS_OPT_BRANCH_FORM, form), (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
     stats = compare_states(got, want, 1e-14)
     assert stats["common"] >= 256
     # same stream applied in several calls gives the same result
@@ -124,9 +129,11 @@ def test_adder_workload_full_and_closed_form():
     assert np.max(np.abs(re + 1j * im - amp)) < 1e-12
 
 
-def test_givens_workload_few_layers():
+@pytest.mark.parametrize("form", [0, 1])
+def test_givens_workload_few_layers(form):
     gates = W.givens_workload(seed=2, nqubits=64, modes=4, layers=3)
-    got, want = run_both(64, gates, eps=1e-14, capacity=700_000)
+    got, want = run_both(64, gates, eps=1e-14, capacity=700_000,
+                         options=[(sps.SPS_OPT_BRANCH_FORM, form)])
     compare_states(got, want, 1e-14)
 
 
@@ -223,6 +230,7 @@ def test_capacity_overflow_leaves_last_good_state():
 def test_probe_limit_reports_table_full_without_hanging():
     st = sps.SparseState(30, 1 << 12)
     st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)      # exercise the global table
+    st.set_option(sps.SPS_OPT_BRANCH_FORM, 1)        # the scatter table has the probe limit
     st.apply(W.to_array([W.H(q) for q in range(8)]), 0.0)
     st.sync()
     st.set_option(sps.SPS_OPT_PROBE_LIMIT, 1)
@@ -241,9 +249,12 @@ def test_probe_limit_reports_table_full_without_hanging():
 def test_high_load_factor_collisions():
     n = 50
     gates = W.to_array([W.H(q) for q in range(12)] + [W.Ry(q, 0.3 * q) for q in range(12, 16)])
-    got, want = run_both(n, gates, eps=0.0, capacity=1 << 16,
-                         options=[(sps.SPS_OPT_LOAD_FACTOR_PCT, 90),
-                                  (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
+    for form in (1, 2):
+        got, want = run_both(n, gates, eps=0.0, capacity=1 << 16,
+                             options=[(sps.SPS_OPT_LOAD_FACTOR_PCT, 90),
+                                      (sps.SPS_OPT_SMALL_RUN_CAP, 0),
+                                      (sps.SPS_OPT_BRANCH_FORM, form)])
+        compare_states(got, want, 0.0)
     compare_states(got, want, 0.0)
 
 
@@ -305,6 +316,7 @@ def test_counters_count_launches():
     gates = W.to_array([W.X(0), W.Z(1), W.H(2), W.CX(2, 3), W.H(4)])
     st = sps.SparseState(24, 4096)
     st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)
+    st.sync()   # the gather form allocates nothing; the scatter table comes on first use
     c0 = st.counters().kernel_launches
     st.apply(gates, 0.0)
     c = st.counters()
