@@ -553,6 +553,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         r.pass_serial = ++serial;
         r.fail_tag = (next_apply << 32) | (p.first_gate & 0xFFFFFFFFull);
         r.eps2 = prune_eps * prune_eps;
+        r.eps = prune_eps;
         if (p.kind == PASS_FUSED) {
           r.nops = (uint32_t)p.ops.size();
           r.flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
@@ -674,7 +675,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
           if (n < 0) return cuda_ok(cudaGetLastError());
         }
       } else {
-        if (++s->epoch == 0) {  // epochs wrapped: make every slot free again
+        if (++s->epoch == 0x10000u) {  // the 16-bit epoch wrapped: make every slot free again
           if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0) return cuda_ok(cudaGetLastError());
           s->counters.kernel_launches += 1;
           s->epoch = 1;

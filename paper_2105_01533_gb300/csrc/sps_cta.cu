@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
         if (op.givens) active = active && (x != label_bit(k0, k1, op.qbit));
         if (!active) {
           l0 = k0; h0 = k1; v0r = re; v0i = im;
-          w0 = keep_amp(re, im, rp.eps2);
+          w0 = keep_amp(re, im, rp.eps2, eps_pattern(rp.eps));
         } else {
           const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
           const uint32_t j = lookup<KW>(tab, A, p0, p1);
@@ -206,17 +206,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
             const double a1r = x ? re : pre, a1i = x ? im : pim;
             l0 = x ? p0 : k0; h0 = x ? p1 : k1;
             l1 = x ? k0 : p0; h1 = x ? k1 : p1;
-            double t0r, t0i, t1r, t1i;
-            mat_times(op, 0, 0, a0r, a0i, &t0r, &t0i);
-            mat_times(op, 0, 1, a1r, a1i, &t1r, &t1i);
-            v0r = __dadd_rn(t0r, t1r);
-            v0i = __dadd_rn(t0i, t1i);
-            mat_times(op, 1, 0, a0r, a0i, &t0r, &t0i);
-            mat_times(op, 1, 1, a1r, a1i, &t1r, &t1i);
-            v1r = __dadd_rn(t0r, t1r);
-            v1i = __dadd_rn(t0i, t1i);
-            w0 = keep_amp(v0r, v0i, rp.eps2);
-            w1 = keep_amp(v1r, v1i, rp.eps2);
+            pair_action(op, j != EMPTY_IDX, x, a0r, a0i, a1r, a1i, &v0r, &v0i, &v1r, &v1i);
+            w0 = keep_amp(v0r, v0i, rp.eps2, eps_pattern(rp.eps));
+            w1 = keep_amp(v1r, v1i, rp.eps2, eps_pattern(rp.eps));
           }
         }
       }

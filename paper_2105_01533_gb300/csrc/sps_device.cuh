@@ -74,10 +74,49 @@ __device__ __forceinline__ void mat_times(const BranchOp& op, int row, int x, do
   }
 }
 
+// Both outputs of the 2x2 action on (a0, a1), the amplitudes of the labels with
+// selector bit 0 and 1: n0 = M00 a0 + M01 a1, n1 = M10 a0 + M11 a1, each
+// product and sum rounded once. With the partner absent one input is zero and
+// its products are zeros, so n = M[.][x] a exactly (x + 0 = x; only the sign of
+// a zero result can differ, and zeros are pruned).
+__device__ __forceinline__ void pair_action(const BranchOp& op, bool both, bool x, double a0r,
+                                            double a0i, double a1r, double a1i, double* n0r,
+                                            double* n0i, double* n1r, double* n1i) {
+  if (!both) {
+    const int xi = x ? 1 : 0;
+    const double ar = x ? a1r : a0r, ai = x ? a1i : a0i;
+    mat_times(op, 0, xi, ar, ai, n0r, n0i);
+    mat_times(op, 1, xi, ar, ai, n1r, n1i);
+    return;
+  }
+  double t0r, t0i, t1r, t1i;
+  mat_times(op, 0, 0, a0r, a0i, &t0r, &t0i);
+  mat_times(op, 0, 1, a1r, a1i, &t1r, &t1i);
+  *n0r = __dadd_rn(t0r, t1r);
+  *n0i = __dadd_rn(t0i, t1i);
+  mat_times(op, 1, 0, a0r, a0i, &t0r, &t0i);
+  mat_times(op, 1, 1, a1r, a1i, &t1r, &t1i);
+  *n1r = __dadd_rn(t0r, t1r);
+  *n1i = __dadd_rn(t0i, t1i);
+}
+
 // keep an entry after a branching pass: not exactly zero and re^2 + im^2 >= eps^2
-__device__ __forceinline__ bool keep_amp(double re, double im, double eps2) {
+// (each product and the sum rounded once). The FP64 pipe is scarce, so the
+// common cases are decided on the bit patterns: for non-negative doubles the
+// IEEE order is the unsigned-integer order, and rounding is monotone, so
+// |re| >= eps or |im| >= eps already implies re^2 + im^2 >= eps^2 as rounded.
+__device__ __forceinline__ bool keep_amp(double re, double im, double eps2, uint64_t eps_bits) {
+  const uint64_t ar = (uint64_t)__double_as_longlong(re) & 0x7FFFFFFFFFFFFFFFull;
+  const uint64_t ai = (uint64_t)__double_as_longlong(im) & 0x7FFFFFFFFFFFFFFFull;
+  if ((ar | ai) == 0ull) return false;
+  if (ar >= eps_bits || ai >= eps_bits) return true;
   const double mag2 = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
-  return !(re == 0.0 && im == 0.0) && !(mag2 < eps2);
+  return !(mag2 < eps2);
+}
+
+// bit pattern of eps = sqrt(eps2) as passed by the host (eps >= 0)
+__device__ __forceinline__ uint64_t eps_pattern(double eps) {
+  return (uint64_t)__double_as_longlong(eps);
 }
 
 }  // namespace dev

@@ -1,10 +1,13 @@
 // Gather-form branching pass on the whole GPU (the insert-once rule of Sec. 3.1).
 //
 //   k_gather_build  every input label claims one slot of an open-addressing
-//                   index table: slot = (epoch << 32) | index, claimed with a
-//                   64-bit CAS. Labels are distinct, so no label comparison is
-//                   needed here. A slot whose epoch differs from the pass's is
-//                   free, so the table never needs clearing between passes.
+//                   index table: slot = epoch (16 bits) | fingerprint (16 bits,
+//                   the top of the label's hash) | index (32 bits), claimed
+//                   with a 64-bit CAS. Labels are distinct, so no label
+//                   comparison is needed here. A slot whose epoch differs from
+//                   the pass's is free, so the table needs clearing only when
+//                   the 16-bit epoch wraps. The fingerprint lets a lookup skip
+//                   almost every foreign slot without reading its label.
 //   k_gather_emit   every entry: inactive -> itself; active -> look up the
 //                   partner label (flip mask applied); if the partner exists
 //                   and this entry's selector bit is 0, the partner writes the
@@ -30,6 +33,7 @@ using namespace dev;
 struct GatherArgs {
   BranchOp op;
   double eps2;
+  double eps;
   uint64_t capacity;
   uint64_t fail_tag;
   uint32_t load_pct, max_log2, pass_serial, epoch;
@@ -52,17 +56,19 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
   if (ctl->status != 0u) return;
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
   const SoA s = pick(bufs, ctl->cur);
-  const unsigned long long tag = (unsigned long long)a.epoch << 32;
+  const unsigned long long ep = (unsigned long long)a.epoch << 48;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k0 = s.lo[i];
     const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
-    uint64_t h = hash_label<KW>(k0, k1) & mask;
+    const uint64_t hv = hash_label<KW>(k0, k1);
+    const unsigned long long mine = ep | ((hv >> 48) << 32) | i;
+    uint64_t h = hv & mask;
     bool ok = false;
     for (uint64_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
       const unsigned long long v = __ldcg(itab + h);
-      if ((v & 0xFFFFFFFF00000000ull) == tag) continue;   // taken in this pass
-      if (atomicCAS(itab + h, v, tag | i) == v) {
+      if ((v & 0xFFFF000000000000ull) == ep) continue;   // taken in this pass
+      if (atomicCAS(itab + h, v, mine) == v) {
         ok = true;
         break;
       }
@@ -77,12 +83,15 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
 
 template <int KW>
 __device__ __forceinline__ uint64_t find_label(const unsigned long long* itab, uint64_t mask,
-                                               unsigned long long tag, const SoA& s, uint64_t lo,
+                                               unsigned long long ep, const SoA& s, uint64_t lo,
                                                uint64_t hi) {
-  uint64_t h = hash_label<KW>(lo, hi) & mask;
+  const uint64_t hv = hash_label<KW>(lo, hi);
+  const unsigned long long fp = (hv >> 48) << 32;
+  uint64_t h = hv & mask;
   for (uint64_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
     const unsigned long long v = __ldcg(itab + h);
-    if ((v & 0xFFFFFFFF00000000ull) != tag) return ~0ull;
+    if ((v & 0xFFFF000000000000ull) != ep) return ~0ull;
+    if ((v & 0x0000FFFF00000000ull) != fp) continue;
     const uint64_t j = v & 0xFFFFFFFFull;
     if (s.lo[j] == lo && (KW == 1 || s.hi[j] == hi)) return j;
   }
@@ -103,7 +112,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
   const unsigned cur = ctl->cur;
   const SoA s = pick(bufs, cur);
   const SoA out = pick(bufs, cur ^ 1u);
-  const unsigned long long tag = (unsigned long long)a.epoch << 32;
+  const unsigned long long ep = (unsigned long long)a.epoch << 48;
   const BranchOp& op = a.op;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned nwarps = blockDim.x >> 5;
@@ -122,10 +131,10 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
       if (op.givens) active = active && (x != label_bit(k0, k1, op.qbit));
       if (!active) {
         l0 = k0; h0 = k1; v0r = re; v0i = im;
-        w0 = keep_amp(re, im, a.eps2);
+        w0 = keep_amp(re, im, a.eps2, eps_pattern(a.eps));
       } else {
         const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
-        const uint64_t j = find_label<KW>(itab, mask, tag, s, p0, p1);
+        const uint64_t j = find_label<KW>(itab, mask, ep, s, p0, p1);
         if (j == ~0ull || x) {   // else the partner with selector bit 1 writes the pair
           const double pre = j != ~0ull ? s.re[j] : 0.0;
           const double pim = j != ~0ull ? s.im[j] : 0.0;
@@ -133,17 +142,9 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
           const double a1r = x ? re : pre, a1i = x ? im : pim;
           l0 = x ? p0 : k0; h0 = x ? p1 : k1;
           l1 = x ? k0 : p0; h1 = x ? k1 : p1;
-          double t0r, t0i, t1r, t1i;
-          mat_times(op, 0, 0, a0r, a0i, &t0r, &t0i);
-          mat_times(op, 0, 1, a1r, a1i, &t1r, &t1i);
-          v0r = __dadd_rn(t0r, t1r);
-          v0i = __dadd_rn(t0i, t1i);
-          mat_times(op, 1, 0, a0r, a0i, &t0r, &t0i);
-          mat_times(op, 1, 1, a1r, a1i, &t1r, &t1i);
-          v1r = __dadd_rn(t0r, t1r);
-          v1i = __dadd_rn(t0i, t1i);
-          w0 = keep_amp(v0r, v0i, a.eps2);
-          w1 = keep_amp(v1r, v1i, a.eps2);
+          pair_action(op, j != ~0ull, x, a0r, a0i, a1r, a1i, &v0r, &v0i, &v1r, &v1i);
+          w0 = keep_amp(v0r, v0i, a.eps2, eps_pattern(a.eps));
+          w1 = keep_amp(v1r, v1i, a.eps2, eps_pattern(a.eps));
         }
       }
     }
@@ -236,6 +237,7 @@ int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   GatherArgs a;
   a.op = b.op;
   a.eps2 = b.eps * b.eps;
+  a.eps = b.eps;
   a.capacity = b.capacity;
   a.fail_tag = b.fail_tag;
   a.load_pct = b.load_pct;

@@ -114,7 +114,7 @@ struct Pass {
 };
 
 // One pass of a small-state run (k_small_run), stored in the plan arena.
-struct RunPass {            // 48 bytes
+struct RunPass {            // 64 bytes
   uint32_t kind;            // PASS_FUSED or PASS_BRANCH
   uint32_t nops;            // fused: ops
   uint32_t ops_off;         // byte offset of the FOp array in the arena
@@ -125,8 +125,10 @@ struct RunPass {            // 48 bytes
   uint32_t reserved;
   uint64_t fail_tag;
   double eps2;
+  double eps;
+  uint64_t reserved2;
 };
-static_assert(sizeof(RunPass) == 48, "RunPass layout");
+static_assert(sizeof(RunPass) == 64, "RunPass layout");
 
 constexpr uint32_t kSmallCap = 2048;          // entries a small-state run holds
 constexpr uint32_t kSmallThreads = 1024;

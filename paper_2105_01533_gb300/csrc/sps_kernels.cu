@@ -305,6 +305,7 @@ __global__ void k_table_clear(Slot* table, uint64_t nslots) {
 struct BranchArgs {
   BranchOp op;
   double eps2;
+  double eps;
   uint64_t capacity;
   uint64_t fail_tag;
   uint32_t load_pct, max_log2, probe_limit, pass_serial;
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
         hi = kk.y;
         re = aa.x;
         im = aa.y;
-        keep = keep_amp(re, im, a.eps2);
+        keep = keep_amp(re, im, a.eps2, eps_pattern(a.eps));
         ulonglong2* p = reinterpret_cast<ulonglong2*>(table + i);
         p[0] = make_ulonglong2(EMPTY, EMPTY);
         p[1] = make_ulonglong2(0ull, 0ull);
@@ -660,6 +661,7 @@ BranchArgs branch_args(const BranchLaunch& b) {
   BranchArgs a;
   a.op = b.op;
   a.eps2 = b.eps * b.eps;
+  a.eps = b.eps;
   a.capacity = b.capacity;
   a.fail_tag = b.fail_tag;
   a.load_pct = b.load_pct;

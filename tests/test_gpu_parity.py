@@ -412,3 +412,20 @@ def test_bitslice_sizes(nnz_log2):
                                   (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
     compare_states(got, want, 1e-14)
     assert len(got[1]) > (1 << nnz_log2)
+
+
+def test_gather_epoch_wraps():
+    """66,000 gather passes (H.H pairs) push the 16-bit table epoch through a
+    wrap; the state must come back unchanged."""
+    n = 20
+    st = sps.SparseState(n, 1 << 12)
+    st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)
+    st.set_option(sps.SPS_OPT_BRANCH_FORM, 2)
+    prep = W.to_array([W.H(q) for q in range(6)] + [W.Ry(7, 0.4), W.T(7)])
+    st.apply(prep, 0.0)
+    before = st.get_amplitudes()
+    pair = W.to_array([W.H(9), W.H(9)])
+    st.apply(np.tile(pair, 33_000), 1e-14)
+    after = st.get_amplitudes()
+    compare_states(after, before, 1e-14, atol=1e-11)
+    st.close()
