@@ -57,10 +57,17 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
   const SoA s = pick(bufs, ctl->cur);
   const unsigned long long ep = (unsigned long long)a.epoch << 48;
+  const BranchOp& op = a.op;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k0 = s.lo[i];
     const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    // The partner of an active label is active too (flipping the target bits
+    // keeps the controls and the Givens condition), so only active labels are
+    // ever looked up: index those alone.
+    bool active = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
+    if (op.givens) active = active && (label_bit(k0, k1, op.sbit) != label_bit(k0, k1, op.qbit));
+    if (!active) continue;
     const uint64_t hv = hash_label<KW>(k0, k1);
     const unsigned long long mine = ep | ((hv >> 48) << 32) | i;
     uint64_t h = hv & mask;
