@@ -160,8 +160,9 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
 typedef enum sps_option {
   SPS_OPT_LOAD_FACTOR_PCT = 1, /* target branching-table load, 10..90 (default 50) */
   SPS_OPT_PROBE_LIMIT = 2,     /* max slots probed per insert, >= 1 (default: table size) */
-  SPS_OPT_BLOCK_THREADS = 3,   /* threads per block of the per-element kernels: 128..1024 */
-  SPS_OPT_MAX_FUSED_OPS = 4,   /* longest op list of one fused pass, >= 1 (default 4096) */
+  SPS_OPT_BLOCK_THREADS = 3,   /* threads per block of the per-element kernels: 128 or
+                                  256 (default 256) */
+  SPS_OPT_MAX_FUSED_OPS = 4,   /* longest op list of one fused pass, 1..512 (default 512) */
   SPS_OPT_COOP_WIDTH = 5,      /* lanes probing one insert together: 1, 2, 4 or 8 */
   SPS_OPT_PROFILE = 6,         /* 1: time every kernel launch with CUDA events on the
                                   state's stream and log its entry counts; 0: off */
@@ -174,6 +175,9 @@ typedef enum sps_option {
                                   memory; 0 = never */
   SPS_OPT_BITSLICE_MIN_NNZ = 9, /* ... and only when the nonzero bound before the
                                   pass is at least this (default 262,144) */
+  SPS_OPT_BITSLICE_GROUPS = 11, /* groups of 32 entries per warp tile in the
+                                  bit-sliced pass: even, 2..32; 0 = chosen from
+                                  the state size (default) */
   SPS_OPT_BRANCH_FORM = 10     /* branching passes on the whole GPU: 0 default
                                   (gather), 1 scatter (labels emitted into a
                                   32-byte-slot table, FP64 atomic accumulation,

@@ -66,6 +66,7 @@ struct sps_state {
   int coop = 1;
   uint32_t bitslice_min_ops = 8;
   uint64_t bitslice_min_nnz = 1u << 18;   // below this the direct kernel is faster
+  uint32_t bs_groups = 0;                  // bit-sliced tile groups, 0 = heuristic
   uint32_t small_cap = kSmallCap;   // 0 disables small-state runs
   // plan arena: bit-sliced op lists and phase tables of the current sps_apply
   unsigned char* arena = nullptr;
@@ -639,6 +640,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         bl.has_phase = p.has_phase;
         bl.has_cnt = b.has_cnt;
         bl.list_len = (uint32_t)b.list.size();
+        bl.groups = s->bs_groups;
         n = launch_fused_bs(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
       } else {
         n = launch_fused(lc, s->kw, s->ctl, s->bufs, p, s->nnz_bound, ps.slot);
@@ -850,6 +852,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_MAX_FUSED_OPS:
       if (v < 1 || v > (int64_t)kMaxFusedOps) return SPS_ERR_ARG;
       s->max_fused_ops = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_BITSLICE_GROUPS:
+      if (v < 0 || v > 32 || (v & 1)) return SPS_ERR_ARG;
+      s->bs_groups = (uint32_t)v;
       return SPS_OK;
     case SPS_OPT_BRANCH_FORM:
       if (v < 0 || v > 2) return SPS_ERR_ARG;

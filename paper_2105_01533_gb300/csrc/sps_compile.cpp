@@ -213,14 +213,13 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
     for (int w = 0; w < 2; ++w)
       for (int b = 0; b < 64; ++b)
         if ((o.c[w] >> b) & 1ull) conds.push_back((uint8_t)(64 * w + b));
-    if (conds.size() <= 3) {
-      so.nc = (uint8_t)conds.size();
-      for (size_t k = 0; k < conds.size(); ++k) so.c[k] = conds[k];
-    } else {
-      so.nc = SOP_LIST;
+    so.c[0] = so.c[1] = so.c[2] = SOP_ONES;
+    for (size_t k = 0; k < conds.size() && k < 3; ++k) so.c[k] = conds[k];
+    if (conds.size() > 3) {
+      so.kind |= SOP_LIST;
       so.list_off = (uint16_t)out->list.size();
-      so.list_n = (uint16_t)conds.size();
-      out->list.insert(out->list.end(), conds.begin(), conds.end());
+      so.list_n = (uint16_t)(conds.size() - 3);
+      out->list.insert(out->list.end(), conds.begin() + 3, conds.end());
     }
     if (o.t[0] | o.t[1]) {
       so.kind |= SOP_FLIP;
@@ -251,6 +250,11 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
   }
   out->aux_bits = aux;
   out->na = (aux + 31) / 32;
+  // unused condition slots read the all-ones row that follows the aux rows
+  const uint8_t ones = (uint8_t)(32 * (out->nw + out->na));
+  for (SOp& so : out->ops)
+    for (int k = 0; k < 3; ++k)
+      if (so.c[k] == SOP_ONES) so.c[k] = ones;
   const uint32_t nch = out->nchunks();
   out->tables.assign((size_t)nch * 256 * 2, 0.0);
   for (uint32_t c = 0; c < nch; ++c) {

@@ -61,14 +61,18 @@ __device__ __forceinline__ uint64_t hash_label(uint64_t lo, uint64_t hi) {
 
 // contribution M[row][x] * (re, im), rounded like the plain formula
 // (re*mr - im*mi, re*mi + im*mr) with every product and sum rounded once.
+// (The entries are picked with selects, not a runtime index: indexing a
+// kernel-parameter struct with a runtime value copies it to local memory.)
 __device__ __forceinline__ void mat_times(const BranchOp& op, int row, int x, double re,
                                           double im, double* o_re, double* o_im) {
-  const double mr = op.m_re[row][x];
+  const double mr = row == 0 ? (x ? op.m_re[0][1] : op.m_re[0][0])
+                             : (x ? op.m_re[1][1] : op.m_re[1][0]);
   if (op.real_m) {
     *o_re = __dmul_rn(mr, re);
     *o_im = __dmul_rn(mr, im);
   } else {
-    const double mi = op.m_im[row][x];
+    const double mi = row == 0 ? (x ? op.m_im[0][1] : op.m_im[0][0])
+                               : (x ? op.m_im[1][1] : op.m_im[1][0]);
     *o_re = __dsub_rn(__dmul_rn(mr, re), __dmul_rn(mi, im));
     *o_im = __dadd_rn(__dmul_rn(mr, im), __dmul_rn(mi, re));
   }

@@ -67,19 +67,20 @@ struct BranchOp {
 // "aux" bits: 0..2 the counter (if any), then one fire plane per arbitrary
 // phase slot. After the op walk every entry gets its aux word back, and its
 // phase is the product over 8-bit chunks of precomputed tables.
-enum SOpKind : uint8_t { SOP_FLIP = 1, SOP_CNT = 2, SOP_FIRE = 4, SOP_SEL = 8 };
-constexpr uint8_t SOP_LIST = 0xFF;   // conditions come from the list
+enum SOpKind : uint8_t { SOP_FLIP = 1, SOP_CNT = 2, SOP_FIRE = 4, SOP_SEL = 8, SOP_LIST = 16 };
+// Row index of a constant all-ones plane: unused condition slots point here so
+// the condition is always the AND of three rows.
+constexpr uint8_t SOP_ONES = 255;
 
-struct SOp {                // 16 bytes
-  uint8_t kind;
-  uint8_t nc;               // 0..3 inline conditions, or SOP_LIST
-  uint8_t c[3];             // condition rows
-  uint8_t t;                // flip row
+struct SOp {                // 16 bytes, read as four 32-bit words
+  uint8_t kind;             // word 0
+  uint8_t c[3];             // condition rows (SOP_ONES when unused)
+  uint8_t t;                // word 1: flip row
   uint8_t s;                // selector row
-  uint8_t a0, a1;           // counter steps for sel = 0 / 1
   uint8_t f0, f1;           // aux rows written for sel = 0 / sel = 1 (f1 only with SEL)
-  uint8_t reserved;
-  uint16_t list_off, list_n;
+  uint8_t a0, a1;           // word 2: counter steps for sel = 0 / 1
+  uint16_t reserved;
+  uint16_t list_off, list_n;  // word 3: extra conditions (SOP_LIST)
 };
 static_assert(sizeof(SOp) == 16, "SOp layout");
 
@@ -214,6 +215,7 @@ struct BsLaunch {
   const double* tables;
   uint32_t nops, nw, na, nchunks;
   uint32_t has_perm, has_phase, has_cnt, list_len;
+  uint32_t groups;          // groups of 32 entries per warp tile (even, 2..32), 0 = choose
 };
 int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
                     uint64_t nnz_bound, unsigned long long* plog);

@@ -158,15 +158,15 @@ struct BsArgs {
   const double* tables;
   uint32_t nops, nw, na, nchunks;
   uint32_t has_perm, has_phase, has_cnt, list_len;
-  uint32_t groups;   // groups of 32 entries per warp tile (1..32)
+  uint32_t groups;   // groups of 32 entries per warp tile (even, 2..32)
 };
 
 template <int KW>
-__global__ void __launch_bounds__(256) k_fused_bs(Ctl* ctl, Bufs bufs,
+__global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
                                                   const __grid_constant__ BsArgs a,
                                                   unsigned long long* plog) {
   extern __shared__ __align__(16) unsigned char smem[];
-  SOp* sops = reinterpret_cast<SOp*>(smem);
+  uint4* sops = reinterpret_cast<uint4*>(smem);
   double2* stab = reinterpret_cast<double2*>(smem + 16 * a.nops);
   uint8_t* slist = reinterpret_cast<uint8_t*>(stab + 256 * a.nchunks);
   uint32_t* splanes =
@@ -177,11 +177,10 @@ __global__ void __launch_bounds__(256) k_fused_bs(Ctl* ctl, Bufs bufs,
     plog[1] = n;
   }
   if (ctl->status != 0u) return;
-  // stage the op list, the phase tables and the condition list
+  // stage the op list, the phase tables and the extra-condition list
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.ops);
-    uint4* dst = reinterpret_cast<uint4*>(sops);
-    for (uint32_t i = threadIdx.x; i < a.nops; i += blockDim.x) dst[i] = src[i];
+    for (uint32_t i = threadIdx.x; i < a.nops; i += blockDim.x) sops[i] = src[i];
     const double2* ts = reinterpret_cast<const double2*>(a.tables);
     for (uint32_t i = threadIdx.x; i < 256 * a.nchunks; i += blockDim.x) stab[i] = ts[i];
     for (uint32_t i = threadIdx.x; i < a.list_len; i += blockDim.x) slist[i] = a.list[i];
@@ -190,12 +189,15 @@ __global__ void __launch_bounds__(256) k_fused_bs(Ctl* ctl, Bufs bufs,
   const SoA s = pick(bufs, ctl->cur);
   const unsigned lane = threadIdx.x & 31u;
   const unsigned warp = threadIdx.x >> 5;
-  const uint32_t rows = 32u * (a.nw + a.na);
-  uint32_t* pl = splanes + (size_t)warp * rows * 33u;
   const uint32_t G = a.groups;
+  const uint32_t S = G + 1u;                       // column stride (odd: conflict-free)
+  const uint32_t rows = 32u * (a.nw + a.na) + 1u;  // + the all-ones row
+  const uint32_t ones_row = rows - 1u;
+  uint32_t* pl = splanes + (size_t)warp * rows * S;
   const uint64_t tile_entries = 32ull * G;
   const uint64_t ntiles = (n + tile_entries - 1) / tile_entries;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint32_t c = lane; c < S; c += 32u) pl[ones_row * S + c] = 0xFFFFFFFFu;
   for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < ntiles;
        tile += nwarps) {
     const uint64_t base = tile * tile_entries;
@@ -208,41 +210,45 @@ __global__ void __launch_bounds__(256) k_fused_bs(Ctl* ctl, Bufs bufs,
       for (uint32_t w = 0; w < a.nw; ++w) {
         const uint64_t src = w < 2 ? lo : hi;
         const uint32_t x = (uint32_t)(src >> (32 * (w & 1u)));
-        pl[(32u * w + lane) * 33u + g] = transpose32(x, lane);
+        pl[(32u * w + lane) * S + g] = transpose32(x, lane);
       }
     }
-    for (uint32_t r = 32u * a.nw; r < rows; ++r) pl[r * 33u + lane] = 0u;
+    for (uint32_t r = 32u * a.nw; r < ones_row; ++r)
+      for (uint32_t c = lane; c < G; c += 32u) pl[r * S + c] = 0u;
     __syncwarp();
     // 2. op walk, lane g on group g
     if (lane < G) {
       uint32_t* col = pl + lane;
       uint32_t c0 = 0u, c1 = 0u, c2 = 0u;
       for (uint32_t j = 0; j < a.nops; ++j) {
-        const SOp o = sops[j];
-        uint32_t f = 0xFFFFFFFFu;
-        if (o.nc != SOP_LIST) {
-          if (o.nc > 0) f &= col[o.c[0] * 33u];
-          if (o.nc > 1) f &= col[o.c[1] * 33u];
-          if (o.nc > 2) f &= col[o.c[2] * 33u];
-        } else {
-          for (uint32_t k = 0; k < o.list_n; ++k) f &= col[slist[o.list_off + k] * 33u];
+        const uint4 w = sops[j];
+        uint32_t f = col[((w.x >> 8) & 0xFFu) * S] & col[((w.x >> 16) & 0xFFu) * S] &
+                     col[(w.x >> 24) * S];
+        const uint32_t kind = w.x & 0xFFu;
+        if (kind == SOP_FLIP) {   // X / CNOT / Toffoli
+          col[(w.y & 0xFFu) * S] ^= f;
+          continue;
         }
-        const uint32_t sel = (o.kind & SOP_SEL) ? col[o.s * 33u] : 0u;
-        if (o.kind & SOP_CNT) {
-          cnt_add(c0, c1, c2, o.a0, f & ~sel);
-          if (o.kind & SOP_SEL) cnt_add(c0, c1, c2, o.a1, f & sel);
+        if (kind & SOP_LIST) {
+          const uint32_t off = w.w & 0xFFFFu, cnt = w.w >> 16;
+          for (uint32_t k = 0; k < cnt; ++k) f &= col[slist[off + k] * S];
         }
-        if (o.kind & SOP_FIRE) {
-          col[o.f0 * 33u] = f & ~sel;
-          if (o.kind & SOP_SEL) col[o.f1 * 33u] = f & sel;
+        const uint32_t sel = (kind & SOP_SEL) ? col[((w.y >> 8) & 0xFFu) * S] : 0u;
+        if (kind & SOP_CNT) {
+          cnt_add(c0, c1, c2, w.z & 0xFFu, f & ~sel);
+          if (kind & SOP_SEL) cnt_add(c0, c1, c2, (w.z >> 8) & 0xFFu, f & sel);
         }
-        if (o.kind & SOP_FLIP) col[o.t * 33u] ^= f;
+        if (kind & SOP_FIRE) {
+          col[((w.y >> 16) & 0xFFu) * S] = f & ~sel;
+          if (kind & SOP_SEL) col[(w.y >> 24) * S] = f & sel;
+        }
+        if (kind & SOP_FLIP) col[(w.y & 0xFFu) * S] ^= f;
       }
       if (a.has_cnt) {
         const uint32_t r0 = 32u * a.nw;
-        col[r0 * 33u] = c0;
-        col[(r0 + 1u) * 33u] = c1;
-        col[(r0 + 2u) * 33u] = c2;
+        col[r0 * S] = c0;
+        col[(r0 + 1u) * S] = c1;
+        col[(r0 + 2u) * S] = c2;
       }
     }
     __syncwarp();
@@ -252,12 +258,12 @@ __global__ void __launch_bounds__(256) k_fused_bs(Ctl* ctl, Bufs bufs,
       const bool valid = e < n;
       uint64_t lo = 0ull, hi = 0ull;
       for (uint32_t w = 0; w < a.nw; ++w) {
-        const uint64_t x = transpose32(pl[(32u * w + lane) * 33u + g], lane);
+        const uint64_t x = transpose32(pl[(32u * w + lane) * S + g], lane);
         if (w < 2) lo |= x << (32 * w); else hi |= x << (32 * (w - 2));
       }
       uint32_t aux0 = 0u, aux1 = 0u;
-      if (a.na > 0) aux0 = transpose32(pl[(32u * a.nw + lane) * 33u + g], lane);
-      if (a.na > 1) aux1 = transpose32(pl[(32u * (a.nw + 1u) + lane) * 33u + g], lane);
+      if (a.na > 0) aux0 = transpose32(pl[(32u * a.nw + lane) * S + g], lane);
+      if (a.na > 1) aux1 = transpose32(pl[(32u * (a.nw + 1u) + lane) * S + g], lane);
       if (valid) {
         if (a.has_perm) {
           s.lo[e] = lo;
@@ -632,24 +638,35 @@ int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uin
   a.has_phase = b.has_phase;
   a.has_cnt = b.has_cnt;
   a.list_len = b.list_len;
+  const int sms = lc.max_blocks / 8 > 0 ? lc.max_blocks / 8 : 1;
   const size_t fixed = bs_smem_fixed(b);
-  const size_t per_warp = (size_t)32 * (b.nw + b.na) * 33 * 4;
+  const size_t rows = 32 * (size_t)(b.nw + b.na) + 1;
   const size_t budget = 200 * 1024;
-  int warps = 8;
+  // groups per tile: enough tiles to give every resident warp work, else as
+  // many groups as fit (more groups per op walk = fewer instructions per entry)
+  uint32_t G = b.groups;
+  int warps = 16;
+  if (G == 0) {
+    G = 32;
+    while (G > 2) {
+      const size_t per_warp = rows * (G + 1) * 4;
+      int w = 16;
+      while (w > 1 && fixed + w * per_warp > budget) w >>= 1;
+      const uint64_t resident = (uint64_t)sms * w * (budget / (fixed + w * per_warp));
+      const uint64_t tiles = (nnz_bound + 32ull * G - 1) / (32ull * G);
+      if (tiles >= resident && w >= 8) break;
+      G -= 2;
+    }
+  }
+  a.groups = G;
+  const size_t per_warp = rows * (G + 1) * 4;
   while (warps > 1 && fixed + warps * per_warp > budget) warps >>= 1;
   if (fixed + warps * per_warp > budget) return -1;
   const size_t smem = fixed + warps * per_warp;
-  // enough warps to fill the GPU: tiles of 32 x G entries
-  const uint64_t want_warps = (uint64_t)(lc.max_blocks > 0 ? lc.max_blocks : 1) * 4;
-  uint64_t g = (nnz_bound + 32 * want_warps - 1) / (32 * want_warps);
-  if (g < 1) g = 1;
-  if (g > 32) g = 32;
-  a.groups = (uint32_t)g;
-  const uint64_t tiles = (nnz_bound + 32 * g - 1) / (32 * g);
+  const uint64_t tiles = (nnz_bound + 32ull * G - 1) / (32ull * G);
   uint64_t blocks = (tiles + warps - 1) / warps;
   const int per_sm_blocks = (int)((227 * 1024) / (smem + 1024));
-  const uint64_t max_blocks = (uint64_t)(lc.max_blocks / 8 > 0 ? lc.max_blocks / 8 : 1) *
-                              (per_sm_blocks > 0 ? per_sm_blocks : 1);
+  const uint64_t max_blocks = (uint64_t)sms * (per_sm_blocks > 0 ? per_sm_blocks : 1);
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
   cudaFuncSetAttribute(k_fused_bs<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

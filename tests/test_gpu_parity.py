@@ -401,15 +401,17 @@ def test_bitslice_many_phase_slots_and_split():
     compare_states(got, want, 1e-14)
 
 
-@pytest.mark.parametrize("nnz_log2", [5, 10, 15, 17])
-def test_bitslice_sizes(nnz_log2):
+@pytest.mark.parametrize("nnz_log2,groups", [(5, 0), (10, 0), (15, 0), (17, 0), (15, 2),
+                                             (17, 8), (17, 32)])
+def test_bitslice_sizes(nnz_log2, groups):
     """Tiles of 1..32 groups and a ragged tail: 2^k entries plus a few."""
     n = 70
     prep = [W.H(q) for q in range(nnz_log2)] + [W.Ry(40, 0.3, 0)] + [W.H(41, 1)]
     gates = np.concatenate([W.to_array(prep), perm_diag_run(9, n, 200, max_controls=3)])
     got, want = run_both(n, gates, eps=1e-14, capacity=1 << 19,
                          options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1),
-                                  (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
+                                  (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0),
+                                  (sps.SPS_OPT_BITSLICE_GROUPS, groups)])
     compare_states(got, want, 1e-14)
     assert len(got[1]) > (1 << nnz_log2)
 
