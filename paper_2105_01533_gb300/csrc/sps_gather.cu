@@ -30,8 +30,6 @@ namespace {
 
 using namespace dev;
 
-constexpr int kBuildU = 4;   // inputs per thread per step in the index build
-constexpr int kEmitU = 2;    // inputs per thread per step in the emit
 
 struct GatherArgs {
   BranchOp op;
@@ -61,49 +59,32 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
   const SoA s = pick(bufs, ctl->cur);
   const unsigned long long ep = (unsigned long long)a.epoch << 48;
   const BranchOp& op = a.op;
-  // kBuildU inputs per thread per step, so their dependent load/CAS chains overlap
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < n;
-       i0 += stride * kBuildU) {
-    uint64_t h[kBuildU];
-    unsigned long long mine[kBuildU];
-    bool todo[kBuildU];
-#pragma unroll
-    for (int u = 0; u < kBuildU; ++u) {
-      const uint64_t i = i0 + u * stride;
-      todo[u] = false;
-      if (i >= n) continue;
-      const uint64_t k0 = s.lo[i];
-      const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
-      // The partner of an active label is active too (flipping the target bits
-      // keeps the controls and the Givens condition), so only active labels are
-      // ever looked up: index those alone.
-      bool active = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
-      if (op.givens) active = active && (label_bit(k0, k1, op.sbit) != label_bit(k0, k1, op.qbit));
-      if (!active) continue;
-      const uint64_t hv = hash_label<KW>(k0, k1);
-      mine[u] = ep | ((hv >> 48) << 32) | i;
-      h[u] = hv & mask;
-      todo[u] = true;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k0 = s.lo[i];
+    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    // The partner of an active label is active too (flipping the target bits
+    // keeps the controls and the Givens condition), so only active labels are
+    // ever looked up: index those alone.
+    bool active = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
+    if (op.givens) active = active && (label_bit(k0, k1, op.sbit) != label_bit(k0, k1, op.qbit));
+    if (!active) continue;
+    const uint64_t hv = hash_label<KW>(k0, k1);
+    const unsigned long long mine = ep | ((hv >> 48) << 32) | i;
+    uint64_t h = hv & mask;
+    bool ok = false;
+    for (uint64_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
+      const unsigned long long v = __ldcg(itab + h);
+      if ((v & 0xFFFF000000000000ull) == ep) continue;   // taken in this pass
+      if (atomicCAS(itab + h, v, mine) == v) {
+        ok = true;
+        break;
+      }
+      // lost the race: the slot now belongs to this pass, go on
     }
-#pragma unroll
-    for (int u = 0; u < kBuildU; ++u) {
-      if (!todo[u]) continue;
-      bool ok = false;
-      uint64_t hh = h[u];
-      for (uint64_t p = 0; p <= mask; ++p, hh = (hh + 1) & mask) {
-        const unsigned long long v = __ldcg(itab + hh);
-        if ((v & 0xFFFF000000000000ull) == ep) continue;   // taken in this pass
-        if (atomicCAS(itab + hh, v, mine[u]) == v) {
-          ok = true;
-          break;
-        }
-        // lost the race: the slot now belongs to this pass, go on
-      }
-      if (!ok) {
-        fail(ctl, SPS_ERR_TABLE_FULL, a.pass_serial, a.fail_tag);
-        return;
-      }
+    if (!ok) {
+      fail(ctl, SPS_ERR_TABLE_FULL, a.pass_serial, a.fail_tag);
+      return;
     }
   }
 }
@@ -143,21 +124,13 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
   const BranchOp& op = a.op;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned nwarps = blockDim.x >> 5;
-  // Each step takes kEmitU * blockDim consecutive inputs per block (thread t
-  // takes inputs t, t + blockDim, ...); outputs of the step are compacted with
-  // one block scan and one global atomic.
-  const uint64_t step_in = (uint64_t)kEmitU * blockDim.x;
-  for (uint64_t base = blockIdx.x * step_in; base < n; base += (uint64_t)gridDim.x * step_in) {
-    uint64_t l0[kEmitU], h0[kEmitU], l1[kEmitU], h1[kEmitU];
-    double v0r[kEmitU], v0i[kEmitU], v1r[kEmitU], v1i[kEmitU];
-    bool w0[kEmitU], w1[kEmitU];
-#pragma unroll
-    for (int u = 0; u < kEmitU; ++u) {
-      const uint64_t i = base + (uint64_t)u * blockDim.x + threadIdx.x;
-      w0[u] = w1[u] = false;
-      l0[u] = h0[u] = l1[u] = h1[u] = 0ull;
-      v0r[u] = v0i[u] = v1r[u] = v1i[u] = 0.0;
-      if (i >= n) continue;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    uint64_t l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+    double v0r = 0, v0i = 0, v1r = 0, v1i = 0;
+    bool w0 = false, w1 = false;
+    if (i < n) {
       const uint64_t k0 = s.lo[i];
       const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
       const double re = s.re[i], im = s.im[i];
@@ -165,31 +138,26 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
       const bool x = label_bit(k0, k1, op.sbit);
       if (op.givens) active = active && (x != label_bit(k0, k1, op.qbit));
       if (!active) {
-        l0[u] = k0; h0[u] = k1; v0r[u] = re; v0i[u] = im;
-        w0[u] = keep_amp(re, im, a.eps2, eps_pattern(a.eps));
-        continue;
+        l0 = k0; h0 = k1; v0r = re; v0i = im;
+        w0 = keep_amp(re, im, a.eps2, eps_pattern(a.eps));
+      } else {
+        const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
+        const uint64_t j = find_label<KW>(itab, mask, ep, s, p0, p1);
+        if (j == ~0ull || x) {   // else the partner with selector bit 1 writes the pair
+          const double pre = j != ~0ull ? s.re[j] : 0.0;
+          const double pim = j != ~0ull ? s.im[j] : 0.0;
+          const double a0r = x ? pre : re, a0i = x ? pim : im;
+          const double a1r = x ? re : pre, a1i = x ? im : pim;
+          l0 = x ? p0 : k0; h0 = x ? p1 : k1;
+          l1 = x ? k0 : p0; h1 = x ? k1 : p1;
+          pair_action(op, j != ~0ull, x, a0r, a0i, a1r, a1i, &v0r, &v0i, &v1r, &v1i);
+          w0 = keep_amp(v0r, v0i, a.eps2, eps_pattern(a.eps));
+          w1 = keep_amp(v1r, v1i, a.eps2, eps_pattern(a.eps));
+        }
       }
-      const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
-      const uint64_t j = find_label<KW>(itab, mask, ep, s, p0, p1);
-      if (j != ~0ull && !x) continue;   // the partner with selector bit 1 writes the pair
-      const double pre = j != ~0ull ? s.re[j] : 0.0;
-      const double pim = j != ~0ull ? s.im[j] : 0.0;
-      const double a0r = x ? pre : re, a0i = x ? pim : im;
-      const double a1r = x ? re : pre, a1i = x ? im : pim;
-      l0[u] = x ? p0 : k0; h0[u] = x ? p1 : k1;
-      l1[u] = x ? k0 : p0; h1[u] = x ? k1 : p1;
-      pair_action(op, j != ~0ull, x, a0r, a0i, a1r, a1i, &v0r[u], &v0i[u], &v1r[u], &v1i[u]);
-      w0[u] = keep_amp(v0r[u], v0i[u], a.eps2, eps_pattern(a.eps));
-      w1[u] = keep_amp(v1r[u], v1i[u], a.eps2, eps_pattern(a.eps));
     }
-    unsigned mine = 0, b[2 * kEmitU];
-#pragma unroll
-    for (int u = 0; u < kEmitU; ++u) {
-      b[2 * u] = __ballot_sync(FULL, w0[u]);
-      b[2 * u + 1] = __ballot_sync(FULL, w1[u]);
-      mine += __popc(b[2 * u]) + __popc(b[2 * u + 1]);
-    }
-    if (lane == 0) warp_cnt[warp] = mine;
+    const unsigned b0 = __ballot_sync(FULL, w0), b1 = __ballot_sync(FULL, w1);
+    if (lane == 0) warp_cnt[warp] = __popc(b0) + __popc(b1);
     __syncthreads();
     if (warp == 0) {
       const unsigned v = lane < nwarps ? warp_cnt[lane] : 0u;
@@ -204,26 +172,22 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
         block_base = total ? atomicAdd(&ctl->out_count, (unsigned long long)total) : 0ull;
     }
     __syncthreads();
-    // warp-local order: all of slot (u, output) for every lane, slot by slot
     const unsigned below = (1u << lane) - 1u;
-    uint64_t pos = block_base + warp_cnt[warp];
-#pragma unroll
-    for (int u = 0; u < kEmitU; ++u) {
-#pragma unroll
-      for (int o = 0; o < 2; ++o) {
-        const unsigned bb = b[2 * u + o];
-        const bool w = o == 0 ? w0[u] : w1[u];
-        if (w) {
-          const uint64_t q = pos + __popc(bb & below);
-          if (q < a.capacity) {
-            out.lo[q] = o == 0 ? l0[u] : l1[u];
-            if (KW == 2) out.hi[q] = o == 0 ? h0[u] : h1[u];
-            out.re[q] = o == 0 ? v0r[u] : v1r[u];
-            out.im[q] = o == 0 ? v0i[u] : v1i[u];
-          }
-        }
-        pos += __popc(bb);
+    uint64_t pos = block_base + warp_cnt[warp] + __popc(b0 & below) + __popc(b1 & below);
+    if (w0) {
+      if (pos < a.capacity) {
+        out.lo[pos] = l0;
+        if (KW == 2) out.hi[pos] = h0;
+        out.re[pos] = v0r;
+        out.im[pos] = v0i;
       }
+      ++pos;
+    }
+    if (w1 && pos < a.capacity) {
+      out.lo[pos] = l1;
+      if (KW == 2) out.hi[pos] = h1;
+      out.re[pos] = v1r;
+      out.im[pos] = v1i;
     }
     __syncthreads();
   }

@@ -644,19 +644,14 @@ int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uin
   const size_t budget = 200 * 1024;
   // groups per tile: enough tiles to give every resident warp work, else as
   // many groups as fit (more groups per op walk = fewer instructions per entry)
+  // Measured on GB300 (adder, 4M entries): 8 groups per tile beat 16 and 32 -
+  // the op walk is latency-bound, so more resident warps win over fewer
+  // instructions per entry. Fewer groups when the state is small.
   uint32_t G = b.groups;
   int warps = 16;
   if (G == 0) {
-    G = 32;
-    while (G > 2) {
-      const size_t per_warp = rows * (G + 1) * 4;
-      int w = 16;
-      while (w > 1 && fixed + w * per_warp > budget) w >>= 1;
-      const uint64_t resident = (uint64_t)sms * w * (budget / (fixed + w * per_warp));
-      const uint64_t tiles = (nnz_bound + 32ull * G - 1) / (32ull * G);
-      if (tiles >= resident && w >= 8) break;
-      G -= 2;
-    }
+    G = 8;
+    while (G > 2 && (nnz_bound + 32ull * G - 1) / (32ull * G) < (uint64_t)sms * 16) G -= 2;
   }
   a.groups = G;
   const size_t per_warp = rows * (G + 1) * 4;
