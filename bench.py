@@ -369,6 +369,11 @@ def run_ours(args, dist, rank, world, local_rank):
                "p99_step_ms": round(float(np.percentile(step_ms, 99)), 5)}
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
+    if args.batched and wl["name"].startswith("adder67"):
+        bres = run_batched(args, sps, torch, args.batch_count, steps=args.batch_steps,
+                           warmup=1)
+        if res is not None:
+            res["batched"] = bres
     st.close()
     return res
 
@@ -400,6 +405,75 @@ def run_e2e(args, sps, torch, wl, st, flush, U, dist):
     return {"value": round(units / total, 1), "unit": UNIT,
             "h2d_bytes_per_step": int(wl["gates"].nbytes), "d2h_bytes_per_step": int(got * 32 + 64),
             "steps": k}
+
+
+# ---- batched form -----------------------------------------------------------------------
+def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_every: int = 32):
+    """4,096 independent circuits (qubits 20..100, depth 200..5000, caps
+    2^8..2^16) in one persistent launch per step, against the plain per-circuit
+    path on every `sample_every`-th circuit of the same set."""
+    from paper_2105_01533_gb300 import workloads as W
+    t0 = time.perf_counter()
+    circs = W.batched_workload_fast(count, first_seed=1)
+    gen_s = time.perf_counter() - t0
+    b = sps.Batch()
+    for c in circs:
+        b.add(c.nqubits, c.cap, c.gates, EPS)
+    tuned = b.tune(repeats=1)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, warmup)):
+        b.reset()
+        b.run()
+        b.sync()
+    upd = b.updates()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        b.reset()
+        ev[i][0].record(stream)
+        b.run()
+        ev[i][1].record(stream)
+        left = b.sync()
+        assert left == 0
+    ms = [a.elapsed_time(e) for a, e in ev]
+    failed = sum(1 for i in range(len(circs)) if b.status(i)["status"] != 0)
+    b.close()
+    batched_rate = upd * steps / (sum(ms) * 1e-3)
+    # the plain path on a sample of the same circuits, one circuit at a time
+    sample = circs[::sample_every]
+    sb = sps.Batch()
+    for c in sample:
+        sb.add(c.nqubits, c.cap, c.gates, EPS)
+    sb.run()
+    sb.sync()
+    upd_s = sb.updates()
+    sb.close()
+    states = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in sample:
+        st = states.get((c.nqubits, c.cap))
+        if st is None:
+            st = states[(c.nqubits, c.cap)] = sps.SparseState(c.nqubits, c.cap)
+        st.reset()
+        st.apply(c.gates, EPS)
+        st.sync()
+    plain_s = time.perf_counter() - t0
+    for st in states.values():
+        st.close()
+    plain_rate = upd_s / plain_s
+    return {"workload": "batched%d: qubits U{20..100}, depth U{200..5000}, caps 2^U[8,16], "
+                        "mix 70%% X/CNOT/Toffoli, 20%% Z/S/T/CRz, 10%% H within the cap; FP64, "
+                        "eps 1e-14" % count,
+            "circuits": count, "gates": int(sum(len(c.gates) for c in circs)),
+            "updates_per_step": int(upd), "value": round(batched_rate, 1), "unit": UNIT,
+            "ms_per_step": round(float(np.median(ms)), 3), "steps": steps,
+            "launches_per_step": 1, "failed_circuits": failed, "tuned_config": tuned,
+            "plain_value": round(plain_rate, 1),
+            "plain_sample": "every %dth circuit (%d circuits), one sps_apply + sync each, "
+                            "wall clock" % (sample_every, len(sample)),
+            "batched_vs_plain": round(batched_rate / plain_rate, 2),
+            "generate_s": round(gen_s, 1)}
 
 
 # ---- the oracle on the host ------------------------------------------------------------
@@ -482,6 +556,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--opt", action="append", default=[],
                     help="library option NAME=VALUE (e.g. bitslice_min_ops=0), repeatable")
+    ap.add_argument("--batched", type=int, default=1,
+                    help="also measure the batched form (1) or not (0)")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--dump-profile", default=None,
                     help="write the per-launch records of one profiled step to this JSON file")
     args = ap.parse_args()

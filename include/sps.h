@@ -229,6 +229,76 @@ sps_status sps_plan(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                     uint32_t max_fused_ops, uint32_t* kind, uint64_t* first_gate,
                     uint32_t* ops, size_t cap, size_t* npasses, size_t* failed_gate);
 
+/* ---- Batched circuits ---------------------------------------------------------
+ * Many independent circuits, each from |0...0>, advanced by one persistent
+ * kernel launch. Blocks take circuits from a queue ordered by estimated work
+ * (largest first); a circuit whose capacity fits the shared-memory cap runs
+ * with its state in shared memory, others on their own device buffers. Each
+ * circuit's progress is kept on the device, so sps_batch_run may advance every
+ * circuit by a bounded number of passes and be called again to resume.
+ * Branching passes use the insert-once rule of Sec. 3.1 (gather form, no
+ * amplitude atomics); results equal sps_apply's. */
+typedef struct sps_batch sps_batch;
+
+typedef struct sps_batch_config {
+  uint32_t threads;        /* threads per block: 256, 512 or 1024 */
+  uint32_t blocks_per_sm;  /* persistent blocks per SM: 1..4 */
+  uint32_t smem_cap;       /* circuits with capacity <= this (power of two,
+                              64..2048, or 0) keep their state in shared memory */
+  uint32_t reserved;
+} sps_batch_config;
+
+/* Creates an empty batch bound to `cuda_stream` (NULL = legacy default). */
+sps_status sps_batch_create(void* cuda_stream, sps_batch** out);
+void sps_batch_destroy(sps_batch* b);
+
+/* Adds one circuit (gates copied; validated like sps_apply, SPS_ERR_ARG with
+ * *failed_gate on a bad record). capacity: 1..2^24 nonzeros. *index receives
+ * its position. Circuits can only be added before the first run or reset. */
+sps_status sps_batch_add(sps_batch* b, uint32_t nqubits, uint64_t capacity,
+                         const sps_gate* gates, size_t ngates, double prune_eps,
+                         uint32_t* index, size_t* failed_gate);
+
+/* Enqueues one launch advancing every unfinished circuit by up to max_passes
+ * passes (0 = to completion). The first call allocates device memory. */
+sps_status sps_batch_run(sps_batch* b, uint32_t max_passes);
+
+/* Waits for the batch's stream and reads back every circuit's progress;
+ * *unfinished (nullable) receives the number still to run. */
+sps_status sps_batch_sync(sps_batch* b, uint32_t* unfinished);
+
+/* After sps_batch_sync: status of circuit `index` (SPS_OK or SPS_ERR_CAPACITY
+ * with *failed_gate the first gate of the failing pass; the state is then the
+ * one before that pass), its nonzero count and whether it has finished. */
+sps_status sps_batch_circuit_status(sps_batch* b, uint32_t index, sps_status* status,
+                                    size_t* failed_gate, uint64_t* nnz, int* finished);
+
+/* After sps_batch_sync: copies circuit `index`'s state out (host or device
+ * pointers, key_hi nullable), like sps_get_amplitudes. */
+sps_status sps_batch_get_amplitudes(sps_batch* b, uint32_t index, uint64_t* key_hi,
+                                    uint64_t* key_lo, double* re, double* im, uint64_t cap,
+                                    uint64_t* nnz_out);
+
+/* Enqueues a reset of every circuit to |0...0> with no progress. */
+sps_status sps_batch_reset(sps_batch* b);
+
+sps_status sps_batch_set_config(sps_batch* b, const sps_batch_config* cfg);
+sps_status sps_batch_get_config(sps_batch* b, sps_batch_config* cfg);
+
+/* Autotuner: runs the whole batch to completion `repeats` times under each of
+ * a fixed set of block sizes, blocks per SM and shared-memory caps, keeps the
+ * fastest (timed with CUDA events on the batch's stream), writes it to *best
+ * and *best_ms (nullable) and leaves the batch reset. */
+sps_status sps_batch_tune(sps_batch* b, uint32_t repeats, sps_batch_config* best,
+                          float* best_ms);
+
+/* Number of circuits and of batched launches enqueued so far. */
+sps_status sps_batch_counts(sps_batch* b, uint32_t* ncircuits, uint64_t* launches);
+
+/* After sps_batch_sync: nonzero-amplitude updates done since the last reset,
+ * summed over circuits (each applied gate counts the nonzeros before it). */
+sps_status sps_batch_updates(sps_batch* b, uint64_t* total);
+
 /* Allocation-free variant of one branching pass, for callers that must not
  * allocate device memory (a host framework that owns all device memory and
  * forbids library allocations, a service whose device footprint is fixed at

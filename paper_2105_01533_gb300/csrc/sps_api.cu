@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "sps.h"
+#include "sps_batch.h"
 #include "sps_internal.h"
 
 using namespace sps;
@@ -147,6 +148,32 @@ void release_all(sps_state* s) {
   s->hflag = nullptr;
   cudaGetLastError();
 }
+
+}  // namespace
+
+void* sps::hook_alloc(size_t bytes, void* stream) {
+  sps_alloc_fn a;
+  void* ctx;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc ? g_alloc : default_alloc;
+    ctx = g_alloc ? g_alloc_ctx : nullptr;
+  }
+  return a(ctx, (bytes + 255) & ~size_t(255), stream);
+}
+
+void sps::hook_free(void* p, size_t bytes, void* stream) {
+  sps_free_fn f;
+  void* ctx;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    f = g_alloc ? g_free : default_free;
+    ctx = g_alloc ? g_alloc_ctx : nullptr;
+  }
+  f(ctx, p, (bytes + 255) & ~size_t(255), stream);
+}
+
+namespace {
 
 LaunchCfg cfg_of(const sps_state* s) {
   LaunchCfg lc;

@@ -34,7 +34,10 @@ KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_apply", "sps_sync",
            "sps_nnz", "sps_get_amplitudes", "sps_set_amplitudes", "sps_probability",
            "sps_set_option", "sps_get_counters", "sps_profile_read", "sps_plan", "sps_status_str",
-           "sps_branch_apply_static")
+           "sps_branch_apply_static", "sps_batch_create", "sps_batch_destroy", "sps_batch_add",
+           "sps_batch_run", "sps_batch_sync", "sps_batch_circuit_status",
+           "sps_batch_get_amplitudes", "sps_batch_reset", "sps_batch_set_config",
+           "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates")
 
 
 class SpsError(RuntimeError):
@@ -57,6 +60,11 @@ class KernelRecord(ctypes.Structure):
                 ("ms", ctypes.c_float), ("nops", ctypes.c_uint32), ("n_in", ctypes.c_uint64),
                 ("n_out", ctypes.c_uint64), ("flags", ctypes.c_uint32),
                 ("label_bytes", ctypes.c_uint32)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("smem_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -110,6 +118,33 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_branch_apply_static.argtypes = [vp, u32, vp, vp, vp, vp, u64, dbl, vp, vp, vp, vp,
                                             u64, pu64, vp]
     lib.sps_branch_apply_static.restype = st
+    lib.sps_batch_create.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.sps_batch_create.restype = st
+    lib.sps_batch_destroy.argtypes = [vp]
+    lib.sps_batch_destroy.restype = None
+    lib.sps_batch_add.argtypes = [vp, u32, u64, vp, sz, dbl, ctypes.POINTER(u32), psz]
+    lib.sps_batch_add.restype = st
+    lib.sps_batch_run.argtypes = [vp, u32]
+    lib.sps_batch_run.restype = st
+    lib.sps_batch_sync.argtypes = [vp, ctypes.POINTER(u32)]
+    lib.sps_batch_sync.restype = st
+    lib.sps_batch_circuit_status.argtypes = [vp, u32, ctypes.POINTER(st), psz, pu64,
+                                             ctypes.POINTER(ctypes.c_int)]
+    lib.sps_batch_circuit_status.restype = st
+    lib.sps_batch_get_amplitudes.argtypes = [vp, u32, vp, vp, vp, vp, u64, pu64]
+    lib.sps_batch_get_amplitudes.restype = st
+    lib.sps_batch_reset.argtypes = [vp]
+    lib.sps_batch_reset.restype = st
+    lib.sps_batch_set_config.argtypes = [vp, ctypes.POINTER(BatchConfig)]
+    lib.sps_batch_set_config.restype = st
+    lib.sps_batch_get_config.argtypes = [vp, ctypes.POINTER(BatchConfig)]
+    lib.sps_batch_get_config.restype = st
+    lib.sps_batch_tune.argtypes = [vp, u32, ctypes.POINTER(BatchConfig), ctypes.POINTER(ctypes.c_float)]
+    lib.sps_batch_tune.restype = st
+    lib.sps_batch_counts.argtypes = [vp, ctypes.POINTER(u32), pu64]
+    lib.sps_batch_counts.restype = st
+    lib.sps_batch_updates.argtypes = [vp, pu64]
+    lib.sps_batch_updates.restype = st
     lib.sps_status_str.argtypes = [st]
     lib.sps_status_str.restype = ctypes.c_char_p
     _lib = lib
@@ -380,3 +415,113 @@ class SparseState:
         re = np.ascontiguousarray(re, np.float64)
         im = np.ascontiguousarray(im, np.float64)
         sps_set_amplitudes(self._h, hi, lo, re, im, len(lo))
+
+
+# ---- batched circuits -------------------------------------------------------------
+class Batch:
+    """Many independent circuits advanced by one persistent launch."""
+
+    def __init__(self, stream: Optional[int] = None, torch_memory: bool = True):
+        if torch_memory:
+            use_torch_allocator()
+        if stream is None:
+            stream = current_stream_handle()
+        self.stream = stream
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.sps_batch_create(stream, ctypes.byref(h)), "sps_batch_create")
+        self._h = h.value
+        self.n = 0
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def close(self) -> None:
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            load_library().sps_batch_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, nqubits: int, capacity: int, gates, eps: float = 0.0) -> int:
+        g = gate_array(gates)
+        idx = ctypes.c_uint32(0)
+        bad = ctypes.c_size_t(0)
+        rc = load_library().sps_batch_add(self._h, nqubits, capacity, _ptr(g), g.size, float(eps),
+                                          ctypes.byref(idx), ctypes.byref(bad))
+        _check(rc, "sps_batch_add", bad.value if rc == SPS_ERR_ARG else None)
+        self.n += 1
+        return idx.value
+
+    def run(self, max_passes: int = 0) -> None:
+        _check(load_library().sps_batch_run(self._h, max_passes), "sps_batch_run")
+
+    def sync(self) -> int:
+        u = ctypes.c_uint32(0)
+        _check(load_library().sps_batch_sync(self._h, ctypes.byref(u)), "sps_batch_sync")
+        return u.value
+
+    def reset(self) -> None:
+        _check(load_library().sps_batch_reset(self._h), "sps_batch_reset")
+
+    def status(self, index: int):
+        st = ctypes.c_int(0)
+        fg = ctypes.c_size_t(0)
+        nnz = ctypes.c_uint64(0)
+        fin = ctypes.c_int(0)
+        _check(load_library().sps_batch_circuit_status(self._h, index, ctypes.byref(st),
+                                                       ctypes.byref(fg), ctypes.byref(nnz),
+                                                       ctypes.byref(fin)), "sps_batch_circuit_status")
+        return {"status": st.value, "failed_gate": fg.value, "nnz": nnz.value,
+                "finished": bool(fin.value)}
+
+    def get_amplitudes(self, index: int, sort: bool = True):
+        n = self.status(index)["nnz"]
+        hi = np.empty(n, np.uint64)
+        lo = np.empty(n, np.uint64)
+        re = np.empty(n, np.float64)
+        im = np.empty(n, np.float64)
+        got = ctypes.c_uint64(0)
+        if n:
+            _check(load_library().sps_batch_get_amplitudes(self._h, index, _ptr(hi), _ptr(lo),
+                                                           _ptr(re), _ptr(im), n,
+                                                           ctypes.byref(got)),
+                   "sps_batch_get_amplitudes")
+        if sort and n:
+            order = np.lexsort((lo, hi))
+            hi, lo, re, im = hi[order], lo[order], re[order], im[order]
+        return hi, lo, re, im
+
+    def config(self) -> BatchConfig:
+        c = BatchConfig()
+        _check(load_library().sps_batch_get_config(self._h, ctypes.byref(c)), "sps_batch_get_config")
+        return c
+
+    def set_config(self, threads: int, blocks_per_sm: int, smem_cap: int) -> None:
+        c = BatchConfig(threads, blocks_per_sm, smem_cap, 0)
+        _check(load_library().sps_batch_set_config(self._h, ctypes.byref(c)), "sps_batch_set_config")
+
+    def tune(self, repeats: int = 1):
+        c = BatchConfig()
+        ms = ctypes.c_float(0)
+        _check(load_library().sps_batch_tune(self._h, repeats, ctypes.byref(c), ctypes.byref(ms)),
+               "sps_batch_tune")
+        return {"threads": c.threads, "blocks_per_sm": c.blocks_per_sm, "smem_cap": c.smem_cap,
+                "ms": ms.value}
+
+    def updates(self) -> int:
+        t = ctypes.c_uint64(0)
+        _check(load_library().sps_batch_updates(self._h, ctypes.byref(t)), "sps_batch_updates")
+        return t.value
+
+    def launches(self) -> int:
+        n = ctypes.c_uint32(0)
+        l = ctypes.c_uint64(0)
+        _check(load_library().sps_batch_counts(self._h, ctypes.byref(n), ctypes.byref(l)),
+               "sps_batch_counts")
+        return l.value

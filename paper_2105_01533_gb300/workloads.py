@@ -361,3 +361,114 @@ def batched_workload(count: int = 4096, first_seed: int = 1, qubits=(20, 100),
         g = random_mix(s, nq, d, keep_branch=CountingBound(cap))
         out.append(BatchCircuit(s, nq, cap, g))
     return out
+
+
+# Batched workload, vectorised ----------------------------------------------------
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix_block(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Values offset+1 .. offset+count of the SplitMix64 stream of `seed`
+    (the generator is counter based: value k mixes seed + k * golden)."""
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & _M64) + k * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def _below(u: np.ndarray, n) -> np.ndarray:
+    """Uniform integers in [0, n) from 64-bit draws (32-bit multiply-shift)."""
+    return (((u >> np.uint64(32)) * np.asarray(n, np.uint64)) >> np.uint64(32)).astype(np.int64)
+
+
+def _set_bits(q: np.ndarray):
+    lo = np.where(q < 64, np.left_shift(np.uint64(1), (q % 64).astype(np.uint64)), np.uint64(0))
+    hi = np.where(q >= 64, np.left_shift(np.uint64(1), (q % 64).astype(np.uint64)), np.uint64(0))
+    return lo.astype(np.uint64), hi.astype(np.uint64)
+
+
+def random_mix_fast(seed: int, nqubits: int, ngates: int, h_budget: int) -> np.ndarray:
+    """Vectorised random mix for the batched workload: H on 8 distinct qubits,
+    then `ngates` gates, each from six draws of the counter-based SplitMix64
+    stream of `seed`: class u0 < 0.7 X/CNOT/Toffoli (1:1:1 by u1 % 3), < 0.9
+    Z/S/T/controlled-Rz (1:1:1:1 by u1 % 4), else an H candidate. Only the
+    first `h_budget` H candidates are kept (so 2^(8 + h_budget) bounds the
+    nonzeros); a later one becomes X/CNOT/Toffoli or Z/S/T/CRz in the ratio
+    7:2 by u1 % 9. Qubits: q0 = u2 below n, q1 = u3 below n-1 skipping q0,
+    q2 = u4 below n-2 skipping both; angle = 2 pi (u5 >> 11) 2^-53."""
+    n = nqubits
+    rng = SplitMix64(seed)
+    first = rng.distinct(n, min(8, n))
+    u = splitmix_block(seed ^ 0x5DEECE66D, 6 * ngates).reshape(ngates, 6)
+    f0 = (u[:, 0] >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    kind = (u[:, 1] % np.uint64(36)).astype(np.int64)
+    cls = np.where(f0 < 0.7, 0, np.where(f0 < 0.9, 1, 2))
+    is_h = cls == 2
+    h_rank = np.cumsum(is_h) - 1
+    rejected = is_h & (h_rank >= h_budget)
+    cls = np.where(rejected, np.where(kind % 9 < 7, 0, 1), cls)
+    q0 = _below(u[:, 2], n)
+    q1 = _below(u[:, 3], n - 1)
+    q1 = q1 + (q1 >= q0)
+    a, b = np.minimum(q0, q1), np.maximum(q0, q1)
+    q2 = _below(u[:, 4], n - 2)
+    q2 = q2 + (q2 >= a)
+    q2 = q2 + (q2 >= b)
+    theta = 2.0 * math.pi * (u[:, 5] >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    g = np.zeros(ngates, dtype=GATE_DTYPE)
+    op = np.zeros(ngates, np.uint8)
+    t0 = np.zeros(ngates, np.int64)
+    clo = np.zeros(ngates, np.uint64)
+    chi = np.zeros(ngates, np.uint64)
+    th = np.zeros(ngates, np.float64)
+    # permutations: X(q0), CX(q0 -> q1), CCX(q0, q1 -> q2)
+    pk = kind % 3
+    perm = cls == 0
+    op[perm] = OP_X
+    t0[perm] = np.where(pk == 0, q0, np.where(pk == 1, q1, q2))[perm]
+    l0, h0 = _set_bits(q0)
+    l1, h1 = _set_bits(q1)
+    m1 = perm & (pk >= 1)
+    clo[m1] |= l0[m1]
+    chi[m1] |= h0[m1]
+    m2 = perm & (pk == 2)
+    clo[m2] |= l1[m2]
+    chi[m2] |= h1[m2]
+    # diagonals: Z, S, T on q0; controlled Rz(theta) q0 -> q1
+    dk = kind % 4
+    diag = cls == 1
+    op[diag] = np.array([OP_Z, OP_S, OP_T, OP_RZ], np.uint8)[dk[diag]]
+    t0[diag] = np.where(dk == 3, q1, q0)[diag]
+    m3 = diag & (dk == 3)
+    clo[m3] |= l0[m3]
+    chi[m3] |= h0[m3]
+    th[m3] = theta[m3]
+    # kept H candidates
+    hk = cls == 2
+    op[hk] = OP_H
+    t0[hk] = q0[hk]
+    g["op"] = op
+    g["t0"] = t0.astype(np.uint16)
+    g["cmask"][:, 0] = clo
+    g["cmask"][:, 1] = chi
+    g["theta"] = th
+    return np.concatenate([to_array([H(q) for q in first]), g])
+
+
+def batched_workload_fast(count: int = 4096, first_seed: int = 1, qubits=(20, 100),
+                          depth=(200, 5000), log2_cap=(8, 16)) -> List[BatchCircuit]:
+    """The batched workload: circuit s (seeds first_seed..) has qubits uniform
+    on [qubits], depth uniform on [depth], nonzero cap 2^u with u uniform on
+    [log2_cap], and the gates of :func:`random_mix_fast` with an H budget of
+    floor(log2 cap) - 8 (so the nonzeros never exceed the cap)."""
+    out = []
+    for s in range(first_seed, first_seed + count):
+        rng = SplitMix64(s * 0x2545F4914F6CDD1D + 7)
+        nq = qubits[0] + rng.below(qubits[1] - qubits[0] + 1)
+        d = depth[0] + rng.below(depth[1] - depth[0] + 1)
+        cap = int(2.0 ** (log2_cap[0] + (log2_cap[1] - log2_cap[0]) * rng.uniform()))
+        budget = max(0, int(math.floor(math.log2(cap))) - 8)
+        out.append(BatchCircuit(s, nq, cap, random_mix_fast(s, nq, d, budget)))
+    return out
