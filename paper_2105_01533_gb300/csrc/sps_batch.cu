@@ -96,9 +96,11 @@ __device__ void run_circuit(BatchDesc* dp, uint32_t max_passes, uint32_t smem_ca
   }
 }
 
-__global__ void k_batch(BatchDesc* desc, const uint32_t* order, uint32_t ncirc, uint32_t* head,
-                        uint32_t* gtabs, uint32_t gtab_slots, uint32_t max_passes,
-                        uint32_t smem_cap) {
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT) k_batch(BatchDesc* desc, const uint32_t* order,
+                                                uint32_t ncirc, uint32_t* head, uint32_t* gtabs,
+                                                uint32_t gtab_slots, uint32_t max_passes,
+                                                uint32_t smem_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t warp_sums[33];
   __shared__ uint32_t s_next;
@@ -149,13 +151,27 @@ int launch_batch(void* stream, int sms, const BatchConfig& cfg, BatchDesc* desc,
                  const uint32_t* order, uint32_t ncirc, uint32_t* head, uint32_t* gtabs,
                  uint32_t gtab_slots, uint32_t max_passes) {
   const size_t smem = batch_smem_bytes(cfg.smem_cap);
-  if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return -1;
   const int blocks = sms * (int)cfg.blocks_per_sm;
-  k_batch<<<blocks, cfg.threads, smem, (cudaStream_t)stream>>>(desc, order, ncirc, head, gtabs,
-                                                                gtab_slots, max_passes,
-                                                                cfg.smem_cap);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cfg.threads <= 256) {
+    if (cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return -1;
+    k_batch<256><<<blocks, cfg.threads, smem, st>>>(desc, order, ncirc, head, gtabs, gtab_slots,
+                                                    max_passes, cfg.smem_cap);
+  } else if (cfg.threads <= 512) {
+    if (cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return -1;
+    k_batch<512><<<blocks, cfg.threads, smem, st>>>(desc, order, ncirc, head, gtabs, gtab_slots,
+                                                    max_passes, cfg.smem_cap);
+  } else {
+    if (cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return -1;
+    k_batch<1024><<<blocks, cfg.threads, smem, st>>>(desc, order, ncirc, head, gtabs, gtab_slots,
+                                                     max_passes, cfg.smem_cap);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -528,10 +544,18 @@ sps_status sps_batch_tune(sps_batch* b, uint32_t repeats, sps_batch_config* best
     sps_status st = ensure_gtabs(b);
     if (st != SPS_OK) break;
     float tsum = 0.0f;
+    bool skip = false;
     for (uint32_t r = 0; r < repeats; ++r) {
       if ((st = sps_batch_reset(b)) != SPS_OK) break;
       cudaEventRecord(e0, b->stream);
-      if ((st = sps_batch_run(b, 0)) != SPS_OK) break;
+      if ((st = sps_batch_run(b, 0)) != SPS_OK) {
+        // a configuration this device cannot launch is skipped, not fatal
+        if (st == SPS_ERR_CUDA && cudaStreamSynchronize(b->stream) == cudaSuccess) {
+          st = SPS_OK;
+          skip = true;
+        }
+        break;
+      }
       cudaEventRecord(e1, b->stream);
       if ((st = cuda_st(cudaEventSynchronize(e1))) != SPS_OK) break;
       float ms = 0.0f;
@@ -544,6 +568,7 @@ sps_status sps_batch_tune(sps_batch* b, uint32_t repeats, sps_batch_config* best
       b->cfg = keep;
       return st;
     }
+    if (skip) continue;
     if (tsum / repeats < best_t) {
       best_t = tsum / repeats;
       win = c;
