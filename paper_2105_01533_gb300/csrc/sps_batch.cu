@@ -71,7 +71,7 @@ __device__ void run_circuit(BatchDesc* dp, uint32_t max_passes, uint32_t smem_ca
                                warp_sums, &upd);
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
       g.lo[i] = A.lo[i];
-      if (KW == 2) g.hi[i] = A.hi[i];
+      g.hi[i] = A.hi[i];   // zero for 64-bit labels: the buffers always hold valid high words
       g.re[i] = A.re[i];
       g.im[i] = A.im[i];
     }
@@ -498,9 +498,21 @@ sps_status sps_batch_get_amplitudes(sps_batch* b, uint32_t index, uint64_t* key_
   const size_t bytes = 8 * d.nnz;
   bool ok = cudaMemcpyAsync(key_lo, d.lo[c], bytes, cudaMemcpyDefault, b->stream) == cudaSuccess &&
             cudaMemcpyAsync(re, d.re[c], bytes, cudaMemcpyDefault, b->stream) == cudaSuccess &&
-            cudaMemcpyAsync(im, d.im[c], bytes, cudaMemcpyDefault, b->stream) == cudaSuccess &&
-            (!key_hi ||
-             cudaMemcpyAsync(key_hi, d.hi[c], bytes, cudaMemcpyDefault, b->stream) == cudaSuccess);
+            cudaMemcpyAsync(im, d.im[c], bytes, cudaMemcpyDefault, b->stream) == cudaSuccess;
+  if (ok && key_hi) {
+    if (d.kw == 2) {
+      ok = cudaMemcpyAsync(key_hi, d.hi[c], bytes, cudaMemcpyDefault, b->stream) == cudaSuccess;
+    } else {
+      cudaPointerAttributes at;
+      const bool dev = cudaPointerGetAttributes(&at, key_hi) == cudaSuccess &&
+                       (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+      cudaGetLastError();
+      if (dev)
+        ok = cudaMemsetAsync(key_hi, 0, bytes, b->stream) == cudaSuccess;
+      else
+        std::memset(key_hi, 0, bytes);
+    }
+  }
   if (!ok) return cuda_st(cudaGetLastError());
   return cuda_st(cudaStreamSynchronize(b->stream));
 }
