@@ -136,6 +136,11 @@ sps_status sps_sync(sps_state* s, size_t* failed_gate);
 /* Synchronises like sps_sync and writes the number of stored nonzeros. */
 sps_status sps_nnz(sps_state* s, uint64_t* nnz);
 
+/* Synchronises like sps_sync and writes the nonzero-amplitude updates done
+ * since creation or the last sps_reset: every applied gate counts the number
+ * of nonzeros before it (passes skipped after an error count nothing). */
+sps_status sps_get_updates(sps_state* s, uint64_t* updates);
+
 /* Synchronises, then copies the state out in unspecified order: entry i is
  * (key_hi[i], key_lo[i], re[i], im[i]). Each pointer is host or device memory
  * of at least `cap` elements; key_hi may be NULL. *nnz_out receives the count;
@@ -298,6 +303,58 @@ sps_status sps_batch_counts(sps_batch* b, uint32_t* ncircuits, uint64_t* launche
 /* After sps_batch_sync: nonzero-amplitude updates done since the last reset,
  * summed over circuits (each applied gate counts the nonzeros before it). */
 sps_status sps_batch_updates(sps_batch* b, uint64_t* total);
+
+/* ---- Serving: continuous batching of requests ---------------------------------
+ * A request is a circuit from |0...0> with a capacity (its projected peak
+ * nonzero count). Requests are admitted in arrival order while an active slot
+ * and enough of the memory budget are free (small requests: 64 B per capacity
+ * entry; large ones, capacity > 65,536: 96 B per entry plus 4 MiB). Each
+ * sps_server_tick admits what fits, advances every active request by at most
+ * passes_per_tick passes (0 = to completion) - small requests together in one
+ * batched launch on the server's stream, large ones each as a whole-GPU state
+ * on its own stream, so their work overlaps on the device - waits for them,
+ * and copies finished requests to host memory, releasing their device memory.
+ * Results equal sps_apply's for the same circuit. */
+typedef struct sps_server sps_server;
+
+typedef struct sps_server_request_info {
+  int state;               /* 0 pending, 1 active, 2 done */
+  sps_status status;       /* SPS_OK or the device-side error of the request */
+  size_t failed_gate;      /* with an error: first gate of the failing pass */
+  uint64_t nnz;            /* when done */
+  uint64_t submit_tick;    /* server tick count at submission, admission and */
+  uint64_t admit_tick;     /* completion (ticks are counted by sps_server_tick) */
+  uint64_t done_tick;
+  int large;               /* 1: ran as a whole-GPU state */
+  uint64_t updates;        /* when done: nonzero-amplitude updates it took */
+} sps_server_request_info;
+
+sps_status sps_server_create(uint64_t mem_budget_bytes, uint32_t max_active,
+                             uint32_t passes_per_tick, void* cuda_stream, sps_server** out);
+void sps_server_destroy(sps_server* s);
+
+/* Queues a request (gates copied and validated; SPS_ERR_ARG with
+ * *failed_gate on a bad record; SPS_ERR_CAPACITY if it could never fit the
+ * budget). *id receives its handle. */
+sps_status sps_server_submit(sps_server* s, uint32_t nqubits, uint64_t capacity,
+                             const sps_gate* gates, size_t ngates, double prune_eps,
+                             uint64_t* id, size_t* failed_gate);
+
+/* One scheduling step (blocking). Counts after the step go to the nullable
+ * outputs: requests active, still pending, and finished in this step. */
+sps_status sps_server_tick(sps_server* s, uint32_t* n_active, uint32_t* n_pending,
+                           uint32_t* n_done);
+
+sps_status sps_server_poll(sps_server* s, uint64_t id, sps_server_request_info* info);
+
+/* Copies a finished request's state (host pointers; key_hi nullable) and
+ * forgets the request. SPS_ERR_CAPACITY with *nnz_out set if cap is too small. */
+sps_status sps_server_result(sps_server* s, uint64_t id, uint64_t* key_hi, uint64_t* key_lo,
+                             double* re, double* im, uint64_t cap, uint64_t* nnz_out);
+
+/* Ticks so far, batched launches enqueued, device bytes charged to requests. */
+sps_status sps_server_stats(sps_server* s, uint64_t* ticks, uint64_t* launches,
+                            uint64_t* bytes_in_use);
 
 /* Allocation-free variant of one branching pass, for callers that must not
  * allocate device memory (a host framework that owns all device memory and

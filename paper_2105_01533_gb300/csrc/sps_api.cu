@@ -748,6 +748,14 @@ sps_status sps_sync(sps_state* s, size_t* failed_gate) {
   return (sps_status)c.status;
 }
 
+sps_status sps_get_updates(sps_state* s, uint64_t* updates) {
+  if (!s || !updates) return SPS_ERR_ARG;
+  const sps_status st = sps_sync(s, nullptr);
+  if (st != SPS_OK) return st;
+  *updates = s->ctl_host->updates;
+  return SPS_OK;
+}
+
 sps_status sps_nnz(sps_state* s, uint64_t* nnz) {
   if (!s || !nnz) return SPS_ERR_ARG;
   const sps_status st = sps_sync(s, nullptr);

@@ -55,8 +55,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
   }
   __syncthreads();
   const RunPass* passes = reinterpret_cast<const RunPass*>(arena + pass_off);
-  const uint32_t done =
-      cta::run_passes<KW>(arena, passes, 0, npasses, A, B, n, cap, tab, kSmallTableSlots, warp_sums);
+  uint64_t upd = 0;
+  const uint32_t done = cta::run_passes<KW>(arena, passes, 0, npasses, A, B, n, cap, tab,
+                                            kSmallTableSlots, warp_sums, &upd);
   if (done < npasses && threadIdx.x == 0)
     fail(ctl, SPS_ERR_CAPACITY, passes[done].pass_serial, passes[done].fail_tag);
   // publish the state (after the last pass that succeeded) to the other buffer
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
     __threadfence();
     ctl->nnz = n;
     ctl->cur = cur ^ 1u;
+    ctl->updates += done < npasses ? upd - n : upd;
     if (plog) {
       plog[0] = n0;
       plog[1] = n;

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
         } else {
           ctl->nnz = total;
           ctl->cur = cur ^ 1u;
+          ctl->updates += n;
           published = true;
         }
       }

@@ -156,7 +156,8 @@ struct Ctl {
   unsigned int fail_pass;        // pass serial of the failing pass
   unsigned int blocks_done;      // last-block detection in the compaction
   unsigned long long fail_gate;  // (apply serial << 32) | first gate of failing pass
-  unsigned long long reserved[3];
+  unsigned long long updates;    // sum over applied gates of the nonzeros before them
+  unsigned long long reserved[2];
 };
 
 struct SoA {

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
     plog[1] = n;
   }
   if (ctl->status != 0u) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->updates += n * a.nops;
   const SoA s = pick(bufs, ctl->cur);
   const double r = 0.70710678118654752440;  // sqrt(0.5)
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
     plog[1] = n;
   }
   if (ctl->status != 0u) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->updates += n * a.nops;
   // stage the op list, the phase tables and the extra-condition list
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.ops);
@@ -485,6 +487,7 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
         } else {
           ctl->nnz = total;
           ctl->cur = cur ^ 1u;
+          ctl->updates += n_in;
           published = true;
         }
       }
@@ -559,6 +562,7 @@ __global__ void k_reset_state(Ctl* ctl, Bufs bufs, int key_words) {
   ctl->nnz = 1ull;
   ctl->cur = 0u;
   ctl->status = 0u;
+  ctl->updates = 0ull;
   ctl->fail_pass = 0u;
   ctl->fail_gate = 0ull;
   ctl->out_count = 0ull;

@@ -37,7 +37,9 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_branch_apply_static", "sps_batch_create", "sps_batch_destroy", "sps_batch_add",
            "sps_batch_run", "sps_batch_sync", "sps_batch_circuit_status",
            "sps_batch_get_amplitudes", "sps_batch_reset", "sps_batch_set_config",
-           "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates")
+           "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates",
+           "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
+           "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats")
 
 
 class SpsError(RuntimeError):
@@ -65,6 +67,13 @@ class KernelRecord(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("smem_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ServerRequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("failed_gate", ctypes.c_size_t),
+                ("nnz", ctypes.c_uint64), ("submit_tick", ctypes.c_uint64),
+                ("admit_tick", ctypes.c_uint64), ("done_tick", ctypes.c_uint64),
+                ("large", ctypes.c_int), ("updates", ctypes.c_uint64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -145,6 +154,22 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_batch_counts.restype = st
     lib.sps_batch_updates.argtypes = [vp, pu64]
     lib.sps_batch_updates.restype = st
+    lib.sps_get_updates.argtypes = [vp, pu64]
+    lib.sps_get_updates.restype = st
+    lib.sps_server_create.argtypes = [u64, u32, u32, vp, ctypes.POINTER(vp)]
+    lib.sps_server_create.restype = st
+    lib.sps_server_destroy.argtypes = [vp]
+    lib.sps_server_destroy.restype = None
+    lib.sps_server_submit.argtypes = [vp, u32, u64, vp, sz, dbl, pu64, psz]
+    lib.sps_server_submit.restype = st
+    lib.sps_server_tick.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    lib.sps_server_tick.restype = st
+    lib.sps_server_poll.argtypes = [vp, u64, ctypes.POINTER(ServerRequestInfo)]
+    lib.sps_server_poll.restype = st
+    lib.sps_server_result.argtypes = [vp, u64, vp, vp, vp, vp, u64, pu64]
+    lib.sps_server_result.restype = st
+    lib.sps_server_stats.argtypes = [vp, pu64, pu64, pu64]
+    lib.sps_server_stats.restype = st
     lib.sps_status_str.argtypes = [st]
     lib.sps_status_str.restype = ctypes.c_char_p
     _lib = lib
@@ -386,6 +411,11 @@ class SparseState:
     def nnz(self) -> int:
         return sps_nnz(self._h)
 
+    def updates(self) -> int:
+        u = ctypes.c_uint64(0)
+        _check(load_library().sps_get_updates(self._h, ctypes.byref(u)), "sps_get_updates")
+        return u.value
+
     def set_option(self, opt: int, value: int) -> None:
         sps_set_option(self._h, opt, value)
 
@@ -525,3 +555,73 @@ class Batch:
         _check(load_library().sps_batch_counts(self._h, ctypes.byref(n), ctypes.byref(l)),
                "sps_batch_counts")
         return l.value
+
+
+# ---- serving --------------------------------------------------------------------
+class Server:
+    """Continuous batching of circuit requests (see include/sps.h)."""
+
+    def __init__(self, mem_budget_bytes: int, max_active: int = 1024, passes_per_tick: int = 8,
+                 stream: Optional[int] = None, torch_memory: bool = True):
+        if torch_memory:
+            use_torch_allocator()
+        if stream is None:
+            stream = current_stream_handle()
+        h = ctypes.c_void_p()
+        _check(load_library().sps_server_create(int(mem_budget_bytes), max_active, passes_per_tick,
+                                                stream, ctypes.byref(h)), "sps_server_create")
+        self._h = h.value
+
+    def close(self) -> None:
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            load_library().sps_server_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, nqubits: int, capacity: int, gates, eps: float = 0.0) -> int:
+        g = gate_array(gates)
+        rid = ctypes.c_uint64(0)
+        bad = ctypes.c_size_t(0)
+        rc = load_library().sps_server_submit(self._h, nqubits, capacity, _ptr(g), g.size,
+                                              float(eps), ctypes.byref(rid), ctypes.byref(bad))
+        _check(rc, "sps_server_submit", bad.value if rc == SPS_ERR_ARG else None)
+        return rid.value
+
+    def tick(self):
+        a, p, d = ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
+        _check(load_library().sps_server_tick(self._h, ctypes.byref(a), ctypes.byref(p),
+                                              ctypes.byref(d)), "sps_server_tick")
+        return a.value, p.value, d.value
+
+    def poll(self, rid: int) -> dict:
+        info = ServerRequestInfo()
+        _check(load_library().sps_server_poll(self._h, rid, ctypes.byref(info)), "sps_server_poll")
+        return {"state": info.state, "status": info.status, "failed_gate": info.failed_gate,
+                "nnz": info.nnz, "submit_tick": info.submit_tick, "admit_tick": info.admit_tick,
+                "done_tick": info.done_tick, "large": bool(info.large), "updates": info.updates}
+
+    def result(self, rid: int, sort: bool = True):
+        n = self.poll(rid)["nnz"]
+        hi = np.empty(n, np.uint64)
+        lo = np.empty(n, np.uint64)
+        re = np.empty(n, np.float64)
+        im = np.empty(n, np.float64)
+        got = ctypes.c_uint64(0)
+        buf = lambda a: _ptr(a) if n else ctypes.c_void_p(1).value  # noqa: E731
+        _check(load_library().sps_server_result(self._h, rid, buf(hi), buf(lo), buf(re), buf(im), n,
+                                                ctypes.byref(got)), "sps_server_result")
+        if sort and n:
+            order = np.lexsort((lo, hi))
+            hi, lo, re, im = hi[order], lo[order], re[order], im[order]
+        return hi, lo, re, im
+
+    def stats(self) -> dict:
+        t, l, b = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(load_library().sps_server_stats(self._h, ctypes.byref(t), ctypes.byref(l),
+                                               ctypes.byref(b)), "sps_server_stats")
+        return {"ticks": t.value, "launches": l.value, "bytes_in_use": b.value}
