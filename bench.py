@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import math
 import json
 import os
 import statistics
@@ -374,6 +375,10 @@ def run_ours(args, dist, rank, world, local_rank):
                            warmup=1)
         if res is not None:
             res["batched"] = bres
+    if args.served and wl["name"].startswith("adder67"):
+        sres = run_served(args, sps, torch, args.serve_count, args.serve_seconds)
+        if res is not None:
+            res["served"] = sres
     st.close()
     return res
 
@@ -476,6 +481,108 @@ def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_ev
             "generate_s": round(gen_s, 1)}
 
 
+# ---- served form ------------------------------------------------------------------------
+def serve_requests(count: int, seed: int = 77):
+    """Request families: random mixes (70%), ripple-carry adders with a
+    log-uniform superposition width (20%), Givens circuits (10%)."""
+    from paper_2105_01533_gb300 import workloads as W
+    rng = W.SplitMix64(seed)
+    out = []
+    randoms = W.batched_workload_fast(count, first_seed=10_000 + seed, depth=(200, 2000),
+                                      log2_cap=(8, 14))
+    for i in range(count):
+        u = rng.uniform()
+        if u < 0.7:
+            c = randoms[i]
+            out.append(("random", c.nqubits, c.cap, c.gates))
+        elif u < 0.9:
+            w = int(round(math.exp(math.log(6) + (math.log(20) - math.log(6)) * rng.uniform())))
+            wl = W.adder_workload(seed=1000 + i, nbits=32, width=w, n_cp=16)
+            out.append(("adder", wl.layout.nqubits, 1 << w, wl.gates))
+        else:
+            n = (32, 48, 64)[rng.below(3)]
+            k = 2 + rng.below(3)
+            layers = 5 + rng.below(26)
+            g = W.givens_workload(seed=2000 + i, nqubits=n, modes=k, layers=layers)
+            out.append(("givens", n, math.comb(n, k), g))
+    return out
+
+
+def run_served(args, sps, torch, count: int, arrive_s: float):
+    """Continuous batching under a Poisson stream: capacity at saturation, then
+    arrivals at 0.8x that rate; latency = completion - scheduled arrival."""
+    import random as _random
+    reqs = serve_requests(count)
+    free, _total = torch.cuda.mem_get_info()
+    budget = int(free * 0.9) - (8 << 30)
+
+    def drive(arrivals):
+        srv = sps.Server(mem_budget_bytes=budget, max_active=2048, passes_per_tick=16)
+        t0 = time.perf_counter()
+        ids, done_at, upd = {}, {}, 0
+        k = 0
+        while k < len(arrivals) or len(done_at) < len(arrivals):
+            now = time.perf_counter() - t0
+            while k < len(arrivals) and arrivals[k] <= now:
+                nm, nq, cap, g = reqs[k % len(reqs)]
+                ids[srv.submit(nq, cap, g, EPS)] = k
+                k += 1
+            if not ids or len(done_at) == len(ids):
+                time.sleep(0.0005)
+                continue
+            _, _, nd = srv.tick()
+            if nd:
+                t = time.perf_counter() - t0
+                for rid, j in ids.items():
+                    if j not in done_at and srv.poll(rid)["state"] == 2:
+                        done_at[j] = t
+                        upd += srv.poll(rid)["updates"]
+        elapsed = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = [done_at[j] - arrivals[j] for j in range(len(arrivals))]
+        return elapsed, upd, lat, st
+
+    # saturation: everything arrives at once
+    sat_n = min(count, 256)
+    el, upd, lat, _ = drive([0.0] * sat_n)
+    cap_rps = sat_n / el
+    sat_rate = upd / el
+    # Poisson arrivals at 0.8x the saturation rate
+    lam = 0.8 * cap_rps
+    rnd = _random.Random(5)
+    t, arr = 0.0, []
+    while t < arrive_s and len(arr) < count:
+        t += rnd.expovariate(lam)
+        arr.append(t)
+    el2, upd2, lat2, st2 = drive(arr)
+    # the plain path, one request at a time, on the saturation set
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pu = 0
+    for (nm, nq, cap, g) in reqs[:sat_n]:
+        s1 = sps.SparseState(nq, cap)
+        s1.apply(g, EPS)
+        pu += s1.updates()
+        s1.close()
+    plain_s = time.perf_counter() - t0
+    fam = {}
+    for r in reqs[:len(arr)]:
+        fam[r[0]] = fam.get(r[0], 0) + 1
+    return {"workload": "served: Poisson stream of random mixes (70%%), adders with log-uniform "
+                        "superposition width 6..20 (20%%), Givens circuits n 32..64, 2..4 modes "
+                        "(10%%); peak nonzeros up to 2^20; FP64, eps 1e-14", "requests": len(arr),
+            "families": fam, "lambda_rps": round(lam, 2), "capacity_rps": round(cap_rps, 2),
+            "saturation_value": round(sat_rate, 1), "value": round(upd2 / el2, 1), "unit": UNIT,
+            "p50_latency_ms": round(1e3 * float(np.percentile(lat2, 50)), 3),
+            "p99_latency_ms": round(1e3 * float(np.percentile(lat2, 99)), 3),
+            "saturation_p99_latency_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+            "ticks": st2["ticks"], "batched_launches": st2["launches"],
+            "plain_value": round(pu / plain_s, 1),
+            "served_vs_plain": round(sat_rate / (pu / plain_s), 2),
+            "memory_budget_gb": round(budget / 2 ** 30, 1)}
+
+
 # ---- the oracle on the host ------------------------------------------------------------
 def oracle_rate(wl, budget_s: float, prefix_cache={}):
     """Run the oracle over the gate stream (gate by gate, single thread) until
@@ -559,6 +666,10 @@ def main():
     ap.add_argument("--batched", type=int, default=1,
                     help="also measure the batched form (1) or not (0)")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--served", type=int, default=1,
+                    help="also measure the served form (1) or not (0)")
+    ap.add_argument("--serve-count", type=int, default=2000)
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--dump-profile", default=None,
                     help="write the per-launch records of one profiled step to this JSON file")
