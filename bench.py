@@ -517,7 +517,7 @@ def run_served(args, sps, torch, count: int, arrive_s: float):
     budget = int(free * 0.9) - (8 << 30)
 
     def drive(arrivals):
-        srv = sps.Server(mem_budget_bytes=budget, max_active=2048, passes_per_tick=16)
+        srv = sps.Server(mem_budget_bytes=budget, max_active=2048, passes_per_tick=32)
         t0 = time.perf_counter()
         ids, done_at, upd = {}, {}, 0
         k = 0
@@ -533,10 +533,9 @@ def run_served(args, sps, torch, count: int, arrive_s: float):
             _, _, nd = srv.tick()
             if nd:
                 t = time.perf_counter() - t0
-                for rid, j in ids.items():
-                    if j not in done_at and srv.poll(rid)["state"] == 2:
-                        done_at[j] = t
-                        upd += srv.poll(rid)["updates"]
+                for rid in srv.completed():
+                    done_at[ids[rid]] = t
+                    upd += srv.poll(rid)["updates"]
         elapsed = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
@@ -569,9 +568,9 @@ def run_served(args, sps, torch, count: int, arrive_s: float):
     fam = {}
     for r in reqs[:len(arr)]:
         fam[r[0]] = fam.get(r[0], 0) + 1
-    return {"workload": "served: Poisson stream of random mixes (70%%), adders with log-uniform "
-                        "superposition width 6..20 (20%%), Givens circuits n 32..64, 2..4 modes "
-                        "(10%%); peak nonzeros up to 2^20; FP64, eps 1e-14", "requests": len(arr),
+    return {"workload": "served: Poisson stream of random mixes (70%), adders with log-uniform "
+                        "superposition width 6..20 (20%), Givens circuits n 32..64, 2..4 modes "
+                        "(10%); peak nonzeros up to 2^20; FP64, eps 1e-14", "requests": len(arr),
             "families": fam, "lambda_rps": round(lam, 2), "capacity_rps": round(cap_rps, 2),
             "saturation_value": round(sat_rate, 1), "value": round(upd2 / el2, 1), "unit": UNIT,
             "p50_latency_ms": round(1e3 * float(np.percentile(lat2, 50)), 3),

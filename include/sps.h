@@ -347,6 +347,10 @@ sps_status sps_server_tick(sps_server* s, uint32_t* n_active, uint32_t* n_pendin
 
 sps_status sps_server_poll(sps_server* s, uint64_t id, sps_server_request_info* info);
 
+/* Ids of the requests that finished in the last tick (up to cap; *n gets
+ * the count, SPS_ERR_CAPACITY if cap was too small). */
+sps_status sps_server_completed(sps_server* s, uint64_t* ids, size_t cap, size_t* n);
+
 /* Copies a finished request's state (host pointers; key_hi nullable) and
  * forgets the request. SPS_ERR_CAPACITY with *nnz_out set if cap is too small. */
 sps_status sps_server_result(sps_server* s, uint64_t id, uint64_t* key_hi, uint64_t* key_lo,

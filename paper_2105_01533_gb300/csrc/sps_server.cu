@@ -74,6 +74,7 @@ struct sps_server {
   std::map<uint64_t, Request> reqs;
   std::deque<uint64_t> pending;
   std::vector<uint64_t> active;
+  std::vector<uint64_t> last_done;   // finished in the last tick
   // small-route device state: descriptors per slot
   BatchDesc* desc = nullptr;
   std::vector<BatchDesc> host_desc;
@@ -356,6 +357,7 @@ sps_status sps_server_tick(sps_server* s, uint32_t* n_active, uint32_t* n_pendin
   // 3. harvest finished requests
   uint32_t done = 0;
   std::vector<uint64_t> still;
+  s->last_done.clear();
   for (uint64_t id : s->active) {
     Request& r = s->reqs[id];
     bool finished = false;
@@ -387,6 +389,7 @@ sps_status sps_server_tick(sps_server* s, uint32_t* n_active, uint32_t* n_pendin
     release_request(s, r);
     r.state = REQ_DONE;
     r.done_tick = s->tick;
+    s->last_done.push_back(r.id);
     ++done;
   }
   s->active.swap(still);
@@ -428,6 +431,13 @@ sps_status sps_server_result(sps_server* s, uint64_t id, uint64_t* key_hi, uint6
   if (key_hi) std::memcpy(key_hi, r.hi.data(), 8 * n);
   s->reqs.erase(it);   // the result is handed over once
   return SPS_OK;
+}
+
+sps_status sps_server_completed(sps_server* s, uint64_t* ids, size_t cap, size_t* n) {
+  if (!s || !n || (cap && !ids)) return SPS_ERR_ARG;
+  *n = s->last_done.size();
+  for (size_t i = 0; i < s->last_done.size() && i < cap; ++i) ids[i] = s->last_done[i];
+  return s->last_done.size() > cap ? SPS_ERR_CAPACITY : SPS_OK;
 }
 
 sps_status sps_server_stats(sps_server* s, uint64_t* ticks, uint64_t* launches, uint64_t* bytes_in_use) {

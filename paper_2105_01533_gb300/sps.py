@@ -39,7 +39,8 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_batch_get_amplitudes", "sps_batch_reset", "sps_batch_set_config",
            "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates",
            "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
-           "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats")
+           "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
+           "sps_server_completed")
 
 
 class SpsError(RuntimeError):
@@ -168,6 +169,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_server_poll.restype = st
     lib.sps_server_result.argtypes = [vp, u64, vp, vp, vp, vp, u64, pu64]
     lib.sps_server_result.restype = st
+    lib.sps_server_completed.argtypes = [vp, pu64, sz, psz]
+    lib.sps_server_completed.restype = st
     lib.sps_server_stats.argtypes = [vp, pu64, pu64, pu64]
     lib.sps_server_stats.restype = st
     lib.sps_status_str.argtypes = [st]
@@ -619,6 +622,14 @@ class Server:
             order = np.lexsort((lo, hi))
             hi, lo, re, im = hi[order], lo[order], re[order], im[order]
         return hi, lo, re, im
+
+    def completed(self, cap: int = 65536):
+        """Ids of the requests that finished in the last tick."""
+        ids = np.zeros(cap, np.uint64)
+        n = ctypes.c_size_t(0)
+        _check(load_library().sps_server_completed(self._h, _ptr(ids), cap, ctypes.byref(n)),
+               "sps_server_completed")
+        return [int(x) for x in ids[:n.value]]
 
     def stats(self) -> dict:
         t, l, b = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
