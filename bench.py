@@ -372,10 +372,10 @@ def run_ours(args, dist, rank, world, local_rank):
             res["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
     if args.batched and wl["name"].startswith("adder67"):
         bres = run_batched(args, sps, torch, args.batch_count, steps=args.batch_steps,
-                           warmup=1)
+                           warmup=1, dist=dist, rank=rank, world=world)
         if res is not None:
             res["batched"] = bres
-    if args.served and wl["name"].startswith("adder67"):
+    if args.served and wl["name"].startswith("adder67") and rank == 0:
         sres = run_served(args, sps, torch, args.serve_count, args.serve_seconds)
         if res is not None:
             res["served"] = sres
@@ -413,13 +413,18 @@ def run_e2e(args, sps, torch, wl, st, flush, U, dist):
 
 
 # ---- batched form -----------------------------------------------------------------------
-def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_every: int = 32):
+def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_every: int = 32,
+                dist=None, rank: int = 0, world: int = 1):
     """4,096 independent circuits (qubits 20..100, depth 200..5000, caps
     2^8..2^16) in one persistent launch per step, against the plain per-circuit
-    path on every `sample_every`-th circuit of the same set."""
+    path on every `sample_every`-th circuit of the same set. With several ranks
+    each runs its longest-processing-time share; only totals are reduced."""
+    from paper_2105_01533_gb300 import shard
     from paper_2105_01533_gb300 import workloads as W
     t0 = time.perf_counter()
     circs = W.batched_workload_fast(count, first_seed=1)
+    if world > 1:
+        circs = shard.my_share(circs, rank, world)
     gen_s = time.perf_counter() - t0
     b = sps.Batch()
     for c in circs:
@@ -443,7 +448,8 @@ def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_ev
     ms = [a.elapsed_time(e) for a, e in ev]
     failed = sum(1 for i in range(len(circs)) if b.status(i)["status"] != 0)
     b.close()
-    batched_rate = upd * steps / (sum(ms) * 1e-3)
+    tot_upd, tot_s = shard.reduce_totals(float(upd) * steps, sum(ms) * 1e-3)
+    batched_rate = tot_upd / tot_s
     # the plain path on a sample of the same circuits, one circuit at a time
     sample = circs[::sample_every]
     sb = sps.Batch()
@@ -471,7 +477,8 @@ def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_ev
                         "mix 70%% X/CNOT/Toffoli, 20%% Z/S/T/CRz, 10%% H within the cap; FP64, "
                         "eps 1e-14" % count,
             "circuits": count, "gates": int(sum(len(c.gates) for c in circs)),
-            "updates_per_step": int(upd), "value": round(batched_rate, 1), "unit": UNIT,
+            "updates_per_step": int(tot_upd / steps), "value": round(batched_rate, 1), "unit": UNIT,
+            "scaling": "weak" if world > 1 else None, "ranks": world,
             "ms_per_step": round(float(np.median(ms)), 3), "steps": steps,
             "launches_per_step": 1, "failed_circuits": failed, "tuned_config": tuned,
             "plain_value": round(plain_rate, 1),
