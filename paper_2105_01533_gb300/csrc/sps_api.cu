@@ -818,14 +818,14 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
   }
   if (launch_set_nnz(s->stream, s->ctl, n) < 0 ||
       cudaMemsetAsync(s->dflag, 0, sizeof(unsigned), s->stream) != cudaSuccess ||
-      launch_check_labels(s->stream, s->kw, s->ctl, chk, lim0, lim1, s->dflag, n) < 0)
+      launch_check_labels(s->stream, s->kw, s->ctl, chk, lim0, lim1, s->dflag, n, 1) < 0)
     return cuda_ok(cudaGetLastError());
   int launched = 2;
   if (s->kw == 1 && key_hi && n) {
     // labels in bufs[1].lo are the high words; every one must be zero
     Bufs hib = s->bufs;
     hib.b[0].lo = s->bufs.b[1].lo;
-    if (launch_check_labels(s->stream, 1, s->ctl, hib, 0ull, 0ull, s->dflag, n) < 0)
+    if (launch_check_labels(s->stream, 1, s->ctl, hib, 0ull, 0ull, s->dflag, n, 0) < 0)
       return cuda_ok(cudaGetLastError());
     ++launched;
   }

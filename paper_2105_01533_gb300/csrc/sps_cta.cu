@@ -62,15 +62,22 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
     fail(ctl, SPS_ERR_CAPACITY, passes[done].pass_serial, passes[done].fail_tag);
   // publish the state (after the last pass that succeeded) to the other buffer
   const SoA out = pick(bufs, cur ^ 1u);
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the labels
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    out.lo[i] = A.lo[i];
-    if (KW == 2) out.hi[i] = A.hi[i];
+    const uint64_t lo = A.lo[i], hi = A.hi[i];
+    out.lo[i] = lo;
+    if (KW == 2) out.hi[i] = hi;
     out.re[i] = A.re[i];
     out.im[i] = A.im[i];
+    mo0 |= lo;
+    mo1 |= hi;
+    ma0 &= lo;
+    ma1 &= hi;
   }
-  __syncthreads();
+  merge_label_masks(ctl, mo0, mo1, ma0, ma1);   // ends with a block barrier
   if (threadIdx.x == 0) {
     __threadfence();
+    publish_label_masks(ctl);
     ctl->nnz = n;
     ctl->cur = cur ^ 1u;
     ctl->updates += done < npasses ? upd - n : upd;

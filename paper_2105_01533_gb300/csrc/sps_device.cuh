@@ -42,6 +42,71 @@ __device__ __forceinline__ void fail(Ctl* ctl, unsigned code, uint32_t pass_seri
   }
 }
 
+// Block-wide OR/AND of per-thread label words, merged into ctl->nor/nand
+// (all threads of the block must call it).
+__device__ __forceinline__ void merge_label_masks(Ctl* ctl, uint64_t or0, uint64_t or1,
+                                                  uint64_t and0, uint64_t and1) {
+  __shared__ unsigned long long sm[4][32];
+  for (int d = 16; d > 0; d >>= 1) {
+    or0 |= __shfl_xor_sync(0xFFFFFFFFu, or0, d);
+    or1 |= __shfl_xor_sync(0xFFFFFFFFu, or1, d);
+    and0 &= __shfl_xor_sync(0xFFFFFFFFu, and0, d);
+    and1 &= __shfl_xor_sync(0xFFFFFFFFu, and1, d);
+  }
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    sm[0][warp] = or0;
+    sm[1][warp] = or1;
+    sm[2][warp] = and0;
+    sm[3][warp] = and1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned nw = blockDim.x >> 5;
+    for (unsigned w = 1; w < nw; ++w) {
+      or0 |= sm[0][w];
+      or1 |= sm[1][w];
+      and0 &= sm[2][w];
+      and1 &= sm[3][w];
+    }
+    if (or0) atomicOr(&ctl->nor[0], or0);
+    if (or1) atomicOr(&ctl->nor[1], or1);
+    if (~and0) atomicAnd(&ctl->nand[0], and0);
+    if (~and1) atomicAnd(&ctl->nand[1], and1);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void reset_next_masks(Ctl* ctl) {
+  ctl->nor[0] = ctl->nor[1] = 0ull;
+  ctl->nand[0] = ctl->nand[1] = ~0ull;
+}
+
+// Publishes the next masks as current and resets them (one thread, after
+// every block has merged).
+__device__ __forceinline__ void publish_label_masks(Ctl* ctl) {
+  ctl->cor[0] = atomicOr(&ctl->nor[0], 0ull);
+  ctl->cor[1] = atomicOr(&ctl->nor[1], 0ull);
+  ctl->cand[0] = atomicAnd(&ctl->nand[0], ~0ull);
+  ctl->cand[1] = atomicAnd(&ctl->nand[1], ~0ull);
+  reset_next_masks(ctl);
+}
+
+// Ends an in-place pass that changed labels: the last block to arrive
+// publishes the merged masks.
+__device__ __forceinline__ void finish_inplace_masks(Ctl* ctl) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&ctl->blocks_done2, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      publish_label_masks(ctl);
+      ctl->blocks_done2 = 0u;
+      __threadfence();
+    }
+  }
+}
+
 // murmur3 64-bit finaliser
 __device__ __forceinline__ uint64_t fmix64(uint64_t z) {
   z ^= z >> 33;

@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
     plog[1] = 0ull;
   }
   if (ctl->status != 0u) return;
+  // Flip bits constant over the state: no entry has a partner, nothing to index.
+  if (flip_bits_constant(*ctl, a.op.m)) return;
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
   const SoA s = pick(bufs, ctl->cur);
   const unsigned long long ep = (unsigned long long)a.epoch << 48;
@@ -124,6 +126,8 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
   const BranchOp& op = a.op;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned nwarps = blockDim.x >> 5;
+  const bool no_partners = flip_bits_constant(*ctl, op.m);
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the written labels
   for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
        base += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t i = base + threadIdx.x;
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
         w0 = keep_amp(re, im, a.eps2, eps_pattern(a.eps));
       } else {
         const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
-        const uint64_t j = find_label<KW>(itab, mask, ep, s, p0, p1);
+        const uint64_t j = no_partners ? ~0ull : find_label<KW>(itab, mask, ep, s, p0, p1);
         if (j == ~0ull || x) {   // else the partner with selector bit 1 writes the pair
           const double pre = j != ~0ull ? s.re[j] : 0.0;
           const double pim = j != ~0ull ? s.im[j] : 0.0;
@@ -155,6 +159,18 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
           w1 = keep_amp(v1r, v1i, a.eps2, eps_pattern(a.eps));
         }
       }
+    }
+    if (w0) {
+      mo0 |= l0;
+      mo1 |= h0;
+      ma0 &= l0;
+      ma1 &= h0;
+    }
+    if (w1) {
+      mo0 |= l1;
+      mo1 |= h1;
+      ma0 &= l1;
+      ma1 &= h1;
     }
     const unsigned b0 = __ballot_sync(FULL, w0), b1 = __ballot_sync(FULL, w1);
     if (lane == 0) warp_cnt[warp] = __popc(b0) + __popc(b1);
@@ -191,6 +207,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
     }
     __syncthreads();
   }
+  merge_label_masks(ctl, mo0, mo1, ma0, ma1);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
@@ -208,6 +225,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
           published = true;
         }
       }
+      if (published) publish_label_masks(ctl); else reset_next_masks(ctl);
       if (plog) {
         plog[0] = n;
         plog[1] = published ? total : n;

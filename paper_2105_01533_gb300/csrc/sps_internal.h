@@ -157,8 +157,21 @@ struct Ctl {
   unsigned int blocks_done;      // last-block detection in the compaction
   unsigned long long fail_gate;  // (apply serial << 32) | first gate of failing pass
   unsigned long long updates;    // sum over applied gates of the nonzeros before them
-  unsigned long long reserved[2];
+  // OR and AND of every stored label (word 0 = qubits 0..63): a qubit whose
+  // OR and AND bits agree has the same value in every label. Kernels that
+  // write labels build the next masks in nor/nand and publish them with the
+  // state; unknown masks are OR = ~0, AND = 0 (no qubit constant).
+  unsigned long long cor[2], cand[2];
+  unsigned long long nor[2], nand[2];
+  unsigned int blocks_done2;     // last-block detection of in-place passes
+  unsigned int reserved;
 };
+
+// No entry can have a partner for a gate whose flip bits are constant over
+// the state (the partner would differ in a constant bit).
+__host__ __device__ inline bool flip_bits_constant(const Ctl& c, const uint64_t m[2]) {
+  return (((c.cor[0] ^ c.cand[0]) & m[0]) | ((c.cor[1] ^ c.cand[1]) & m[1])) == 0ull;
+}
 
 struct SoA {
   uint64_t* lo;
@@ -240,8 +253,10 @@ int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs 
                        double* partials, int nblocks, double* result);
 int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz);
 int launch_reset_state(void* stream, int key_words, Ctl* ctl, Bufs bufs);
-int launch_check_labels(void* stream, int key_words, const Ctl* ctl, Bufs bufs,
-                        uint64_t lim_lo, uint64_t lim_hi, unsigned int* bad_flag, uint64_t n);
+// masks != 0: also publish the OR/AND label masks of the checked labels
+int launch_check_labels(void* stream, int key_words, Ctl* ctl, Bufs bufs,
+                        uint64_t lim_lo, uint64_t lim_hi, unsigned int* bad_flag, uint64_t n,
+                        int masks);
 int launch_reset_status(void* stream, Ctl* ctl);
 
 }  // namespace sps

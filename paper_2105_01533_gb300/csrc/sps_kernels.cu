@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->updates += n * a.nops;
   const SoA s = pick(bufs, ctl->cur);
   const double r = 0.70710678118654752440;  // sqrt(0.5)
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the new labels
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t k0 = s.lo[i];
@@ -84,6 +85,10 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
     if (a.has_perm) {
       s.lo[i] = k0;
       if (KW == 2) s.hi[i] = k1;
+      mo0 |= k0;
+      mo1 |= k1;
+      ma0 &= k0;
+      ma1 &= k1;
     }
     cnt &= 7u;
     if (a.has_phase && (cnt != 0u || any_ph)) {
@@ -109,6 +114,10 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
       s.re[i] = re;
       s.im[i] = im;
     }
+  }
+  if (a.has_perm) {
+    merge_label_masks(ctl, mo0, mo1, ma0, ma1);
+    finish_inplace_masks(ctl);
   }
 }
 
@@ -200,6 +209,7 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
   const uint64_t ntiles = (n + tile_entries - 1) / tile_entries;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint32_t c = lane; c < S; c += 32u) pl[ones_row * S + c] = 0xFFFFFFFFu;
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the new labels
   for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < ntiles;
        tile += nwarps) {
     const uint64_t base = tile * tile_entries;
@@ -270,6 +280,10 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
         if (a.has_perm) {
           s.lo[e] = lo;
           if (KW == 2) s.hi[e] = hi;
+          mo0 |= lo;
+          mo1 |= hi;
+          ma0 &= lo;
+          ma1 &= hi;
         }
         if (a.has_phase && (aux0 | aux1)) {
           double pr = 1.0, pi = 0.0;
@@ -297,6 +311,10 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
       }
     }
     __syncwarp();
+  }
+  if (a.has_perm) {
+    merge_label_masks(ctl, mo0, mo1, ma0, ma1);
+    finish_inplace_masks(ctl);
   }
 }
 
@@ -425,6 +443,7 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
   const SoA out = pick(bufs, cur ^ 1u);
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned nwarps = blockDim.x >> 5;
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the kept labels
   for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < size;
        base += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t i = base + threadIdx.x;
@@ -463,6 +482,10 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
     }
     __syncthreads();
     if (keep) {
+      mo0 |= lo;
+      mo1 |= hi;
+      ma0 &= lo;
+      ma1 &= hi;
       const uint64_t pos = block_base + warp_cnt[warp] + __popc(ballot & ((1u << lane) - 1u));
       if (write_ok && pos < a.capacity) {
         out.lo[pos] = lo;
@@ -473,6 +496,7 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
     }
     __syncthreads();
   }
+  merge_label_masks(ctl, mo0, mo1, ma0, ma1);
   // The last block to finish publishes the pass result.
   if (threadIdx.x == 0) {
     __threadfence();
@@ -491,6 +515,7 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
           published = true;
         }
       }
+      if (published) publish_label_masks(ctl); else reset_next_masks(ctl);
       if (plog) {
         plog[0] = n_in;
         plog[1] = published ? total : n_in;
@@ -551,6 +576,10 @@ __global__ void k_set_nnz(Ctl* ctl, unsigned long long nnz) {
   ctl->status = 0u;
   ctl->out_count = 0ull;
   ctl->blocks_done = 0u;
+  ctl->blocks_done2 = 0u;
+  ctl->cor[0] = ctl->cor[1] = ~0ull;   // labels not inspected: no qubit known constant
+  ctl->cand[0] = ctl->cand[1] = 0ull;
+  reset_next_masks(ctl);
 }
 
 // |0...0>: one entry (label 0, amplitude 1) in buffer 0.
@@ -567,6 +596,10 @@ __global__ void k_reset_state(Ctl* ctl, Bufs bufs, int key_words) {
   ctl->fail_gate = 0ull;
   ctl->out_count = 0ull;
   ctl->blocks_done = 0u;
+  ctl->blocks_done2 = 0u;
+  ctl->cor[0] = ctl->cor[1] = 0ull;    // the single label 0
+  ctl->cand[0] = ctl->cand[1] = 0ull;
+  reset_next_masks(ctl);
 }
 
 __global__ void k_reset_status(Ctl* ctl) {
@@ -575,17 +608,31 @@ __global__ void k_reset_status(Ctl* ctl) {
   ctl->fail_gate = 0ull;
   ctl->out_count = 0ull;
   ctl->blocks_done = 0u;
+  ctl->blocks_done2 = 0u;
+  reset_next_masks(ctl);
 }
 
+// Flags labels outside the register; with `masks` also publishes the OR/AND
+// masks of the uploaded labels.
 template <int KW>
-__global__ void k_check_labels(const Ctl* ctl, Bufs bufs, uint64_t lim0, uint64_t lim1,
-                               unsigned* bad) {
+__global__ void k_check_labels(Ctl* ctl, Bufs bufs, uint64_t lim0, uint64_t lim1, unsigned* bad,
+                               int masks) {
   const uint64_t n = ctl->nnz;
   const SoA s = pick(bufs, ctl->cur);
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k0 = s.lo[i];
     const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
-    if ((s.lo[i] & ~lim0) != 0ull || (k1 & ~lim1) != 0ull) atomicOr(bad, 1u);
+    if ((k0 & ~lim0) != 0ull || (k1 & ~lim1) != 0ull) atomicOr(bad, 1u);
+    mo0 |= k0;
+    mo1 |= k1;
+    ma0 &= k0;
+    ma1 &= k1;
+  }
+  if (masks) {
+    merge_label_masks(ctl, mo0, mo1, ma0, ma1);
+    finish_inplace_masks(ctl);
   }
 }
 
@@ -761,13 +808,15 @@ int launch_reset_status(void* stream, Ctl* ctl) {
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_check_labels(void* stream, int key_words, const Ctl* ctl, Bufs bufs, uint64_t lim_lo,
-                        uint64_t lim_hi, unsigned int* bad_flag, uint64_t n) {
+int launch_check_labels(void* stream, int key_words, Ctl* ctl, Bufs bufs, uint64_t lim_lo,
+                        uint64_t lim_hi, unsigned int* bad_flag, uint64_t n, int masks) {
   const int blocks = grid_for(n, 256, 1024);
   if (key_words == 1)
-    k_check_labels<1><<<blocks, 256, 0, (cudaStream_t)stream>>>(ctl, bufs, lim_lo, lim_hi, bad_flag);
+    k_check_labels<1><<<blocks, 256, 0, (cudaStream_t)stream>>>(ctl, bufs, lim_lo, lim_hi, bad_flag,
+                                                                 masks);
   else
-    k_check_labels<2><<<blocks, 256, 0, (cudaStream_t)stream>>>(ctl, bufs, lim_lo, lim_hi, bad_flag);
+    k_check_labels<2><<<blocks, 256, 0, (cudaStream_t)stream>>>(ctl, bufs, lim_lo, lim_hi, bad_flag,
+                                                                 masks);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
