@@ -52,6 +52,7 @@ struct sps_state {
   unsigned long long* itab = nullptr;  // gather-form index table
   uint32_t itab_log2 = 8;
   uint32_t epoch = 0;
+  MaskRing masks;             // rotation of the device label-mask buffers
   int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
@@ -419,7 +420,7 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
   if (!ok) return fail(SPS_ERR_CUDA);
   LaunchCfg lc = cfg_of(s);
   if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0 ||
-      launch_set_nnz(s->stream, s->ctl, 1) < 0)
+      launch_reset_state(s->stream, s->kw, s->ctl, s->bufs, s->masks.writer()) < 0)
     return fail(SPS_ERR_CUDA);
   s->counters.kernel_launches += 2;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(cuda_ok(cudaGetLastError()));
@@ -430,7 +431,8 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
 
 sps_status sps_reset(sps_state* s) {
   if (!s) return SPS_ERR_ARG;
-  if (launch_reset_state(s->stream, s->kw, s->ctl, s->bufs) < 0) return cuda_ok(cudaGetLastError());
+  if (launch_reset_state(s->stream, s->kw, s->ctl, s->bufs, s->masks.writer()) < 0)
+    return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 1;
   s->nnz_bound = 1;
   return SPS_OK;
@@ -531,7 +533,9 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   //    the records of the small runs, packed into one upload
   std::vector<BsPass> bs(passes.size());
   std::vector<size_t> bs_off(passes.size(), 0);
-  std::vector<size_t> run_off(passes.size(), 0);
+  std::vector<size_t> run_off(passes.size(), 0);   // small run: its RunPass array; direct
+                                                   // fused pass: its op stream
+  std::vector<size_t> ph_off(passes.size(), 0);    // direct fused pass: its phase pairs
   size_t arena_bytes = 0;
   std::vector<unsigned char> blob;   // small-run payloads, appended after the bit-sliced plans
   {
@@ -566,6 +570,11 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
     };
     while (i < passes.size()) {
       if (!seg_end[i]) {
+        const Pass& p = passes[i];
+        if (p.kind == PASS_FUSED && bs[i].ops.empty()) {   // direct fused pass
+          run_off[i] = put(p.words.data(), p.words.size() * sizeof(OpWord));
+          if (!p.phases.empty()) ph_off[i] = put(p.phases.data(), p.phases.size() * sizeof(PhasePair));
+        }
         ++serial;
         ++i;
         continue;
@@ -584,8 +593,9 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         r.eps = prune_eps;
         if (p.kind == PASS_FUSED) {
           r.nops = (uint32_t)p.ops.size();
+          r.nwords = (uint32_t)p.words.size();
           r.flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
-          r.ops_off = (uint32_t)put(p.ops.data(), p.ops.size() * sizeof(FOp));
+          r.ops_off = (uint32_t)put(p.words.data(), p.words.size() * sizeof(OpWord));
           r.ph_off = p.phases.empty() ? 0u : (uint32_t)put(p.phases.data(), p.phases.size() * sizeof(PhasePair));
         } else {
           r.br_off = (uint32_t)put(&p.br, sizeof(BranchOp));
@@ -630,7 +640,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       ProfScope ps(s, 4, s->pass_serial + 1, (uint32_t)(j - pi), 3u);
       const int n = launch_small_run(s->stream, s->kw, s->ctl, s->bufs, s->arena,
                                      (uint32_t)run_off[pi], (uint32_t)(j - pi),
-                                     s->capacity, ps.slot);
+                                     s->capacity, s->masks.writer(), ps.slot);
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
       s->pass_serial += (uint32_t)(j - pi);
@@ -668,9 +678,13 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         bl.has_cnt = b.has_cnt;
         bl.list_len = (uint32_t)b.list.size();
         bl.groups = s->bs_groups;
+        bl.mg = p.has_perm ? s->masks.writer() : 0u;
         n = launch_fused_bs(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
       } else {
-        n = launch_fused(lc, s->kw, s->ctl, s->bufs, p, s->nnz_bound, ps.slot);
+        n = launch_fused(lc, s->kw, s->ctl, s->bufs, p,
+                         reinterpret_cast<const OpWord*>(s->arena + run_off[pi]),
+                         reinterpret_cast<const PhasePair*>(s->arena + ph_off[pi]), s->nnz_bound,
+                         p.has_perm ? s->masks.writer() : 0u, ps.slot);
       }
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
@@ -687,6 +701,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       b.coop = s->coop;
       b.capacity = s->capacity;
       b.fail_tag = tag;
+      b.mg = s->masks.writer();   // the pass writes labels: compaction or gather emit
       const bool scatter = s->branch_form == 1 || s->capacity >= (1ull << 32);
       if (scatter) {
         const sps_status ts = ensure_scatter_table(s);
@@ -816,16 +831,17 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
     if (cudaMemcpyAsync(s->bufs.b[1].lo, key_hi, n * 8, cudaMemcpyDefault, s->stream) != cudaSuccess)
       return cuda_ok(cudaGetLastError());
   }
-  if (launch_set_nnz(s->stream, s->ctl, n) < 0 ||
+  if (launch_set_nnz(s->stream, s->ctl, n, s->masks.writer()) < 0 ||
       cudaMemsetAsync(s->dflag, 0, sizeof(unsigned), s->stream) != cudaSuccess ||
-      launch_check_labels(s->stream, s->kw, s->ctl, chk, lim0, lim1, s->dflag, n, 1) < 0)
+      launch_check_labels(s->stream, s->kw, s->ctl, chk, lim0, lim1, s->dflag, n,
+                          s->masks.writer()) < 0)
     return cuda_ok(cudaGetLastError());
   int launched = 2;
   if (s->kw == 1 && key_hi && n) {
     // labels in bufs[1].lo are the high words; every one must be zero
     Bufs hib = s->bufs;
     hib.b[0].lo = s->bufs.b[1].lo;
-    if (launch_check_labels(s->stream, 1, s->ctl, hib, 0ull, 0ull, s->dflag, n, 0) < 0)
+    if (launch_check_labels(s->stream, 1, s->ctl, hib, 0ull, 0ull, s->dflag, n, kNoMasks) < 0)
       return cuda_ok(cudaGetLastError());
     ++launched;
   }
@@ -842,7 +858,7 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
     ok = cudaMemsetAsync(b.lo, 0, 8, s->stream) == cudaSuccess &&
          (s->kw == 1 || cudaMemsetAsync(b.hi, 0, 8, s->stream) == cudaSuccess) &&
          cudaMemcpyAsync(b.re, &kOne, 8, cudaMemcpyHostToDevice, s->stream) == cudaSuccess &&
-         cudaMemsetAsync(b.im, 0, 8, s->stream) == cudaSuccess && launch_set_nnz(s->stream, s->ctl, 1) >= 0 &&
+         cudaMemsetAsync(b.im, 0, 8, s->stream) == cudaSuccess && launch_set_nnz(s->stream, s->ctl, 1, s->masks.writer()) >= 0 &&
          cudaStreamSynchronize(s->stream) == cudaSuccess;
     s->nnz_bound = 1;
     s->counters.kernel_launches += 1;

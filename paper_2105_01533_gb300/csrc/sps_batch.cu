@@ -207,7 +207,8 @@ void pack_circuit(const std::vector<Pass>& passes, double eps, std::vector<unsig
     if (p.kind == PASS_FUSED) {
       r.nops = (uint32_t)p.ops.size();
       r.flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
-      r.ops_off = (uint32_t)put(p.ops.data(), p.ops.size() * sizeof(FOp));
+      r.nwords = (uint32_t)p.words.size();
+      r.ops_off = (uint32_t)put(p.words.data(), p.words.size() * sizeof(OpWord));
       r.ph_off = p.phases.empty() ? 0u
                                   : (uint32_t)put(p.phases.data(), p.phases.size() * sizeof(PhasePair));
       w += bound * (uint64_t)p.ops.size();

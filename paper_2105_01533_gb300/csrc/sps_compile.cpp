@@ -96,6 +96,7 @@ void lower_perm_diag(const sps_gate& g, Pass* p) {
     default:
       break;
   }
+  set_fop_kind(o);
   p->ops.push_back(o);
 }
 
@@ -178,7 +179,38 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
     }
     lower_perm_diag(g, run);
   }
+  for (Pass& p : *out)
+    if (p.kind == PASS_FUSED) encode_ops(p.ops, &p.words);
   return SPS_OK;
+}
+
+void encode_ops(const std::vector<FOp>& ops, std::vector<OpWord>* words) {
+  words->clear();
+  auto form = [](const FOp& o) {
+    if (o.kind == FOP_FLIP) return OPS_FLIP64;
+    if (o.kind == (FOP_FLIP | FOP_HI)) return OPS_FLIP128;
+    return OPS_GEN;
+  };
+  size_t i = 0;
+  while (i < ops.size()) {
+    const uint32_t f = form(ops[i]);
+    size_t j = i;
+    while (j < ops.size() && form(ops[j]) == f) ++j;
+    words->push_back(OpWord{f, (uint32_t)(j - i), 0u, 0u});
+    for (size_t k = i; k < j; ++k) {
+      const FOp& o = ops[k];
+      if (f == OPS_FLIP64) {
+        words->push_back(OpWord{(uint32_t)o.c[0], (uint32_t)(o.c[0] >> 32), (uint32_t)o.t[0],
+                                (uint32_t)(o.t[0] >> 32)});
+      } else {
+        OpWord w[3];
+        static_assert(sizeof(w) == sizeof(FOp), "FOp is three words");
+        std::memcpy(w, &o, sizeof(FOp));
+        words->insert(words->end(), w, w + (f == OPS_FLIP128 ? 2 : 3));
+      }
+    }
+    i = j;
+  }
 }
 
 // ---- bit-sliced form ------------------------------------------------------------

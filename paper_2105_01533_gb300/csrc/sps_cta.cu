@@ -30,7 +30,7 @@ template <int KW>
 __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs,
                                                              const unsigned char* arena,
                                                              uint32_t pass_off, uint32_t npasses,
-                                                             uint64_t capacity,
+                                                             uint64_t capacity, uint32_t mg,
                                                              unsigned long long* plog) {
   extern __shared__ __align__(16) unsigned char smem[];
   cta::Bufs A = smem_bufs(smem);
@@ -74,10 +74,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
     ma0 &= lo;
     ma1 &= hi;
   }
-  merge_label_masks(ctl, mo0, mo1, ma0, ma1);   // ends with a block barrier
+  merge_label_masks(ctl, mg_wr(mg), mo0, mo1, ma0, ma1);
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    publish_label_masks(ctl);
+    reset_label_masks(ctl, mg_rs(mg));
     ctl->nnz = n;
     ctl->cur = cur ^ 1u;
     ctl->updates += done < npasses ? upd - n : upd;
@@ -91,17 +92,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
 }  // namespace
 
 int launch_small_run(void* stream, int key_words, Ctl* ctl, Bufs bufs, const unsigned char* arena,
-                     uint32_t pass_off, uint32_t npasses, uint64_t capacity,
+                     uint32_t pass_off, uint32_t npasses, uint64_t capacity, uint32_t mg,
                      unsigned long long* plog) {
   const size_t smem = 64 * kSmallCap + 4 * (kSmallTableSlots + 33);
   if (key_words == 1) {
     cudaFuncSetAttribute(k_small_run<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_small_run<1><<<1, kSmallThreads, smem, (cudaStream_t)stream>>>(ctl, bufs, arena, pass_off,
-                                                                      npasses, capacity, plog);
+                                                                      npasses, capacity, mg, plog);
   } else {
     cudaFuncSetAttribute(k_small_run<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_small_run<2><<<1, kSmallThreads, smem, (cudaStream_t)stream>>>(ctl, bufs, arena, pass_off,
-                                                                      npasses, capacity, plog);
+                                                                      npasses, capacity, mg, plog);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

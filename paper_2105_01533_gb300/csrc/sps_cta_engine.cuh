@@ -73,33 +73,14 @@ __device__ __forceinline__ uint32_t lookup(const uint32_t* tab, uint32_t mask, c
 
 template <int KW>
 __device__ void fused_pass(const unsigned char* arena, const RunPass& rp, const Bufs& A, uint32_t n) {
-  const FOp* ops = reinterpret_cast<const FOp*>(arena + rp.ops_off);
+  const uint4* ops = reinterpret_cast<const uint4*>(arena + rp.ops_off);
   const PhasePair* ph = reinterpret_cast<const PhasePair*>(arena + rp.ph_off);
-  const double r = 0.70710678118654752440;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
     uint64_t k0 = A.lo[i], k1 = A.hi[i];
     uint32_t cnt = 0;
     bool any = false;
     double acc_re = 1.0, acc_im = 0.0;
-    for (uint32_t j = 0; j < rp.nops; ++j) {
-      const FOp o = ops[j];
-      bool cond = (k0 & o.c[0]) == o.c[0];
-      if (KW == 2) cond = cond && ((k1 & o.c[1]) == o.c[1]);
-      const bool sel = o.sbit != NO_SEL && label_bit(k0, k1, o.sbit);
-      cnt += cond ? (sel ? o.a1 : o.a0) : 0u;
-      if (o.ph != NO_PH && cond) {
-        const PhasePair pp = ph[o.ph];
-        const double pr = sel ? pp.re1 : pp.re0, pim = sel ? pp.im1 : pp.im0;
-        const double nr = acc_re * pr - acc_im * pim;
-        const double ni = acc_re * pim + acc_im * pr;
-        acc_re = nr;
-        acc_im = ni;
-        any = true;
-      }
-      const uint64_t m = cond ? ~0ull : 0ull;
-      k0 ^= o.t[0] & m;
-      if (KW == 2) k1 ^= o.t[1] & m;
-    }
+    walk_ops<KW>(ops, rp.nwords, ph, k0, k1, cnt, any, acc_re, acc_im);
     A.lo[i] = k0;
     A.hi[i] = k1;
     cnt &= 7u;
@@ -111,18 +92,7 @@ __device__ void fused_pass(const unsigned char* arena, const RunPass& rp, const 
         re = nr;
         im = ni;
       }
-      if (cnt & 1u) {
-        const double nr = r * (re - im);
-        const double ni = r * (re + im);
-        re = nr;
-        im = ni;
-      }
-      switch (cnt >> 1) {
-        case 1: { const double t = re; re = -im; im = t; break; }
-        case 2: re = -re; im = -im; break;
-        case 3: { const double t = re; re = im; im = -t; break; }
-        default: break;
-      }
+      apply_pi4(cnt, re, im);
       A.re[i] = re;
       A.im[i] = im;
     }

@@ -42,68 +42,213 @@ __device__ __forceinline__ void fail(Ctl* ctl, unsigned code, uint32_t pass_seri
   }
 }
 
-// Block-wide OR/AND of per-thread label words, merged into ctl->nor/nand
-// (all threads of the block must call it).
-__device__ __forceinline__ void merge_label_masks(Ctl* ctl, uint64_t or0, uint64_t or1,
+// ---- label masks (OR and AND of the stored labels, Ctl::lm) -------------------
+struct LabelMasks { uint64_t or0, or1, and0, and1; };
+
+// The masks in buffer b, reduced over its stripes; every lane of the calling
+// warp (which must be converged) gets them.
+__device__ __forceinline__ LabelMasks read_label_masks(const Ctl* ctl, uint32_t b) {
+  static_assert(kMaskStripes == 32, "one stripe per lane");
+  const unsigned long long* p = ctl->lm[b][threadIdx.x & 31u];
+  LabelMasks m{__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3)};
+  for (int d = 16; d > 0; d >>= 1) {
+    m.or0 |= __shfl_xor_sync(0xFFFFFFFFu, m.or0, d);
+    m.or1 |= __shfl_xor_sync(0xFFFFFFFFu, m.or1, d);
+    m.and0 &= __shfl_xor_sync(0xFFFFFFFFu, m.and0, d);
+    m.and1 &= __shfl_xor_sync(0xFFFFFFFFu, m.and1, d);
+  }
+  return m;
+}
+
+// No entry can have a partner for a gate whose flip bits are constant over
+// the state (the partner would differ in a constant bit).
+__device__ __forceinline__ bool flip_bits_constant(const LabelMasks& m, const uint64_t f[2]) {
+  return (((m.or0 ^ m.and0) & f[0]) | ((m.or1 ^ m.and1) & f[1])) == 0ull;
+}
+
+// Warp-wide OR/AND of per-lane label words, merged into one stripe of buffer
+// b with atomics whose results are not waited for. The calling warp must be
+// converged; lanes without labels pass (0, 0, ~0, ~0).
+__device__ __forceinline__ void merge_label_masks(Ctl* ctl, uint32_t b, uint64_t or0, uint64_t or1,
                                                   uint64_t and0, uint64_t and1) {
-  __shared__ unsigned long long sm[4][32];
   for (int d = 16; d > 0; d >>= 1) {
     or0 |= __shfl_xor_sync(0xFFFFFFFFu, or0, d);
     or1 |= __shfl_xor_sync(0xFFFFFFFFu, or1, d);
     and0 &= __shfl_xor_sync(0xFFFFFFFFu, and0, d);
     and1 &= __shfl_xor_sync(0xFFFFFFFFu, and1, d);
   }
-  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    sm[0][warp] = or0;
-    sm[1][warp] = or1;
-    sm[2][warp] = and0;
-    sm[3][warp] = and1;
+  if ((threadIdx.x & 31u) == 0) {
+    const unsigned stripe = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kMaskStripes;
+    unsigned long long* p = ctl->lm[b][stripe];
+    if (or0) atomicOr(p, or0);
+    if (or1) atomicOr(p + 1, or1);
+    if (~and0) atomicAnd(p + 2, and0);
+    if (~and1) atomicAnd(p + 3, and1);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned nw = blockDim.x >> 5;
-    for (unsigned w = 1; w < nw; ++w) {
-      or0 |= sm[0][w];
-      or1 |= sm[1][w];
-      and0 &= sm[2][w];
-      and1 &= sm[3][w];
-    }
-    if (or0) atomicOr(&ctl->nor[0], or0);
-    if (or1) atomicOr(&ctl->nor[1], or1);
-    if (~and0) atomicAnd(&ctl->nand[0], and0);
-    if (~and1) atomicAnd(&ctl->nand[1], and1);
+}
+
+// Sets buffer b to the given masks (one thread).
+__device__ __forceinline__ void set_label_masks(Ctl* ctl, uint32_t b, uint64_t or0, uint64_t or1,
+                                                uint64_t and0, uint64_t and1) {
+  for (int i = 0; i < kMaskStripes; ++i) {
+    unsigned long long* p = ctl->lm[b][i];
+    p[0] = i == 0 ? or0 : 0ull;
+    p[1] = i == 0 ? or1 : 0ull;
+    p[2] = i == 0 ? and0 : ~0ull;
+    p[3] = i == 0 ? and1 : ~0ull;
   }
-  __syncthreads();
 }
 
-__device__ __forceinline__ void reset_next_masks(Ctl* ctl) {
-  ctl->nor[0] = ctl->nor[1] = 0ull;
-  ctl->nand[0] = ctl->nand[1] = ~0ull;
+// Empties buffer b for the next merge (one thread).
+__device__ __forceinline__ void reset_label_masks(Ctl* ctl, uint32_t b) {
+  set_label_masks(ctl, b, 0ull, 0ull, ~0ull, ~0ull);
 }
 
-// Publishes the next masks as current and resets them (one thread, after
-// every block has merged).
-__device__ __forceinline__ void publish_label_masks(Ctl* ctl) {
-  ctl->cor[0] = atomicOr(&ctl->nor[0], 0ull);
-  ctl->cor[1] = atomicOr(&ctl->nor[1], 0ull);
-  ctl->cand[0] = atomicAnd(&ctl->nand[0], ~0ull);
-  ctl->cand[1] = atomicAnd(&ctl->nand[1], ~0ull);
-  reset_next_masks(ctl);
+// Masks that claim nothing: no qubit known constant (one thread).
+__device__ __forceinline__ void unknown_label_masks(Ctl* ctl, uint32_t b) {
+  set_label_masks(ctl, b, ~0ull, ~0ull, 0ull, 0ull);
 }
 
-// Ends an in-place pass that changed labels: the last block to arrive
-// publishes the merged masks.
-__device__ __forceinline__ void finish_inplace_masks(Ctl* ctl) {
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned done = atomicAdd(&ctl->blocks_done2, 1u);
-    if (done == gridDim.x - 1) {
-      __threadfence();
-      publish_label_masks(ctl);
-      ctl->blocks_done2 = 0u;
-      __threadfence();
+// Runs a fused pass's encoded op stream (OPS_* runs of 16-byte words, in
+// shared or global memory; every thread reads the same word, a broadcast) on
+// E labels at once: flips each label in place, adds the pi/4 steps to cnt and
+// multiplies the arbitrary phases into acc. A label is handled as four 32-bit
+// words, so a condition test or a flip is one three-input logic instruction
+// per word; the E labels are independent chains, which the scheduler
+// interleaves (the walk of one label is a chain of dependent instructions).
+template <int KW, int E>
+__device__ __forceinline__ void walk_ops_n(const uint4* __restrict__ sq, uint32_t nwords,
+                                           const PhasePair* __restrict__ ph, uint64_t (&k0)[E],
+                                           uint64_t (&k1)[E], uint32_t (&cnt)[E],
+                                           bool (&any_ph)[E], double (&acc_re)[E],
+                                           double (&acc_im)[E]) {
+  uint32_t w0[E], w1[E], w2[E], w3[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    w0[e] = (uint32_t)k0[e];
+    w1[e] = (uint32_t)(k0[e] >> 32);
+    w2[e] = (uint32_t)k1[e];
+    w3[e] = (uint32_t)(k1[e] >> 32);
+  }
+  uint32_t pos = 0;
+  while (pos < nwords) {
+    const uint4 h = sq[pos++];
+    const uint32_t count = h.y;
+    if (h.x == OPS_FLIP64) {
+      const uint4* q = sq + pos;
+#pragma unroll 8
+      for (uint32_t j = 0; j < count; ++j) {
+        const uint4 o = q[j];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t miss = ((w0[e] & o.x) ^ o.x) | ((w1[e] & o.y) ^ o.y);
+          const uint32_t m = miss == 0u ? ~0u : 0u;
+          w0[e] ^= o.z & m;
+          w1[e] ^= o.w & m;
+        }
+      }
+      pos += count;
+    } else if (h.x == OPS_FLIP128) {
+      const uint4* q = sq + pos;
+#pragma unroll 4
+      for (uint32_t j = 0; j < count; ++j) {
+        const uint4 c = q[2 * j], t = q[2 * j + 1];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          uint32_t miss = ((w0[e] & c.x) ^ c.x) | ((w1[e] & c.y) ^ c.y);
+          if (KW == 2) miss |= ((w2[e] & c.z) ^ c.z) | ((w3[e] & c.w) ^ c.w);
+          const uint32_t m = miss == 0u ? ~0u : 0u;
+          w0[e] ^= t.x & m;
+          w1[e] ^= t.y & m;
+          if (KW == 2) {
+            w2[e] ^= t.z & m;
+            w3[e] ^= t.w & m;
+          }
+        }
+      }
+      pos += 2 * count;
+    } else {
+      const uint4* q = sq + pos;
+#pragma unroll 2
+      for (uint32_t j = 0; j < count; ++j) {
+        const uint4 c = q[3 * j], t = q[3 * j + 1];
+        const uint2 meta = *reinterpret_cast<const uint2*>(q + 3 * j + 2);
+        const uint32_t kind = meta.x >> 24;   // a0 | a1 << 8 | sbit << 16 | kind << 24
+        const uint32_t b = (meta.x >> 16) & 0xFFu;
+        const PhasePair* pp = ph + (meta.y & 0xFFFFu);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          uint32_t miss = ((w0[e] & c.x) ^ c.x) | ((w1[e] & c.y) ^ c.y);
+          if (KW == 2) miss |= ((w2[e] & c.z) ^ c.z) | ((w3[e] & c.w) ^ c.w);
+          const bool cond = miss == 0u;
+          bool sel = false;
+          if (kind & FOP_SEL) {
+            const uint32_t word = b < 32 ? w0[e] : b < 64 ? w1[e] : b < 96 ? w2[e] : w3[e];
+            sel = (word >> (b & 31u)) & 1u;
+          }
+          cnt[e] += cond ? (sel ? (meta.x >> 8) & 0xFFu : meta.x & 0xFFu) : 0u;
+          if ((kind & FOP_PH) && cond) {
+            const double pr = sel ? pp->re1 : pp->re0;
+            const double pi = sel ? pp->im1 : pp->im0;
+            const double nr = acc_re[e] * pr - acc_im[e] * pi;
+            const double ni = acc_re[e] * pi + acc_im[e] * pr;
+            acc_re[e] = nr;
+            acc_im[e] = ni;
+            any_ph[e] = true;
+          }
+          const uint32_t m = cond ? ~0u : 0u;
+          w0[e] ^= t.x & m;
+          w1[e] ^= t.y & m;
+          if (KW == 2) {
+            w2[e] ^= t.z & m;
+            w3[e] ^= t.w & m;
+          }
+        }
+      }
+      pos += 3 * count;
     }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    k0[e] = ((uint64_t)w1[e] << 32) | w0[e];
+    k1[e] = ((uint64_t)w3[e] << 32) | w2[e];
+  }
+}
+
+// One label at a time (the one-block engine).
+template <int KW>
+__device__ __forceinline__ void walk_ops(const uint4* __restrict__ sq, uint32_t nwords,
+                                         const PhasePair* __restrict__ ph, uint64_t& k0,
+                                         uint64_t& k1, uint32_t& cnt, bool& any_ph,
+                                         double& acc_re, double& acc_im) {
+  uint64_t a0[1] = {k0}, a1[1] = {k1};
+  uint32_t c[1] = {cnt};
+  bool an[1] = {any_ph};
+  double ar[1] = {acc_re}, ai[1] = {acc_im};
+  walk_ops_n<KW, 1>(sq, nwords, ph, a0, a1, c, an, ar, ai);
+  k0 = a0[0];
+  k1 = a1[0];
+  cnt = c[0];
+  any_ph = an[0];
+  acc_re = ar[0];
+  acc_im = ai[0];
+}
+
+// Multiplies an amplitude by e^{i pi cnt / 4} (cnt mod 8), exactly for the
+// quarter turns; the odd steps cost one rounding of each part.
+__device__ __forceinline__ void apply_pi4(uint32_t cnt, double& re, double& im) {
+  if (cnt & 1u) {  // times e^{i pi/4} = sqrt(0.5) (1 + i)
+    const double r = 0.70710678118654752440;  // sqrt(0.5)
+    const double nr = r * (re - im);
+    const double ni = r * (re + im);
+    re = nr;
+    im = ni;
+  }
+  switch ((cnt >> 1) & 3u) {  // times i^(cnt/2)
+    case 1: { const double t = re; re = -im; im = t; break; }
+    case 2: re = -re; im = -im; break;
+    case 3: { const double t = re; re = im; im = -t; break; }
+    default: break;
   }
 }
 

@@ -38,6 +38,7 @@ struct GatherArgs {
   uint64_t capacity;
   uint64_t fail_tag;
   uint32_t load_pct, max_log2, pass_serial, epoch;
+  uint32_t mg;   // label-mask buffers (MaskRing): build reads rd; emit reads rd, writes wr
 };
 
 // The table holds n_in labels at the load factor: size for n_in, not 2 n_in.
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
   }
   if (ctl->status != 0u) return;
   // Flip bits constant over the state: no entry has a partner, nothing to index.
-  if (flip_bits_constant(*ctl, a.op.m)) return;
+  if (flip_bits_constant(read_label_masks(ctl, mg_rd(a.mg)), a.op.m)) return;
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
   const SoA s = pick(bufs, ctl->cur);
   const unsigned long long ep = (unsigned long long)a.epoch << 48;
@@ -126,7 +127,8 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
   const BranchOp& op = a.op;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned nwarps = blockDim.x >> 5;
-  const bool no_partners = flip_bits_constant(*ctl, op.m);
+  const bool no_partners = flip_bits_constant(read_label_masks(ctl, mg_rd(a.mg)), op.m);
+  if (blockIdx.x == 0 && threadIdx.x == 0) reset_label_masks(ctl, mg_rs(a.mg));
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the written labels
   for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
        base += (uint64_t)gridDim.x * blockDim.x) {
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
     }
     __syncthreads();
   }
-  merge_label_masks(ctl, mo0, mo1, ma0, ma1);
+  merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
@@ -225,7 +227,6 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
           published = true;
         }
       }
-      if (published) publish_label_masks(ctl); else reset_next_masks(ctl);
       if (plog) {
         plog[0] = n;
         plog[1] = published ? total : n;
@@ -271,6 +272,7 @@ int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   a.max_log2 = b.max_log2;
   a.pass_serial = b.pass_serial;
   a.epoch = epoch;
+  a.mg = b.mg;
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {

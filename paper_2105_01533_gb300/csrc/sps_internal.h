@@ -34,12 +34,26 @@ struct FOp {            // 48 bytes
   uint64_t t[2];        // xor mask applied when the condition holds
   uint8_t a0, a1;       // pi/4 steps added when sel = 0 / 1 (mod 8)
   uint8_t sbit;         // selector qubit or NO_SEL
-  uint8_t reserved;
+  uint8_t kind;         // FOP_* flags, derived from the fields (set_fop_kind)
   uint16_t ph;          // index into the pass's phase pairs or NO_PH
   uint16_t reserved2;
   uint64_t reserved3;
 };
 static_assert(sizeof(FOp) == 48, "FOp layout");
+
+// FOp::kind flags: which parts of the op do anything, so the per-entry walk
+// skips the rest (the flags are uniform over a warp: every thread walks the
+// same list).
+constexpr uint8_t FOP_FLIP = 1;   // t != 0
+constexpr uint8_t FOP_CNT = 2;    // a0 or a1 != 0
+constexpr uint8_t FOP_PH = 4;     // ph != NO_PH
+constexpr uint8_t FOP_SEL = 8;    // sbit != NO_SEL
+constexpr uint8_t FOP_HI = 16;    // c or t touch qubits 64..127
+inline void set_fop_kind(FOp& o) {
+  o.kind = (uint8_t)(((o.t[0] | o.t[1]) ? FOP_FLIP : 0) | ((o.a0 | o.a1) ? FOP_CNT : 0) |
+                     (o.ph != NO_PH ? FOP_PH : 0) | (o.sbit != NO_SEL ? FOP_SEL : 0) |
+                     ((o.c[1] | o.t[1] | (o.sbit != NO_SEL && o.sbit >= 64)) ? FOP_HI : 0));
+}
 
 struct PhasePair { double re0, im0, re1, im1; };   // phase for sel = 0, sel = 1
 
@@ -98,6 +112,20 @@ struct BsPass {
   uint32_t nchunks() const { return (aux_bits + 7) / 8; }
 };
 
+// ---- encoded op stream of a fused pass ------------------------------------------
+// The direct and one-block fused passes walk the op list as a stream of 16-byte
+// words. A header word {OPS_*, count, 0, 0} starts each run of ops of one form:
+//   OPS_FLIP64   count words {c.lo, c.hi, t.lo, t.hi} (32-bit halves): a pure
+//                flip whose condition and target lie in qubits 0..63;
+//   OPS_FLIP128  count x 2 words: the 128-bit condition, then the target;
+//   OPS_GEN      count x 3 words: FOp records (phases, counters, selectors).
+// A flip costs the walk one load and five logic instructions, a general op
+// about four times that.
+struct OpWord { uint32_t x, y, z, w; };
+static_assert(sizeof(OpWord) == 16, "OpWord layout");
+constexpr uint32_t OPS_FLIP64 = 1, OPS_FLIP128 = 2, OPS_GEN = 3;
+void encode_ops(const std::vector<FOp>& ops, std::vector<OpWord>* words);
+
 // ---- a compiled pass -----------------------------------------------------------
 enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2 };
 
@@ -106,6 +134,7 @@ struct Pass {
   uint64_t first_gate;
   // fused
   std::vector<FOp> ops;
+  std::vector<OpWord> words;  // ops encoded for the direct walk (encode_ops)
   std::vector<PhasePair> phases;
   bool has_perm = false;    // some op flips label bits
   bool has_phase = false;   // some op changes amplitudes
@@ -118,12 +147,12 @@ struct Pass {
 struct RunPass {            // 64 bytes
   uint32_t kind;            // PASS_FUSED or PASS_BRANCH
   uint32_t nops;            // fused: ops
-  uint32_t ops_off;         // byte offset of the FOp array in the arena
+  uint32_t ops_off;         // byte offset of the encoded op stream in the arena
   uint32_t ph_off;          // byte offset of the PhasePair array
   uint32_t br_off;          // byte offset of the BranchOp
   uint32_t flags;           // bit 0: permutes, bit 1: changes amplitudes
   uint32_t pass_serial;
-  uint32_t reserved;
+  uint32_t nwords;          // fused: words of the encoded op stream
   uint64_t fail_tag;
   double eps2;
   double eps;
@@ -138,7 +167,8 @@ constexpr uint32_t kSmallTableSlots = 8192;   // input index table, load <= 25%
 // Builds the bit-sliced form of a fused pass for an nqubits-qubit state.
 void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out);
 
-// Op lists travel as kernel parameters (<= 32 KB), which bounds one fused pass.
+// Bounds of one fused pass: ops, arbitrary phases (each a table entry of the
+// bit-sliced form) and, below, its fire slots.
 constexpr uint32_t kMaxFusedOps = 512;
 constexpr uint32_t kMaxFusedPhases = 96;
 constexpr uint32_t kDefaultMaxFusedOps = kMaxFusedOps;
@@ -148,6 +178,7 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                    uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad);
 
 // ---- device-side control block -------------------------------------------------
+constexpr int kMaskStripes = 32;
 struct Ctl {
   unsigned long long nnz;        // entries in the current buffer
   unsigned long long out_count;  // compaction output counter of the running pass
@@ -157,21 +188,29 @@ struct Ctl {
   unsigned int blocks_done;      // last-block detection in the compaction
   unsigned long long fail_gate;  // (apply serial << 32) | first gate of failing pass
   unsigned long long updates;    // sum over applied gates of the nonzeros before them
-  // OR and AND of every stored label (word 0 = qubits 0..63): a qubit whose
-  // OR and AND bits agree has the same value in every label. Kernels that
-  // write labels build the next masks in nor/nand and publish them with the
-  // state; unknown masks are OR = ~0, AND = 0 (no qubit constant).
-  unsigned long long cor[2], cand[2];
-  unsigned long long nor[2], nand[2];
-  unsigned int blocks_done2;     // last-block detection of in-place passes
-  unsigned int reserved;
+  // OR and AND of every stored label (qubits 0..63 in word 0): a qubit whose
+  // OR and AND bits agree has the same value in every label. Three rotating
+  // buffers: a pass that writes labels reads the masks of its input from
+  // buffer rd, merges those of its output into buffer wr (fire-and-forget
+  // atomics spread over kMaskStripes stripes, so blocks do not queue on one
+  // address) and resets buffer rs for the pass after it; kernel boundaries
+  // order the three. The host advances the rotation (MaskRing).
+  unsigned long long lm[3][kMaskStripes][4];   // {or0, or1, and0, and1}
 };
 
-// No entry can have a partner for a gate whose flip bits are constant over
-// the state (the partner would differ in a constant bit).
-__host__ __device__ inline bool flip_bits_constant(const Ctl& c, const uint64_t m[2]) {
-  return (((c.cor[0] ^ c.cand[0]) & m[0]) | ((c.cor[1] ^ c.cand[1]) & m[1])) == 0ull;
-}
+// Mask buffer indices of one label-writing launch, packed rd | wr << 8 | rs << 16.
+struct MaskRing {
+  uint32_t gen = 0;
+  uint32_t reader() const { return gen % 3u; }
+  uint32_t writer() {
+    const uint32_t v = (gen % 3u) | (((gen + 1u) % 3u) << 8) | (((gen + 2u) % 3u) << 16);
+    ++gen;
+    return v;
+  }
+};
+__host__ __device__ constexpr uint32_t mg_rd(uint32_t mg) { return mg & 0xFFu; }
+__host__ __device__ constexpr uint32_t mg_wr(uint32_t mg) { return (mg >> 8) & 0xFFu; }
+__host__ __device__ constexpr uint32_t mg_rs(uint32_t mg) { return (mg >> 16) & 0xFFu; }
 
 struct SoA {
   uint64_t* lo;
@@ -210,14 +249,17 @@ struct LaunchCfg {
 // `plog` (nullable) receives two words per launch for profiling: entries read
 // and entries in the state afterwards.
 int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots);
+// words / ph: the pass's encoded op stream and phase pairs in device memory
 int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
-                 uint64_t nnz_bound, unsigned long long* plog);
+                 const OpWord* words, const PhasePair* ph, uint64_t nnz_bound, uint32_t mg,
+                 unsigned long long* plog);
 struct BranchLaunch {
   BranchOp op;
   double eps;
   uint32_t load_pct, max_log2, probe_limit, pass_serial;
   int coop;
   uint64_t capacity, fail_tag;
+  uint32_t mg;   // label-mask buffers (MaskRing): rd for the gather passes, all for the writer
 };
 int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,
                        const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog);
@@ -230,13 +272,14 @@ struct BsLaunch {
   uint32_t nops, nw, na, nchunks;
   uint32_t has_perm, has_phase, has_cnt, list_len;
   uint32_t groups;          // groups of 32 entries per warp tile (even, 2..32), 0 = choose
+  uint32_t mg;              // label-mask buffers (MaskRing)
 };
 int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
                     uint64_t nnz_bound, unsigned long long* plog);
 // Runs npasses consecutive passes (RunPass records at arena + pass_off) in one
 // CTA with the state in shared memory; the host guarantees nnz <= kSmallCap.
 int launch_small_run(void* stream, int key_words, Ctl* ctl, Bufs bufs, const unsigned char* arena,
-                     uint32_t pass_off, uint32_t npasses, uint64_t capacity,
+                     uint32_t pass_off, uint32_t npasses, uint64_t capacity, uint32_t mg,
                      unsigned long long* plog);
 // Gather form of a branching pass (insert-once rule, Sec. 3.1) on the whole GPU:
 // k_gather_build claims one slot per input label in an index table whose
@@ -251,12 +294,14 @@ int launch_itab_clear(const LaunchCfg& lc, unsigned long long* itab, uint64_t ns
 int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
                        double* partials, int nblocks, double* result);
-int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz);
-int launch_reset_state(void* stream, int key_words, Ctl* ctl, Bufs bufs);
-// masks != 0: also publish the OR/AND label masks of the checked labels
+// mg: label-mask buffers of a launch that writes labels (MaskRing::writer)
+int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz, uint32_t mg);
+int launch_reset_state(void* stream, int key_words, Ctl* ctl, Bufs bufs, uint32_t mg);
+// mg != kNoMasks: also merge the OR/AND masks of the checked labels
+constexpr uint32_t kNoMasks = 0xFFFFFFFFu;
 int launch_check_labels(void* stream, int key_words, Ctl* ctl, Bufs bufs,
                         uint64_t lim_lo, uint64_t lim_hi, unsigned int* bad_flag, uint64_t n,
-                        int masks);
+                        uint32_t mg);
 int launch_reset_status(void* stream, Ctl* ctl);
 
 }  // namespace sps

@@ -32,17 +32,18 @@ namespace {
 using namespace dev;
 
 // ---------------------------------------------------------------------------
-// Fused phase/permutation pass.
-template <int MAXOPS, int MAXPH>
+// Fused phase/permutation pass. Each block first copies the encoded op stream
+// and the phases from the plan arena into shared memory (all lines in flight
+// at once): walked straight from global memory, the warps of an SM advance in
+// step and wait one L2 round trip for every new 128-byte line of the stream.
 struct FusedArgs {
-  uint32_t nops, nph, has_perm, has_phase;
-  FOp ops[MAXOPS];
-  PhasePair ph[MAXPH];
+  const uint4* words;
+  const PhasePair* ph;
+  uint32_t nwords, nph, nops, has_perm, has_phase, mg;
 };
 
-template <int KW, int MAXOPS, int MAXPH>
-__global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
-                                               const __grid_constant__ FusedArgs<MAXOPS, MAXPH> a,
+template <int KW>
+__global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedArgs a,
                                                unsigned long long* plog) {
   const uint64_t n = ctl->nnz;
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -50,38 +51,31 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
     plog[1] = n;
   }
   if (ctl->status != 0u) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->updates += n * a.nops;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->updates += n * a.nops;
+    if (a.has_perm) reset_label_masks(ctl, mg_rs(a.mg));
+  }
   const SoA s = pick(bufs, ctl->cur);
-  const double r = 0.70710678118654752440;  // sqrt(0.5)
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  // the first label is in flight while the op stream is staged
+  uint64_t k0 = i < n ? s.lo[i] : 0ull;
+  uint64_t k1 = (KW == 2 && i < n) ? s.hi[i] : 0ull;
+  extern __shared__ uint4 fsm[];
+  PhasePair* sph = reinterpret_cast<PhasePair*>(fsm + a.nwords);
+  for (uint32_t w = threadIdx.x; w < a.nwords; w += blockDim.x) fsm[w] = a.words[w];
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.ph);
+    uint4* dst = reinterpret_cast<uint4*>(sph);
+    for (uint32_t w = threadIdx.x; w < 2 * a.nph; w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the new labels
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t k0 = s.lo[i];
-    uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+  for (; i < n; i += stride) {
     uint32_t cnt = 0;
     bool any_ph = false;
     double acc_re = 1.0, acc_im = 0.0;
-    for (uint32_t j = 0; j < a.nops; ++j) {
-      const FOp& o = a.ops[j];
-      bool cond = (k0 & o.c[0]) == o.c[0];
-      if (KW == 2) cond = cond && ((k1 & o.c[1]) == o.c[1]);
-      const bool sel = o.sbit != NO_SEL && label_bit(k0, k1, o.sbit);
-      const uint32_t step = sel ? o.a1 : o.a0;
-      cnt += cond ? step : 0u;
-      if (o.ph != NO_PH && cond) {
-        const PhasePair& pp = a.ph[o.ph];
-        const double pr = sel ? pp.re1 : pp.re0;
-        const double pi = sel ? pp.im1 : pp.im0;
-        const double nr = acc_re * pr - acc_im * pi;
-        const double ni = acc_re * pi + acc_im * pr;
-        acc_re = nr;
-        acc_im = ni;
-        any_ph = true;
-      }
-      const uint64_t m = cond ? ~0ull : 0ull;
-      k0 ^= o.t[0] & m;
-      if (KW == 2) k1 ^= o.t[1] & m;
-    }
+    walk_ops<KW>(fsm, a.nwords, sph, k0, k1, cnt, any_ph, acc_re, acc_im);
     if (a.has_perm) {
       s.lo[i] = k0;
       if (KW == 2) s.hi[i] = k1;
@@ -99,26 +93,17 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs,
         re = nr;
         im = ni;
       }
-      if (cnt & 1u) {  // times e^{i pi/4} = sqrt(0.5) (1 + i)
-        const double nr = r * (re - im);
-        const double ni = r * (re + im);
-        re = nr;
-        im = ni;
-      }
-      switch (cnt >> 1) {  // times i^(cnt/2)
-        case 1: { const double t = re; re = -im; im = t; break; }
-        case 2: re = -re; im = -im; break;
-        case 3: { const double t = re; re = im; im = -t; break; }
-        default: break;
-      }
+      apply_pi4(cnt, re, im);
       s.re[i] = re;
       s.im[i] = im;
     }
+    const uint64_t nx = i + stride;
+    if (nx < n) {
+      k0 = s.lo[nx];
+      k1 = KW == 2 ? s.hi[nx] : 0ull;
+    }
   }
-  if (a.has_perm) {
-    merge_label_masks(ctl, mo0, mo1, ma0, ma1);
-    finish_inplace_masks(ctl);
-  }
+  if (a.has_perm) merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
 }
 
 // ---------------------------------------------------------------------------
@@ -169,6 +154,7 @@ struct BsArgs {
   uint32_t nops, nw, na, nchunks;
   uint32_t has_perm, has_phase, has_cnt, list_len;
   uint32_t groups;   // groups of 32 entries per warp tile (even, 2..32)
+  uint32_t mg;       // label-mask buffers (MaskRing)
 };
 
 template <int KW>
@@ -187,7 +173,10 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
     plog[1] = n;
   }
   if (ctl->status != 0u) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->updates += n * a.nops;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->updates += n * a.nops;
+    if (a.has_perm) reset_label_masks(ctl, mg_rs(a.mg));
+  }
   // stage the op list, the phase tables and the extra-condition list
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.ops);
@@ -312,10 +301,7 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
     }
     __syncwarp();
   }
-  if (a.has_perm) {
-    merge_label_masks(ctl, mo0, mo1, ma0, ma1);
-    finish_inplace_masks(ctl);
-  }
+  if (a.has_perm) merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
 }
 
 // ---------------------------------------------------------------------------
@@ -335,6 +321,7 @@ struct BranchArgs {
   uint64_t capacity;
   uint64_t fail_tag;
   uint32_t load_pct, max_log2, probe_limit, pass_serial;
+  uint32_t mg;   // label-mask buffers (MaskRing), for the compaction
 };
 
 // Inserts (lo, hi) -> (re, im): claims a slot for the label if it is not in
@@ -437,6 +424,7 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
   // An error from an earlier pass means this pass never filled the table.
   if (status0 != 0u && ctl->fail_pass != a.pass_serial) return;
   const bool write_ok = status0 == 0u;
+  if (write_ok && blockIdx.x == 0 && threadIdx.x == 0) reset_label_masks(ctl, mg_rs(a.mg));
   const uint64_t n_in = ctl->nnz;
   const uint64_t size = 1ull << table_log2_for(n_in, a.load_pct, a.max_log2);
   const unsigned cur = ctl->cur;
@@ -496,7 +484,7 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
     }
     __syncthreads();
   }
-  merge_label_masks(ctl, mo0, mo1, ma0, ma1);
+  merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
   // The last block to finish publishes the pass result.
   if (threadIdx.x == 0) {
     __threadfence();
@@ -515,7 +503,6 @@ __global__ void __launch_bounds__(256) k_branch_compact(Ctl* ctl, Bufs bufs, Slo
           published = true;
         }
       }
-      if (published) publish_label_masks(ctl); else reset_next_masks(ctl);
       if (plog) {
         plog[0] = n_in;
         plog[1] = published ? total : n_in;
@@ -570,20 +557,18 @@ __global__ void k_sum_partials(const double* partials, int n, double* out) {
   if (threadIdx.x == 0) *out = t;
 }
 
-__global__ void k_set_nnz(Ctl* ctl, unsigned long long nnz) {
+__global__ void k_set_nnz(Ctl* ctl, unsigned long long nnz, uint32_t mg) {
   ctl->nnz = nnz;
   ctl->cur = 0u;
   ctl->status = 0u;
   ctl->out_count = 0ull;
   ctl->blocks_done = 0u;
-  ctl->blocks_done2 = 0u;
-  ctl->cor[0] = ctl->cor[1] = ~0ull;   // labels not inspected: no qubit known constant
-  ctl->cand[0] = ctl->cand[1] = 0ull;
-  reset_next_masks(ctl);
+  unknown_label_masks(ctl, mg_wr(mg));   // labels not inspected
+  reset_label_masks(ctl, mg_rs(mg));
 }
 
 // |0...0>: one entry (label 0, amplitude 1) in buffer 0.
-__global__ void k_reset_state(Ctl* ctl, Bufs bufs, int key_words) {
+__global__ void k_reset_state(Ctl* ctl, Bufs bufs, int key_words, uint32_t mg) {
   bufs.b[0].lo[0] = 0ull;
   if (key_words == 2) bufs.b[0].hi[0] = 0ull;
   bufs.b[0].re[0] = 1.0;
@@ -596,28 +581,28 @@ __global__ void k_reset_state(Ctl* ctl, Bufs bufs, int key_words) {
   ctl->fail_gate = 0ull;
   ctl->out_count = 0ull;
   ctl->blocks_done = 0u;
-  ctl->blocks_done2 = 0u;
-  ctl->cor[0] = ctl->cor[1] = 0ull;    // the single label 0
-  ctl->cand[0] = ctl->cand[1] = 0ull;
-  reset_next_masks(ctl);
+  set_label_masks(ctl, mg_wr(mg), 0ull, 0ull, 0ull, 0ull);   // the single label 0
+  reset_label_masks(ctl, mg_rs(mg));
 }
 
+// After a failed pass: passes that failed or were skipped left the mask
+// buffers out of step with the state, so all three claim nothing.
 __global__ void k_reset_status(Ctl* ctl) {
   ctl->status = 0u;
   ctl->fail_pass = 0u;
   ctl->fail_gate = 0ull;
   ctl->out_count = 0ull;
   ctl->blocks_done = 0u;
-  ctl->blocks_done2 = 0u;
-  reset_next_masks(ctl);
+  for (uint32_t b = 0; b < 3; ++b) unknown_label_masks(ctl, b);
 }
 
-// Flags labels outside the register; with `masks` also publishes the OR/AND
-// masks of the uploaded labels.
+// Flags labels outside the register; unless mg is kNoMasks also merges the
+// OR/AND masks of the uploaded labels.
 template <int KW>
 __global__ void k_check_labels(Ctl* ctl, Bufs bufs, uint64_t lim0, uint64_t lim1, unsigned* bad,
-                               int masks) {
+                               uint32_t mg) {
   const uint64_t n = ctl->nnz;
+  if (mg != kNoMasks && blockIdx.x == 0 && threadIdx.x == 0) reset_label_masks(ctl, mg_rs(mg));
   const SoA s = pick(bufs, ctl->cur);
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
@@ -630,10 +615,13 @@ __global__ void k_check_labels(Ctl* ctl, Bufs bufs, uint64_t lim0, uint64_t lim1
     ma0 &= k0;
     ma1 &= k1;
   }
-  if (masks) {
-    merge_label_masks(ctl, mo0, mo1, ma0, ma1);
-    finish_inplace_masks(ctl);
-  }
+  if (mg != kNoMasks) merge_label_masks(ctl, mg_wr(mg), mo0, mo1, ma0, ma1);
+}
+
+// lc.max_blocks is the SM count times the resident blocks of lc.threads threads
+int sm_count(const LaunchCfg& lc) {
+  const int s = (int)((int64_t)lc.max_blocks * lc.threads / 2048);
+  return s > 0 ? s : 1;
 }
 
 int grid_for(uint64_t work, int threads, int max_blocks) {
@@ -641,33 +629,6 @@ int grid_for(uint64_t work, int threads, int max_blocks) {
   if (b < 1) b = 1;
   if (b > (uint64_t)max_blocks) b = max_blocks;
   return (int)b;
-}
-
-template <int KW, int MAXOPS, int MAXPH>
-int fused_impl(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const Pass& p, uint64_t nnz_bound,
-               unsigned long long* plog) {
-  static_assert(sizeof(FusedArgs<MAXOPS, MAXPH>) <= 32000, "kernel parameter limit");
-  FusedArgs<MAXOPS, MAXPH> a;
-  a.nops = (uint32_t)p.ops.size();
-  a.nph = (uint32_t)p.phases.size();
-  a.has_perm = p.has_perm;
-  a.has_phase = p.has_phase;
-  for (uint32_t j = 0; j < a.nops; ++j) a.ops[j] = p.ops[j];
-  for (uint32_t j = 0; j < a.nph; ++j) a.ph[j] = p.phases[j];
-  const int blocks = grid_for(nnz_bound, lc.threads, lc.max_blocks);
-  k_fused<KW, MAXOPS, MAXPH><<<blocks, lc.threads, 0, (cudaStream_t)lc.stream>>>(ctl, bufs, a, plog);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
-}
-
-template <int KW>
-int fused_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const Pass& p, uint64_t nnz_bound,
-             unsigned long long* plog) {
-  const size_t no = p.ops.size(), np = p.phases.size();
-  if (no <= 16 && np <= 8) return fused_impl<KW, 16, 8>(lc, ctl, bufs, p, nnz_bound, plog);
-  if (no <= 128 && np <= 32) return fused_impl<KW, 128, 32>(lc, ctl, bufs, p, nnz_bound, plog);
-  if (no <= kMaxFusedOps && np <= kMaxFusedPhases)
-    return fused_impl<KW, kMaxFusedOps, kMaxFusedPhases>(lc, ctl, bufs, p, nnz_bound, plog);
-  return -1;
 }
 
 size_t bs_smem_fixed(const BsLaunch& b) {
@@ -689,7 +650,7 @@ int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uin
   a.has_phase = b.has_phase;
   a.has_cnt = b.has_cnt;
   a.list_len = b.list_len;
-  const int sms = lc.max_blocks / 8 > 0 ? lc.max_blocks / 8 : 1;
+  const int sms = sm_count(lc);
   const size_t fixed = bs_smem_fixed(b);
   const size_t rows = 32 * (size_t)(b.nw + b.na) + 1;
   const size_t budget = 200 * 1024;
@@ -705,6 +666,7 @@ int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uin
     while (G > 2 && (nnz_bound + 32ull * G - 1) / (32ull * G) < (uint64_t)sms * 16) G -= 2;
   }
   a.groups = G;
+  a.mg = b.mg;
   const size_t per_warp = rows * (G + 1) * 4;
   while (warps > 1 && fixed + warps * per_warp > budget) warps >>= 1;
   if (fixed + warps * per_warp > budget) return -1;
@@ -731,6 +693,7 @@ BranchArgs branch_args(const BranchLaunch& b) {
   a.max_log2 = b.max_log2;
   a.probe_limit = b.probe_limit;
   a.pass_serial = b.pass_serial;
+  a.mg = b.mg;
   return a;
 }
 
@@ -743,10 +706,27 @@ int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots) {
 }
 
 int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
-                 uint64_t nnz_bound, unsigned long long* plog) {
+                 const OpWord* words, const PhasePair* ph, uint64_t nnz_bound, uint32_t mg,
+                 unsigned long long* plog) {
   if (p.ops.empty()) return 0;
-  return key_words == 1 ? fused_kw<1>(lc, ctl, bufs, p, nnz_bound, plog)
-                        : fused_kw<2>(lc, ctl, bufs, p, nnz_bound, plog);
+  FusedArgs a;
+  a.words = reinterpret_cast<const uint4*>(words);
+  a.ph = ph;
+  a.nwords = (uint32_t)p.words.size();
+  a.nph = (uint32_t)p.phases.size();
+  a.nops = (uint32_t)p.ops.size();
+  a.has_perm = p.has_perm;
+  a.has_phase = p.has_phase;
+  a.mg = mg;
+  const int blocks = grid_for(nnz_bound, lc.threads, lc.max_blocks);
+  // at most 4 words per op and 96 phases: <= 35 KB, under the default 48 KB
+  const size_t smem = 16 * (size_t)a.nwords + sizeof(PhasePair) * a.nph;
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  if (key_words == 1)
+    k_fused<1><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+  else
+    k_fused<2><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
@@ -793,13 +773,13 @@ int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs 
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
-int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz) {
-  k_set_nnz<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, nnz);
+int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz, uint32_t mg) {
+  k_set_nnz<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, nnz, mg);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_reset_state(void* stream, int key_words, Ctl* ctl, Bufs bufs) {
-  k_reset_state<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, bufs, key_words);
+int launch_reset_state(void* stream, int key_words, Ctl* ctl, Bufs bufs, uint32_t mg) {
+  k_reset_state<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, bufs, key_words, mg);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -809,14 +789,14 @@ int launch_reset_status(void* stream, Ctl* ctl) {
 }
 
 int launch_check_labels(void* stream, int key_words, Ctl* ctl, Bufs bufs, uint64_t lim_lo,
-                        uint64_t lim_hi, unsigned int* bad_flag, uint64_t n, int masks) {
+                        uint64_t lim_hi, unsigned int* bad_flag, uint64_t n, uint32_t mg) {
   const int blocks = grid_for(n, 256, 1024);
   if (key_words == 1)
     k_check_labels<1><<<blocks, 256, 0, (cudaStream_t)stream>>>(ctl, bufs, lim_lo, lim_hi, bad_flag,
-                                                                 masks);
+                                                                 mg);
   else
     k_check_labels<2><<<blocks, 256, 0, (cudaStream_t)stream>>>(ctl, bufs, lim_lo, lim_hi, bad_flag,
-                                                                 masks);
+                                                                 mg);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -120,11 +120,14 @@ extern "C" sps_status sps_branch_apply_static(
   b.coop = 1;
   b.capacity = out_cap;
   b.fail_tag = 0;
+  MaskRing ring;
+  const uint32_t mg_set = ring.writer();
+  b.mg = ring.writer();
 
   // The array keeps the previous call's contents: reset the control block and
   // clear the part of the table this call uses before emitting into it.
   const uint64_t slots = 1ull << table_log2_for(n_in, b.load_pct, kStaticTableLog2);
-  if (launch_table_clear(lc, table, slots) < 0 || launch_set_nnz(cuda_stream, ctl, n_in) < 0 ||
+  if (launch_table_clear(lc, table, slots) < 0 || launch_set_nnz(cuda_stream, ctl, n_in, mg_set) < 0 ||
       launch_branch_emit(lc, kw, ctl, bufs, table, b, n_in, nullptr) < 0 ||
       launch_branch_compact(lc, kw, ctl, bufs, table, b, n_in, nullptr) < 0) {
     cudaGetLastError();
