@@ -161,6 +161,14 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
 sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
                            double* p);
 
+/* As sps_probability, but only enqueues: the sum is written to *out (pinned
+ * host memory or device memory, owned by the caller, valid until the stream
+ * has passed this point, e.g. until the next sps_sync) in stream order after
+ * every pass enqueued before. With a pending device-side error it is the sum
+ * over the last good state; the error is reported by the next sps_sync. */
+sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
+                                 double* out);
+
 /* Tuning options (see sps_set_option). */
 typedef enum sps_option {
   SPS_OPT_LOAD_FACTOR_PCT = 1, /* target branching-table load, 10..90 (default 50) */
@@ -183,12 +191,25 @@ typedef enum sps_option {
   SPS_OPT_BITSLICE_GROUPS = 11, /* groups of 32 entries per warp tile in the
                                   bit-sliced pass: even, 2..32; 0 = chosen from
                                   the state size (default) */
-  SPS_OPT_BRANCH_FORM = 10     /* branching passes on the whole GPU: 0 default
+  SPS_OPT_BRANCH_FORM = 10,    /* branching passes on the whole GPU: 0 default
                                   (gather), 1 scatter (labels emitted into a
                                   32-byte-slot table, FP64 atomic accumulation,
                                   separate prune/compact walk), 2 gather (each
                                   pair written once after a partner lookup in an
                                   index table; the insert-once rule of Sec. 3.1) */
+  SPS_OPT_EXPAND = 12          /* 1 (default): a run of up to 24 consecutive
+                                  branching gates that act on every entry and
+                                  whose flipped qubits are known to hold one
+                                  value across the state (the host tracks this
+                                  from sps_reset / sps_set_amplitudes through the
+                                  gates) is applied in one expansion pass: no
+                                  entry can meet a partner, so each entry writes
+                                  its 2^d images with amplitude a times a product
+                                  of matrix entries taken from per-8-gate tables
+                                  (rounded once per table entry, so results match
+                                  one-pass-per-gate within a few ulp rather than
+                                  bit for bit; entries are pruned on the final
+                                  amplitude). 0: one pass per gate */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:
@@ -206,7 +227,8 @@ sps_status sps_get_counters(sps_state* s, sps_counters* out);
 
 /* One profiled kernel launch (SPS_OPT_PROFILE). kind: 1 fused phase /
  * permutation pass, 2 scatter emit, 3 scatter compaction, 4 small-state run
- * (several passes in one block), 5 gather index build, 6 gather emit. n_in: entries
+ * (several passes in one block), 5 gather index build, 6 gather emit,
+ * 7 expansion pass (SPS_OPT_EXPAND; nops = gates). n_in: entries
  * the kernel read; n_out: entries in the state after it. flags: bit 0 the
  * pass permutes labels, bit 1 it changes amplitudes. label_bytes: 8 or 16. */
 typedef struct sps_kernel_record {
@@ -225,7 +247,8 @@ typedef struct sps_kernel_record {
 sps_status sps_profile_read(sps_state* s, sps_kernel_record* out, size_t cap, size_t* n);
 
 /* Host-only: compiles a gate list for an nqubits-qubit state and describes the
- * passes without touching a GPU. For pass i: kind[i] = 1 (fused phase /
+ * passes without touching a GPU, for a state of which nothing is known (so no
+ * expansion passes). For pass i: kind[i] = 1 (fused phase /
  * permutation run) or 2 (branching gate), first_gate[i] = index of its first
  * gate, ops[i] = number of device ops in the pass. At most `cap` passes are
  * written; *npasses receives the total. max_fused_ops as in SPS_OPT_MAX_FUSED_OPS

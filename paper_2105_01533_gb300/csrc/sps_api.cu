@@ -53,6 +53,8 @@ struct sps_state {
   uint32_t itab_log2 = 8;
   uint32_t epoch = 0;
   MaskRing masks;             // rotation of the device label-mask buffers
+  KnownBits kb;               // qubits known constant once every enqueued pass ran
+  bool expand = true;         // SPS_OPT_EXPAND
   int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
@@ -210,6 +212,38 @@ bool is_device_pointer(const void* p) {
 void label_limits(uint32_t nq, uint64_t* lim0, uint64_t* lim1) {
   *lim0 = nq >= 64 ? ~0ull : ((1ull << nq) - 1);
   *lim1 = nq <= 64 ? 0ull : (nq >= 128 ? ~0ull : ((1ull << (nq - 64)) - 1));
+}
+
+// The state is |0...0>: every qubit known, value 0.
+void know_all_zero(sps_state* s) {
+  label_limits(s->nqubits, &s->kb.known[0], &s->kb.known[1]);
+  s->kb.val[0] = s->kb.val[1] = 0ull;
+}
+
+// After a failure nothing is assumed.
+void know_nothing(sps_state* s) { s->kb = KnownBits(); }
+
+// Knowledge from the label masks the device holds for the current state
+// (stream synchronised): a qubit is known where OR and AND agree.
+sps_status know_from_device(sps_state* s) {
+  unsigned long long lm[kMaskStripes][4];
+  if (cudaMemcpy(lm, s->ctl->lm[s->masks.reader()], sizeof(lm), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return cuda_ok(cudaGetLastError());
+  uint64_t o0 = 0, o1 = 0, a0 = ~0ull, a1 = ~0ull;
+  for (int i = 0; i < kMaskStripes; ++i) {
+    o0 |= lm[i][0];
+    o1 |= lm[i][1];
+    a0 &= lm[i][2];
+    a1 &= lm[i][3];
+  }
+  uint64_t lim0, lim1;
+  label_limits(s->nqubits, &lim0, &lim1);
+  s->kb.known[0] = ~(o0 ^ a0) & lim0;
+  s->kb.known[1] = ~(o1 ^ a1) & lim1;
+  s->kb.val[0] = o0 & s->kb.known[0];
+  s->kb.val[1] = o1 & s->kb.known[1];
+  return SPS_OK;
 }
 
 cudaEvent_t take_event(sps_state* s) {
@@ -425,6 +459,7 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
   s->counters.kernel_launches += 2;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(cuda_ok(cudaGetLastError()));
   s->nnz_bound = 1;
+  know_all_zero(s);
   *out = s;
   return SPS_OK;
 }
@@ -435,6 +470,7 @@ sps_status sps_reset(sps_state* s) {
     return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 1;
   s->nnz_bound = 1;
+  know_all_zero(s);
   return SPS_OK;
 }
 
@@ -484,12 +520,22 @@ void sps_destroy(sps_state* s) {
   delete s;
 }
 
+// Upper bound on the nonzeros after pass p, given bound b before it.
+static uint64_t bound_after(const Pass& p, uint64_t b, uint64_t capacity) {
+  uint32_t doublings = 0;
+  if (p.kind == PASS_BRANCH) doublings = 1;
+  if (p.kind == PASS_EXPAND) doublings = p.ex_d;
+  for (uint32_t k = 0; k < doublings && b < capacity; ++k) b *= 2;
+  return b < capacity ? b : capacity;
+}
+
 sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
                      size_t* failed_gate) {
   if (!s || (ngates && !gates) || !(prune_eps >= 0.0)) return SPS_ERR_ARG;
   std::vector<Pass> passes;
   size_t bad = 0;
-  const sps_status cs = compile(gates, ngates, s->nqubits, s->max_fused_ops, &passes, &bad);
+  const sps_status cs =
+      compile(gates, ngates, s->nqubits, s->max_fused_ops, &passes, &bad, &s->kb, s->expand);
   if (cs != SPS_OK) {
     if (failed_gate) *failed_gate = bad;
     return cs;
@@ -504,16 +550,15 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
     uint64_t b = s->nnz_bound;
     for (size_t i = 0; i < passes.size(); ++i) {
       bound_at[i] = b;
-      if (passes[i].kind == PASS_BRANCH) b = 2 * b < s->capacity ? 2 * b : s->capacity;
+      b = bound_after(passes[i], b, s->capacity);
     }
     b = s->nnz_bound;
     for (size_t i = 0; i < passes.size();) {
       if (s->small_cap && b <= s->small_cap) {
         size_t j = i;
         uint64_t bb = b;
-        while (j < passes.size()) {
-          const uint64_t after =
-              passes[j].kind == PASS_BRANCH ? (2 * bb < s->capacity ? 2 * bb : s->capacity) : bb;
+        while (j < passes.size() && passes[j].kind != PASS_EXPAND) {
+          const uint64_t after = bound_after(passes[j], bb, s->capacity);
           if (after > s->small_cap) break;
           bb = after;
           ++j;
@@ -525,7 +570,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
           continue;
         }
       }
-      if (passes[i].kind == PASS_BRANCH) b = 2 * b < s->capacity ? 2 * b : s->capacity;
+      b = bound_after(passes[i], b, s->capacity);
       ++i;
     }
   }
@@ -534,8 +579,10 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   std::vector<BsPass> bs(passes.size());
   std::vector<size_t> bs_off(passes.size(), 0);
   std::vector<size_t> run_off(passes.size(), 0);   // small run: its RunPass array; direct
-                                                   // fused pass: its op stream
-  std::vector<size_t> ph_off(passes.size(), 0);    // direct fused pass: its phase pairs
+                                                   // fused pass: its op stream; expansion:
+                                                   // its factor tables
+  std::vector<size_t> ph_off(passes.size(), 0);    // direct fused pass: its phase pairs;
+                                                   // expansion: its mask tables
   size_t arena_bytes = 0;
   std::vector<unsigned char> blob;   // small-run payloads, appended after the bit-sliced plans
   {
@@ -574,6 +621,10 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         if (p.kind == PASS_FUSED && bs[i].ops.empty()) {   // direct fused pass
           run_off[i] = put(p.words.data(), p.words.size() * sizeof(OpWord));
           if (!p.phases.empty()) ph_off[i] = put(p.phases.data(), p.phases.size() * sizeof(PhasePair));
+        }
+        if (p.kind == PASS_EXPAND) {   // factor tables, then mask tables
+          run_off[i] = put(p.ex_f.data(), p.ex_f.size() * sizeof(double));
+          ph_off[i] = put(p.ex_m.data(), p.ex_m.size() * sizeof(uint64_t));
         }
         ++serial;
         ++i;
@@ -656,6 +707,26 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
     }
     const uint32_t serial = ++s->pass_serial;
     const uint64_t tag = ((uint64_t)s->apply_serial << 32) | (p.first_gate & 0xFFFFFFFFull);
+    if (p.kind == PASS_EXPAND) {
+      ExpandLaunch e;
+      e.f = reinterpret_cast<const double*>(s->arena + run_off[pi]);
+      e.m = reinterpret_cast<const uint64_t*>(s->arena + ph_off[pi]);
+      e.d = p.ex_d;
+      e.real = p.ex_real ? 1u : 0u;
+      e.pass_serial = serial;
+      e.mg = s->masks.writer();
+      e.eps = prune_eps;
+      e.capacity = s->capacity;
+      e.fail_tag = tag;
+      ProfScope ps(s, 7, serial, p.ex_d, 3u);
+      const int n = launch_expand(lc, s->kw, s->ctl, s->bufs, e, s->nnz_bound, ps.slot);
+      ps.done();
+      if (n < 0) return cuda_ok(cudaGetLastError());
+      s->counters.branch_passes++;
+      s->counters.kernel_launches += 1;
+      s->nnz_bound = bound_after(p, s->nnz_bound, s->capacity);
+      continue;
+    }
     if (p.kind == PASS_FUSED) {
       const uint32_t flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
       ProfScope ps(s, 1, serial, (uint32_t)p.ops.size(), flags);
@@ -752,7 +823,9 @@ sps_status sps_sync(sps_state* s, size_t* failed_gate) {
   s->nnz_bound = c.nnz > 0 ? c.nnz : 1;
   if (c.status == 0u) return SPS_OK;
   if (failed_gate) *failed_gate = (size_t)(c.fail_gate & 0xFFFFFFFFull);
-  // recover: clear the error and the table; the state is the last good one
+  // recover: clear the error and the table; the state is the last good one,
+  // which passes enqueued after the failed one no longer describe
+  know_nothing(s);
   const LaunchCfg lc = cfg_of(s);
   if (launch_reset_status(s->stream, s->ctl) < 0 ||
       (s->table && launch_table_clear(lc, s->table, s->table_slots) < 0))
@@ -862,9 +935,10 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
          cudaStreamSynchronize(s->stream) == cudaSuccess;
     s->nnz_bound = 1;
     s->counters.kernel_launches += 1;
+    know_all_zero(s);
     return ok ? SPS_ERR_ARG : cuda_ok(cudaGetLastError());
   }
-  return SPS_OK;
+  return know_from_device(s);
 }
 
 sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t value[2], double* p) {
@@ -882,6 +956,19 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
   st = cuda_ok(cudaStreamSynchronize(s->stream));
   if (st != SPS_OK) return st;
   *p = *s->hresult;
+  return SPS_OK;
+}
+
+sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
+                                 double* out) {
+  if (!s || !mask || !value || !out) return SPS_ERR_ARG;
+  const LaunchCfg lc = cfg_of(s);
+  if (launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0], value[1],
+                         s->partials, s->prob_blocks, s->dresult) < 0)
+    return cuda_ok(cudaGetLastError());
+  s->counters.kernel_launches += 2;
+  if (cudaMemcpyAsync(out, s->dresult, sizeof(double), cudaMemcpyDefault, s->stream) != cudaSuccess)
+    return cuda_ok(cudaGetLastError());
   return SPS_OK;
 }
 
@@ -907,6 +994,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_BITSLICE_GROUPS:
       if (v < 0 || v > 32 || (v & 1)) return SPS_ERR_ARG;
       s->bs_groups = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_EXPAND:
+      if (v != 0 && v != 1) return SPS_ERR_ARG;
+      s->expand = v == 1;
       return SPS_OK;
     case SPS_OPT_BRANCH_FORM:
       if (v < 0 || v > 2) return SPS_ERR_ARG;

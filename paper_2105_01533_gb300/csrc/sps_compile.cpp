@@ -3,6 +3,7 @@
 // applied per element in a single pass (Sec. 3.2, composition of (f, g) pairs).
 // Angles are turned into cos/sin here, once, with the host libm, so the device
 // evaluates no transcendental function.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -143,10 +144,94 @@ void lower_branch(const sps_gate& g, Pass* p) {
   std::memcpy(b.m_im, mi, sizeof(mi));
 }
 
+// ---- known-constant qubits ------------------------------------------------------
+bool kb_has(const KnownBits& k, uint32_t q) { return (k.known[q >> 6] >> (q & 63)) & 1ull; }
+bool kb_val(const KnownBits& k, uint32_t q) { return (k.val[q >> 6] >> (q & 63)) & 1ull; }
+void kb_forget(KnownBits& k, uint32_t q) { k.known[q >> 6] &= ~(1ull << (q & 63)); }
+
+// Controls: 1 = all known 1 (the gate acts everywhere), 0 = some known 0 (the
+// gate acts nowhere), -1 = depends on the entry.
+int controls_state(const sps_gate& g, const KnownBits& k) {
+  const uint64_t zero = (g.cmask[0] & k.known[0] & ~k.val[0]) | (g.cmask[1] & k.known[1] & ~k.val[1]);
+  if (zero) return 0;
+  const uint64_t unknown = (g.cmask[0] & ~k.known[0]) | (g.cmask[1] & ~k.known[1]);
+  return unknown ? -1 : 1;
+}
+
+// Advances the knowledge over one gate (never claims more than holds: a qubit
+// stays known only if the gate cannot change it in any label).
+void track(const sps_gate& g, KnownBits& k) {
+  const int cs = controls_state(g, k);
+  if (cs == 0) return;
+  switch (g.op) {
+    case SPS_OP_X: case SPS_OP_Y:
+      if (cs == 1 && kb_has(k, g.t0)) k.val[g.t0 >> 6] ^= 1ull << (g.t0 & 63);
+      else kb_forget(k, g.t0);
+      break;
+    case SPS_OP_H: case SPS_OP_RX: case SPS_OP_RY:
+      kb_forget(k, g.t0);
+      break;
+    case SPS_OP_GIVENS:
+      if (kb_has(k, g.t0) && kb_has(k, g.t1) && kb_val(k, g.t0) == kb_val(k, g.t1)) break;
+      kb_forget(k, g.t0);
+      kb_forget(k, g.t1);
+      break;
+    default:   // diagonal gates keep every label
+      break;
+  }
+}
+
+// A branching gate joins an expansion pass if it acts on every entry and only
+// flips qubits known constant: then no entry has a partner.
+bool expandable(const sps_gate& g, const KnownBits& k) {
+  if (controls_state(g, k) != 1 || !kb_has(k, g.t0)) return false;
+  if (g.op == SPS_OP_GIVENS)
+    return kb_has(k, g.t1) && kb_val(k, g.t0) != kb_val(k, g.t1);
+  return true;
+}
+
+// Per-chunk tables of an expansion pass: for chunk choices u, the product of
+// M_j[x_j ^ u_j][x_j] (the entry taking the amplitude from the selector value
+// x_j to the chosen output) over the chunk's gates in order, and the xor of
+// the chosen flips. Built by doubling, one complex product per entry; each
+// entry carries at most 8 roundings.
+void build_expand(Pass* p) {
+  p->ex_d = (uint32_t)p->ex_ops.size();
+  const uint32_t nch = p->ex_chunks();
+  p->ex_f.assign((size_t)nch * 256 * 2, 0.0);
+  p->ex_m.assign((size_t)nch * 256 * 2, 0ull);
+  p->ex_real = true;
+  for (const BranchOp& b : p->ex_ops) p->ex_real = p->ex_real && b.real_m;
+  for (uint32_t ch = 0; ch < nch; ++ch) {
+    const uint32_t j0 = ch * kExpandChunk;
+    const uint32_t g = std::min<uint32_t>(kExpandChunk, p->ex_d - j0);
+    double* f = &p->ex_f[(size_t)ch * 256 * 2];
+    uint64_t* m = &p->ex_m[(size_t)ch * 256 * 2];
+    f[0] = 1.0;
+    for (uint32_t b = 0; b < g; ++b) {   // entries [0, 2^b) hold the first b gates
+      const BranchOp& op = p->ex_ops[j0 + b];
+      const uint32_t x = p->ex_x[j0 + b];
+      for (uint32_t u = 0; u < (1u << b); ++u) {
+        const double fr = f[2 * u], fi = f[2 * u + 1];
+        const uint64_t m0 = m[2 * u], m1 = m[2 * u + 1];
+        for (uint32_t cb = 0; cb < 2; ++cb) {   // entry u (cb = 0) and u + 2^b (cb = 1)
+          const uint32_t row = x ^ cb, v = u | (cb << b);
+          const double er = op.m_re[row][x], ei = op.m_im[row][x];
+          f[2 * v] = fr * er - fi * ei;
+          f[2 * v + 1] = fr * ei + fi * er;
+          m[2 * v] = m0 ^ (cb ? op.m[0] : 0ull);
+          m[2 * v + 1] = m1 ^ (cb ? op.m[1] : 0ull);
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
-                   uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad) {
+                   uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad, KnownBits* kb,
+                   bool expand) {
   if (max_fused_ops == 0 || max_fused_ops > kMaxFusedOps) max_fused_ops = kDefaultMaxFusedOps;
   out->clear();
   for (size_t i = 0; i < ngates; ++i) {
@@ -156,18 +241,37 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
       return SPS_ERR_ARG;
     }
   }
+  KnownBits k = kb ? *kb : KnownBits();
   Pass* run = nullptr;
+  Pass* ex = nullptr;
   for (size_t i = 0; i < ngates; ++i) {
     const sps_gate& g = gates[i];
     if (is_branch(g.op)) {
       run = nullptr;
       Pass p;
-      p.kind = PASS_BRANCH;
       p.first_gate = i;
       lower_branch(g, &p);
+      if (expand && kb && expandable(g, k)) {
+        if (ex == nullptr || ex->ex_ops.size() >= kMaxExpandGates) {
+          Pass e;
+          e.kind = PASS_EXPAND;
+          e.first_gate = i;
+          out->push_back(std::move(e));
+          ex = &out->back();
+        }
+        ex->ex_ops.push_back(p.br);
+        ex->ex_x.push_back(kb_val(k, g.t0) ? 1 : 0);
+        track(g, k);
+        continue;
+      }
+      ex = nullptr;
+      p.kind = PASS_BRANCH;
       out->push_back(std::move(p));
+      track(g, k);
       continue;
     }
+    ex = nullptr;
+    track(g, k);
     const uint32_t slots = g.op == SPS_OP_P ? 1u : (g.op == SPS_OP_RZ ? 2u : 0u);
     if (run == nullptr || run->ops.size() >= max_fused_ops || run->phases.size() >= kMaxFusedPhases ||
         run->fire_slots + slots > kMaxFireSlots) {
@@ -179,8 +283,11 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
     }
     lower_perm_diag(g, run);
   }
-  for (Pass& p : *out)
+  for (Pass& p : *out) {
     if (p.kind == PASS_FUSED) encode_ops(p.ops, &p.words);
+    if (p.kind == PASS_EXPAND) build_expand(&p);
+  }
+  if (kb) *kb = k;
   return SPS_OK;
 }
 
@@ -216,9 +323,7 @@ void encode_ops(const std::vector<FOp>& ops, std::vector<OpWord>* words) {
 // ---- bit-sliced form ------------------------------------------------------------
 namespace {
 
-using cld = long double;
-struct CL { cld re, im; };
-CL cl_mul(CL a, CL b) { return CL{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+struct CL { double re, im; };
 
 }  // namespace
 
@@ -233,7 +338,7 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
   // factor of every aux bit, for the chunk tables
   std::vector<CL> factor;
   if (cnt) {
-    const cld r = std::sqrt((cld)0.5);
+    const double r = std::sqrt(0.5);
     factor.push_back(CL{r, r});      // counter bit 0: e^{i pi/4}
     factor.push_back(CL{0, 1});      // counter bit 1: e^{i pi/2}
     factor.push_back(CL{-1, 0});     // counter bit 2: e^{i pi}
@@ -287,17 +392,22 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
   for (SOp& so : out->ops)
     for (int k = 0; k < 3; ++k)
       if (so.c[k] == SOP_ONES) so.c[k] = ones;
+  // chunk tables by doubling: entry idx = entry (idx without its top bit) times
+  // the factor of that bit, one complex product each
   const uint32_t nch = out->nchunks();
   out->tables.assign((size_t)nch * 256 * 2, 0.0);
   for (uint32_t c = 0; c < nch; ++c) {
-    for (uint32_t idx = 0; idx < 256; ++idx) {
-      CL acc{1, 0};
-      for (uint32_t b = 0; b < 8; ++b) {
-        const uint32_t bit = 8 * c + b;
-        if (((idx >> b) & 1u) && bit < aux) acc = cl_mul(acc, factor[bit]);
+    double* t = &out->tables[(size_t)c * 256 * 2];
+    t[0] = 1.0;
+    for (uint32_t b = 0; b < 8; ++b) {
+      const uint32_t bit = 8 * c + b;
+      const double fr = bit < aux ? (double)factor[bit].re : 1.0;
+      const double fi = bit < aux ? (double)factor[bit].im : 0.0;
+      for (uint32_t u = 0; u < (1u << b); ++u) {
+        const uint32_t v = u | (1u << b);
+        t[2 * v] = t[2 * u] * fr - t[2 * u + 1] * fi;
+        t[2 * v + 1] = t[2 * u] * fi + t[2 * u + 1] * fr;
       }
-      out->tables[((size_t)c * 256 + idx) * 2] = (double)acc.re;
-      out->tables[((size_t)c * 256 + idx) * 2 + 1] = (double)acc.im;
     }
   }
 }

@@ -238,6 +238,140 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Expansion pass (d branching gates, each active everywhere and flipping only
+// qubits constant before it, so no two paths meet): output t = (i, c) with
+// i = t >> d and c the d choices; label k_i ^ mask(c), amplitude a_i * F0[c0] *
+// F1[c1] * F2[c2] from per-8-gate tables staged in shared memory; pruned on
+// the final amplitude (every matrix entry has modulus <= 1, so no path falls
+// below eps before its end and rises above it after). Survivors are compacted
+// as in the gather emit; the last block publishes the count.
+struct ExpandArgs {
+  const double2* f;        // chunks x 256 path factors
+  const ulonglong2* m;     // chunks x 256 flip masks
+  uint32_t d, chunks, real, pass_serial, mg;
+  double eps2, eps;
+  uint64_t capacity, fail_tag;
+};
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const ExpandArgs a,
+                                                unsigned long long* plog) {
+  __shared__ unsigned warp_cnt[32];
+  __shared__ unsigned long long block_base;
+  __shared__ double2 sf[3 * 256];
+  __shared__ ulonglong2 sm[3 * 256];
+  if (ctl->status != 0u) return;
+  const uint64_t n = ctl->nnz;
+  const unsigned cur = ctl->cur;
+  const SoA s = pick(bufs, cur);
+  const SoA out = pick(bufs, cur ^ 1u);
+  if (blockIdx.x == 0 && threadIdx.x == 0) reset_label_masks(ctl, mg_rs(a.mg));
+  for (uint32_t w = threadIdx.x; w < 256 * a.chunks; w += blockDim.x) {
+    sf[w] = a.f[w];
+    sm[w] = a.m[w];
+  }
+  __syncthreads();
+  const uint64_t total = n << a.d;
+  const uint64_t cmask = (1ull << a.d) - 1ull;
+  const uint64_t eps_bits = eps_pattern(a.eps);
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned nwarps = blockDim.x >> 5;
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < total;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = base + threadIdx.x;
+    uint64_t l0 = 0, l1 = 0;
+    double vr = 0.0, vi = 0.0;
+    bool w = false;
+    if (t < total) {
+      const uint64_t i = t >> a.d;
+      const uint32_t c = (uint32_t)(t & cmask);
+      l0 = s.lo[i];
+      l1 = KW == 2 ? s.hi[i] : 0ull;
+      vr = s.re[i];
+      vi = s.im[i];
+      for (uint32_t ch = 0; ch < a.chunks; ++ch) {
+        const uint32_t u = ch * 256u + ((c >> (8u * ch)) & 0xFFu);
+        const ulonglong2 mk = sm[u];
+        l0 ^= mk.x;
+        l1 ^= mk.y;
+        const double2 f = sf[u];
+        if (a.real) {
+          vr = vr * f.x;
+          vi = vi * f.x;
+        } else {
+          const double nr = vr * f.x - vi * f.y;
+          const double ni = vr * f.y + vi * f.x;
+          vr = nr;
+          vi = ni;
+        }
+      }
+      w = keep_amp(vr, vi, a.eps2, eps_bits);
+    }
+    if (w) {
+      mo0 |= l0;
+      mo1 |= l1;
+      ma0 &= l0;
+      ma1 &= l1;
+    }
+    const unsigned b0 = __ballot_sync(FULL, w);
+    if (lane == 0) warp_cnt[warp] = __popc(b0);
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned v = lane < nwarps ? warp_cnt[lane] : 0u;
+      unsigned incl = v;
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const unsigned x = __shfl_up_sync(FULL, incl, dd);
+        if (lane >= (unsigned)dd) incl += x;
+      }
+      const unsigned tot = __shfl_sync(FULL, incl, 31);
+      if (lane < nwarps) warp_cnt[lane] = incl - v;
+      if (lane == 0)
+        block_base = tot ? atomicAdd(&ctl->out_count, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    if (w) {
+      const uint64_t pos = block_base + warp_cnt[warp] + __popc(b0 & ((1u << lane) - 1u));
+      if (pos < a.capacity) {
+        out.lo[pos] = l0;
+        if (KW == 2) out.hi[pos] = l1;
+        out.re[pos] = vr;
+        out.im[pos] = vi;
+      }
+    }
+    __syncthreads();
+  }
+  merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long got = atomicAdd(&ctl->out_count, 0ull);
+      bool published = false;
+      if (ctl->status == 0u) {
+        if (got > a.capacity) {
+          fail(ctl, SPS_ERR_CAPACITY, a.pass_serial, a.fail_tag);
+        } else {
+          ctl->nnz = got;
+          ctl->cur = cur ^ 1u;
+          // the nonzeros before each of the d gates: n, 2n, ..., 2^(d-1) n
+          ctl->updates += n * cmask;
+          published = true;
+        }
+      }
+      if (plog) {
+        plog[0] = n;
+        plog[1] = published ? got : n;
+      }
+      ctl->out_count = 0ull;
+      ctl->blocks_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
 __global__ void k_itab_clear(unsigned long long* itab, uint64_t nslots) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nslots;
        i += (uint64_t)gridDim.x * blockDim.x)
@@ -286,6 +420,29 @@ int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
     else
       k_gather_emit<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
   }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const ExpandLaunch& e,
+                  uint64_t nnz_bound, unsigned long long* plog) {
+  ExpandArgs a;
+  a.f = reinterpret_cast<const double2*>(e.f);
+  a.m = reinterpret_cast<const ulonglong2*>(e.m);
+  a.d = e.d;
+  a.chunks = (e.d + kExpandChunk - 1) / kExpandChunk;
+  a.real = e.real;
+  a.pass_serial = e.pass_serial;
+  a.mg = e.mg;
+  a.eps2 = e.eps * e.eps;
+  a.eps = e.eps;
+  a.capacity = e.capacity;
+  a.fail_tag = e.fail_tag;
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  const int blocks = grid_of(nnz_bound << e.d, lc.threads, lc.max_blocks);
+  if (key_words == 1)
+    k_expand<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, a, plog);
+  else
+    k_expand<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, a, plog);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -127,7 +127,21 @@ constexpr uint32_t OPS_FLIP64 = 1, OPS_FLIP128 = 2, OPS_GEN = 3;
 void encode_ops(const std::vector<FOp>& ops, std::vector<OpWord>* words);
 
 // ---- a compiled pass -----------------------------------------------------------
-enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2 };
+enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2, PASS_EXPAND = 3 };
+
+// Qubits known (on the host, conservatively) to hold one value in every stored
+// label: bit q of known set => every label has bit q = bit q of val.
+struct KnownBits {
+  uint64_t known[2] = {0ull, 0ull};
+  uint64_t val[2] = {0ull, 0ull};
+};
+
+// Expansion pass: d branching gates, each active on every entry and flipping
+// only qubits known constant before it, so no two paths meet. Output (i, c)
+// for c in [0, 2^d): label k_i ^ mask(c), amplitude a_i * factor(c), both taken
+// from per-chunk tables over 8 gates (c = c0 | c1 << 8 | c2 << 16).
+constexpr uint32_t kExpandChunk = 8;
+constexpr uint32_t kMaxExpandGates = 24;
 
 struct Pass {
   PassKind kind;
@@ -141,6 +155,14 @@ struct Pass {
   uint32_t fire_slots = 0;  // aux bits its arbitrary phases need in bit-sliced form
   // branch
   BranchOp br{};
+  // expand
+  std::vector<BranchOp> ex_ops; // its gates, in order
+  std::vector<uint8_t> ex_x;    // value of each gate's selector qubit before it
+  uint32_t ex_d = 0;            // gates
+  bool ex_real = false;         // every path factor is real
+  std::vector<double> ex_f;     // per chunk: 256 x (re, im) products of matrix entries
+  std::vector<uint64_t> ex_m;   // per chunk: 256 x (lo, hi) xor of the flip masks
+  uint32_t ex_chunks() const { return (ex_d + kExpandChunk - 1) / kExpandChunk; }
 };
 
 // One pass of a small-state run (k_small_run), stored in the plan arena.
@@ -174,8 +196,11 @@ constexpr uint32_t kMaxFusedPhases = 96;
 constexpr uint32_t kDefaultMaxFusedOps = kMaxFusedOps;
 
 // Validates and compiles; on a bad record returns SPS_ERR_ARG with *bad set.
+// With kb (nullable) the compiler tracks the known-constant qubits through the
+// gates (updating *kb on success) and, if expand, forms expansion passes.
 sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
-                   uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad);
+                   uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad,
+                   KnownBits* kb = nullptr, bool expand = false);
 
 // ---- device-side control block -------------------------------------------------
 constexpr int kMaskStripes = 32;
@@ -291,6 +316,16 @@ int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        unsigned long long* itab, uint32_t epoch, const BranchLaunch& b,
                        uint64_t nnz_bound, int part, unsigned long long* plog);
 int launch_itab_clear(const LaunchCfg& lc, unsigned long long* itab, uint64_t nslots);
+// Expansion pass (PASS_EXPAND); f, m: its tables in device memory.
+struct ExpandLaunch {
+  const double* f;
+  const uint64_t* m;
+  uint32_t d, real, pass_serial, mg;
+  double eps;
+  uint64_t capacity, fail_tag;
+};
+int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const ExpandLaunch& e,
+                  uint64_t nnz_bound, unsigned long long* plog);
 int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
                        double* partials, int nblocks, double* result);

@@ -27,7 +27,7 @@ SPS_ERR_CUDA, SPS_ERR_OOM, SPS_ERR_NO_DEVICE = 4, 5, 6
 SPS_OPT_LOAD_FACTOR_PCT, SPS_OPT_PROBE_LIMIT, SPS_OPT_BLOCK_THREADS = 1, 2, 3
 SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
 SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP, SPS_OPT_BITSLICE_MIN_NNZ = 7, 8, 9
-SPS_OPT_BRANCH_FORM, SPS_OPT_BITSLICE_GROUPS = 10, 11
+SPS_OPT_BRANCH_FORM, SPS_OPT_BITSLICE_GROUPS, SPS_OPT_EXPAND = 10, 11, 12
 KIND_SMALL_RUN, KIND_GATHER_BUILD, KIND_GATHER_EMIT = 4, 5, 6
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 
@@ -40,7 +40,7 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates",
            "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
-           "sps_server_completed")
+           "sps_server_completed", "sps_probability_async")
 
 
 class SpsError(RuntimeError):
@@ -119,6 +119,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_set_amplitudes.restype = st
     lib.sps_probability.argtypes = [vp, vp, vp, ctypes.POINTER(dbl)]
     lib.sps_probability.restype = st
+    lib.sps_probability_async.argtypes = [vp, vp, vp, vp]
+    lib.sps_probability_async.restype = st
     lib.sps_set_option.argtypes = [vp, ctypes.c_int, i64]
     lib.sps_set_option.restype = st
     lib.sps_get_counters.argtypes = [vp, ctypes.POINTER(Counters)]
@@ -312,6 +314,15 @@ def sps_probability(h: int, mask: Sequence[int], value: Sequence[int]) -> float:
     return p.value
 
 
+def sps_probability_async(h: int, mask: Sequence[int], value: Sequence[int], out_ptr: int) -> None:
+    """Enqueue the probability; the double lands at out_ptr (pinned host or
+    device memory) in stream order."""
+    m = np.array([int(mask[0]), int(mask[1])], np.uint64)
+    v = np.array([int(value[0]), int(value[1])], np.uint64)
+    _check(load_library().sps_probability_async(h, _ptr(m), _ptr(v), ctypes.c_void_p(out_ptr)),
+           "sps_probability_async")
+
+
 def sps_set_option(h: int, opt: int, value: int) -> None:
     _check(load_library().sps_set_option(h, opt, int(value)), "sps_set_option")
 
@@ -427,6 +438,10 @@ class SparseState:
 
     def probability(self, mask, value) -> float:
         return sps_probability(self._h, mask, value)
+
+    def probability_async(self, mask, value, out_ptr: int) -> None:
+        """Enqueue the probability into out_ptr (pinned host or device memory)."""
+        sps_probability_async(self._h, mask, value, out_ptr)
 
     def get_amplitudes(self, sort: bool = True):
         """(hi, lo, re, im) numpy arrays, sorted by (hi, lo) unless sort=False."""

@@ -89,8 +89,10 @@ def test_branching_only_is_bit_identical(small_cap, form):
         else:
             recs.append(W.Givens(q[0], q[1], rng.angle()))
     gates = W.to_array(recs)
+    # one pass per gate (no expansion passes): every product and sum as the oracle's
     got, want = run_both(n, gates, eps=0.0, options=[(sps.SPS_OPT_SMALL_RUN_CAP, small_cap),
-                                                     (sps.SPS_OPT_BRANCH_FORM, form)])
+                                                     (sps.SPS_OPT_BRANCH_FORM, form),
+                                                     (sps.SPS_OPT_EXPAND, 0)])
     for a, b in zip(got, want):
         np.testing.assert_array_equal(a, b)
 
@@ -231,6 +233,7 @@ def test_probe_limit_reports_table_full_without_hanging():
     st = sps.SparseState(30, 1 << 12)
     st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)      # exercise the global table
     st.set_option(sps.SPS_OPT_BRANCH_FORM, 1)        # the scatter table has the probe limit
+    st.set_option(sps.SPS_OPT_EXPAND, 0)             # one table pass per gate
     st.apply(W.to_array([W.H(q) for q in range(8)]), 0.0)
     st.sync()
     st.set_option(sps.SPS_OPT_PROBE_LIMIT, 1)
@@ -253,7 +256,8 @@ def test_high_load_factor_collisions():
         got, want = run_both(n, gates, eps=0.0, capacity=1 << 16,
                              options=[(sps.SPS_OPT_LOAD_FACTOR_PCT, 90),
                                       (sps.SPS_OPT_SMALL_RUN_CAP, 0),
-                                      (sps.SPS_OPT_BRANCH_FORM, form)])
+                                      (sps.SPS_OPT_BRANCH_FORM, form),
+                                      (sps.SPS_OPT_EXPAND, 0)])
         compare_states(got, want, 0.0)
     compare_states(got, want, 0.0)
 
@@ -316,6 +320,7 @@ def test_counters_count_launches():
     gates = W.to_array([W.X(0), W.Z(1), W.H(2), W.CX(2, 3), W.H(4)])
     st = sps.SparseState(24, 4096)
     st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)
+    st.set_option(sps.SPS_OPT_EXPAND, 0)
     st.sync()   # the gather form allocates nothing; the scatter table comes on first use
     c0 = st.counters().kernel_launches
     st.apply(gates, 0.0)
@@ -324,11 +329,20 @@ def test_counters_count_launches():
     assert c.kernel_launches - c0 == 2 * 1 + 2 * 2
     st.close()
     st = sps.SparseState(24, 4096)        # all five passes fit one small-state run
+    st.set_option(sps.SPS_OPT_EXPAND, 0)
     c0 = st.counters().kernel_launches
     st.apply(gates, 0.0)
     c = st.counters()
     assert c.fused_passes == 2 and c.branch_passes == 2
     assert c.kernel_launches - c0 == 1
+    st.close()
+    # H(2) and H(4) flip qubits still 0 in every label: one expansion launch each
+    st = sps.SparseState(24, 4096)
+    c0 = st.counters().kernel_launches
+    st.apply(gates, 0.0)
+    c = st.counters()
+    assert c.fused_passes == 2 and c.branch_passes == 2
+    assert c.kernel_launches - c0 == 4
     st.close()
 
 
@@ -430,4 +444,24 @@ def test_gather_epoch_wraps():
     st.apply(np.tile(pair, 33_000), 1e-14)
     after = st.get_amplitudes()
     compare_states(after, before, 1e-14, atol=1e-11)
+    st.close()
+
+
+def test_probability_async_matches():
+    import torch
+    st = sps.SparseState(40, 1 << 12)
+    out = torch.full((3,), float("nan"), dtype=torch.float64, pin_memory=True)
+    st.apply(W.to_array([W.H(q) for q in range(6)] + [W.Ry(7, 0.3, 0), W.T(2)]), 1e-14)
+    st.probability_async((0b101, 0), (0b001, 0), out.data_ptr())
+    st.apply(W.to_array([W.H(0), W.CX(1, 9)]), 1e-14)
+    st.probability_async((1 << 9, 0), (1 << 9, 0), out.data_ptr() + 8)
+    dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st.probability_async((0, 0), (0, 0), dev.data_ptr())          # into device memory
+    st.sync()
+    torch.cuda.synchronize()
+    orc = OracleState(40)
+    orc.apply(W.to_array([W.H(q) for q in range(6)] + [W.Ry(7, 0.3, 0), W.T(2)]), eps=1e-14)
+    assert abs(out[0].item() - orc.probability((0b101, 0), (0b001, 0))) < 1e-12
+    assert abs(out[1].item() - st.probability((1 << 9, 0), (1 << 9, 0))) < 1e-15
+    assert abs(dev.item() - 1.0) < 1e-12
     st.close()
