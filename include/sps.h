@@ -197,7 +197,7 @@ typedef enum sps_option {
                                   separate prune/compact walk), 2 gather (each
                                   pair written once after a partner lookup in an
                                   index table; the insert-once rule of Sec. 3.1) */
-  SPS_OPT_EXPAND = 12          /* 1 (default): a run of up to 24 consecutive
+  SPS_OPT_EXPAND = 12,         /* 1 (default): a run of up to 24 consecutive
                                   branching gates that act on every entry and
                                   whose flipped qubits are known to hold one
                                   value across the state (the host tracks this
@@ -210,6 +210,15 @@ typedef enum sps_option {
                                   one-pass-per-gate within a few ulp rather than
                                   bit for bit; entries are pruned on the final
                                   amplitude). 0: one pass per gate */
+  SPS_OPT_FOLD = 13            /* 1 (default): in runs of phase/permutation gates,
+                                  qubits known to hold one value (tracked as for
+                                  SPS_OPT_EXPAND) are resolved on the host: gates
+                                  with a control known 0 are dropped, known
+                                  controls leave the condition, flips of known
+                                  qubits are collected into one flip, and
+                                  adjacent flips with one condition merge. The
+                                  result is the same; the device walks fewer
+                                  ops. 0: one op per gate */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:

@@ -55,6 +55,7 @@ struct sps_state {
   MaskRing masks;             // rotation of the device label-mask buffers
   KnownBits kb;               // qubits known constant once every enqueued pass ran
   bool expand = true;         // SPS_OPT_EXPAND
+  bool fold = true;           // SPS_OPT_FOLD
   int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
@@ -535,7 +536,8 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   std::vector<Pass> passes;
   size_t bad = 0;
   const sps_status cs =
-      compile(gates, ngates, s->nqubits, s->max_fused_ops, &passes, &bad, &s->kb, s->expand);
+      compile(gates, ngates, s->nqubits, s->max_fused_ops, &passes, &bad, &s->kb, s->expand,
+              s->fold);
   if (cs != SPS_OK) {
     if (failed_gate) *failed_gate = bad;
     return cs;
@@ -581,7 +583,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   std::vector<size_t> run_off(passes.size(), 0);   // small run: its RunPass array; direct
                                                    // fused pass: its op stream; expansion:
                                                    // its factor tables
-  std::vector<size_t> ph_off(passes.size(), 0);    // direct fused pass: its phase pairs;
+  std::vector<size_t> ph_off(passes.size(), 0);    // direct fused pass: its fire-slot tables;
                                                    // expansion: its mask tables
   size_t arena_bytes = 0;
   std::vector<unsigned char> blob;   // small-run payloads, appended after the bit-sliced plans
@@ -620,7 +622,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         const Pass& p = passes[i];
         if (p.kind == PASS_FUSED && bs[i].ops.empty()) {   // direct fused pass
           run_off[i] = put(p.words.data(), p.words.size() * sizeof(OpWord));
-          if (!p.phases.empty()) ph_off[i] = put(p.phases.data(), p.phases.size() * sizeof(PhasePair));
+          if (!p.ftab.empty()) ph_off[i] = put(p.ftab.data(), p.ftab.size() * sizeof(double));
         }
         if (p.kind == PASS_EXPAND) {   // factor tables, then mask tables
           run_off[i] = put(p.ex_f.data(), p.ex_f.size() * sizeof(double));
@@ -643,11 +645,11 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         r.eps2 = prune_eps * prune_eps;
         r.eps = prune_eps;
         if (p.kind == PASS_FUSED) {
-          r.nops = (uint32_t)p.ops.size();
+          r.nops = p.ngates;
           r.nwords = (uint32_t)p.words.size();
           r.flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
           r.ops_off = (uint32_t)put(p.words.data(), p.words.size() * sizeof(OpWord));
-          r.ph_off = p.phases.empty() ? 0u : (uint32_t)put(p.phases.data(), p.phases.size() * sizeof(PhasePair));
+          r.ph_off = p.ftab.empty() ? 0u : (uint32_t)put(p.ftab.data(), p.ftab.size() * sizeof(double));
         } else {
           r.br_off = (uint32_t)put(&p.br, sizeof(BranchOp));
         }
@@ -741,6 +743,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         base += align16(b.tables.size() * 8);
         bl.list = base;
         bl.nops = (uint32_t)b.ops.size();
+        bl.ngates = p.ngates;
         bl.nw = b.nw;
         bl.na = b.na;
         bl.nchunks = b.nchunks();
@@ -754,7 +757,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       } else {
         n = launch_fused(lc, s->kw, s->ctl, s->bufs, p,
                          reinterpret_cast<const OpWord*>(s->arena + run_off[pi]),
-                         reinterpret_cast<const PhasePair*>(s->arena + ph_off[pi]), s->nnz_bound,
+                         reinterpret_cast<const double*>(s->arena + ph_off[pi]), s->nnz_bound,
                          p.has_perm ? s->masks.writer() : 0u, ps.slot);
       }
       ps.done();
@@ -998,6 +1001,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_EXPAND:
       if (v != 0 && v != 1) return SPS_ERR_ARG;
       s->expand = v == 1;
+      return SPS_OK;
+    case SPS_OPT_FOLD:
+      if (v != 0 && v != 1) return SPS_ERR_ARG;
+      s->fold = v == 1;
       return SPS_OK;
     case SPS_OPT_BRANCH_FORM:
       if (v < 0 || v > 2) return SPS_ERR_ARG;

@@ -205,12 +205,12 @@ void pack_circuit(const std::vector<Pass>& passes, double eps, std::vector<unsig
     r.eps2 = eps * eps;
     r.eps = eps;
     if (p.kind == PASS_FUSED) {
-      r.nops = (uint32_t)p.ops.size();
+      r.nops = p.ngates;
       r.flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
       r.nwords = (uint32_t)p.words.size();
       r.ops_off = (uint32_t)put(p.words.data(), p.words.size() * sizeof(OpWord));
-      r.ph_off = p.phases.empty() ? 0u
-                                  : (uint32_t)put(p.phases.data(), p.phases.size() * sizeof(PhasePair));
+      r.ph_off = p.ftab.empty() ? 0u
+                                : (uint32_t)put(p.ftab.data(), p.ftab.size() * sizeof(double));
       w += bound * (uint64_t)p.ops.size();
     } else {
       r.br_off = (uint32_t)put(&p.br, sizeof(BranchOp));

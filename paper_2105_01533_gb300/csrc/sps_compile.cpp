@@ -227,11 +227,85 @@ void build_expand(Pass* p) {
   }
 }
 
+// ---- known qubits in fused runs ---------------------------------------------------
+// Appends a pure flip (condition c, targets t) to the run. It merges into the
+// previous op when that is a pure flip with the same condition that flips no
+// qubit of the condition: the two then act as one flip of both targets.
+void append_flip(Pass* run, uint64_t c0, uint64_t c1, uint64_t t0, uint64_t t1) {
+  if (!run->ops.empty()) {
+    FOp& prev = run->ops.back();
+    if ((prev.kind & FOP_FLIP) && (prev.kind & ~(FOP_FLIP | FOP_HI)) == 0 && prev.c[0] == c0 &&
+        prev.c[1] == c1 && ((prev.t[0] & c0) | (prev.t[1] & c1)) == 0) {
+      prev.t[0] ^= t0;
+      prev.t[1] ^= t1;
+      set_fop_kind(prev);
+      if ((prev.t[0] | prev.t[1]) == 0) run->ops.pop_back();   // the two cancel
+      return;
+    }
+  }
+  const uint64_t cm[2] = {c0, c1};
+  FOp o = make_op(cm);
+  o.t[0] = t0;
+  o.t[1] = t1;
+  set_fop_kind(o);
+  run->ops.push_back(o);
+}
+
+// Lowers one phase/permutation gate with the qubits known before it resolved:
+// a gate with a control known 0 (or a phase gate whose target is known 0) does
+// nothing; known controls (all 1) leave the condition; an unconditional flip of
+// a known qubit only toggles its value, recorded in pending and applied to the
+// labels later by one flip (the device sees a known qubit's true value only
+// where an op reads or conditionally flips it, which materialises it first).
+void lower_known(const sps_gate& g, Pass* run, const KnownBits& k, uint64_t pending[2]) {
+  if (controls_state(g, k) == 0) return;
+  sps_gate h = g;
+  h.cmask[0] &= ~k.known[0];
+  h.cmask[1] &= ~k.known[1];
+  const uint32_t t = g.t0;
+  const uint64_t tb0 = t < 64 ? 1ull << t : 0ull, tb1 = t >= 64 ? 1ull << (t - 64) : 0ull;
+  auto materialize = [&]() {
+    const uint64_t m0 = pending[0] & tb0, m1 = pending[1] & tb1;
+    if (m0 | m1) {
+      append_flip(run, 0ull, 0ull, m0, m1);
+      pending[0] ^= m0;
+      pending[1] ^= m1;
+    }
+  };
+  switch (g.op) {
+    case SPS_OP_X:
+      if ((h.cmask[0] | h.cmask[1]) == 0 && kb_has(k, t)) {
+        pending[0] ^= tb0;
+        pending[1] ^= tb1;
+        return;
+      }
+      materialize();
+      append_flip(run, h.cmask[0], h.cmask[1], tb0, tb1);
+      return;
+    case SPS_OP_Z: case SPS_OP_S: case SPS_OP_SDG: case SPS_OP_T: case SPS_OP_TDG:
+    case SPS_OP_P: {
+      if (kb_has(k, t) && !kb_val(k, t)) return;   // the target is 0 everywhere
+      lower_perm_diag(h, run);
+      if (kb_has(k, t)) {                           // the target is 1 everywhere
+        FOp& o = run->ops.back();
+        o.c[0] &= ~tb0;
+        o.c[1] &= ~tb1;
+        set_fop_kind(o);
+      }
+      return;
+    }
+    default:   // Y and Rz read the target's value on the device
+      materialize();
+      lower_perm_diag(h, run);
+      return;
+  }
+}
+
 }  // namespace
 
 sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                    uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad, KnownBits* kb,
-                   bool expand) {
+                   bool expand, bool fold) {
   if (max_fused_ops == 0 || max_fused_ops > kMaxFusedOps) max_fused_ops = kDefaultMaxFusedOps;
   out->clear();
   for (size_t i = 0; i < ngates; ++i) {
@@ -242,12 +316,19 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
     }
   }
   KnownBits k = kb ? *kb : KnownBits();
+  const bool fold_known = kb != nullptr && fold;
   Pass* run = nullptr;
   Pass* ex = nullptr;
+  uint64_t pending[2] = {0ull, 0ull};
+  auto close_run = [&]() {
+    if (run && (pending[0] | pending[1])) append_flip(run, 0ull, 0ull, pending[0], pending[1]);
+    pending[0] = pending[1] = 0ull;
+    run = nullptr;
+  };
   for (size_t i = 0; i < ngates; ++i) {
     const sps_gate& g = gates[i];
     if (is_branch(g.op)) {
-      run = nullptr;
+      close_run();
       Pass p;
       p.first_gate = i;
       lower_branch(g, &p);
@@ -271,28 +352,45 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
       continue;
     }
     ex = nullptr;
-    track(g, k);
     const uint32_t slots = g.op == SPS_OP_P ? 1u : (g.op == SPS_OP_RZ ? 2u : 0u);
-    if (run == nullptr || run->ops.size() >= max_fused_ops || run->phases.size() >= kMaxFusedPhases ||
-        run->fire_slots + slots > kMaxFireSlots) {
+    // folding may add two flips (a materialised known qubit, the pending ones)
+    const size_t room = fold_known ? 2 : 0;
+    if (run == nullptr || run->ops.size() + room >= max_fused_ops ||
+        run->phases.size() >= kMaxFusedPhases || run->fire_slots + slots > kMaxFireSlots) {
+      close_run();
       Pass p;
       p.kind = PASS_FUSED;
       p.first_gate = i;
       out->push_back(std::move(p));
       run = &out->back();
     }
-    lower_perm_diag(g, run);
+    if (fold_known)
+      lower_known(g, run, k, pending);
+    else
+      lower_perm_diag(g, run);
+    ++run->ngates;
+    track(g, k);
   }
+  close_run();
   for (Pass& p : *out) {
-    if (p.kind == PASS_FUSED) encode_ops(p.ops, &p.words);
+    if (p.kind == PASS_FUSED) encode_ops(&p);
     if (p.kind == PASS_EXPAND) build_expand(&p);
   }
   if (kb) *kb = k;
   return SPS_OK;
 }
 
-void encode_ops(const std::vector<FOp>& ops, std::vector<OpWord>* words) {
+void encode_ops(Pass* p) {
+  const std::vector<FOp>& ops = p->ops;
+  std::vector<OpWord>* words = &p->words;
   words->clear();
+  p->has_perm = p->has_phase = false;
+  for (const FOp& o : ops) {
+    p->has_perm = p->has_perm || (o.kind & FOP_FLIP);
+    p->has_phase = p->has_phase || (o.kind & (FOP_CNT | FOP_PH));
+  }
+  // fire slots in op order; slot k's factor is the phase its op applies
+  std::vector<double> factor;
   auto form = [](const FOp& o) {
     if (o.kind == FOP_FLIP) return OPS_FLIP64;
     if (o.kind == (FOP_FLIP | FOP_HI)) return OPS_FLIP128;
@@ -309,14 +407,49 @@ void encode_ops(const std::vector<FOp>& ops, std::vector<OpWord>* words) {
       if (f == OPS_FLIP64) {
         words->push_back(OpWord{(uint32_t)o.c[0], (uint32_t)(o.c[0] >> 32), (uint32_t)o.t[0],
                                 (uint32_t)(o.t[0] >> 32)});
-      } else {
-        OpWord w[3];
-        static_assert(sizeof(w) == sizeof(FOp), "FOp is three words");
-        std::memcpy(w, &o, sizeof(FOp));
-        words->insert(words->end(), w, w + (f == OPS_FLIP128 ? 2 : 3));
+        continue;
       }
+      FOp e = o;
+      if (f == OPS_GEN) {
+        uint32_t f0 = 0xFF, f1 = 0xFF;
+        if (o.ph != NO_PH) {
+          const PhasePair& pp = p->phases[o.ph];
+          f0 = (uint32_t)(factor.size() / 2);
+          factor.push_back(pp.re0);
+          factor.push_back(pp.im0);
+          if (o.sbit != NO_SEL) {
+            f1 = (uint32_t)(factor.size() / 2);
+            factor.push_back(pp.re1);
+            factor.push_back(pp.im1);
+          }
+        }
+        e.ph = (uint16_t)(f0 | (f1 << 8));
+      }
+      OpWord w[3];
+      static_assert(sizeof(w) == sizeof(FOp), "FOp is three words");
+      std::memcpy(w, &e, sizeof(FOp));
+      words->insert(words->end(), w, w + (f == OPS_FLIP128 ? 2 : 3));
     }
     i = j;
+  }
+  // per-8-slot tables by doubling: entry v = entry (v without its top bit)
+  // times the factor of that bit
+  const uint32_t nslots = (uint32_t)(factor.size() / 2);
+  const uint32_t nch = (nslots + 7) / 8;
+  p->ftab.assign((size_t)nch * 256 * 2, 0.0);
+  for (uint32_t c = 0; c < nch; ++c) {
+    double* t = &p->ftab[(size_t)c * 256 * 2];
+    t[0] = 1.0;
+    for (uint32_t b = 0; b < 8; ++b) {
+      const uint32_t slot = 8 * c + b;
+      const double fr = slot < nslots ? factor[2 * slot] : 1.0;
+      const double fi = slot < nslots ? factor[2 * slot + 1] : 0.0;
+      for (uint32_t u = 0; u < (1u << b); ++u) {
+        const uint32_t v = u | (1u << b);
+        t[2 * v] = t[2 * u] * fr - t[2 * u + 1] * fi;
+        t[2 * v + 1] = t[2 * u] * fi + t[2 * u + 1] * fr;
+      }
+    }
   }
 }
 
@@ -358,11 +491,13 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
       so.list_n = (uint16_t)(conds.size() - 3);
       out->list.insert(out->list.end(), conds.begin() + 3, conds.end());
     }
-    if (o.t[0] | o.t[1]) {
+    std::vector<uint8_t> tbits;   // a merged flip has several targets, one condition
+    for (int w = 0; w < 2; ++w)
+      for (int b = 0; b < 64; ++b)
+        if ((o.t[w] >> b) & 1ull) tbits.push_back((uint8_t)(64 * w + b));
+    if (!tbits.empty()) {
       so.kind |= SOP_FLIP;
-      for (int w = 0; w < 2; ++w)
-        for (int b = 0; b < 64; ++b)
-          if ((o.t[w] >> b) & 1ull) so.t = (uint8_t)(64 * w + b);
+      so.t = tbits[0];
     }
     if (o.sbit != NO_SEL) {
       so.kind |= SOP_SEL;
@@ -384,6 +519,13 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
       }
     }
     out->ops.push_back(so);
+    // further targets: the same condition (no target is in it), flip only
+    for (size_t k = 1; k < tbits.size(); ++k) {
+      SOp x = so;
+      x.kind = (uint8_t)(SOP_FLIP | (so.kind & SOP_LIST));
+      x.t = tbits[k];
+      out->ops.push_back(x);
+    }
   }
   out->aux_bits = aux;
   out->na = (aux + 31) / 32;

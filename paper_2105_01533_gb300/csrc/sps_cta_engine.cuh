@@ -74,24 +74,18 @@ __device__ __forceinline__ uint32_t lookup(const uint32_t* tab, uint32_t mask, c
 template <int KW>
 __device__ void fused_pass(const unsigned char* arena, const RunPass& rp, const Bufs& A, uint32_t n) {
   const uint4* ops = reinterpret_cast<const uint4*>(arena + rp.ops_off);
-  const PhasePair* ph = reinterpret_cast<const PhasePair*>(arena + rp.ph_off);
+  const double2* ftab = reinterpret_cast<const double2*>(arena + rp.ph_off);
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
     uint64_t k0 = A.lo[i], k1 = A.hi[i];
     uint32_t cnt = 0;
-    bool any = false;
-    double acc_re = 1.0, acc_im = 0.0;
-    walk_ops<KW>(ops, rp.nwords, ph, k0, k1, cnt, any, acc_re, acc_im);
+    uint64_t fire = 0ull;
+    walk_ops<KW>(ops, rp.nwords, k0, k1, cnt, fire);
     A.lo[i] = k0;
     A.hi[i] = k1;
     cnt &= 7u;
-    if (cnt != 0u || any) {
+    if (cnt != 0u || fire != 0ull) {
       double re = A.re[i], im = A.im[i];
-      if (any) {
-        const double nr = re * acc_re - im * acc_im;
-        const double ni = re * acc_im + im * acc_re;
-        re = nr;
-        im = ni;
-      }
+      apply_fire(fire, ftab, re, im);
       apply_pi4(cnt, re, im);
       A.re[i] = re;
       A.im[i] = im;

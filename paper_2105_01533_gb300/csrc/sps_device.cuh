@@ -112,16 +112,14 @@ __device__ __forceinline__ void unknown_label_masks(Ctl* ctl, uint32_t b) {
 // Runs a fused pass's encoded op stream (OPS_* runs of 16-byte words, in
 // shared or global memory; every thread reads the same word, a broadcast) on
 // E labels at once: flips each label in place, adds the pi/4 steps to cnt and
-// multiplies the arbitrary phases into acc. A label is handled as four 32-bit
-// words, so a condition test or a flip is one three-input logic instruction
-// per word; the E labels are independent chains, which the scheduler
-// interleaves (the walk of one label is a chain of dependent instructions).
+// sets the fire-slot bit of every arbitrary phase that applies (the product
+// of those phases is taken afterwards, apply_fire). A label is handled as
+// four 32-bit words, so a condition test or a flip is one three-input logic
+// instruction per word.
 template <int KW, int E>
 __device__ __forceinline__ void walk_ops_n(const uint4* __restrict__ sq, uint32_t nwords,
-                                           const PhasePair* __restrict__ ph, uint64_t (&k0)[E],
-                                           uint64_t (&k1)[E], uint32_t (&cnt)[E],
-                                           bool (&any_ph)[E], double (&acc_re)[E],
-                                           double (&acc_im)[E]) {
+                                           uint64_t (&k0)[E], uint64_t (&k1)[E],
+                                           uint32_t (&cnt)[E], uint64_t (&fire)[E]) {
   uint32_t w0[E], w1[E], w2[E], w3[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -175,7 +173,7 @@ __device__ __forceinline__ void walk_ops_n(const uint4* __restrict__ sq, uint32_
         const uint2 meta = *reinterpret_cast<const uint2*>(q + 3 * j + 2);
         const uint32_t kind = meta.x >> 24;   // a0 | a1 << 8 | sbit << 16 | kind << 24
         const uint32_t b = (meta.x >> 16) & 0xFFu;
-        const PhasePair* pp = ph + (meta.y & 0xFFFFu);
+        const uint32_t f0 = meta.y & 0xFFu, f1 = (meta.y >> 8) & 0xFFu;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           uint32_t miss = ((w0[e] & c.x) ^ c.x) | ((w1[e] & c.y) ^ c.y);
@@ -187,15 +185,7 @@ __device__ __forceinline__ void walk_ops_n(const uint4* __restrict__ sq, uint32_
             sel = (word >> (b & 31u)) & 1u;
           }
           cnt[e] += cond ? (sel ? (meta.x >> 8) & 0xFFu : meta.x & 0xFFu) : 0u;
-          if ((kind & FOP_PH) && cond) {
-            const double pr = sel ? pp->re1 : pp->re0;
-            const double pi = sel ? pp->im1 : pp->im0;
-            const double nr = acc_re[e] * pr - acc_im[e] * pi;
-            const double ni = acc_re[e] * pi + acc_im[e] * pr;
-            acc_re[e] = nr;
-            acc_im[e] = ni;
-            any_ph[e] = true;
-          }
+          if ((kind & FOP_PH) && cond) fire[e] |= 1ull << (sel ? f1 : f0);
           const uint32_t m = cond ? ~0u : 0u;
           w0[e] ^= t.x & m;
           w1[e] ^= t.y & m;
@@ -215,23 +205,33 @@ __device__ __forceinline__ void walk_ops_n(const uint4* __restrict__ sq, uint32_
   }
 }
 
-// One label at a time (the one-block engine).
+// One label at a time.
 template <int KW>
 __device__ __forceinline__ void walk_ops(const uint4* __restrict__ sq, uint32_t nwords,
-                                         const PhasePair* __restrict__ ph, uint64_t& k0,
-                                         uint64_t& k1, uint32_t& cnt, bool& any_ph,
-                                         double& acc_re, double& acc_im) {
-  uint64_t a0[1] = {k0}, a1[1] = {k1};
+                                         uint64_t& k0, uint64_t& k1, uint32_t& cnt,
+                                         uint64_t& fire) {
+  uint64_t a0[1] = {k0}, a1[1] = {k1}, f[1] = {fire};
   uint32_t c[1] = {cnt};
-  bool an[1] = {any_ph};
-  double ar[1] = {acc_re}, ai[1] = {acc_im};
-  walk_ops_n<KW, 1>(sq, nwords, ph, a0, a1, c, an, ar, ai);
+  walk_ops_n<KW, 1>(sq, nwords, a0, a1, c, f);
   k0 = a0[0];
   k1 = a1[0];
   cnt = c[0];
-  any_ph = an[0];
-  acc_re = ar[0];
-  acc_im = ai[0];
+  fire = f[0];
+}
+
+// Multiplies an amplitude by the phases of the set fire-slot bits, one table
+// entry (the product of up to 8 slots' phases) per non-zero byte.
+__device__ __forceinline__ void apply_fire(uint64_t fire, const double2* __restrict__ tab,
+                                           double& re, double& im) {
+  for (uint32_t c = 0; fire != 0ull; ++c, fire >>= 8) {
+    const uint32_t v = (uint32_t)(fire & 0xFFull);
+    if (v == 0u) continue;
+    const double2 t = tab[c * 256u + v];
+    const double nr = re * t.x - im * t.y;
+    const double ni = re * t.y + im * t.x;
+    re = nr;
+    im = ni;
+  }
 }
 
 // Multiplies an amplitude by e^{i pi cnt / 4} (cnt mod 8), exactly for the

@@ -118,13 +118,19 @@ struct BsPass {
 //   OPS_FLIP64   count words {c.lo, c.hi, t.lo, t.hi} (32-bit halves): a pure
 //                flip whose condition and target lie in qubits 0..63;
 //   OPS_FLIP128  count x 2 words: the 128-bit condition, then the target;
-//   OPS_GEN      count x 3 words: FOp records (phases, counters, selectors).
+//   OPS_GEN      count x 3 words: FOp records (phases, counters, selectors),
+//                except that the ph field holds the op's fire slots f0 | f1 << 8
+//                (f1 for sel = 1, 0xFF if none): an arbitrary phase that applies
+//                sets its slot bit, and the product of the phases of the set
+//                bits is taken at the end from per-8-slot tables.
 // A flip costs the walk one load and five logic instructions, a general op
 // about four times that.
 struct OpWord { uint32_t x, y, z, w; };
 static_assert(sizeof(OpWord) == 16, "OpWord layout");
 constexpr uint32_t OPS_FLIP64 = 1, OPS_FLIP128 = 2, OPS_GEN = 3;
-void encode_ops(const std::vector<FOp>& ops, std::vector<OpWord>* words);
+struct Pass;
+// Encodes the pass's ops (p.words) and builds its fire-slot tables (p.ftab).
+void encode_ops(Pass* p);
 
 // ---- a compiled pass -----------------------------------------------------------
 enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2, PASS_EXPAND = 3 };
@@ -146,9 +152,11 @@ constexpr uint32_t kMaxExpandGates = 24;
 struct Pass {
   PassKind kind;
   uint64_t first_gate;
+  uint32_t ngates = 0;      // fused: gates of the run (its ops may be fewer or more)
   // fused
   std::vector<FOp> ops;
   std::vector<OpWord> words;  // ops encoded for the direct walk (encode_ops)
+  std::vector<double> ftab;   // fire-slot tables: chunks x 256 x (re, im) (encode_ops)
   std::vector<PhasePair> phases;
   bool has_perm = false;    // some op flips label bits
   bool has_phase = false;   // some op changes amplitudes
@@ -168,9 +176,9 @@ struct Pass {
 // One pass of a small-state run (k_small_run), stored in the plan arena.
 struct RunPass {            // 64 bytes
   uint32_t kind;            // PASS_FUSED or PASS_BRANCH
-  uint32_t nops;            // fused: ops
+  uint32_t nops;            // fused: gates of the run (the update count)
   uint32_t ops_off;         // byte offset of the encoded op stream in the arena
-  uint32_t ph_off;          // byte offset of the PhasePair array
+  uint32_t ph_off;          // fused: byte offset of the fire-slot tables
   uint32_t br_off;          // byte offset of the BranchOp
   uint32_t flags;           // bit 0: permutes, bit 1: changes amplitudes
   uint32_t pass_serial;
@@ -197,10 +205,11 @@ constexpr uint32_t kDefaultMaxFusedOps = kMaxFusedOps;
 
 // Validates and compiles; on a bad record returns SPS_ERR_ARG with *bad set.
 // With kb (nullable) the compiler tracks the known-constant qubits through the
-// gates (updating *kb on success) and, if expand, forms expansion passes.
+// gates (updating *kb on success); if expand it forms expansion passes, if
+// fold it resolves known qubits in fused runs (lower_known).
 sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                    uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad,
-                   KnownBits* kb = nullptr, bool expand = false);
+                   KnownBits* kb = nullptr, bool expand = false, bool fold = false);
 
 // ---- device-side control block -------------------------------------------------
 constexpr int kMaskStripes = 32;
@@ -274,9 +283,9 @@ struct LaunchCfg {
 // `plog` (nullable) receives two words per launch for profiling: entries read
 // and entries in the state afterwards.
 int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots);
-// words / ph: the pass's encoded op stream and phase pairs in device memory
+// words / ftab: the pass's encoded op stream and fire-slot tables in device memory
 int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
-                 const OpWord* words, const PhasePair* ph, uint64_t nnz_bound, uint32_t mg,
+                 const OpWord* words, const double* ftab, uint64_t nnz_bound, uint32_t mg,
                  unsigned long long* plog);
 struct BranchLaunch {
   BranchOp op;
@@ -295,6 +304,7 @@ struct BsLaunch {
   const uint8_t* list;
   const double* tables;
   uint32_t nops, nw, na, nchunks;
+  uint32_t ngates;          // gates of the run, for the update count
   uint32_t has_perm, has_phase, has_cnt, list_len;
   uint32_t groups;          // groups of 32 entries per warp tile (even, 2..32), 0 = choose
   uint32_t mg;              // label-mask buffers (MaskRing)

@@ -38,8 +38,8 @@ using namespace dev;
 // step and wait one L2 round trip for every new 128-byte line of the stream.
 struct FusedArgs {
   const uint4* words;
-  const PhasePair* ph;
-  uint32_t nwords, nph, nops, has_perm, has_phase, mg;
+  const double2* ftab;   // fire-slot tables (read through L1; a few entries per label)
+  uint32_t nwords, ngates, has_perm, has_phase, mg;
 };
 
 template <int KW>
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedA
   }
   if (ctl->status != 0u) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->updates += n * a.nops;
+    ctl->updates += n * a.ngates;
     if (a.has_perm) reset_label_masks(ctl, mg_rs(a.mg));
   }
   const SoA s = pick(bufs, ctl->cur);
@@ -62,20 +62,13 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedA
   uint64_t k0 = i < n ? s.lo[i] : 0ull;
   uint64_t k1 = (KW == 2 && i < n) ? s.hi[i] : 0ull;
   extern __shared__ uint4 fsm[];
-  PhasePair* sph = reinterpret_cast<PhasePair*>(fsm + a.nwords);
   for (uint32_t w = threadIdx.x; w < a.nwords; w += blockDim.x) fsm[w] = a.words[w];
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(a.ph);
-    uint4* dst = reinterpret_cast<uint4*>(sph);
-    for (uint32_t w = threadIdx.x; w < 2 * a.nph; w += blockDim.x) dst[w] = src[w];
-  }
   __syncthreads();
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the new labels
   for (; i < n; i += stride) {
     uint32_t cnt = 0;
-    bool any_ph = false;
-    double acc_re = 1.0, acc_im = 0.0;
-    walk_ops<KW>(fsm, a.nwords, sph, k0, k1, cnt, any_ph, acc_re, acc_im);
+    uint64_t fire = 0ull;
+    walk_ops<KW>(fsm, a.nwords, k0, k1, cnt, fire);
     if (a.has_perm) {
       s.lo[i] = k0;
       if (KW == 2) s.hi[i] = k1;
@@ -85,14 +78,9 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedA
       ma1 &= k1;
     }
     cnt &= 7u;
-    if (a.has_phase && (cnt != 0u || any_ph)) {
+    if (a.has_phase && (cnt != 0u || fire != 0ull)) {
       double re = s.re[i], im = s.im[i];
-      if (any_ph) {
-        const double nr = re * acc_re - im * acc_im;
-        const double ni = re * acc_im + im * acc_re;
-        re = nr;
-        im = ni;
-      }
+      apply_fire(fire, a.ftab, re, im);
       apply_pi4(cnt, re, im);
       s.re[i] = re;
       s.im[i] = im;
@@ -104,6 +92,11 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedA
     }
   }
   if (a.has_perm) merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
+}
+
+// A fused run whose gates all resolved on the host still counts its updates.
+__global__ void k_count_updates(Ctl* ctl, uint32_t ngates) {
+  if (ctl->status == 0u) ctl->updates += ctl->nnz * ngates;
 }
 
 // ---------------------------------------------------------------------------
@@ -151,7 +144,7 @@ struct BsArgs {
   const SOp* ops;
   const uint8_t* list;
   const double* tables;
-  uint32_t nops, nw, na, nchunks;
+  uint32_t nops, ngates, nw, na, nchunks;
   uint32_t has_perm, has_phase, has_cnt, list_len;
   uint32_t groups;   // groups of 32 entries per warp tile (even, 2..32)
   uint32_t mg;       // label-mask buffers (MaskRing)
@@ -174,7 +167,7 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
   }
   if (ctl->status != 0u) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->updates += n * a.nops;
+    ctl->updates += n * a.ngates;
     if (a.has_perm) reset_label_masks(ctl, mg_rs(a.mg));
   }
   // stage the op list, the phase tables and the extra-condition list
@@ -643,6 +636,7 @@ int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uin
   a.list = b.list;
   a.tables = b.tables;
   a.nops = b.nops;
+  a.ngates = b.ngates;
   a.nw = b.nw;
   a.na = b.na;
   a.nchunks = b.nchunks;
@@ -706,21 +700,23 @@ int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots) {
 }
 
 int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
-                 const OpWord* words, const PhasePair* ph, uint64_t nnz_bound, uint32_t mg,
+                 const OpWord* words, const double* ftab, uint64_t nnz_bound, uint32_t mg,
                  unsigned long long* plog) {
-  if (p.ops.empty()) return 0;
+  if (p.ops.empty()) {   // every gate resolved on the host: only the update count
+    k_count_updates<<<1, 1, 0, (cudaStream_t)lc.stream>>>(ctl, p.ngates);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  }
   FusedArgs a;
   a.words = reinterpret_cast<const uint4*>(words);
-  a.ph = ph;
+  a.ftab = reinterpret_cast<const double2*>(ftab);
   a.nwords = (uint32_t)p.words.size();
-  a.nph = (uint32_t)p.phases.size();
-  a.nops = (uint32_t)p.ops.size();
+  a.ngates = p.ngates;
   a.has_perm = p.has_perm;
   a.has_phase = p.has_phase;
   a.mg = mg;
   const int blocks = grid_for(nnz_bound, lc.threads, lc.max_blocks);
-  // at most 4 words per op and 96 phases: <= 35 KB, under the default 48 KB
-  const size_t smem = 16 * (size_t)a.nwords + sizeof(PhasePair) * a.nph;
+  // at most 4 words per op: <= 32 KB, under the default 48 KB
+  const size_t smem = 16 * (size_t)a.nwords;
   cudaStream_t st = (cudaStream_t)lc.stream;
   if (key_words == 1)
     k_fused<1><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
