@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <memory>
 #include <vector>
 
 #include "sps.h"
@@ -27,6 +28,28 @@ constexpr size_t kProfileCap = 1 << 16;   // profiled launches kept between read
 struct Allocation {
   void* ptr;
   size_t bytes;
+};
+
+// A compiled apply: its passes, how they are launched and the arena image
+// they read. A state keeps the last one: an apply with the same gates, prune
+// threshold, options, starting knowledge and nonzero bound reuses it, and its
+// image while the arena still holds it, instead of compiling and uploading.
+struct ApplyPlan {
+  std::vector<sps_gate> gates;
+  uint64_t eps_bits = 0;
+  KnownBits kb_in, kb_out;
+  uint64_t bound_in = 0;
+  std::vector<uint64_t> opts;
+  std::vector<Pass> passes;
+  std::vector<size_t> seg_end;      // > 0: a small-state run starts here, ends there
+  std::vector<uint64_t> bound_at;   // nonzero bound before each pass
+  std::vector<BsPass> bs;           // bit-sliced plans of long fused runs
+  std::vector<size_t> bs_off;
+  std::vector<size_t> run_off;      // small run: its RunPass array; direct fused pass: its
+                                    // op stream; expansion: its factor tables
+  std::vector<size_t> ph_off;       // direct fused pass: its fire-slot tables; expansion:
+                                    // its mask tables
+  std::vector<unsigned char> image;
 };
 
 }  // namespace
@@ -53,6 +76,8 @@ struct sps_state {
   uint32_t itab_log2 = 8;
   uint32_t epoch = 0;
   MaskRing masks;             // rotation of the device label-mask buffers
+  std::unique_ptr<ApplyPlan> plan;   // the last compiled apply
+  bool plan_resident = false;        // the arena holds plan->image
   KnownBits kb;               // qubits known constant once every enqueued pass ran
   bool expand = true;         // SPS_OPT_EXPAND
   bool fold = true;           // SPS_OPT_FOLD
@@ -530,43 +555,54 @@ static uint64_t bound_after(const Pass& p, uint64_t b, uint64_t capacity) {
   return b < capacity ? b : capacity;
 }
 
-sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
-                     size_t* failed_gate) {
-  if (!s || (ngates && !gates) || !(prune_eps >= 0.0)) return SPS_ERR_ARG;
-  std::vector<Pass> passes;
-  size_t bad = 0;
-  const sps_status cs =
-      compile(gates, ngates, s->nqubits, s->max_fused_ops, &passes, &bad, &s->kb, s->expand,
-              s->fold);
-  if (cs != SPS_OK) {
-    if (failed_gate) *failed_gate = bad;
-    return cs;
-  }
-  const LaunchCfg lc = cfg_of(s);
-  const uint32_t limit = s->probe_limit ? s->probe_limit : (uint32_t)(s->table_slots > 0xFFFFFFFFull ? 0xFFFFFFFFu : s->table_slots);
+// Options the compiled plan and its image depend on.
+static std::vector<uint64_t> plan_options(const sps_state* s) {
+  return {s->nqubits, (uint64_t)s->kw, s->capacity, s->max_fused_ops, s->expand ? 1ull : 0ull,
+          s->fold ? 1ull : 0ull, s->small_cap, s->bitslice_min_ops, s->bitslice_min_nnz};
+}
+
+static bool plan_matches(const ApplyPlan& p, const sps_state* s, const sps_gate* gates,
+                         size_t ngates, uint64_t eps_bits, const std::vector<uint64_t>& opts) {
+  return p.gates.size() == ngates && p.eps_bits == eps_bits && p.bound_in == s->nnz_bound &&
+         p.kb_in.known[0] == s->kb.known[0] && p.kb_in.known[1] == s->kb.known[1] &&
+         p.kb_in.val[0] == s->kb.val[0] && p.kb_in.val[1] == s->kb.val[1] && p.opts == opts &&
+         (ngates == 0 || std::memcmp(p.gates.data(), gates, ngates * sizeof(sps_gate)) == 0);
+}
+
+// Compiles an apply: passes, small-state segments, bit-sliced plans and the
+// arena image. Small-run records hold each pass's index in the apply (+1) and
+// its first gate; the kernel adds the launch's serial base and apply serial.
+static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
+                             ApplyPlan* P, size_t* bad) {
+  P->kb_out = s->kb;
+  const sps_status cs = compile(gates, ngates, s->nqubits, s->max_fused_ops, &P->passes, bad,
+                                &P->kb_out, s->expand, s->fold);
+  if (cs != SPS_OK) return cs;
+  const std::vector<Pass>& passes = P->passes;
+  const size_t np = passes.size();
   // 1. segments of consecutive passes that a small-state run can take: the
   //    nonzero bound (doubling per branching pass) stays within small_cap
-  std::vector<size_t> seg_end(passes.size(), 0);   // > 0: a run starts here, ends there
-  std::vector<uint64_t> bound_at(passes.size(), 0);  // nonzero bound before each pass
+  P->seg_end.assign(np, 0);
+  P->bound_at.assign(np, 0);
   {
     uint64_t b = s->nnz_bound;
-    for (size_t i = 0; i < passes.size(); ++i) {
-      bound_at[i] = b;
+    for (size_t i = 0; i < np; ++i) {
+      P->bound_at[i] = b;
       b = bound_after(passes[i], b, s->capacity);
     }
     b = s->nnz_bound;
-    for (size_t i = 0; i < passes.size();) {
+    for (size_t i = 0; i < np;) {
       if (s->small_cap && b <= s->small_cap) {
         size_t j = i;
         uint64_t bb = b;
-        while (j < passes.size() && passes[j].kind != PASS_EXPAND) {
+        while (j < np && passes[j].kind != PASS_EXPAND) {
           const uint64_t after = bound_after(passes[j], bb, s->capacity);
           if (after > s->small_cap) break;
           bb = after;
           ++j;
         }
         if (j > i) {
-          seg_end[i] = j;
+          P->seg_end[i] = j;
           b = bb;
           i = j;
           continue;
@@ -576,113 +612,136 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       ++i;
     }
   }
-  // 2. device data: bit-sliced plans of long fused runs outside small runs, and
-  //    the records of the small runs, packed into one upload
-  std::vector<BsPass> bs(passes.size());
-  std::vector<size_t> bs_off(passes.size(), 0);
-  std::vector<size_t> run_off(passes.size(), 0);   // small run: its RunPass array; direct
-                                                   // fused pass: its op stream; expansion:
-                                                   // its factor tables
-  std::vector<size_t> ph_off(passes.size(), 0);    // direct fused pass: its fire-slot tables;
-                                                   // expansion: its mask tables
-  size_t arena_bytes = 0;
-  std::vector<unsigned char> blob;   // small-run payloads, appended after the bit-sliced plans
-  {
-    size_t i = 0;
-    while (i < passes.size()) {
-      if (seg_end[i]) {
-        i = seg_end[i];
-        continue;
-      }
+  // 2. device data: bit-sliced plans of long fused runs outside small runs,
+  //    then the op streams, tables and small-run records
+  P->bs.assign(np, BsPass());
+  P->bs_off.assign(np, 0);
+  P->run_off.assign(np, 0);
+  P->ph_off.assign(np, 0);
+  size_t bs_bytes = 0;
+  for (size_t i = 0; i < np;) {
+    if (P->seg_end[i]) {
+      i = P->seg_end[i];
+      continue;
+    }
+    const Pass& p = passes[i];
+    if (p.kind == PASS_FUSED && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops &&
+        P->bound_at[i] >= s->bitslice_min_nnz) {
+      build_bitslice(p, s->nqubits, &P->bs[i]);
+      P->bs_off[i] = bs_bytes;
+      bs_bytes += align16(P->bs[i].ops.size() * sizeof(SOp)) +
+                  align16(P->bs[i].tables.size() * 8) + align16(P->bs[i].list.size());
+    }
+    ++i;
+  }
+  std::vector<unsigned char>& img = P->image;
+  img.assign(bs_bytes, 0);
+  for (size_t i = 0; i < np; ++i) {
+    const BsPass& b = P->bs[i];
+    if (b.ops.empty()) continue;
+    unsigned char* dst = img.data() + P->bs_off[i];
+    std::memcpy(dst, b.ops.data(), b.ops.size() * sizeof(SOp));
+    dst += align16(b.ops.size() * sizeof(SOp));
+    std::memcpy(dst, b.tables.data(), b.tables.size() * 8);
+    dst += align16(b.tables.size() * 8);
+    if (!b.list.empty()) std::memcpy(dst, b.list.data(), b.list.size());
+  }
+  auto put = [&](const void* src, size_t bytes) {
+    const size_t at = img.size();
+    img.resize(align16(at + bytes), 0);
+    std::memcpy(img.data() + at, src, bytes);
+    return at;
+  };
+  for (size_t i = 0; i < np;) {
+    if (!P->seg_end[i]) {
       const Pass& p = passes[i];
-      if (p.kind == PASS_FUSED && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops &&
-          bound_at[i] >= s->bitslice_min_nnz) {
-        build_bitslice(p, s->nqubits, &bs[i]);
-        bs_off[i] = arena_bytes;
-        arena_bytes += align16(bs[i].ops.size() * sizeof(SOp)) + align16(bs[i].tables.size() * 8) +
-                       align16(bs[i].list.size());
+      if (p.kind == PASS_FUSED && P->bs[i].ops.empty()) {   // direct fused pass
+        P->run_off[i] = put(p.words.data(), p.words.size() * sizeof(OpWord));
+        if (!p.ftab.empty()) P->ph_off[i] = put(p.ftab.data(), p.ftab.size() * sizeof(double));
+      }
+      if (p.kind == PASS_EXPAND) {   // factor tables, then mask tables
+        P->run_off[i] = put(p.ex_f.data(), p.ex_f.size() * sizeof(double));
+        P->ph_off[i] = put(p.ex_m.data(), p.ex_m.size() * sizeof(uint64_t));
       }
       ++i;
+      continue;
     }
-  }
-  {
-    uint32_t serial = s->pass_serial;
-    const uint64_t next_apply = (uint64_t)s->apply_serial + 1;
-    size_t i = 0;
-    // offsets are from the arena base: the blob follows the bit-sliced plans
-    const size_t base = arena_bytes;
-    auto put = [&](const void* src, size_t bytes) {
-      const size_t at = blob.size();
-      blob.resize(align16(at + bytes), 0);
-      std::memcpy(blob.data() + at, src, bytes);
-      return base + at;
-    };
-    while (i < passes.size()) {
-      if (!seg_end[i]) {
-        const Pass& p = passes[i];
-        if (p.kind == PASS_FUSED && bs[i].ops.empty()) {   // direct fused pass
-          run_off[i] = put(p.words.data(), p.words.size() * sizeof(OpWord));
-          if (!p.ftab.empty()) ph_off[i] = put(p.ftab.data(), p.ftab.size() * sizeof(double));
-        }
-        if (p.kind == PASS_EXPAND) {   // factor tables, then mask tables
-          run_off[i] = put(p.ex_f.data(), p.ex_f.size() * sizeof(double));
-          ph_off[i] = put(p.ex_m.data(), p.ex_m.size() * sizeof(uint64_t));
-        }
-        ++serial;
-        ++i;
-        continue;
+    const size_t j = P->seg_end[i];
+    std::vector<RunPass> recs(j - i);
+    for (size_t k = i; k < j; ++k) {
+      const Pass& p = passes[k];
+      RunPass& r = recs[k - i];
+      std::memset(&r, 0, sizeof(r));
+      r.kind = p.kind;
+      r.pass_serial = (uint32_t)(k + 1);
+      r.fail_tag = p.first_gate & 0xFFFFFFFFull;
+      r.eps2 = prune_eps * prune_eps;
+      r.eps = prune_eps;
+      if (p.kind == PASS_FUSED) {
+        r.nops = p.ngates;
+        r.nwords = (uint32_t)p.words.size();
+        r.flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
+        r.ops_off = (uint32_t)put(p.words.data(), p.words.size() * sizeof(OpWord));
+        r.ph_off = p.ftab.empty() ? 0u : (uint32_t)put(p.ftab.data(), p.ftab.size() * sizeof(double));
+      } else {
+        r.br_off = (uint32_t)put(&p.br, sizeof(BranchOp));
       }
-      const size_t j = seg_end[i];
-      std::vector<RunPass> recs(j - i);
-      std::vector<size_t> payload(j - i, 0);
-      for (size_t k = i; k < j; ++k) {
-        const Pass& p = passes[k];
-        RunPass& r = recs[k - i];
-        std::memset(&r, 0, sizeof(r));
-        r.kind = p.kind;
-        r.pass_serial = ++serial;
-        r.fail_tag = (next_apply << 32) | (p.first_gate & 0xFFFFFFFFull);
-        r.eps2 = prune_eps * prune_eps;
-        r.eps = prune_eps;
-        if (p.kind == PASS_FUSED) {
-          r.nops = p.ngates;
-          r.nwords = (uint32_t)p.words.size();
-          r.flags = (p.has_perm ? 1u : 0u) | (p.has_phase ? 2u : 0u);
-          r.ops_off = (uint32_t)put(p.words.data(), p.words.size() * sizeof(OpWord));
-          r.ph_off = p.ftab.empty() ? 0u : (uint32_t)put(p.ftab.data(), p.ftab.size() * sizeof(double));
-        } else {
-          r.br_off = (uint32_t)put(&p.br, sizeof(BranchOp));
-        }
-      }
-      run_off[i] = put(recs.data(), recs.size() * sizeof(RunPass));
-      i = j;
     }
+    P->run_off[i] = put(recs.data(), recs.size() * sizeof(RunPass));
+    i = j;
   }
-  const size_t blob_base = arena_bytes;
-  arena_bytes += blob.size();
-  if (arena_bytes) {
-    const sps_status as = ensure_arena(s, arena_bytes);
+  return SPS_OK;
+}
+
+sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
+                     size_t* failed_gate) {
+  if (!s || (ngates && !gates) || !(prune_eps >= 0.0)) return SPS_ERR_ARG;
+  uint64_t eps_bits;
+  std::memcpy(&eps_bits, &prune_eps, sizeof(eps_bits));
+  std::vector<uint64_t> opts = plan_options(s);
+  if (!s->plan || !plan_matches(*s->plan, s, gates, ngates, eps_bits, opts)) {
+    std::unique_ptr<ApplyPlan> np(new (std::nothrow) ApplyPlan());
+    if (!np) return SPS_ERR_OOM;
+    size_t bad = 0;
+    const sps_status cs = build_plan(s, gates, ngates, prune_eps, np.get(), &bad);
+    if (cs != SPS_OK) {
+      if (failed_gate) *failed_gate = bad;
+      return cs;
+    }
+    np->gates.assign(gates, gates + ngates);
+    np->eps_bits = eps_bits;
+    np->kb_in = s->kb;
+    np->bound_in = s->nnz_bound;
+    np->opts = std::move(opts);
+    s->plan = std::move(np);
+    s->plan_resident = false;
+  }
+  const ApplyPlan& P = *s->plan;
+  if (!s->plan_resident && !P.image.empty()) {
+    const sps_status as = ensure_arena(s, P.image.size());
     if (as != SPS_OK) return as;
     sps_state::Staging* stg = nullptr;
-    const sps_status ss = take_staging(s, arena_bytes, &stg);
+    const sps_status ss = take_staging(s, P.image.size(), &stg);
     if (ss != SPS_OK) return ss;
-    for (size_t i = 0; i < passes.size(); ++i) {
-      if (bs[i].ops.empty()) continue;
-      unsigned char* dst = stg->host + bs_off[i];
-      std::memcpy(dst, bs[i].ops.data(), bs[i].ops.size() * sizeof(SOp));
-      dst += align16(bs[i].ops.size() * sizeof(SOp));
-      std::memcpy(dst, bs[i].tables.data(), bs[i].tables.size() * 8);
-      dst += align16(bs[i].tables.size() * 8);
-      if (!bs[i].list.empty()) std::memcpy(dst, bs[i].list.data(), bs[i].list.size());
-    }
-    if (!blob.empty()) std::memcpy(stg->host + blob_base, blob.data(), blob.size());
+    std::memcpy(stg->host, P.image.data(), P.image.size());
     // runs in stream order after earlier kernels that read the arena
-    if (cudaMemcpyAsync(s->arena, stg->host, arena_bytes, cudaMemcpyHostToDevice, s->stream) !=
+    if (cudaMemcpyAsync(s->arena, stg->host, P.image.size(), cudaMemcpyHostToDevice, s->stream) !=
             cudaSuccess ||
         cudaEventRecord(stg->copied, s->stream) != cudaSuccess)
       return cuda_ok(cudaGetLastError());
     stg->pending = true;
   }
+  s->plan_resident = true;
+  s->kb = P.kb_out;
+  const std::vector<Pass>& passes = P.passes;
+  const std::vector<size_t>& seg_end = P.seg_end;
+  const std::vector<BsPass>& bs = P.bs;
+  const std::vector<size_t>& bs_off = P.bs_off;
+  const std::vector<size_t>& run_off = P.run_off;
+  const std::vector<size_t>& ph_off = P.ph_off;
+  const LaunchCfg lc = cfg_of(s);
+  const uint32_t limit = s->probe_limit ? s->probe_limit : (uint32_t)(s->table_slots > 0xFFFFFFFFull ? 0xFFFFFFFFu : s->table_slots);
+  const uint32_t serial_base = s->pass_serial;
   ++s->apply_serial;
   for (size_t pi = 0; pi < passes.size(); ++pi) {
     const Pass& p = passes[pi];
@@ -692,8 +751,8 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       for (size_t k = pi; k < j; ++k) nbranch += passes[k].kind == PASS_BRANCH ? 1u : 0u;
       ProfScope ps(s, 4, s->pass_serial + 1, (uint32_t)(j - pi), 3u);
       const int n = launch_small_run(s->stream, s->kw, s->ctl, s->bufs, s->arena,
-                                     (uint32_t)run_off[pi], (uint32_t)(j - pi),
-                                     s->capacity, s->masks.writer(), ps.slot);
+                                     (uint32_t)run_off[pi], (uint32_t)(j - pi), s->capacity,
+                                     s->masks.writer(), serial_base, s->apply_serial, ps.slot);
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
       s->pass_serial += (uint32_t)(j - pi);
@@ -952,7 +1011,7 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
   if (launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0], value[1],
                          s->partials, s->prob_blocks, s->dresult) < 0)
     return cuda_ok(cudaGetLastError());
-  s->counters.kernel_launches += 2;
+  s->counters.kernel_launches += 1;
   if (cudaMemcpyAsync(s->hresult, s->dresult, sizeof(double), cudaMemcpyDeviceToHost, s->stream) !=
       cudaSuccess)
     return cuda_ok(cudaGetLastError());
@@ -969,7 +1028,7 @@ sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uin
   if (launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0], value[1],
                          s->partials, s->prob_blocks, s->dresult) < 0)
     return cuda_ok(cudaGetLastError());
-  s->counters.kernel_launches += 2;
+  s->counters.kernel_launches += 1;
   if (cudaMemcpyAsync(out, s->dresult, sizeof(double), cudaMemcpyDefault, s->stream) != cudaSuccess)
     return cuda_ok(cudaGetLastError());
   return SPS_OK;

@@ -31,6 +31,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
                                                              const unsigned char* arena,
                                                              uint32_t pass_off, uint32_t npasses,
                                                              uint64_t capacity, uint32_t mg,
+                                                             uint32_t serial_base,
+                                                             uint32_t apply_serial,
                                                              unsigned long long* plog) {
   extern __shared__ __align__(16) unsigned char smem[];
   cta::Bufs A = smem_bufs(smem);
@@ -59,7 +61,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
   const uint32_t done = cta::run_passes<KW>(arena, passes, 0, npasses, A, B, n, cap, tab,
                                             kSmallTableSlots, warp_sums, &upd);
   if (done < npasses && threadIdx.x == 0)
-    fail(ctl, SPS_ERR_CAPACITY, passes[done].pass_serial, passes[done].fail_tag);
+    fail(ctl, SPS_ERR_CAPACITY, serial_base + passes[done].pass_serial,
+         ((uint64_t)apply_serial << 32) | passes[done].fail_tag);
   // publish the state (after the last pass that succeeded) to the other buffer
   const SoA out = pick(bufs, cur ^ 1u);
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the labels
@@ -93,16 +96,18 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_run(Ctl* ctl, Bufs bufs
 
 int launch_small_run(void* stream, int key_words, Ctl* ctl, Bufs bufs, const unsigned char* arena,
                      uint32_t pass_off, uint32_t npasses, uint64_t capacity, uint32_t mg,
-                     unsigned long long* plog) {
+                     uint32_t serial_base, uint32_t apply_serial, unsigned long long* plog) {
   const size_t smem = 64 * kSmallCap + 4 * (kSmallTableSlots + 33);
   if (key_words == 1) {
     cudaFuncSetAttribute(k_small_run<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_small_run<1><<<1, kSmallThreads, smem, (cudaStream_t)stream>>>(ctl, bufs, arena, pass_off,
-                                                                      npasses, capacity, mg, plog);
+                                                                      npasses, capacity, mg, serial_base,
+                                                                      apply_serial, plog);
   } else {
     cudaFuncSetAttribute(k_small_run<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_small_run<2><<<1, kSmallThreads, smem, (cudaStream_t)stream>>>(ctl, bufs, arena, pass_off,
-                                                                      npasses, capacity, mg, plog);
+                                                                      npasses, capacity, mg, serial_base,
+                                                                      apply_serial, plog);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -181,9 +181,10 @@ struct RunPass {            // 64 bytes
   uint32_t ph_off;          // fused: byte offset of the fire-slot tables
   uint32_t br_off;          // byte offset of the BranchOp
   uint32_t flags;           // bit 0: permutes, bit 1: changes amplitudes
-  uint32_t pass_serial;
+  uint32_t pass_serial;     // small run: pass index in the apply + 1 (the launch adds
+                            // its serial base); batch: pass index
   uint32_t nwords;          // fused: words of the encoded op stream
-  uint64_t fail_tag;
+  uint64_t fail_tag;        // small run: first gate (the launch adds the apply serial)
   double eps2;
   double eps;
   uint64_t reserved2;
@@ -315,7 +316,7 @@ int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, con
 // CTA with the state in shared memory; the host guarantees nnz <= kSmallCap.
 int launch_small_run(void* stream, int key_words, Ctl* ctl, Bufs bufs, const unsigned char* arena,
                      uint32_t pass_off, uint32_t npasses, uint64_t capacity, uint32_t mg,
-                     unsigned long long* plog);
+                     uint32_t serial_base, uint32_t apply_serial, unsigned long long* plog);
 // Gather form of a branching pass (insert-once rule, Sec. 3.1) on the whole GPU:
 // k_gather_build claims one slot per input label in an index table whose
 // 64-bit slots hold (epoch << 32 | input index), so a new epoch per pass makes
@@ -336,7 +337,7 @@ struct ExpandLaunch {
 };
 int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const ExpandLaunch& e,
                   uint64_t nnz_bound, unsigned long long* plog);
-int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
+int launch_probability(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
                        double* partials, int nblocks, double* result);
 // mg: label-mask buffers of a launch that writes labels (MaskRing::writer)

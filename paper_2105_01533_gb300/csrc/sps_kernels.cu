@@ -18,7 +18,8 @@
 //                    the slots it read and, in the last block, publishes the new
 //                    count and flips the buffers.
 //   k_probability    sum of |a|^2 over labels matching (mask, value) with a
-//                    fixed-order two-level reduction.
+//                    fixed-order two-level reduction (block sums, then the last
+//                    block to finish adds them in block order).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -522,10 +523,11 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 template <int KW>
-__global__ void __launch_bounds__(256) k_probability(const Ctl* ctl, Bufs bufs, uint64_t m0,
+__global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64_t m0,
                                                      uint64_t m1, uint64_t v0, uint64_t v1,
-                                                     double* partials) {
+                                                     double* partials, double* result) {
   __shared__ double sh[32];
+  __shared__ bool last;
   const uint64_t n = ctl->nnz;
   const SoA s = pick(bufs, ctl->cur);
   double acc = 0.0;
@@ -539,15 +541,21 @@ __global__ void __launch_bounds__(256) k_probability(const Ctl* ctl, Bufs bufs, 
     }
   }
   const double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
-}
-
-__global__ void k_sum_partials(const double* partials, int n, double* out) {
-  __shared__ double sh[32];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
-  const double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) *out = t;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s2 = 0.0;
+  for (uint32_t b = threadIdx.x; b < gridDim.x; b += blockDim.x) s2 += __ldcg(partials + b);
+  const double total = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    *result = total;
+    ctl->blocks_done = 0u;
+  }
 }
 
 __global__ void k_set_nnz(Ctl* ctl, unsigned long long nnz, uint32_t mg) {
@@ -757,16 +765,17 @@ int launch_branch_compact(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs buf
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_probability(const LaunchCfg& lc, int key_words, const Ctl* ctl, Bufs bufs,
+int launch_probability(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
                        double* partials, int nblocks, double* result) {
   cudaStream_t st = (cudaStream_t)lc.stream;
   if (key_words == 1)
-    k_probability<1><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi, partials);
+    k_probability<1><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
+                                              partials, result);
   else
-    k_probability<2><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi, partials);
-  k_sum_partials<<<1, 256, 0, st>>>(partials, nblocks, result);
-  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
+    k_probability<2><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
+                                              partials, result);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz, uint32_t mg) {

@@ -465,3 +465,51 @@ def test_probability_async_matches():
     assert abs(out[1].item() - st.probability((1 << 9, 0), (1 << 9, 0))) < 1e-15
     assert abs(dev.item() - 1.0) < 1e-12
     st.close()
+
+
+def test_repeated_applies_reuse_the_plan():
+    """The same gate list applied again (same start, options, threshold) runs
+    the cached plan and image; anything that differs compiles afresh. Results
+    must not depend on which happened."""
+    n = 50
+    a = W.to_array([W.H(q) for q in range(5)] + [W.CX(0, 20), W.T(20), W.Ry(21, 0.4, 1)] +
+                   [W.CCX(1, 2, 22), W.P(22, 0.9), W.H(3)])
+    b = W.to_array([W.H(30), W.X(31, 30), W.Rz(31, 0.3), W.Givens(30, 32, 0.5)])
+    orc_a = OracleState(n)
+    orc_a.apply(a, eps=1e-14)
+    want_a = orc_a.get()
+    orc_ab = orc_a.clone()
+    orc_ab.apply(b, eps=1e-14)
+    want_ab = orc_ab.get()
+    for small in (0, 2048):
+        st = sps.SparseState(n, 1 << 12)
+        st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, small)
+        for rep in range(3):
+            st.reset()
+            st.apply(a, 1e-14)
+            compare_states(st.get_amplitudes(), want_a, 1e-14)
+            st.apply(b, 1e-14)                 # another plan in between
+            compare_states(st.get_amplitudes(), want_ab, 1e-14)
+        st.reset()
+        st.apply(a, 1e-3)                      # another threshold: compiled afresh
+        orc = OracleState(n)
+        orc.apply(a, eps=1e-3)
+        compare_states(st.get_amplitudes(), orc.get(), 1e-3)
+        st.close()
+
+
+def test_cached_plan_reports_failures():
+    """A capacity failure inside a reused plan names the same gate."""
+    for small in (0, 2048):
+        st = sps.SparseState(30, 40)
+        st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, small)
+        st.set_option(sps.SPS_OPT_EXPAND, 0)
+        g = W.to_array([W.H(q) for q in range(5)] + [W.X(9), W.H(10)])   # 32 -> 64 > 40
+        for _ in range(2):
+            st.reset()
+            st.apply(g, 0.0)
+            with pytest.raises(sps.SpsError) as e:
+                st.sync()
+            assert e.value.status == sps.SPS_ERR_CAPACITY and e.value.failed_gate == 6
+            assert st.nnz() == 32
+        st.close()
