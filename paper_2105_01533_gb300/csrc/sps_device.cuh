@@ -66,25 +66,53 @@ __device__ __forceinline__ bool flip_bits_constant(const LabelMasks& m, const ui
   return (((m.or0 ^ m.and0) & f[0]) | ((m.or1 ^ m.and1) & f[1])) == 0ull;
 }
 
-// Warp-wide OR/AND of per-lane label words, merged into one stripe of buffer
-// b with atomics whose results are not waited for. The calling warp must be
-// converged; lanes without labels pass (0, 0, ~0, ~0).
+// Block-wide OR/AND of per-thread label words, merged into one stripe of
+// buffer b with atomics whose results are not waited for (one set per block,
+// so the stripes see few atomics each). Every thread of the block must call it;
+// threads without labels pass (0, 0, ~0, ~0).
 __device__ __forceinline__ void merge_label_masks(Ctl* ctl, uint32_t b, uint64_t or0, uint64_t or1,
                                                   uint64_t and0, uint64_t and1) {
+  __shared__ unsigned long long part[4][32];
   for (int d = 16; d > 0; d >>= 1) {
     or0 |= __shfl_xor_sync(0xFFFFFFFFu, or0, d);
     or1 |= __shfl_xor_sync(0xFFFFFFFFu, or1, d);
     and0 &= __shfl_xor_sync(0xFFFFFFFFu, and0, d);
     and1 &= __shfl_xor_sync(0xFFFFFFFFu, and1, d);
   }
-  if ((threadIdx.x & 31u) == 0) {
-    const unsigned stripe = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kMaskStripes;
-    unsigned long long* p = ctl->lm[b][stripe];
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    part[0][warp] = or0;
+    part[1][warp] = or1;
+    part[2][warp] = and0;
+    part[3][warp] = and1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (unsigned w = 1; w < (blockDim.x >> 5); ++w) {
+      or0 |= part[0][w];
+      or1 |= part[1][w];
+      and0 &= part[2][w];
+      and1 &= part[3][w];
+    }
+    unsigned long long* p = ctl->lm[b][blockIdx.x % kMaskStripes];
     if (or0) atomicOr(p, or0);
     if (or1) atomicOr(p + 1, or1);
     if (~and0) atomicAnd(p + 2, and0);
     if (~and1) atomicAnd(p + 3, and1);
   }
+  __syncthreads();
+}
+
+// The masks in buffer b for every thread of the block (all must call it): one
+// warp reads the stripes.
+__device__ __forceinline__ LabelMasks read_label_masks_block(const Ctl* ctl, uint32_t b) {
+  __shared__ LabelMasks shared;
+  if (threadIdx.x < 32) {
+    const LabelMasks m = read_label_masks(ctl, b);
+    if (threadIdx.x == 0) shared = m;
+  }
+  __syncthreads();
+  return shared;
 }
 
 // Sets buffer b to the given masks (one thread).
@@ -319,13 +347,20 @@ __device__ __forceinline__ void pair_action(const BranchOp& op, bool both, bool 
 // common cases are decided on the bit patterns: for non-negative doubles the
 // IEEE order is the unsigned-integer order, and rounding is monotone, so
 // |re| >= eps or |im| >= eps already implies re^2 + im^2 >= eps^2 as rounded.
+// The FP64 test, out of line: inlined, the compiler evaluates it on every call
+// (predicated, to avoid a branch) and the products load the scarce FP64 pipe
+// although the bit-pattern tests decide almost every entry.
+static __device__ __noinline__ bool keep_amp_fp64(double re, double im, double eps2) {
+  const double mag2 = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+  return !(mag2 < eps2);
+}
+
 __device__ __forceinline__ bool keep_amp(double re, double im, double eps2, uint64_t eps_bits) {
   const uint64_t ar = (uint64_t)__double_as_longlong(re) & 0x7FFFFFFFFFFFFFFFull;
   const uint64_t ai = (uint64_t)__double_as_longlong(im) & 0x7FFFFFFFFFFFFFFFull;
   if ((ar | ai) == 0ull) return false;
   if (ar >= eps_bits || ai >= eps_bits) return true;
-  const double mag2 = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
-  return !(mag2 < eps2);
+  return keep_amp_fp64(re, im, eps2);
 }
 
 // bit pattern of eps = sqrt(eps2) as passed by the host (eps >= 0)

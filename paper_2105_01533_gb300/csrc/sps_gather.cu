@@ -55,9 +55,10 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
     plog[0] = n;
     plog[1] = 0ull;
   }
-  if (ctl->status != 0u) return;
+  // (another block may set the status meanwhile: decide for the whole block)
+  if (__syncthreads_or(ctl->status != 0u)) return;
   // Flip bits constant over the state: no entry has a partner, nothing to index.
-  if (flip_bits_constant(read_label_masks(ctl, mg_rd(a.mg)), a.op.m)) return;
+  if (flip_bits_constant(read_label_masks_block(ctl, mg_rd(a.mg)), a.op.m)) return;
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
   const SoA s = pick(bufs, ctl->cur);
   const unsigned long long ep = (unsigned long long)a.epoch << 48;
@@ -116,8 +117,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
                                                      unsigned long long* plog) {
   __shared__ unsigned warp_cnt[32];
   __shared__ unsigned long long block_base;
-  const unsigned status0 = ctl->status;
-  if (status0 != 0u) return;
+  if (__syncthreads_or(ctl->status != 0u)) return;
   const uint64_t n = ctl->nnz;
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
   const unsigned cur = ctl->cur;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
   const BranchOp& op = a.op;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned nwarps = blockDim.x >> 5;
-  const bool no_partners = flip_bits_constant(read_label_masks(ctl, mg_rd(a.mg)), op.m);
+  const bool no_partners = flip_bits_constant(read_label_masks_block(ctl, mg_rd(a.mg)), op.m);
   if (blockIdx.x == 0 && threadIdx.x == 0) reset_label_masks(ctl, mg_rs(a.mg));
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the written labels
   for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
@@ -244,8 +244,11 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
 // i = t >> d and c the d choices; label k_i ^ mask(c), amplitude a_i * F0[c0] *
 // F1[c1] * F2[c2] from per-8-gate tables staged in shared memory; pruned on
 // the final amplitude (every matrix entry has modulus <= 1, so no path falls
-// below eps before its end and rises above it after). Survivors are compacted
-// as in the gather emit; the last block publishes the count.
+// below eps before its end and rises above it after).
+// A warp owns spans of 256 consecutive outputs, 8 per lane. With d >= 8 a span
+// shares its input and its choices above the first 8 gates, so the warp forms
+// that head once and each output costs one table product. Survivors of a span
+// take one atomic for their place; the last block publishes the count.
 struct ExpandArgs {
   const double2* f;        // chunks x 256 path factors
   const ulonglong2* m;     // chunks x 256 flip masks
@@ -254,11 +257,23 @@ struct ExpandArgs {
   uint64_t capacity, fail_tag;
 };
 
+// (re, im) *= f; a real factor leaves an exactly zero imaginary part at zero
+// (skipping the product, which would only give it a sign).
+__device__ __forceinline__ void times(bool real, double2 f, double& re, double& im) {
+  if (real) {
+    re = re * f.x;
+    if (im != 0.0) im = im * f.x;
+  } else {
+    const double nr = re * f.x - im * f.y;
+    const double ni = re * f.y + im * f.x;
+    re = nr;
+    im = ni;
+  }
+}
+
 template <int KW>
 __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const ExpandArgs a,
                                                 unsigned long long* plog) {
-  __shared__ unsigned warp_cnt[32];
-  __shared__ unsigned long long block_base;
   __shared__ double2 sf[3 * 256];
   __shared__ ulonglong2 sm[3 * 256];
   if (ctl->status != 0u) return;
@@ -275,74 +290,92 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const Expan
   const uint64_t total = n << a.d;
   const uint64_t cmask = (1ull << a.d) - 1ull;
   const uint64_t eps_bits = eps_pattern(a.eps);
-  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const unsigned nwarps = blockDim.x >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  const bool wide = a.d >= 8;
+  const uint64_t spans = (total + 255) / 256;
+  const uint64_t nwarp = (uint64_t)gridDim.x * (blockDim.x >> 5);
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;
-  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < total;
-       base += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t t = base + threadIdx.x;
-    uint64_t l0 = 0, l1 = 0;
-    double vr = 0.0, vi = 0.0;
-    bool w = false;
-    if (t < total) {
-      const uint64_t i = t >> a.d;
-      const uint32_t c = (uint32_t)(t & cmask);
-      l0 = s.lo[i];
-      l1 = KW == 2 ? s.hi[i] : 0ull;
-      vr = s.re[i];
-      vi = s.im[i];
-      for (uint32_t ch = 0; ch < a.chunks; ++ch) {
+  for (uint64_t sp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sp < spans;
+       sp += nwarp) {
+    const uint64_t t0 = sp * 256;
+    uint64_t h0 = 0, h1 = 0;
+    double hr = 0.0, hi = 0.0;
+    if (wide) {   // the span's input and its choices above the first 8 gates
+      const uint64_t i = t0 >> a.d;
+      const uint32_t c = (uint32_t)(t0 & cmask);
+      h0 = s.lo[i];
+      h1 = KW == 2 ? s.hi[i] : 0ull;
+      hr = s.re[i];
+      hi = s.im[i];
+      for (uint32_t ch = 1; ch < a.chunks; ++ch) {
         const uint32_t u = ch * 256u + ((c >> (8u * ch)) & 0xFFu);
-        const ulonglong2 mk = sm[u];
-        l0 ^= mk.x;
-        l1 ^= mk.y;
-        const double2 f = sf[u];
-        if (a.real) {
-          vr = vr * f.x;
-          vi = vi * f.x;
+        h0 ^= sm[u].x;
+        h1 ^= sm[u].y;
+        times(a.real != 0u, sf[u], hr, hi);
+      }
+    }
+    uint64_t L0[8], L1[8];
+    double VR[8], VI[8];
+    unsigned bal[8];
+    unsigned count = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint64_t t = t0 + 32u * k + lane;
+      bool keep = false;
+      uint64_t l0 = 0, l1 = 0;
+      double vr = 0.0, vi = 0.0;
+      if (t < total) {
+        uint32_t c0;
+        if (wide) {
+          c0 = 32u * k + lane;
+          l0 = h0;
+          l1 = h1;
+          vr = hr;
+          vi = hi;
         } else {
-          const double nr = vr * f.x - vi * f.y;
-          const double ni = vr * f.y + vi * f.x;
-          vr = nr;
-          vi = ni;
+          const uint64_t i = t >> a.d;
+          c0 = (uint32_t)(t & cmask);
+          l0 = s.lo[i];
+          l1 = KW == 2 ? s.hi[i] : 0ull;
+          vr = s.re[i];
+          vi = s.im[i];
         }
+        l0 ^= sm[c0].x;
+        l1 ^= sm[c0].y;
+        times(a.real != 0u, sf[c0], vr, vi);
+        keep = keep_amp(vr, vi, a.eps2, eps_bits);
       }
-      w = keep_amp(vr, vi, a.eps2, eps_bits);
+      L0[k] = l0;
+      L1[k] = l1;
+      VR[k] = vr;
+      VI[k] = vi;
+      bal[k] = __ballot_sync(FULL, keep);
+      count += __popc(bal[k]);
     }
-    if (w) {
-      mo0 |= l0;
-      mo1 |= l1;
-      ma0 &= l0;
-      ma1 &= l1;
-    }
-    const unsigned b0 = __ballot_sync(FULL, w);
-    if (lane == 0) warp_cnt[warp] = __popc(b0);
-    __syncthreads();
-    if (warp == 0) {
-      const unsigned v = lane < nwarps ? warp_cnt[lane] : 0u;
-      unsigned incl = v;
-      for (int dd = 1; dd < 32; dd <<= 1) {
-        const unsigned x = __shfl_up_sync(FULL, incl, dd);
-        if (lane >= (unsigned)dd) incl += x;
+    unsigned long long base = 0ull;
+    if (lane == 0 && count) base = atomicAdd(&ctl->out_count, (unsigned long long)count);
+    base = __shfl_sync(FULL, base, 0);
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if ((bal[k] >> lane) & 1u) {
+        const uint64_t pos = base + __popc(bal[k] & below);
+        if (pos < a.capacity) {
+          out.lo[pos] = L0[k];
+          if (KW == 2) out.hi[pos] = L1[k];
+          out.re[pos] = VR[k];
+          out.im[pos] = VI[k];
+        }
+        mo0 |= L0[k];
+        mo1 |= L1[k];
+        ma0 &= L0[k];
+        ma1 &= L1[k];
       }
-      const unsigned tot = __shfl_sync(FULL, incl, 31);
-      if (lane < nwarps) warp_cnt[lane] = incl - v;
-      if (lane == 0)
-        block_base = tot ? atomicAdd(&ctl->out_count, (unsigned long long)tot) : 0ull;
+      base += __popc(bal[k]);
     }
-    __syncthreads();
-    if (w) {
-      const uint64_t pos = block_base + warp_cnt[warp] + __popc(b0 & ((1u << lane) - 1u));
-      if (pos < a.capacity) {
-        out.lo[pos] = l0;
-        if (KW == 2) out.hi[pos] = l1;
-        out.re[pos] = vr;
-        out.im[pos] = vi;
-      }
-    }
-    __syncthreads();
   }
   merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
@@ -438,7 +471,8 @@ int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const
   a.capacity = e.capacity;
   a.fail_tag = e.fail_tag;
   cudaStream_t st = (cudaStream_t)lc.stream;
-  const int blocks = grid_of(nnz_bound << e.d, lc.threads, lc.max_blocks);
+  // one warp per span of 256 outputs
+  const int blocks = grid_of((nnz_bound << e.d) / 8 + 1, lc.threads, lc.max_blocks);
   if (key_words == 1)
     k_expand<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, a, plog);
   else
