@@ -67,6 +67,8 @@ def _load():
     lib.orc_set.restype = i32
     lib.orc_probability.argtypes = [vp, vp, vp]
     lib.orc_probability.restype = dbl
+    lib.orc_measure.argtypes = [vp, u32, dbl, vp]
+    lib.orc_measure.restype = i32
     lib.orc_dense_run.argtypes = [u32, vp, u64, vp, vp]
     lib.orc_dense_run.restype = i32
     lib.orc_classical_eval.argtypes = [u32, vp, u64, vp, vp, u64, pu64]
@@ -147,6 +149,14 @@ class OracleState:
         v = np.ascontiguousarray(value, np.uint64)
         assert m.size == 2 and v.size == 2
         return float(self._lib.orc_probability(self._h, _ptr(m), _ptr(v)))
+
+
+    def measure(self, qubit: int, r: float):
+        """Measures one qubit with collapse; returns (outcome, its probability)."""
+        out = np.zeros(2, np.float64)
+        if self._lib.orc_measure(self._h, int(qubit), float(r), _ptr(out)) != 0:
+            raise ValueError("bad measurement argument")
+        return int(out[0]), float(out[1])
 
 
 def dense_run(nqubits: int, gates) -> np.ndarray:

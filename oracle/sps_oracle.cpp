@@ -378,6 +378,44 @@ double orc_probability(void* h, const uint64_t* mask, const uint64_t* value) {
   return p;
 }
 
+// Measurement of qubit q in the computational basis with collapse (Sec. 2.1: the
+// outcome b is observed with probability |alpha|^2 summed over the labels that
+// show it, and the state is projected onto those labels; Sec. 3 lists
+// measurements among the operations). Steps, in this order:
+//   p0 = sum |alpha_k|^2 over labels with bit q = 0, p1 likewise for bit q = 1;
+//   outcome = 1 iff r * (p0 + p1) < p1 (r in [0, 1) drawn by the caller);
+//   the labels with bit q != outcome are removed and each kept amplitude is
+//   divided by sqrt(p_outcome), so the state has norm 1 afterwards.
+// out[0] = outcome, out[1] = p_outcome / (p0 + p1). Returns 1 on a bad
+// argument, 0 otherwise; an empty state stays empty (outcome 0, probability 0).
+int orc_measure(void* h, uint32_t q, double r, double* out) {
+  State* st = static_cast<State*>(h);
+  if (q >= st->nqubits || !(r >= 0.0 && r < 1.0)) return 1;
+  const uint64_t bit = 1ull << (q & 63);
+  double p0 = 0.0, p1 = 0.0;
+  for (const auto& kv : st->map) {
+    const uint64_t w = q < 64 ? kv.first.lo : kv.first.hi;
+    const double m = kv.second.re * kv.second.re + kv.second.im * kv.second.im;
+    if (w & bit) p1 += m; else p0 += m;
+  }
+  const double total = p0 + p1;
+  const int outcome = r * total < p1 ? 1 : 0;
+  const double pk = outcome ? p1 : p0;
+  out[0] = outcome;
+  out[1] = total > 0.0 ? pk / total : 0.0;
+  Map m;
+  if (pk > 0.0) {
+    const double scale = 1.0 / std::sqrt(pk);
+    for (const auto& kv : st->map) {
+      const uint64_t w = q < 64 ? kv.first.lo : kv.first.hi;
+      if (((w & bit) != 0) == (outcome == 1))
+        m[kv.first] = Cplx{kv.second.re * scale, kv.second.im * scale};
+    }
+  }
+  st->map.swap(m);
+  return 0;
+}
+
 // ---- dense statevector checker (Sec. 2.2) -----------------------------------
 // Runs the gates on |0...0> over all 2^n amplitudes. Only qubits < 64 and
 // controls in word 0 are allowed (n <= 26). Returns 1 on a bad record.

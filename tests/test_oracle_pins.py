@@ -300,3 +300,68 @@ def test_bad_records_are_rejected():
         st.apply(W.to_array([W.X(1, 1)]))          # control on its own target
     with pytest.raises(ValueError):
         st.apply(W.to_array([W.Givens(2, 2, 0.1)]))
+
+
+# ---- measurement with collapse ----------------------------------------------------
+def test_measure_bell_pair_closed_form():
+    """(|00> + |11>)/sqrt2: each outcome has probability 1/2 and leaves the
+    matching basis state with amplitude 1 (Sec. 2.1 projection)."""
+    for r, outcome, label in ((0.3, 1, 3), (0.7, 0, 0)):
+        st = run_oracle(4, W.to_array([W.H(0), W.CX(0, 1)]))
+        got = st.measure(0, r)
+        assert got[0] == outcome and abs(got[1] - 0.5) < 1e-15
+        hi, lo, re, im = st.get()
+        assert lo.tolist() == [label] and abs(re[0] - 1.0) < 1e-15 and im[0] == 0.0
+        # the partner qubit is now determined: measuring it is certain
+        assert st.measure(1, 0.999)[0] == outcome
+
+
+def test_measure_matches_numpy_projection():
+    """Marginals and post-measurement states against a numpy statevector from the
+    tensor simulator: P(q = 1) = sum over indices with bit q set of |v|^2, and
+    the kept part of v divided by its norm."""
+    n = 7
+    gates = W.to_array([W.H(q) for q in range(4)] + [W.Ry(4, 0.8, 1), W.Rx(5, 1.3, 2),
+                       W.CX(0, 6), W.T(3), W.P(5, 0.4, 0), W.Givens(2, 6, 0.5), W.H(1)])
+    v = kron_ref.tensor_run(n, gates)
+    idx = np.arange(1 << n)
+    for q in range(n):
+        p1 = float(np.sum(np.abs(v[((idx >> q) & 1) == 1]) ** 2))
+        for r in (0.05, 0.37, 0.61, 0.95):
+            if abs(r - p1) < 1e-9:     # a draw on the edge: either outcome is right
+                continue
+            st = run_oracle(n, gates)
+            outcome, p = st.measure(q, r)
+            assert outcome == (1 if r < p1 else 0)
+            assert abs(p - (p1 if outcome else 1 - p1)) < 1e-12
+            w = np.where(((idx >> q) & 1) == outcome, v, 0)
+            w = w / np.linalg.norm(w)
+            np.testing.assert_allclose(sparse_vector(st, n), w, atol=1e-12)
+
+
+def test_measure_constant_qubit_and_unnormalised_state():
+    """A qubit that is 0 in every label: outcome 0 with probability 1, amplitudes
+    unchanged. An input of norm 2: probabilities are relative, the result has
+    norm 1."""
+    st = run_oracle(10, W.to_array([W.H(0), W.H(1)]))
+    before = st.get()
+    assert st.measure(7, 0.999999) == (0, 1.0)
+    after = st.get()
+    for a, b in zip(after[:2], before[:2]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_allclose(after[2], before[2], rtol=1e-15)   # divided by sqrt(1 + ulp)
+    st = OracleState(10)
+    st.set(np.zeros(4, np.uint64), np.array([0, 1, 2, 3], np.uint64),
+           np.array([1.0, 1.0, 1.0, 1.0]), np.zeros(4))            # norm^2 = 4
+    outcome, p = st.measure(1, 0.6)                                 # P(bit 1 = 1) = 1/2
+    assert outcome == 0 and p == 0.5
+    hi, lo, re, im = st.get()
+    assert sorted(lo.tolist()) == [0, 1]
+    np.testing.assert_allclose(re, [1 / math.sqrt(2)] * 2, rtol=1e-15)
+
+
+def test_measure_rejects_bad_arguments():
+    st = OracleState(5)
+    for q, r in ((5, 0.5), (0, 1.0), (0, -0.1), (0, float("nan"))):
+        with pytest.raises(ValueError):
+            st.measure(q, r)
