@@ -169,6 +169,22 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
 sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
                                  double* out);
 
+/* Measures qubit `qubit` in the computational basis and collapses the state
+ * (Sec. 2.1: outcome b has probability sum |alpha_k|^2 over the labels whose
+ * bit `qubit` is b, and the state is projected onto those labels; Sec. 3 lists
+ * measurements among the simulator's operations). p0 and p1 are those sums
+ * over the current state, formed on the device in a fixed order; the outcome is
+ * 1 iff r * (p0 + p1) < p1, with r in [0, 1) drawn by the caller; labels
+ * showing the other value are removed and the kept amplitudes are divided by
+ * sqrt(p_outcome), so the state has norm 1 afterwards. Only enqueues: out[0] =
+ * outcome (0.0 or 1.0) and out[1] = p_outcome / (p0 + p1) are written to `out`
+ * (2 doubles of pinned host or device memory, caller-owned, valid until the
+ * stream passes this point) in stream order. An empty state stays empty
+ * (outcome 0, probability 0). Counts as one gate in sps_get_updates.
+ * Errors: SPS_ERR_ARG for qubit >= nqubits or r outside [0, 1) (nothing is
+ * enqueued); a pending device error skips it and is reported by sps_sync. */
+sps_status sps_measure(sps_state* s, uint32_t qubit, double r, double* out);
+
 /* Tuning options (see sps_set_option). */
 typedef enum sps_option {
   SPS_OPT_LOAD_FACTOR_PCT = 1, /* target branching-table load, 10..90 (default 50) */
@@ -237,7 +253,8 @@ sps_status sps_get_counters(sps_state* s, sps_counters* out);
 /* One profiled kernel launch (SPS_OPT_PROFILE). kind: 1 fused phase /
  * permutation pass, 2 scatter emit, 3 scatter compaction, 4 small-state run
  * (several passes in one block), 5 gather index build, 6 gather emit,
- * 7 expansion pass (SPS_OPT_EXPAND; nops = gates). n_in: entries
+ * 7 expansion pass (SPS_OPT_EXPAND; nops = gates), 8 measurement (sums and
+ * collapse, timed together). n_in: entries
  * the kernel read; n_out: entries in the state after it. flags: bit 0 the
  * pass permutes labels, bit 1 it changes amplitudes. label_bytes: 8 or 16. */
 typedef struct sps_kernel_record {

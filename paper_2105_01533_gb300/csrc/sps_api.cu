@@ -84,6 +84,7 @@ struct sps_state {
   int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
+  double* dmeasure = nullptr;   // {outcome, probability, scale} of the last measurement
   double* hresult = nullptr;  // pinned
   unsigned* dflag = nullptr;
   unsigned* hflag = nullptr;  // pinned
@@ -455,9 +456,12 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
   s->itab = (unsigned long long*)p;
   if ((st = dev_alloc(s, sizeof(Ctl), &p)) != SPS_OK) return fail(st);
   s->ctl = (Ctl*)p;
-  if ((st = dev_alloc(s, sizeof(double) * (s->prob_blocks + 1), &p)) != SPS_OK) return fail(st);
+  // partials: 2 per block (the measurement's two sums), then the probability
+  // result and the measurement's three results
+  if ((st = dev_alloc(s, sizeof(double) * (2 * s->prob_blocks + 4), &p)) != SPS_OK) return fail(st);
   s->partials = (double*)p;
-  s->dresult = s->partials + s->prob_blocks;
+  s->dresult = s->partials + 2 * s->prob_blocks;
+  s->dmeasure = s->dresult + 1;
   if ((st = dev_alloc(s, 256, &p)) != SPS_OK) return fail(st);
   s->dflag = (unsigned*)p;
   if ((st = dev_alloc(s, 2 * sizeof(unsigned long long) * kProfileCap, &p)) != SPS_OK) return fail(st);
@@ -1030,6 +1034,23 @@ sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uin
     return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 1;
   if (cudaMemcpyAsync(out, s->dresult, sizeof(double), cudaMemcpyDefault, s->stream) != cudaSuccess)
+    return cuda_ok(cudaGetLastError());
+  return SPS_OK;
+}
+
+sps_status sps_measure(sps_state* s, uint32_t qubit, double r, double* out) {
+  if (!s || !out || qubit >= s->nqubits || !(r >= 0.0 && r < 1.0)) return SPS_ERR_ARG;
+  const LaunchCfg lc = cfg_of(s);
+  const uint32_t serial = ++s->pass_serial;
+  ProfScope ps(s, 8, serial, 1, 1u);
+  const int n = launch_measure(lc, s->kw, s->ctl, s->bufs, qubit, r, s->partials, s->prob_blocks,
+                               s->dmeasure, s->nnz_bound, s->masks.writer(), ps.slot);
+  ps.done();
+  if (n < 0) return cuda_ok(cudaGetLastError());
+  s->counters.kernel_launches += (uint64_t)n;
+  s->counters.gates += 1;
+  if (cudaMemcpyAsync(out, s->dmeasure, 2 * sizeof(double), cudaMemcpyDefault, s->stream) !=
+      cudaSuccess)
     return cuda_ok(cudaGetLastError());
   return SPS_OK;
 }

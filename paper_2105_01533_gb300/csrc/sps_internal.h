@@ -337,6 +337,11 @@ struct ExpandLaunch {
 };
 int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const ExpandLaunch& e,
                   uint64_t nnz_bound, unsigned long long* plog);
+// Measurement with collapse: partials holds 2 * nblocks doubles; res receives
+// {outcome, probability of the outcome, 1 / sqrt(p_outcome)}.
+int launch_measure(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, uint32_t qubit,
+                   double r, double* partials, int nblocks, double* res, uint64_t nnz_bound,
+                   uint32_t mg, unsigned long long* plog);
 int launch_probability(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
                        double* partials, int nblocks, double* result);

@@ -558,6 +558,137 @@ __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64
   }
 }
 
+// ---------------------------------------------------------------------------
+// Measurement of one qubit with collapse (Sec. 2.1). k_measure_sum: block sums
+// of |a|^2 over the labels with the qubit 0 and 1; the last block adds them in
+// block order, draws the outcome (1 iff r * (p0 + p1) < p1) and stores
+// res = {outcome, p_outcome / (p0 + p1), 1 / sqrt(p_outcome)}. k_collapse keeps
+// the labels that show the outcome, scales them and compacts them into the
+// other buffer; its last block publishes the count.
+template <int KW>
+__global__ void __launch_bounds__(256) k_measure_sum(Ctl* ctl, Bufs bufs, uint32_t word,
+                                                     uint64_t bit, double r, double* partials,
+                                                     double* res) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  if (ctl->status != 0u) return;
+  const uint64_t n = ctl->nnz;
+  const SoA s = pick(bufs, ctl->cur);
+  double a0 = 0.0, a1 = 0.0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = (KW == 2 && word) ? s.hi[i] : s.lo[i];
+    const double re = s.re[i], im = s.im[i];
+    const double m = re * re + im * im;
+    if (k & bit) a1 += m; else a0 += m;
+  }
+  const double t0 = block_sum(a0, sh);
+  __syncthreads();
+  const double t1 = block_sum(a1, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = t0;
+    partials[gridDim.x + blockIdx.x] = t1;
+    __threadfence();
+    last = atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s0 = 0.0, s1 = 0.0;
+  for (uint32_t b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    s0 += __ldcg(partials + b);
+    s1 += __ldcg(partials + gridDim.x + b);
+  }
+  const double p0 = block_sum(s0, sh);
+  __syncthreads();
+  const double p1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    const double total = p0 + p1;
+    const bool one = r * total < p1;
+    const double pk = one ? p1 : p0;
+    res[0] = one ? 1.0 : 0.0;
+    res[1] = total > 0.0 ? pk / total : 0.0;
+    res[2] = pk > 0.0 ? 1.0 / sqrt(pk) : 0.0;
+    ctl->blocks_done = 0u;
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_collapse(Ctl* ctl, Bufs bufs, uint32_t word, uint64_t bit,
+                                                  const double* res, uint32_t mg,
+                                                  unsigned long long* plog) {
+  __shared__ unsigned warp_cnt[32];
+  __shared__ unsigned long long block_base;
+  if (ctl->status != 0u) return;
+  const uint64_t n = ctl->nnz;
+  const unsigned cur = ctl->cur;
+  const SoA s = pick(bufs, cur);
+  const SoA out = pick(bufs, cur ^ 1u);
+  if (blockIdx.x == 0 && threadIdx.x == 0) reset_label_masks(ctl, mg_rs(mg));
+  const bool one = __ldcg(res) != 0.0;
+  const double scale = __ldcg(res + 2);
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned nwarps = blockDim.x >> 5;
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    bool keep = false;
+    uint64_t lo = 0, hi = 0;
+    if (i < n) {
+      lo = s.lo[i];
+      hi = KW == 2 ? s.hi[i] : 0ull;
+      keep = scale != 0.0 && ((((word ? hi : lo) & bit) != 0ull) == one);
+    }
+    const unsigned ballot = __ballot_sync(FULL, keep);
+    if (lane == 0) warp_cnt[warp] = __popc(ballot);
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned v = lane < nwarps ? warp_cnt[lane] : 0u;
+      unsigned incl = v;
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= (unsigned)d) incl += t;
+      }
+      const unsigned total = __shfl_sync(FULL, incl, 31);
+      if (lane < nwarps) warp_cnt[lane] = incl - v;
+      if (lane == 0) block_base = total ? atomicAdd(&ctl->out_count, (unsigned long long)total) : 0ull;
+    }
+    __syncthreads();
+    if (keep) {
+      const uint64_t pos = block_base + warp_cnt[warp] + __popc(ballot & ((1u << lane) - 1u));
+      out.lo[pos] = lo;
+      if (KW == 2) out.hi[pos] = hi;
+      out.re[pos] = s.re[i] * scale;
+      out.im[pos] = s.im[i] * scale;
+      mo0 |= lo;
+      mo1 |= hi;
+      ma0 &= lo;
+      ma1 &= hi;
+    }
+    __syncthreads();
+  }
+  merge_label_masks(ctl, mg_wr(mg), mo0, mo1, ma0, ma1);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long total = atomicAdd(&ctl->out_count, 0ull);
+      ctl->nnz = total;        // never more than before: the buffers hold it
+      ctl->cur = cur ^ 1u;
+      ctl->updates += n;
+      if (plog) {
+        plog[0] = n;
+        plog[1] = total;
+      }
+      ctl->out_count = 0ull;
+      ctl->blocks_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
 __global__ void k_set_nnz(Ctl* ctl, unsigned long long nnz, uint32_t mg) {
   ctl->nnz = nnz;
   ctl->cur = 0u;
@@ -776,6 +907,23 @@ int launch_probability(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
     k_probability<2><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
                                               partials, result);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_measure(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, uint32_t qubit,
+                   double r, double* partials, int nblocks, double* res, uint64_t nnz_bound,
+                   uint32_t mg, unsigned long long* plog) {
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  const uint32_t word = qubit >> 6;
+  const uint64_t bit = 1ull << (qubit & 63u);
+  const int blocks = grid_for(nnz_bound, lc.threads, lc.max_blocks);
+  if (key_words == 1) {
+    k_measure_sum<1><<<nblocks, 256, 0, st>>>(ctl, bufs, word, bit, r, partials, res);
+    k_collapse<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, word, bit, res, mg, plog);
+  } else {
+    k_measure_sum<2><<<nblocks, 256, 0, st>>>(ctl, bufs, word, bit, r, partials, res);
+    k_collapse<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, word, bit, res, mg, plog);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
 int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz, uint32_t mg) {

@@ -40,7 +40,7 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates",
            "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
-           "sps_server_completed", "sps_probability_async")
+           "sps_server_completed", "sps_probability_async", "sps_measure")
 
 
 class SpsError(RuntimeError):
@@ -121,6 +121,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_probability.restype = st
     lib.sps_probability_async.argtypes = [vp, vp, vp, vp]
     lib.sps_probability_async.restype = st
+    lib.sps_measure.argtypes = [vp, u32, dbl, vp]
+    lib.sps_measure.restype = st
     lib.sps_set_option.argtypes = [vp, ctypes.c_int, i64]
     lib.sps_set_option.restype = st
     lib.sps_get_counters.argtypes = [vp, ctypes.POINTER(Counters)]
@@ -323,6 +325,13 @@ def sps_probability_async(h: int, mask: Sequence[int], value: Sequence[int], out
            "sps_probability_async")
 
 
+def sps_measure(h: int, qubit: int, r: float, out_ptr: int) -> None:
+    """Enqueue a measurement with collapse; {outcome, probability} land at out_ptr
+    (two doubles, pinned host or device memory) in stream order."""
+    _check(load_library().sps_measure(h, int(qubit), float(r), ctypes.c_void_p(out_ptr)),
+           "sps_measure")
+
+
 def sps_set_option(h: int, opt: int, value: int) -> None:
     _check(load_library().sps_set_option(h, opt, int(value)), "sps_set_option")
 
@@ -442,6 +451,18 @@ class SparseState:
     def probability_async(self, mask, value, out_ptr: int) -> None:
         """Enqueue the probability into out_ptr (pinned host or device memory)."""
         sps_probability_async(self._h, mask, value, out_ptr)
+
+    def measure(self, qubit: int, r: float):
+        """Measure one qubit with collapse (r uniform in [0, 1)); waits and
+        returns (outcome, probability of the outcome)."""
+        out = np.zeros(2, np.float64)
+        sps_measure(self._h, qubit, r, out.ctypes.data)
+        self.sync()
+        return int(out[0]), float(out[1])
+
+    def measure_async(self, qubit: int, r: float, out_ptr: int) -> None:
+        """Enqueue a measurement; {outcome, probability} land at out_ptr."""
+        sps_measure(self._h, qubit, r, out_ptr)
 
     def get_amplitudes(self, sort: bool = True):
         """(hi, lo, re, im) numpy arrays, sorted by (hi, lo) unless sort=False."""
