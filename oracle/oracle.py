@@ -67,6 +67,8 @@ def _load():
     lib.orc_set.restype = i32
     lib.orc_probability.argtypes = [vp, vp, vp]
     lib.orc_probability.restype = dbl
+    lib.orc_pauli_exp.argtypes = [vp, vp, vp, vp, dbl, dbl]
+    lib.orc_pauli_exp.restype = i32
     lib.orc_measure.argtypes = [vp, u32, dbl, vp]
     lib.orc_measure.restype = i32
     lib.orc_dense_run.argtypes = [u32, vp, u64, vp, vp]
@@ -150,6 +152,14 @@ class OracleState:
         assert m.size == 2 and v.size == 2
         return float(self._lib.orc_probability(self._h, _ptr(m), _ptr(v)))
 
+
+    def pauli_exp(self, x, z, controls, theta: float, eps: float = 0.0) -> None:
+        """exp(-i theta/2 P) for the Pauli string with X-or-Y mask x and Z-or-Y
+        mask z (two words each), under the control mask."""
+        xs, zs, cs = (np.ascontiguousarray(v, np.uint64) for v in (x, z, controls))
+        if self._lib.orc_pauli_exp(self._h, _ptr(xs), _ptr(zs), _ptr(cs), float(theta),
+                                   float(eps)) != 0:
+            raise ValueError("bad Pauli string")
 
     def measure(self, qubit: int, r: float):
         """Measures one qubit with collapse; returns (outcome, its probability)."""

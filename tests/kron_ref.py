@@ -133,3 +133,18 @@ def tensor_run(n: int, gates, start_index: int = 0) -> np.ndarray:
         psi[sel] = sub
     # flatten: axis 0 is qubit n-1 -> C-order flattening gives index = label
     return psi.reshape(-1)
+
+
+def pauli_exp_unitary(n: int, x: int, z: int, controls: int, theta: float) -> np.ndarray:
+    """exp(-i theta/2 P) for the Pauli string with X at x-only bits, Z at z-only
+    bits and Y where both are set (qubit order as embed), as a controlled gate."""
+    ops = {}
+    for q in range(n):
+        bx, bz = (x >> q) & 1, (z >> q) & 1
+        if bx or bz:
+            ops[q] = PY if (bx and bz) else (PX if bx else PZ)
+    target = expm(-0.5j * theta * embed(n, ops))
+    if not controls:
+        return target
+    proj = embed(n, {c: P1 for c in range(n) if (controls >> c) & 1})
+    return (np.eye(1 << n, dtype=complex) - proj) + proj @ target

@@ -365,3 +365,45 @@ def test_measure_rejects_bad_arguments():
     for q, r in ((5, 0.5), (0, 1.0), (0, -0.1), (0, float("nan"))):
         with pytest.raises(ValueError):
             st.measure(q, r)
+
+
+# ---- Pauli exponentials ---------------------------------------------------------------
+def test_pauli_exp_matches_kron_definition():
+    """exp(-i theta/2 P) for random Pauli strings (X, Y and Z factors) with 0 or 1
+    control, on a random 5-qubit state: against scipy's matrix exponential of the
+    Kronecker product of the factors."""
+    n = 5
+    rng = W.SplitMix64(2024)
+    prep = W.to_array([W.H(0), W.Ry(1, 0.7), W.H(2), W.Rx(3, 1.9, 0), W.T(2), W.H(4),
+                       W.P(4, 0.3, 1)])
+    for trial in range(24):
+        x = rng.below(1 << n)
+        z = rng.below(1 << n)
+        if (x | z) == 0:
+            z = 1
+        free = [q for q in range(n) if not ((x | z) >> q) & 1]
+        c = (1 << free[rng.below(len(free))]) if free and trial % 2 else 0
+        theta = rng.angle()
+        want = kron_ref.pauli_exp_unitary(n, x, z, c, theta) @ kron_ref.kron_run(n, prep)
+        st = run_oracle(n, prep)
+        st.pauli_exp((x, 0), (z, 0), (c, 0), theta)
+        np.testing.assert_allclose(sparse_vector(st, n), want, atol=1e-12)
+
+
+def test_single_factor_exponentials_are_rotations():
+    """exp(-i t/2 X_q), exp(-i t/2 Y_q), exp(-i t/2 Z_q) equal Rx, Ry, Rz on q."""
+    n = 4
+    prep = W.to_array([W.H(0), W.Ry(1, 0.4), W.H(3), W.T(3)])
+    for (x, z), gate in (((1 << 2, 0), W.Rx), ((1 << 2, 1 << 2), W.Ry), ((0, 1 << 2), W.Rz)):
+        a = run_oracle(n, prep)
+        a.pauli_exp((x, 0), (z, 0), (0, 0), 0.9)
+        b = run_oracle(n, W.to_array(list(prep) + [gate(2, 0.9)]))
+        np.testing.assert_allclose(sparse_vector(a, n), sparse_vector(b, n), atol=1e-15)
+
+
+def test_pauli_exp_rejects_bad_strings():
+    st = OracleState(6)
+    for x, z, c in (((0, 0), (0, 0), (0, 0)), ((1 << 6, 0), (0, 0), (0, 0)),
+                    ((1, 0), (0, 0), (1, 0)), ((0, 0), (1 << 2, 0), (1 << 2, 0))):
+        with pytest.raises(ValueError):
+            st.pauli_exp(x, z, c, 0.5)
