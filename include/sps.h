@@ -169,6 +169,23 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
 sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
                                  double* out);
 
+/* Applies exp(-i theta/2 P) for a Pauli string P (Sec. 3 lists Pauli
+ * exponentials among the simulator's operations; Sec. 2.1 defines X, Y, Z and
+ * R_P(theta) = exp(-i theta P / 2)). x[2] marks the qubits whose factor is X or
+ * Y, z[2] those whose factor is Z or Y (Y where both are set; two words as in
+ * sps_gate.cmask); cmask[2] are controls, disjoint from the string. With
+ * P|j> = i^nY (-1)^popcount(j & z) |j ^ x> (nY = number of Y factors), a label
+ * j with every control set goes to cos(theta/2)|j> - i sin(theta/2) P|j>.
+ * A string with X or Y factors is one branching pass on the pairs (j, j ^ x)
+ * (Sec. 3.1), pruned with prune_eps; a string of Z factors only is diagonal
+ * and runs as a fused run (a CNOT ladder onto one z qubit, Rz, the ladder
+ * undone). Enqueues only, like sps_apply; counts as one gate for the update
+ * counter (the diagonal form counts its ladder). Errors: SPS_ERR_ARG for an
+ * empty string, masks beyond nqubits, controls on the string or a non-finite
+ * theta; device errors as for sps_apply (the failing gate is reported as 0). */
+sps_status sps_pauli_exp(sps_state* s, const uint64_t x[2], const uint64_t z[2],
+                         const uint64_t cmask[2], double theta, double prune_eps);
+
 /* Measures qubit `qubit` in the computational basis and collapses the state
  * (Sec. 2.1: outcome b has probability sum |alpha_k|^2 over the labels whose
  * bit `qubit` is b, and the state is projected onto those labels; Sec. 3 lists

@@ -3,6 +3,7 @@
 // the gate application runs in the kernels of sps_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -559,6 +560,66 @@ static uint64_t bound_after(const Pass& p, uint64_t b, uint64_t capacity) {
   return b < capacity ? b : capacity;
 }
 
+// One branching pass on the whole GPU (gather form, or scatter form when chosen
+// or when the capacity needs 64-bit table indices); advances the nonzero bound.
+static sps_status launch_branch_pass(sps_state* s, const LaunchCfg& lc, const BranchOp& op,
+                                     double prune_eps, uint32_t serial, uint64_t tag,
+                                     uint32_t limit) {
+  BranchLaunch b;
+  b.op = op;
+  b.eps = prune_eps;
+  b.load_pct = s->load_pct;
+  b.max_log2 = s->max_log2;
+  b.probe_limit = limit;
+  b.pass_serial = serial;
+  b.coop = s->coop;
+  b.capacity = s->capacity;
+  b.fail_tag = tag;
+  b.mg = s->masks.writer();   // the pass writes labels: compaction or gather emit
+  const bool scatter = s->branch_form == 1 || s->capacity >= (1ull << 32);
+  if (scatter) {
+    const sps_status ts = ensure_scatter_table(s);
+    if (ts != SPS_OK) return ts;
+    {
+      ProfScope ps(s, 2, serial, 1, 3u);
+      const int n = launch_branch_emit(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
+      ps.done();
+      if (n < 0) return cuda_ok(cudaGetLastError());
+    }
+    {
+      ProfScope ps(s, 3, serial, 1, 3u);
+      const int n = launch_branch_compact(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
+      ps.done();
+      if (n < 0) return cuda_ok(cudaGetLastError());
+    }
+  } else {
+    if (++s->epoch == 0x10000u) {  // the 16-bit epoch wrapped: make every slot free again
+      if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0) return cuda_ok(cudaGetLastError());
+      s->counters.kernel_launches += 1;
+      s->epoch = 1;
+    }
+    b.max_log2 = s->itab_log2;
+    ProfScope pb(s, 5, serial, 1, 3u);
+    int n = launch_gather_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, b, s->nnz_bound, 0, pb.slot);
+    pb.done();
+    if (n < 0) return cuda_ok(cudaGetLastError());
+    ProfScope pe(s, 6, serial, 1, 3u);
+    n = launch_gather_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, b, s->nnz_bound, 1, pe.slot);
+    pe.done();
+    if (n < 0) return cuda_ok(cudaGetLastError());
+  }
+  s->counters.branch_passes++;
+  s->counters.kernel_launches += 2;
+  const uint64_t nb = s->nnz_bound * 2;
+  s->nnz_bound = nb < s->capacity ? nb : s->capacity;
+  return SPS_OK;
+}
+
+static uint32_t probe_limit_of(const sps_state* s) {
+  return s->probe_limit ? s->probe_limit
+                        : (uint32_t)(s->table_slots > 0xFFFFFFFFull ? 0xFFFFFFFFu : s->table_slots);
+}
+
 // Options the compiled plan and its image depend on.
 static std::vector<uint64_t> plan_options(const sps_state* s) {
   return {s->nqubits, (uint64_t)s->kw, s->capacity, s->max_fused_ops, s->expand ? 1ull : 0ull,
@@ -828,53 +889,8 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       s->counters.fused_passes++;
       s->counters.kernel_launches += (uint64_t)n;
     } else {
-      BranchLaunch b;
-      b.op = p.br;
-      b.eps = prune_eps;
-      b.load_pct = s->load_pct;
-      b.max_log2 = s->max_log2;
-      b.probe_limit = limit;
-      b.pass_serial = serial;
-      b.coop = s->coop;
-      b.capacity = s->capacity;
-      b.fail_tag = tag;
-      b.mg = s->masks.writer();   // the pass writes labels: compaction or gather emit
-      const bool scatter = s->branch_form == 1 || s->capacity >= (1ull << 32);
-      if (scatter) {
-        const sps_status ts = ensure_scatter_table(s);
-        if (ts != SPS_OK) return ts;
-        {
-          ProfScope ps(s, 2, serial, 1, 3u);
-          const int n = launch_branch_emit(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
-          ps.done();
-          if (n < 0) return cuda_ok(cudaGetLastError());
-        }
-        {
-          ProfScope ps(s, 3, serial, 1, 3u);
-          const int n = launch_branch_compact(lc, s->kw, s->ctl, s->bufs, s->table, b, s->nnz_bound, ps.slot);
-          ps.done();
-          if (n < 0) return cuda_ok(cudaGetLastError());
-        }
-      } else {
-        if (++s->epoch == 0x10000u) {  // the 16-bit epoch wrapped: make every slot free again
-          if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0) return cuda_ok(cudaGetLastError());
-          s->counters.kernel_launches += 1;
-          s->epoch = 1;
-        }
-        b.max_log2 = s->itab_log2;
-        ProfScope pb(s, 5, serial, 1, 3u);
-        int n = launch_gather_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, b, s->nnz_bound, 0, pb.slot);
-        pb.done();
-        if (n < 0) return cuda_ok(cudaGetLastError());
-        ProfScope pe(s, 6, serial, 1, 3u);
-        n = launch_gather_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, b, s->nnz_bound, 1, pe.slot);
-        pe.done();
-        if (n < 0) return cuda_ok(cudaGetLastError());
-      }
-      s->counters.branch_passes++;
-      s->counters.kernel_launches += 2;
-      const uint64_t nb = s->nnz_bound * 2;
-      s->nnz_bound = nb < s->capacity ? nb : s->capacity;
+      const sps_status bs2 = launch_branch_pass(s, lc, p.br, prune_eps, serial, tag, limit);
+      if (bs2 != SPS_OK) return bs2;
     }
   }
   s->counters.gates += ngates;
@@ -1035,6 +1051,78 @@ sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uin
   s->counters.kernel_launches += 1;
   if (cudaMemcpyAsync(out, s->dresult, sizeof(double), cudaMemcpyDefault, s->stream) != cudaSuccess)
     return cuda_ok(cudaGetLastError());
+  return SPS_OK;
+}
+
+sps_status sps_pauli_exp(sps_state* s, const uint64_t x[2], const uint64_t z[2],
+                         const uint64_t cmask[2], double theta, double prune_eps) {
+  if (!s || !x || !z || !cmask || !(prune_eps >= 0.0) || !std::isfinite(theta)) return SPS_ERR_ARG;
+  uint64_t lim[2];
+  label_limits(s->nqubits, &lim[0], &lim[1]);
+  for (int w = 0; w < 2; ++w)
+    if (((x[w] | z[w] | cmask[w]) & ~lim[w]) || (cmask[w] & (x[w] | z[w]))) return SPS_ERR_ARG;
+  if ((x[0] | x[1] | z[0] | z[1]) == 0) return SPS_ERR_ARG;
+  if ((x[0] | x[1]) == 0) {
+    // A string of Z factors is diagonal: exp(-i t/2 P) multiplies a label by
+    // e^(-i t/2) or e^(i t/2) as the parity of its z bits is 0 or 1. A ladder of
+    // CNOTs puts that parity on the top z qubit, Rz(t) applies the phase, the
+    // ladder is undone: one fused run.
+    std::vector<uint32_t> bits;
+    for (uint32_t q = 0; q < s->nqubits; ++q)
+      if ((z[q >> 6] >> (q & 63)) & 1ull) bits.push_back(q);
+    const uint32_t t = bits.back();
+    std::vector<sps_gate> g;
+    auto rec = [&](uint8_t op, uint32_t tq, const uint64_t c[2], double th) {
+      sps_gate r;
+      std::memset(&r, 0, sizeof(r));
+      r.op = op;
+      r.t0 = (uint16_t)tq;
+      r.cmask[0] = c[0];
+      r.cmask[1] = c[1];
+      r.theta = th;
+      g.push_back(r);
+    };
+    for (size_t i = 0; i + 1 < bits.size(); ++i) {
+      const uint64_t c[2] = {bits[i] < 64 ? 1ull << bits[i] : 0ull,
+                             bits[i] >= 64 ? 1ull << (bits[i] - 64) : 0ull};
+      rec(SPS_OP_X, t, c, 0.0);
+    }
+    rec(SPS_OP_RZ, t, cmask, theta);
+    for (size_t i = bits.size() - 1; i-- > 0;) {
+      const uint64_t c[2] = {bits[i] < 64 ? 1ull << bits[i] : 0ull,
+                             bits[i] >= 64 ? 1ull << (bits[i] - 64) : 0ull};
+      rec(SPS_OP_X, t, c, 0.0);
+    }
+    return sps_apply(s, g.data(), g.size(), prune_eps, nullptr);
+  }
+  BranchOp op;
+  std::memset(&op, 0, sizeof(op));
+  op.c[0] = cmask[0];
+  op.c[1] = cmask[1];
+  op.m[0] = x[0];
+  op.m[1] = x[1];
+  op.sbit = x[0] ? (uint32_t)__builtin_ctzll(x[0]) : 64u + (uint32_t)__builtin_ctzll(x[1]);
+  op.pauli = 1;
+  op.pz[0] = z[0];
+  op.pz[1] = z[1];
+  op.ny = (uint32_t)(__builtin_popcountll(x[0] & z[0]) + __builtin_popcountll(x[1] & z[1])) & 3u;
+  op.m_re[0][0] = op.m_re[1][1] = std::cos(0.5 * theta);
+  op.psin = std::sin(0.5 * theta);
+  op.real_m = 0;
+  // knowledge: the flipped qubits vary afterwards unless a control is known 0
+  const bool never = ((cmask[0] & s->kb.known[0] & ~s->kb.val[0]) |
+                      (cmask[1] & s->kb.known[1] & ~s->kb.val[1])) != 0ull;
+  if (!never) {
+    s->kb.known[0] &= ~x[0];
+    s->kb.known[1] &= ~x[1];
+  }
+  const LaunchCfg lc = cfg_of(s);
+  ++s->apply_serial;
+  const uint32_t serial = ++s->pass_serial;
+  const uint64_t tag = (uint64_t)s->apply_serial << 32;
+  const sps_status bs = launch_branch_pass(s, lc, op, prune_eps, serial, tag, probe_limit_of(s));
+  if (bs != SPS_OK) return bs;
+  s->counters.gates += 1;
   return SPS_OK;
 }
 

@@ -144,7 +144,11 @@ __device__ bool branch_pass(const unsigned char* arena, const RunPass& rp, const
           const double a1r = x ? re : pre, a1i = x ? im : pim;
           l0 = x ? p0 : k0; h0 = x ? p1 : k1;
           l1 = x ? k0 : p0; h1 = x ? k1 : p1;
-          pair_action(op, j != EMPTY_IDX, x, a0r, a0i, a1r, a1i, &v0r, &v0i, &v1r, &v1i);
+          if (op.pauli)
+            pair_action(pauli_pair(op, l0, h0, l1, h1), j != EMPTY_IDX, x, a0r, a0i, a1r, a1i,
+                        &v0r, &v0i, &v1r, &v1i);
+          else
+            pair_action(op, j != EMPTY_IDX, x, a0r, a0i, a1r, a1i, &v0r, &v0i, &v1r, &v1i);
           w0 = keep_amp(v0r, v0i, rp.eps2, eps_bits);
           w1 = keep_amp(v1r, v1i, rp.eps2, eps_bits);
         }

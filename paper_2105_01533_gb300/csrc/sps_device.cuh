@@ -316,6 +316,27 @@ __device__ __forceinline__ void mat_times(const BranchOp& op, int row, int x, do
   }
 }
 
+// The 2x2 matrix of a Pauli exponential on one pair (k0: selector bit 0, k1: 1):
+// P|j> = phi(j)|j ^ x> with phi(j) = i^nY (-1)^popcount(j & z), so the entry
+// taking a(j) to j ^ x is -i sin(t/2) phi(j) = sin(t/2) i^(nY + 3 + 2 parity):
+// a real or an imaginary +-sin, never a sum. The diagonal is cos(t/2).
+__device__ __forceinline__ BranchOp pauli_pair(const BranchOp& op, uint64_t lo0, uint64_t hi0,
+                                               uint64_t lo1, uint64_t hi1) {
+  BranchOp m = op;
+  const int e0 = (int)(op.ny + 3u + 2u * (uint32_t)(__popcll(lo0 & op.pz[0]) +
+                                                    __popcll(hi0 & op.pz[1]))) & 3;
+  const int e1 = (int)(op.ny + 3u + 2u * (uint32_t)(__popcll(lo1 & op.pz[0]) +
+                                                    __popcll(hi1 & op.pz[1]))) & 3;
+  const double sn = op.psin;
+  m.m_re[1][0] = e0 == 0 ? sn : (e0 == 2 ? -sn : 0.0);   // from k0 to k1
+  m.m_im[1][0] = e0 == 1 ? sn : (e0 == 3 ? -sn : 0.0);
+  m.m_re[0][1] = e1 == 0 ? sn : (e1 == 2 ? -sn : 0.0);   // from k1 to k0
+  m.m_im[0][1] = e1 == 1 ? sn : (e1 == 3 ? -sn : 0.0);
+  m.m_im[0][0] = m.m_im[1][1] = 0.0;
+  m.real_m = 0;
+  return m;
+}
+
 // Both outputs of the 2x2 action on (a0, a1), the amplitudes of the labels with
 // selector bit 0 and 1: n0 = M00 a0 + M01 a1, n1 = M10 a0 + M11 a1, each
 // product and sum rounded once. With the partner absent one input is zero and

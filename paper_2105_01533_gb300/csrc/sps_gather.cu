@@ -156,7 +156,11 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
           const double a1r = x ? re : pre, a1i = x ? im : pim;
           l0 = x ? p0 : k0; h0 = x ? p1 : k1;
           l1 = x ? k0 : p0; h1 = x ? k1 : p1;
-          pair_action(op, j != ~0ull, x, a0r, a0i, a1r, a1i, &v0r, &v0i, &v1r, &v1i);
+          if (op.pauli)
+            pair_action(pauli_pair(op, l0, h0, l1, h1), j != ~0ull, x, a0r, a0i, a1r, a1i, &v0r,
+                        &v0i, &v1r, &v1i);
+          else
+            pair_action(op, j != ~0ull, x, a0r, a0i, a1r, a1i, &v0r, &v0i, &v1r, &v1i);
           w0 = keep_amp(v0r, v0i, a.eps2, eps_pattern(a.eps));
           w1 = keep_amp(v1r, v1i, a.eps2, eps_pattern(a.eps));
         }

@@ -70,6 +70,13 @@ struct BranchOp {
   uint32_t real_m;      // 1: every entry of M is real
   double m_re[2][2];
   double m_im[2][2];
+  // Pauli exponential exp(-i t/2 P) (pauli = 1): m = the X-or-Y mask of P, pz
+  // its Z-or-Y mask, ny = (number of Y factors) mod 4, m_re diagonal = cos(t/2),
+  // psin = sin(t/2); the off-diagonal entries depend on the pair (pauli_pair).
+  uint64_t pz[2];
+  uint32_t pauli;
+  uint32_t ny;
+  double psin;
 };
 
 // ---- bit-sliced form of a fused pass ------------------------------------------

@@ -390,14 +390,15 @@ __global__ void __launch_bounds__(256) k_branch_emit(Ctl* ctl, Bufs bufs, Slot* 
       // k0 side: the label whose selector bit is 0
       const uint64_t a0 = x ? f0 : k0, a1 = x ? f1 : k1;
       const uint64_t b0 = x ? k0 : f0, b1 = x ? k1 : f1;
-      if (op.m_re[0][xi] != 0.0 || op.m_im[0][xi] != 0.0) {
+      const BranchOp pm = op.pauli ? pauli_pair(op, a0, a1, b0, b1) : op;
+      if (pm.m_re[0][xi] != 0.0 || pm.m_im[0][xi] != 0.0) {
         double vr, vi;
-        mat_times(op, 0, xi, re, im, &vr, &vi);
+        mat_times(pm, 0, xi, re, im, &vr, &vi);
         ok = table_add<KW>(table, mask, a.probe_limit, a0, a1, vr, vi);
       }
-      if (ok && (op.m_re[1][xi] != 0.0 || op.m_im[1][xi] != 0.0)) {
+      if (ok && (pm.m_re[1][xi] != 0.0 || pm.m_im[1][xi] != 0.0)) {
         double vr, vi;
-        mat_times(op, 1, xi, re, im, &vr, &vi);
+        mat_times(pm, 1, xi, re, im, &vr, &vi);
         ok = table_add<KW>(table, mask, a.probe_limit, b0, b1, vr, vi);
       }
     }

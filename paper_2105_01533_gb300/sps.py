@@ -40,7 +40,7 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates",
            "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
-           "sps_server_completed", "sps_probability_async", "sps_measure")
+           "sps_server_completed", "sps_probability_async", "sps_measure", "sps_pauli_exp")
 
 
 class SpsError(RuntimeError):
@@ -123,6 +123,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_probability_async.restype = st
     lib.sps_measure.argtypes = [vp, u32, dbl, vp]
     lib.sps_measure.restype = st
+    lib.sps_pauli_exp.argtypes = [vp, vp, vp, vp, dbl, dbl]
+    lib.sps_pauli_exp.restype = st
     lib.sps_set_option.argtypes = [vp, ctypes.c_int, i64]
     lib.sps_set_option.restype = st
     lib.sps_get_counters.argtypes = [vp, ctypes.POINTER(Counters)]
@@ -332,6 +334,12 @@ def sps_measure(h: int, qubit: int, r: float, out_ptr: int) -> None:
            "sps_measure")
 
 
+def sps_pauli_exp(h: int, x, z, controls, theta: float, eps: float = 0.0) -> None:
+    xs, zs, cs = (np.array([int(v[0]), int(v[1])], np.uint64) for v in (x, z, controls))
+    _check(load_library().sps_pauli_exp(h, _ptr(xs), _ptr(zs), _ptr(cs), float(theta), float(eps)),
+           "sps_pauli_exp")
+
+
 def sps_set_option(h: int, opt: int, value: int) -> None:
     _check(load_library().sps_set_option(h, opt, int(value)), "sps_set_option")
 
@@ -451,6 +459,10 @@ class SparseState:
     def probability_async(self, mask, value, out_ptr: int) -> None:
         """Enqueue the probability into out_ptr (pinned host or device memory)."""
         sps_probability_async(self._h, mask, value, out_ptr)
+
+    def pauli_exp(self, x, z, controls, theta: float, eps: float = 0.0) -> None:
+        """exp(-i theta/2 P): x / z are the X-or-Y and Z-or-Y masks (two words)."""
+        sps_pauli_exp(self._h, x, z, controls, theta, eps)
 
     def measure(self, qubit: int, r: float):
         """Measure one qubit with collapse (r uniform in [0, 1)); waits and
