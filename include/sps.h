@@ -243,7 +243,7 @@ typedef enum sps_option {
                                   one-pass-per-gate within a few ulp rather than
                                   bit for bit; entries are pruned on the final
                                   amplitude). 0: one pass per gate */
-  SPS_OPT_FOLD = 13            /* 1 (default): in runs of phase/permutation gates,
+  SPS_OPT_FOLD = 13,           /* 1 (default): in runs of phase/permutation gates,
                                   qubits known to hold one value (tracked as for
                                   SPS_OPT_EXPAND) are resolved on the host: gates
                                   with a control known 0 are dropped, known
@@ -252,6 +252,14 @@ typedef enum sps_option {
                                   adjacent flips with one condition merge. The
                                   result is the same; the device walks fewer
                                   ops. 0: one op per gate */
+  SPS_OPT_COMMUTE = 14         /* 1: before compiling, rewrite each sps_apply
+                                  stream with gate commuting queues (see
+                                  sps_commute): H, Rx and Ry wait per qubit and
+                                  cancel, merge or let phase/permutation gates
+                                  pass. The state is the same up to rounding;
+                                  pruning applies to the rewritten stream, and
+                                  the update count counts the gates that run.
+                                  0 (default): gate by gate */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:
@@ -288,6 +296,20 @@ typedef struct sps_kernel_record {
 /* Synchronises, then moves up to `cap` records of profiled launches (oldest
  * first) into out[] and *n; records that do not fit stay queued. */
 sps_status sps_profile_read(sps_state* s, sps_kernel_record* out, size_t cap, size_t* n);
+
+/* Host-only: gate commuting queues (Sec. 3.3 and Fig. 1). Rewrites a gate list
+ * into one that computes the same state: H, Rx and Ry gates (without controls)
+ * wait in per-qubit queues (pending op Ry Rx H on the qubit, above a queue of
+ * phase/permutation gates); an incoming gate is commuted down through the
+ * queues of its qubits with H H = 1, Rx(a) Rx(b) = Rx(a+b), Ry likewise,
+ * H Ry(t) = Ry(-t) H, X Ry(t) = Ry(-t) X, Z Ry(t) = Ry(-t) Z, Z Rx(t) = Rx(-t) Z,
+ * X Rx = Rx X, X H = H Z and Z H = H X (controlled X and Z through H on the
+ * target); where no identity applies, the qubit's queue is emitted after the
+ * phase/permutation queue. Everything is emitted at the end. Writes up to cap
+ * records to out and the count to *nout (SPS_ERR_CAPACITY if more than cap).
+ * Errors: SPS_ERR_ARG with *failed_gate on a bad record. */
+sps_status sps_commute(const sps_gate* gates, size_t ngates, uint32_t nqubits, sps_gate* out,
+                       size_t cap, size_t* nout, size_t* failed_gate);
 
 /* Host-only: compiles a gate list for an nqubits-qubit state and describes the
  * passes without touching a GPU, for a state of which nothing is known (so no

@@ -82,6 +82,7 @@ struct sps_state {
   KnownBits kb;               // qubits known constant once every enqueued pass ran
   bool expand = true;         // SPS_OPT_EXPAND
   bool fold = true;           // SPS_OPT_FOLD
+  bool commute = false;       // SPS_OPT_COMMUTE
   int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
@@ -623,7 +624,8 @@ static uint32_t probe_limit_of(const sps_state* s) {
 // Options the compiled plan and its image depend on.
 static std::vector<uint64_t> plan_options(const sps_state* s) {
   return {s->nqubits, (uint64_t)s->kw, s->capacity, s->max_fused_ops, s->expand ? 1ull : 0ull,
-          s->fold ? 1ull : 0ull, s->small_cap, s->bitslice_min_ops, s->bitslice_min_nnz};
+          s->fold ? 1ull : 0ull, s->small_cap, s->bitslice_min_ops, s->bitslice_min_nnz,
+          s->commute ? 1ull : 0ull};
 }
 
 static bool plan_matches(const ApplyPlan& p, const sps_state* s, const sps_gate* gates,
@@ -640,9 +642,19 @@ static bool plan_matches(const ApplyPlan& p, const sps_state* s, const sps_gate*
 static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
                              ApplyPlan* P, size_t* bad) {
   P->kb_out = s->kb;
+  std::vector<sps_gate> rewritten;
+  std::vector<size_t> origin;
+  if (s->commute) {
+    const sps_status rs = commute_gates(gates, ngates, s->nqubits, &rewritten, &origin, bad);
+    if (rs != SPS_OK) return rs;
+    gates = rewritten.data();
+    ngates = rewritten.size();
+  }
   const sps_status cs = compile(gates, ngates, s->nqubits, s->max_fused_ops, &P->passes, bad,
                                 &P->kb_out, s->expand, s->fold);
   if (cs != SPS_OK) return cs;
+  if (s->commute)   // failures name the caller's gate
+    for (Pass& p : P->passes) p.first_gate = origin[p.first_gate];
   const std::vector<Pass>& passes = P->passes;
   const size_t np = passes.size();
   // 1. segments of consecutive passes that a small-state run can take: the
@@ -1174,6 +1186,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
       if (v != 0 && v != 1) return SPS_ERR_ARG;
       s->fold = v == 1;
       return SPS_OK;
+    case SPS_OPT_COMMUTE:
+      if (v != 0 && v != 1) return SPS_ERR_ARG;
+      s->commute = v == 1;
+      return SPS_OK;
     case SPS_OPT_BRANCH_FORM:
       if (v < 0 || v > 2) return SPS_ERR_ARG;
       s->branch_form = (int)v;
@@ -1225,6 +1241,24 @@ sps_status sps_plan(const sps_gate* gates, size_t ngates, uint32_t nqubits, uint
     if (first_gate) first_gate[i] = passes[i].first_gate;
     if (ops) ops[i] = passes[i].kind == PASS_FUSED ? (uint32_t)passes[i].ops.size() : 1u;
   }
+  return SPS_OK;
+}
+
+sps_status sps_commute(const sps_gate* gates, size_t ngates, uint32_t nqubits, sps_gate* out,
+                       size_t cap, size_t* nout, size_t* failed_gate) {
+  if ((ngates && !gates) || !nout || (cap && !out) || nqubits < 1 || nqubits > 127)
+    return SPS_ERR_ARG;
+  std::vector<sps_gate> g;
+  std::vector<size_t> origin;
+  size_t bad = 0;
+  const sps_status st = commute_gates(gates, ngates, nqubits, &g, &origin, &bad);
+  if (st != SPS_OK) {
+    if (failed_gate) *failed_gate = bad;
+    return st;
+  }
+  *nout = g.size();
+  if (g.size() > cap) return SPS_ERR_CAPACITY;
+  if (!g.empty()) std::memcpy(out, g.data(), g.size() * sizeof(sps_gate));
   return SPS_OK;
 }
 

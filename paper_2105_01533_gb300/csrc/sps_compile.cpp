@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "sps_internal.h"
 
@@ -301,7 +303,155 @@ void lower_known(const sps_gate& g, Pass* run, const KnownBits& k, uint64_t pend
   }
 }
 
+// ---- gate commuting queues (Sec. 3.3, Fig. 1) ------------------------------------
+// Queues per qubit an H, an Rx and an Ry; the pending operation on qubit q is
+// Ry(ay) Rx(ax) H^h (H first), above a queue of phase/permutation gates (applied
+// before all of them). An incoming gate is commuted down through the queues of
+// its qubits with the identities H H = 1, Rx(a) Rx(b) = Rx(a + b), Ry likewise,
+// H Ry(t) = Ry(-t) H, X Ry(t) = Ry(-t) X, Z Ry(t) = Ry(-t) Z, Z Rx(t) = Rx(-t) Z,
+// X commutes with Rx, and X H = H Z, Z H = H X (with controls where they hold:
+// C-X and C-Z through H on the target). Where no such identity applies, the
+// qubit's queue is flushed: the phase/permutation queue, then its H, Rx, Ry are
+// emitted. At the end everything is flushed, so the stream computes the same
+// state; gates that cancel or merge are never run.
+class Commuter {
+ public:
+  Commuter(uint32_t n, std::vector<sps_gate>* out, std::vector<size_t>* origin)
+      : q_(n), out_(out), origin_(origin) {}
+
+  void push(const sps_gate& g, size_t idx) {
+    const uint32_t t = g.t0;
+    const bool controlled = (g.cmask[0] | g.cmask[1]) != 0;
+    if (is_branch(g.op)) {
+      if (controlled || g.op == SPS_OP_GIVENS) {
+        flush_qubit(t);
+        if (g.op == SPS_OP_GIVENS) flush_qubit(g.t1);
+        flush_controls(g);
+        flush_perm();
+        emit(g, idx);
+        return;
+      }
+      Queue& e = q_[t];
+      if (g.op == SPS_OP_H) {
+        if (e.rx) flush_qubit(t);
+        if (e.ry) e.ay = -e.ay;
+        e.h = !e.h;
+        if (e.h) e.oh = idx;
+      } else if (g.op == SPS_OP_RX) {
+        if (e.ry) flush_qubit(t);
+        if (e.rx) {
+          e.ax += g.theta;
+        } else {
+          e.rx = true;
+          e.ax = g.theta;
+          e.ox = idx;
+        }
+      } else {   // Ry
+        if (e.ry) {
+          e.ay += g.theta;
+        } else {
+          e.ry = true;
+          e.ay = g.theta;
+          e.oy = idx;
+        }
+      }
+      return;
+    }
+    flush_controls(g);
+    sps_gate h = g;
+    Queue& e = q_[t];
+    if (e.any()) {
+      if (g.op == SPS_OP_X) {
+        if (e.ry && controlled) flush_qubit(t);
+        if (e.ry) e.ay = -e.ay;
+        if (e.h) h.op = SPS_OP_Z;   // C-X H = H C-Z (both on the target)
+      } else if (g.op == SPS_OP_Z) {
+        if ((e.ry || e.rx) && controlled) flush_qubit(t);
+        if (e.ry) e.ay = -e.ay;
+        if (e.rx) e.ax = -e.ax;
+        if (e.h) h.op = SPS_OP_X;   // C-Z H = H C-X
+      } else {
+        flush_qubit(t);
+      }
+    }
+    perm_.push_back({h, idx});
+  }
+
+  void finish() {
+    flush_perm();
+    for (uint32_t t = 0; t < q_.size(); ++t) emit_queue(t);
+  }
+
+ private:
+  struct Queue {
+    bool h = false, rx = false, ry = false;
+    double ax = 0.0, ay = 0.0;
+    size_t oh = 0, ox = 0, oy = 0;
+    bool any() const { return h || rx || ry; }
+  };
+
+  void emit(const sps_gate& g, size_t idx) {
+    out_->push_back(g);
+    origin_->push_back(idx);
+  }
+  void flush_perm() {
+    for (const auto& pg : perm_) emit(pg.first, pg.second);
+    perm_.clear();
+  }
+  void emit_queue(uint32_t t) {
+    Queue& e = q_[t];
+    sps_gate g;
+    std::memset(&g, 0, sizeof(g));
+    g.t0 = (uint16_t)t;
+    if (e.h) {
+      g.op = SPS_OP_H;
+      emit(g, e.oh);
+    }
+    if (e.rx) {
+      g.op = SPS_OP_RX;
+      g.theta = e.ax;
+      emit(g, e.ox);
+    }
+    if (e.ry) {
+      g.op = SPS_OP_RY;
+      g.theta = e.ay;
+      emit(g, e.oy);
+    }
+    e = Queue();
+  }
+  void flush_qubit(uint32_t t) {
+    if (!q_[t].any()) return;
+    flush_perm();
+    emit_queue(t);
+  }
+  void flush_controls(const sps_gate& g) {
+    for (int w = 0; w < 2; ++w)
+      for (uint64_t m = g.cmask[w]; m; m &= m - 1) flush_qubit(64 * w + (uint32_t)__builtin_ctzll(m));
+  }
+
+  std::vector<Queue> q_;
+  std::vector<std::pair<sps_gate, size_t>> perm_;
+  std::vector<sps_gate>* out_;
+  std::vector<size_t>* origin_;
+};
+
 }  // namespace
+
+sps_status commute_gates(const sps_gate* gates, size_t ngates, uint32_t nqubits,
+                         std::vector<sps_gate>* out, std::vector<size_t>* origin, size_t* bad) {
+  out->clear();
+  origin->clear();
+  for (size_t i = 0; i < ngates; ++i) {
+    if (!check(gates[i], nqubits)) {
+      if (bad) *bad = i;
+      return SPS_ERR_ARG;
+    }
+  }
+  Commuter c(nqubits, out, origin);
+  for (size_t i = 0; i < ngates; ++i) c.push(gates[i], i);
+  c.finish();
+  return SPS_OK;
+}
 
 sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                    uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad, KnownBits* kb,

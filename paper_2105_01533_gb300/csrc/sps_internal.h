@@ -212,6 +212,13 @@ constexpr uint32_t kMaxFusedPhases = 96;
 constexpr uint32_t kDefaultMaxFusedOps = kMaxFusedOps;
 
 // Validates and compiles; on a bad record returns SPS_ERR_ARG with *bad set.
+// Gate commuting queues (Sec. 3.3): rewrites the stream so that H, Rx and Ry
+// gates wait in per-qubit queues and cancel, merge or pass phase/permutation
+// gates where a commutation identity allows; origin[i] is the input index of
+// output gate i. Validates first (SPS_ERR_ARG with *bad).
+sps_status commute_gates(const sps_gate* gates, size_t ngates, uint32_t nqubits,
+                         std::vector<sps_gate>* out, std::vector<size_t>* origin, size_t* bad);
+
 // With kb (nullable) the compiler tracks the known-constant qubits through the
 // gates (updating *kb on success); if expand it forms expansion passes, if
 // fold it resolves known qubits in fused runs (lower_known).

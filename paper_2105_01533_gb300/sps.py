@@ -28,6 +28,7 @@ SPS_OPT_LOAD_FACTOR_PCT, SPS_OPT_PROBE_LIMIT, SPS_OPT_BLOCK_THREADS = 1, 2, 3
 SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
 SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP, SPS_OPT_BITSLICE_MIN_NNZ = 7, 8, 9
 SPS_OPT_BRANCH_FORM, SPS_OPT_BITSLICE_GROUPS, SPS_OPT_EXPAND, SPS_OPT_FOLD = 10, 11, 12, 13
+SPS_OPT_COMMUTE = 14
 KIND_SMALL_RUN, KIND_GATHER_BUILD, KIND_GATHER_EMIT = 4, 5, 6
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 
@@ -40,7 +41,8 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates",
            "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
-           "sps_server_completed", "sps_probability_async", "sps_measure", "sps_pauli_exp")
+           "sps_server_completed", "sps_probability_async", "sps_measure", "sps_pauli_exp",
+           "sps_commute")
 
 
 class SpsError(RuntimeError):
@@ -125,6 +127,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_measure.restype = st
     lib.sps_pauli_exp.argtypes = [vp, vp, vp, vp, dbl, dbl]
     lib.sps_pauli_exp.restype = st
+    lib.sps_commute.argtypes = [vp, sz, u32, vp, sz, psz, psz]
+    lib.sps_commute.restype = st
     lib.sps_set_option.argtypes = [vp, ctypes.c_int, i64]
     lib.sps_set_option.restype = st
     lib.sps_get_counters.argtypes = [vp, ctypes.POINTER(Counters)]
@@ -338,6 +342,19 @@ def sps_pauli_exp(h: int, x, z, controls, theta: float, eps: float = 0.0) -> Non
     xs, zs, cs = (np.array([int(v[0]), int(v[1])], np.uint64) for v in (x, z, controls))
     _check(load_library().sps_pauli_exp(h, _ptr(xs), _ptr(zs), _ptr(cs), float(theta), float(eps)),
            "sps_pauli_exp")
+
+
+def sps_commute(gates, nqubits: int) -> np.ndarray:
+    """Host-only gate commuting queues: the rewritten gate array (same state)."""
+    g = gate_array(gates)
+    cap = 4 * len(g) + 8
+    out = np.zeros(cap, dtype=g.dtype)
+    nout = ctypes.c_size_t(0)
+    bad = ctypes.c_size_t(0)
+    code = load_library().sps_commute(_ptr(g), len(g), nqubits, out.ctypes.data, cap,
+                                      ctypes.byref(nout), ctypes.byref(bad))
+    _check(code, "sps_commute", bad.value if code == SPS_ERR_ARG else None)
+    return out[:nout.value].copy()
 
 
 def sps_set_option(h: int, opt: int, value: int) -> None:

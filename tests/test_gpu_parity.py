@@ -513,3 +513,40 @@ def test_cached_plan_reports_failures():
             assert e.value.status == sps.SPS_ERR_CAPACITY and e.value.failed_gate == 6
             assert st.nnz() == 32
         st.close()
+
+
+def test_commuting_queues_on_the_device():
+    """SPS_OPT_COMMUTE: the rewritten stream runs on the device; the state equals
+    the oracle's gate-by-gate result, with fewer branching passes, and a
+    failure names the caller's gate."""
+    n = 24
+    rng = W.SplitMix64(9)
+    recs = []
+    for _ in range(300):
+        q = rng.distinct(10, 2)          # at most 2^10 labels
+        k = rng.below(6)
+        recs.append([W.H(q[0]), W.X(q[0]), W.Ry(q[0], rng.angle()), W.CX(q[1], q[0]),
+                     W.Z(q[0]), W.T(q[0])][k])
+    gates = W.to_array(recs)
+    orc = OracleState(n)
+    orc.apply(gates, eps=1e-14)
+    want = orc.get()
+    passes = []
+    for commute in (0, 1):
+        st = sps.SparseState(n, 1 << 16)
+        st.set_option(sps.SPS_OPT_COMMUTE, commute)
+        st.apply(gates, 1e-14)
+        compare_states(st.get_amplitudes(), want, 1e-14)
+        passes.append(st.counters().branch_passes)
+        st.close()
+    assert passes[1] < passes[0]
+    st = sps.SparseState(20, 40)
+    st.set_option(sps.SPS_OPT_COMMUTE, 1)
+    st.set_option(sps.SPS_OPT_EXPAND, 0)
+    g = W.to_array([W.H(q) for q in range(5)] + [W.X(9), W.T(7), W.H(10), W.T(10)])
+    # T(10) flushes H(10) early; the queued H(0..4) run at the end, H(4) makes 64 > 40
+    st.apply(g, 0.0)
+    with pytest.raises(sps.SpsError) as e:
+        st.sync()
+    assert e.value.status == sps.SPS_ERR_CAPACITY and e.value.failed_gate == 4
+    st.close()
