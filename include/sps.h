@@ -252,7 +252,7 @@ typedef enum sps_option {
                                   adjacent flips with one condition merge. The
                                   result is the same; the device walks fewer
                                   ops. 0: one op per gate */
-  SPS_OPT_COMMUTE = 14         /* 1: before compiling, rewrite each sps_apply
+  SPS_OPT_COMMUTE = 14,        /* 1: before compiling, rewrite each sps_apply
                                   stream with gate commuting queues (see
                                   sps_commute): H, Rx and Ry wait per qubit and
                                   cancel, merge or let phase/permutation gates
@@ -260,6 +260,16 @@ typedef enum sps_option {
                                   pruning applies to the rewritten stream, and
                                   the update count counts the gates that run.
                                   0 (default): gate by gate */
+  SPS_OPT_LAYER_GATES = 15     /* most branching gates in one layer pass, 1..4
+                                  (default 4; 1 = one pass per gate): consecutive
+                                  branching gates on pairwise disjoint qubits
+                                  (targets and controls) run as one gather pass
+                                  in which the member of each group with the
+                                  largest selector pattern applies the gates in
+                                  order to the group, with the same products,
+                                  sums and pruning as one pass per gate (bit for
+                                  bit). Not used inside one-block runs or with
+                                  the scatter form */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:

@@ -83,6 +83,7 @@ struct sps_state {
   bool expand = true;         // SPS_OPT_EXPAND
   bool fold = true;           // SPS_OPT_FOLD
   bool commute = false;       // SPS_OPT_COMMUTE
+  uint32_t layer_max = kMaxLayerGates;   // SPS_OPT_LAYER_GATES
   int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
@@ -557,6 +558,7 @@ static uint64_t bound_after(const Pass& p, uint64_t b, uint64_t capacity) {
   uint32_t doublings = 0;
   if (p.kind == PASS_BRANCH) doublings = 1;
   if (p.kind == PASS_EXPAND) doublings = p.ex_d;
+  if (p.kind == PASS_LAYER) doublings = (uint32_t)p.lay.size();
   for (uint32_t k = 0; k < doublings && b < capacity; ++k) b *= 2;
   return b < capacity ? b : capacity;
 }
@@ -625,7 +627,7 @@ static uint32_t probe_limit_of(const sps_state* s) {
 static std::vector<uint64_t> plan_options(const sps_state* s) {
   return {s->nqubits, (uint64_t)s->kw, s->capacity, s->max_fused_ops, s->expand ? 1ull : 0ull,
           s->fold ? 1ull : 0ull, s->small_cap, s->bitslice_min_ops, s->bitslice_min_nnz,
-          s->commute ? 1ull : 0ull};
+          s->commute ? 1ull : 0ull, s->layer_max};
 }
 
 static bool plan_matches(const ApplyPlan& p, const sps_state* s, const sps_gate* gates,
@@ -651,10 +653,36 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
     ngates = rewritten.size();
   }
   const sps_status cs = compile(gates, ngates, s->nqubits, s->max_fused_ops, &P->passes, bad,
-                                &P->kb_out, s->expand, s->fold);
+                                &P->kb_out, s->expand, s->fold, s->layer_max);
   if (cs != SPS_OK) return cs;
-  if (s->commute)   // failures name the caller's gate
-    for (Pass& p : P->passes) p.first_gate = origin[p.first_gate];
+  // layers that a one-block run would take go back to one pass per gate (the
+  // one-block engine runs passes, the layer kernels are whole-GPU)
+  if (s->small_cap) {
+    std::vector<Pass> split;
+    uint64_t b = s->nnz_bound;
+    for (Pass& p : P->passes) {
+      if (p.kind == PASS_LAYER && b <= s->small_cap) {
+        for (size_t j = 0; j < p.lay.size(); ++j) {
+          Pass q;
+          q.kind = PASS_BRANCH;
+          q.first_gate = p.lay_gate[j];
+          q.br = p.lay[j];
+          b = bound_after(q, b, s->capacity);
+          split.push_back(std::move(q));
+        }
+        continue;
+      }
+      b = bound_after(p, b, s->capacity);
+      split.push_back(std::move(p));
+    }
+    P->passes.swap(split);
+  }
+  if (s->commute) {   // failures name the caller's gate
+    for (Pass& p : P->passes) {
+      p.first_gate = origin[p.first_gate];
+      for (uint64_t& g : p.lay_gate) g = origin[g];
+    }
+  }
   const std::vector<Pass>& passes = P->passes;
   const size_t np = passes.size();
   // 1. segments of consecutive passes that a small-state run can take: the
@@ -862,6 +890,46 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       if (n < 0) return cuda_ok(cudaGetLastError());
       s->counters.branch_passes++;
       s->counters.kernel_launches += 1;
+      s->nnz_bound = bound_after(p, s->nnz_bound, s->capacity);
+      continue;
+    }
+    if (p.kind == PASS_LAYER) {
+      const bool scatter = s->branch_form == 1 || s->capacity >= (1ull << 32);
+      if (scatter) {   // the layer kernels are gather-form: one pass per gate
+        for (size_t j = 0; j < p.lay.size(); ++j) {
+          const uint64_t tg = ((uint64_t)s->apply_serial << 32) | (p.lay_gate[j] & 0xFFFFFFFFull);
+          const sps_status bs2 = launch_branch_pass(s, lc, p.lay[j], prune_eps,
+                                                    j ? ++s->pass_serial : serial, tg, limit);
+          if (bs2 != SPS_OK) return bs2;
+        }
+        continue;
+      }
+      if (++s->epoch == 0x10000u) {  // the 16-bit epoch wrapped: make every slot free again
+        if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0) return cuda_ok(cudaGetLastError());
+        s->counters.kernel_launches += 1;
+        s->epoch = 1;
+      }
+      LayerLaunch l;
+      std::memset(&l, 0, sizeof(l));
+      l.d = (uint32_t)p.lay.size();
+      for (uint32_t j = 0; j < l.d; ++j) l.ops[j] = p.lay[j];
+      l.eps = prune_eps;
+      l.load_pct = s->load_pct;
+      l.max_log2 = s->itab_log2;
+      l.pass_serial = serial;
+      l.mg = s->masks.writer();
+      l.capacity = s->capacity;
+      l.fail_tag = tag;
+      ProfScope pb(s, 5, serial, l.d, 3u);
+      int n = launch_layer_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, l, s->nnz_bound, 0, pb.slot);
+      pb.done();
+      if (n < 0) return cuda_ok(cudaGetLastError());
+      ProfScope pe(s, 6, serial, l.d, 3u);
+      n = launch_layer_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, l, s->nnz_bound, 1, pe.slot);
+      pe.done();
+      if (n < 0) return cuda_ok(cudaGetLastError());
+      s->counters.branch_passes++;
+      s->counters.kernel_launches += 2;
       s->nnz_bound = bound_after(p, s->nnz_bound, s->capacity);
       continue;
     }
@@ -1189,6 +1257,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_COMMUTE:
       if (v != 0 && v != 1) return SPS_ERR_ARG;
       s->commute = v == 1;
+      return SPS_OK;
+    case SPS_OPT_LAYER_GATES:
+      if (v < 1 || v > (int64_t)kMaxLayerGates) return SPS_ERR_ARG;
+      s->layer_max = (uint32_t)v;
       return SPS_OK;
     case SPS_OPT_BRANCH_FORM:
       if (v < 0 || v > 2) return SPS_ERR_ARG;

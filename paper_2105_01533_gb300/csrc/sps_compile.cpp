@@ -455,7 +455,8 @@ sps_status commute_gates(const sps_gate* gates, size_t ngates, uint32_t nqubits,
 
 sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                    uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad, KnownBits* kb,
-                   bool expand, bool fold) {
+                   bool expand, bool fold, uint32_t layer_max) {
+  if (layer_max > kMaxLayerGates) layer_max = kMaxLayerGates;
   if (max_fused_ops == 0 || max_fused_ops > kMaxFusedOps) max_fused_ops = kDefaultMaxFusedOps;
   out->clear();
   for (size_t i = 0; i < ngates; ++i) {
@@ -469,6 +470,7 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
   const bool fold_known = kb != nullptr && fold;
   Pass* run = nullptr;
   Pass* ex = nullptr;
+  Pass* lay = nullptr;   // the last pass, while it is a branch or layer pass
   uint64_t pending[2] = {0ull, 0ull};
   auto close_run = [&]() {
     if (run && (pending[0] | pending[1])) append_flip(run, 0ull, 0ull, pending[0], pending[1]);
@@ -492,16 +494,42 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
         }
         ex->ex_ops.push_back(p.br);
         ex->ex_x.push_back(kb_val(k, g.t0) ? 1 : 0);
+        lay = nullptr;
         track(g, k);
         continue;
       }
       ex = nullptr;
+      Mask128 sup;
+      sup.w[0] = g.cmask[0];
+      sup.w[1] = g.cmask[1];
+      sup.set(g.t0);
+      if (g.op == SPS_OP_GIVENS) sup.set(g.t1);
+      if (lay != nullptr) {
+        const size_t have = lay->kind == PASS_LAYER ? lay->lay.size() : 1;
+        if (have < layer_max && ((lay->sup[0] & sup.w[0]) | (lay->sup[1] & sup.w[1])) == 0) {
+          if (lay->kind == PASS_BRANCH) {
+            lay->kind = PASS_LAYER;
+            lay->lay.push_back(lay->br);
+            lay->lay_gate.push_back(lay->first_gate);
+          }
+          lay->lay.push_back(p.br);
+          lay->lay_gate.push_back(i);
+          lay->sup[0] |= sup.w[0];
+          lay->sup[1] |= sup.w[1];
+          track(g, k);
+          continue;
+        }
+      }
       p.kind = PASS_BRANCH;
+      p.sup[0] = sup.w[0];
+      p.sup[1] = sup.w[1];
       out->push_back(std::move(p));
+      lay = &out->back();
       track(g, k);
       continue;
     }
     ex = nullptr;
+    lay = nullptr;
     const uint32_t slots = g.op == SPS_OP_P ? 1u : (g.op == SPS_OP_RZ ? 2u : 0u);
     // folding may add two flips (a materialised known qubit, the pending ones)
     const size_t room = fold_known ? 2 : 0;

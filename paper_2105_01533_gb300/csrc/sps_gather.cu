@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "sps_device.cuh"
 #include "sps_internal.h"
@@ -415,6 +416,284 @@ __global__ void k_itab_clear(unsigned long long* itab, uint64_t nslots) {
     itab[i] = 0ull;
 }
 
+// ---------------------------------------------------------------------------
+// Layer pass: d <= 4 branching gates on pairwise disjoint qubits, in one
+// gather pass with the same arithmetic and pruning points as d passes.
+// A label k activates the gates whose controls (and Givens condition) it
+// satisfies; the flips of its active gates span its group {k ^ m(S)}, and every
+// member activates the same gates (no gate flips another's qubits). Members
+// that differ from k only in gates with partners possible (flip qubits not
+// constant, from the label masks) are looked up in the index; the present
+// member with the largest selector pattern over those gates writes the group:
+// it runs the gates in order over the group's amplitude vector (pair actions
+// on its pairs, pruning after each gate as a pass would; an inactive gate only
+// prunes) and emits the survivors. It also counts the nonzeros before each
+// gate, so the update count is exact.
+struct LayerArgs {
+  BranchOp ops[kMaxLayerGates];
+  uint32_t d;
+  double eps2, eps;
+  uint64_t capacity, fail_tag;
+  uint32_t load_pct, max_log2, pass_serial, epoch, mg;
+};
+
+template <int KW>
+__device__ __forceinline__ uint32_t layer_active(const LayerArgs& a, uint64_t k0, uint64_t k1) {
+  uint32_t act = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kMaxLayerGates; ++j) {
+    if (j < a.d) {
+      const BranchOp& op = a.ops[j];
+      bool on = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
+      if (op.givens) on = on && (label_bit(k0, k1, op.sbit) != label_bit(k0, k1, op.qbit));
+      act |= on ? (1u << j) : 0u;
+    }
+  }
+  return act;
+}
+
+// Gates whose flip qubits are not constant over the state: only those can pair.
+__device__ __forceinline__ uint32_t layer_pairable(const LayerArgs& a, const LabelMasks& lm) {
+  uint32_t p = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kMaxLayerGates; ++j)
+    if (j < a.d && !flip_bits_constant(lm, a.ops[j].m)) p |= 1u << j;
+  return p;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_layer_build(Ctl* ctl, Bufs bufs, unsigned long long* itab,
+                                                     const __grid_constant__ LayerArgs a,
+                                                     unsigned long long* plog) {
+  const uint64_t n = ctl->nnz;
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+    plog[0] = n;
+    plog[1] = 0ull;
+  }
+  if (__syncthreads_or(ctl->status != 0u)) return;
+  const uint32_t pairable = layer_pairable(a, read_label_masks_block(ctl, mg_rd(a.mg)));
+  if (pairable == 0u) return;
+  const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
+  const SoA s = pick(bufs, ctl->cur);
+  const unsigned long long ep = (unsigned long long)a.epoch << 48;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k0 = s.lo[i];
+    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    if ((layer_active<KW>(a, k0, k1) & pairable) == 0u) continue;   // never looked up
+    const uint64_t hv = hash_label<KW>(k0, k1);
+    const unsigned long long mine = ep | ((hv >> 48) << 32) | i;
+    uint64_t h = hv & mask;
+    bool ok = false;
+    for (uint64_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
+      const unsigned long long v = __ldcg(itab + h);
+      if ((v & 0xFFFF000000000000ull) == ep) continue;
+      if (atomicCAS(itab + h, v, mine) == v) {
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) {
+      fail(ctl, SPS_ERR_TABLE_FULL, a.pass_serial, a.fail_tag);
+      return;
+    }
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_layer_emit(Ctl* ctl, Bufs bufs,
+                                                    const unsigned long long* itab,
+                                                    const __grid_constant__ LayerArgs a,
+                                                    unsigned long long* plog) {
+  __shared__ unsigned warp_cnt[32];
+  __shared__ unsigned long long block_base;
+  if (__syncthreads_or(ctl->status != 0u)) return;
+  const uint64_t n = ctl->nnz;
+  const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
+  const unsigned cur = ctl->cur;
+  const SoA s = pick(bufs, cur);
+  const SoA out = pick(bufs, cur ^ 1u);
+  const unsigned long long ep = (unsigned long long)a.epoch << 48;
+  const uint32_t pairable = layer_pairable(a, read_label_masks_block(ctl, mg_rd(a.mg)));
+  if (blockIdx.x == 0 && threadIdx.x == 0) reset_label_masks(ctl, mg_rs(a.mg));
+  const uint64_t eps_bits = eps_pattern(a.eps);
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned nwarps = blockDim.x >> 5;
+  uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;
+  unsigned long long upd = 0;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    double vr[16], vi[16];
+    uint32_t present = 0;   // bit u: member u of the group survives
+    uint32_t act = 0;
+    uint64_t k0 = 0, k1 = 0;
+    uint32_t u_me = 0;
+    if (i < n) {
+      k0 = s.lo[i];
+      k1 = KW == 2 ? s.hi[i] : 0ull;
+      act = layer_active<KW>(a, k0, k1);
+      // member index: bit b = the selector of the b-th active gate
+      uint32_t lpos = 0;   // positions (in member-index bits) of pairable active gates
+      {
+        uint32_t b = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < kMaxLayerGates; ++j) {
+          if ((act >> j) & 1u) {
+            if (label_bit(k0, k1, a.ops[j].sbit)) u_me |= 1u << b;
+            if ((pairable >> j) & 1u) lpos |= 1u << b;
+            ++b;
+          }
+        }
+      }
+      present = 1u << u_me;
+      vr[u_me] = s.re[i];
+      vi[u_me] = s.im[i];
+      bool writer = true;
+      // the other members that may be present: flips of subsets of lpos
+      for (uint32_t sm = lpos; sm != 0u && writer; sm = (sm - 1u) & lpos) {
+        uint64_t p0 = k0, p1 = k1;
+        uint32_t b = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < kMaxLayerGates; ++j) {
+          if ((act >> j) & 1u) {
+            if ((sm >> b) & 1u) {
+              p0 ^= a.ops[j].m[0];
+              p1 ^= a.ops[j].m[1];
+            }
+            ++b;
+          }
+        }
+        const uint64_t jx = find_label<KW>(itab, mask, ep, s, p0, p1);
+        if (jx == ~0ull) continue;
+        const uint32_t u = u_me ^ sm;
+        if ((u & lpos) > (u_me & lpos)) {
+          writer = false;   // a member with a larger pattern writes the group
+        } else {
+          present |= 1u << u;
+          vr[u] = s.re[jx];
+          vi[u] = s.im[jx];
+        }
+      }
+      if (!writer) {
+        present = 0u;
+      } else {
+        uint32_t b = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < kMaxLayerGates; ++j) {
+          if (j < a.d) {
+            upd += __popc(present);   // nonzeros of the group before gate j
+            if ((act >> j) & 1u) {
+              const uint32_t na = __popc(act);
+              for (uint32_t u = 0; u < (1u << na); ++u) {
+                if ((u >> b) & 1u) continue;
+                const uint32_t u1 = u | (1u << b);
+                const bool q0 = (present >> u) & 1u, q1 = (present >> u1) & 1u;
+                if (!q0 && !q1) continue;
+                double n0r, n0i, n1r, n1i;
+                pair_action(a.ops[j], q0 && q1, q1 && !q0, q0 ? vr[u] : 0.0, q0 ? vi[u] : 0.0,
+                            q1 ? vr[u1] : 0.0, q1 ? vi[u1] : 0.0, &n0r, &n0i, &n1r, &n1i);
+                vr[u] = n0r;
+                vi[u] = n0i;
+                vr[u1] = n1r;
+                vi[u1] = n1i;
+                const bool w0 = keep_amp(n0r, n0i, a.eps2, eps_bits);
+                const bool w1 = keep_amp(n1r, n1i, a.eps2, eps_bits);
+                present = (present & ~((1u << u) | (1u << u1))) | (w0 ? 1u << u : 0u) |
+                          (w1 ? 1u << u1 : 0u);
+              }
+              ++b;
+            } else {
+              for (uint32_t pr = present; pr; pr &= pr - 1u) {
+                const uint32_t u = __ffs(pr) - 1u;
+                if (!keep_amp(vr[u], vi[u], a.eps2, eps_bits)) present &= ~(1u << u);
+              }
+            }
+          }
+        }
+      }
+    }
+    // compaction: each thread writes its surviving members contiguously
+    const uint32_t cnt = __popc(present);
+    uint32_t incl = cnt;
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, incl, dd);
+      if (lane >= (unsigned)dd) incl += t;
+    }
+    if (lane == 31) warp_cnt[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned v = lane < nwarps ? warp_cnt[lane] : 0u;
+      unsigned winc = v;
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL, winc, dd);
+        if (lane >= (unsigned)dd) winc += t;
+      }
+      const unsigned tot = __shfl_sync(FULL, winc, 31);
+      if (lane < nwarps) warp_cnt[lane] = winc - v;
+      if (lane == 0) block_base = tot ? atomicAdd(&ctl->out_count, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    uint64_t pos = block_base + warp_cnt[warp] + (incl - cnt);
+    for (uint32_t pr = present; pr; pr &= pr - 1u) {
+      const uint32_t u = __ffs(pr) - 1u;
+      uint64_t l0 = k0, l1 = k1;
+      uint32_t b = 0;
+#pragma unroll
+      for (uint32_t j = 0; j < kMaxLayerGates; ++j) {
+        if ((act >> j) & 1u) {
+          if (((u ^ u_me) >> b) & 1u) {
+            l0 ^= a.ops[j].m[0];
+            l1 ^= a.ops[j].m[1];
+          }
+          ++b;
+        }
+      }
+      if (pos < a.capacity) {
+        out.lo[pos] = l0;
+        if (KW == 2) out.hi[pos] = l1;
+        out.re[pos] = vr[u];
+        out.im[pos] = vi[u];
+      }
+      ++pos;
+      mo0 |= l0;
+      mo1 |= l1;
+      ma0 &= l0;
+      ma1 &= l1;
+    }
+    __syncthreads();
+  }
+  merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
+  // exact update count: the group writers' per-gate sizes
+  for (int dd = 16; dd > 0; dd >>= 1) upd += __shfl_xor_sync(FULL, upd, dd);
+  if (lane == 0 && upd) atomicAdd(&ctl->updates, upd);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long total = atomicAdd(&ctl->out_count, 0ull);
+      bool published = false;
+      if (ctl->status == 0u) {
+        if (total > a.capacity) {
+          fail(ctl, SPS_ERR_CAPACITY, a.pass_serial, a.fail_tag);
+        } else {
+          ctl->nnz = total;
+          ctl->cur = cur ^ 1u;
+          published = true;
+        }
+      }
+      if (plog) {
+        plog[0] = n;
+        plog[1] = published ? total : n;
+      }
+      ctl->out_count = 0ull;
+      ctl->blocks_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
 int grid_of(uint64_t work, int threads, int max_blocks) {
   uint64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -423,6 +702,38 @@ int grid_of(uint64_t work, int threads, int max_blocks) {
 }
 
 }  // namespace
+
+int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                      unsigned long long* itab, uint32_t epoch, const LayerLaunch& l,
+                      uint64_t nnz_bound, int part, unsigned long long* plog) {
+  LayerArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (uint32_t j = 0; j < l.d; ++j) a.ops[j] = l.ops[j];
+  a.d = l.d;
+  a.eps2 = l.eps * l.eps;
+  a.eps = l.eps;
+  a.capacity = l.capacity;
+  a.fail_tag = l.fail_tag;
+  a.load_pct = l.load_pct;
+  a.max_log2 = l.max_log2;
+  a.pass_serial = l.pass_serial;
+  a.epoch = epoch;
+  a.mg = l.mg;
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
+  if (part == 0) {
+    if (key_words == 1)
+      k_layer_build<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    else
+      k_layer_build<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+  } else {
+    if (key_words == 1)
+      k_layer_emit<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    else
+      k_layer_emit<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_itab_clear(const LaunchCfg& lc, unsigned long long* itab, uint64_t nslots) {
   k_itab_clear<<<grid_of(nslots, lc.threads, lc.max_blocks), lc.threads, 0,

@@ -140,7 +140,11 @@ struct Pass;
 void encode_ops(Pass* p);
 
 // ---- a compiled pass -----------------------------------------------------------
-enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2, PASS_EXPAND = 3 };
+enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2, PASS_EXPAND = 3, PASS_LAYER = 4 };
+
+// Layer pass: up to kMaxLayerGates consecutive branching gates whose qubits
+// (targets and controls) are pairwise disjoint, applied in one gather pass.
+constexpr uint32_t kMaxLayerGates = 4;
 
 // Qubits known (on the host, conservatively) to hold one value in every stored
 // label: bit q of known set => every label has bit q = bit q of val.
@@ -170,6 +174,10 @@ struct Pass {
   uint32_t fire_slots = 0;  // aux bits its arbitrary phases need in bit-sliced form
   // branch
   BranchOp br{};
+  uint64_t sup[2] = {0ull, 0ull};   // branch / layer: qubits its gates touch
+  // layer
+  std::vector<BranchOp> lay;        // its gates, in order
+  std::vector<uint64_t> lay_gate;   // the index of each in the stream
   // expand
   std::vector<BranchOp> ex_ops; // its gates, in order
   std::vector<uint8_t> ex_x;    // value of each gate's selector qubit before it
@@ -222,9 +230,11 @@ sps_status commute_gates(const sps_gate* gates, size_t ngates, uint32_t nqubits,
 // With kb (nullable) the compiler tracks the known-constant qubits through the
 // gates (updating *kb on success); if expand it forms expansion passes, if
 // fold it resolves known qubits in fused runs (lower_known).
+// layer_max > 1 groups consecutive disjoint branching gates into layer passes.
 sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                    uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad,
-                   KnownBits* kb = nullptr, bool expand = false, bool fold = false);
+                   KnownBits* kb = nullptr, bool expand = false, bool fold = false,
+                   uint32_t layer_max = 1);
 
 // ---- device-side control block -------------------------------------------------
 constexpr int kMaskStripes = 32;
@@ -341,6 +351,18 @@ int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        unsigned long long* itab, uint32_t epoch, const BranchLaunch& b,
                        uint64_t nnz_bound, int part, unsigned long long* plog);
 int launch_itab_clear(const LaunchCfg& lc, unsigned long long* itab, uint64_t nslots);
+// Layer pass (PASS_LAYER), gather form: part 0 indexes the labels that may be
+// looked up, part 1 writes every group once (see sps_gather.cu).
+struct LayerLaunch {
+  BranchOp ops[kMaxLayerGates];
+  uint32_t d;
+  double eps;
+  uint32_t load_pct, max_log2, pass_serial, mg;
+  uint64_t capacity, fail_tag;
+};
+int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                      unsigned long long* itab, uint32_t epoch, const LayerLaunch& l,
+                      uint64_t nnz_bound, int part, unsigned long long* plog);
 // Expansion pass (PASS_EXPAND); f, m: its tables in device memory.
 struct ExpandLaunch {
   const double* f;
