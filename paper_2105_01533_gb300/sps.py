@@ -179,7 +179,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_server_poll.restype = st
     lib.sps_server_result.argtypes = [vp, u64, vp, vp, vp, vp, u64, pu64]
     lib.sps_server_result.restype = st
-    lib.sps_server_completed.argtypes = [vp, pu64, sz, psz]
+    lib.sps_server_completed.argtypes = [vp, vp, sz, psz]
     lib.sps_server_completed.restype = st
     lib.sps_server_stats.argtypes = [vp, pu64, pu64, pu64]
     lib.sps_server_stats.restype = st

@@ -72,6 +72,26 @@ def test_served_mix_equals_alone(passes_per_tick):
     srv.close()
 
 
+def test_completed_lists_each_request_once():
+    """sps_server_completed reports the requests that finished in the last tick:
+    over the whole run every request appears exactly once, after it is done."""
+    reqs = [(20 + 3 * k, 256, W.to_array([W.H(q) for q in range(k % 5 + 1)] + [W.X(19)]))
+            for k in range(12)]
+    srv = sps.Server(mem_budget_bytes=1 << 26, max_active=16, passes_per_tick=2)
+    ids = [srv.submit(nq, cap, g, EPS) for nq, cap, g in reqs]
+    seen = []
+    for _ in range(10000):
+        srv.tick()
+        done_now = srv.completed()
+        for i in done_now:
+            assert srv.poll(i)["state"] == 2
+        seen += done_now
+        if all(srv.poll(i)["state"] == 2 for i in ids):
+            break
+    assert sorted(seen) == sorted(ids)
+    srv.close()
+
+
 def test_admission_follows_budget_and_order():
     reqs = request_mix()[:10]          # small random mixes
     need = max(64 * cap for _, cap, _ in reqs) + 64 * 1024
