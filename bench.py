@@ -191,7 +191,8 @@ def measured_peaks():
 
 
 KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact", 4: "k_small_run",
-              5: "k_gather_build", 6: "k_gather_emit", 7: "k_expand"}
+              5: "k_gather_build", 6: "k_gather_emit", 7: "k_expand", 8: "k_measure",
+              9: "k_amp_index", 10: "k_amp_layer"}
 
 
 def algorithmic_bytes(r) -> float:
@@ -205,9 +206,9 @@ def algorithmic_bytes(r) -> float:
         return per * r["n_in"]
     if r["kind"] == 2:
         return (lb + 16) * r["n_in"]
-    if r["kind"] in (4, 6, 7):   # read the old state once, write the new one once
+    if r["kind"] in (4, 6, 7, 10):   # read the old state once, write the new one once
         return (lb + 16) * (r["n_in"] + r["n_out"])
-    if r["kind"] == 5:        # index the input labels
+    if r["kind"] in (5, 9):   # index the input labels
         return lb * r["n_in"]
     return (lb + 16) * r["n_out"]
 

@@ -269,7 +269,34 @@ typedef enum sps_option {
                                   order to the group, with the same products,
                                   sums and pruning as one pass per gate (bit for
                                   bit). Not used inside one-block runs or with
-                                  the scatter form */
+                                  the scatter form */,
+  SPS_OPT_EXPAND_WALK = 16     /* 1 (default): a run of phase/permutation gates
+                                  right after an expansion pass (SPS_OPT_EXPAND)
+                                  is applied by the expansion kernel to its
+                                  outputs before they are stored: one launch,
+                                  the state written once, the same values bit
+                                  for bit (as the direct fused form; a run that
+                                  takes the bit-sliced form, see
+                                  SPS_OPT_BITSLICE_MIN_OPS, stays a pass of its
+                                  own). 0: two passes */,
+  SPS_OPT_FUSED_LABELS = 17    /* labels each thread of a direct fused pass walks
+                                  together (sharing each op's decode): 1, 2, 4
+                                  or 8; 0 (default) picks the most that still
+                                  leave about four warps per SM */,
+  SPS_OPT_AMP_ONLY = 18        /* 1 (default): a gather-form branching pass (one
+                                  gate, or a layer pass) first tries the
+                                  amplitude-only form: if every active label
+                                  finds all members of its group and no value
+                                  falls below eps or to zero, the labels stay
+                                  in place and only amplitudes are written,
+                                  with lookups in an index of all labels that
+                                  stays valid while labels do not move (a pass
+                                  that moves labels, or another use of the
+                                  index table, makes the next attempt rebuild
+                                  it). The result is the same bit for bit.
+                                  Where the form does not apply the usual
+                                  kernels run, and the next 1, 2, 4 .. 64
+                                  passes skip the attempt. 0: never */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:
@@ -289,8 +316,11 @@ sps_status sps_get_counters(sps_state* s, sps_counters* out);
  * permutation pass, 2 scatter emit, 3 scatter compaction, 4 small-state run
  * (several passes in one block), 5 gather index build, 6 gather emit,
  * 7 expansion pass (SPS_OPT_EXPAND; nops = gates), 8 measurement (sums and
- * collapse, timed together). n_in: entries
- * the kernel read; n_out: entries in the state after it. flags: bit 0 the
+ * collapse, timed together), 9 label index of amplitude-only passes
+ * (SPS_OPT_AMP_ONLY; n_in 0 when the index was still valid or the attempt is
+ * skipped), 10 amplitude-only attempt (n_out 0 when it did not take the pass;
+ * then kinds 5 and 6 follow with n_in > 0; they show n_in 0 when skipped).
+ * n_in: entries the kernel read; n_out: entries in the state after it. flags: bit 0 the
  * pass permutes labels, bit 1 it changes amplitudes. label_bytes: 8 or 16. */
 typedef struct sps_kernel_record {
   uint32_t kind;

@@ -50,6 +50,9 @@ struct ApplyPlan {
                                     // op stream; expansion: its factor tables
   std::vector<size_t> ph_off;       // direct fused pass: its fire-slot tables; expansion:
                                     // its mask tables
+  std::vector<uint8_t> walk_next;   // expansion: the fused pass after it runs in its kernel
+  std::vector<size_t> amp_end;      // > 0: a run of branching passes on disjoint qubits starts
+                                    // here (ends there) with one amplitude-only attempt
   std::vector<unsigned char> image;
 };
 
@@ -84,6 +87,10 @@ struct sps_state {
   bool fold = true;           // SPS_OPT_FOLD
   bool commute = false;       // SPS_OPT_COMMUTE
   uint32_t layer_max = kMaxLayerGates;   // SPS_OPT_LAYER_GATES
+  bool expand_walk = true;               // SPS_OPT_EXPAND_WALK
+  int fused_labels = 0;                  // SPS_OPT_FUSED_LABELS (0: by size)
+  bool amp = true;                       // SPS_OPT_AMP_ONLY
+  bool amp_force = true;                 // the label index must be rebuilt before use
   int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
@@ -251,7 +258,10 @@ void know_all_zero(sps_state* s) {
 }
 
 // After a failure nothing is assumed.
-void know_nothing(sps_state* s) { s->kb = KnownBits(); }
+void know_nothing(sps_state* s) {
+  s->kb = KnownBits();
+  s->amp_force = true;
+}
 
 // Knowledge from the label masks the device holds for the current state
 // (stream synchronised): a qubit is known where OR and AND agree.
@@ -499,6 +509,7 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
 
 sps_status sps_reset(sps_state* s) {
   if (!s) return SPS_ERR_ARG;
+  s->amp_force = true;
   if (launch_reset_state(s->stream, s->kw, s->ctl, s->bufs, s->masks.writer()) < 0)
     return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 1;
@@ -563,11 +574,61 @@ static uint64_t bound_after(const Pass& p, uint64_t b, uint64_t capacity) {
   return b < capacity ? b : capacity;
 }
 
+// A fresh 16-bit epoch for the index table; when it wraps, every slot is made
+// free again (which also drops the label index of amplitude-only passes).
+static sps_status next_epoch(sps_state* s, const LaunchCfg& lc) {
+  if (++s->epoch == 0x10000u) {
+    if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0) return cuda_ok(cudaGetLastError());
+    s->counters.kernel_launches += 1;
+    s->epoch = 1;
+    s->amp_force = true;
+  }
+  return SPS_OK;
+}
+
+// The amplitude-only attempt of a run of gather-form branching passes, d gates
+// in all (index check or rebuild, then the attempt); the run's own kernels,
+// launched after it with fallback = 1, run only if it did not take the run.
+static sps_status launch_amp_attempt(sps_state* s, const LaunchCfg& lc, const BranchOp* ops,
+                                     uint32_t d, double prune_eps, uint32_t serial, uint64_t tag) {
+  const sps_status es = next_epoch(s, lc);
+  if (es != SPS_OK) return es;
+  AmpLaunch l;
+  std::memset(&l, 0, sizeof(l));
+  l.d = d;
+  for (uint32_t j = 0; j < d; ++j) l.ops[j] = ops[j];
+  l.eps = prune_eps;
+  l.load_pct = s->load_pct;
+  l.max_log2 = s->itab_log2;
+  l.pass_serial = serial;
+  l.fail_tag = tag;
+  const uint32_t force = s->amp_force ? 1u : 0u;
+  {
+    ProfScope pi(s, 9, serial, d, 0u);
+    const int n = launch_amp_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, force, l,
+                                  s->nnz_bound, 0, pi.slot);
+    pi.done();
+    if (n < 0) return cuda_ok(cudaGetLastError());
+  }
+  {
+    ProfScope pa(s, 10, serial, d, 2u);
+    const int n = launch_amp_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, force, l,
+                                  s->nnz_bound, 1, pa.slot);
+    pa.done();
+    if (n < 0) return cuda_ok(cudaGetLastError());
+  }
+  s->amp_force = false;
+  s->counters.kernel_launches += 2;
+  return SPS_OK;
+}
+
 // One branching pass on the whole GPU (gather form, or scatter form when chosen
 // or when the capacity needs 64-bit table indices); advances the nonzero bound.
+// fallback: the gather kernels run only if an amplitude-only attempt launched
+// just before did not take the pass.
 static sps_status launch_branch_pass(sps_state* s, const LaunchCfg& lc, const BranchOp& op,
                                      double prune_eps, uint32_t serial, uint64_t tag,
-                                     uint32_t limit) {
+                                     uint32_t limit, uint32_t fallback = 0) {
   BranchLaunch b;
   b.op = op;
   b.eps = prune_eps;
@@ -579,6 +640,7 @@ static sps_status launch_branch_pass(sps_state* s, const LaunchCfg& lc, const Br
   b.capacity = s->capacity;
   b.fail_tag = tag;
   b.mg = s->masks.writer();   // the pass writes labels: compaction or gather emit
+  b.fallback = fallback;
   const bool scatter = s->branch_form == 1 || s->capacity >= (1ull << 32);
   if (scatter) {
     const sps_status ts = ensure_scatter_table(s);
@@ -596,11 +658,8 @@ static sps_status launch_branch_pass(sps_state* s, const LaunchCfg& lc, const Br
       if (n < 0) return cuda_ok(cudaGetLastError());
     }
   } else {
-    if (++s->epoch == 0x10000u) {  // the 16-bit epoch wrapped: make every slot free again
-      if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0) return cuda_ok(cudaGetLastError());
-      s->counters.kernel_launches += 1;
-      s->epoch = 1;
-    }
+    const sps_status es = next_epoch(s, lc);
+    if (es != SPS_OK) return es;
     b.max_log2 = s->itab_log2;
     ProfScope pb(s, 5, serial, 1, 3u);
     int n = launch_gather_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, b, s->nnz_bound, 0, pb.slot);
@@ -627,7 +686,8 @@ static uint32_t probe_limit_of(const sps_state* s) {
 static std::vector<uint64_t> plan_options(const sps_state* s) {
   return {s->nqubits, (uint64_t)s->kw, s->capacity, s->max_fused_ops, s->expand ? 1ull : 0ull,
           s->fold ? 1ull : 0ull, s->small_cap, s->bitslice_min_ops, s->bitslice_min_nnz,
-          s->commute ? 1ull : 0ull, s->layer_max};
+          s->commute ? 1ull : 0ull, s->layer_max, s->expand_walk ? 1ull : 0ull,
+          s->amp ? 1ull : 0ull};
 }
 
 static bool plan_matches(const ApplyPlan& p, const sps_state* s, const sps_gate* gates,
@@ -717,7 +777,61 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
       ++i;
     }
   }
-  // 2. device data: bit-sliced plans of long fused runs outside small runs,
+  // 2a. runs of branching passes on pairwise disjoint qubits (targets and
+  //     controls), up to kMaxAmpGates gates, outside small runs: one
+  //     amplitude-only attempt each
+  P->amp_end.assign(np, 0);
+  if (s->amp) {
+    auto branching = [&](const Pass& q) {
+      return (q.kind == PASS_BRANCH && !q.br.pauli) || q.kind == PASS_LAYER;
+    };
+    for (size_t i = 0; i < np;) {
+      if (P->seg_end[i]) {
+        i = P->seg_end[i];
+        continue;
+      }
+      if (!branching(passes[i])) {
+        ++i;
+        continue;
+      }
+      uint64_t sup0 = 0, sup1 = 0;
+      uint32_t gates = 0;
+      size_t j = i;
+      while (j < np && !P->seg_end[j] && branching(passes[j])) {
+        const Pass& q = passes[j];
+        uint64_t q0 = 0, q1 = 0;
+        uint32_t g = 0;
+        auto add = [&](const BranchOp& op) {
+          q0 |= op.c[0] | op.m[0];
+          q1 |= op.c[1] | op.m[1];
+          ++g;
+        };
+        if (q.kind == PASS_BRANCH) add(q.br);
+        else for (const BranchOp& op : q.lay) add(op);
+        if (gates + g > kMaxAmpGates || (q0 & sup0) || (q1 & sup1)) break;
+        sup0 |= q0;
+        sup1 |= q1;
+        gates += g;
+        ++j;
+      }
+      P->amp_end[i] = j;
+      i = j;
+    }
+  }
+  // 2b. an expansion takes the fused run right after it (outside small runs),
+  //    unless that run is long enough and the state large enough for the
+  //    bit-sliced form (faster there than the per-label walk)
+  P->walk_next.assign(np, 0);
+  if (s->expand_walk)
+    for (size_t i = 0; i + 1 < np; ++i) {
+      const Pass& f = passes[i + 1];
+      const bool sliced = s->bitslice_min_ops && f.ops.size() >= s->bitslice_min_ops &&
+                          P->bound_at[i + 1] >= s->bitslice_min_nnz;
+      if (passes[i].kind == PASS_EXPAND && !P->seg_end[i] && f.kind == PASS_FUSED &&
+          !P->seg_end[i + 1] && !sliced)
+        P->walk_next[i] = 1;
+    }
+  // 3. device data: bit-sliced plans of long fused runs outside small runs,
   //    then the op streams, tables and small-run records
   P->bs.assign(np, BsPass());
   P->bs_off.assign(np, 0);
@@ -730,7 +844,8 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
       continue;
     }
     const Pass& p = passes[i];
-    if (p.kind == PASS_FUSED && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops &&
+    const bool walked = i > 0 && P->walk_next[i - 1];
+    if (p.kind == PASS_FUSED && !walked && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops &&
         P->bound_at[i] >= s->bitslice_min_nnz) {
       build_bitslice(p, s->nqubits, &P->bs[i]);
       P->bs_off[i] = bs_bytes;
@@ -848,6 +963,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   const uint32_t limit = s->probe_limit ? s->probe_limit : (uint32_t)(s->table_slots > 0xFFFFFFFFull ? 0xFFFFFFFFu : s->table_slots);
   const uint32_t serial_base = s->pass_serial;
   ++s->apply_serial;
+  size_t amp_run_end = 0;   // passes before this index belong to an attempted run
   for (size_t pi = 0; pi < passes.size(); ++pi) {
     const Pass& p = passes[pi];
     if (seg_end[pi]) {
@@ -860,6 +976,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
                                      s->masks.writer(), serial_base, s->apply_serial, ps.slot);
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
+      s->amp_force = true;   // the run moves labels
       s->pass_serial += (uint32_t)(j - pi);
       s->counters.branch_passes += nbranch;
       s->counters.fused_passes += (j - pi) - nbranch;
@@ -871,6 +988,21 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       pi = j - 1;
       continue;
     }
+    const bool scatter = s->branch_form == 1 || s->capacity >= (1ull << 32);
+    if (P.amp_end[pi] && !scatter) {   // a run's attempt, then its passes as fallbacks
+      BranchOp ops[kMaxAmpGates];
+      uint32_t d = 0;
+      for (size_t k = pi; k < P.amp_end[pi]; ++k) {
+        if (passes[k].kind == PASS_BRANCH) ops[d++] = passes[k].br;
+        else for (const BranchOp& op : passes[k].lay) ops[d++] = op;
+      }
+      const uint64_t tg = ((uint64_t)s->apply_serial << 32) | (p.first_gate & 0xFFFFFFFFull);
+      const sps_status as = launch_amp_attempt(s, lc, ops, d, prune_eps, s->pass_serial + 1, tg);
+      if (as != SPS_OK) return as;
+      amp_run_end = P.amp_end[pi];
+    }
+    const uint32_t fb = pi < amp_run_end ? 1u : 0u;   // a fallback pass of an attempted run
+    if (!fb && (p.kind == PASS_BRANCH || p.kind == PASS_LAYER)) s->amp_force = true;
     const uint32_t serial = ++s->pass_serial;
     const uint64_t tag = ((uint64_t)s->apply_serial << 32) | (p.first_gate & 0xFFFFFFFFull);
     if (p.kind == PASS_EXPAND) {
@@ -884,17 +1016,36 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       e.eps = prune_eps;
       e.capacity = s->capacity;
       e.fail_tag = tag;
+      e.words = nullptr;
+      e.ftab = nullptr;
+      e.nwords = 0;
+      e.fused_gates = 0;
+      e.has_phase = 0;
+      const bool walk = P.walk_next[pi] != 0;
+      if (walk) {   // the fused run after the expansion, applied before the stores
+        const Pass& f = passes[pi + 1];
+        e.words = reinterpret_cast<const OpWord*>(s->arena + run_off[pi + 1]);
+        e.ftab = reinterpret_cast<const double*>(s->arena + ph_off[pi + 1]);
+        e.nwords = (uint32_t)f.words.size();
+        e.fused_gates = f.ngates;
+        e.has_phase = f.has_phase ? 1u : 0u;
+      }
       ProfScope ps(s, 7, serial, p.ex_d, 3u);
       const int n = launch_expand(lc, s->kw, s->ctl, s->bufs, e, s->nnz_bound, ps.slot);
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
+      s->amp_force = true;
       s->counters.branch_passes++;
       s->counters.kernel_launches += 1;
       s->nnz_bound = bound_after(p, s->nnz_bound, s->capacity);
+      if (walk) {   // the fused pass is done: keep the pass serials in step
+        ++s->pass_serial;
+        s->counters.fused_passes++;
+        ++pi;
+      }
       continue;
     }
     if (p.kind == PASS_LAYER) {
-      const bool scatter = s->branch_form == 1 || s->capacity >= (1ull << 32);
       if (scatter) {   // the layer kernels are gather-form: one pass per gate
         for (size_t j = 0; j < p.lay.size(); ++j) {
           const uint64_t tg = ((uint64_t)s->apply_serial << 32) | (p.lay_gate[j] & 0xFFFFFFFFull);
@@ -904,13 +1055,11 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         }
         continue;
       }
-      if (++s->epoch == 0x10000u) {  // the 16-bit epoch wrapped: make every slot free again
-        if (launch_itab_clear(lc, s->itab, 1ull << s->itab_log2) < 0) return cuda_ok(cudaGetLastError());
-        s->counters.kernel_launches += 1;
-        s->epoch = 1;
-      }
+      const sps_status es = next_epoch(s, lc);
+      if (es != SPS_OK) return es;
       LayerLaunch l;
       std::memset(&l, 0, sizeof(l));
+      l.fallback = fb;
       l.d = (uint32_t)p.lay.size();
       for (uint32_t j = 0; j < l.d; ++j) l.ops[j] = p.lay[j];
       l.eps = prune_eps;
@@ -962,14 +1111,15 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         n = launch_fused(lc, s->kw, s->ctl, s->bufs, p,
                          reinterpret_cast<const OpWord*>(s->arena + run_off[pi]),
                          reinterpret_cast<const double*>(s->arena + ph_off[pi]), s->nnz_bound,
-                         p.has_perm ? s->masks.writer() : 0u, ps.slot);
+                         p.has_perm ? s->masks.writer() : 0u, s->fused_labels, ps.slot);
       }
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
+      if (p.has_perm) s->amp_force = true;   // labels changed in place
       s->counters.fused_passes++;
       s->counters.kernel_launches += (uint64_t)n;
     } else {
-      const sps_status bs2 = launch_branch_pass(s, lc, p.br, prune_eps, serial, tag, limit);
+      const sps_status bs2 = launch_branch_pass(s, lc, p.br, prune_eps, serial, tag, limit, fb);
       if (bs2 != SPS_OK) return bs2;
     }
   }
@@ -1044,6 +1194,7 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
                               const double* re, const double* im, uint64_t n) {
   if (!s || (n && (!key_lo || !re || !im))) return SPS_ERR_ARG;
   if (n > s->capacity) return SPS_ERR_CAPACITY;
+  s->amp_force = true;
   sps_status st = sps_sync(s, nullptr);
   if (st != SPS_OK) return st;
   const SoA b = s->bufs.b[0];
@@ -1200,6 +1351,7 @@ sps_status sps_pauli_exp(sps_state* s, const uint64_t x[2], const uint64_t z[2],
   ++s->apply_serial;
   const uint32_t serial = ++s->pass_serial;
   const uint64_t tag = (uint64_t)s->apply_serial << 32;
+  s->amp_force = true;   // an out-of-place pass: labels move, index slots are taken
   const sps_status bs = launch_branch_pass(s, lc, op, prune_eps, serial, tag, probe_limit_of(s));
   if (bs != SPS_OK) return bs;
   s->counters.gates += 1;
@@ -1210,6 +1362,7 @@ sps_status sps_measure(sps_state* s, uint32_t qubit, double r, double* out) {
   if (!s || !out || qubit >= s->nqubits || !(r >= 0.0 && r < 1.0)) return SPS_ERR_ARG;
   const LaunchCfg lc = cfg_of(s);
   const uint32_t serial = ++s->pass_serial;
+  s->amp_force = true;   // the collapse moves labels
   ProfScope ps(s, 8, serial, 1, 1u);
   const int n = launch_measure(lc, s->kw, s->ctl, s->bufs, qubit, r, s->partials, s->prob_blocks,
                                s->dmeasure, s->nnz_bound, s->masks.writer(), ps.slot);
@@ -1261,6 +1414,18 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_LAYER_GATES:
       if (v < 1 || v > (int64_t)kMaxLayerGates) return SPS_ERR_ARG;
       s->layer_max = (uint32_t)v;
+      return SPS_OK;
+    case SPS_OPT_EXPAND_WALK:
+      if (v != 0 && v != 1) return SPS_ERR_ARG;
+      s->expand_walk = v == 1;
+      return SPS_OK;
+    case SPS_OPT_AMP_ONLY:
+      if (v != 0 && v != 1) return SPS_ERR_ARG;
+      s->amp = v == 1;
+      return SPS_OK;
+    case SPS_OPT_FUSED_LABELS:
+      if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return SPS_ERR_ARG;
+      s->fused_labels = (int)v;
       return SPS_OK;
     case SPS_OPT_BRANCH_FORM:
       if (v < 0 || v > 2) return SPS_ERR_ARG;

@@ -247,6 +247,16 @@ __device__ __forceinline__ void walk_ops(const uint4* __restrict__ sq, uint32_t 
   fire = f[0];
 }
 
+// (re, im) * (tr, ti) with every product and sum rounded once (no contraction
+// into fused multiply-adds), so every kernel that applies a phase gets the
+// same bits whatever the compiler schedules around it.
+__device__ __forceinline__ void cmul_rn(double& re, double& im, double tr, double ti) {
+  const double nr = __dsub_rn(__dmul_rn(re, tr), __dmul_rn(im, ti));
+  const double ni = __dadd_rn(__dmul_rn(re, ti), __dmul_rn(im, tr));
+  re = nr;
+  im = ni;
+}
+
 // Multiplies an amplitude by the phases of the set fire-slot bits, one table
 // entry (the product of up to 8 slots' phases) per non-zero byte.
 __device__ __forceinline__ void apply_fire(uint64_t fire, const double2* __restrict__ tab,
@@ -255,10 +265,7 @@ __device__ __forceinline__ void apply_fire(uint64_t fire, const double2* __restr
     const uint32_t v = (uint32_t)(fire & 0xFFull);
     if (v == 0u) continue;
     const double2 t = tab[c * 256u + v];
-    const double nr = re * t.x - im * t.y;
-    const double ni = re * t.y + im * t.x;
-    re = nr;
-    im = ni;
+    cmul_rn(re, im, t.x, t.y);
   }
 }
 
@@ -267,8 +274,8 @@ __device__ __forceinline__ void apply_fire(uint64_t fire, const double2* __restr
 __device__ __forceinline__ void apply_pi4(uint32_t cnt, double& re, double& im) {
   if (cnt & 1u) {  // times e^{i pi/4} = sqrt(0.5) (1 + i)
     const double r = 0.70710678118654752440;  // sqrt(0.5)
-    const double nr = r * (re - im);
-    const double ni = r * (re + im);
+    const double nr = __dmul_rn(r, __dsub_rn(re, im));
+    const double ni = __dmul_rn(r, __dadd_rn(re, im));
     re = nr;
     im = ni;
   }

@@ -40,7 +40,24 @@ struct GatherArgs {
   uint64_t fail_tag;
   uint32_t load_pct, max_log2, pass_serial, epoch;
   uint32_t mg;   // label-mask buffers (MaskRing): build reads rd; emit reads rd, writes wr
+  uint32_t fallback;   // 1: skip if the amplitude-only form took the pass
 };
+
+// A fallback launch whose pass the amplitude-only form already produced.
+__device__ __forceinline__ bool amp_took(const Ctl* ctl, uint32_t fallback) {
+  return fallback != 0u && *reinterpret_cast<const volatile unsigned*>(&ctl->amp_state) == 1u;
+}
+
+// A skipped emit still advances the label masks: the labels are those of its
+// input, so buffer wr gets buffer rd's masks and rs is emptied (block 0).
+__device__ __forceinline__ void carry_label_masks(Ctl* ctl, uint32_t mg) {
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const LabelMasks m = read_label_masks(ctl, mg_rd(mg));
+  if (threadIdx.x == 0) {
+    set_label_masks(ctl, mg_wr(mg), m.or0, m.or1, m.and0, m.and1);
+    reset_label_masks(ctl, mg_rs(mg));
+  }
+}
 
 // The table holds n_in labels at the load factor: size for n_in, not 2 n_in.
 __device__ __forceinline__ uint64_t itab_mask(uint64_t n, uint32_t load_pct, uint32_t max_log2) {
@@ -53,11 +70,12 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
                                                       unsigned long long* plog) {
   const uint64_t n = ctl->nnz;
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
-    plog[0] = n;
+    plog[0] = amp_took(ctl, a.fallback) ? 0ull : n;
     plog[1] = 0ull;
   }
   // (another block may set the status meanwhile: decide for the whole block)
-  if (__syncthreads_or(ctl->status != 0u)) return;
+  if (__syncthreads_or(ctl->status != 0u) || amp_took(ctl, a.fallback)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->index_ok = 0u;   // slots are taken over
   // Flip bits constant over the state: no entry has a partner, nothing to index.
   if (flip_bits_constant(read_label_masks_block(ctl, mg_rd(a.mg)), a.op.m)) return;
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
@@ -120,6 +138,14 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
   __shared__ unsigned long long block_base;
   if (__syncthreads_or(ctl->status != 0u)) return;
   const uint64_t n = ctl->nnz;
+  if (amp_took(ctl, a.fallback)) {
+    carry_label_masks(ctl, a.mg);
+    if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+      plog[0] = 0ull;
+      plog[1] = n;
+    }
+    return;
+  }
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
   const unsigned cur = ctl->cur;
   const SoA s = pick(bufs, cur);
@@ -229,6 +255,7 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
           ctl->nnz = total;
           ctl->cur = cur ^ 1u;
           ctl->updates += n;
+          ctl->index_ok = 0u;   // the labels moved
           published = true;
         }
       }
@@ -250,37 +277,44 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
 // F1[c1] * F2[c2] from per-8-gate tables staged in shared memory; pruned on
 // the final amplitude (every matrix entry has modulus <= 1, so no path falls
 // below eps before its end and rises above it after).
-// A warp owns spans of 256 consecutive outputs, 8 per lane. With d >= 8 a span
+// A warp owns spans of 32 E consecutive outputs, E per lane. With d >= 8 a span
 // shares its input and its choices above the first 8 gates, so the warp forms
 // that head once and each output costs one table product. Survivors of a span
 // take one atomic for their place; the last block publishes the count.
+// With WALK the phase/permutation run that follows the expansion runs on the
+// outputs before they are stored (the E labels of a lane walk the op stream
+// together, sharing each op's decode): the state is written once, with the
+// same values as the two passes one after the other.
 struct ExpandArgs {
   const double2* f;        // chunks x 256 path factors
   const ulonglong2* m;     // chunks x 256 flip masks
   uint32_t d, chunks, real, pass_serial, mg;
   double eps2, eps;
   uint64_t capacity, fail_tag;
+  // the fused run that follows (WALK): op stream, fire-slot tables, gate count
+  const uint4* words;
+  const double2* ftab;
+  uint32_t nwords, fused_gates, has_phase;
 };
 
 // (re, im) *= f; a real factor leaves an exactly zero imaginary part at zero
 // (skipping the product, which would only give it a sign).
+// Every product and sum is rounded once (see cmul_rn).
 __device__ __forceinline__ void times(bool real, double2 f, double& re, double& im) {
   if (real) {
-    re = re * f.x;
-    if (im != 0.0) im = im * f.x;
+    re = __dmul_rn(re, f.x);
+    if (im != 0.0) im = __dmul_rn(im, f.x);
   } else {
-    const double nr = re * f.x - im * f.y;
-    const double ni = re * f.y + im * f.x;
-    re = nr;
-    im = ni;
+    cmul_rn(re, im, f.x, f.y);
   }
 }
 
-template <int KW>
-__global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const ExpandArgs a,
+template <int KW, int E, bool WALK>
+__global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const __grid_constant__ ExpandArgs a,
                                                 unsigned long long* plog) {
   __shared__ double2 sf[3 * 256];
   __shared__ ulonglong2 sm[3 * 256];
+  extern __shared__ uint4 fsm[];   // WALK: the op stream
   if (ctl->status != 0u) return;
   const uint64_t n = ctl->nnz;
   const unsigned cur = ctl->cur;
@@ -291,18 +325,21 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const Expan
     sf[w] = a.f[w];
     sm[w] = a.m[w];
   }
+  if (WALK)
+    for (uint32_t w = threadIdx.x; w < a.nwords; w += blockDim.x) fsm[w] = a.words[w];
   __syncthreads();
+  constexpr uint32_t kSpan = 32u * E;
   const uint64_t total = n << a.d;
   const uint64_t cmask = (1ull << a.d) - 1ull;
   const uint64_t eps_bits = eps_pattern(a.eps);
   const unsigned lane = threadIdx.x & 31u;
   const bool wide = a.d >= 8;
-  const uint64_t spans = (total + 255) / 256;
+  const uint64_t spans = (total + kSpan - 1) / kSpan;
   const uint64_t nwarp = (uint64_t)gridDim.x * (blockDim.x >> 5);
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;
   for (uint64_t sp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sp < spans;
        sp += nwarp) {
-    const uint64_t t0 = sp * 256;
+    const uint64_t t0 = sp * kSpan;
     uint64_t h0 = 0, h1 = 0;
     double hr = 0.0, hi = 0.0;
     if (wide) {   // the span's input and its choices above the first 8 gates
@@ -319,20 +356,20 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const Expan
         times(a.real != 0u, sf[u], hr, hi);
       }
     }
-    uint64_t L0[8], L1[8];
-    double VR[8], VI[8];
-    unsigned bal[8];
+    uint64_t L0[E], L1[E];
+    double VR[E], VI[E];
+    unsigned bal[E];
     unsigned count = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < E; ++k) {
       const uint64_t t = t0 + 32u * k + lane;
       bool keep = false;
       uint64_t l0 = 0, l1 = 0;
       double vr = 0.0, vi = 0.0;
       if (t < total) {
         uint32_t c0;
-        if (wide) {
-          c0 = 32u * k + lane;
+        if (wide) {   // a span lies inside one block of 256 choices
+          c0 = (uint32_t)(t & 0xFFu);
           l0 = h0;
           l1 = h1;
           vr = hr;
@@ -357,12 +394,32 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const Expan
       bal[k] = __ballot_sync(FULL, keep);
       count += __popc(bal[k]);
     }
+    if (WALK) {   // the fused run, on every lane's E labels at once
+      uint32_t cnt[E];
+      uint64_t fire[E];
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        cnt[k] = 0u;
+        fire[k] = 0ull;
+      }
+      walk_ops_n<KW, E>(fsm, a.nwords, L0, L1, cnt, fire);
+      if (a.has_phase) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const uint32_t c8 = cnt[k] & 7u;
+          if (((bal[k] >> lane) & 1u) && (c8 != 0u || fire[k] != 0ull)) {
+            apply_fire(fire[k], a.ftab, VR[k], VI[k]);
+            apply_pi4(c8, VR[k], VI[k]);
+          }
+        }
+      }
+    }
     unsigned long long base = 0ull;
     if (lane == 0 && count) base = atomicAdd(&ctl->out_count, (unsigned long long)count);
     base = __shfl_sync(FULL, base, 0);
     const unsigned below = (1u << lane) - 1u;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < E; ++k) {
       if ((bal[k] >> lane) & 1u) {
         const uint64_t pos = base + __popc(bal[k] & below);
         if (pos < a.capacity) {
@@ -394,8 +451,9 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const Expan
         } else {
           ctl->nnz = got;
           ctl->cur = cur ^ 1u;
-          // the nonzeros before each of the d gates: n, 2n, ..., 2^(d-1) n
-          ctl->updates += n * cmask;
+          // the nonzeros before each of the d gates: n, 2n, ..., 2^(d-1) n;
+          // then every gate of the fused run on the expanded state
+          ctl->updates += n * cmask + got * a.fused_gates;
           published = true;
         }
       }
@@ -435,6 +493,8 @@ struct LayerArgs {
   double eps2, eps;
   uint64_t capacity, fail_tag;
   uint32_t load_pct, max_log2, pass_serial, epoch, mg;
+  uint32_t fallback;   // 1: skip if the amplitude-only form took the pass
+  uint32_t force;      // amplitude-only index: rebuild whatever the device says
 };
 
 template <int KW>
@@ -467,10 +527,11 @@ __global__ void __launch_bounds__(256) k_layer_build(Ctl* ctl, Bufs bufs, unsign
                                                      unsigned long long* plog) {
   const uint64_t n = ctl->nnz;
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
-    plog[0] = n;
+    plog[0] = amp_took(ctl, a.fallback) ? 0ull : n;
     plog[1] = 0ull;
   }
-  if (__syncthreads_or(ctl->status != 0u)) return;
+  if (__syncthreads_or(ctl->status != 0u) || amp_took(ctl, a.fallback)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->index_ok = 0u;   // slots are taken over
   const uint32_t pairable = layer_pairable(a, read_label_masks_block(ctl, mg_rd(a.mg)));
   if (pairable == 0u) return;
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
@@ -509,6 +570,14 @@ __global__ void __launch_bounds__(256) k_layer_emit(Ctl* ctl, Bufs bufs,
   __shared__ unsigned long long block_base;
   if (__syncthreads_or(ctl->status != 0u)) return;
   const uint64_t n = ctl->nnz;
+  if (amp_took(ctl, a.fallback)) {
+    carry_label_masks(ctl, a.mg);
+    if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+      plog[0] = 0ull;
+      plog[1] = n;
+    }
+    return;
+  }
   const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
   const unsigned cur = ctl->cur;
   const SoA s = pick(bufs, cur);
@@ -680,12 +749,314 @@ __global__ void __launch_bounds__(256) k_layer_emit(Ctl* ctl, Bufs bufs,
         } else {
           ctl->nnz = total;
           ctl->cur = cur ^ 1u;
+          ctl->index_ok = 0u;   // the labels moved
           published = true;
         }
       }
       if (plog) {
         plog[0] = n;
         plog[1] = published ? total : n;
+      }
+      ctl->out_count = 0ull;
+      ctl->blocks_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Amplitude-only form of a run of branching passes (up to 32 gates on pairwise
+// disjoint qubits). Where every active label finds each member of its group
+// and no value on the way falls below eps or to zero, the run maps the set of
+// labels onto itself: the state after it has the same labels, in the same
+// places, with new amplitudes, and each entry is written to the same index of
+// the other buffer (no compaction). A label's group is spanned by the flips of
+// the gates it activates; its member with every selector bit 0 (the writer)
+// takes the group: one lane looks up the partner of a pair; a group of 4, 8 or
+// 16 members takes 16 lanes, one per member, that look up their members in
+// parallel and run the gates in order as butterflies over shuffles (each lane
+// its own row of each pair action, pruned after every gate as a pass would).
+// The lookups use an index of every label that stays valid while passes keep
+// labels in place. Every entry written once means every group had its writer;
+// anything else (a member absent, a value pruned, a group of more than 16)
+// leaves the run to the usual kernels launched after it (fallback = 1), and a
+// failed attempt makes the following runs skip the attempt for a while (1, 2,
+// 4 ... up to 64 runs), so states that keep changing do not pay for it.
+struct AmpArgs {
+  BranchOp ops[kMaxAmpGates];
+  uint32_t d;
+  double eps2, eps;
+  uint32_t load_pct, max_log2, pass_serial, epoch, force;
+  uint64_t fail_tag;
+};
+
+template <int KW>
+__device__ __forceinline__ uint32_t amp_active(const AmpArgs& a, uint64_t k0, uint64_t k1) {
+  uint32_t act = 0;
+  for (uint32_t j = 0; j < a.d; ++j) {
+    const BranchOp& op = a.ops[j];
+    bool on = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
+    if (op.givens) on = on && (label_bit(k0, k1, op.sbit) != label_bit(k0, k1, op.qbit));
+    act |= on ? (1u << j) : 0u;
+  }
+  return act;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_amp_index(Ctl* ctl, Bufs bufs, unsigned long long* itab,
+                                                   const __grid_constant__ AmpArgs a,
+                                                   unsigned long long* plog) {
+  const bool err = ctl->status != 0u;
+  const uint32_t backoff = ctl->amp_backoff;
+  const bool attempt = !err && backoff == 0u;
+  const bool rebuild = attempt && (a.force != 0u || ctl->index_ok == 0u);
+  const uint64_t n = ctl->nnz;
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+    plog[0] = rebuild ? n : 0ull;
+    plog[1] = n;
+  }
+  if (rebuild) {
+    const uint64_t mask = itab_mask(n, a.load_pct, a.max_log2);
+    const SoA s = pick(bufs, ctl->cur);
+    const unsigned long long ep = (unsigned long long)a.epoch << 48;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+      const uint64_t k0 = s.lo[i];
+      const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+      const uint64_t hv = hash_label<KW>(k0, k1);
+      const unsigned long long mine = ep | ((hv >> 48) << 32) | i;
+      uint64_t h = hv & mask;
+      bool ok = false;
+      for (uint64_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
+        const unsigned long long v = __ldcg(itab + h);
+        if ((v & 0xFFFF000000000000ull) == ep) continue;
+        if (atomicCAS(itab + h, v, mine) == v) {
+          ok = true;
+          break;
+        }
+      }
+      if (!ok) {
+        fail(ctl, SPS_ERR_TABLE_FULL, a.pass_serial, a.fail_tag);
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const bool ok = ctl->status == 0u;
+      if (rebuild) {
+        ctl->index_ok = ok ? 1u : 0u;
+        ctl->index_epoch = a.epoch;
+        ctl->index_n = n;
+      }
+      ctl->amp_go = attempt && ok ? 1u : 0u;
+      ctl->amp_state = 0u;
+      ctl->amp_fail = 0u;
+      ctl->out_count = 0ull;
+      if (backoff) ctl->amp_backoff = backoff - 1u;
+      ctl->blocks_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// Output row r of a pair action with both members present, rounded as
+// pair_action rounds it (each product and the sum once).
+__device__ __forceinline__ void row_action(const BranchOp& op, int r, double a0r, double a0i,
+                                           double a1r, double a1i, double* nr, double* ni) {
+  double t0r, t0i, t1r, t1i;
+  mat_times(op, r, 0, a0r, a0i, &t0r, &t0i);
+  mat_times(op, r, 1, a1r, a1i, &t1r, &t1i);
+  *nr = __dadd_rn(t0r, t1r);
+  *ni = __dadd_rn(t0i, t1i);
+}
+
+// The b-th set bit of act (b < popc(act)).
+__device__ __forceinline__ uint32_t nth_bit(uint32_t act, uint32_t b) {
+  for (uint32_t k = 0; k < b; ++k) act &= act - 1u;
+  return __ffs(act) - 1u;
+}
+
+constexpr uint32_t kAmpQueue = 256;   // >= threads per block
+constexpr uint32_t kAmpWide = 4;      // most active gates of a group (16 members)
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
+                                                   const unsigned long long* itab,
+                                                   const __grid_constant__ AmpArgs a,
+                                                   unsigned long long* plog) {
+  __shared__ uint32_t q1[kAmpQueue], q2[kAmpQueue];
+  __shared__ unsigned n1, n2;
+  const bool go = ctl->amp_go != 0u;
+  const uint64_t n = ctl->nnz;
+  const unsigned cur = ctl->cur;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  bool bad = false;
+  unsigned long long written = 0;   // entries this thread wrote
+  if (go) {
+    const uint64_t mask = itab_mask(ctl->index_n, a.load_pct, a.max_log2);
+    const unsigned long long ep = (unsigned long long)ctl->index_epoch << 48;
+    const SoA s = pick(bufs, cur);
+    const SoA out = pick(bufs, cur ^ 1u);
+    const uint64_t eps_bits = eps_pattern(a.eps);
+    // (no thread polls the others' failures: every iteration would load one
+    // shared address from L2, which costs more than finishing the pass)
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n && !bad; base += stride) {
+      if (threadIdx.x == 0) n1 = n2 = 0u;
+      __syncthreads();
+      // 1. scan: untouched entries are copied, writers queued
+      const uint64_t i = base + threadIdx.x;
+      if (i < n) {
+        const uint64_t k0 = s.lo[i];
+        const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+        const uint32_t act = amp_active<KW>(a, k0, k1);
+        if (act == 0u) {   // every gate only prunes this entry
+          const double re = s.re[i], im = s.im[i];
+          bad = !keep_amp(re, im, a.eps2, eps_bits);
+          out.lo[i] = k0;
+          if (KW == 2) out.hi[i] = k1;
+          out.re[i] = re;
+          out.im[i] = im;
+          ++written;
+        } else if (__popc(act) > kAmpWide) {
+          bad = true;
+        } else {
+          bool writer = true;
+          for (uint32_t rem = act; rem; rem &= rem - 1u)
+            writer = writer && !label_bit(k0, k1, a.ops[__ffs(rem) - 1u].sbit);
+          if (writer) {
+            if ((act & (act - 1u)) == 0u) q1[atomicAdd(&n1, 1u)] = (uint32_t)(i - base);
+            else q2[atomicAdd(&n2, 1u)] = (uint32_t)(i - base);
+          }
+        }
+      }
+      __syncthreads();
+      const unsigned c1 = n1, c2 = n2;
+      // 2. pairs: the writer looks up its partner and writes both
+      for (unsigned t = threadIdx.x; t < c1; t += blockDim.x) {
+        const uint64_t j0 = base + q1[t];
+        const uint64_t k0 = s.lo[j0];
+        const uint64_t k1 = KW == 2 ? s.hi[j0] : 0ull;
+        const uint32_t act = amp_active<KW>(a, k0, k1);
+        const BranchOp& op = a.ops[__ffs(act) - 1u];
+        const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
+        const uint64_t j1 = find_label<KW>(itab, mask, ep, s, p0, p1);
+        if (j1 == ~0ull) {
+          bad = true;
+          continue;
+        }
+        const double a0r = s.re[j0], a0i = s.im[j0], a1r = s.re[j1], a1i = s.im[j1];
+        // gates before it are inactive for the pair: they prune its inputs
+        if ((act & 1u) == 0u && (!keep_amp(a0r, a0i, a.eps2, eps_bits) ||
+                                 !keep_amp(a1r, a1i, a.eps2, eps_bits))) {
+          bad = true;
+          continue;
+        }
+        double n0r, n0i, n1r, n1i;
+        pair_action(op, true, false, a0r, a0i, a1r, a1i, &n0r, &n0i, &n1r, &n1i);
+        // (later gates are inactive for the pair: they prune what this kept)
+        if (!keep_amp(n0r, n0i, a.eps2, eps_bits) || !keep_amp(n1r, n1i, a.eps2, eps_bits)) {
+          bad = true;
+          continue;
+        }
+        out.lo[j0] = k0;
+        out.lo[j1] = p0;
+        if (KW == 2) {
+          out.hi[j0] = k1;
+          out.hi[j1] = p1;
+        }
+        out.re[j0] = n0r;
+        out.im[j0] = n0i;
+        out.re[j1] = n1r;
+        out.im[j1] = n1i;
+        written += 2;
+      }
+      // 3. groups of 4..16: 16 lanes each, lane u = member u (every lane of
+      //    the warp runs every shuffle; lanes past the group's size idle)
+      for (unsigned g0 = 2u * warp; g0 < c2; g0 += 2u * nwarps) {
+        const unsigned g = g0 + (lane >> 4);
+        const uint32_t u = lane & 15u;
+        const bool have = g < c2;
+        uint64_t k0 = 0, k1 = 0;
+        uint32_t act = 0, na = 0;
+        if (have) {
+          const uint64_t jw = base + q2[g];
+          k0 = s.lo[jw];
+          k1 = KW == 2 ? s.hi[jw] : 0ull;
+          act = amp_active<KW>(a, k0, k1);
+          na = __popc(act);
+        }
+        const bool mine = have && u < (1u << na);
+        uint64_t l0 = k0, l1 = k1, jx = ~0ull;
+        double re = 0.0, im = 0.0;
+        if (mine) {
+          for (uint32_t b = 0; b < na; ++b)
+            if ((u >> b) & 1u) {
+              const BranchOp& op = a.ops[nth_bit(act, b)];
+              l0 ^= op.m[0];
+              l1 ^= op.m[1];
+            }
+          jx = u == 0u ? base + q2[g] : find_label<KW>(itab, mask, ep, s, l0, l1);
+          if (jx == ~0ull) {
+            bad = true;
+          } else {
+            re = s.re[jx];
+            im = s.im[jx];
+            if ((act & 1u) == 0u && !keep_amp(re, im, a.eps2, eps_bits)) bad = true;
+          }
+        }
+        for (uint32_t b = 0; b < kAmpWide; ++b) {
+          const double pr = __shfl_xor_sync(FULL, re, 1u << b);
+          const double pi = __shfl_xor_sync(FULL, im, 1u << b);
+          if (mine && b < na && jx != ~0ull) {
+            const BranchOp& op = a.ops[nth_bit(act, b)];
+            const bool x = (u >> b) & 1u;
+            row_action(op, x ? 1 : 0, x ? pr : re, x ? pi : im, x ? re : pr, x ? im : pi, &re,
+                       &im);
+            if (!keep_amp(re, im, a.eps2, eps_bits)) bad = true;
+          }
+        }
+        if (mine && jx != ~0ull) {
+          out.lo[jx] = l0;
+          if (KW == 2) out.hi[jx] = l1;
+          out.re[jx] = re;
+          out.im[jx] = im;
+          ++written;
+        }
+      }
+      bad = __syncthreads_or(bad);
+    }
+    // every entry written exactly once, or some group had no writer
+    for (int dd = 16; dd > 0; dd >>= 1) written += __shfl_xor_sync(FULL, written, dd);
+    if (lane == 0 && written) atomicAdd(&ctl->out_count, written);
+    if (bad && threadIdx.x == 0) atomicOr(&ctl->amp_fail, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&ctl->blocks_done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const bool took = go && atomicAdd(&ctl->amp_fail, 0u) == 0u &&
+                        atomicAdd(&ctl->out_count, 0ull) == n;
+      if (took) {
+        ctl->cur = cur ^ 1u;
+        ctl->updates += n * a.d;   // no entry appears or goes between the gates
+        ctl->amp_state = 1u;
+        ctl->amp_streak = 0u;
+      } else if (go) {
+        const unsigned st = ctl->amp_streak;
+        ctl->amp_backoff = 1u << (st < 6u ? st : 6u);
+        ctl->amp_streak = st + 1u;
+      }
+      if (plog) {
+        plog[0] = go ? n : 0ull;
+        plog[1] = took ? n : 0ull;
       }
       ctl->out_count = 0ull;
       ctl->blocks_done = 0u;
@@ -719,6 +1090,7 @@ int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   a.pass_serial = l.pass_serial;
   a.epoch = epoch;
   a.mg = l.mg;
+  a.fallback = l.fallback;
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {
@@ -731,6 +1103,37 @@ int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
       k_layer_emit<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
     else
       k_layer_emit<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                    unsigned long long* itab, uint32_t epoch, uint32_t force, const AmpLaunch& l,
+                    uint64_t nnz_bound, int part, unsigned long long* plog) {
+  AmpArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (uint32_t j = 0; j < l.d; ++j) a.ops[j] = l.ops[j];
+  a.d = l.d;
+  a.eps2 = l.eps * l.eps;
+  a.eps = l.eps;
+  a.fail_tag = l.fail_tag;
+  a.load_pct = l.load_pct;
+  a.max_log2 = l.max_log2;
+  a.pass_serial = l.pass_serial;
+  a.epoch = epoch;
+  a.force = force;
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
+  if (part == 0) {
+    if (key_words == 1)
+      k_amp_index<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    else
+      k_amp_index<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+  } else {
+    if (key_words == 1)
+      k_amp_layer<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    else
+      k_amp_layer<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -755,6 +1158,7 @@ int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   a.pass_serial = b.pass_serial;
   a.epoch = epoch;
   a.mg = b.mg;
+  a.fallback = b.fallback;
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {
@@ -771,6 +1175,29 @@ int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+template <int KW, int E, bool WALK>
+static void expand_go(int blocks, int threads, size_t smem, cudaStream_t st, Ctl* ctl, Bufs bufs,
+                      const ExpandArgs& a, unsigned long long* plog) {
+  if (WALK)
+    cudaFuncSetAttribute(k_expand<KW, E, WALK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  k_expand<KW, E, WALK><<<blocks, threads, smem, st>>>(ctl, bufs, a, plog);
+}
+
+template <int KW>
+static void expand_kw(int e_log2, bool walk, int blocks, int threads, size_t smem, cudaStream_t st,
+                      Ctl* ctl, Bufs bufs, const ExpandArgs& a, unsigned long long* plog) {
+  if (!walk) {
+    expand_go<KW, 8, false>(blocks, threads, smem, st, ctl, bufs, a, plog);
+  } else if (e_log2 == 1) {
+    expand_go<KW, 2, true>(blocks, threads, smem, st, ctl, bufs, a, plog);
+  } else if (e_log2 == 2) {
+    expand_go<KW, 4, true>(blocks, threads, smem, st, ctl, bufs, a, plog);
+  } else {
+    expand_go<KW, 8, true>(blocks, threads, smem, st, ctl, bufs, a, plog);
+  }
+}
+
 int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const ExpandLaunch& e,
                   uint64_t nnz_bound, unsigned long long* plog) {
   ExpandArgs a;
@@ -785,13 +1212,35 @@ int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const
   a.eps = e.eps;
   a.capacity = e.capacity;
   a.fail_tag = e.fail_tag;
+  a.words = reinterpret_cast<const uint4*>(e.words);
+  a.ftab = reinterpret_cast<const double2*>(e.ftab);
+  a.nwords = e.nwords;
+  a.fused_gates = e.fused_gates;
+  a.has_phase = e.has_phase;
+  const bool walk = e.nwords > 0;
+  const uint64_t total = nnz_bound << e.d;
+  // Outputs per lane: 8 without a walk; with one, as many as still leave about
+  // four warps per SM (more labels per lane share more decode, fewer warps
+  // hide less latency).
+  int e_log2 = 3;
+  if (walk) {
+    // lc.max_blocks is the SM count times the resident blocks of lc.threads
+    const uint64_t sms = (uint64_t)lc.max_blocks * lc.threads / 2048;
+    const uint64_t warps_wanted = 4ull * (sms ? sms : 1);
+    e_log2 = 1;
+    while (e_log2 < 3 && total / (32ull << (e_log2 + 1)) >= warps_wanted) ++e_log2;
+  }
+  const uint64_t span = 32ull << e_log2;
+  const uint64_t spans = (total + span - 1) / span;
+  const int warps_per_block = lc.threads / 32;
+  const int blocks = grid_of((spans + warps_per_block - 1) / warps_per_block * lc.threads, lc.threads,
+                             lc.max_blocks);
+  const size_t smem = walk ? 16 * (size_t)e.nwords : 0;
   cudaStream_t st = (cudaStream_t)lc.stream;
-  // one warp per span of 256 outputs
-  const int blocks = grid_of((nnz_bound << e.d) / 8 + 1, lc.threads, lc.max_blocks);
   if (key_words == 1)
-    k_expand<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, a, plog);
+    expand_kw<1>(e_log2, walk, blocks, lc.threads, smem, st, ctl, bufs, a, plog);
   else
-    k_expand<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, a, plog);
+    expand_kw<2>(e_log2, walk, blocks, lc.threads, smem, st, ctl, bufs, a, plog);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -145,6 +145,8 @@ enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2, PASS_EXPAND = 3, PAS
 // Layer pass: up to kMaxLayerGates consecutive branching gates whose qubits
 // (targets and controls) are pairwise disjoint, applied in one gather pass.
 constexpr uint32_t kMaxLayerGates = 4;
+// Most gates of one amplitude-only run (disjoint qubits; see launch_amp_part).
+constexpr uint32_t kMaxAmpGates = 32;
 
 // Qubits known (on the host, conservatively) to hold one value in every stored
 // label: bit q of known set => every label has bit q = bit q of val.
@@ -255,6 +257,19 @@ struct Ctl {
   // address) and resets buffer rs for the pass after it; kernel boundaries
   // order the three. The host advances the rotation (MaskRing).
   unsigned long long lm[3][kMaskStripes][4];   // {or0, or1, and0, and1}
+  // Amplitude-only branching passes: a pass whose gates meet only complete
+  // groups and prune nothing keeps every label where it is, so it needs only
+  // new amplitudes and an index of the labels that stays valid across such
+  // passes.
+  unsigned long long index_n;    // entries the index was built for (sets its size)
+  unsigned int index_ok;         // the index table holds every label of the state
+  unsigned int index_epoch;      // its epoch
+  unsigned int amp_go;           // the running pass attempts the amplitude-only form
+  unsigned int amp_state;        // 1: the amplitude-only form produced the pass's state
+  unsigned int amp_fail;         // set by threads that find the form not applicable
+  unsigned int amp_backoff;      // passes still to skip after failed attempts
+  unsigned int amp_streak;       // failed attempts in a row
+  unsigned int amp_pad;
 };
 
 // Mask buffer indices of one label-writing launch, packed rd | wr << 8 | rs << 16.
@@ -309,9 +324,10 @@ struct LaunchCfg {
 // and entries in the state afterwards.
 int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots);
 // words / ftab: the pass's encoded op stream and fire-slot tables in device memory
+// lanes: labels per thread (1, 2, 4 or 8; 0 picks by the nonzero bound)
 int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
                  const OpWord* words, const double* ftab, uint64_t nnz_bound, uint32_t mg,
-                 unsigned long long* plog);
+                 int lanes, unsigned long long* plog);
 struct BranchLaunch {
   BranchOp op;
   double eps;
@@ -319,6 +335,7 @@ struct BranchLaunch {
   int coop;
   uint64_t capacity, fail_tag;
   uint32_t mg;   // label-mask buffers (MaskRing): rd for the gather passes, all for the writer
+  uint32_t fallback = 0;   // 1: runs only if the amplitude-only form did not take the pass
 };
 int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,
                        const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog);
@@ -359,10 +376,28 @@ struct LayerLaunch {
   double eps;
   uint32_t load_pct, max_log2, pass_serial, mg;
   uint64_t capacity, fail_tag;
+  uint32_t fallback;   // as in BranchLaunch
 };
 int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                       unsigned long long* itab, uint32_t epoch, const LayerLaunch& l,
                       uint64_t nnz_bound, int part, unsigned long long* plog);
+// Amplitude-only form of a run of branching passes: l.d gates (1..32) on
+// pairwise disjoint qubits. part 0: unless an earlier failure says to skip
+// this attempt, index every label (epoch `epoch`) if `force` or the device
+// says the index is stale, and decide the attempt; part 1: the attempt
+// itself, which produces the run's state only if every active group is
+// complete (at most 16 members) and nothing is pruned (else the run's own
+// passes, launched after it with fallback = 1, run).
+struct AmpLaunch {
+  BranchOp ops[kMaxAmpGates];
+  uint32_t d;
+  double eps;
+  uint32_t load_pct, max_log2, pass_serial;
+  uint64_t fail_tag;
+};
+int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                    unsigned long long* itab, uint32_t epoch, uint32_t force, const AmpLaunch& l,
+                    uint64_t nnz_bound, int part, unsigned long long* plog);
 // Expansion pass (PASS_EXPAND); f, m: its tables in device memory.
 struct ExpandLaunch {
   const double* f;
@@ -370,6 +405,11 @@ struct ExpandLaunch {
   uint32_t d, real, pass_serial, mg;
   double eps;
   uint64_t capacity, fail_tag;
+  // optional fused run applied to the outputs before they are stored
+  // (nwords == 0: none); fused_gates counts its gates for the update count
+  const OpWord* words;
+  const double* ftab;
+  uint32_t nwords, fused_gates, has_phase;
 };
 int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const ExpandLaunch& e,
                   uint64_t nnz_bound, unsigned long long* plog);

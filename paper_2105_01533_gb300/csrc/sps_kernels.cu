@@ -43,7 +43,10 @@ struct FusedArgs {
   uint32_t nwords, ngates, has_perm, has_phase, mg;
 };
 
-template <int KW>
+// E labels per thread (E consecutive block-wide slices of the state): the E
+// labels walk the op stream together, so each op is read and decoded once for
+// E labels and the E dependent chains overlap.
+template <int KW, int E>
 __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedArgs a,
                                                unsigned long long* plog) {
   const uint64_t n = ctl->nnz;
@@ -57,39 +60,59 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedA
     if (a.has_perm) reset_label_masks(ctl, mg_rs(a.mg));
   }
   const SoA s = pick(bufs, ctl->cur);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  // the first label is in flight while the op stream is staged
-  uint64_t k0 = i < n ? s.lo[i] : 0ull;
-  uint64_t k1 = (KW == 2 && i < n) ? s.hi[i] : 0ull;
+  const uint64_t slice = (uint64_t)blockDim.x;
+  const uint64_t stride = (uint64_t)gridDim.x * slice * E;
+  uint64_t base = blockIdx.x * slice * E + threadIdx.x;
+  // the first labels are in flight while the op stream is staged
+  uint64_t k0[E], k1[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint64_t i = base + e * slice;
+    k0[e] = i < n ? s.lo[i] : 0ull;
+    k1[e] = (KW == 2 && i < n) ? s.hi[i] : 0ull;
+  }
   extern __shared__ uint4 fsm[];
   for (uint32_t w = threadIdx.x; w < a.nwords; w += blockDim.x) fsm[w] = a.words[w];
   __syncthreads();
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the new labels
-  for (; i < n; i += stride) {
-    uint32_t cnt = 0;
-    uint64_t fire = 0ull;
-    walk_ops<KW>(fsm, a.nwords, k0, k1, cnt, fire);
-    if (a.has_perm) {
-      s.lo[i] = k0;
-      if (KW == 2) s.hi[i] = k1;
-      mo0 |= k0;
-      mo1 |= k1;
-      ma0 &= k0;
-      ma1 &= k1;
+  for (; base < n; base += stride) {
+    uint32_t cnt[E];
+    uint64_t fire[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      cnt[e] = 0u;
+      fire[e] = 0ull;
     }
-    cnt &= 7u;
-    if (a.has_phase && (cnt != 0u || fire != 0ull)) {
-      double re = s.re[i], im = s.im[i];
-      apply_fire(fire, a.ftab, re, im);
-      apply_pi4(cnt, re, im);
-      s.re[i] = re;
-      s.im[i] = im;
+    walk_ops_n<KW, E>(fsm, a.nwords, k0, k1, cnt, fire);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint64_t i = base + e * slice;
+      if (i >= n) continue;
+      if (a.has_perm) {
+        s.lo[i] = k0[e];
+        if (KW == 2) s.hi[i] = k1[e];
+        mo0 |= k0[e];
+        mo1 |= k1[e];
+        ma0 &= k0[e];
+        ma1 &= k1[e];
+      }
+      const uint32_t c8 = cnt[e] & 7u;
+      if (a.has_phase && (c8 != 0u || fire[e] != 0ull)) {
+        double re = s.re[i], im = s.im[i];
+        apply_fire(fire[e], a.ftab, re, im);
+        apply_pi4(c8, re, im);
+        s.re[i] = re;
+        s.im[i] = im;
+      }
     }
-    const uint64_t nx = i + stride;
-    if (nx < n) {
-      k0 = s.lo[nx];
-      k1 = KW == 2 ? s.hi[nx] : 0ull;
+    const uint64_t nx = base + stride;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint64_t i = nx + e * slice;
+      if (i < n) {
+        k0[e] = s.lo[i];
+        k1[e] = KW == 2 ? s.hi[i] : 0ull;
+      }
     }
   }
   if (a.has_perm) merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
@@ -281,15 +304,13 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
               pi = t.y;
               any = true;
             } else {
-              const double nr = pr * t.x - pi * t.y;
-              const double ni = pr * t.y + pi * t.x;
-              pr = nr;
-              pi = ni;
+              cmul_rn(pr, pi, t.x, t.y);
             }
           }
-          const double re = s.re[e], im = s.im[e];
-          s.re[e] = re * pr - im * pi;
-          s.im[e] = re * pi + im * pr;
+          double re = s.re[e], im = s.im[e];
+          cmul_rn(re, im, pr, pi);
+          s.re[e] = re;
+          s.im[e] = im;
         }
       }
     }
@@ -841,7 +862,7 @@ int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots) {
 
 int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
                  const OpWord* words, const double* ftab, uint64_t nnz_bound, uint32_t mg,
-                 unsigned long long* plog) {
+                 int lanes, unsigned long long* plog) {
   if (p.ops.empty()) {   // every gate resolved on the host: only the update count
     k_count_updates<<<1, 1, 0, (cudaStream_t)lc.stream>>>(ctl, p.ngates);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
@@ -854,14 +875,29 @@ int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const 
   a.has_perm = p.has_perm;
   a.has_phase = p.has_phase;
   a.mg = mg;
-  const int blocks = grid_for(nnz_bound, lc.threads, lc.max_blocks);
+  // labels per thread: as many as still leave about four warps per SM per
+  // label slot (SPS_OPT_FUSED_LABELS overrides)
+  int e = lanes;
+  if (e == 0) {
+    const uint64_t warps_wanted = 4ull * (uint64_t)sm_count(lc);
+    e = 1;
+    while (e < 8 && nnz_bound / (32ull * (uint64_t)(2 * e)) >= warps_wanted) e *= 2;
+  }
+  const int blocks = grid_for((nnz_bound + e - 1) / e, lc.threads, lc.max_blocks);
   // at most 4 words per op: <= 32 KB, under the default 48 KB
   const size_t smem = 16 * (size_t)a.nwords;
   cudaStream_t st = (cudaStream_t)lc.stream;
-  if (key_words == 1)
-    k_fused<1><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
-  else
-    k_fused<2><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+  if (key_words == 1) {
+    if (e == 1) k_fused<1, 1><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+    else if (e == 2) k_fused<1, 2><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+    else if (e == 4) k_fused<1, 4><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+    else k_fused<1, 8><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+  } else {
+    if (e == 1) k_fused<2, 1><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+    else if (e == 2) k_fused<2, 2><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+    else if (e == 4) k_fused<2, 4><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+    else k_fused<2, 8><<<blocks, lc.threads, smem, st>>>(ctl, bufs, a, plog);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -28,7 +28,8 @@ SPS_OPT_LOAD_FACTOR_PCT, SPS_OPT_PROBE_LIMIT, SPS_OPT_BLOCK_THREADS = 1, 2, 3
 SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
 SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP, SPS_OPT_BITSLICE_MIN_NNZ = 7, 8, 9
 SPS_OPT_BRANCH_FORM, SPS_OPT_BITSLICE_GROUPS, SPS_OPT_EXPAND, SPS_OPT_FOLD = 10, 11, 12, 13
-SPS_OPT_COMMUTE, SPS_OPT_LAYER_GATES = 14, 15
+SPS_OPT_COMMUTE, SPS_OPT_LAYER_GATES, SPS_OPT_EXPAND_WALK, SPS_OPT_FUSED_LABELS = 14, 15, 16, 17
+SPS_OPT_AMP_ONLY = 18
 KIND_SMALL_RUN, KIND_GATHER_BUILD, KIND_GATHER_EMIT = 4, 5, 6
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 
