@@ -889,7 +889,8 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
                                                    const unsigned long long* itab,
                                                    const __grid_constant__ AmpArgs a,
                                                    unsigned long long* plog) {
-  __shared__ uint32_t q1[kAmpQueue], q2[kAmpQueue];
+  __shared__ uint32_t q1[kAmpQueue], q2[kAmpQueue];   // writers' offsets in the slice
+  __shared__ uint32_t a1[kAmpQueue], a2[kAmpQueue];   // and their active gates
   __shared__ unsigned n1, n2;
   const bool go = ctl->amp_go != 0u;
   const uint64_t n = ctl->nnz;
@@ -930,8 +931,15 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
           for (uint32_t rem = act; rem; rem &= rem - 1u)
             writer = writer && !label_bit(k0, k1, a.ops[__ffs(rem) - 1u].sbit);
           if (writer) {
-            if ((act & (act - 1u)) == 0u) q1[atomicAdd(&n1, 1u)] = (uint32_t)(i - base);
-            else q2[atomicAdd(&n2, 1u)] = (uint32_t)(i - base);
+            if ((act & (act - 1u)) == 0u) {
+              const unsigned t = atomicAdd(&n1, 1u);
+              q1[t] = (uint32_t)(i - base);
+              a1[t] = act;
+            } else {
+              const unsigned t = atomicAdd(&n2, 1u);
+              q2[t] = (uint32_t)(i - base);
+              a2[t] = act;
+            }
           }
         }
       }
@@ -942,7 +950,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
         const uint64_t j0 = base + q1[t];
         const uint64_t k0 = s.lo[j0];
         const uint64_t k1 = KW == 2 ? s.hi[j0] : 0ull;
-        const uint32_t act = amp_active<KW>(a, k0, k1);
+        const uint32_t act = a1[t];
         const BranchOp& op = a.ops[__ffs(act) - 1u];
         const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
         const uint64_t j1 = find_label<KW>(itab, mask, ep, s, p0, p1);
@@ -988,7 +996,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
           const uint64_t jw = base + q2[g];
           k0 = s.lo[jw];
           k1 = KW == 2 ? s.hi[jw] : 0ull;
-          act = amp_active<KW>(a, k0, k1);
+          act = a2[g];
           na = __popc(act);
         }
         const bool mine = have && u < (1u << na);

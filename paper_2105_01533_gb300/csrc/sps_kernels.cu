@@ -291,24 +291,35 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
           ma0 &= lo;
           ma1 &= hi;
         }
-        if (a.has_phase && (aux0 | aux1)) {
-          double pr = 1.0, pi = 0.0;
-          bool any = false;
-          for (uint32_t c = 0; c < a.nchunks; ++c) {
-            const uint32_t word = c < 4 ? aux0 : aux1;
-            const uint32_t idx = (word >> (8 * (c & 3u))) & 0xFFu;
-            if (idx == 0u) continue;
-            const double2 t = stab[c * 256u + idx];
-            if (!any) {
-              pr = t.x;
-              pi = t.y;
-              any = true;
-            } else {
-              cmul_rn(pr, pi, t.x, t.y);
-            }
-          }
+        // the pi/4 counter (aux bits 0..2) is applied exactly as in the direct
+        // form (quarter turns are swaps and signs, no FP64 products); the
+        // tables then see only the fire slots
+        uint32_t cnt = 0u;
+        if (a.has_cnt) {
+          cnt = aux0 & 7u;
+          aux0 &= ~7u;
+        }
+        if (a.has_phase && (aux0 | aux1 | cnt)) {
           double re = s.re[e], im = s.im[e];
-          cmul_rn(re, im, pr, pi);
+          if (aux0 | aux1) {
+            double pr = 1.0, pi = 0.0;
+            bool any = false;
+            for (uint32_t c = 0; c < a.nchunks; ++c) {
+              const uint32_t word = c < 4 ? aux0 : aux1;
+              const uint32_t idx = (word >> (8 * (c & 3u))) & 0xFFu;
+              if (idx == 0u) continue;
+              const double2 t = stab[c * 256u + idx];
+              if (!any) {
+                pr = t.x;
+                pi = t.y;
+                any = true;
+              } else {
+                cmul_rn(pr, pi, t.x, t.y);
+              }
+            }
+            cmul_rn(re, im, pr, pi);
+          }
+          apply_pi4(cnt, re, im);
           s.re[e] = re;
           s.im[e] = im;
         }
