@@ -875,6 +875,23 @@ __device__ __forceinline__ void row_action(const BranchOp& op, int r, double a0r
   *ni = __dadd_rn(t0i, t1i);
 }
 
+// Row r of a pair action whose matrix is real (REAL) or general, with the
+// rounding of pair_action; the real form issues only its own FP64 products
+// (a run-time choice between the two forms is compiled as both, predicated,
+// and the FP64 pipe is scarce).
+template <bool REAL>
+__device__ __forceinline__ void row_of(const BranchOp& op, int r, double a0r, double a0i,
+                                       double a1r, double a1i, double* nr, double* ni) {
+  if (REAL) {
+    const double m0 = r == 0 ? op.m_re[0][0] : op.m_re[1][0];
+    const double m1 = r == 0 ? op.m_re[0][1] : op.m_re[1][1];
+    *nr = __dadd_rn(__dmul_rn(m0, a0r), __dmul_rn(m1, a1r));
+    *ni = __dadd_rn(__dmul_rn(m0, a0i), __dmul_rn(m1, a1i));
+  } else {
+    row_action(op, r, a0r, a0i, a1r, a1i, nr, ni);
+  }
+}
+
 // The b-th set bit of act (b < popc(act)).
 __device__ __forceinline__ uint32_t nth_bit(uint32_t act, uint32_t b) {
   for (uint32_t k = 0; k < b; ++k) act &= act - 1u;
@@ -884,12 +901,12 @@ __device__ __forceinline__ uint32_t nth_bit(uint32_t act, uint32_t b) {
 constexpr uint32_t kAmpQueue = 256;   // >= threads per block
 constexpr uint32_t kAmpWide = 4;      // most active gates of a group (16 members)
 
-template <int KW>
+template <int KW, bool REAL>
 __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
                                                    const unsigned long long* itab,
                                                    const __grid_constant__ AmpArgs a,
                                                    unsigned long long* plog) {
-  __shared__ uint32_t q1[kAmpQueue], q2[kAmpQueue];   // writers' offsets in the slice
+  __shared__ uint32_t q1[kAmpQueue], q2[kAmpQueue];   // writers' entry indices
   __shared__ uint32_t a1[kAmpQueue], a2[kAmpQueue];   // and their active gates
   __shared__ unsigned n1, n2;
   const bool go = ctl->amp_go != 0u;
@@ -906,12 +923,18 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
     const uint64_t eps_bits = eps_pattern(a.eps);
     // (no thread polls the others' failures: every iteration would load one
     // shared address from L2, which costs more than finishing the pass)
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n && !bad; base += stride) {
+    // A block's warps take chunks of 32 entries spread over the state (chunk
+    // w + W t of the block lies G chunks apart from the next, G blocks, W
+    // warps per block): the writers of large groups can sit in clusters of the
+    // state, and a block whose slice held a cluster would finish long after
+    // the others.
+    const uint64_t nchunks = (n + 31) / 32;
+    const uint64_t G = gridDim.x;
+    for (uint64_t t = 0; blockIdx.x + G * nwarps * t < nchunks && !bad; ++t) {
       if (threadIdx.x == 0) n1 = n2 = 0u;
       __syncthreads();
       // 1. scan: untouched entries are copied, writers queued
-      const uint64_t i = base + threadIdx.x;
+      const uint64_t i = (blockIdx.x + G * (warp + nwarps * t)) * 32u + lane;
       if (i < n) {
         const uint64_t k0 = s.lo[i];
         const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
@@ -932,13 +955,13 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
             writer = writer && !label_bit(k0, k1, a.ops[__ffs(rem) - 1u].sbit);
           if (writer) {
             if ((act & (act - 1u)) == 0u) {
-              const unsigned t = atomicAdd(&n1, 1u);
-              q1[t] = (uint32_t)(i - base);
-              a1[t] = act;
+              const unsigned q = atomicAdd(&n1, 1u);
+              q1[q] = (uint32_t)i;
+              a1[q] = act;
             } else {
-              const unsigned t = atomicAdd(&n2, 1u);
-              q2[t] = (uint32_t)(i - base);
-              a2[t] = act;
+              const unsigned q = atomicAdd(&n2, 1u);
+              q2[q] = (uint32_t)i;
+              a2[q] = act;
             }
           }
         }
@@ -946,11 +969,11 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
       __syncthreads();
       const unsigned c1 = n1, c2 = n2;
       // 2. pairs: the writer looks up its partner and writes both
-      for (unsigned t = threadIdx.x; t < c1; t += blockDim.x) {
-        const uint64_t j0 = base + q1[t];
+      for (unsigned t1 = threadIdx.x; t1 < c1; t1 += blockDim.x) {
+        const uint64_t j0 = q1[t1];
         const uint64_t k0 = s.lo[j0];
         const uint64_t k1 = KW == 2 ? s.hi[j0] : 0ull;
-        const uint32_t act = a1[t];
+        const uint32_t act = a1[t1];
         const BranchOp& op = a.ops[__ffs(act) - 1u];
         const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
         const uint64_t j1 = find_label<KW>(itab, mask, ep, s, p0, p1);
@@ -966,7 +989,8 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
           continue;
         }
         double n0r, n0i, n1r, n1i;
-        pair_action(op, true, false, a0r, a0i, a1r, a1i, &n0r, &n0i, &n1r, &n1i);
+        row_of<REAL>(op, 0, a0r, a0i, a1r, a1i, &n0r, &n0i);
+        row_of<REAL>(op, 1, a0r, a0i, a1r, a1i, &n1r, &n1i);
         // (later gates are inactive for the pair: they prune what this kept)
         if (!keep_amp(n0r, n0i, a.eps2, eps_bits) || !keep_amp(n1r, n1i, a.eps2, eps_bits)) {
           bad = true;
@@ -993,7 +1017,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
         uint64_t k0 = 0, k1 = 0;
         uint32_t act = 0, na = 0;
         if (have) {
-          const uint64_t jw = base + q2[g];
+          const uint64_t jw = q2[g];
           k0 = s.lo[jw];
           k1 = KW == 2 ? s.hi[jw] : 0ull;
           act = a2[g];
@@ -1009,7 +1033,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
               l0 ^= op.m[0];
               l1 ^= op.m[1];
             }
-          jx = u == 0u ? base + q2[g] : find_label<KW>(itab, mask, ep, s, l0, l1);
+          jx = u == 0u ? (uint64_t)q2[g] : find_label<KW>(itab, mask, ep, s, l0, l1);
           if (jx == ~0ull) {
             bad = true;
           } else {
@@ -1024,8 +1048,8 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
           if (mine && b < na && jx != ~0ull) {
             const BranchOp& op = a.ops[nth_bit(act, b)];
             const bool x = (u >> b) & 1u;
-            row_action(op, x ? 1 : 0, x ? pr : re, x ? pi : im, x ? re : pr, x ? im : pi, &re,
-                       &im);
+            row_of<REAL>(op, x ? 1 : 0, x ? pr : re, x ? pi : im, x ? re : pr, x ? im : pi, &re,
+                         &im);
             if (!keep_amp(re, im, a.eps2, eps_bits)) bad = true;
           }
         }
@@ -1138,10 +1162,15 @@ int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
     else
       k_amp_index<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
   } else {
-    if (key_words == 1)
-      k_amp_layer<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
-    else
-      k_amp_layer<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    bool real = true;
+    for (uint32_t j = 0; j < l.d; ++j) real = real && l.ops[j].real_m && !l.ops[j].pauli;
+    if (key_words == 1) {
+      if (real) k_amp_layer<1, true><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+      else k_amp_layer<1, false><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    } else {
+      if (real) k_amp_layer<2, true><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+      else k_amp_layer<2, false><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+    }
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
