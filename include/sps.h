@@ -293,10 +293,15 @@ typedef enum sps_option {
                                   stays valid while labels do not move (a pass
                                   that moves labels, or another use of the
                                   index table, makes the next attempt rebuild
-                                  it). The result is the same bit for bit.
+                                  it). Branching passes on pairwise disjoint
+                                  qubits (up to 32 gates) share one attempt,
+                                  and a run of phase gates right after them is
+                                  applied by it before the stores. The result
+                                  is the same bit for bit (as the direct fused
+                                  form, which such a phase run then takes).
                                   Where the form does not apply the usual
                                   kernels run, and the next 1, 2, 4 .. 64
-                                  passes skip the attempt. 0: never */
+                                  attempts are skipped. 0: never */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:

@@ -53,6 +53,8 @@ struct ApplyPlan {
   std::vector<uint8_t> walk_next;   // expansion: the fused pass after it runs in its kernel
   std::vector<size_t> amp_end;      // > 0: a run of branching passes on disjoint qubits starts
                                     // here (ends there) with one amplitude-only attempt
+  std::vector<uint8_t> amp_walk;    // run start: the phase-only fused pass after the run is
+                                    // walked by the attempt (and is its fallback)
   std::vector<unsigned char> image;
 };
 
@@ -590,7 +592,8 @@ static sps_status next_epoch(sps_state* s, const LaunchCfg& lc) {
 // in all (index check or rebuild, then the attempt); the run's own kernels,
 // launched after it with fallback = 1, run only if it did not take the run.
 static sps_status launch_amp_attempt(sps_state* s, const LaunchCfg& lc, const BranchOp* ops,
-                                     uint32_t d, double prune_eps, uint32_t serial, uint64_t tag) {
+                                     uint32_t d, double prune_eps, uint32_t serial, uint64_t tag,
+                                     const Pass* walk, const OpWord* words, const double* ftab) {
   const sps_status es = next_epoch(s, lc);
   if (es != SPS_OK) return es;
   AmpLaunch l;
@@ -602,6 +605,13 @@ static sps_status launch_amp_attempt(sps_state* s, const LaunchCfg& lc, const Br
   l.max_log2 = s->itab_log2;
   l.pass_serial = serial;
   l.fail_tag = tag;
+  if (walk) {   // the phase-only run after the run, walked on the outputs
+    l.words = words;
+    l.ftab = ftab;
+    l.nwords = (uint32_t)walk->words.size();
+    l.fused_gates = walk->ngates;
+    l.has_phase = walk->has_phase ? 1u : 0u;
+  }
   const uint32_t force = s->amp_force ? 1u : 0u;
   {
     ProfScope pi(s, 9, serial, d, 0u);
@@ -818,6 +828,21 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
       i = j;
     }
   }
+  // (not a run long enough, on a state large enough, for the bit-sliced form:
+  // there the separate bit-sliced pass is faster than walking each output)
+  P->amp_walk.assign(np, 0);
+  std::vector<uint8_t> amp_walked(np, 0);   // fused passes walked by an attempt
+  for (size_t i = 0; i < np; ++i) {
+    const size_t j = P->amp_end[i];
+    if (!j || j >= np) continue;
+    const Pass& f = passes[j];
+    const bool sliced = s->bitslice_min_ops && f.ops.size() >= s->bitslice_min_ops &&
+                        P->bound_at[j] >= s->bitslice_min_nnz;
+    if (f.kind == PASS_FUSED && !f.has_perm && !P->seg_end[j] && !sliced) {
+      P->amp_walk[i] = 1;
+      amp_walked[j] = 1;
+    }
+  }
   // 2b. an expansion takes the fused run right after it (outside small runs),
   //    unless that run is long enough and the state large enough for the
   //    bit-sliced form (faster there than the per-label walk)
@@ -844,7 +869,9 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
       continue;
     }
     const Pass& p = passes[i];
-    const bool walked = i > 0 && P->walk_next[i - 1];
+    // a run walked by an expansion or by an amplitude-only attempt stays in the
+    // direct form (the walk is the direct form's arithmetic)
+    const bool walked = (i > 0 && P->walk_next[i - 1]) || amp_walked[i];
     if (p.kind == PASS_FUSED && !walked && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops &&
         P->bound_at[i] >= s->bitslice_min_nnz) {
       build_bitslice(p, s->nqubits, &P->bs[i]);
@@ -997,9 +1024,19 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         else for (const BranchOp& op : passes[k].lay) ops[d++] = op;
       }
       const uint64_t tg = ((uint64_t)s->apply_serial << 32) | (p.first_gate & 0xFFFFFFFFull);
-      const sps_status as = launch_amp_attempt(s, lc, ops, d, prune_eps, s->pass_serial + 1, tg);
+      const Pass* walk = nullptr;
+      const OpWord* words = nullptr;
+      const double* ftab = nullptr;
+      if (P.amp_walk[pi]) {
+        const size_t j = P.amp_end[pi];
+        walk = &passes[j];
+        words = reinterpret_cast<const OpWord*>(s->arena + run_off[j]);
+        ftab = reinterpret_cast<const double*>(s->arena + ph_off[j]);
+      }
+      const sps_status as = launch_amp_attempt(s, lc, ops, d, prune_eps, s->pass_serial + 1, tg,
+                                               walk, words, ftab);
       if (as != SPS_OK) return as;
-      amp_run_end = P.amp_end[pi];
+      amp_run_end = P.amp_end[pi] + (walk ? 1 : 0);
     }
     const uint32_t fb = pi < amp_run_end ? 1u : 0u;   // a fallback pass of an attempted run
     if (!fb && (p.kind == PASS_BRANCH || p.kind == PASS_LAYER)) s->amp_force = true;
@@ -1106,12 +1143,13 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         bl.list_len = (uint32_t)b.list.size();
         bl.groups = s->bs_groups;
         bl.mg = p.has_perm ? s->masks.writer() : 0u;
+        bl.fallback = fb;
         n = launch_fused_bs(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
       } else {
         n = launch_fused(lc, s->kw, s->ctl, s->bufs, p,
                          reinterpret_cast<const OpWord*>(s->arena + run_off[pi]),
                          reinterpret_cast<const double*>(s->arena + ph_off[pi]), s->nnz_bound,
-                         p.has_perm ? s->masks.writer() : 0u, s->fused_labels, ps.slot);
+                         p.has_perm ? s->masks.writer() : 0u, s->fused_labels, fb, ps.slot);
       }
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());

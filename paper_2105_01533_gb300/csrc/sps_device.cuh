@@ -127,6 +127,11 @@ __device__ __forceinline__ void set_label_masks(Ctl* ctl, uint32_t b, uint64_t o
   }
 }
 
+// A fallback launch whose pass an amplitude-only attempt already produced.
+__device__ __forceinline__ bool amp_took(const Ctl* ctl, uint32_t fallback) {
+  return fallback != 0u && *reinterpret_cast<const volatile unsigned*>(&ctl->amp_state) == 1u;
+}
+
 // Empties buffer b for the next merge (one thread).
 __device__ __forceinline__ void reset_label_masks(Ctl* ctl, uint32_t b) {
   set_label_masks(ctl, b, 0ull, 0ull, ~0ull, ~0ull);

@@ -43,11 +43,6 @@ struct GatherArgs {
   uint32_t fallback;   // 1: skip if the amplitude-only form took the pass
 };
 
-// A fallback launch whose pass the amplitude-only form already produced.
-__device__ __forceinline__ bool amp_took(const Ctl* ctl, uint32_t fallback) {
-  return fallback != 0u && *reinterpret_cast<const volatile unsigned*>(&ctl->amp_state) == 1u;
-}
-
 // A skipped emit still advances the label masks: the labels are those of its
 // input, so buffer wr gets buffer rd's masks and rs is emptied (block 0).
 __device__ __forceinline__ void carry_label_masks(Ctl* ctl, uint32_t mg) {
@@ -788,7 +783,34 @@ struct AmpArgs {
   double eps2, eps;
   uint32_t load_pct, max_log2, pass_serial, epoch, force;
   uint64_t fail_tag;
+  // WALK: the phase-only fused run after the run, applied to every output
+  // before it is stored (as the direct fused pass would apply it)
+  const uint4* words;
+  const double2* ftab;
+  uint32_t nwords, fused_gates, has_phase;
 };
+
+// Stores one output of an amplitude-only run (WALK: after the phase run).
+template <int KW, bool WALK>
+__device__ __forceinline__ void amp_store(const AmpArgs& a, const uint4* fsm, const SoA& out,
+                                          uint64_t j, uint64_t k0, uint64_t k1, double re,
+                                          double im) {
+  if (WALK) {
+    uint64_t l0 = k0, l1 = k1;   // a phase-only run leaves the label as it is
+    uint32_t cnt = 0;
+    uint64_t fire = 0ull;
+    walk_ops<KW>(fsm, a.nwords, l0, l1, cnt, fire);
+    cnt &= 7u;
+    if (a.has_phase && (cnt != 0u || fire != 0ull)) {
+      apply_fire(fire, a.ftab, re, im);
+      apply_pi4(cnt, re, im);
+    }
+  }
+  out.lo[j] = k0;
+  if (KW == 2) out.hi[j] = k1;
+  out.re[j] = re;
+  out.im[j] = im;
+}
 
 template <int KW>
 __device__ __forceinline__ uint32_t amp_active(const AmpArgs& a, uint64_t k0, uint64_t k1) {
@@ -901,7 +923,7 @@ __device__ __forceinline__ uint32_t nth_bit(uint32_t act, uint32_t b) {
 constexpr uint32_t kAmpQueue = 256;   // >= threads per block
 constexpr uint32_t kAmpWide = 4;      // most active gates of a group (16 members)
 
-template <int KW, bool REAL>
+template <int KW, bool REAL, bool WALK>
 __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
                                                    const unsigned long long* itab,
                                                    const __grid_constant__ AmpArgs a,
@@ -909,7 +931,12 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
   __shared__ uint32_t q1[kAmpQueue], q2[kAmpQueue];   // writers' entry indices
   __shared__ uint32_t a1[kAmpQueue], a2[kAmpQueue];   // and their active gates
   __shared__ unsigned n1, n2;
+  extern __shared__ uint4 fsm[];                      // WALK: the phase run's op stream
   const bool go = ctl->amp_go != 0u;
+  if (WALK && go) {
+    for (uint32_t w = threadIdx.x; w < a.nwords; w += blockDim.x) fsm[w] = a.words[w];
+    __syncthreads();
+  }
   const uint64_t n = ctl->nnz;
   const unsigned cur = ctl->cur;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -942,10 +969,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
         if (act == 0u) {   // every gate only prunes this entry
           const double re = s.re[i], im = s.im[i];
           bad = !keep_amp(re, im, a.eps2, eps_bits);
-          out.lo[i] = k0;
-          if (KW == 2) out.hi[i] = k1;
-          out.re[i] = re;
-          out.im[i] = im;
+          amp_store<KW, WALK>(a, fsm, out, i, k0, k1, re, im);
           ++written;
         } else if (__popc(act) > kAmpWide) {
           bad = true;
@@ -996,16 +1020,8 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
           bad = true;
           continue;
         }
-        out.lo[j0] = k0;
-        out.lo[j1] = p0;
-        if (KW == 2) {
-          out.hi[j0] = k1;
-          out.hi[j1] = p1;
-        }
-        out.re[j0] = n0r;
-        out.im[j0] = n0i;
-        out.re[j1] = n1r;
-        out.im[j1] = n1i;
+        amp_store<KW, WALK>(a, fsm, out, j0, k0, k1, n0r, n0i);
+        amp_store<KW, WALK>(a, fsm, out, j1, p0, p1, n1r, n1i);
         written += 2;
       }
       // 3. groups of 4..16: 16 lanes each, lane u = member u (every lane of
@@ -1054,10 +1070,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
           }
         }
         if (mine && jx != ~0ull) {
-          out.lo[jx] = l0;
-          if (KW == 2) out.hi[jx] = l1;
-          out.re[jx] = re;
-          out.im[jx] = im;
+          amp_store<KW, WALK>(a, fsm, out, jx, l0, l1, re, im);
           ++written;
         }
       }
@@ -1078,7 +1091,8 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
                         atomicAdd(&ctl->out_count, 0ull) == n;
       if (took) {
         ctl->cur = cur ^ 1u;
-        ctl->updates += n * a.d;   // no entry appears or goes between the gates
+        // no entry appears or goes between the gates (nor in the phase run)
+        ctl->updates += n * (a.d + (WALK ? a.fused_gates : 0u));
         ctl->amp_state = 1u;
         ctl->amp_streak = 0u;
       } else if (go) {
@@ -1139,6 +1153,23 @@ int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+template <int KW, bool WALK>
+static void amp_go(bool real, int blocks, int threads, size_t smem, cudaStream_t st, Ctl* ctl,
+                   Bufs bufs, const unsigned long long* itab, const AmpArgs& a,
+                   unsigned long long* plog) {
+  if (real) {
+    if (WALK)
+      cudaFuncSetAttribute(k_amp_layer<KW, true, WALK>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_amp_layer<KW, true, WALK><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
+  } else {
+    if (WALK)
+      cudaFuncSetAttribute(k_amp_layer<KW, false, WALK>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_amp_layer<KW, false, WALK><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
+  }
+}
+
 int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                     unsigned long long* itab, uint32_t epoch, uint32_t force, const AmpLaunch& l,
                     uint64_t nnz_bound, int part, unsigned long long* plog) {
@@ -1154,6 +1185,11 @@ int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   a.pass_serial = l.pass_serial;
   a.epoch = epoch;
   a.force = force;
+  a.words = reinterpret_cast<const uint4*>(l.words);
+  a.ftab = reinterpret_cast<const double2*>(l.ftab);
+  a.nwords = l.nwords;
+  a.fused_gates = l.fused_gates;
+  a.has_phase = l.has_phase;
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {
@@ -1164,12 +1200,14 @@ int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   } else {
     bool real = true;
     for (uint32_t j = 0; j < l.d; ++j) real = real && l.ops[j].real_m && !l.ops[j].pauli;
+    const bool walk = l.fused_gates > 0;   // (a run with no ops left only counts)
+    const size_t smem = 16 * (size_t)l.nwords;
     if (key_words == 1) {
-      if (real) k_amp_layer<1, true><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
-      else k_amp_layer<1, false><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+      if (walk) amp_go<1, true>(real, blocks, lc.threads, smem, st, ctl, bufs, itab, a, plog);
+      else amp_go<1, false>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
     } else {
-      if (real) k_amp_layer<2, true><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
-      else k_amp_layer<2, false><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+      if (walk) amp_go<2, true>(real, blocks, lc.threads, smem, st, ctl, bufs, itab, a, plog);
+      else amp_go<2, false>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
     }
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

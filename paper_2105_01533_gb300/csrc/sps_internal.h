@@ -324,10 +324,11 @@ struct LaunchCfg {
 // and entries in the state afterwards.
 int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots);
 // words / ftab: the pass's encoded op stream and fire-slot tables in device memory
-// lanes: labels per thread (1, 2, 4 or 8; 0 picks by the nonzero bound)
+// lanes: labels per thread (1, 2, 4 or 8; 0 picks by the nonzero bound);
+// fallback: 1 if an amplitude-only attempt before it may have taken the pass
 int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
                  const OpWord* words, const double* ftab, uint64_t nnz_bound, uint32_t mg,
-                 int lanes, unsigned long long* plog);
+                 int lanes, uint32_t fallback, unsigned long long* plog);
 struct BranchLaunch {
   BranchOp op;
   double eps;
@@ -350,6 +351,7 @@ struct BsLaunch {
   uint32_t has_perm, has_phase, has_cnt, list_len;
   uint32_t groups;          // groups of 32 entries per warp tile (even, 2..32), 0 = choose
   uint32_t mg;              // label-mask buffers (MaskRing)
+  uint32_t fallback = 0;    // as in launch_fused
 };
 int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
                     uint64_t nnz_bound, unsigned long long* plog);
@@ -394,6 +396,11 @@ struct AmpLaunch {
   double eps;
   uint32_t load_pct, max_log2, pass_serial;
   uint64_t fail_tag;
+  // optional phase-only fused run after the run (nwords == 0: none), walked on
+  // every output before it is stored; fused_gates counts its gates
+  const OpWord* words;
+  const double* ftab;
+  uint32_t nwords, fused_gates, has_phase;
 };
 int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                     unsigned long long* itab, uint32_t epoch, uint32_t force, const AmpLaunch& l,

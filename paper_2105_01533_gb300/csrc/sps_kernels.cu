@@ -41,6 +41,7 @@ struct FusedArgs {
   const uint4* words;
   const double2* ftab;   // fire-slot tables (read through L1; a few entries per label)
   uint32_t nwords, ngates, has_perm, has_phase, mg;
+  uint32_t fallback;     // 1: skip if an amplitude-only attempt took the pass
 };
 
 // E labels per thread (E consecutive block-wide slices of the state): the E
@@ -50,11 +51,12 @@ template <int KW, int E>
 __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedArgs a,
                                                unsigned long long* plog) {
   const uint64_t n = ctl->nnz;
+  const bool skip = amp_took(ctl, a.fallback);
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
-    plog[0] = n;
+    plog[0] = skip ? 0ull : n;
     plog[1] = n;
   }
-  if (ctl->status != 0u) return;
+  if (ctl->status != 0u || skip) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->updates += n * a.ngates;
     if (a.has_perm) reset_label_masks(ctl, mg_rs(a.mg));
@@ -119,8 +121,8 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedA
 }
 
 // A fused run whose gates all resolved on the host still counts its updates.
-__global__ void k_count_updates(Ctl* ctl, uint32_t ngates) {
-  if (ctl->status == 0u) ctl->updates += ctl->nnz * ngates;
+__global__ void k_count_updates(Ctl* ctl, uint32_t ngates, uint32_t fallback) {
+  if (ctl->status == 0u && !amp_took(ctl, fallback)) ctl->updates += ctl->nnz * ngates;
 }
 
 // ---------------------------------------------------------------------------
@@ -172,6 +174,7 @@ struct BsArgs {
   uint32_t has_perm, has_phase, has_cnt, list_len;
   uint32_t groups;   // groups of 32 entries per warp tile (even, 2..32)
   uint32_t mg;       // label-mask buffers (MaskRing)
+  uint32_t fallback; // 1: skip if an amplitude-only attempt took the pass
 };
 
 template <int KW>
@@ -185,11 +188,12 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
   uint32_t* splanes =
       reinterpret_cast<uint32_t*>(smem + ((16 * a.nops + 4096 * a.nchunks + a.list_len + 15) & ~15u));
   const uint64_t n = ctl->nnz;
+  const bool skip = amp_took(ctl, a.fallback);
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
-    plog[0] = n;
+    plog[0] = skip ? 0ull : n;
     plog[1] = n;
   }
-  if (ctl->status != 0u) return;
+  if (ctl->status != 0u || skip) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->updates += n * a.ngates;
     if (a.has_perm) reset_label_masks(ctl, mg_rs(a.mg));
@@ -816,6 +820,7 @@ int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uin
   a.has_phase = b.has_phase;
   a.has_cnt = b.has_cnt;
   a.list_len = b.list_len;
+  a.fallback = b.fallback;
   const int sms = sm_count(lc);
   const size_t fixed = bs_smem_fixed(b);
   const size_t rows = 32 * (size_t)(b.nw + b.na) + 1;
@@ -873,12 +878,13 @@ int launch_table_clear(const LaunchCfg& lc, Slot* table, uint64_t nslots) {
 
 int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const Pass& p,
                  const OpWord* words, const double* ftab, uint64_t nnz_bound, uint32_t mg,
-                 int lanes, unsigned long long* plog) {
+                 int lanes, uint32_t fallback, unsigned long long* plog) {
   if (p.ops.empty()) {   // every gate resolved on the host: only the update count
-    k_count_updates<<<1, 1, 0, (cudaStream_t)lc.stream>>>(ctl, p.ngates);
+    k_count_updates<<<1, 1, 0, (cudaStream_t)lc.stream>>>(ctl, p.ngates, fallback);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
   }
   FusedArgs a;
+  a.fallback = fallback;
   a.words = reinterpret_cast<const uint4*>(words);
   a.ftab = reinterpret_cast<const double2*>(ftab);
   a.nwords = (uint32_t)p.words.size();
