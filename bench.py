@@ -244,7 +244,8 @@ def roofline(records, workload: str):
         b["ms"] += r["ms"]
         b["bytes"] += algorithmic_bytes(r)
         b["n"] += 1
-        b["entries"] += r["n_out"] if r["kind"] == 3 else r["n_in"]
+        # entries a launch processes: outputs for a compaction or an expansion
+        b["entries"] += r["n_out"] if r["kind"] in (3, 7) else r["n_in"]
     total = sum(b["ms"] for b in by.values()) or 1.0
     kind = max(by, key=lambda k: by[k]["ms"])
     b = by[kind]
