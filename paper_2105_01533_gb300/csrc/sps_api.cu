@@ -55,6 +55,8 @@ struct ApplyPlan {
                                     // here (ends there) with one amplitude-only attempt
   std::vector<uint8_t> amp_walk;    // run start: the phase-only fused pass after the run is
                                     // walked by the attempt (and is its fallback)
+  std::vector<std::vector<uint64_t>> amp_par;   // run start: that pass as sign conditions
+                                                // (c0, c1 pairs) when it holds only signs
   std::vector<unsigned char> image;
 };
 
@@ -593,7 +595,8 @@ static sps_status next_epoch(sps_state* s, const LaunchCfg& lc) {
 // launched after it with fallback = 1, run only if it did not take the run.
 static sps_status launch_amp_attempt(sps_state* s, const LaunchCfg& lc, const BranchOp* ops,
                                      uint32_t d, double prune_eps, uint32_t serial, uint64_t tag,
-                                     const Pass* walk, const OpWord* words, const double* ftab) {
+                                     const Pass* walk, const OpWord* words, const double* ftab,
+                                     const std::vector<uint64_t>* par) {
   const sps_status es = next_epoch(s, lc);
   if (es != SPS_OK) return es;
   AmpLaunch l;
@@ -605,7 +608,11 @@ static sps_status launch_amp_attempt(sps_state* s, const LaunchCfg& lc, const Br
   l.max_log2 = s->itab_log2;
   l.pass_serial = serial;
   l.fail_tag = tag;
-  if (walk) {   // the phase-only run after the run, walked on the outputs
+  if (walk && par) {   // the sign-only run after the run, as a parity
+    l.fused_gates = walk->ngates;
+    l.npar = (uint32_t)(par->size() / 2);
+    for (size_t c = 0; c < par->size(); ++c) l.par[c] = (*par)[c];
+  } else if (walk) {   // the phase-only run after the run, walked on the outputs
     l.words = words;
     l.ftab = ftab;
     l.nwords = (uint32_t)walk->words.size();
@@ -828,20 +835,49 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
       i = j;
     }
   }
-  // (not a run long enough, on a state large enough, for the bit-sliced form:
-  // there the separate bit-sliced pass is faster than walking each output)
+  // A run long enough, on a state large enough, for the bit-sliced form is
+  // faster as that separate pass than walked on each output, unless it holds
+  // only signs (Z and controlled Z: pi steps, no selector, no flip, no
+  // arbitrary phase): then the attempt applies it as a parity of conditions.
   P->amp_walk.assign(np, 0);
+  P->amp_par.assign(np, std::vector<uint64_t>());
   std::vector<uint8_t> amp_walked(np, 0);   // fused passes walked by an attempt
   for (size_t i = 0; i < np; ++i) {
     const size_t j = P->amp_end[i];
     if (!j || j >= np) continue;
     const Pass& f = passes[j];
+    if (f.kind != PASS_FUSED || f.has_perm || P->seg_end[j]) continue;
     const bool sliced = s->bitslice_min_ops && f.ops.size() >= s->bitslice_min_ops &&
                         P->bound_at[j] >= s->bitslice_min_nnz;
-    if (f.kind == PASS_FUSED && !f.has_perm && !P->seg_end[j] && !sliced) {
+    if (!sliced) {
       P->amp_walk[i] = 1;
       amp_walked[j] = 1;
+      continue;
     }
+    std::vector<uint64_t> par;
+    bool signs = true;
+    for (const FOp& o : f.ops) {
+      if ((o.t[0] | o.t[1]) || o.ph != NO_PH || (o.a0 & 3u) || (o.a1 & 3u)) {
+        signs = false;
+        break;
+      }
+      // sign steps s0, s1 (pi or none) for sel = 0 / 1: the sign flips where
+      // c and (s0 xor (sel and (s0 xor s1))) hold, i.e. the parity of "c" (if
+      // s0) and "c and the selector bit" (if s0 != s1)
+      const bool s0 = (o.a0 & 7u) == 4u;
+      const bool s1 = o.sbit != NO_SEL && (o.a1 & 7u) == 4u;
+      if (s0) {
+        par.push_back(o.c[0]);
+        par.push_back(o.c[1]);
+      }
+      if (o.sbit != NO_SEL && s0 != s1) {
+        uint64_t sb[2] = {0ull, 0ull};
+        sb[o.sbit >> 6] = 1ull << (o.sbit & 63u);
+        par.push_back(o.c[0] | sb[0]);
+        par.push_back(o.c[1] | sb[1]);
+      }
+    }
+    if (signs && par.size() <= 2 * kMaxAmpParity && f.ngates > 0) P->amp_par[i] = std::move(par);
   }
   // 2b. an expansion takes the fused run right after it (outside small runs),
   //    unless that run is long enough and the state large enough for the
@@ -1027,14 +1063,18 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       const Pass* walk = nullptr;
       const OpWord* words = nullptr;
       const double* ftab = nullptr;
+      const std::vector<uint64_t>* par = nullptr;
       if (P.amp_walk[pi]) {
         const size_t j = P.amp_end[pi];
         walk = &passes[j];
         words = reinterpret_cast<const OpWord*>(s->arena + run_off[j]);
         ftab = reinterpret_cast<const double*>(s->arena + ph_off[j]);
+      } else if (!P.amp_par[pi].empty()) {
+        walk = &passes[P.amp_end[pi]];
+        par = &P.amp_par[pi];
       }
       const sps_status as = launch_amp_attempt(s, lc, ops, d, prune_eps, s->pass_serial + 1, tg,
-                                               walk, words, ftab);
+                                               walk, words, ftab, par);
       if (as != SPS_OK) return as;
       amp_run_end = P.amp_end[pi] + (walk ? 1 : 0);
     }

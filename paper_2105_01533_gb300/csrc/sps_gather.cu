@@ -788,14 +788,31 @@ struct AmpArgs {
   const uint4* words;
   const double2* ftab;
   uint32_t nwords, fused_gates, has_phase;
+  // PARITY: a phase run of signs only, as conditions (all bits set) whose
+  // count of holding ones decides the sign (pi steps: 4 + 4 = a full turn)
+  uint64_t par[2 * kMaxAmpParity];
+  uint32_t npar;
 };
 
-// Stores one output of an amplitude-only run (WALK: after the phase run).
-template <int KW, bool WALK>
+constexpr int AMP_PLAIN = 0, AMP_WALK = 1, AMP_PARITY = 2;
+
+// Stores one output of an amplitude-only run (POST: after the phase run that
+// follows it, walked or as a sign parity).
+template <int KW, int POST>
 __device__ __forceinline__ void amp_store(const AmpArgs& a, const uint4* fsm, const SoA& out,
                                           uint64_t j, uint64_t k0, uint64_t k1, double re,
                                           double im) {
-  if (WALK) {
+  if (POST == AMP_PARITY) {
+    uint32_t odd = 0u;
+    for (uint32_t c = 0; c < a.npar; ++c)
+      odd ^= ((k0 & a.par[2 * c]) == a.par[2 * c] && (k1 & a.par[2 * c + 1]) == a.par[2 * c + 1])
+                 ? 1u : 0u;
+    if (odd) {   // times e^{i pi}, as apply_pi4 multiplies it
+      re = -re;
+      im = -im;
+    }
+  }
+  if (POST == AMP_WALK) {
     uint64_t l0 = k0, l1 = k1;   // a phase-only run leaves the label as it is
     uint32_t cnt = 0;
     uint64_t fire = 0ull;
@@ -923,7 +940,7 @@ __device__ __forceinline__ uint32_t nth_bit(uint32_t act, uint32_t b) {
 constexpr uint32_t kAmpQueue = 256;   // >= threads per block
 constexpr uint32_t kAmpWide = 4;      // most active gates of a group (16 members)
 
-template <int KW, bool REAL, bool WALK>
+template <int KW, bool REAL, int POST>
 __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
                                                    const unsigned long long* itab,
                                                    const __grid_constant__ AmpArgs a,
@@ -931,9 +948,9 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
   __shared__ uint32_t q1[kAmpQueue], q2[kAmpQueue];   // writers' entry indices
   __shared__ uint32_t a1[kAmpQueue], a2[kAmpQueue];   // and their active gates
   __shared__ unsigned n1, n2;
-  extern __shared__ uint4 fsm[];                      // WALK: the phase run's op stream
+  extern __shared__ uint4 fsm[];                      // AMP_WALK: the phase run's op stream
   const bool go = ctl->amp_go != 0u;
-  if (WALK && go) {
+  if (POST == AMP_WALK && go) {
     for (uint32_t w = threadIdx.x; w < a.nwords; w += blockDim.x) fsm[w] = a.words[w];
     __syncthreads();
   }
@@ -969,7 +986,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
         if (act == 0u) {   // every gate only prunes this entry
           const double re = s.re[i], im = s.im[i];
           bad = !keep_amp(re, im, a.eps2, eps_bits);
-          amp_store<KW, WALK>(a, fsm, out, i, k0, k1, re, im);
+          amp_store<KW, POST>(a, fsm, out, i, k0, k1, re, im);
           ++written;
         } else if (__popc(act) > kAmpWide) {
           bad = true;
@@ -1020,8 +1037,8 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
           bad = true;
           continue;
         }
-        amp_store<KW, WALK>(a, fsm, out, j0, k0, k1, n0r, n0i);
-        amp_store<KW, WALK>(a, fsm, out, j1, p0, p1, n1r, n1i);
+        amp_store<KW, POST>(a, fsm, out, j0, k0, k1, n0r, n0i);
+        amp_store<KW, POST>(a, fsm, out, j1, p0, p1, n1r, n1i);
         written += 2;
       }
       // 3. groups of 4..16: 16 lanes each, lane u = member u (every lane of
@@ -1070,7 +1087,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
           }
         }
         if (mine && jx != ~0ull) {
-          amp_store<KW, WALK>(a, fsm, out, jx, l0, l1, re, im);
+          amp_store<KW, POST>(a, fsm, out, jx, l0, l1, re, im);
           ++written;
         }
       }
@@ -1092,7 +1109,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
       if (took) {
         ctl->cur = cur ^ 1u;
         // no entry appears or goes between the gates (nor in the phase run)
-        ctl->updates += n * (a.d + (WALK ? a.fused_gates : 0u));
+        ctl->updates += n * (a.d + (POST != AMP_PLAIN ? a.fused_gates : 0u));
         ctl->amp_state = 1u;
         ctl->amp_streak = 0u;
       } else if (go) {
@@ -1153,20 +1170,20 @@ int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-template <int KW, bool WALK>
+template <int KW, int POST>
 static void amp_go(bool real, int blocks, int threads, size_t smem, cudaStream_t st, Ctl* ctl,
                    Bufs bufs, const unsigned long long* itab, const AmpArgs& a,
                    unsigned long long* plog) {
   if (real) {
-    if (WALK)
-      cudaFuncSetAttribute(k_amp_layer<KW, true, WALK>,
+    if (POST == AMP_WALK)
+      cudaFuncSetAttribute(k_amp_layer<KW, true, POST>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_amp_layer<KW, true, WALK><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
+    k_amp_layer<KW, true, POST><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
   } else {
-    if (WALK)
-      cudaFuncSetAttribute(k_amp_layer<KW, false, WALK>,
+    if (POST == AMP_WALK)
+      cudaFuncSetAttribute(k_amp_layer<KW, false, POST>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_amp_layer<KW, false, WALK><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
+    k_amp_layer<KW, false, POST><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
   }
 }
 
@@ -1190,6 +1207,8 @@ int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   a.nwords = l.nwords;
   a.fused_gates = l.fused_gates;
   a.has_phase = l.has_phase;
+  a.npar = l.npar;
+  for (uint32_t c = 0; c < 2 * l.npar; ++c) a.par[c] = l.par[c];
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {
@@ -1200,14 +1219,17 @@ int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   } else {
     bool real = true;
     for (uint32_t j = 0; j < l.d; ++j) real = real && l.ops[j].real_m && !l.ops[j].pauli;
-    const bool walk = l.fused_gates > 0;   // (a run with no ops left only counts)
-    const size_t smem = 16 * (size_t)l.nwords;
+    // (a phase run with no ops left only counts its gates: a walk of no words)
+    const int post = l.npar ? AMP_PARITY : l.fused_gates ? AMP_WALK : AMP_PLAIN;
+    const size_t smem = post == AMP_WALK ? 16 * (size_t)l.nwords : 0;
     if (key_words == 1) {
-      if (walk) amp_go<1, true>(real, blocks, lc.threads, smem, st, ctl, bufs, itab, a, plog);
-      else amp_go<1, false>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
+      if (post == AMP_PARITY) amp_go<1, AMP_PARITY>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
+      else if (post == AMP_WALK) amp_go<1, AMP_WALK>(real, blocks, lc.threads, smem, st, ctl, bufs, itab, a, plog);
+      else amp_go<1, AMP_PLAIN>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
     } else {
-      if (walk) amp_go<2, true>(real, blocks, lc.threads, smem, st, ctl, bufs, itab, a, plog);
-      else amp_go<2, false>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
+      if (post == AMP_PARITY) amp_go<2, AMP_PARITY>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
+      else if (post == AMP_WALK) amp_go<2, AMP_WALK>(real, blocks, lc.threads, smem, st, ctl, bufs, itab, a, plog);
+      else amp_go<2, AMP_PLAIN>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
     }
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

@@ -147,6 +147,8 @@ enum PassKind : uint32_t { PASS_FUSED = 1, PASS_BRANCH = 2, PASS_EXPAND = 3, PAS
 constexpr uint32_t kMaxLayerGates = 4;
 // Most gates of one amplitude-only run (disjoint qubits; see launch_amp_part).
 constexpr uint32_t kMaxAmpGates = 32;
+// Most sign conditions of a sign-only phase run an attempt applies by parity.
+constexpr uint32_t kMaxAmpParity = 64;
 
 // Qubits known (on the host, conservatively) to hold one value in every stored
 // label: bit q of known set => every label has bit q = bit q of val.
@@ -401,6 +403,10 @@ struct AmpLaunch {
   const OpWord* words;
   const double* ftab;
   uint32_t nwords, fused_gates, has_phase;
+  // or (npar > 0) a phase run of signs only: the amplitude is negated where an
+  // odd number of the npar conditions (c0, c1 pairs: all bits set) hold
+  uint64_t par[2 * kMaxAmpParity];
+  uint32_t npar;
 };
 int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                     unsigned long long* itab, uint32_t epoch, uint32_t force, const AmpLaunch& l,

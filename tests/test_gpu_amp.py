@@ -187,3 +187,29 @@ def test_uploaded_state_and_option_values():
         with pytest.raises(sps.SpsError):
             st.set_option(sps.SPS_OPT_AMP_ONLY, v)
     st.close()
+
+
+@pytest.mark.parametrize("phases", ["cz", "cz+t"])
+def test_sign_runs_taken_by_parity(phases):
+    """With the bit-sliced form chosen for every phase run (thresholds at
+    their minimum), a run of Z and controlled-Z gates after an amplitude-only
+    run is applied by it as a parity of conditions; a run with a T gate is not
+    (it stays a bit-sliced pass of its own). Both equal the passes without the
+    amplitude-only form bit for bit."""
+    n, modes = 20, 3
+    g = W.givens_workload(seed=9, nqubits=n, modes=modes, layers=16)
+    parts = [g[:modes]]
+    rng = W.SplitMix64(77)
+    for i in range(modes, len(g), n):
+        layer = [tuple(r) for r in g[i:i + n]]
+        if phases == "cz+t":
+            layer.append(W.T(rng.below(n)))
+        layer += [W.Z(rng.below(n))]
+        parts.append(layer)
+    opts = [(sps.SPS_OPT_BITSLICE_MIN_NNZ, 1), (sps.SPS_OPT_BITSLICE_MIN_OPS, 1),
+            (sps.SPS_OPT_SMALL_RUN_CAP, 0)]
+    got, upd, took = run(n, parts, 1e-14, 1 << 12, 1, opts)
+    ref, upd0, _ = run(n, parts, 1e-14, 1 << 12, 0, opts)
+    identical(got, ref)
+    assert upd == upd0 and took > 0
+    compare_states(got, oracle(n, parts, 1e-14), 1e-14)
