@@ -1,0 +1,68 @@
+"""Host logic of bench.py that shapes the reported numbers (no GPU): the
+algorithmic bytes credited per launch, the roofline object built from profile
+records, and the DRAM traffic taken from the committed ncu record, which must
+be ignored once the kernel sources no longer match the capture."""
+
+import importlib.util
+import json
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def rec(kind, n_in, n_out, flags=3, lb=16, ms=1.0):
+    return {"kind": kind, "n_in": n_in, "n_out": n_out, "flags": flags, "label_bytes": lb, "ms": ms,
+            "nops": 1, "pass": 1}
+
+
+def test_algorithmic_bytes_per_kind(bench):
+    # fused pass: read the label, write it back if it permutes, amplitude r+w if phases
+    assert bench.algorithmic_bytes(rec(1, 100, 100, flags=3)) == (16 + 16 + 32) * 100
+    assert bench.algorithmic_bytes(rec(1, 100, 100, flags=2)) == (16 + 32) * 100
+    assert bench.algorithmic_bytes(rec(1, 100, 100, flags=1, lb=8)) == (8 + 8) * 100
+    # expansion, gather emit, amplitude-only run: read the old state, write the new
+    for k in (6, 7, 10):
+        assert bench.algorithmic_bytes(rec(k, 10, 40)) == (16 + 16) * 50
+    # index builds read labels only
+    for k in (5, 9):
+        assert bench.algorithmic_bytes(rec(k, 10, 0, lb=8)) == 8 * 10
+
+
+def test_traffic_record_is_used_only_for_matching_sources(bench, tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ncu_traffic.json").write_text(json.dumps(
+        {"k_amp_layer": {"givens64": {"source_hash": h, "dram_bytes_per_entry": 2.0}},
+         "k_fused": {"adder67-w24": {"source_hash": "0" * 16, "dram_bytes_per_entry": 9.0}}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the hash is of the kernel sources under ROOT: point it back at the repository's
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    assert bench.ncu_traffic("k_amp_layer", "givens64", 1000) == 2000.0
+    assert bench.ncu_traffic("k_fused", "adder67-w24", 1000) is None      # stale capture
+    assert bench.ncu_traffic("k_expand", "adder67", 1000) is None         # none recorded
+
+
+def test_roofline_picks_the_dominant_kernel_and_scales_traffic(bench, monkeypatch):
+    monkeypatch.setattr(bench, "measured_peaks", lambda: (6000.0, "measured"))
+    monkeypatch.setattr(bench, "ncu_traffic",
+                        lambda k, w, n: 3.0 * n if (k, w) == ("k_expand", "adder67") else None)
+    recs = [rec(7, 1, 65536, ms=0.02), rec(7, 1, 65536, ms=0.022), rec(8, 65536, 65536, ms=0.001)]
+    r = bench.roofline(recs, "adder67")
+    assert r["kernel"] == "k_expand"
+    # two launches of (16 + 16) * (1 + 65536) bytes in 0.042 ms in all
+    want = 32 * 65537 / (0.021e-3) / 1e9
+    assert abs(r["achieved"] - round(want, 2)) < 0.01
+    assert abs(r["frac"] - round(want / 6000.0, 4)) < 1e-4
+    assert r["traffic"] == 3.0 * 65536      # expansions count their outputs
+    assert set(r["time_share"]) == {"k_expand", "k_measure"}
