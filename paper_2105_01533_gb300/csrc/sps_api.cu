@@ -95,6 +95,7 @@ struct sps_state {
   int fused_labels = 0;                  // SPS_OPT_FUSED_LABELS (0: by size)
   bool amp = true;                       // SPS_OPT_AMP_ONLY
   bool amp_force = true;                 // the label index must be rebuilt before use
+  bool reset_pending = false;            // sps_reset not yet enqueued (see flush_reset)
   int branch_form = 0;               // 0 auto (gather), 1 scatter, 2 gather
   double* partials = nullptr;
   double* dresult = nullptr;
@@ -234,7 +235,21 @@ sps_status cuda_ok(cudaError_t e) {
 }
 
 // Reads the control block after the stream drains.
+// sps_reset only records the reset: the next apply that starts with an
+// expansion pass builds its outputs from |0...0> itself (one launch fewer per
+// reset-apply cycle); any other use of the state enqueues the reset first.
+sps_status flush_reset(sps_state* s) {
+  if (!s->reset_pending) return SPS_OK;
+  s->reset_pending = false;
+  if (launch_reset_state(s->stream, s->kw, s->ctl, s->bufs, s->masks.writer()) < 0)
+    return cuda_ok(cudaGetLastError());
+  s->counters.kernel_launches += 1;
+  return SPS_OK;
+}
+
 sps_status read_ctl(sps_state* s) {
+  const sps_status fs = flush_reset(s);
+  if (fs != SPS_OK) return fs;
   if (cudaMemcpyAsync(s->ctl_host, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream) !=
       cudaSuccess)
     return cuda_ok(cudaGetLastError());
@@ -514,9 +529,7 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
 sps_status sps_reset(sps_state* s) {
   if (!s) return SPS_ERR_ARG;
   s->amp_force = true;
-  if (launch_reset_state(s->stream, s->kw, s->ctl, s->bufs, s->masks.writer()) < 0)
-    return cuda_ok(cudaGetLastError());
-  s->counters.kernel_launches += 1;
+  s->reset_pending = true;   // enqueued by the next use of the state (flush_reset)
   s->nnz_bound = 1;
   know_all_zero(s);
   return SPS_OK;
@@ -1027,6 +1040,17 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   const uint32_t serial_base = s->pass_serial;
   ++s->apply_serial;
   size_t amp_run_end = 0;   // passes before this index belong to an attempted run
+  // a pending reset is taken by a leading expansion pass, else enqueued now
+  bool from_reset = false;
+  if (s->reset_pending) {
+    if (!passes.empty() && passes[0].kind == PASS_EXPAND && !seg_end[0]) {
+      from_reset = true;
+      s->reset_pending = false;
+    } else {
+      const sps_status fs = flush_reset(s);
+      if (fs != SPS_OK) return fs;
+    }
+  }
   for (size_t pi = 0; pi < passes.size(); ++pi) {
     const Pass& p = passes[pi];
     if (seg_end[pi]) {
@@ -1098,6 +1122,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       e.nwords = 0;
       e.fused_gates = 0;
       e.has_phase = 0;
+      e.from_reset = from_reset && pi == 0 ? 1u : 0u;
       const bool walk = P.walk_next[pi] != 0;
       if (walk) {   // the fused run after the expansion, applied before the stores
         const Pass& f = passes[pi + 1];
@@ -1332,13 +1357,21 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
   return know_from_device(s);
 }
 
+// Blocks of a probability readout: about 1,024 entries each (the last block
+// adds the block sums in block order, so fewer blocks mean a shorter tail),
+// at most prob_blocks.
+static int prob_grid(const sps_state* s) {
+  const uint64_t b = (s->nnz_bound + 1023) / 1024;
+  return b < 1 ? 1 : b > (uint64_t)s->prob_blocks ? s->prob_blocks : (int)b;
+}
+
 sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t value[2], double* p) {
   if (!s || !mask || !value || !p) return SPS_ERR_ARG;
   sps_status st = sps_sync(s, nullptr);
   if (st != SPS_OK) return st;
   const LaunchCfg lc = cfg_of(s);
   if (launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0], value[1],
-                         s->partials, s->prob_blocks, s->dresult) < 0)
+                         s->partials, prob_grid(s), s->dresult) < 0)
     return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 1;
   if (cudaMemcpyAsync(s->hresult, s->dresult, sizeof(double), cudaMemcpyDeviceToHost, s->stream) !=
@@ -1353,9 +1386,11 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
 sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
                                  double* out) {
   if (!s || !mask || !value || !out) return SPS_ERR_ARG;
+  const sps_status fs = flush_reset(s);
+  if (fs != SPS_OK) return fs;
   const LaunchCfg lc = cfg_of(s);
   if (launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0], value[1],
-                         s->partials, s->prob_blocks, s->dresult) < 0)
+                         s->partials, prob_grid(s), s->dresult) < 0)
     return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 1;
   if (cudaMemcpyAsync(out, s->dresult, sizeof(double), cudaMemcpyDefault, s->stream) != cudaSuccess)
@@ -1371,6 +1406,8 @@ sps_status sps_pauli_exp(sps_state* s, const uint64_t x[2], const uint64_t z[2],
   for (int w = 0; w < 2; ++w)
     if (((x[w] | z[w] | cmask[w]) & ~lim[w]) || (cmask[w] & (x[w] | z[w]))) return SPS_ERR_ARG;
   if ((x[0] | x[1] | z[0] | z[1]) == 0) return SPS_ERR_ARG;
+  const sps_status fs = flush_reset(s);
+  if (fs != SPS_OK) return fs;
   if ((x[0] | x[1]) == 0) {
     // A string of Z factors is diagonal: exp(-i t/2 P) multiplies a label by
     // e^(-i t/2) or e^(i t/2) as the parity of its z bits is 0 or 1. A ladder of
@@ -1438,6 +1475,8 @@ sps_status sps_pauli_exp(sps_state* s, const uint64_t x[2], const uint64_t z[2],
 
 sps_status sps_measure(sps_state* s, uint32_t qubit, double r, double* out) {
   if (!s || !out || qubit >= s->nqubits || !(r >= 0.0 && r < 1.0)) return SPS_ERR_ARG;
+  const sps_status fs = flush_reset(s);
+  if (fs != SPS_OK) return fs;
   const LaunchCfg lc = cfg_of(s);
   const uint32_t serial = ++s->pass_serial;
   s->amp_force = true;   // the collapse moves labels

@@ -290,6 +290,11 @@ struct ExpandArgs {
   const uint4* words;
   const double2* ftab;
   uint32_t nwords, fused_gates, has_phase;
+  // 1: the input is |0...0> from a reset not yet enqueued: no entry is read, and
+  // the last block does the reset's work on the control block (clears the
+  // status, the failure record and the update count; on a capacity failure it
+  // leaves |0...0> as the state)
+  uint32_t from_reset;
 };
 
 // (re, im) *= f; a real factor leaves an exactly zero imaginary part at zero
@@ -310,9 +315,10 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const __gri
   __shared__ double2 sf[3 * 256];
   __shared__ ulonglong2 sm[3 * 256];
   extern __shared__ uint4 fsm[];   // WALK: the op stream
-  if (ctl->status != 0u) return;
-  const uint64_t n = ctl->nnz;
-  const unsigned cur = ctl->cur;
+  const bool rst = a.from_reset != 0u;
+  if (!rst && ctl->status != 0u) return;
+  const uint64_t n = rst ? 1ull : ctl->nnz;
+  const unsigned cur = rst ? 0u : ctl->cur;
   const SoA s = pick(bufs, cur);
   const SoA out = pick(bufs, cur ^ 1u);
   if (blockIdx.x == 0 && threadIdx.x == 0) reset_label_masks(ctl, mg_rs(a.mg));
@@ -340,10 +346,10 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const __gri
     if (wide) {   // the span's input and its choices above the first 8 gates
       const uint64_t i = t0 >> a.d;
       const uint32_t c = (uint32_t)(t0 & cmask);
-      h0 = s.lo[i];
-      h1 = KW == 2 ? s.hi[i] : 0ull;
-      hr = s.re[i];
-      hi = s.im[i];
+      h0 = rst ? 0ull : s.lo[i];
+      h1 = (KW == 2 && !rst) ? s.hi[i] : 0ull;
+      hr = rst ? 1.0 : s.re[i];
+      hi = rst ? 0.0 : s.im[i];
       for (uint32_t ch = 1; ch < a.chunks; ++ch) {
         const uint32_t u = ch * 256u + ((c >> (8u * ch)) & 0xFFu);
         h0 ^= sm[u].x;
@@ -372,10 +378,10 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const __gri
         } else {
           const uint64_t i = t >> a.d;
           c0 = (uint32_t)(t & cmask);
-          l0 = s.lo[i];
-          l1 = KW == 2 ? s.hi[i] : 0ull;
-          vr = s.re[i];
-          vi = s.im[i];
+          l0 = rst ? 0ull : s.lo[i];
+          l1 = (KW == 2 && !rst) ? s.hi[i] : 0ull;
+          vr = rst ? 1.0 : s.re[i];
+          vi = rst ? 0.0 : s.im[i];
         }
         l0 ^= sm[c0].x;
         l1 ^= sm[c0].y;
@@ -440,9 +446,23 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const __gri
       __threadfence();
       const unsigned long long got = atomicAdd(&ctl->out_count, 0ull);
       bool published = false;
+      if (rst) {   // the reset's work: a clean status, no failure, no updates yet
+        ctl->status = 0u;
+        ctl->fail_pass = 0u;
+        ctl->fail_gate = 0ull;
+        ctl->updates = 0ull;
+      }
       if (ctl->status == 0u) {
         if (got > a.capacity) {
           fail(ctl, SPS_ERR_CAPACITY, a.pass_serial, a.fail_tag);
+          if (rst) {   // the state before the pass: |0...0> in buffer 0
+            s.lo[0] = 0ull;
+            if (KW == 2) s.hi[0] = 0ull;
+            s.re[0] = 1.0;
+            s.im[0] = 0.0;
+            ctl->nnz = 1ull;
+            ctl->cur = 0u;
+          }
         } else {
           ctl->nnz = got;
           ctl->cur = cur ^ 1u;
@@ -1314,6 +1334,7 @@ int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const
   a.nwords = e.nwords;
   a.fused_gates = e.fused_gates;
   a.has_phase = e.has_phase;
+  a.from_reset = e.from_reset;
   const bool walk = e.nwords > 0;
   const uint64_t total = nnz_bound << e.d;
   // Outputs per lane: 8 without a walk; with one, as many as still leave about

@@ -423,6 +423,9 @@ struct ExpandLaunch {
   const OpWord* words;
   const double* ftab;
   uint32_t nwords, fused_gates, has_phase;
+  // 1: the input is |0...0> (a reset not yet enqueued): the kernel does the
+  // reset's work on the control block and reads no entry
+  uint32_t from_reset;
 };
 int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const ExpandLaunch& e,
                   uint64_t nnz_bound, unsigned long long* plog);
