@@ -103,8 +103,12 @@ sps_status sps_set_allocator(sps_alloc_fn alloc, sps_free_fn release, void* ctx)
 sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream,
                       sps_state** out);
 
-/* Enqueues a reset to |0...0> on the state's stream (no host wait). Also
- * clears a pending device-side error. */
+/* Resets the state to |0...0> (no host wait). Also clears a pending
+ * device-side error. The reset is recorded and carried out by the next call
+ * that uses the state, in stream order: an sps_apply whose first pass is an
+ * expansion (SPS_OPT_EXPAND) starts from |0...0> in that pass's own launch
+ * (if that pass fails, the state is |0...0>); any other call enqueues the
+ * reset first. */
 sps_status sps_reset(sps_state* s);
 
 /* Frees the state's device memory (after its stream's pending work). NULL ok. */
