@@ -14,5 +14,6 @@ from .oracle import (  # noqa: F401
     OracleState,
     dense_run,
     classical_eval,
+    sector_run,
     lib_path,
 )

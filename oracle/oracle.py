@@ -75,6 +75,10 @@ def _load():
     lib.orc_dense_run.restype = i32
     lib.orc_classical_eval.argtypes = [u32, vp, u64, vp, vp, u64, pu64]
     lib.orc_classical_eval.restype = i32
+    lib.orc_sector_size.argtypes = [u32, u64]
+    lib.orc_sector_size.restype = u64
+    lib.orc_sector_run.argtypes = [u32, u64, vp, u64, vp, vp, vp, u64, pu64]
+    lib.orc_sector_run.restype = i32
     _lib = lib
     return lib
 
@@ -194,3 +198,26 @@ def classical_eval(nqubits: int, gates, hi, lo):
     if rc != 0:
         raise ValueError("classical_eval: record %d is not a valid X gate" % bad.value)
     return hi, lo
+
+
+def sector_run(nqubits: int, start: int, gates):
+    """Dense simulation inside the weight sector of the basis state |start>
+    (n <= 64): every label of that Hamming weight in increasing order and its
+    amplitude (complex128, zeros included). Only Givens and diagonal gates
+    (which conserve the weight) are accepted."""
+    lib = _load()
+    g = _gate_buffer(gates)
+    size = int(lib.orc_sector_size(nqubits, start))
+    if size == 0:
+        raise ValueError("sector_run: n out of range")
+    labels = np.empty(size, np.uint64)
+    re = np.empty(size, np.float64)
+    im = np.empty(size, np.float64)
+    bad = ctypes.c_uint64(0)
+    rc = lib.orc_sector_run(nqubits, start, _ptr(g), g.size, _ptr(labels), _ptr(re), _ptr(im),
+                            size, ctypes.byref(bad))
+    if rc == 1:
+        raise ValueError("sector_run: record %d is invalid or leaves the sector" % bad.value)
+    if rc != 0:
+        raise ValueError("sector_run: bad size or start label")
+    return labels, re + 1j * im

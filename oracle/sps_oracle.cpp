@@ -36,7 +36,10 @@
 // Also here, as independent checkers for the pins:
 //   * a dense 2^n Schroedinger statevector simulator (Sec. 2.2), n <= 26;
 //   * a classical evaluator for permutation-only circuits: a key is pushed
-//     through X/CNOT/Toffoli/MCX gates one at a time.
+//     through X/CNOT/Toffoli/MCX gates one at a time;
+//   * a dense simulator restricted to one Hamming-weight sector (every label
+//     with k bits set, ranked by the combinatorial number system) for
+//     number-conserving circuits (Givens and diagonal gates), n <= 64.
 
 #include <cmath>
 #include <complex>
@@ -553,6 +556,134 @@ int orc_classical_eval(uint32_t n, const void* gates, uint64_t ngates, uint64_t*
     }
     lo[i] = k.lo;
     hi[i] = k.hi;
+  }
+  return 0;
+}
+
+}  // extern "C"
+
+// ---- dense simulator on a fixed-weight sector ---------------------------------
+// Gates that conserve the number of set bits (Givens, and the diagonal gates
+// Z, S, Sdg, T, Tdg, P, Rz with any controls) keep a state inside the span of
+// the C(n, k) labels of weight k. This checker holds ALL of them as a dense
+// vector, one amplitude per label, indexed by the combinatorial number system
+// (colex rank: for set bits c_1 < ... < c_k the index is sum_i C(c_i, i)).
+// Gosper's successor enumerates the labels in increasing order, which is the
+// same order, so label[rank] is filled by counting. No pruning, no map: a
+// pair (i, j) of a Givens gate is found by ranking the partner label.
+// The arithmetic of each amplitude is the same as the sparse simulator's
+// (the same complex products and sums, in the same order), so without pruning
+// the two agree bit for bit. n <= 64 (labels in one word).
+namespace {
+uint64_t binom_tab[65][65];
+bool binom_ready = false;
+void binom_init() {
+  if (binom_ready) return;
+  for (int a = 0; a <= 64; ++a) {
+    binom_tab[a][0] = 1;
+    for (int b = 1; b <= 64; ++b)
+      binom_tab[a][b] = a == 0 ? 0 : binom_tab[a - 1][b - 1] + binom_tab[a - 1][b];
+  }
+  binom_ready = true;
+}
+uint64_t colex_rank(uint64_t label) {
+  uint64_t r = 0;
+  int i = 1;
+  while (label) {
+    const int c = __builtin_ctzll(label);
+    r += binom_tab[c][i];
+    ++i;
+    label &= label - 1;
+  }
+  return r;
+}
+bool sector_gate_ok(const GateRec& g) {
+  switch (g.op) {
+    case OP_GIVENS: case OP_Z: case OP_S: case OP_SDG: case OP_T: case OP_TDG:
+    case OP_P: case OP_RZ:
+      return true;
+    default:
+      return false;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+// Number of labels of the sector of `start` on n qubits (C(n, popcount)).
+uint64_t orc_sector_size(uint32_t n, uint64_t start) {
+  binom_init();
+  if (n < 1 || n > 64) return 0;
+  return binom_tab[n][__builtin_popcountll(start)];
+}
+
+// Runs the gates on |start> inside its weight sector. labels/re/im receive
+// all C(n, k) labels (increasing) and their amplitudes (zeros included).
+// Returns 0, 1 on an invalid record or one that leaves the sector (*bad set),
+// 2 if cap < C(n, k) or n is out of range.
+int orc_sector_run(uint32_t n, uint64_t start, const void* gates, uint64_t ngates,
+                   uint64_t* labels, double* re, double* im, uint64_t cap, uint64_t* bad) {
+  binom_init();
+  if (n < 1 || n > 64) return 2;
+  if (n < 64 && (start >> n) != 0) return 2;
+  const int k = __builtin_popcountll(start);
+  const uint64_t size = binom_tab[n][k];
+  if (cap < size) return 2;
+  const GateRec* gs = static_cast<const GateRec*>(gates);
+  for (uint64_t gi = 0; gi < ngates; ++gi) {
+    if (!valid(gs[gi], n) || !sector_gate_ok(gs[gi]) || gs[gi].cmask[1] != 0) {
+      if (bad) *bad = gi;
+      return 1;
+    }
+  }
+  // labels of weight k in increasing order (Gosper's successor)
+  uint64_t v = k == 0 ? 0ull : (k == 64 ? ~0ull : ((1ull << k) - 1));
+  for (uint64_t r = 0; r < size; ++r) {
+    labels[r] = v;
+    if (r + 1 < size) {
+      const uint64_t t = v | (v - 1);
+      v = (t + 1) | (((~t & -~t) - 1) >> (__builtin_ctzll(v) + 1));
+    }
+  }
+  std::vector<Cplx> a(size, Cplx{0.0, 0.0});
+  a[colex_rank(start)] = Cplx{1.0, 0.0};
+  for (uint64_t gi = 0; gi < ngates; ++gi) {
+    const GateRec& g = gs[gi];
+    const uint64_t cm = g.cmask[0];
+    if (g.op == OP_GIVENS) {
+      Cplx M[2][2];
+      branch_matrix(g, M);
+      const uint64_t pm = 1ull << g.t0, qm = 1ull << g.t1;
+      for (uint64_t r = 0; r < size; ++r) {
+        const uint64_t L = labels[r];
+        // r is the first member of its pair: bit p = 0, bit q = 1
+        if ((L & pm) || !(L & qm) || (L & cm) != cm) continue;
+        const uint64_t j = colex_rank((L | pm) & ~qm);
+        const Cplx a0 = a[r], a1 = a[j];
+        a[r] = cadd(cmul(M[0][0], a0), cmul(M[0][1], a1));
+        a[j] = cadd(cmul(M[1][0], a0), cmul(M[1][1], a1));
+      }
+    } else {
+      // the factor on a label whose controls hold, by its target bit (taken
+      // from the gate's definition once per gate); elsewhere the factor is 1
+      Key same;
+      const Key k0{cm, 0ull};
+      const Key k1{cm | (1ull << g.t0), 0ull};
+      const Cplx f0 = perm_diag_action(g, k0, &same);
+      const Cplx f1 = perm_diag_action(g, k1, &same);
+      const uint64_t tm = 1ull << g.t0;
+      for (uint64_t r = 0; r < size; ++r) {
+        const uint64_t L = labels[r];
+        if ((L & cm) != cm) continue;
+        const Cplx f = (L & tm) ? f1 : f0;
+        if (f.re == 1.0 && f.im == 0.0) continue;   // 1 * a = a
+        a[r] = cmul(f, a[r]);
+      }
+    }
+  }
+  for (uint64_t r = 0; r < size; ++r) {
+    re[r] = a[r].re;
+    im[r] = a[r].im;
   }
   return 0;
 }

@@ -86,3 +86,51 @@ def test_bad_record_is_reported():
     with pytest.raises(sps.SpsError) as e:
         sps.sps_commute(g, 5)
     assert e.value.status == sps.SPS_ERR_ARG and e.value.failed_gate == 1
+
+
+def test_fig1_walkthrough():
+    """Sec. 3.3, Fig. 1, replayed on 8 qubits. Starting queues (black in the
+    figure): phase/permutation queue CNOT(0->3), Z(2), CZ(1,4); H queued on
+    qubits 1..4; Rx(0.75) on qubit 4; Ry(0.6) on qubit 1; Rx(-pi/4) on qubit 6.
+    Steps: (a) H on qubit 0 only sets its H queue; (b) H on qubit 1 flips the
+    queued Ry angle (H Ry(t) = Ry(-t) H) and cancels the queued H (H H = 1);
+    (c) X on qubit 2 adds Z(2) to the phase/permutation queue (X H = H Z);
+    (d) CCNOT(3,4 -> 5) cannot pass the queued Rx on qubit 4 nor the H gates:
+    the whole phase/permutation queue is executed, then H on 3 and 4, then
+    Rx(0.75), and the CCNOT waits in the emptied queue; (e) the Rx(-pi/4) on
+    qubit 6 is never executed by these steps. Each prefix is rewritten by
+    sps_commute (which emits whatever is still queued at the end: the
+    phase/permutation queue, then per qubit H, Rx, Ry) and must compute the
+    same state as the original stream."""
+    n = 8
+    start = [W.CX(0, 3), W.Z(2), W.CZ(1, 4), W.H(1), W.H(2), W.H(3), W.H(4),
+             W.Rx(4, 0.75), W.Ry(1, 0.6), W.Rx(6, -np.pi / 4)]
+    steps = [W.H(0), W.H(1), W.X(2), W.X(5, 3, 4)]
+    CX = (W.OP_X, 3, 1 << 0, 0.0)
+    Z2 = (W.OP_Z, 2, 0, 0.0)
+    CZ = (W.OP_Z, 4, 1 << 1, 0.0)
+    H = lambda q: (W.OP_H, q, 0, 0.0)                         # noqa: E731
+    RX4 = (W.OP_RX, 4, 0, 0.75)
+    RX6 = (W.OP_RX, 6, 0, round(-np.pi / 4, 12))
+    want = {
+        "start": [CX, Z2, CZ, H(1), (W.OP_RY, 1, 0, 0.6), H(2), H(3), H(4), RX4, RX6],
+        "a": [CX, Z2, CZ, H(0), H(1), (W.OP_RY, 1, 0, 0.6), H(2), H(3), H(4), RX4, RX6],
+        "b": [CX, Z2, CZ, H(0), (W.OP_RY, 1, 0, -0.6), H(2), H(3), H(4), RX4, RX6],
+        "c": [CX, Z2, CZ, Z2, H(0), (W.OP_RY, 1, 0, -0.6), H(2), H(3), H(4), RX4, RX6],
+        "d": [CX, Z2, CZ, Z2, H(3), H(4), RX4, (W.OP_X, 5, (1 << 3) | (1 << 4), 0.0),
+              H(0), (W.OP_RY, 1, 0, -0.6), H(2), RX6],
+    }
+    for k, name in enumerate(["start", "a", "b", "c", "d"]):
+        g = W.to_array(start + steps[:k])
+        r = sps.sps_commute(g, n)
+        assert ops(r) == want[name], name
+        a = OracleState(n)
+        a.apply(g)
+        b = OracleState(n)
+        b.apply(r)
+        compare_states(b.get(), a.get(), 0.0)
+    # (d): what ran before the CCNOT is exactly the caption's flush, and (e)
+    # the Rx(-pi/4) on qubit 6 only comes out at the very end
+    d = want["d"]
+    assert d.index((W.OP_X, 5, (1 << 3) | (1 << 4), 0.0)) == 7
+    assert d[-1] == RX6

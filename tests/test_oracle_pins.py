@@ -14,7 +14,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import OracleState, classical_eval, dense_run
+from oracle import OracleState, classical_eval, dense_run, sector_run
 from paper_2105_01533_gb300 import workloads as W
 
 import kron_ref
@@ -192,6 +192,27 @@ def test_prune_threshold_is_strict():
     assert st.nnz() == 1
     st.apply(W.to_array([W.H(0), W.H(0)]), eps=5e-8 * math.sqrt(0.5) * math.sqrt(0.5) * 2)
     assert st.nnz() in (0, 1)
+
+
+def test_prune_keeps_an_entry_at_exactly_eps_squared():
+    """The strict reading: an entry with re^2 + im^2 == eps^2 exactly stays,
+    one an ulp below goes. eps = 2^-20 makes eps^2 = 2^-40 exact, and Ry(0)
+    copies each amplitude unchanged (cos 0 = 1) while its partner gets an
+    exact zero (sin 0 = 0), which always goes."""
+    eps = 2.0 ** -20
+    below = np.nextafter(eps, 0.0)
+    assert below * below < eps * eps
+    st = OracleState(4)
+    st.set([0, 0, 0, 0], [0, 2, 4, 8], [eps, below, 0.0, -eps], [0.0, 0.0, eps, 0.0])
+    st.apply(W.to_array([W.Ry(0, 0.0)]), eps=eps)
+    hi, lo, re, im = st.get()
+    assert lo.tolist() == [0, 4, 8]
+    assert re.tolist() == [eps, 0.0, -eps] and im.tolist() == [0.0, eps, 0.0]
+    # the insert-once mode prunes the same way
+    st = OracleState(4)
+    st.set([0, 0], [0, 2], [eps, below], [0.0, 0.0])
+    st.apply(W.to_array([W.Ry(0, 0.0)]), eps=eps, mode=1)
+    assert st.get()[1].tolist() == [0]
 
 
 # ---- reversible arithmetic ------------------------------------------------------
@@ -407,3 +428,48 @@ def test_pauli_exp_rejects_bad_strings():
                     ((1, 0), (0, 0), (1, 0)), ((0, 0), (1 << 2, 0), (1 << 2, 0))):
         with pytest.raises(ValueError):
             st.pauli_exp(x, z, c, 0.5)
+
+
+# ---- weight-sector dense checker ---------------------------------------------
+def test_sector_labels_are_the_weight_k_set():
+    labels, amp = sector_run(16, 0b1111, W.to_array([]))
+    assert len(labels) == math.comb(16, 4)
+    assert np.all(np.diff(labels.astype(np.int64)) > 0)
+    assert {bin(int(x)).count("1") for x in labels} == {4}
+    assert np.count_nonzero(amp) == 1 and amp[labels == 0b1111][0] == 1.0
+
+
+def test_sector_sim_matches_tensor_simulator():
+    """A number-conserving circuit on 10 qubits, 3 modes: the sector vector
+    embedded in 2^10 equals the n-axis tensor simulator (Sec. 2.2), and the
+    tensor state is exactly zero outside the sector."""
+    n, k = 10, 3
+    gates = W.givens_workload(seed=4, nqubits=n, modes=k, layers=8)
+    gates = np.concatenate([gates, W.to_array([W.Rz(2, 0.7, 5), W.T(4), W.P(1, 1.3, 0)])])
+    labels, amp = sector_run(n, (1 << k) - 1, gates[k:])
+    want = kron_ref.tensor_run(n, gates)
+    np.testing.assert_allclose(amp, want[labels.astype(np.int64)], rtol=0, atol=1e-12)
+    outside = np.ones(1 << n, bool)
+    outside[labels.astype(np.int64)] = False
+    assert np.max(np.abs(want[outside])) < 1e-15
+    assert abs(np.sum(np.abs(amp) ** 2) - 1.0) < 1e-12
+
+
+def test_sector_sim_bit_identical_to_sparse_oracle():
+    """Without pruning the sparse oracle and the sector vector form every
+    amplitude with the same products and sums."""
+    n, k = 24, 3
+    gates = W.givens_workload(seed=5, nqubits=n, modes=k, layers=10)
+    labels, amp = sector_run(n, (1 << k) - 1, gates[k:])
+    hi, lo, re, im = run_oracle(n, gates, eps=0.0).get()
+    nz = amp != 0
+    np.testing.assert_array_equal(lo, labels[nz])
+    np.testing.assert_array_equal(re, amp[nz].real)
+    np.testing.assert_array_equal(im, amp[nz].imag)
+
+
+def test_sector_sim_rejects_weight_changing_gates():
+    with pytest.raises(ValueError):
+        sector_run(8, 0b11, W.to_array([W.H(0)]))
+    with pytest.raises(ValueError):
+        sector_run(8, 0b11, W.to_array([W.X(3)]))
