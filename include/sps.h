@@ -509,19 +509,21 @@ sps_status sps_server_stats(sps_server* s, uint64_t* ticks, uint64_t* launches,
  * receives the count. nqubits (1..127) fixes the label width: for <= 63
  * qubits in_hi/out_hi are ignored and may be NULL. Input labels must be
  * distinct and use only qubits below nqubits.
- * Scratch: a fixed 8 MiB + 64 B array inside the library image (262,144
- * table slots and a control block), held by every GPU that loads the library
- * until the process exits. It allocates nothing: no cudaMalloc, cudaFree or
- * allocating library call. Limit: n_in <= 65,536, else SPS_ERR_CAPACITY
- * before anything is launched.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Scratch: a fixed array inside the library image, 8,391,776 bytes (262,144
+ * table slots of 32 B and a 3,160-byte control block), held by every GPU that
+ * loads the library until the process exits. It allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call. Limit: n_in <= 65,536,
+ * else SPS_ERR_CAPACITY before anything is launched.
+ * Each call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, a host-side query), so a device reset between calls
+ * does not leave a stale address behind.
  * Every call uses the same array and it keeps the last call's contents; each
  * call clears the part it needs first. Calls that overlap on the GPU (on
  * different streams, host threads or processes sharing a context) race on the
  * array and give wrong results: serialise them. The call synchronises
  * `cuda_stream` before returning.
- * Errors: SPS_ERR_ARG (bad gate or pointers), SPS_ERR_CAPACITY (n_in too
+ * Errors: SPS_ERR_ARG (bad gate or pointers, or an out_* array equal to its
+ * in_* counterpart), SPS_ERR_CAPACITY (n_in too
  * large, or more than out_cap entries result; *n_out = 0),
  * SPS_ERR_TABLE_FULL, SPS_ERR_CUDA, SPS_ERR_NO_DEVICE. */
 sps_status sps_branch_apply_static(const sps_gate* gate, uint32_t nqubits,

@@ -9,10 +9,10 @@
 // allocator callback, where allocating again would re-enter the allocator.
 //
 // The array below is part of the library image: every GPU that loads
-// libsps.so holds it (8 MiB + 64 B) until the process exits.
+// libsps.so holds it (8 MiB of table slots plus the 3,160-byte control block,
+// 8,391,776 bytes in all) until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <vector>
 
 #include "sps.h"
@@ -28,35 +28,29 @@ struct StaticScratch {
   Slot table[1u << kStaticTableLog2];
   Ctl ctl;
 };
+// the footprint the header states: keep the two in step
+static_assert(sizeof(Ctl) == 3160, "control block size changed: update sps.h");
+static_assert(sizeof(StaticScratch) == 8391776, "scratch size changed: update sps.h");
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
-constexpr int kMaxDevices = 128;
-std::mutex g_static_mu;
-StaticScratch* g_static_addr[kMaxDevices] = {};
-int g_static_sms[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the symbol itself as a device address).
+// Device address of the scratch array on the current device. Host code cannot
+// use the symbol itself as a device address; the lookup is a host-side query
+// (no stream operation) and is made on every call, so the address stays right
+// if the device's context was reset and the module loaded again elsewhere.
 sps_status static_scratch(int device, StaticScratch** out, int* sms) {
-  if (device < 0 || device >= kMaxDevices) return SPS_ERR_NO_DEVICE;
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_addr[device]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return SPS_ERR_CUDA;
-    }
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
-      cudaGetLastError();
-      return SPS_ERR_CUDA;
-    }
-    g_static_addr[device] = static_cast<StaticScratch*>(p);
-    g_static_sms[device] = n;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return SPS_ERR_CUDA;
   }
-  *out = g_static_addr[device];
-  *sms = g_static_sms[device];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return SPS_ERR_CUDA;
+  }
+  *out = static_cast<StaticScratch*>(p);
+  *sms = n;
   return SPS_OK;
 }
 
@@ -76,6 +70,10 @@ extern "C" sps_status sps_branch_apply_static(
   if (n_in > kStaticMaxInput) return SPS_ERR_CAPACITY;
   if (n_in && (!in_lo || !in_re || !in_im || (kw == 2 && !in_hi))) return SPS_ERR_ARG;
   if (!out_lo || !out_re || !out_im || (kw == 2 && !out_hi)) return SPS_ERR_ARG;
+  // outputs must not alias inputs: the compaction writes while the table
+  // still refers to entries of the input arrays
+  if (out_lo == in_lo || out_re == in_re || out_im == in_im || (kw == 2 && out_hi == in_hi))
+    return SPS_ERR_ARG;
   // the gate must be a single valid two-nonzero gate
   std::vector<Pass> passes;
   size_t bad = 0;

@@ -87,8 +87,7 @@ def test_givens_layers_take_the_amplitude_form(n, modes, layers, lay):
     identical(got, ref)
     assert upd == upd0
     assert took > 0 and took0 == 0
-    if n <= 40:
-        compare_states(got, oracle(n, parts, 1e-14), 1e-14)
+    compare_states(got, oracle(n, parts, 1e-14), 1e-14)
 
 
 @pytest.mark.parametrize("seed", range(3))

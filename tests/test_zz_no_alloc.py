@@ -110,3 +110,36 @@ def test_static_branch_limits(torch):
     n = sps.sps_branch_apply_static(W.to_array([W.H(0)]), 30, (None, lo, re, im), 16, 0.0, out,
                                     64, h)
     assert n == 32
+
+
+def test_static_branch_rejects_aliased_outputs(torch):
+    """Writing the result over the input would corrupt entries the pass still
+    reads: such a call is refused before anything is launched."""
+    h = int(torch.cuda.current_stream().cuda_stream)
+    arrs = device_arrays(torch, 64)
+    with pytest.raises(sps.SpsError) as e:
+        sps.sps_branch_apply_static(W.to_array([W.H(0)]), 30, arrs, 8, 0.0, arrs, 64, h)
+    assert e.value.status == sps.SPS_ERR_ARG
+
+
+def test_static_branch_at_its_input_limit(torch):
+    """Exactly 65,536 distinct inputs under H on a qubit none of them sets:
+    131,072 outputs in a table at its 50% load limit, the same as sps_apply."""
+    h = int(torch.cuda.current_stream().cuda_stream)
+    n_in = 1 << 16
+    eps = 1e-14
+    gate = W.to_array([W.H(0)])
+    lo = (torch.arange(n_in, dtype=torch.int64, device="cuda") << 1)
+    re = torch.full((n_in,), 2.0 ** -8, dtype=torch.float64, device="cuda")
+    im = torch.zeros(n_in, dtype=torch.float64, device="cuda")
+    ins = (torch.zeros(n_in, dtype=torch.int64, device="cuda"), lo, re, im)
+    out = device_arrays(torch, 2 * n_in)
+    n = sps.sps_branch_apply_static(gate, 40, ins, n_in, eps, out, 2 * n_in, h)
+    assert n == 2 * n_in
+    got = to_host(torch, out, n, 1)
+    st = sps.SparseState(40, 2 * n_in)
+    st.set_amplitudes(None, lo.cpu().numpy().view(np.uint64), re.cpu().numpy(), im.cpu().numpy())
+    st.apply(gate, eps)
+    want = st.get_amplitudes()
+    st.close()
+    compare_states(got, want, eps)
