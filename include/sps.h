@@ -305,7 +305,16 @@ typedef enum sps_option {
                                   form, which such a phase run then takes).
                                   Where the form does not apply the usual
                                   kernels run, and the next 1, 2, 4 .. 64
-                                  attempts are skipped. 0: never */
+                                  attempts are skipped. 0: never */,
+  SPS_OPT_BITSLICE_JIT = 19    /* bit-sliced passes compiled for their run at run
+                                  time (NVRTC; the op walk as straight-line code
+                                  on registers, every row offset a constant; one
+                                  compile per distinct run, cached for the
+                                  process): 0 never, 1 (default) when the nonzero
+                                  bound before the pass is at least 2^20, 2
+                                  always. Where the runtime compiler is missing
+                                  or a compile fails the general kernel runs;
+                                  the results are the same */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:
@@ -532,6 +541,12 @@ sps_status sps_branch_apply_static(const sps_gate* gate, uint32_t nqubits,
                                    double prune_eps, uint64_t* out_hi, uint64_t* out_lo,
                                    double* out_re, double* out_im, uint64_t out_cap,
                                    uint64_t* n_out, void* cuda_stream);
+
+/* Host-only: 1 if the runtime compiler used by SPS_OPT_BITSLICE_JIT is
+ * available and compiles the specialised kernel of a small sample run for
+ * sm_103a, else 0; `log` (nullable, cap bytes) receives "ok" or the
+ * compiler's message. Needs no GPU. */
+int sps_jit_selftest(char* log, size_t cap);
 
 /* Static text for a status code. */
 const char* sps_status_str(sps_status st);

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsps.so")
-SOURCES = ["sps_api.cu", "sps_kernels.cu", "sps_compile.cpp", "sps_noalloc.cu", "sps_cta.cu", "sps_gather.cu", "sps_batch.cu", "sps_server.cu"]
+SOURCES = ["sps_api.cu", "sps_kernels.cu", "sps_compile.cpp", "sps_noalloc.cu", "sps_cta.cu", "sps_gather.cu", "sps_batch.cu", "sps_server.cu", "sps_jit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         list(ex.map(compile_one, SOURCES, objs))
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

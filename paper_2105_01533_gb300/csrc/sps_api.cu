@@ -45,7 +45,9 @@ struct ApplyPlan {
   std::vector<size_t> seg_end;      // > 0: a small-state run starts here, ends there
   std::vector<uint64_t> bound_at;   // nonzero bound before each pass
   std::vector<BsPass> bs;           // bit-sliced plans of long fused runs
-  std::vector<size_t> bs_off;
+  std::vector<size_t> bs_off;       // their phase factors in the arena image
+  std::vector<uint64_t> bs_tab;     // their phase tables: first entry in the table space
+  uint64_t bs_tab_entries = 0;      // table space the plan needs (16 B per entry)
   std::vector<size_t> run_off;      // small run: its RunPass array; direct fused pass: its
                                     // op stream; expansion: its factor tables
   std::vector<size_t> ph_off;       // direct fused pass: its fire-slot tables; expansion:
@@ -113,10 +115,15 @@ struct sps_state {
   uint32_t bitslice_min_ops = 8;
   uint64_t bitslice_min_nnz = 1u << 18;   // below this the direct kernel is faster
   uint32_t bs_groups = 0;                  // bit-sliced tile groups, 0 = heuristic
+  int bs_jit = 1;                          // SPS_OPT_BITSLICE_JIT
   uint32_t small_cap = kSmallCap;   // 0 disables small-state runs
-  // plan arena: bit-sliced op lists and phase tables of the current sps_apply
+  // plan arena: op streams, factors and tables of the current sps_apply
   unsigned char* arena = nullptr;
   size_t arena_cap = 0;
+  // phase tables of the bit-sliced passes, built on the device when the plan
+  // is uploaded
+  long long* bs_tables = nullptr;
+  size_t bs_tables_cap = 0;
   struct Staging {
     unsigned char* host = nullptr;   // pinned
     size_t cap = 0;
@@ -342,6 +349,29 @@ sps_status ensure_arena(sps_state* s, size_t bytes) {
   return SPS_OK;
 }
 
+// Makes the bit-sliced phase-table space at least `bytes` long (the old one is
+// released in stream order, like the arena).
+sps_status ensure_bs_tables(sps_state* s, size_t bytes) {
+  if (bytes <= s->bs_tables_cap) return SPS_OK;
+  size_t cap = s->bs_tables_cap ? s->bs_tables_cap : (1u << 20);
+  while (cap < bytes) cap *= 2;
+  void* p = s->alloc(s->alloc_ctx, cap, s->stream);
+  if (!p) return SPS_ERR_OOM;
+  if (s->bs_tables) {
+    for (auto it = s->allocs.begin(); it != s->allocs.end(); ++it) {
+      if (it->ptr == s->bs_tables) {
+        s->release(s->alloc_ctx, it->ptr, it->bytes, s->stream);
+        s->allocs.erase(it);
+        break;
+      }
+    }
+  }
+  s->allocs.push_back({p, cap});
+  s->bs_tables = (long long*)p;
+  s->bs_tables_cap = cap;
+  return SPS_OK;
+}
+
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // The scatter-form table (32-byte slots for 2 * capacity labels at 50% load)
@@ -411,6 +441,8 @@ struct ProfScope {
 }  // namespace
 
 extern "C" {
+
+int sps_jit_selftest(char* log, size_t cap) { return bs_jit_selftest(log, cap); }
 
 const char* sps_status_str(sps_status st) {
   switch (st) {
@@ -909,6 +941,8 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
   //    then the op streams, tables and small-run records
   P->bs.assign(np, BsPass());
   P->bs_off.assign(np, 0);
+  P->bs_tab.assign(np, 0);
+  P->bs_tab_entries = 0;
   P->run_off.assign(np, 0);
   P->ph_off.assign(np, 0);
   size_t bs_bytes = 0;
@@ -924,9 +958,14 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
     if (p.kind == PASS_FUSED && !walked && s->bitslice_min_ops && p.ops.size() >= s->bitslice_min_ops &&
         P->bound_at[i] >= s->bitslice_min_nnz) {
       build_bitslice(p, s->nqubits, &P->bs[i]);
-      P->bs_off[i] = bs_bytes;
-      bs_bytes += align16(P->bs[i].ops.size() * sizeof(SOp)) +
-                  align16(P->bs[i].tables.size() * 8) + align16(P->bs[i].list.size());
+      if (P->bs[i].op_words() > kBsMaxOps) {   // too long for one launch: direct form
+        P->bs[i] = BsPass();
+      } else {
+        P->bs_off[i] = bs_bytes;
+        bs_bytes += align16(P->bs[i].factors.size() * 8);
+        P->bs_tab[i] = P->bs_tab_entries;
+        P->bs_tab_entries += P->bs[i].table_entries();
+      }
     }
     ++i;
   }
@@ -934,13 +973,8 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
   img.assign(bs_bytes, 0);
   for (size_t i = 0; i < np; ++i) {
     const BsPass& b = P->bs[i];
-    if (b.ops.empty()) continue;
-    unsigned char* dst = img.data() + P->bs_off[i];
-    std::memcpy(dst, b.ops.data(), b.ops.size() * sizeof(SOp));
-    dst += align16(b.ops.size() * sizeof(SOp));
-    std::memcpy(dst, b.tables.data(), b.tables.size() * 8);
-    dst += align16(b.tables.size() * 8);
-    if (!b.list.empty()) std::memcpy(dst, b.list.data(), b.list.size());
+    if (b.ops.empty() || b.factors.empty()) continue;
+    std::memcpy(img.data() + P->bs_off[i], b.factors.data(), b.factors.size() * 8);
   }
   auto put = [&](const void* src, size_t bytes) {
     const size_t at = img.size();
@@ -1013,6 +1047,11 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
     s->plan_resident = false;
   }
   const ApplyPlan& P = *s->plan;
+  const bool build_tables = !s->plan_resident;   // a plan new to the device
+  if (build_tables && P.bs_tab_entries) {
+    const sps_status ts = ensure_bs_tables(s, (size_t)P.bs_tab_entries * 16);
+    if (ts != SPS_OK) return ts;
+  }
   if (!s->plan_resident && !P.image.empty()) {
     const sps_status as = ensure_arena(s, P.image.size());
     if (as != SPS_OK) return as;
@@ -1189,27 +1228,22 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       ProfScope ps(s, 1, serial, (uint32_t)p.ops.size(), flags);
       int n;
       if (!bs[pi].ops.empty()) {
-        const BsPass& b = bs[pi];
         BsLaunch bl;
-        const unsigned char* base = s->arena + bs_off[pi];
-        bl.ops = reinterpret_cast<const SOp*>(base);
-        base += align16(b.ops.size() * sizeof(SOp));
-        bl.tables = reinterpret_cast<const double*>(base);
-        base += align16(b.tables.size() * 8);
-        bl.list = base;
-        bl.nops = (uint32_t)b.ops.size();
+        bl.plan = &bs[pi];
+        bl.factors = reinterpret_cast<const long long*>(s->arena + bs_off[pi]);
+        bl.tables = s->bs_tables + 2 * P.bs_tab[pi];
+        bl.build_tables = build_tables ? 1u : 0u;
         bl.ngates = p.ngates;
-        bl.nw = b.nw;
-        bl.na = b.na;
-        bl.nchunks = b.nchunks();
         bl.has_perm = p.has_perm;
         bl.has_phase = p.has_phase;
-        bl.has_cnt = b.has_cnt;
-        bl.list_len = (uint32_t)b.list.size();
         bl.groups = s->bs_groups;
         bl.mg = p.has_perm ? s->masks.writer() : 0u;
         bl.fallback = fb;
-        n = launch_fused_bs(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
+        n = 0;
+        if (s->bs_jit == 2 || (s->bs_jit == 1 && s->nnz_bound >= kBsJitMinNnz))
+          n = launch_fused_bs_jit(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
+        if (n == 0) n = launch_fused_bs(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
+        if (n == 0) n = -1;   // the plan was checked to fit one launch
       } else {
         n = launch_fused(lc, s->kw, s->ctl, s->bufs, p,
                          reinterpret_cast<const OpWord*>(s->arena + run_off[pi]),
@@ -1539,6 +1573,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_AMP_ONLY:
       if (v != 0 && v != 1) return SPS_ERR_ARG;
       s->amp = v == 1;
+      return SPS_OK;
+    case SPS_OPT_BITSLICE_JIT:
+      if (v < 0 || v > 2) return SPS_ERR_ARG;
+      s->bs_jit = (int)v;
       return SPS_OK;
     case SPS_OPT_FUSED_LABELS:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return SPS_ERR_ARG;

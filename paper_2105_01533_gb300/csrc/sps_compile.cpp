@@ -636,17 +636,49 @@ namespace {
 
 struct CL { double re, im; };
 
+// x in [-1, 1] as fixed point with 2^62 = 1 (exact: a double has 53 bits)
+long long to_q62(double x) { return std::llround(std::ldexp(x, 62)); }
+
 }  // namespace
 
 void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
   *out = BsPass();
-  out->nw = (nqubits + 31) / 32;
+  BsPass& b = *out;
+  b.nw = (nqubits + 31) / 32;
+  std::memset(b.row_of, kNoRow, sizeof(b.row_of));
+  // qubits the ops read (conditions, selectors) and flip
+  uint64_t used[2] = {0ull, 0ull}, flipped[2] = {0ull, 0ull};
   bool cnt = false;
-  for (const FOp& o : p.ops) cnt = cnt || o.a0 != 0 || o.a1 != 0;
-  out->has_cnt = cnt;
-  const uint32_t label_rows = 32 * out->nw;
+  for (const FOp& o : p.ops) {
+    for (int w = 0; w < 2; ++w) {
+      used[w] |= o.c[w] | o.t[w];
+      flipped[w] |= o.t[w];
+    }
+    if (o.sbit != NO_SEL) used[o.sbit >> 6] |= 1ull << (o.sbit & 63u);
+    cnt = cnt || o.a0 != 0 || o.a1 != 0;
+  }
+  // a 64-bit half with a flipped bit is written back whole: every valid bit of
+  // it gets a row (its other bits are 0 in every label)
+  for (int h = 0; h < 2; ++h) {
+    if (!flipped[h]) continue;
+    const uint64_t valid = nqubits >= 64 * (h + 1) ? ~0ull
+                         : (nqubits <= 64u * h ? 0ull : ((1ull << (nqubits - 64 * h)) - 1));
+    used[h] |= valid;
+    for (int k = 0; k < 2; ++k)
+      if ((valid >> (32 * k)) & 0xFFFFFFFFull) b.word_out |= 1u << (2 * h + k);
+  }
+  uint32_t row = 0;
+  for (uint32_t w = 0; w < 4; ++w) {
+    const uint32_t bits = (uint32_t)(used[w >> 1] >> (32 * (w & 1u)));
+    b.word_bits[w] = bits;
+    for (uint32_t j = 0; j < 32; ++j)
+      if ((bits >> j) & 1u) b.row_of[w][j] = (uint8_t)row++;
+  }
+  b.label_rows = row;
+  auto row_q = [&](uint32_t q) { return b.row_of[q >> 5][q & 31u]; };
+  b.has_cnt = cnt;
+  b.aux_row0 = row;
   uint32_t aux = cnt ? 3u : 0u;
-  // factor of every aux bit, for the chunk tables
   std::vector<CL> factor;
   if (cnt) {
     const double r = std::sqrt(0.5);
@@ -654,80 +686,94 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
     factor.push_back(CL{0, 1});      // counter bit 1: e^{i pi/2}
     factor.push_back(CL{-1, 0});     // counter bit 2: e^{i pi}
   }
+  for (const FOp& o : p.ops)
+    if (o.ph != NO_PH) aux += o.sbit != NO_SEL ? 2u : 1u;
+  b.aux_bits = aux;
+  const uint8_t scratch = (uint8_t)(b.aux_row0 + aux);
+  b.ones_row = scratch + 1u;
+  b.nrows = b.ones_row + 1u;
+  uint32_t next_aux = b.aux_row0 + (cnt ? 3u : 0u);
+  const uint8_t ones = (uint8_t)b.ones_row;
   for (const FOp& o : p.ops) {
     SOp so;
     std::memset(&so, 0, sizeof(so));
+    so.c[0] = so.c[1] = so.c[2] = ones;
+    so.t = so.s = so.f0 = so.f1 = kNoRow;
     std::vector<uint8_t> conds;
-    for (int w = 0; w < 2; ++w)
-      for (int b = 0; b < 64; ++b)
-        if ((o.c[w] >> b) & 1ull) conds.push_back((uint8_t)(64 * w + b));
-    so.c[0] = so.c[1] = so.c[2] = SOP_ONES;
-    for (size_t k = 0; k < conds.size() && k < 3; ++k) so.c[k] = conds[k];
+    for (uint32_t w = 0; w < 2; ++w)
+      for (uint32_t q = 0; q < 64; ++q)
+        if ((o.c[w] >> q) & 1ull) conds.push_back(row_q(64 * w + q));
     if (conds.size() > 3) {
-      so.kind |= SOP_LIST;
-      so.list_off = (uint16_t)out->list.size();
-      so.list_n = (uint16_t)(conds.size() - 3);
-      out->list.insert(out->list.end(), conds.begin() + 3, conds.end());
+      // AND the conditions past the second into the scratch row, three at a time
+      size_t k = 2;
+      bool first = true;
+      while (k < conds.size()) {
+        SOp a;
+        std::memset(&a, 0, sizeof(a));
+        a.kind = SOP_AND;
+        a.t = scratch;
+        a.s = a.f0 = a.f1 = kNoRow;
+        a.c[0] = first ? conds[k++] : scratch;
+        a.c[1] = k < conds.size() ? conds[k++] : ones;
+        a.c[2] = k < conds.size() ? conds[k++] : ones;
+        first = false;
+        b.ops.push_back(a);
+      }
+      conds.resize(2);
+      conds.push_back(scratch);
     }
+    for (size_t k = 0; k < conds.size(); ++k) so.c[k] = conds[k];
     std::vector<uint8_t> tbits;   // a merged flip has several targets, one condition
-    for (int w = 0; w < 2; ++w)
-      for (int b = 0; b < 64; ++b)
-        if ((o.t[w] >> b) & 1ull) tbits.push_back((uint8_t)(64 * w + b));
+    for (uint32_t w = 0; w < 2; ++w)
+      for (uint32_t q = 0; q < 64; ++q)
+        if ((o.t[w] >> q) & 1ull) tbits.push_back(row_q(64 * w + q));
     if (!tbits.empty()) {
       so.kind |= SOP_FLIP;
       so.t = tbits[0];
     }
     if (o.sbit != NO_SEL) {
       so.kind |= SOP_SEL;
-      so.s = o.sbit;
+      so.s = row_q(o.sbit);
     }
     if (o.a0 || o.a1) {
       so.kind |= SOP_CNT;
-      so.a0 = o.a0;
-      so.a1 = o.a1;
+      so.a0 = o.a0 & 7u;
+      so.a1 = o.a1 & 7u;
     }
     if (o.ph != NO_PH) {
       const PhasePair& pp = p.phases[o.ph];
       so.kind |= SOP_FIRE;
-      so.f0 = (uint8_t)(label_rows + aux++);
+      so.f0 = (uint8_t)next_aux++;
       factor.push_back(CL{pp.re0, pp.im0});
       if (o.sbit != NO_SEL) {
-        so.f1 = (uint8_t)(label_rows + aux++);
+        so.f1 = (uint8_t)next_aux++;
         factor.push_back(CL{pp.re1, pp.im1});
       }
     }
-    out->ops.push_back(so);
+    b.ops.push_back(so);
     // further targets: the same condition (no target is in it), flip only
     for (size_t k = 1; k < tbits.size(); ++k) {
       SOp x = so;
-      x.kind = (uint8_t)(SOP_FLIP | (so.kind & SOP_LIST));
+      x.kind = SOP_FLIP;
       x.t = tbits[k];
-      out->ops.push_back(x);
+      b.ops.push_back(x);
     }
   }
-  out->aux_bits = aux;
-  out->na = (aux + 31) / 32;
-  // unused condition slots read the all-ones row that follows the aux rows
-  const uint8_t ones = (uint8_t)(32 * (out->nw + out->na));
-  for (SOp& so : out->ops)
-    for (int k = 0; k < 3; ++k)
-      if (so.c[k] == SOP_ONES) so.c[k] = ones;
-  // chunk tables by doubling: entry idx = entry (idx without its top bit) times
-  // the factor of that bit, one complex product each
-  const uint32_t nch = out->nchunks();
-  out->tables.assign((size_t)nch * 256 * 2, 0.0);
-  for (uint32_t c = 0; c < nch; ++c) {
-    double* t = &out->tables[(size_t)c * 256 * 2];
-    t[0] = 1.0;
-    for (uint32_t b = 0; b < 8; ++b) {
-      const uint32_t bit = 8 * c + b;
-      const double fr = bit < aux ? (double)factor[bit].re : 1.0;
-      const double fi = bit < aux ? (double)factor[bit].im : 0.0;
-      for (uint32_t u = 0; u < (1u << b); ++u) {
-        const uint32_t v = u | (1u << b);
-        t[2 * v] = t[2 * u] * fr - t[2 * u + 1] * fi;
-        t[2 * v + 1] = t[2 * u] * fi + t[2 * u + 1] * fr;
-      }
+  b.factors.resize(2 * (size_t)aux);
+  for (uint32_t i = 0; i < aux; ++i) {
+    b.factors[2 * i] = to_q62(factor[i].re);
+    b.factors[2 * i + 1] = to_q62(factor[i].im);
+  }
+  // phase tables: the aux bits in as few chunks of at most kBsMaxChunkBits as
+  // possible, split evenly (one table product per extra chunk and entry)
+  if (aux > 0) {
+    b.nchunks = (aux + kBsMaxChunkBits - 1) / kBsMaxChunkBits;
+    uint32_t at = 0;
+    for (uint32_t c = 0; c < b.nchunks; ++c) {
+      const uint32_t bits = aux / b.nchunks + (c < aux % b.nchunks ? 1u : 0u);
+      b.chunk_shift[c] = at;
+      b.chunk_bits[c] = bits;
+      at += bits;
     }
   }
 }

@@ -84,39 +84,61 @@ struct BranchOp {
 // label bit, bit i = entry i). A gate then acts on 32 entries with a few logic
 // ops: X with controls c is P[t] ^= AND(P[c]); pi/4 phases add a constant to a
 // 3-plane counter; arbitrary phases record the planes on which they fire.
-// Plane rows 0 .. 32*nw-1 hold label bits (row = qubit), rows 32*nw .. hold
-// "aux" bits: 0..2 the counter (if any), then one fire plane per arbitrary
-// phase slot. After the op walk every entry gets its aux word back, and its
-// phase is the product over 8-bit chunks of precomputed tables.
-enum SOpKind : uint8_t { SOP_FLIP = 1, SOP_CNT = 2, SOP_FIRE = 4, SOP_SEL = 8, SOP_LIST = 16 };
-// Row index of a constant all-ones plane: unused condition slots point here so
-// the condition is always the AND of three rows.
-constexpr uint8_t SOP_ONES = 255;
+// A warp keeps a tile of G groups of 32 entries in shared memory, one row per
+// plane and one column per group, and lane g walks the op list on column g.
+// Rows: the label bits the pass needs (every valid bit of a 64-bit label half
+// that the pass writes back, and the condition and selector bits elsewhere),
+// then the aux rows (the counter's 3 planes, if any, then one fire plane per
+// arbitrary phase slot), a scratch row for long condition lists and a row of
+// all ones (unused condition slots read it, so a condition is always the AND
+// of three rows). After the walk every entry gets its aux word back; its
+// phase is the product over chunks of the aux bits of tables built on the
+// device (fixed point, 2^62 = 1), one FP64 complex product per entry.
+enum SOpKind : uint8_t { SOP_FLIP = 1, SOP_CNT = 2, SOP_FIRE = 4, SOP_SEL = 8, SOP_AND = 32 };
+constexpr uint8_t kNoRow = 0xFF;
 
-struct SOp {                // 16 bytes, read as four 32-bit words
-  uint8_t kind;             // word 0
-  uint8_t c[3];             // condition rows (SOP_ONES when unused)
-  uint8_t t;                // word 1: flip row
+struct SOp {                // rows; the launch turns them into shared-memory offsets
+  uint8_t kind;
+  uint8_t c[3];             // condition rows (the ones row when unused)
+  uint8_t t;                // flip row (SOP_AND: the row assigned)
   uint8_t s;                // selector row
   uint8_t f0, f1;           // aux rows written for sel = 0 / sel = 1 (f1 only with SEL)
-  uint8_t a0, a1;           // word 2: counter steps for sel = 0 / 1
-  uint16_t reserved;
-  uint16_t list_off, list_n;  // word 3: extra conditions (SOP_LIST)
+  uint8_t a0, a1;           // counter steps for sel = 0 / 1 (mod 8)
 };
-static_assert(sizeof(SOp) == 16, "SOp layout");
 
 constexpr uint32_t kMaxAuxBits = 64;     // counter (3) + fire slots
 constexpr uint32_t kMaxFireSlots = kMaxAuxBits - 3;
+constexpr uint32_t kBsMaxOps = 1024;     // op words of one bit-sliced launch (kernel parameters)
+constexpr uint32_t kBsMaxChunkBits = 18; // aux bits per phase table (4 MiB)
+constexpr uint64_t kBsJitMinNnz = 1ull << 20;   // SPS_OPT_BITSLICE_JIT = 1: from this bound
 
 struct BsPass {
-  uint32_t nw = 0;          // label words of 32 bits transposed
-  uint32_t na = 0;          // aux words
-  uint32_t aux_bits = 0;
+  uint32_t nw = 0;            // 32-bit words of a label (nqubits / 32 rounded up)
+  uint32_t nrows = 0;         // rows per tile column: label + aux + scratch + ones
+  uint32_t label_rows = 0;
+  uint32_t aux_row0 = 0, aux_bits = 0;
+  uint32_t ones_row = 0;
   bool has_cnt = false;
+  uint32_t word_bits[4] = {0, 0, 0, 0};  // bit j of word w has a row
+  uint32_t word_out = 0;      // bit w: word w is written back
+  uint8_t row_of[4][32];      // row of bit j of word w, or kNoRow
   std::vector<SOp> ops;
-  std::vector<uint8_t> list;
-  std::vector<double> tables;   // nchunks * 256 * (re, im)
-  uint32_t nchunks() const { return (aux_bits + 7) / 8; }
+  std::vector<long long> factors;        // aux_bits x (re, im), fixed point 2^62
+  uint32_t nchunks = 0;
+  uint32_t chunk_shift[4] = {0, 0, 0, 0};
+  uint32_t chunk_bits[4] = {0, 0, 0, 0};
+  // 16-byte words of the launch's op stream: one per flip or scratch AND, two
+  // per general op
+  uint32_t op_words() const {
+    uint32_t n = 0;
+    for (const SOp& o : ops) n += (o.kind != SOP_FLIP && o.kind != SOP_AND) ? 2u : 1u;
+    return n;
+  }
+  uint64_t table_entries() const {
+    uint64_t t = 0;
+    for (uint32_t c = 0; c < nchunks; ++c) t += 1ull << chunk_bits[c];
+    return t;
+  }
 };
 
 // ---- encoded op stream of a fused pass ------------------------------------------
@@ -345,18 +367,32 @@ int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, 
 int launch_branch_compact(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,
                           const BranchLaunch& b, uint64_t nnz_bound, unsigned long long* plog);
 struct BsLaunch {
-  const SOp* ops;           // device copies (plan arena)
-  const uint8_t* list;
-  const double* tables;
-  uint32_t nops, nw, na, nchunks;
-  uint32_t ngates;          // gates of the run, for the update count
-  uint32_t has_perm, has_phase, has_cnt, list_len;
-  uint32_t groups;          // groups of 32 entries per warp tile (even, 2..32), 0 = choose
-  uint32_t mg;              // label-mask buffers (MaskRing)
-  uint32_t fallback = 0;    // as in launch_fused
+  const BsPass* plan;
+  const long long* factors;  // device copy of plan->factors (plan arena)
+  long long* tables;         // device table space (plan->table_entries() x 16 B)
+  uint32_t build_tables;     // 1: build the tables from the factors first
+  uint32_t ngates;           // gates of the run, for the update count
+  uint32_t has_perm, has_phase;
+  uint32_t groups;           // groups of 32 entries per warp tile (2..32), 0 = choose
+  uint32_t mg;               // label-mask buffers (MaskRing)
+  uint32_t fallback = 0;     // as in launch_fused
 };
+// Returns the kernels enqueued (1 or more), 0 if the plan does not fit one
+// launch (then the pass must take the direct form), -1 on a launch error.
 int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
                     uint64_t nnz_bound, unsigned long long* plog);
+// Builds the pass's phase tables from its factors (kernels enqueued, -1 on error).
+int launch_bs_tables(const LaunchCfg& lc, const BsLaunch& b);
+// The bit-sliced pass compiled for this plan (sps_jit.cu): the op walk as
+// straight-line code on registers and every row offset a constant. Returns
+// the kernels enqueued (tables included), 0 if this form is not available
+// (runtime compiler missing or the compile failed: use launch_fused_bs), -1
+// on a launch error.
+int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
+                        uint64_t nnz_bound, unsigned long long* plog);
+// Host-only check of the runtime compiler: generates and compiles the kernel
+// of a small sample pass; returns 1 if it compiled, 0 if not available.
+int bs_jit_selftest(char* log, size_t cap);
 // Runs npasses consecutive passes (RunPass records at arena + pass_off) in one
 // CTA with the state in shared memory; the host guarantees nnz <= kSmallCap.
 int launch_small_run(void* stream, int key_words, Ctl* ctl, Bufs bufs, const unsigned char* arena,

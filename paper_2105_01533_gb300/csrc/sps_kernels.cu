@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "sps_device.cuh"
 #include "sps_internal.h"
@@ -120,33 +121,50 @@ __global__ void __launch_bounds__(256) k_fused(Ctl* ctl, Bufs bufs, const FusedA
   if (a.has_perm) merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
 }
 
-// A fused run whose gates all resolved on the host still counts its updates.
-__global__ void k_count_updates(Ctl* ctl, uint32_t ngates, uint32_t fallback) {
-  if (ctl->status == 0u && !amp_took(ctl, fallback)) ctl->updates += ctl->nnz * ngates;
-}
-
 // ---------------------------------------------------------------------------
-// Bit-sliced fused pass. A warp owns a tile of `groups` x 32 entries:
-//   1. load: 32 entries at a time, each 32-bit label word is transposed across
-//      the warp (shuffle butterfly), so lane j holds bit-plane j of the group;
-//      planes go to shared memory, row = plane, column = group (stride 33 keeps
-//      every access bank-conflict free);
+// Bit-sliced fused pass. A warp owns a tile of G groups x 32 entries:
+//   1. load: 32 entries at a time; each 32-bit label word the pass needs is
+//      transposed across the warp (shuffle butterfly), so lane j holds
+//      bit-plane j of the group; planes go to shared memory, row = plane,
+//      column = group (stride G + 1 keeps every access bank-conflict free);
 //   2. walk: lane g runs the op list on group g's planes (one logic op handles
-//      32 entries), keeping the pi/4 counter in three registers and writing the
-//      fire planes of arbitrary phases to aux rows;
+//      32 entries), keeping the pi/4 counter in three registers and writing
+//      the fire planes of arbitrary phases to aux rows; the op list sits in
+//      the kernel parameters (constant bank), so every lane reads the same op;
 //   3. store: planes are transposed back; labels are written if the pass
-//      permutes; the aux word selects precomputed chunk phases, multiplied
-//      into the amplitude only where it is not 1.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, unsigned lane) {
+//      permutes; each entry's aux word selects one entry per phase table, the
+//      entries are multiplied in fixed point (integer pipe) and the amplitude
+//      takes one FP64 complex product (two real products where it is real).
+
+// One butterfly transpose of a 32 x 32 bit block held one word per lane:
+// afterwards lane j holds bit j of every lane's word (bit i from lane i).
+// Stage m exchanges m x m sub-blocks between lanes l and l ^ m: the lane keeps
+// the half selected by `keep` and takes the partner's other half rotated into
+// place, so a stage is a shuffle, a funnel-shift rotate and a bit select with
+// per-lane constants set up once.
+struct Transposer {
+  uint32_t rot[5], keep[5];
+  __device__ __forceinline__ void init(unsigned lane) {
 #pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) {
-    const uint32_t mk = m == 16 ? 0x0000FFFFu : m == 8 ? 0x00FF00FFu : m == 4 ? 0x0F0F0F0Fu
-                      : m == 2 ? 0x33333333u : 0x55555555u;
-    const uint32_t y = __shfl_xor_sync(FULL, x, m);
-    x = (lane & m) == 0 ? ((x & mk) | ((y & mk) << m)) : ((x & ~mk) | ((y >> m) & mk));
+    for (int i = 0; i < 5; ++i) {
+      const uint32_t m = 16u >> i;
+      const uint32_t mk = i == 0 ? 0x0000FFFFu : i == 1 ? 0x00FF00FFu : i == 2 ? 0x0F0F0F0Fu
+                        : i == 3 ? 0x33333333u : 0x55555555u;
+      const bool upper = (lane & m) != 0u;
+      rot[i] = upper ? 32u - m : m;
+      keep[i] = upper ? ~mk : mk;
+    }
   }
-  return x;
-}
+  __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const uint32_t y = __shfl_xor_sync(FULL, x, 16u >> i);
+      const uint32_t t = __funnelshift_l(y, y, rot[i]);
+      x = (x & keep[i]) | (t & ~keep[i]);
+    }
+    return x;
+  }
+};
 
 // adds the constant k (0..7) to the 3-plane counter where f is set
 __device__ __forceinline__ void cnt_add(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t k,
@@ -166,27 +184,71 @@ __device__ __forceinline__ void cnt_add(uint32_t& c0, uint32_t& c1, uint32_t& c2
   if (k & 4u) c2 ^= f;
 }
 
+// Fixed-point complex product: a (scale 2^qa) times b (scale 2^62) gives
+// scale 2^(qa - 2); three high products (a = ar + i ai, b = br + i bi):
+// re = br (ar + ai) - ai (br + bi), im = br (ar + ai) + ar (bi - br).
+__device__ __forceinline__ void qmul(long long& ar, long long& ai, long long br, long long bi) {
+  const long long k1 = __mul64hi(br, ar + ai);
+  const long long k2 = __mul64hi(ar, bi - br);
+  const long long k3 = __mul64hi(ai, br + bi);
+  ar = k1 - k3;
+  ai = k1 + k2;
+}
+
+// v * 2^-q as a double, rounded to nearest (ties away), on the integer pipe
+// (|v| >= 1 after the sign, so the result is a normal number).
+__device__ __forceinline__ double q_to_double(long long v, int q) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)m);
+  m <<= lz;                                     // leading one at bit 63
+  unsigned long long r = (m >> 11) + ((m >> 10) & 1ull);
+  int e = 63 - lz - q;
+  if (r >> 53) {
+    r >>= 1;
+    ++e;
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) |
+                                          (r & 0x000FFFFFFFFFFFFFull)));
+}
+
+// Op stream of the walk (kernel parameters): one 16-byte word per op,
+// x, y, z = byte offsets of the three condition rows in a tile column and
+// w = the target row's offset; bit 31 of w marks a general op (kind in bits
+// 24..30) whose second word holds {selector row, f0 row, f1 row,
+// a0 | a1 << 8}. A pure flip (X, CNOT, Toffoli) is one word; SOP_AND (the
+// scratch row of long condition lists) is one word with the tag.
+constexpr uint32_t kBsGeneral = 0x80000000u;
+
 struct BsArgs {
-  const SOp* ops;
-  const uint8_t* list;
-  const double* tables;
-  uint32_t nops, ngates, nw, na, nchunks;
-  uint32_t has_perm, has_phase, has_cnt, list_len;
-  uint32_t groups;   // groups of 32 entries per warp tile (even, 2..32)
-  uint32_t mg;       // label-mask buffers (MaskRing)
-  uint32_t fallback; // 1: skip if an amplitude-only attempt took the pass
+  uint32_t nwords, ngates;
+  uint32_t groups, stride;     // G, G + 1
+  uint32_t rows;               // rows per tile column
+  uint32_t word_bits[4];       // bits of word w that have rows
+  uint32_t word_out;           // words written back
+  uint32_t aux_row0, naux, ones_row;
+  uint32_t has_perm, has_phase, has_cnt;
+  uint32_t nchunks;
+  uint32_t chunk_shift[4], chunk_bits[4];
+  const longlong2* tables[4];
+  uint32_t mg;                 // label-mask buffers (MaskRing)
+  uint32_t fallback;           // 1: skip if an amplitude-only attempt took the pass
+  uint8_t row_of[4][32];       // row of bit j of word w (kNoRow: none)
+  uint4 ops[kBsMaxOps];
 };
 
-template <int KW>
-__global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
+__device__ __forceinline__ uint32_t& plane(unsigned char* col, uint32_t off) {
+  return *reinterpret_cast<uint32_t*>(col + off);
+}
+
+// NW: 32-bit words of a label the kernel handles (1..4); KW: 64-bit label
+// words in memory (1 or 2).
+template <int KW, int NW>
+__global__ void __launch_bounds__(128) k_fused_bs(Ctl* ctl, Bufs bufs,
                                                   const __grid_constant__ BsArgs a,
                                                   unsigned long long* plog) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint4* sops = reinterpret_cast<uint4*>(smem);
-  double2* stab = reinterpret_cast<double2*>(smem + 16 * a.nops);
-  uint8_t* slist = reinterpret_cast<uint8_t*>(stab + 256 * a.nchunks);
-  uint32_t* splanes =
-      reinterpret_cast<uint32_t*>(smem + ((16 * a.nops + 4096 * a.nchunks + a.list_len + 15) & ~15u));
+  extern __shared__ __align__(16) uint32_t bsm[];
   const uint64_t n = ctl->nnz;
   const bool skip = amp_took(ctl, a.fallback);
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -198,140 +260,246 @@ __global__ void __launch_bounds__(512) k_fused_bs(Ctl* ctl, Bufs bufs,
     ctl->updates += n * a.ngates;
     if (a.has_perm) reset_label_masks(ctl, mg_rs(a.mg));
   }
-  // stage the op list, the phase tables and the extra-condition list
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(a.ops);
-    for (uint32_t i = threadIdx.x; i < a.nops; i += blockDim.x) sops[i] = src[i];
-    const double2* ts = reinterpret_cast<const double2*>(a.tables);
-    for (uint32_t i = threadIdx.x; i < 256 * a.nchunks; i += blockDim.x) stab[i] = ts[i];
-    for (uint32_t i = threadIdx.x; i < a.list_len; i += blockDim.x) slist[i] = a.list[i];
-  }
-  __syncthreads();
   const SoA s = pick(bufs, ctl->cur);
   const unsigned lane = threadIdx.x & 31u;
   const unsigned warp = threadIdx.x >> 5;
-  const uint32_t G = a.groups;
-  const uint32_t S = G + 1u;                       // column stride (odd: conflict-free)
-  const uint32_t rows = 32u * (a.nw + a.na) + 1u;  // + the all-ones row
-  const uint32_t ones_row = rows - 1u;
-  uint32_t* pl = splanes + (size_t)warp * rows * S;
+  const uint32_t G = a.groups, S = a.stride;
+  uint32_t* pl = bsm + (size_t)warp * a.rows * S;
   const uint64_t tile_entries = 32ull * G;
   const uint64_t ntiles = (n + tile_entries - 1) / tile_entries;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint32_t c = lane; c < S; c += 32u) pl[ones_row * S + c] = 0xFFFFFFFFu;
+  for (uint32_t c = lane; c < S; c += 32u) pl[a.ones_row * S + c] = 0xFFFFFFFFu;
+  Transposer tr;
+  tr.init(lane);
+  // this lane's row in each label word (offset in words; -1: none)
+  int my_row[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t r = a.row_of[w][lane];
+    my_row[w] = r == kNoRow ? -1 : (int)(r * S);
+  }
+  const int aux0 = lane < a.naux ? (int)((a.aux_row0 + lane) * S) : -1;
+  const int aux1 = lane + 32u < a.naux ? (int)((a.aux_row0 + 32u + lane) * S) : -1;
   uint64_t mo0 = 0, mo1 = 0, ma0 = ~0ull, ma1 = ~0ull;   // OR / AND of the new labels
   for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < ntiles;
        tile += nwarps) {
     const uint64_t base = tile * tile_entries;
-    // 1. load and transpose
-    for (uint32_t g = 0; g < G; ++g) {
-      const uint64_t e = base + 32ull * g + lane;
-      const bool valid = e < n;
-      const uint64_t lo = valid ? s.lo[e] : 0ull;
-      const uint64_t hi = (KW == 2 && valid) ? s.hi[e] : 0ull;
-      for (uint32_t w = 0; w < a.nw; ++w) {
-        const uint64_t src = w < 2 ? lo : hi;
-        const uint32_t x = (uint32_t)(src >> (32 * (w & 1u)));
-        pl[(32u * w + lane) * S + g] = transpose32(x, lane);
+    const uint64_t tile_n = n - base < tile_entries ? n - base : tile_entries;
+    // the amplitudes are used after the walk: start moving them into L2 now
+    if (a.has_phase)
+      for (uint64_t off = 16ull * lane; off < tile_n; off += 512ull) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(s.re + base + off));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(s.im + base + off));
+      }
+    // 1. load and transpose, 8 groups at a time (their loads in flight together)
+    for (uint32_t g0 = 0; g0 < G; g0 += 8u) {
+      uint64_t lo[8], hi[8];
+#pragma unroll
+      for (uint32_t k = 0; k < 8u; ++k) {
+        const uint64_t e = base + 32ull * (g0 + k) + lane;
+        const bool valid = g0 + k < G && e < n;
+        lo[k] = valid ? __ldcs(s.lo + e) : 0ull;
+        hi[k] = (KW == 2 && valid) ? __ldcs(s.hi + e) : 0ull;
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < 8u; ++k) {
+        const uint32_t g = g0 + k;
+        if (g >= G) break;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          if (a.word_bits[w] == 0u) continue;
+          const uint64_t src = w < 2 ? lo[k] : hi[k];
+          const uint32_t t = tr((uint32_t)(src >> (32 * (w & 1))));
+          if (my_row[w] >= 0) pl[my_row[w] + g] = t;
+        }
       }
     }
-    for (uint32_t r = 32u * a.nw; r < ones_row; ++r)
-      for (uint32_t c = lane; c < G; c += 32u) pl[r * S + c] = 0u;
+    // the next tile's labels move into L2 while this one is walked
+    {
+      const uint64_t nb = base + nwarps * tile_entries;
+      if (nb < n) {
+        const uint64_t nn = n - nb < tile_entries ? n - nb : tile_entries;
+        for (uint64_t off = 16ull * lane; off < nn; off += 512ull) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(s.lo + nb + off));
+          if (KW == 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(s.hi + nb + off));
+        }
+      }
+    }
     __syncwarp();
     // 2. op walk, lane g on group g
     if (lane < G) {
-      uint32_t* col = pl + lane;
+      unsigned char* col = reinterpret_cast<unsigned char*>(pl + lane);
       uint32_t c0 = 0u, c1 = 0u, c2 = 0u;
-      for (uint32_t j = 0; j < a.nops; ++j) {
-        const uint4 w = sops[j];
-        uint32_t f = col[((w.x >> 8) & 0xFFu) * S] & col[((w.x >> 16) & 0xFFu) * S] &
-                     col[(w.x >> 24) * S];
-        const uint32_t kind = w.x & 0xFFu;
-        if (kind == SOP_FLIP) {   // X / CNOT / Toffoli
-          col[(w.y & 0xFFu) * S] ^= f;
+      for (uint32_t j = 0; j < a.nwords;) {
+        const uint4 w = a.ops[j++];
+        const uint32_t f = plane(col, w.x) & plane(col, w.y) & plane(col, w.z);
+        if (!(w.w & kBsGeneral)) {   // X / CNOT / Toffoli
+          plane(col, w.w) ^= f;
           continue;
         }
-        if (kind & SOP_LIST) {
-          const uint32_t off = w.w & 0xFFFFu, cnt = w.w >> 16;
-          for (uint32_t k = 0; k < cnt; ++k) f &= col[slist[off + k] * S];
+        const uint32_t kind = (w.w >> 24) & 0x7Fu;
+        const uint32_t toff = w.w & 0x00FFFFFFu;
+        if (kind == SOP_AND) {
+          plane(col, toff) = f;
+          continue;
         }
-        const uint32_t sel = (kind & SOP_SEL) ? col[((w.y >> 8) & 0xFFu) * S] : 0u;
+        const uint4 e = a.ops[j++];
+        const uint32_t sel = (kind & SOP_SEL) ? plane(col, e.x) : 0u;
         if (kind & SOP_CNT) {
-          cnt_add(c0, c1, c2, w.z & 0xFFu, f & ~sel);
-          if (kind & SOP_SEL) cnt_add(c0, c1, c2, (w.z >> 8) & 0xFFu, f & sel);
+          cnt_add(c0, c1, c2, e.w & 7u, f & ~sel);
+          if (kind & SOP_SEL) cnt_add(c0, c1, c2, (e.w >> 8) & 7u, f & sel);
         }
         if (kind & SOP_FIRE) {
-          col[((w.y >> 16) & 0xFFu) * S] = f & ~sel;
-          if (kind & SOP_SEL) col[(w.y >> 24) * S] = f & sel;
+          plane(col, e.y) = f & ~sel;
+          if (kind & SOP_SEL) plane(col, e.z) = f & sel;
         }
-        if (kind & SOP_FLIP) col[(w.y & 0xFFu) * S] ^= f;
+        if (kind & SOP_FLIP) plane(col, toff) ^= f;
       }
-      if (a.has_cnt) {
-        const uint32_t r0 = 32u * a.nw;
-        col[r0 * S] = c0;
-        col[(r0 + 1u) * S] = c1;
-        col[(r0 + 2u) * S] = c2;
+      if (a.has_cnt) {   // the counter planes are aux rows 0..2
+        pl[a.aux_row0 * S + lane] = c0;
+        pl[(a.aux_row0 + 1u) * S + lane] = c1;
+        pl[(a.aux_row0 + 2u) * S + lane] = c2;
       }
     }
     __syncwarp();
-    // 3. transpose back and store
-    for (uint32_t g = 0; g < G; ++g) {
-      const uint64_t e = base + 32ull * g + lane;
-      const bool valid = e < n;
-      uint64_t lo = 0ull, hi = 0ull;
-      for (uint32_t w = 0; w < a.nw; ++w) {
-        const uint64_t x = transpose32(pl[(32u * w + lane) * S + g], lane);
-        if (w < 2) lo |= x << (32 * w); else hi |= x << (32 * (w - 2));
-      }
-      uint32_t aux0 = 0u, aux1 = 0u;
-      if (a.na > 0) aux0 = transpose32(pl[(32u * a.nw + lane) * S + g], lane);
-      if (a.na > 1) aux1 = transpose32(pl[(32u * (a.nw + 1u) + lane) * S + g], lane);
-      if (valid) {
+    // 3. transpose back and store, 4 groups at a time: the phase-table entries
+    //    and amplitudes of the 4 entries a lane writes are in flight together
+    for (uint32_t g0 = 0; g0 < G; g0 += 4u) {
+      uint64_t aux[4];
+      uint64_t ent[4];
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        const uint32_t g = g0 + k;
+        aux[k] = 0ull;
+        ent[k] = base + 32ull * g + lane;
+        if (g >= G) continue;
+        const bool valid = ent[k] < n;
         if (a.has_perm) {
-          s.lo[e] = lo;
-          if (KW == 2) s.hi[e] = hi;
-          mo0 |= lo;
-          mo1 |= hi;
-          ma0 &= lo;
-          ma1 &= hi;
-        }
-        // the pi/4 counter (aux bits 0..2) is applied exactly as in the direct
-        // form (quarter turns are swaps and signs, no FP64 products); the
-        // tables then see only the fire slots
-        uint32_t cnt = 0u;
-        if (a.has_cnt) {
-          cnt = aux0 & 7u;
-          aux0 &= ~7u;
-        }
-        if (a.has_phase && (aux0 | aux1 | cnt)) {
-          double re = s.re[e], im = s.im[e];
-          if (aux0 | aux1) {
-            double pr = 1.0, pi = 0.0;
-            bool any = false;
-            for (uint32_t c = 0; c < a.nchunks; ++c) {
-              const uint32_t word = c < 4 ? aux0 : aux1;
-              const uint32_t idx = (word >> (8 * (c & 3u))) & 0xFFu;
-              if (idx == 0u) continue;
-              const double2 t = stab[c * 256u + idx];
-              if (!any) {
-                pr = t.x;
-                pi = t.y;
-                any = true;
-              } else {
-                cmul_rn(pr, pi, t.x, t.y);
-              }
-            }
-            cmul_rn(re, im, pr, pi);
+          uint64_t lo = 0ull, hi = 0ull;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            if (!((a.word_out >> w) & 1u)) continue;
+            const uint64_t x = tr(my_row[w] >= 0 ? pl[my_row[w] + g] : 0u);
+            if (w < 2) lo |= x << (32 * w);
+            else hi |= x << (32 * (w - 2));
           }
-          apply_pi4(cnt, re, im);
-          s.re[e] = re;
-          s.im[e] = im;
+          if (valid) {
+            if (a.word_out & 3u) s.lo[ent[k]] = lo;
+            else lo = s.lo[ent[k]];
+            if (KW == 2) {
+              if (a.word_out & 12u) s.hi[ent[k]] = hi;
+              else hi = s.hi[ent[k]];
+            }
+            mo0 |= lo;
+            mo1 |= hi;
+            ma0 &= lo;
+            ma1 &= hi;
+          }
+        }
+        if (a.has_phase) {
+          const uint32_t x0 = tr(aux0 >= 0 ? pl[aux0 + g] : 0u);
+          const uint32_t x1 = a.naux > 32u ? tr(aux1 >= 0 ? pl[aux1 + g] : 0u) : 0u;
+          aux[k] = valid ? ((uint64_t)x0 | ((uint64_t)x1 << 32)) : 0ull;
+        }
+      }
+      if (a.has_phase) {
+        const uint32_t m0 = (1u << a.chunk_bits[0]) - 1u;
+        const uint32_t m1 = a.nchunks > 1 ? (1u << a.chunk_bits[1]) - 1u : 0u;
+        double re[4], im[4];
+        longlong2 t0[4], t1[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4u; ++k) {
+          re[k] = im[k] = 0.0;
+          t0[k] = t1[k] = make_longlong2(0, 0);
+          if (aux[k] == 0ull) continue;
+          re[k] = __ldcs(s.re + ent[k]);
+          im[k] = __ldcs(s.im + ent[k]);
+          const uint32_t i0 = (uint32_t)(aux[k] >> a.chunk_shift[0]) & m0;
+          const uint32_t i1 = (uint32_t)(aux[k] >> a.chunk_shift[1]) & m1;
+          if (i0) t0[k] = __ldg(a.tables[0] + i0);
+          if (i1) t1[k] = __ldg(a.tables[1] + i1);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4u; ++k) {
+          if (aux[k] == 0ull) continue;
+          long long pr = 0, pi = 0;
+          int q = 62;
+          bool any = false;
+          if ((uint32_t)(aux[k] >> a.chunk_shift[0]) & m0) {
+            pr = t0[k].x;
+            pi = t0[k].y;
+            any = true;
+          }
+          if ((uint32_t)(aux[k] >> a.chunk_shift[1]) & m1) {
+            if (any) {
+              qmul(pr, pi, t1[k].x, t1[k].y);
+              q -= 2;
+            } else {
+              pr = t1[k].x;
+              pi = t1[k].y;
+              any = true;
+            }
+          }
+          for (uint32_t c = 2; c < a.nchunks; ++c) {
+            const uint32_t idx =
+                (uint32_t)(aux[k] >> a.chunk_shift[c]) & ((1u << a.chunk_bits[c]) - 1u);
+            if (idx == 0u) continue;
+            const longlong2 t = __ldg(a.tables[c] + idx);
+            if (any) {
+              qmul(pr, pi, t.x, t.y);
+              q -= 2;
+            } else {
+              pr = t.x;
+              pi = t.y;
+              any = true;
+            }
+          }
+          const double fr = q_to_double(pr, q), fi = q_to_double(pi, q);
+          if (im[k] == 0.0) {
+            s.re[ent[k]] = re[k] * fr;
+            s.im[ent[k]] = re[k] * fi;
+          } else {
+            s.re[ent[k]] = fma(re[k], fr, -(im[k] * fi));
+            s.im[ent[k]] = fma(re[k], fi, im[k] * fr);
+          }
         }
       }
     }
     __syncwarp();
   }
   if (a.has_perm) merge_label_masks(ctl, mg_wr(a.mg), mo0, mo1, ma0, ma1);
+}
+
+// Phase tables of a bit-sliced pass: entry idx of chunk c is the product of
+// the factors of the aux bits set in idx (fixed point, 2^62 = 1, each product
+// rounded to nearest), one thread per entry.
+__device__ __forceinline__ long long q62_mul(long long a, long long b) {
+  const long long hi = __mul64hi(a, b);
+  const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+  // (hi:lo) >> 62, rounded: bit 61 of lo is the half
+  return (long long)(((unsigned long long)hi << 2) | (lo >> 62)) + (long long)((lo >> 61) & 1ull);
+}
+
+__global__ void k_bs_tables(const longlong2* factors, longlong2* out, uint32_t bits,
+                            uint32_t shift) {
+  const uint32_t size = 1u << bits;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < size;
+       idx += gridDim.x * blockDim.x) {
+    long long re = 1ll << 62, im = 0;
+    for (uint32_t m = idx; m; m &= m - 1u) {
+      const longlong2 f = factors[shift + __ffs(m) - 1u];
+      const long long r = q62_mul(re, f.x) - q62_mul(im, f.y);
+      const long long i = q62_mul(re, f.y) + q62_mul(im, f.x);
+      re = r;
+      im = i;
+    }
+    out[idx] = make_longlong2(re, im);
+  }
+}
+
+// A fused run whose gates all resolved on the host still counts its updates.
+__global__ void k_count_updates(Ctl* ctl, uint32_t ngates, uint32_t fallback) {
+  if (ctl->status == 0u && !amp_took(ctl, fallback)) ctl->updates += ctl->nnz * ngates;
 }
 
 // ---------------------------------------------------------------------------
@@ -800,57 +968,120 @@ int grid_for(uint64_t work, int threads, int max_blocks) {
   return (int)b;
 }
 
-size_t bs_smem_fixed(const BsLaunch& b) {
-  return ((16 * (size_t)b.nops + 4096 * (size_t)b.nchunks + b.list_len + 15) & ~(size_t)15);
+// Shared memory of one block of the bit-sliced pass: 4 warps, each a tile of
+// rows x (G + 1) words.
+constexpr int kBsWarps = 4;
+size_t bs_block_smem(uint32_t rows, uint32_t G) {
+  return (size_t)kBsWarps * rows * (G + 1) * 4;
+}
+// Resident blocks per SM for a tile of G groups (registers and shared memory,
+// as the runtime computes them).
+template <int KW, int NW>
+int bs_blocks_per_sm(uint32_t rows, uint32_t G) {
+  const size_t smem = bs_block_smem(rows, G);
+  if (smem > 200 * 1024) return 0;
+  if (cudaFuncSetAttribute(k_fused_bs<KW, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int k = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_fused_bs<KW, NW>, kBsWarps * 32, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return k;
 }
 
-template <int KW>
+template <int KW, int NW>
 int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uint64_t nnz_bound,
                 unsigned long long* plog) {
-  BsArgs a;
-  a.ops = b.ops;
-  a.list = b.list;
-  a.tables = b.tables;
-  a.nops = b.nops;
-  a.ngates = b.ngates;
-  a.nw = b.nw;
-  a.na = b.na;
-  a.nchunks = b.nchunks;
-  a.has_perm = b.has_perm;
-  a.has_phase = b.has_phase;
-  a.has_cnt = b.has_cnt;
-  a.list_len = b.list_len;
-  a.fallback = b.fallback;
+  const BsPass& P = *b.plan;
+  if (P.op_words() > kBsMaxOps || P.nrows > 250) return 0;
   const int sms = sm_count(lc);
-  const size_t fixed = bs_smem_fixed(b);
-  const size_t rows = 32 * (size_t)(b.nw + b.na) + 1;
-  const size_t budget = 200 * 1024;
-  // groups per tile: enough tiles to give every resident warp work, else as
-  // many groups as fit (more groups per op walk = fewer instructions per entry)
-  // Measured on GB300 (adder, 4M entries): 8 groups per tile beat 16 and 32 -
-  // the op walk is latency-bound, so more resident warps win over fewer
-  // instructions per entry. Fewer groups when the state is small.
+  // groups per tile: the most (fewest instructions per entry) that still give
+  // every resident warp at least two tiles
   uint32_t G = b.groups;
-  int warps = 16;
   if (G == 0) {
-    G = 8;
-    while (G > 2 && (nnz_bound + 32ull * G - 1) / (32ull * G) < (uint64_t)sms * 16) G -= 2;
+    G = 4;
+    for (uint32_t g = 32; g >= 8; g >>= 1) {
+      const uint64_t tiles = (nnz_bound + 32ull * g - 1) / (32ull * g);
+      const uint64_t resident = (uint64_t)sms * bs_blocks_per_sm<KW, NW>(P.nrows, g) * kBsWarps;
+      if (tiles >= 2 * resident) {
+        G = g;
+        break;
+      }
+    }
   }
+  if (G < 2) G = 2;
+  if (G > 32) G = 32;
+  const int bps = bs_blocks_per_sm<KW, NW>(P.nrows, G);
+  if (bps < 1) return 0;
+  static thread_local BsArgs a;   // 16 KB of ops: keep it off the stack
+  std::memset(&a, 0, sizeof(a) - sizeof(a.ops));
+  static_assert(sizeof(BsArgs) < 32000, "kernel parameters must stay under 32 KB");
+  const uint32_t S = G + 1;
+  const uint32_t rb = 4u * S;     // bytes per row of a tile column
+  a.ngates = b.ngates;
   a.groups = G;
+  a.stride = S;
+  a.rows = P.nrows;
+  a.word_out = P.word_out;
+  for (uint32_t w = 0; w < 4; ++w) {
+    a.word_bits[w] = P.word_bits[w];
+    for (uint32_t j = 0; j < 32; ++j) a.row_of[w][j] = P.row_of[w][j];
+  }
+  a.aux_row0 = P.aux_row0;
+  a.naux = P.aux_bits;
+  a.ones_row = P.ones_row;
+  a.has_perm = b.has_perm;
+  a.has_phase = b.has_phase && P.aux_bits > 0;
+  a.has_cnt = P.has_cnt ? 1u : 0u;
+  a.nchunks = P.nchunks;
+  uint64_t toff = 0;
+  for (uint32_t c = 0; c < P.nchunks; ++c) {
+    a.chunk_shift[c] = P.chunk_shift[c];
+    a.chunk_bits[c] = P.chunk_bits[c];
+    a.tables[c] = reinterpret_cast<const longlong2*>(b.tables) + toff;
+    toff += 1ull << P.chunk_bits[c];
+  }
   a.mg = b.mg;
-  const size_t per_warp = rows * (G + 1) * 4;
-  while (warps > 1 && fixed + warps * per_warp > budget) warps >>= 1;
-  if (fixed + warps * per_warp > budget) return -1;
-  const size_t smem = fixed + warps * per_warp;
+  a.fallback = b.fallback;
+  auto off = [&](uint8_t r) -> uint32_t { return r == kNoRow ? 0u : (uint32_t)r * rb; };
+  uint32_t nw = 0;
+  for (size_t j = 0; j < P.ops.size(); ++j) {
+    const SOp& o = P.ops[j];
+    const bool general = o.kind != SOP_FLIP;
+    if (nw + (general && o.kind != SOP_AND ? 2u : 1u) > kBsMaxOps) return 0;
+    uint4 w;
+    w.x = off(o.c[0]);
+    w.y = off(o.c[1]);
+    w.z = off(o.c[2]);
+    w.w = off(o.t) | (general ? (kBsGeneral | ((uint32_t)o.kind << 24)) : 0u);
+    a.ops[nw++] = w;
+    if (general && o.kind != SOP_AND) {
+      uint4 e;
+      e.x = off(o.s);
+      e.y = off(o.f0);
+      e.z = off(o.f1);
+      e.w = (uint32_t)(o.a0 & 7u) | ((uint32_t)(o.a1 & 7u) << 8);
+      a.ops[nw++] = e;
+    }
+  }
+  a.nwords = nw;
+  cudaStream_t st = (cudaStream_t)lc.stream;
+  const int launched = b.build_tables ? launch_bs_tables(lc, b) : 0;
+  if (launched < 0) return -1;
+  const size_t smem = bs_block_smem(P.nrows, G);
   const uint64_t tiles = (nnz_bound + 32ull * G - 1) / (32ull * G);
-  uint64_t blocks = (tiles + warps - 1) / warps;
-  const int per_sm_blocks = (int)((227 * 1024) / (smem + 1024));
-  const uint64_t max_blocks = (uint64_t)sms * (per_sm_blocks > 0 ? per_sm_blocks : 1);
+  uint64_t blocks = (tiles + kBsWarps - 1) / kBsWarps;
+  const uint64_t max_blocks = (uint64_t)sms * bps;
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
-  cudaFuncSetAttribute(k_fused_bs<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_fused_bs<KW><<<(int)blocks, warps * 32, smem, (cudaStream_t)lc.stream>>>(ctl, bufs, a, plog);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  cudaFuncSetAttribute(k_fused_bs<KW, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_fused_bs<KW, NW><<<(int)blocks, kBsWarps * 32, smem, st>>>(ctl, bufs, a, plog);
+  return cudaPeekAtLastError() == cudaSuccess ? launched + 1 : -1;
 }
 
 BranchArgs branch_args(const BranchLaunch& b) {
@@ -918,11 +1149,33 @@ int launch_fused(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const 
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+int launch_bs_tables(const LaunchCfg& lc, const BsLaunch& b) {
+  const BsPass& P = *b.plan;
+  if (!(b.has_phase && P.aux_bits > 0)) return 0;
+  uint64_t toff = 0;
+  int launched = 0;
+  for (uint32_t c = 0; c < P.nchunks; ++c) {
+    const uint32_t size = 1u << P.chunk_bits[c];
+    const int blocks = (int)((size + 255) / 256);
+    k_bs_tables<<<blocks, 256, 0, (cudaStream_t)lc.stream>>>(
+        reinterpret_cast<const longlong2*>(b.factors), reinterpret_cast<longlong2*>(b.tables) + toff,
+        P.chunk_bits[c], P.chunk_shift[c]);
+    toff += size;
+    ++launched;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? launched : -1;
+}
+
 int launch_fused_bs(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
                     uint64_t nnz_bound, unsigned long long* plog) {
-  if (b.nops == 0) return 0;
-  return key_words == 1 ? fused_bs_kw<1>(lc, ctl, bufs, b, nnz_bound, plog)
-                        : fused_bs_kw<2>(lc, ctl, bufs, b, nnz_bound, plog);
+  if (b.plan == nullptr || b.plan->ops.empty()) return 0;
+  const uint32_t nw = b.plan->nw;
+  if (key_words == 1)
+    return nw <= 1 ? fused_bs_kw<1, 1>(lc, ctl, bufs, b, nnz_bound, plog)
+                   : fused_bs_kw<1, 2>(lc, ctl, bufs, b, nnz_bound, plog);
+  if (nw <= 2) return fused_bs_kw<2, 2>(lc, ctl, bufs, b, nnz_bound, plog);
+  return nw == 3 ? fused_bs_kw<2, 3>(lc, ctl, bufs, b, nnz_bound, plog)
+                 : fused_bs_kw<2, 4>(lc, ctl, bufs, b, nnz_bound, plog);
 }
 
 int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, Slot* table,

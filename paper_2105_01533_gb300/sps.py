@@ -29,7 +29,7 @@ SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
 SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP, SPS_OPT_BITSLICE_MIN_NNZ = 7, 8, 9
 SPS_OPT_BRANCH_FORM, SPS_OPT_BITSLICE_GROUPS, SPS_OPT_EXPAND, SPS_OPT_FOLD = 10, 11, 12, 13
 SPS_OPT_COMMUTE, SPS_OPT_LAYER_GATES, SPS_OPT_EXPAND_WALK, SPS_OPT_FUSED_LABELS = 14, 15, 16, 17
-SPS_OPT_AMP_ONLY = 18
+SPS_OPT_AMP_ONLY, SPS_OPT_BITSLICE_JIT = 18, 19
 KIND_SMALL_RUN, KIND_GATHER_BUILD, KIND_GATHER_EMIT = 4, 5, 6
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 
@@ -43,6 +43,7 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
            "sps_server_completed", "sps_probability_async", "sps_measure", "sps_pauli_exp",
+           "sps_jit_selftest",
            "sps_commute")
 
 
@@ -186,6 +187,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_server_stats.restype = st
     lib.sps_status_str.argtypes = [st]
     lib.sps_status_str.restype = ctypes.c_char_p
+    lib.sps_jit_selftest.argtypes = [vp, sz]
+    lib.sps_jit_selftest.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -402,6 +405,14 @@ def sps_branch_apply_static(gate, nqubits: int, in_arrays, n_in: int, prune_eps:
         _ptr(oh), _ptr(ol), _ptr(orr), _ptr(oi), out_cap, ctypes.byref(n), stream)
     _check(rc, "sps_branch_apply_static")
     return n.value
+
+
+def sps_jit_selftest():
+    """(ok, message): whether the runtime compiler builds the specialised
+    bit-sliced kernel of a sample run (host only, no GPU needed)."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    ok = load_library().sps_jit_selftest(buf, len(buf))
+    return bool(ok), buf.value.decode(errors="replace")
 
 
 def sps_status_str(code: int) -> str:

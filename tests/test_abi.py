@@ -126,3 +126,10 @@ def test_plan_rejects_bad_records(lib):
 
 def test_plan_of_empty_stream(lib):
     assert sps.sps_plan(np.zeros(0, W.GATE_DTYPE), 10) == []
+
+
+def test_runtime_compiler_builds_the_specialised_kernel(lib):
+    """The bit-sliced pass specialised per run (SPS_OPT_BITSLICE_JIT) is
+    generated and compiled for sm_103a on the host; no GPU is needed."""
+    ok, msg = sps.sps_jit_selftest()
+    assert ok, msg

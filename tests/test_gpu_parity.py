@@ -396,21 +396,26 @@ def perm_diag_run(seed, n, ngates, max_controls=5, p_arbitrary=0.15):
 
 
 @pytest.mark.parametrize("n", [9, 24, 40, 64, 100, 127])
-@pytest.mark.parametrize("min_ops", [1, 0])
-def test_bitslice_and_direct_long_runs(n, min_ops):
+@pytest.mark.parametrize("min_ops,jit", [(1, 0), (0, 0), (1, 2)])
+def test_bitslice_and_direct_long_runs(n, min_ops, jit):
+    """Long phase/permutation runs in the direct form, the general bit-sliced
+    kernel and the bit-sliced kernel compiled for the run (jit 2)."""
     rng = W.SplitMix64(n)
     k = min(n, 12)
     prep = W.to_array([W.H(q) for q in rng.distinct(n, k)] + [W.Ry(rng.below(n), 0.77)])
     gates = np.concatenate([prep, perm_diag_run(100 + n, n, 300)])
     got, want = run_both(n, gates, eps=1e-14, capacity=1 << 14,
                          options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, min_ops),
-                                  (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
+                                  (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0),
+                                  (sps.SPS_OPT_BITSLICE_JIT, jit)])
     compare_states(got, want, 1e-14)
 
 
-def test_bitslice_many_phase_slots_and_split():
+@pytest.mark.parametrize("jit", [0, 2])
+def test_bitslice_many_phase_slots_and_split(jit):
     """More arbitrary phases than one pass holds: 70 Rz (140 fire slots) plus
-    40 P; the compiler splits the run, each part uses two aux words."""
+    40 P; the compiler splits the run, each part uses two aux words and up to
+    four phase tables."""
     n = 30
     rng = W.SplitMix64(77)
     prep = [W.H(q) for q in range(10)]
@@ -422,21 +427,25 @@ def test_bitslice_many_phase_slots_and_split():
     plan = sps.sps_plan(gates, n)
     assert sum(1 for k, _, _ in plan if k == 1) >= 2
     got, want = run_both(n, gates, eps=1e-14, options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1),
-                                                       (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0)])
+                                                       (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0),
+                                                       (sps.SPS_OPT_BITSLICE_JIT, jit)])
     compare_states(got, want, 1e-14)
 
 
-@pytest.mark.parametrize("nnz_log2,groups", [(5, 0), (10, 0), (15, 0), (17, 0), (15, 2),
-                                             (17, 8), (17, 32)])
-def test_bitslice_sizes(nnz_log2, groups):
-    """Tiles of 1..32 groups and a ragged tail: 2^k entries plus a few."""
+@pytest.mark.parametrize("nnz_log2,groups,jit", [(5, 0, 0), (10, 0, 0), (15, 0, 0), (17, 0, 0),
+                                                 (15, 2, 0), (17, 8, 0), (17, 32, 0), (5, 0, 2),
+                                                 (12, 0, 2), (17, 0, 2)])
+def test_bitslice_sizes(nnz_log2, groups, jit):
+    """Tiles of 1..32 groups and a ragged tail: 2^k entries plus a few (the
+    compiled form always takes tiles of 32 groups)."""
     n = 70
     prep = [W.H(q) for q in range(nnz_log2)] + [W.Ry(40, 0.3, 0)] + [W.H(41, 1)]
     gates = np.concatenate([W.to_array(prep), perm_diag_run(9, n, 200, max_controls=3)])
     got, want = run_both(n, gates, eps=1e-14, capacity=1 << 19,
                          options=[(sps.SPS_OPT_BITSLICE_MIN_OPS, 1),
                                   (sps.SPS_OPT_BITSLICE_MIN_NNZ, 0), (sps.SPS_OPT_SMALL_RUN_CAP, 0),
-                                  (sps.SPS_OPT_BITSLICE_GROUPS, groups)])
+                                  (sps.SPS_OPT_BITSLICE_GROUPS, groups),
+                                  (sps.SPS_OPT_BITSLICE_JIT, jit)])
     compare_states(got, want, 1e-14)
     assert len(got[1]) > (1 << nnz_log2)
 
