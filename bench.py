@@ -1,17 +1,22 @@
 """Benchmark: nonzero-amplitude updates/s of the sparse-state gate path.
 
-Workload (default ``adder67``): 67 qubits with 128-bit labels; H on the low
-16 bits of register a (65,536 nonzeros), X gates loading a seeded 32-bit
-constant into b, a 32-bit ripple-carry adder, 32 controlled-phase gates on
-seeded pairs of a/b qubits, then the inverse adder; FP64 amplitudes, prune
-eps 1e-14. Other workloads: ``adder67-w24`` (a over 24 bits, 16.8 M nonzeros),
-``givens64`` (64 qubits, 4 occupied modes, 500 Givens/CZ layers).
+Headline workload (default ``adder67-w24``, the larger-than-L2 reversible
+arithmetic config): 67 qubits with 128-bit labels; H on the low 24 bits of
+register a (16,777,216 nonzeros, a 537 MB state), X gates loading a seeded
+32-bit constant into b, a 32-bit ripple-carry adder, 32 controlled-phase gates
+on seeded pairs of a/b qubits, then the inverse adder; FP64 amplitudes, prune
+eps 1e-14. Other workloads: ``adder67`` (a over 16 bits, L2-resident),
+``adder67-w22``, ``givens64`` (64 qubits, 4 occupied modes, 500 Givens/CZ
+layers), ``givens64-m5`` / ``givens64-m6`` (5 / 6 occupied modes, the
+7,624,512- / 74,974,368-label sectors: a block of layers on a filled sector).
 
 A step = reset to |0...0>, apply the whole gate stream (every branching pass
 and fused phase/permutation pass), read the probability of one register value
-back (the readout kernels). Updates per step U = sum over gates of the nonzero
+back (the readout kernel). Updates per step U = sum over gates of the nonzero
 count before the gate. ``value`` = U * steps / (sum of per-step device times);
 L2 is flushed (a 512 MB write) between timed steps, outside the timed events.
+The default run adds sub-lines for the other configs, the batched and the
+served forms.
 
 ``--impl reference`` times the CPU oracle (the only reference this method has)
 on a bounded sample of the same workload on the host cores.
@@ -48,6 +53,9 @@ L2_FLUSH_BYTES = 512 << 20
 
 # ---- workloads -------------------------------------------------------------------
 def make_workload(name: str):
+    """A workload: its gates, qubits, capacity and readout. Block workloads
+    (``block`` set) prepare a state with ``prep`` untimed and time applies of
+    ``block`` on it."""
     if name == "adder67":
         wl = W.adder_workload(seed=1, width=16)
         return dict(name=name, gates=wl.gates, nqubits=wl.layout.nqubits, capacity=1 << 17,
@@ -58,8 +66,9 @@ def make_workload(name: str):
         wl = W.adder_workload(seed=1, width=24)
         return dict(name=name, gates=wl.gates, nqubits=wl.layout.nqubits, capacity=1 << 25,
                     readout=((0xFFFF, 0), (0, 0)),
-                    desc="adder67-w24: as adder67 with a over 24 bits (16,777,216 nonzeros, "
-                         "537 MB state)")
+                    desc="adder67-w24: 67 qubits, 128-bit labels, H on a[0..23] (16,777,216 "
+                         "nonzeros, 537 MB state), 32-bit ripple-carry adder, 32 CP gates, inverse "
+                         "adder; FP64, eps 1e-14")
     if name == "adder67-w22":
         wl = W.adder_workload(seed=1, width=22)
         return dict(name=name, gates=wl.gates, nqubits=wl.layout.nqubits, capacity=1 << 22,
@@ -72,6 +81,19 @@ def make_workload(name: str):
                     readout=((0xFF, 0), (0x0F, 0)),
                     desc="givens64: 64 qubits, 4 occupied modes (<= 635,376 nonzeros), 500 layers "
                          "of 32 Givens + 32 CZ; FP64, eps 1e-14")
+    if name in ("givens64-m5", "givens64-m6"):
+        modes = 5 if name.endswith("m5") else 6
+        prep_layers, block_layers = 12, (8 if modes == 5 else 4)
+        g = W.givens_workload(seed=2, nqubits=64, modes=modes, layers=prep_layers + block_layers)
+        cut = modes + 64 * prep_layers
+        size = math.comb(64, modes)
+        return dict(name=name, gates=g[cut:], prep=g[:cut], nqubits=64,
+                    capacity=size + 4096, readout=((0xFF, 0), (0x1F, 0)), block=True,
+                    desc="%s: 64 qubits, %d occupied modes (the %s-label sector, %d MB); a step "
+                         "applies %d layers of 32 Givens + 32 CZ to the state left by %d seeded "
+                         "layers (untimed); FP64, eps 1e-14" % (
+                             name, modes, "{:,}".format(size), size * 32 >> 20, block_layers,
+                             prep_layers))
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -193,24 +215,63 @@ def measured_peaks():
 KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact", 4: "k_small_run",
               5: "k_gather_build", 6: "k_gather_emit", 7: "k_expand", 8: "k_measure",
               9: "k_amp_index", 10: "k_amp_layer"}
+ACCOUNTING = ("bytes of the method's passes: 2*B*n per fused phase/permutation pass, "
+              "B*(n_in + n_out) per branching pass, B = 24 (64-bit labels) or 32 (128-bit) "
+              "bytes per entry; index builds count the labels they read")
+
+
+def kernel_name(r) -> str:
+    if r["kind"] == 1 and r["flags"] & 16:
+        return "k_bs_jit"
+    if r["kind"] == 1 and r["flags"] & 8:
+        return "k_fused_bs"
+    return KIND_NAMES[r["kind"]]
 
 
 def algorithmic_bytes(r) -> float:
-    """Bytes a launch must move at minimum: a fused pass reads
-    every label, writes it back if the pass permutes, and reads and writes the
-    amplitude if the pass has phases; a branching pass reads the old state
-    (emit) and writes the new one (compaction)."""
+    """Bytes of the passes of the method one launch carries out: a fused
+    phase/permutation pass reads and writes the state (2*B*n), a branching
+    pass reads the old state and writes the new one (B*(n_in + n_out)); a
+    launch that carries out several passes (an expansion of d gates, an
+    amplitude-only run of d gates, a layer) is credited with each of them."""
     lb = r["label_bytes"]
-    if r["kind"] == 1:
-        per = lb + (lb if r["flags"] & 1 else 0) + (32 if r["flags"] & 2 else 0)
-        return per * r["n_in"]
-    if r["kind"] == 2:
-        return (lb + 16) * r["n_in"]
-    if r["kind"] in (4, 6, 7, 10):   # read the old state once, write the new one once
-        return (lb + 16) * (r["n_in"] + r["n_out"])
-    if r["kind"] in (5, 9):   # index the input labels
-        return lb * r["n_in"]
-    return (lb + 16) * r["n_out"]
+    B = lb + 16
+    k, n_in, n_out, d = r["kind"], r["n_in"], r["n_out"], max(1, r["nops"])
+    if k == 1:
+        return 2.0 * B * n_in
+    if k == 7:   # d gates, each doubling the entries: B * (m + 2m) for m = n_in, 2 n_in, ...
+        b = 3.0 * B * n_in * ((1 << min(d, 60)) - 1)
+        if r["flags"] & 4:   # and the fused run walked on its outputs
+            b += 2.0 * B * n_out
+        return b
+    if k == 10:   # d gates on a state whose labels stay (n_out > 0: the attempt took them)
+        b = 2.0 * B * n_out * d
+        if r["flags"] & 4:
+            b += 2.0 * B * n_out
+        return b
+    if k == 6 and d > 1 and n_in > 0:   # a layer: d passes from n_in to n_out entries
+        q = (n_out / n_in) ** (1.0 / d) if n_out > 0 else 1.0
+        return sum(B * n_in * q ** j * (1.0 + q) for j in range(d))
+    if k in (5, 9):   # label index of a gather or amplitude-only pass
+        return float(lb * n_in)
+    if k == 2:
+        return float(B * n_in)
+    if k == 3:
+        return float(B * n_out)
+    return float(B * (n_in + n_out))
+
+
+def moved_bytes(r) -> float:
+    """The least traffic the launch itself needs: every entry it reads read
+    once, every entry it writes written once."""
+    lb = r["label_bytes"]
+    B = lb + 16
+    k, n_in, n_out = r["kind"], r["n_in"], r["n_out"]
+    if k == 1:
+        return float((lb + (lb if r["flags"] & 1 else 0) + (32 if r["flags"] & 2 else 0)) * n_in)
+    if k == 10:   # labels stay: amplitudes read and written, labels read by the lookups
+        return float((32 + lb) * n_out)
+    return algorithmic_bytes(r) if k in (2, 3, 5, 9) else float(B * (n_in + n_out))
 
 
 def kernel_source_hash() -> str:
@@ -236,29 +297,37 @@ def ncu_traffic(kernel: str, workload: str, n_per_launch: float):
     return e["dram_bytes_per_entry"] * n_per_launch
 
 
-def roofline(records, workload: str):
+def roofline(records, workload: str, steps: int):
+    """The dominant kernel (by time over `steps` profiled steps): its
+    algorithmic bytes per launch over its average launch time."""
     peak, which = measured_peaks()
     by = {}
     for r in records:
-        b = by.setdefault(r["kind"], {"ms": 0.0, "bytes": 0.0, "n": 0, "entries": 0})
+        b = by.setdefault(kernel_name(r), {"ms": 0.0, "bytes": 0.0, "moved": 0.0, "n": 0,
+                                           "entries": 0})
         b["ms"] += r["ms"]
         b["bytes"] += algorithmic_bytes(r)
+        b["moved"] += moved_bytes(r)
         b["n"] += 1
         # entries a launch processes: outputs for a compaction or an expansion
-        b["entries"] += r["n_out"] if r["kind"] in (3, 7) else r["n_in"]
+        b["entries"] += r["n_out"] if r["kind"] in (3, 7, 10) else r["n_in"]
     total = sum(b["ms"] for b in by.values()) or 1.0
-    kind = max(by, key=lambda k: by[k]["ms"])
-    b = by[kind]
+    kern = max(by, key=lambda k: by[k]["ms"])
+    b = by[kern]
     avg_ms = b["ms"] / b["n"]
     avg_bytes = b["bytes"] / b["n"]
     achieved = avg_bytes / (avg_ms * 1e-3) / 1e9
-    share = {KIND_NAMES[k]: round(v["ms"] / total, 4) for k, v in by.items()}
-    traffic = ncu_traffic(KIND_NAMES[kind], workload, b["entries"] / b["n"])
-    return {"bound": "hbm", "kernel": KIND_NAMES[kind], "achieved": round(achieved, 2),
-            "peak": peak, "peak_source": which + " (MEASURED_PEAKS.json hbm_gbs)" if which == "measured"
+    share = {k: round(v["ms"] / total, 4) for k, v in by.items()}
+    traffic = ncu_traffic(kern, workload, b["entries"] / b["n"])
+    return {"bound": "hbm", "kernel": kern, "achieved": round(achieved, 2), "peak": peak,
+            "peak_source": which + " (MEASURED_PEAKS.json hbm_gbs)" if which == "measured"
             else "fallback 6800 GB/s", "unit": "GB/s", "frac": round(achieved / peak, 4),
             "traffic": traffic, "algorithmic_bytes_per_launch": round(avg_bytes),
-            "avg_launch_ms": round(avg_ms, 5), "launches_per_step": None,
+            "accounting": ACCOUNTING,
+            "moved_bytes_per_launch": round(b["moved"] / b["n"]),
+            "achieved_moved": round(b["moved"] / b["n"] / (avg_ms * 1e-3) / 1e9, 2),
+            "avg_launch_ms": round(avg_ms, 5),
+            "launches_per_step": round(b["n"] / max(1, steps), 2),
             "time_share": share}
 
 
@@ -275,6 +344,25 @@ def updates_per_step(sps, wl, st) -> tuple:
         st.apply(wl["gates"][first:bounds[j + 1]], EPS)
         nnz = st.nnz()
     return u, nnz
+
+
+def profiled_steps(sps, torch, st, step, flush, stream, nsteps):
+    """Per-kernel records of `nsteps` steps, every launch bracketed by CUDA
+    events on the state's stream (kept out of the headline timing)."""
+    st.set_option(sps.SPS_OPT_PROFILE, 1)
+    st.profile_read()
+    records = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(nsteps)]
+    for i in range(nsteps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        records += st.profile_read()
+    torch.cuda.synchronize()
+    st.set_option(sps.SPS_OPT_PROFILE, 0)
+    return records, sum(a.elapsed_time(b) for a, b in ev) / max(1, nsteps)
 
 
 def run_ours(args, dist, rank, world, local_rank):
@@ -333,23 +421,8 @@ def run_ours(args, dist, rank, world, local_rank):
     clocks = sampler.stop() if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
 
-    # per-kernel times: the same steps again with every launch bracketed by
-    # CUDA events on the state's stream (kept out of the headline timing)
-    st.set_option(sps.SPS_OPT_PROFILE, 1)
-    st.profile_read()
-    records = []
     prof_steps = min(args.steps, 20)
-    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(prof_steps)]
-    for i in range(prof_steps):
-        flush.zero_()
-        pev[i][0].record(stream)
-        step()
-        pev[i][1].record(stream)
-        records += st.profile_read()
-    torch.cuda.synchronize()
-    st.set_option(sps.SPS_OPT_PROFILE, 0)
-    prof_ms = sum(a.elapsed_time(b) for a, b in pev) / prof_steps
+    records, prof_ms = profiled_steps(sps, torch, st, step, flush, stream, prof_steps)
     if args.dump_profile and rank == 0:
         per_step = len(records) // prof_steps
         with open(args.dump_profile, "w") as f:
@@ -362,8 +435,7 @@ def run_ours(args, dist, rank, world, local_rank):
     # end to end through the public API with host buffers
     e2e = run_e2e(args, sps, torch, wl, st, flush, U, dist)
 
-    rl = roofline(records, wl["name"])
-    rl["launches_per_step"] = round(launches / args.steps, 2)
+    rl = roofline(records, wl["name"], prof_steps)
     rl["profiled_steps"] = prof_steps
     rl["profiled_ms_per_step"] = round(prof_ms, 5)
     res = None
@@ -382,32 +454,99 @@ def run_ours(args, dist, rank, world, local_rank):
                "p99_step_ms": round(float(np.percentile(step_ms, 99)), 5)}
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
-    if args.batched and wl["name"].startswith("adder67"):
+    st.close()
+    del flush
+    if args.sublines and rank == 0:
+        subs = {}
+        for name in args.sublines.split(","):
+            if name and name != wl["name"]:
+                subs[name] = run_sub(args, sps, torch, name)
+        if res is not None:
+            res["sublines"] = subs
+    if args.batched:
         bres = run_batched(args, sps, torch, args.batch_count, steps=args.batch_steps,
                            warmup=1, dist=dist, rank=rank, world=world)
         if res is not None:
             res["batched"] = bres
-    if args.served and wl["name"].startswith("adder67") and rank == 0:
+    if args.served and rank == 0:
         sres = run_served(args, sps, torch, args.serve_count, args.serve_seconds)
         if res is not None:
             res["served"] = sres
-    st.close()
     return res
+
+
+def run_sub(args, sps, torch, name: str):
+    """One more config on its own state: the same step (or, for a block
+    workload, applies of the block on the prepared state), its own roofline."""
+    wl = make_workload(name)
+    st = sps.SparseState(wl["nqubits"], wl["capacity"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    mask, val = wl["readout"]
+    out = torch.zeros(4096, dtype=torch.float64, device="cuda")
+    slot = [0]
+    block = wl.get("block", False)
+    t0 = time.perf_counter()
+    if block:
+        st.apply(wl["prep"], EPS)
+        st.sync()
+
+    def step():
+        if not block:
+            st.reset()
+        st.apply(wl["gates"], EPS)
+        st.probability_async(mask, val, out.data_ptr() + 8 * (slot[0] % 4096))
+        slot[0] += 1
+
+    warm = 2 if block else 3
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    steps = args.sub_steps
+    u0 = st.updates()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    c0 = st.counters().kernel_launches
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = st.counters().kernel_launches - c0
+    U = st.updates() - u0 if block else None
+    if not block:   # the update counter restarts at each reset: one step's count
+        U = st.updates() * steps
+    nnz = st.nnz()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    prof = min(steps, 3)
+    records, prof_ms = profiled_steps(sps, torch, st, step, flush, stream, prof)
+    st.close()
+    del flush
+    total = sum(ms)
+    rl = roofline(records, name, prof)
+    rl["profiled_steps"] = prof
+    return {"workload": wl["desc"], "value": round(U / (total * 1e-3), 1), "unit": UNIT,
+            "ms_per_step": round(total / steps, 5), "steps": steps,
+            "updates_per_step": int(U // steps), "nnz": int(nnz),
+            "gpu_launches_per_step": round(launches / steps, 1), "roofline": rl,
+            "prepare_s": round(prep_s, 2)}
 
 
 def run_e2e(args, sps, torch, wl, st, flush, U, dist):
     """Same metric through the public calls with host buffers: every step
-    copies the gate records from host memory (inside sps_apply) and reads the
-    whole final state back into pinned host arrays."""
-    n = st.nnz()
-    pin = lambda dt: torch.empty(max(n, 1), dtype=dt, pin_memory=True).numpy()  # noqa: E731
-    hi, lo, re, im = pin(torch.int64).view(np.uint64), pin(torch.int64).view(np.uint64), \
-        pin(torch.float64), pin(torch.float64)
+    compiles the gate records from host memory and uploads the plan (the
+    apply-plan cache is off, so nothing of the previous step is reused), and
+    reads the step's result (the probability) back to the host."""
+    mask, val = wl["readout"]
+    st.set_option(sps.SPS_OPT_PLAN_CACHE, 0)
     k = max(3, args.steps // 4)
     for _ in range(2):
         st.reset()
         st.apply(wl["gates"], EPS)
-        sps.sps_get_amplitudes(st.handle, hi, lo, re, im, len(lo))
+        st.probability(mask, val)
+    b0 = st.counters().upload_bytes
     total = 0.0
     for _ in range(k):
         flush.zero_()
@@ -415,13 +554,17 @@ def run_e2e(args, sps, torch, wl, st, flush, U, dist):
         t0 = time.perf_counter()
         st.reset()
         st.apply(wl["gates"], EPS)
-        got = sps.sps_get_amplitudes(st.handle, hi, lo, re, im, len(lo))
+        st.probability(mask, val)
         total += time.perf_counter() - t0
+    up = (st.counters().upload_bytes - b0) / k
+    st.set_option(sps.SPS_OPT_PLAN_CACHE, 1)
     total = max_over_ranks(dist, total)
     units = sum_over_ranks(dist, float(U) * k)
     return {"value": round(units / total, 1), "unit": UNIT,
-            "h2d_bytes_per_step": int(wl["gates"].nbytes), "d2h_bytes_per_step": int(got * 32 + 64),
-            "steps": k}
+            "h2d_bytes_per_step": int(up), "d2h_bytes_per_step": 8,
+            "gate_record_bytes": int(wl["gates"].nbytes), "steps": k,
+            "what": "reset, sps_apply of host gate records (compiled and the plan uploaded "
+                    "each step), sps_probability read back; wall clock"}
 
 
 # ---- batched form -----------------------------------------------------------------------
@@ -459,9 +602,18 @@ def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_ev
         assert left == 0
     ms = [a.elapsed_time(e) for a, e in ev]
     failed = sum(1 for i in range(len(circs)) if b.status(i)["status"] != 0)
+    # the same launches timed by the host clock (the clock the plain path uses)
+    torch.cuda.synchronize()
+    tw = time.perf_counter()
+    for i in range(steps):
+        b.reset()
+        b.run()
+        b.sync()
+    wall_s = time.perf_counter() - tw
     b.close()
     tot_upd, tot_s = shard.reduce_totals(float(upd) * steps, sum(ms) * 1e-3)
     batched_rate = tot_upd / tot_s
+    batched_wall_rate = float(upd) * steps / wall_s
     # the plain path on a sample of the same circuits, one circuit at a time
     sample = circs[::sample_every]
     sb = sps.Batch()
@@ -485,6 +637,7 @@ def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_ev
     for st in states.values():
         st.close()
     plain_rate = upd_s / plain_s
+    cpu = batch_cpu_baseline(circs, args.batch_cpu_every) if rank == 0 and args.batch_cpu_every else None
     return {"workload": "batched%d: qubits U{20..100}, depth U{200..5000}, caps 2^U[8,16], "
                         "mix 70%% X/CNOT/Toffoli, 20%% Z/S/T/CRz, 10%% H within the cap; FP64, "
                         "eps 1e-14" % count,
@@ -493,11 +646,47 @@ def run_batched(args, sps, torch, count: int, steps: int, warmup: int, sample_ev
             "scaling": "weak" if world > 1 else None, "ranks": world,
             "ms_per_step": round(float(np.median(ms)), 3), "steps": steps,
             "launches_per_step": 1, "failed_circuits": failed, "tuned_config": tuned,
+            "value_wall_clock": round(batched_wall_rate, 1),
             "plain_value": round(plain_rate, 1),
             "plain_sample": "every %dth circuit (%d circuits), one sps_apply + sync each, "
-                            "wall clock" % (sample_every, len(sample)),
-            "batched_vs_plain": round(batched_rate / plain_rate, 2),
-            "generate_s": round(gen_s, 1)}
+                            "host wall clock" % (sample_every, len(sample)),
+            "batched_vs_plain": round(batched_wall_rate / plain_rate, 2),
+            "batched_vs_plain_clock": "both by the host wall clock (batched: reset + launch + "
+                                      "sync per step)",
+            "cpu_baseline": cpu, "generate_s": round(gen_s, 1)}
+
+
+def _oracle_circuit(job):
+    """One circuit on the CPU oracle (worker process): (updates, seconds)."""
+    from oracle import OracleState
+    nq, gates = job
+    t0 = time.perf_counter()
+    orc = OracleState(nq)
+    u = orc.apply_counted(gates, eps=EPS)
+    return u, time.perf_counter() - t0
+
+
+def batch_cpu_baseline(circs, every: int):
+    """The oracle over a sample of the batch (every `every`-th circuit) on a
+    pool of all host cores, one circuit per task, largest first; updates per
+    second of wall clock."""
+    import multiprocessing as mp
+    sample = sorted(circs[::every], key=lambda c: -len(c.gates) * c.cap)
+    jobs = [(c.nqubits, c.gates) for c in sample]
+    ncores = os.cpu_count() or 1
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        pool.map(_oracle_circuit, [(20, jobs[0][1][:1])] * ncores)   # workers up
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_circuit, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    upd = sum(u for u, _ in res)
+    return {"value": round(upd / wall, 1), "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": "every %dth circuit of the batch (%d circuits, %d gates), one circuit per "
+                      "task on a pool of %d processes, wall clock %.1f s" % (
+                          every, len(jobs), sum(len(j[1]) for j in jobs), ncores, wall),
+            "cpu": cpu_model()}
 
 
 # ---- served form ------------------------------------------------------------------------
@@ -602,37 +791,58 @@ def run_served(args, sps, torch, count: int, arrive_s: float):
 
 
 # ---- the oracle on the host ------------------------------------------------------------
-def oracle_rate(wl, budget_s: float, prefix_cache={}):
+def oracle_rate(wl, budget_s: float):
     """Run the oracle over the gate stream (gate by gate, single thread) until
     the budget is used; returns (updates, seconds, gates_done)."""
     from oracle import OracleState
     gates = wl["gates"]
     orc = OracleState(wl["nqubits"])
+    if wl.get("block"):
+        orc.apply(wl["prep"], eps=EPS)
     u, done, t = 0, 0, 0.0
     while done < len(gates) and t < budget_s:
-        nnz = orc.nnz()
         t0 = time.perf_counter()
-        orc.apply(gates[done:done + 1], eps=EPS)
+        u += orc.apply_counted(gates[done:done + 1], eps=EPS)
         t += time.perf_counter() - t0
-        u += nnz
         done += 1
     return u, t, done
 
 
 def cpu_baseline(wl, budget_s: float):
-    u, t, done = oracle_rate(wl, budget_s)
-    return {"value": round(u / t, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first %d of %d gates of %s, gate by gate, one host thread (%.1f s)" % (
-                done, len(wl["gates"]), wl["name"], t),
-            "cpu": cpu_model(), "nproc": os.cpu_count()}
+    """The oracle on one host thread, median of three runs of the same bounded
+    sample (the first gates of the stream, as many as fit the budget)."""
+    runs = [oracle_rate(wl, budget_s / 3.0) for _ in range(3)]
+    rates = sorted(u / t for u, t, _ in runs)
+    done = min(d for _, _, d in runs)
+    return {"value": round(rates[1], 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d gates of %s from |0..0>, gate by gate, one host thread; "
+                      "median of 3 runs (%.1f s each)" % (done, len(wl["gates"]), wl["name"],
+                                                          budget_s / 3.0),
+            "runs": [round(r, 1) for r in rates], "cpu": cpu_model(), "nproc": os.cpu_count()}
 
 
 def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; Arm parts are
+    named from their part number)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                if name and name != "-":
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    arm_parts = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1"}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu part")):
+                key = line.lower()
+                if key.startswith("model name"):
                     return line.split(":", 1)[1].strip()
+                if key.startswith("cpu part"):
+                    part = line.split(":", 1)[1].strip()
+                    return arm_parts.get(part, "Arm CPU part " + part)
     except OSError:
         pass
     return "unknown"
@@ -675,8 +885,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="adder67",
-                    choices=["adder67", "adder67-w22", "adder67-w24", "givens64"])
+    ap.add_argument("--workload", default="adder67-w24",
+                    choices=["adder67", "adder67-w22", "adder67-w24", "givens64", "givens64-m5",
+                             "givens64-m6"])
+    ap.add_argument("--sublines", default="adder67,givens64,givens64-m5,givens64-m6",
+                    help="comma-separated configs measured after the headline ('' for none)")
+    ap.add_argument("--sub-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--opt", action="append", default=[],
@@ -689,6 +903,8 @@ def main():
     ap.add_argument("--serve-count", type=int, default=2000)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--batch-cpu-every", type=int, default=8,
+                    help="all-core oracle baseline on every k-th batched circuit (0: skip)")
     ap.add_argument("--dump-profile", default=None,
                     help="write the per-launch records of one profiled step to this JSON file")
     args = ap.parse_args()

@@ -314,7 +314,13 @@ typedef enum sps_option {
                                   bound before the pass is at least 2^20, 2
                                   always. Where the runtime compiler is missing
                                   or a compile fails the general kernel runs;
-                                  the results are the same */
+                                  the results are the same */,
+  SPS_OPT_PLAN_CACHE = 20      /* 1 (default): an sps_apply identical to the
+                                  previous one (gates, threshold, options,
+                                  starting knowledge, nonzero bound) reuses its
+                                  compiled plan and the device copy of it; 0:
+                                  every sps_apply compiles its gates and uploads
+                                  the plan */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:
@@ -327,6 +333,7 @@ typedef struct sps_counters {
   uint64_t fused_passes;     /* per-element phase/permutation passes enqueued */
   uint64_t branch_passes;    /* branching passes enqueued */
   uint64_t kernel_launches;  /* kernels enqueued by this state */
+  uint64_t upload_bytes;     /* compiled plans copied host -> device by sps_apply */
 } sps_counters;
 sps_status sps_get_counters(sps_state* s, sps_counters* out);
 
@@ -339,7 +346,10 @@ sps_status sps_get_counters(sps_state* s, sps_counters* out);
  * skipped), 10 amplitude-only attempt (n_out 0 when it did not take the pass;
  * then kinds 5 and 6 follow with n_in > 0; they show n_in 0 when skipped).
  * n_in: entries the kernel read; n_out: entries in the state after it. flags: bit 0 the
- * pass permutes labels, bit 1 it changes amplitudes. label_bytes: 8 or 16. */
+ * pass permutes labels, bit 1 it changes amplitudes, bit 2 (kinds 7 and 10) the
+ * launch also applied the phase/permutation run after the branching gates,
+ * bit 3 (kind 1) bit-sliced form, bit 4 (kind 1) the form compiled for this
+ * run (SPS_OPT_BITSLICE_JIT). label_bytes: 8 or 16. */
 typedef struct sps_kernel_record {
   uint32_t kind;
   uint32_t pass_serial;

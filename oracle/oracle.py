@@ -61,6 +61,8 @@ def _load():
     lib.orc_nnz.restype = u64
     lib.orc_apply.argtypes = [vp, vp, u64, dbl, i32, pu64]
     lib.orc_apply.restype = i32
+    lib.orc_apply_counted.argtypes = [vp, vp, u64, dbl, i32, pu64, pu64]
+    lib.orc_apply_counted.restype = i32
     lib.orc_get.argtypes = [vp, vp, vp, vp, vp, u64]
     lib.orc_get.restype = i32
     lib.orc_set.argtypes = [vp, vp, vp, vp, vp, u64]
@@ -123,6 +125,18 @@ class OracleState:
                                  ctypes.byref(bad))
         if rc != 0:
             raise ValueError("invalid gate record at index %d" % bad.value)
+
+    def apply_counted(self, gates, eps: float = 0.0, mode: int = 0) -> int:
+        """As apply(); returns the sum over gates of the entries stored before
+        each gate."""
+        g = _gate_buffer(gates)
+        bad = ctypes.c_uint64(0)
+        upd = ctypes.c_uint64(0)
+        rc = self._lib.orc_apply_counted(self._h, _ptr(g), g.size, float(eps), int(mode),
+                                         ctypes.byref(bad), ctypes.byref(upd))
+        if rc != 0:
+            raise ValueError("invalid gate record at index %d" % bad.value)
+        return int(upd.value)
 
     def nnz(self) -> int:
         return int(self._lib.orc_nnz(self._h))

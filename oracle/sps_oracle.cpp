@@ -325,7 +325,11 @@ uint64_t orc_nnz(void* h) { return static_cast<State*>(h)->map.size(); }
 
 // Applies ngates records in order. Returns 0, or 1 with *bad = index of the
 // first invalid record (nothing after it is applied; gates before it are).
-int orc_apply(void* h, const void* gates, uint64_t ngates, double eps, int mode, uint64_t* bad) {
+// Applies the gates in order. If `updates` is not null it receives the sum over
+// gates of the number of stored entries before each gate (the work count the
+// benchmark reports as nonzero-amplitude updates).
+int orc_apply_counted(void* h, const void* gates, uint64_t ngates, double eps, int mode,
+                      uint64_t* bad, uint64_t* updates) {
   State* st = static_cast<State*>(h);
   const GateRec* g = static_cast<const GateRec*>(gates);
   for (uint64_t i = 0; i < ngates; ++i) {
@@ -333,6 +337,7 @@ int orc_apply(void* h, const void* gates, uint64_t ngates, double eps, int mode,
       if (bad) *bad = i;
       return 1;
     }
+    if (updates) *updates += st->map.size();
     if (kind_of(g[i].op) == PERM_DIAG) {
       apply_perm_diag(*st, g[i]);
     } else if (mode == 1) {
@@ -342,6 +347,10 @@ int orc_apply(void* h, const void* gates, uint64_t ngates, double eps, int mode,
     }
   }
   return 0;
+}
+
+int orc_apply(void* h, const void* gates, uint64_t ngates, double eps, int mode, uint64_t* bad) {
+  return orc_apply_counted(h, gates, ngates, eps, mode, bad, nullptr);
 }
 
 // Copies the entries out in the map's (unspecified) order.

@@ -116,6 +116,7 @@ struct sps_state {
   uint64_t bitslice_min_nnz = 1u << 18;   // below this the direct kernel is faster
   uint32_t bs_groups = 0;                  // bit-sliced tile groups, 0 = heuristic
   int bs_jit = 1;                          // SPS_OPT_BITSLICE_JIT
+  bool plan_cache = true;                  // SPS_OPT_PLAN_CACHE
   uint32_t small_cap = kSmallCap;   // 0 disables small-state runs
   // plan arena: op streams, factors and tables of the current sps_apply
   unsigned char* arena = nullptr;
@@ -501,7 +502,7 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
   // table: 2 * capacity labels at the default 50% load, power of two
   s->max_log2 = table_log2_for(capacity, 50, 40);
   s->table_slots = 1ull << s->max_log2;
-  s->prob_blocks = s->sms * 2 < 1024 ? s->sms * 2 : 1024;
+  s->prob_blocks = s->sms * 8 < 2048 ? s->sms * 8 : 2048;
   void* p = nullptr;
   for (int b = 0; b < 2; ++b) {
     if ((st = dev_alloc(s, capacity * 8, &p)) != SPS_OK) return fail(st);
@@ -673,7 +674,7 @@ static sps_status launch_amp_attempt(sps_state* s, const LaunchCfg& lc, const Br
     if (n < 0) return cuda_ok(cudaGetLastError());
   }
   {
-    ProfScope pa(s, 10, serial, d, 2u);
+    ProfScope pa(s, 10, serial, d, walk ? 6u : 2u);
     const int n = launch_amp_part(lc, s->kw, s->ctl, s->bufs, s->itab, s->epoch, force, l,
                                   s->nnz_bound, 1, pa.slot);
     pa.done();
@@ -1029,7 +1030,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
   uint64_t eps_bits;
   std::memcpy(&eps_bits, &prune_eps, sizeof(eps_bits));
   std::vector<uint64_t> opts = plan_options(s);
-  if (!s->plan || !plan_matches(*s->plan, s, gates, ngates, eps_bits, opts)) {
+  if (!s->plan_cache || !s->plan || !plan_matches(*s->plan, s, gates, ngates, eps_bits, opts)) {
     std::unique_ptr<ApplyPlan> np(new (std::nothrow) ApplyPlan());
     if (!np) return SPS_ERR_OOM;
     size_t bad = 0;
@@ -1065,6 +1066,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         cudaEventRecord(stg->copied, s->stream) != cudaSuccess)
       return cuda_ok(cudaGetLastError());
     stg->pending = true;
+    s->counters.upload_bytes += P.image.size();
   }
   s->plan_resident = true;
   s->kb = P.kb_out;
@@ -1171,7 +1173,7 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         e.fused_gates = f.ngates;
         e.has_phase = f.has_phase ? 1u : 0u;
       }
-      ProfScope ps(s, 7, serial, p.ex_d, 3u);
+      ProfScope ps(s, 7, serial, p.ex_d, P.walk_next[pi] ? 7u : 3u);
       const int n = launch_expand(lc, s->kw, s->ctl, s->bufs, e, s->nnz_bound, ps.slot);
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
@@ -1240,10 +1242,13 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
         bl.mg = p.has_perm ? s->masks.writer() : 0u;
         bl.fallback = fb;
         n = 0;
-        if (s->bs_jit == 2 || (s->bs_jit == 1 && s->nnz_bound >= kBsJitMinNnz))
+        if (s->bs_jit == 2 || (s->bs_jit == 1 && s->nnz_bound >= kBsJitMinNnz)) {
           n = launch_fused_bs_jit(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
+          if (n > 0) ps.rec.flags |= 16u;   // the form compiled for this run
+        }
         if (n == 0) n = launch_fused_bs(lc, s->kw, s->ctl, s->bufs, bl, s->nnz_bound, ps.slot);
         if (n == 0) n = -1;   // the plan was checked to fit one launch
+        ps.rec.flags |= 8u;   // bit-sliced
       } else {
         n = launch_fused(lc, s->kw, s->ctl, s->bufs, p,
                          reinterpret_cast<const OpWord*>(s->arena + run_off[pi]),
@@ -1395,7 +1400,7 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
 // adds the block sums in block order, so fewer blocks mean a shorter tail),
 // at most prob_blocks.
 static int prob_grid(const sps_state* s) {
-  const uint64_t b = (s->nnz_bound + 1023) / 1024;
+  const uint64_t b = (s->nnz_bound + 4095) / 4096;
   return b < 1 ? 1 : b > (uint64_t)s->prob_blocks ? s->prob_blocks : (int)b;
 }
 
@@ -1577,6 +1582,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_BITSLICE_JIT:
       if (v < 0 || v > 2) return SPS_ERR_ARG;
       s->bs_jit = (int)v;
+      return SPS_OK;
+    case SPS_OPT_PLAN_CACHE:
+      if (v != 0 && v != 1) return SPS_ERR_ARG;
+      s->plan_cache = v == 1;
       return SPS_OK;
     case SPS_OPT_FUSED_LABELS:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return SPS_ERR_ARG;

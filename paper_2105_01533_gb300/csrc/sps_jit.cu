@@ -182,7 +182,7 @@ __device__ __forceinline__ u64* lm(unsigned char* ctl, u32 b, u32 stripe) {
   return reinterpret_cast<u64*>(ctl + OFF_LM) + ((u64)b * 32u + stripe) * 4u;
 }
 
-extern "C" __global__ void __launch_bounds__(128) k_bs_jit(const JArgs a) {
+extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a) {
   extern __shared__ __align__(16) u32 bsm[];
   __shared__ u64 part[4][32];
   unsigned char* ctl = a.ctl;
@@ -230,17 +230,17 @@ extern "C" __global__ void __launch_bounds__(128) k_bs_jit(const JArgs a) {
       }
     // 1. load and transpose, 8 groups at a time
 #pragma unroll 1
-    for (u32 g0 = 0; g0 < GG; g0 += 8u) {
-      u64 lo[8], hi[8];
+    for (u32 g0 = 0; g0 < GG; g0 += LOAD_BATCH) {
+      u64 lo[LOAD_BATCH], hi[LOAD_BATCH];
 #pragma unroll
-      for (u32 k = 0; k < 8u; ++k) {
+      for (u32 k = 0; k < LOAD_BATCH; ++k) {
         const u64 e = base + 32ull * (g0 + k) + lane;
         const bool valid = e < n;
         lo[k] = valid ? __ldcs(s.lo + e) : 0ull;
         hi[k] = (KW == 2 && valid) ? __ldcs(s.hi + e) : 0ull;
       }
 #pragma unroll
-      for (u32 k = 0; k < 8u; ++k) {
+      for (u32 k = 0; k < LOAD_BATCH; ++k) {
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
           if (WORD_BITS(w) == 0u) continue;
@@ -262,15 +262,15 @@ extern "C" __global__ void __launch_bounds__(128) k_bs_jit(const JArgs a) {
     }
     __syncwarp();
     // 2. the walk, lane g on group g
-    walk(pl + lane);
+    if (lane < GG) walk(pl + lane);
     __syncwarp();
     // 3. transpose back and store, 4 groups at a time
 #pragma unroll 1
-    for (u32 g0 = 0; g0 < GG; g0 += 4u) {
-      u64 aux[4];
-      u64 ent[4];
+    for (u32 g0 = 0; g0 < GG; g0 += STORE_BATCH) {
+      u64 aux[STORE_BATCH];
+      u64 ent[STORE_BATCH];
 #pragma unroll
-      for (u32 k = 0; k < 4u; ++k) {
+      for (u32 k = 0; k < STORE_BATCH; ++k) {
         const u32 g = g0 + k;
         aux[k] = 0ull;
         ent[k] = base + 32ull * g + lane;
@@ -304,10 +304,10 @@ extern "C" __global__ void __launch_bounds__(128) k_bs_jit(const JArgs a) {
         }
       }
       if (HAS_PHASE) {
-        double re[4], im[4];
-        longlong2 t0[4], t1[4];
+        double re[STORE_BATCH], im[STORE_BATCH];
+        longlong2 t0[STORE_BATCH], t1[STORE_BATCH];
 #pragma unroll
-        for (u32 k = 0; k < 4u; ++k) {
+        for (u32 k = 0; k < STORE_BATCH; ++k) {
           re[k] = im[k] = 0.0;
           t0[k] = t1[k] = make_longlong2(0, 0);
           if (aux[k] == 0ull) continue;
@@ -321,7 +321,7 @@ extern "C" __global__ void __launch_bounds__(128) k_bs_jit(const JArgs a) {
           }
         }
 #pragma unroll
-        for (u32 k = 0; k < 4u; ++k) {
+        for (u32 k = 0; k < STORE_BATCH; ++k) {
           if (aux[k] == 0ull) continue;
           i64 pr = 0, pi = 0;
           int q = 62;
@@ -356,7 +356,7 @@ extern "C" __global__ void __launch_bounds__(128) k_bs_jit(const JArgs a) {
             }
           }
           const double fr = q_to_double(pr, q), fi = q_to_double(pi, q);
-          if (im[k] == 0.0) {
+          if ((__double_as_longlong(im[k]) << 1) == 0) {   // a real amplitude
             s.re[ent[k]] = re[k] * fr;
             s.im[ent[k]] = re[k] * fi;
           } else {
@@ -400,12 +400,13 @@ extern "C" __global__ void __launch_bounds__(128) k_bs_jit(const JArgs a) {
 }
 )JIT";
 
-constexpr uint32_t kJitGroups = 32;
 constexpr int kJitWarps = 4;
 
-// The constants and the walk of one plan, then the template.
-std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase) {
-  const uint32_t S = kJitGroups + 1;
+// The constants and the walk of one plan for tiles of G groups (16 or 32),
+// then the template. Tiles of 16 groups leave half the lanes idle in the walk
+// and load and store in smaller batches.
+std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, uint32_t G) {
+  const uint32_t S = G + 1;
   std::string o;
   char buf[256];
   auto def = [&](const char* name, unsigned long long v) {
@@ -414,7 +415,10 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase) 
   };
   def("KW", (unsigned)kw);
   def("NW", P.nw);
-  def("GG", kJitGroups);
+  def("GG", G);
+  def("LB_MIN", 4);
+  def("LOAD_BATCH", G >= 32 ? 8 : 4);
+  def("STORE_BATCH", G >= 32 ? 4 : 2);
   def("SS", S);
   def("ROWS", P.nrows);
   def("AUX0", P.aux_row0);
@@ -576,11 +580,16 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                         uint64_t nnz_bound, unsigned long long* plog) {
   const BsPass& P = *b.plan;
   if (P.ops.empty() || P.nrows > 250 || P.nchunks > 4) return 0;
-  const std::string src = make_source(P, key_words, b.has_perm != 0, b.has_phase != 0);
+  const int sms = lc.max_blocks * lc.threads / 2048 > 0 ? lc.max_blocks * lc.threads / 2048 : 1;
+  // tiles of 32 groups: every lane walks; with 16 the register budget of the
+  // extra resident blocks made the walk spill (SPS_OPT_BITSLICE_GROUPS 2..16
+  // still asks for 16)
+  const uint32_t G = (b.groups == 0 || b.groups >= 32) ? 32u : 16u;
+  const std::string src = make_source(P, key_words, b.has_perm != 0, b.has_phase != 0, G);
   const JitEntry* e = jit_kernel(src);
   if (!e) return 0;
   const void* fn = reinterpret_cast<const void*>(e->kernel);
-  const size_t smem = (size_t)kJitWarps * P.nrows * (kJitGroups + 1) * 4;
+  const size_t smem = (size_t)kJitWarps * P.nrows * (G + 1) * 4;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -614,8 +623,7 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   args.mg_wr = mg_wr(b.mg);
   args.mg_rs = mg_rs(b.mg);
   args.ngates = b.ngates;
-  const int sms = lc.max_blocks * lc.threads / 2048 > 0 ? lc.max_blocks * lc.threads / 2048 : 1;
-  const uint64_t tiles = (nnz_bound + 32ull * kJitGroups - 1) / (32ull * kJitGroups);
+  const uint64_t tiles = (nnz_bound + 32ull * G - 1) / (32ull * G);
   uint64_t blocks = (tiles + kJitWarps - 1) / kJitWarps;
   const uint64_t max_blocks = (uint64_t)sms * bps;
   if (blocks > max_blocks) blocks = max_blocks;
@@ -666,7 +674,7 @@ int bs_jit_selftest(char* log, size_t cap) {
   p.has_phase = true;
   BsPass b;
   build_bitslice(p, 70, &b);
-  const std::string src = make_source(b, 2, true, true);
+  const std::string src = make_source(b, 2, true, true, 32);
   std::string msg;
   const std::string cubin = compile_cubin(src, 10, 3, &msg);
   if (log && cap) {

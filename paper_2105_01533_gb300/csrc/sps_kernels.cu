@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(128) k_fused_bs(Ctl* ctl, Bufs bufs,
             }
           }
           const double fr = q_to_double(pr, q), fi = q_to_double(pi, q);
-          if (im[k] == 0.0) {
+          if ((__double_as_longlong(im[k]) << 1) == 0) {   // a real amplitude
             s.re[ent[k]] = re[k] * fr;
             s.im[ent[k]] = re[k] * fi;
           } else {
@@ -727,6 +727,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
+// Each thread takes 4 consecutive entries per step (two 16-byte label loads);
+// a label word the mask does not test is not read at all, and amplitudes are
+// read only for matching labels.
 template <int KW>
 __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64_t m0,
                                                      uint64_t m1, uint64_t v0, uint64_t v1,
@@ -735,14 +738,35 @@ __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64
   __shared__ bool last;
   const uint64_t n = ctl->nnz;
   const SoA s = pick(bufs, ctl->cur);
+  const bool use0 = (m0 | v0) != 0ull, use1 = KW == 2 && (m1 | v1) != 0ull;
   double acc = 0.0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t k0 = s.lo[i];
-    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
-    if ((k0 & m0) == v0 && (k1 & m1) == v1) {
-      const double re = s.re[i], im = s.im[i];
-      acc += re * re + im * im;
+  const uint64_t stride = 4ull * gridDim.x * blockDim.x;
+  for (uint64_t i = 4ull * (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x); i < n; i += stride) {
+    uint64_t k0[4] = {0ull, 0ull, 0ull, 0ull}, k1[4] = {0ull, 0ull, 0ull, 0ull};
+    if (i + 4 <= n) {   // the buffers are 256-byte aligned and i is a multiple of 4
+      if (use0) {
+        const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + i));
+        const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + i) + 1);
+        k0[0] = a.x; k0[1] = a.y; k0[2] = b.x; k0[3] = b.y;
+      }
+      if (use1) {
+        const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.hi + i));
+        const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(s.hi + i) + 1);
+        k1[0] = a.x; k1[1] = a.y; k1[2] = b.x; k1[3] = b.y;
+      }
+    } else {
+      for (int j = 0; j < 4; ++j)
+        if (i + j < n) {
+          if (use0) k0[j] = s.lo[i + j];
+          if (use1) k1[j] = s.hi[i + j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (i + j < n && (k0[j] & m0) == v0 && (k1[j] & m1) == v1) {
+        const double re = s.re[i + j], im = s.im[i + j];
+        acc += re * re + im * im;
+      }
     }
   }
   const double t = block_sum(acc, sh);

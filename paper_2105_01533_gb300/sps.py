@@ -29,7 +29,7 @@ SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
 SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP, SPS_OPT_BITSLICE_MIN_NNZ = 7, 8, 9
 SPS_OPT_BRANCH_FORM, SPS_OPT_BITSLICE_GROUPS, SPS_OPT_EXPAND, SPS_OPT_FOLD = 10, 11, 12, 13
 SPS_OPT_COMMUTE, SPS_OPT_LAYER_GATES, SPS_OPT_EXPAND_WALK, SPS_OPT_FUSED_LABELS = 14, 15, 16, 17
-SPS_OPT_AMP_ONLY, SPS_OPT_BITSLICE_JIT = 18, 19
+SPS_OPT_AMP_ONLY, SPS_OPT_BITSLICE_JIT, SPS_OPT_PLAN_CACHE = 18, 19, 20
 KIND_SMALL_RUN, KIND_GATHER_BUILD, KIND_GATHER_EMIT = 4, 5, 6
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 
@@ -59,7 +59,8 @@ class SpsError(RuntimeError):
 
 class Counters(ctypes.Structure):
     _fields_ = [("gates", ctypes.c_uint64), ("fused_passes", ctypes.c_uint64),
-                ("branch_passes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+                ("branch_passes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("upload_bytes", ctypes.c_uint64)]
 
 
 class KernelRecord(ctypes.Structure):
