@@ -20,22 +20,43 @@ def bench():
     return mod
 
 
-def rec(kind, n_in, n_out, flags=3, lb=16, ms=1.0):
+def rec(kind, n_in, n_out, flags=3, lb=16, ms=1.0, nops=1):
     return {"kind": kind, "n_in": n_in, "n_out": n_out, "flags": flags, "label_bytes": lb, "ms": ms,
-            "nops": 1, "pass": 1}
+            "nops": nops, "pass": 1}
 
 
 def test_algorithmic_bytes_per_kind(bench):
-    # fused pass: read the label, write it back if it permutes, amplitude r+w if phases
-    assert bench.algorithmic_bytes(rec(1, 100, 100, flags=3)) == (16 + 16 + 32) * 100
-    assert bench.algorithmic_bytes(rec(1, 100, 100, flags=2)) == (16 + 32) * 100
-    assert bench.algorithmic_bytes(rec(1, 100, 100, flags=1, lb=8)) == (8 + 8) * 100
-    # expansion, gather emit, amplitude-only run: read the old state, write the new
-    for k in (6, 7, 10):
-        assert bench.algorithmic_bytes(rec(k, 10, 40)) == (16 + 16) * 50
+    """Bytes of the method's passes: 2*B*n per fused pass, B*(n_in + n_out)
+    per branching pass (B = label bytes + 16), each pass a launch carries out
+    counted."""
+    B = 32
+    # a fused pass reads and writes the state, whatever it changes
+    for flags in (3, 2, 1):
+        assert bench.algorithmic_bytes(rec(1, 100, 100, flags=flags)) == 2 * B * 100
+    assert bench.algorithmic_bytes(rec(1, 100, 100, flags=1, lb=8)) == 2 * 24 * 100
+    # one branching gate as a gather pass: old state in, new state out
+    assert bench.algorithmic_bytes(rec(6, 10, 20)) == B * (10 + 20)
+    # an expansion of d gates doubles d times: sum of B*(m + 2m) for m = n, 2n, ..
+    assert bench.algorithmic_bytes(rec(7, 1, 8, nops=3)) == B * (3 + 6 + 12)
+    assert bench.algorithmic_bytes(rec(7, 1, 8, nops=3, flags=7)) == B * (3 + 6 + 12) + 2 * B * 8
+    # an amplitude-only run of d gates: d passes over a state that keeps its labels
+    assert bench.algorithmic_bytes(rec(10, 50, 50, nops=4, flags=2)) == 4 * 2 * B * 50
+    assert bench.algorithmic_bytes(rec(10, 50, 50, nops=4, flags=6)) == 5 * 2 * B * 50
+    assert bench.algorithmic_bytes(rec(10, 50, 0, nops=4, flags=2)) == 0     # not taken
+    # a layer of 2 gates from 10 to 40 entries: 10 -> 20 -> 40
+    assert abs(bench.algorithmic_bytes(rec(6, 10, 40, nops=2)) - B * (30 + 60)) < 1e-6
     # index builds read labels only
     for k in (5, 9):
         assert bench.algorithmic_bytes(rec(k, 10, 0, lb=8)) == 8 * 10
+
+
+def test_moved_bytes_and_kernel_names(bench):
+    assert bench.moved_bytes(rec(1, 100, 100, flags=2)) == (16 + 32) * 100
+    assert bench.moved_bytes(rec(10, 50, 50, nops=4)) == (32 + 16) * 50
+    assert bench.kernel_name(rec(1, 1, 1, flags=3 | 8 | 16)) == "k_bs_jit"
+    assert bench.kernel_name(rec(1, 1, 1, flags=3 | 8)) == "k_fused_bs"
+    assert bench.kernel_name(rec(1, 1, 1, flags=3)) == "k_fused"
+    assert bench.kernel_name(rec(10, 1, 1)) == "k_amp_layer"
 
 
 def test_traffic_record_is_used_only_for_matching_sources(bench, tmp_path, monkeypatch):
@@ -57,11 +78,13 @@ def test_roofline_picks_the_dominant_kernel_and_scales_traffic(bench, monkeypatc
     monkeypatch.setattr(bench, "measured_peaks", lambda: (6000.0, "measured"))
     monkeypatch.setattr(bench, "ncu_traffic",
                         lambda k, w, n: 3.0 * n if (k, w) == ("k_expand", "adder67") else None)
-    recs = [rec(7, 1, 65536, ms=0.02), rec(7, 1, 65536, ms=0.022), rec(8, 65536, 65536, ms=0.001)]
-    r = bench.roofline(recs, "adder67")
+    recs = [rec(7, 1, 65536, ms=0.02, nops=16), rec(7, 1, 65536, ms=0.022, nops=16),
+            rec(8, 65536, 65536, ms=0.001)]
+    r = bench.roofline(recs, "adder67", steps=2)
     assert r["kernel"] == "k_expand"
-    # two launches of (16 + 16) * (1 + 65536) bytes in 0.042 ms in all
-    want = 32 * 65537 / (0.021e-3) / 1e9
+    assert r["launches_per_step"] == 1.0
+    # two launches of 16 doubling passes from one entry, 0.042 ms in all
+    want = 32 * 3 * (2 ** 16 - 1) / (0.021e-3) / 1e9
     assert abs(r["achieved"] - round(want, 2)) < 0.01
     assert abs(r["frac"] - round(want / 6000.0, 4)) < 1e-4
     assert r["traffic"] == 3.0 * 65536      # expansions count their outputs
