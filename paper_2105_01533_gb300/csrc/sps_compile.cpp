@@ -765,9 +765,11 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
     b.factors[2 * i + 1] = to_q62(factor[i].im);
   }
   // phase tables: the aux bits in as few chunks of at most kBsMaxChunkBits as
-  // possible, split evenly (one table product per extra chunk and entry)
+  // possible, split evenly (one table product per extra chunk and entry); up
+  // to kBsDirectBits aux bits, two chunks that build one direct table
   if (aux > 0) {
-    b.nchunks = (aux + kBsMaxChunkBits - 1) / kBsMaxChunkBits;
+    b.direct = aux <= kBsDirectBits;
+    b.nchunks = b.direct ? (aux > 1 ? 2u : 1u) : (aux + kBsMaxChunkBits - 1) / kBsMaxChunkBits;
     uint32_t at = 0;
     for (uint32_t c = 0; c < b.nchunks; ++c) {
       const uint32_t bits = aux / b.nchunks + (c < aux % b.nchunks ? 1u : 0u);

@@ -111,6 +111,10 @@ constexpr uint32_t kMaxFireSlots = kMaxAuxBits - 3;
 constexpr uint32_t kBsMaxOps = 1024;     // op words of one bit-sliced launch (kernel parameters)
 constexpr uint32_t kBsMaxChunkBits = 18; // aux bits per phase table (4 MiB)
 constexpr uint64_t kBsJitMinNnz = 1ull << 20;   // SPS_OPT_BITSLICE_JIT = 1: from this bound
+// Runs with at most this many aux bits get one table of every aux pattern's
+// phase as doubles (2^bits x 16 B, 64 MiB at most): a lookup per entry and no
+// product; more aux bits use fixed-point chunk tables and products.
+constexpr uint32_t kBsDirectBits = 22;
 
 struct BsPass {
   uint32_t nw = 0;            // 32-bit words of a label (nqubits / 32 rounded up)
@@ -134,7 +138,14 @@ struct BsPass {
     for (const SOp& o : ops) n += (o.kind != SOP_FLIP && o.kind != SOP_AND) ? 2u : 1u;
     return n;
   }
+  // aux_bits <= kBsDirectBits: the kernels look the phase up in one table of
+  // 2^aux_bits doubles (re, im) built from the (two) fixed-point chunk tables
+  bool direct = false;
+  // 16-byte table entries: the fixed-point chunk tables, then the direct table
   uint64_t table_entries() const {
+    return direct_offset() + (direct ? 1ull << aux_bits : 0ull);
+  }
+  uint64_t direct_offset() const {   // first entry of the direct table
     uint64_t t = 0;
     for (uint32_t c = 0; c < nchunks; ++c) t += 1ull << chunk_bits[c];
     return t;

@@ -111,6 +111,7 @@ struct JArgs {
   unsigned char* ctl;
   Soa b[2];
   const longlong2* tab[4];
+  const double2* direct;
   u64* plog;
   u32 fallback, mg_wr, mg_rs, ngates;
 };
@@ -303,7 +304,30 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
           aux[k] = valid ? ((u64)x0 | ((u64)x1 << 32)) : 0ull;
         }
       }
-      if (HAS_PHASE) {
+      if (HAS_PHASE && DIRECT) {   // one table of every aux pattern's phase
+        double2 ph[STORE_BATCH];
+        double re[STORE_BATCH], im[STORE_BATCH];
+#pragma unroll
+        for (u32 k = 0; k < STORE_BATCH; ++k) {
+          ph[k] = make_double2(1.0, 0.0);
+          re[k] = im[k] = 0.0;
+          if (aux[k] == 0ull) continue;
+          re[k] = __ldcs(s.re + ent[k]);
+          im[k] = __ldcs(s.im + ent[k]);
+          ph[k] = __ldg(a.direct + aux[k]);
+        }
+#pragma unroll
+        for (u32 k = 0; k < STORE_BATCH; ++k) {
+          if (aux[k] == 0ull) continue;
+          if ((__double_as_longlong(im[k]) << 1) == 0) {   // a real amplitude
+            s.re[ent[k]] = re[k] * ph[k].x;
+            s.im[ent[k]] = re[k] * ph[k].y;
+          } else {
+            s.re[ent[k]] = fma(re[k], ph[k].x, -(im[k] * ph[k].y));
+            s.im[ent[k]] = fma(re[k], ph[k].y, im[k] * ph[k].x);
+          }
+        }
+      } else if (HAS_PHASE) {
         double re[STORE_BATCH], im[STORE_BATCH];
         longlong2 t0[STORE_BATCH], t1[STORE_BATCH];
 #pragma unroll
@@ -427,6 +451,7 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, 
   def("HAS_PHASE", (has_phase && P.aux_bits > 0) ? 1 : 0);
   def("WORD_OUT", P.word_out);
   def("NCHUNK", P.nchunks);
+  def("DIRECT", P.direct ? 1 : 0);
   def("OFF_NNZ", offsetof(Ctl, nnz));
   def("OFF_CUR", offsetof(Ctl, cur));
   def("OFF_STATUS", offsetof(Ctl, status));
@@ -607,6 +632,7 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
     unsigned char* ctl;
     Soa b[2];
     const void* tab[4];
+    const void* direct;
     unsigned long long* plog;
     uint32_t fallback, mg_wr, mg_rs, ngates;
   } args;
@@ -618,6 +644,7 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
     args.tab[c] = reinterpret_cast<const char*>(b.tables) + 16 * toff;
     toff += 1ull << P.chunk_bits[c];
   }
+  args.direct = P.direct ? reinterpret_cast<const char*>(b.tables) + 16 * P.direct_offset() : nullptr;
   args.plog = plog;
   args.fallback = b.fallback;
   args.mg_wr = mg_wr(b.mg);

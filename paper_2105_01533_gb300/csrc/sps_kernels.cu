@@ -232,6 +232,7 @@ struct BsArgs {
   uint32_t nchunks;
   uint32_t chunk_shift[4], chunk_bits[4];
   const longlong2* tables[4];
+  const double2* direct;       // the direct phase table, or null
   uint32_t mg;                 // label-mask buffers (MaskRing)
   uint32_t fallback;           // 1: skip if an amplitude-only attempt took the pass
   uint8_t row_of[4][32];       // row of bit j of word w (kNoRow: none)
@@ -402,7 +403,30 @@ __global__ void __launch_bounds__(128) k_fused_bs(Ctl* ctl, Bufs bufs,
           aux[k] = valid ? ((uint64_t)x0 | ((uint64_t)x1 << 32)) : 0ull;
         }
       }
-      if (a.has_phase) {
+      if (a.has_phase && a.direct) {   // one table of every aux pattern's phase
+        double2 ph[4];
+        double re[4], im[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4u; ++k) {
+          ph[k] = make_double2(1.0, 0.0);
+          re[k] = im[k] = 0.0;
+          if (aux[k] == 0ull) continue;
+          re[k] = __ldcs(s.re + ent[k]);
+          im[k] = __ldcs(s.im + ent[k]);
+          ph[k] = __ldg(a.direct + aux[k]);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4u; ++k) {
+          if (aux[k] == 0ull) continue;
+          if ((__double_as_longlong(im[k]) << 1) == 0) {   // a real amplitude
+            s.re[ent[k]] = re[k] * ph[k].x;
+            s.im[ent[k]] = re[k] * ph[k].y;
+          } else {
+            s.re[ent[k]] = fma(re[k], ph[k].x, -(im[k] * ph[k].y));
+            s.im[ent[k]] = fma(re[k], ph[k].y, im[k] * ph[k].x);
+          }
+        }
+      } else if (a.has_phase) {
         const uint32_t m0 = (1u << a.chunk_bits[0]) - 1u;
         const uint32_t m1 = a.nchunks > 1 ? (1u << a.chunk_bits[1]) - 1u : 0u;
         double re[4], im[4];
@@ -494,6 +518,25 @@ __global__ void k_bs_tables(const longlong2* factors, longlong2* out, uint32_t b
       im = i;
     }
     out[idx] = make_longlong2(re, im);
+  }
+}
+
+// The direct phase table: entry idx = chunk0[low bits] * chunk1[high bits]
+// (fixed point, rounded once more) as doubles.
+__global__ void k_bs_direct_table(const longlong2* c0, const longlong2* c1, uint32_t bits0,
+                                  uint32_t bits, double2* out) {
+  const uint32_t size = 1u << bits;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < size;
+       idx += gridDim.x * blockDim.x) {
+    const longlong2 a = c0[idx & ((1u << bits0) - 1u)];
+    long long re = a.x, im = a.y;
+    int q = 62;
+    if (bits > bits0) {
+      const longlong2 t = c1[idx >> bits0];
+      qmul(re, im, t.x, t.y);
+      q -= 2;
+    }
+    out[idx] = make_double2(q_to_double(re, q), q_to_double(im, q));
   }
 }
 
@@ -1070,6 +1113,7 @@ int fused_bs_kw(const LaunchCfg& lc, Ctl* ctl, Bufs bufs, const BsLaunch& b, uin
     a.tables[c] = reinterpret_cast<const longlong2*>(b.tables) + toff;
     toff += 1ull << P.chunk_bits[c];
   }
+  a.direct = P.direct ? reinterpret_cast<const double2*>(b.tables) + P.direct_offset() : nullptr;
   a.mg = b.mg;
   a.fallback = b.fallback;
   auto off = [&](uint8_t r) -> uint32_t { return r == kNoRow ? 0u : (uint32_t)r * rb; };
@@ -1185,6 +1229,14 @@ int launch_bs_tables(const LaunchCfg& lc, const BsLaunch& b) {
         reinterpret_cast<const longlong2*>(b.factors), reinterpret_cast<longlong2*>(b.tables) + toff,
         P.chunk_bits[c], P.chunk_shift[c]);
     toff += size;
+    ++launched;
+  }
+  if (P.direct) {
+    const uint32_t size = 1u << P.aux_bits;
+    const longlong2* t = reinterpret_cast<const longlong2*>(b.tables);
+    k_bs_direct_table<<<(int)((size + 255) / 256), 256, 0, (cudaStream_t)lc.stream>>>(
+        t, P.nchunks > 1 ? t + (1ull << P.chunk_bits[0]) : t, P.chunk_bits[0], P.aux_bits,
+        reinterpret_cast<double2*>(b.tables) + P.direct_offset());
     ++launched;
   }
   return cudaPeekAtLastError() == cudaSuccess ? launched : -1;
