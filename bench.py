@@ -221,6 +221,8 @@ ACCOUNTING = ("bytes of the method's passes: 2*B*n per fused phase/permutation p
 
 
 def kernel_name(r) -> str:
+    if r["kind"] == 7 and r["flags"] & 16:   # expansion and bit-sliced run, compiled together
+        return "k_bs_jit_expand"
     if r["kind"] == 1 and r["flags"] & 16:
         return "k_bs_jit"
     if r["kind"] == 1 and r["flags"] & 8:
@@ -450,6 +452,7 @@ def run_ours(args, dist, rank, world, local_rank):
                           "l2": "flushed between timed steps (512 MB write)",
                           "parallelism": "replicas" if world > 1 else "single"},
                "roofline": rl, "e2e": e2e, "gpu_launches": int(launches * world),
+               "device_rates": device_rates(sps),
                "clocks": clocks, "p50_step_ms": round(float(np.median(step_ms)), 5),
                "p99_step_ms": round(float(np.percentile(step_ms, 99)), 5)}
         if world == 1 and not args.no_cpu_baseline:
@@ -473,6 +476,16 @@ def run_ours(args, dist, rank, world, local_rank):
         if res is not None:
             res["served"] = sres
     return res
+
+
+def device_rates(sps) -> dict:
+    """Issue rates measured by the library's probe (lane operations per second):
+    the denominators for kernels bound by FP64 or by instruction issue."""
+    try:
+        r = sps.sps_device_rates()
+    except Exception as e:   # a measurement aid: never fail the bench line for it
+        return {"error": str(e)}
+    return {k: round(v / 1e9, 1) for k, v in r.items()} | {"unit": "G lane-ops/s"}
 
 
 def run_sub(args, sps, torch, name: str):

@@ -558,6 +558,18 @@ sps_status sps_branch_apply_static(const sps_gate* gate, uint32_t nqubits,
  * compiler's message. Needs no GPU. */
 int sps_jit_selftest(char* log, size_t cap);
 
+/* Measures, on the current device, the issue rates of the units the kernels
+ * lean on, as operations per second (lane operations): rates[0] FP64 fused
+ * multiply-add, rates[1] FP32 fused multiply-add, rates[2] three-input 32-bit
+ * logic, rates[3] 32-bit integer multiply-add. Each rate comes from a timed
+ * launch of independent dependent chains (about 20 ms in all); the device
+ * buffer it needs (8 bytes per thread) is allocated and freed with cudaMalloc.
+ * These are the denominators for kernels bound by FP64 or by instruction
+ * issue rather than by memory bandwidth. The paper has no counterpart: it is a
+ * measurement aid. Errors: SPS_ERR_ARG, SPS_ERR_NO_DEVICE, SPS_ERR_OOM,
+ * SPS_ERR_CUDA. */
+sps_status sps_device_rates(double rates[4]);
+
 /* Static text for a status code. */
 const char* sps_status_str(sps_status st);
 

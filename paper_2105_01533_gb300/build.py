@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsps.so")
-SOURCES = ["sps_api.cu", "sps_kernels.cu", "sps_compile.cpp", "sps_noalloc.cu", "sps_cta.cu", "sps_gather.cu", "sps_batch.cu", "sps_server.cu", "sps_jit.cu"]
+SOURCES = ["sps_api.cu", "sps_kernels.cu", "sps_compile.cpp", "sps_noalloc.cu", "sps_cta.cu", "sps_gather.cu", "sps_batch.cu", "sps_server.cu", "sps_jit.cu", "sps_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

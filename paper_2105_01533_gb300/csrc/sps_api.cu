@@ -48,6 +48,12 @@ struct ApplyPlan {
   std::vector<size_t> bs_off;       // their phase factors in the arena image
   std::vector<uint64_t> bs_tab;     // their phase tables: first entry in the table space
   uint64_t bs_tab_entries = 0;      // table space the plan needs (16 B per entry)
+  // passes 0 and 1 as one compiled launch when pass 0 is an expansion from a
+  // pending reset and pass 1 a bit-sliced run (build_bitslice_expand)
+  BsPass bs_ex;
+  bool bs_ex_ok = false;
+  size_t bs_ex_off = 0;             // its factors in the arena image
+  uint64_t bs_ex_tab = 0;           // its phase tables in the table space
   std::vector<size_t> run_off;      // small run: its RunPass array; direct fused pass: its
                                     // op stream; expansion: its factor tables
   std::vector<size_t> ph_off;       // direct fused pass: its fire-slot tables; expansion:
@@ -970,6 +976,20 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
     }
     ++i;
   }
+  // an expansion from |0...0> and the bit-sliced run after it, as one launch
+  // (taken at apply time when the reset is still pending)
+  P->bs_ex_ok = false;
+  if (np >= 2 && s->bs_jit != 0 && passes[0].kind == PASS_EXPAND && !P->seg_end[0] &&
+      passes[1].kind == PASS_FUSED && !P->seg_end[1] && !P->bs[1].ops.empty() &&
+      s->nnz_bound == 1 && passes[0].ex_d < 63 && (1ull << passes[0].ex_d) <= s->capacity &&
+      (s->bs_jit == 2 || (1ull << passes[0].ex_d) >= kBsJitMinNnz) &&
+      build_bitslice_expand(passes[0], passes[1], s->nqubits, prune_eps, &P->bs_ex)) {
+    P->bs_ex_ok = true;
+    P->bs_ex_off = bs_bytes;
+    bs_bytes += align16(P->bs_ex.factors.size() * 8);
+    P->bs_ex_tab = P->bs_tab_entries;
+    P->bs_tab_entries += P->bs_ex.table_entries();
+  }
   std::vector<unsigned char>& img = P->image;
   img.assign(bs_bytes, 0);
   for (size_t i = 0; i < np; ++i) {
@@ -977,6 +997,8 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
     if (b.ops.empty() || b.factors.empty()) continue;
     std::memcpy(img.data() + P->bs_off[i], b.factors.data(), b.factors.size() * 8);
   }
+  if (P->bs_ex_ok && !P->bs_ex.factors.empty())
+    std::memcpy(img.data() + P->bs_ex_off, P->bs_ex.factors.data(), P->bs_ex.factors.size() * 8);
   auto put = [&](const void* src, size_t bytes) {
     const size_t at = img.size();
     img.resize(align16(at + bytes), 0);
@@ -1147,6 +1169,39 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
     if (!fb && (p.kind == PASS_BRANCH || p.kind == PASS_LAYER)) s->amp_force = true;
     const uint32_t serial = ++s->pass_serial;
     const uint64_t tag = ((uint64_t)s->apply_serial << 32) | (p.first_gate & 0xFFFFFFFFull);
+    if (p.kind == PASS_EXPAND && pi == 0 && from_reset && P.bs_ex_ok) {
+      // the expansion and the bit-sliced run after it in one compiled launch
+      const Pass& f = passes[1];
+      BsLaunch bl;
+      bl.plan = &P.bs_ex;
+      bl.factors = reinterpret_cast<const long long*>(s->arena + P.bs_ex_off);
+      bl.tables = s->bs_tables + 2 * P.bs_ex_tab;
+      bl.build_tables = build_tables ? 1u : 0u;
+      bl.ngates = f.ngates;
+      bl.has_perm = 1u;
+      bl.has_phase = P.bs_ex.aux_bits > 0 ? 1u : 0u;
+      bl.groups = 0;
+      MaskRing ring = s->masks;   // taken only if the launch happens
+      bl.mg = ring.writer();
+      bl.fallback = 0;
+      const uint64_t nout = 1ull << p.ex_d;
+      ProfScope ps(s, 7, serial, p.ex_d, 3u | 4u | 8u | 16u);
+      const int n = launch_fused_bs_jit(lc, s->kw, s->ctl, s->bufs, bl, nout, ps.slot);
+      ps.done();
+      if (n < 0) return cuda_ok(cudaGetLastError());
+      if (n > 0) {
+        s->masks = ring;
+        s->amp_force = true;
+        s->counters.branch_passes++;
+        s->counters.fused_passes++;
+        s->counters.kernel_launches += (uint64_t)n;
+        s->nnz_bound = nout;
+        ++s->pass_serial;   // the run's pass serial
+        ++pi;
+        continue;
+      }
+      // the compiled form is not available: the two passes as usual
+    }
     if (p.kind == PASS_EXPAND) {
       ExpandLaunch e;
       e.f = reinterpret_cast<const double*>(s->arena + run_off[pi]);

@@ -641,13 +641,92 @@ long long to_q62(double x) { return std::llround(std::ldexp(x, 62)); }
 
 }  // namespace
 
+namespace {
+void build_bitslice_rows(const Pass& p, uint32_t nqubits, const uint64_t extra[2], bool all_out,
+                         BsPass* out);
+}  // namespace
+
 void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
+  const uint64_t none[2] = {0ull, 0ull};
+  build_bitslice_rows(p, nqubits, none, false, out);
+}
+
+bool build_bitslice_expand(const Pass& ex, const Pass& run, uint32_t nqubits, double eps,
+                           BsPass* out) {
+  if (ex.kind != PASS_EXPAND || run.kind != PASS_FUSED || ex.ex_d == 0 || ex.ex_d > kMaxExpandGates)
+    return false;
+  Pass comb;
+  comb.kind = PASS_FUSED;
+  comb.first_gate = ex.first_gate;
+  comb.ngates = run.ngates;
+  comb.has_perm = true;
+  comb.has_phase = run.has_phase;
+  uint64_t targets[2] = {0ull, 0ull};
+  double cr = 1.0, ci = 0.0, least = 1.0;
+  std::vector<int> choice_qubit(ex.ex_d);
+  for (uint32_t j = 0; j < ex.ex_d; ++j) {
+    const BranchOp& op = ex.ex_ops[j];
+    if (__builtin_popcountll(op.m[0]) + __builtin_popcountll(op.m[1]) != 1) return false;
+    if (ex.ex_x[j] != 0) return false;   // from |0...0>: every selector starts at 0
+    const uint32_t q = op.m[0] ? (uint32_t)__builtin_ctzll(op.m[0]) : 64u + (uint32_t)__builtin_ctzll(op.m[1]);
+    if ((targets[q >> 6] >> (q & 63u)) & 1ull) return false;
+    targets[q >> 6] |= 1ull << (q & 63u);
+    choice_qubit[j] = (int)q;
+    // output bit b (= choice bit j) takes the factor M[b][0]
+    const double r0 = op.m_re[0][0], i0 = op.m_im[0][0], r1 = op.m_re[1][0], i1 = op.m_im[1][0];
+    const double a0 = std::hypot(r0, i0), a1 = std::hypot(r1, i1);
+    least *= std::min(a0, a1);
+    if (r0 == r1 && i0 == i1) {   // the same factor either way: into the common factor
+      const double nr = cr * r0 - ci * i0, ni = cr * i0 + ci * r0;
+      cr = nr;
+      ci = ni;
+    } else {   // a phase slot on the qubit: M[0][0] where it is 0, M[1][0] where it is 1
+      FOp o;
+      std::memset(&o, 0, sizeof(o));
+      o.sbit = (uint8_t)q;
+      o.ph = (uint16_t)comb.phases.size();
+      set_fop_kind(o);
+      comb.ops.push_back(o);
+      comb.phases.push_back(PhasePair{r0, i0, r1, i1});
+      comb.has_phase = true;
+    }
+  }
+  if (!(least > 2.0 * eps) || least == 0.0) return false;
+  // the run's ops after the prefix, their phase pairs after the prefix's
+  const size_t base = comb.phases.size();
+  for (const FOp& o : run.ops) {
+    FOp c = o;
+    if (c.ph != NO_PH) c.ph = (uint16_t)(c.ph + base);
+    comb.ops.push_back(c);
+  }
+  comb.phases.insert(comb.phases.end(), run.phases.begin(), run.phases.end());
+  if (comb.phases.size() > kMaxFusedPhases + kMaxExpandGates) return false;
+  build_bitslice_rows(comb, nqubits, targets, true, out);
+  if (out->aux_bits > kBsDirectBits) return false;   // the phase from one table
+  out->expand = true;
+  out->ex_d = ex.ex_d;
+  out->c_re = cr;
+  out->c_im = ci;
+  out->row_choice.assign(out->nrows, (int8_t)-1);
+  for (uint32_t j = 0; j < ex.ex_d; ++j) {
+    const int q = choice_qubit[j];
+    const uint8_t r = out->row_of[q >> 5][q & 31];
+    if (r == kNoRow) return false;
+    out->row_choice[r] = (int8_t)j;
+  }
+  return out->aux_bits <= kMaxAuxBits && out->op_words() <= kBsMaxOps;
+}
+
+namespace {
+
+void build_bitslice_rows(const Pass& p, uint32_t nqubits, const uint64_t extra[2], bool all_out,
+                         BsPass* out) {
   *out = BsPass();
   BsPass& b = *out;
   b.nw = (nqubits + 31) / 32;
   std::memset(b.row_of, kNoRow, sizeof(b.row_of));
   // qubits the ops read (conditions, selectors) and flip
-  uint64_t used[2] = {0ull, 0ull}, flipped[2] = {0ull, 0ull};
+  uint64_t used[2] = {extra[0], extra[1]}, flipped[2] = {0ull, 0ull};
   bool cnt = false;
   for (const FOp& o : p.ops) {
     for (int w = 0; w < 2; ++w) {
@@ -658,8 +737,14 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
     cnt = cnt || o.a0 != 0 || o.a1 != 0;
   }
   // a 64-bit half with a flipped bit is written back whole: every valid bit of
-  // it gets a row (its other bits are 0 in every label)
+  // it gets a row (its other bits are 0 in every label). With all_out every
+  // half is written, and only the used bits have rows (the others are 0)
   for (int h = 0; h < 2; ++h) {
+    if (all_out) {
+      for (int k = 0; k < 2; ++k)
+        if (32u * (2 * h + k) < nqubits) b.word_out |= 1u << (2 * h + k);
+      continue;
+    }
     if (!flipped[h]) continue;
     const uint64_t valid = nqubits >= 64 * (h + 1) ? ~0ull
                          : (nqubits <= 64u * h ? 0ull : ((1ull << (nqubits - 64 * h)) - 1));
@@ -779,5 +864,7 @@ void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out) {
     }
   }
 }
+
+}  // namespace
 
 }  // namespace sps

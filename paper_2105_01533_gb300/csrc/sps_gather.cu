@@ -300,11 +300,13 @@ struct ExpandArgs {
 // (re, im) *= f; a real factor leaves an exactly zero imaginary part at zero
 // (skipping the product, which would only give it a sign).
 // Every product and sum is rounded once (see cmul_rn).
+// Every lane of the warp must call it (the imaginary product of a real factor
+// runs only in warps where some lane has a nonzero imaginary part: FP64 is
+// scarce on this part and a predicated product still occupies the pipe).
 __device__ __forceinline__ void times(bool real, double2 f, double& re, double& im) {
   if (real) {
     re = __dmul_rn(re, f.x);
-    // an exact zero stays zero (tested on the bit pattern: no FP64 compare)
-    if ((__double_as_longlong(im) << 1) != 0) im = __dmul_rn(im, f.x);
+    if (__any_sync(0xFFFFFFFFu, (__double_as_longlong(im) << 1) != 0)) im = __dmul_rn(im, f.x);
   } else {
     cmul_rn(re, im, f.x, f.y);
   }
@@ -368,8 +370,9 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const __gri
       bool keep = false;
       uint64_t l0 = 0, l1 = 0;
       double vr = 0.0, vi = 0.0;
-      if (t < total) {
-        uint32_t c0;
+      const bool valid = t < total;
+      uint32_t c0 = 0;
+      if (valid) {
         if (wide) {   // a span lies inside one block of 256 choices
           c0 = (uint32_t)(t & 0xFFu);
           l0 = h0;
@@ -386,9 +389,9 @@ __global__ void __launch_bounds__(256) k_expand(Ctl* ctl, Bufs bufs, const __gri
         }
         l0 ^= sm[c0].x;
         l1 ^= sm[c0].y;
-        times(a.real != 0u, sf[c0], vr, vi);
-        keep = keep_amp(vr, vi, a.eps2, eps_bits);
       }
+      times(a.real != 0u, sf[c0], vr, vi);   // every lane (lanes past the end on zeros)
+      if (valid) keep = keep_amp(vr, vi, a.eps2, eps_bits);
       L0[k] = l0;
       L1[k] = l1;
       VR[k] = vr;

@@ -138,6 +138,15 @@ struct BsPass {
     for (const SOp& o : ops) n += (o.kind != SOP_FLIP && o.kind != SOP_AND) ? 2u : 1u;
     return n;
   }
+  // An expansion from |0...0> fused in front of the run (build_bitslice_expand):
+  // the launch generates the expansion's outputs instead of reading a state.
+  // row_choice[r] = the choice bit (output index bit) that label row r holds,
+  // -1 for a row of zeros; every label word is written; c_re, c_im = the
+  // factor common to every output; ex_d = the expansion's gates.
+  bool expand = false;
+  std::vector<int8_t> row_choice;
+  double c_re = 1.0, c_im = 0.0;
+  uint32_t ex_d = 0;
   // aux_bits <= kBsDirectBits: the kernels look the phase up in one table of
   // 2^aux_bits doubles (re, im) built from the (two) fixed-point chunk tables
   bool direct = false;
@@ -249,6 +258,12 @@ constexpr uint32_t kSmallTableSlots = 8192;   // input index table, load <= 25%
 
 // Builds the bit-sliced form of a fused pass for an nqubits-qubit state.
 void build_bitslice(const Pass& p, uint32_t nqubits, BsPass* out);
+// The bit-sliced form of expansion pass `ex` (from |0...0>) followed by fused
+// run `run`, as one pass: false unless every expansion gate flips one qubit
+// and no output can be pruned at eps (every output factor's modulus above
+// 2 eps).
+bool build_bitslice_expand(const Pass& ex, const Pass& run, uint32_t nqubits, double eps,
+                           BsPass* out);
 
 // Bounds of one fused pass: ops, arbitrary phases (each a table entry of the
 // bit-sliced form) and, below, its fire slots.

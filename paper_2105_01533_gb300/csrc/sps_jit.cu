@@ -187,6 +187,16 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
   extern __shared__ __align__(16) u32 bsm[];
   __shared__ u64 part[4][32];
   unsigned char* ctl = a.ctl;
+#if EXPAND
+  // the expansion's 2^EX_D outputs from |0...0> (a reset not yet carried out):
+  // nothing is read, the outputs go to buffer 1, the last block publishes them
+  const u64 n = 1ull << EX_D;
+  if (a.plog && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.plog[0] = 1ull;
+    a.plog[1] = n;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+#else
   const u64 n = *reinterpret_cast<volatile u64*>(ctl + OFF_NNZ);
   const bool skip = a.fallback != 0u && *reinterpret_cast<volatile u32*>(ctl + OFF_AMP_STATE) == 1u;
   if (a.plog && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -196,6 +206,7 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
   if (*reinterpret_cast<volatile u32*>(ctl + OFF_STATUS) != 0u || skip) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *reinterpret_cast<u64*>(ctl + OFF_UPDATES) += n * a.ngates;
+#endif
     if (HAS_PERM)
       for (u32 i = 0; i < 32u; ++i) {
         u64* p = lm(ctl, a.mg_rs, i);
@@ -205,8 +216,12 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
         p[3] = ~0ull;
       }
   }
+#if EXPAND
+  const Soa s = a.b[1];
+#else
   const u32 cur = *reinterpret_cast<volatile u32*>(ctl + OFF_CUR);
   const Soa s = cur ? a.b[1] : a.b[0];
+#endif
   const unsigned lane = threadIdx.x & 31u;
   const unsigned warp = threadIdx.x >> 5;
   u32* pl = bsm + warp * (ROWS * SS);
@@ -224,6 +239,7 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
   for (u64 tile = (u64)blockIdx.x * (blockDim.x >> 5) + warp; tile < ntiles; tile += nwarps) {
     const u64 base = tile * tile_entries;
     const u64 tile_n = n - base < tile_entries ? n - base : tile_entries;
+#if !EXPAND
     if (HAS_PHASE)
       for (u64 off = 16ull * lane; off < tile_n; off += 512ull) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(s.re + base + off));
@@ -261,9 +277,12 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
         }
       }
     }
+#else
+    (void)tile_n;
+#endif
     __syncwarp();
-    // 2. the walk, lane g on group g
-    if (lane < GG) walk(pl + lane);
+    // 2. the walk, lane g on group g (in an expansion: from the generated planes)
+    if (lane < GG) walk(pl + lane, base + 32ull * lane);
     __syncwarp();
     // 3. transpose back and store, 4 groups at a time
 #pragma unroll 1
@@ -286,10 +305,10 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
             else hi |= x << (32 * (w - 2));
           }
           if (valid) {
-            if (WORD_OUT & 3u) s.lo[ent[k]] = lo;
+            if (EXPAND || (WORD_OUT & 3u)) s.lo[ent[k]] = lo;
             else lo = s.lo[ent[k]];
             if (KW == 2) {
-              if (WORD_OUT & 12u) s.hi[ent[k]] = hi;
+              if (EXPAND || (WORD_OUT & 12u)) s.hi[ent[k]] = hi;
               else hi = s.hi[ent[k]];
             }
             mo0 |= lo;
@@ -298,6 +317,12 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
             ma1 &= hi;
           }
         }
+#if EXPAND
+        if (!HAS_PHASE && valid) {   // no phase anywhere: the common factor
+          s.re[ent[k]] = C_RE;
+          s.im[ent[k]] = C_IM;
+        }
+#endif
         if (HAS_PHASE) {
           const u32 x0 = tr(aux0 >= 0 ? pl[aux0 + g] : 0u);
           const u32 x1 = NAUX > 32u ? tr(aux1 >= 0 ? pl[aux1 + g] : 0u) : 0u;
@@ -310,16 +335,31 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
 #pragma unroll
         for (u32 k = 0; k < STORE_BATCH; ++k) {
           ph[k] = make_double2(1.0, 0.0);
+#if EXPAND
+          re[k] = C_RE;
+          im[k] = C_IM;
+          if (ent[k] >= n) continue;
+          if (aux[k] == 0ull) {   // no phase: the common factor
+            s.re[ent[k]] = C_RE;
+            s.im[ent[k]] = C_IM;
+            continue;
+          }
+#else
           re[k] = im[k] = 0.0;
           if (aux[k] == 0ull) continue;
           re[k] = __ldcs(s.re + ent[k]);
           im[k] = __ldcs(s.im + ent[k]);
+#endif
           ph[k] = __ldg(a.direct + aux[k]);
         }
+        bool real = true;
+#pragma unroll
+        for (u32 k = 0; k < STORE_BATCH; ++k) real = real && (__double_as_longlong(im[k]) << 1) == 0;
+        real = __all_sync(FULL, real);   // per warp: no predicated complex form
 #pragma unroll
         for (u32 k = 0; k < STORE_BATCH; ++k) {
           if (aux[k] == 0ull) continue;
-          if ((__double_as_longlong(im[k]) << 1) == 0) {   // a real amplitude
+          if (real) {
             s.re[ent[k]] = re[k] * ph[k].x;
             s.im[ent[k]] = re[k] * ph[k].y;
           } else {
@@ -421,6 +461,27 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
       if (~ma1) atomicAnd(p + 3, ma1);
     }
   }
+#if EXPAND
+  // the last block publishes the outputs and does the reset's work on the
+  // control block (no status, no failure record; the updates of the expansion,
+  // 2^EX_D - 1, and of the run, 2^EX_D per gate)
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const u32 done = atomicAdd(reinterpret_cast<u32*>(ctl + OFF_BLOCKS_DONE), 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      *reinterpret_cast<volatile u32*>(ctl + OFF_STATUS) = 0u;
+      *reinterpret_cast<volatile u32*>(ctl + OFF_FAIL_PASS) = 0u;
+      *reinterpret_cast<volatile u64*>(ctl + OFF_FAIL_GATE) = 0ull;
+      *reinterpret_cast<volatile u64*>(ctl + OFF_UPDATES) = (n - 1ull) + n * a.ngates;
+      *reinterpret_cast<volatile u64*>(ctl + OFF_NNZ) = n;
+      *reinterpret_cast<volatile u32*>(ctl + OFF_CUR) = 1u;
+      *reinterpret_cast<volatile u64*>(ctl + OFF_OUT_COUNT) = 0ull;
+      *reinterpret_cast<volatile u32*>(ctl + OFF_BLOCKS_DONE) = 0u;
+      __threadfence();
+    }
+  }
+#endif
 }
 )JIT";
 
@@ -447,7 +508,15 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, 
   def("ROWS", P.nrows);
   def("AUX0", P.aux_row0);
   def("NAUX", P.aux_bits);
-  def("HAS_PERM", has_perm ? 1 : 0);
+  def("HAS_PERM", (has_perm || P.expand) ? 1 : 0);
+  def("EXPAND", P.expand ? 1 : 0);
+  def("EX_D", P.ex_d);
+  def("OFF_FAIL_PASS", offsetof(Ctl, fail_pass));
+  def("OFF_FAIL_GATE", offsetof(Ctl, fail_gate));
+  def("OFF_BLOCKS_DONE", offsetof(Ctl, blocks_done));
+  def("OFF_OUT_COUNT", offsetof(Ctl, out_count));
+  std::snprintf(buf, sizeof(buf), "#define C_RE %.17g\n#define C_IM %.17g\n", P.c_re, P.c_im);
+  o += buf;
   def("HAS_PHASE", (has_phase && P.aux_bits > 0) ? 1 : 0);
   def("WORD_OUT", P.word_out);
   def("NCHUNK", P.nchunks);
@@ -484,7 +553,7 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, 
   }
   o += "};\n";
   // forward declaration; the walk follows the template
-  o += "__device__ __forceinline__ void walk(unsigned int* col);\n";
+  o += "__device__ __forceinline__ void walk(unsigned int* col, unsigned long long tb);\n";
   o += kTemplate;
   // ---- the walk: straight-line code on registers
   std::vector<uint8_t> read(256, 0), written(256, 0);
@@ -497,13 +566,29 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, 
     if (op.kind & (SOP_FLIP | SOP_AND)) written[op.t] = 1;
     if (op.kind & SOP_FLIP) read[op.t] = 1;
   }
-  o += "__device__ __forceinline__ void walk(unsigned int* col) {\n";
+  o += "__device__ __forceinline__ void walk(unsigned int* col, unsigned long long tb) {\n";
   o += "  u32 c0 = 0u, c1 = 0u, c2 = 0u;\n";
-  for (uint32_t r = 0; r < P.label_rows; ++r)
-    if (read[r] || written[r]) {
+  o += "  (void)tb;\n";
+  // in an expansion every label row is generated: bit i of row r is choice bit
+  // j of output tb + i (for j < 5 a fixed pattern, above it one bit of tb)
+  static const char* kPat[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u",
+                                "0xFFFF0000u"};
+  for (uint32_t r = 0; r < P.label_rows; ++r) {
+    if (P.expand) {
+      const int j = P.row_choice[r];
+      if (j < 0)
+        std::snprintf(buf, sizeof(buf), "  u32 p%u = 0u;\n", r);
+      else if (j < 5)
+        std::snprintf(buf, sizeof(buf), "  u32 p%u = %s;\n", r, kPat[j]);
+      else
+        std::snprintf(buf, sizeof(buf), "  u32 p%u = ((tb >> %d) & 1ull) ? 0xFFFFFFFFu : 0u;\n", r, j);
+      o += buf;
+      written[r] = 1;   // every label row is stored for the transposes back
+    } else if (read[r] || written[r]) {
       std::snprintf(buf, sizeof(buf), "  u32 p%u = col[%u];\n", r, r * S);
       o += buf;
     }
+  }
   std::snprintf(buf, sizeof(buf), "  u32 p%u = 0u;\n", (unsigned)scratch);
   o += buf;
   const uint32_t fire0 = P.aux_row0 + (P.has_cnt ? 3u : 0u);

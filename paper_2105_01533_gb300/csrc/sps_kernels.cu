@@ -415,10 +415,16 @@ __global__ void __launch_bounds__(128) k_fused_bs(Ctl* ctl, Bufs bufs,
           im[k] = __ldcs(s.im + ent[k]);
           ph[k] = __ldg(a.direct + aux[k]);
         }
+        // a warp whose amplitudes are all real takes two products per entry;
+        // decided per warp, so the complex form is not run predicated
+        bool real = true;
+#pragma unroll
+        for (uint32_t k = 0; k < 4u; ++k) real = real && (__double_as_longlong(im[k]) << 1) == 0;
+        real = __all_sync(FULL, real);
 #pragma unroll
         for (uint32_t k = 0; k < 4u; ++k) {
           if (aux[k] == 0ull) continue;
-          if ((__double_as_longlong(im[k]) << 1) == 0) {   // a real amplitude
+          if (real) {
             s.re[ent[k]] = re[k] * ph[k].x;
             s.im[ent[k]] = re[k] * ph[k].y;
           } else {
@@ -784,9 +790,15 @@ __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64
   const bool use0 = (m0 | v0) != 0ull, use1 = KW == 2 && (m1 | v1) != 0ull;
   double acc = 0.0;
   const uint64_t stride = 4ull * gridDim.x * blockDim.x;
-  for (uint64_t i = 4ull * (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x); i < n; i += stride) {
+  // warps iterate together (the loop bound is taken at the warp's first lane)
+  const uint64_t lane_off = 4ull * (threadIdx.x & 31u);
+  for (uint64_t w0 = 4ull * (blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u)); w0 < n;
+       w0 += stride) {
+    const uint64_t i = w0 + lane_off;
     uint64_t k0[4] = {0ull, 0ull, 0ull, 0ull}, k1[4] = {0ull, 0ull, 0ull, 0ull};
-    if (i + 4 <= n) {   // the buffers are 256-byte aligned and i is a multiple of 4
+    if (i >= n) {
+      // past the end: no labels, no match
+    } else if (i + 4 <= n) {   // the buffers are 256-byte aligned and i is a multiple of 4
       if (use0) {
         const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + i));
         const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + i) + 1);
@@ -804,11 +816,19 @@ __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64
           if (use1) k1[j] = s.hi[i + j];
         }
     }
+    uint32_t hit = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (i + j < n && (k0[j] & m0) == v0 && (k1[j] & m1) == v1) {
-        const double re = s.re[i + j], im = s.im[i + j];
-        acc += re * re + im * im;
+    for (int j = 0; j < 4; ++j)
+      if (i + j < n && (k0[j] & m0) == v0 && (k1[j] & m1) == v1) hit |= 1u << j;
+    // FP64 is scarce on this part: only warps with a matching label run the
+    // products (a predicated product still occupies the FP64 pipe)
+    if (__any_sync(FULL, hit != 0u)) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if ((hit >> j) & 1u) {
+          const double re = s.re[i + j], im = s.im[i + j];
+          acc += re * re + im * im;
+        }
       }
     }
   }

@@ -43,7 +43,7 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
            "sps_server_completed", "sps_probability_async", "sps_measure", "sps_pauli_exp",
-           "sps_jit_selftest",
+           "sps_jit_selftest", "sps_device_rates",
            "sps_commute")
 
 
@@ -190,6 +190,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_status_str.restype = ctypes.c_char_p
     lib.sps_jit_selftest.argtypes = [vp, sz]
     lib.sps_jit_selftest.restype = ctypes.c_int
+    lib.sps_device_rates.argtypes = [vp]
+    lib.sps_device_rates.restype = st
     _lib = lib
     return lib
 
@@ -406,6 +408,14 @@ def sps_branch_apply_static(gate, nqubits: int, in_arrays, n_in: int, prune_eps:
         _ptr(oh), _ptr(ol), _ptr(orr), _ptr(oi), out_cap, ctypes.byref(n), stream)
     _check(rc, "sps_branch_apply_static")
     return n.value
+
+
+def sps_device_rates() -> dict:
+    """Measured issue rates of the current device (lane operations per
+    second): FP64 fma, FP32 fma, 3-input logic, 32-bit integer mad."""
+    out = (ctypes.c_double * 4)()
+    _check(load_library().sps_device_rates(out), "sps_device_rates")
+    return {"fp64_fma": out[0], "fp32_fma": out[1], "lop3": out[2], "imad": out[3]}
 
 
 def sps_jit_selftest():
