@@ -83,9 +83,12 @@ def test_roofline_picks_the_dominant_kernel_and_scales_traffic(bench, monkeypatc
     r = bench.roofline(recs, "adder67", steps=2)
     assert r["kernel"] == "k_expand"
     assert r["launches_per_step"] == 1.0
-    # two launches of 16 doubling passes from one entry, 0.042 ms in all
-    want = 32 * 3 * (2 ** 16 - 1) / (0.021e-3) / 1e9
+    # the roofline: what each launch moves (one entry read, 65,536 written)
+    want = 32 * (1 + 65536) / (0.021e-3) / 1e9
     assert abs(r["achieved"] - round(want, 2)) < 0.01
     assert abs(r["frac"] - round(want / 6000.0, 4)) < 1e-4
+    # the work rate: 16 doubling passes from one entry
+    work = 32 * 3 * (2 ** 16 - 1) / (0.021e-3) / 1e9
+    assert abs(r["method_passes"]["rate"] - round(work, 2)) < 0.01
     assert r["traffic"] == 3.0 * 65536      # expansions count their outputs
     assert set(r["time_share"]) == {"k_expand", "k_measure"}
