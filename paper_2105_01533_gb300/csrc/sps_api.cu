@@ -508,7 +508,7 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
   // table: 2 * capacity labels at the default 50% load, power of two
   s->max_log2 = table_log2_for(capacity, 50, 40);
   s->table_slots = 1ull << s->max_log2;
-  s->prob_blocks = s->sms * 8 < 2048 ? s->sms * 8 : 2048;
+  s->prob_blocks = s->sms * 4 < 2048 ? s->sms * 4 : 2048;   // all resident
   void* p = nullptr;
   for (int b = 0; b < 2; ++b) {
     if ((st = dev_alloc(s, capacity * 8, &p)) != SPS_OK) return fail(st);
@@ -1455,7 +1455,7 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
 // adds the block sums in block order, so fewer blocks mean a shorter tail),
 // at most prob_blocks.
 static int prob_grid(const sps_state* s) {
-  const uint64_t b = (s->nnz_bound + 4095) / 4096;
+  const uint64_t b = (s->nnz_bound + 8191) / 8192;
   return b < 1 ? 1 : b > (uint64_t)s->prob_blocks ? s->prob_blocks : (int)b;
 }
 

@@ -776,41 +776,45 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
-// Each thread takes 4 consecutive entries per step (two 16-byte label loads);
-// a label word the mask does not test is not read at all, and amplitudes are
-// read only for matching labels.
+// Each thread takes 8 consecutive entries per step (four 16-byte label loads
+// in flight); a label word the mask does not test is not read at all, and
+// amplitudes are read only for matching labels.
 template <int KW>
 __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64_t m0,
                                                      uint64_t m1, uint64_t v0, uint64_t v1,
                                                      double* partials, double* result) {
   __shared__ double sh[32];
   __shared__ bool last;
+  constexpr int U = 8;
   const uint64_t n = ctl->nnz;
   const SoA s = pick(bufs, ctl->cur);
   const bool use0 = (m0 | v0) != 0ull, use1 = KW == 2 && (m1 | v1) != 0ull;
   double acc = 0.0;
-  const uint64_t stride = 4ull * gridDim.x * blockDim.x;
+  const uint64_t stride = (uint64_t)U * gridDim.x * blockDim.x;
   // warps iterate together (the loop bound is taken at the warp's first lane)
-  const uint64_t lane_off = 4ull * (threadIdx.x & 31u);
-  for (uint64_t w0 = 4ull * (blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u)); w0 < n;
-       w0 += stride) {
+  const uint64_t lane_off = (uint64_t)U * (threadIdx.x & 31u);
+  for (uint64_t w0 = (uint64_t)U * (blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u));
+       w0 < n; w0 += stride) {
     const uint64_t i = w0 + lane_off;
-    uint64_t k0[4] = {0ull, 0ull, 0ull, 0ull}, k1[4] = {0ull, 0ull, 0ull, 0ull};
-    if (i >= n) {
-      // past the end: no labels, no match
-    } else if (i + 4 <= n) {   // the buffers are 256-byte aligned and i is a multiple of 4
-      if (use0) {
-        const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + i));
-        const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + i) + 1);
-        k0[0] = a.x; k0[1] = a.y; k0[2] = b.x; k0[3] = b.y;
+    uint64_t k0[U], k1[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) k0[j] = k1[j] = 0ull;
+    if (i + U <= n) {   // the buffers are 256-byte aligned and i is a multiple of 8
+#pragma unroll
+      for (int h = 0; h < U / 2; ++h) {
+        if (use0) {
+          const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + i) + h);
+          k0[2 * h] = a.x;
+          k0[2 * h + 1] = a.y;
+        }
+        if (use1) {
+          const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.hi + i) + h);
+          k1[2 * h] = a.x;
+          k1[2 * h + 1] = a.y;
+        }
       }
-      if (use1) {
-        const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.hi + i));
-        const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(s.hi + i) + 1);
-        k1[0] = a.x; k1[1] = a.y; k1[2] = b.x; k1[3] = b.y;
-      }
-    } else {
-      for (int j = 0; j < 4; ++j)
+    } else if (i < n) {
+      for (int j = 0; j < U; ++j)
         if (i + j < n) {
           if (use0) k0[j] = s.lo[i + j];
           if (use1) k1[j] = s.hi[i + j];
@@ -818,13 +822,13 @@ __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64
     }
     uint32_t hit = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < U; ++j)
       if (i + j < n && (k0[j] & m0) == v0 && (k1[j] & m1) == v1) hit |= 1u << j;
     // FP64 is scarce on this part: only warps with a matching label run the
     // products (a predicated product still occupies the FP64 pipe)
     if (__any_sync(FULL, hit != 0u)) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < U; ++j) {
         if ((hit >> j) & 1u) {
           const double re = s.re[i + j], im = s.im[i + j];
           acc += re * re + im * im;
