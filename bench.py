@@ -214,7 +214,7 @@ def measured_peaks():
 
 KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact", 4: "k_small_run",
               5: "k_gather_build", 6: "k_gather_emit", 7: "k_expand", 8: "k_measure",
-              9: "k_amp_index", 10: "k_amp_layer"}
+              9: "k_amp_index", 10: "k_amp_layer", 11: "k_chain"}
 MOVED_ACCOUNTING = ("bytes the launch must move: B*n read and written by a fused pass that "
                     "permutes and changes phases (labels only or amplitudes only when it does "
                     "one of the two), B*(n_in + n_out) by a branching pass or an expansion, "
@@ -261,6 +261,8 @@ def algorithmic_bytes(r) -> float:
         return sum(B * n_in * q ** j * (1.0 + q) for j in range(d))
     if k in (5, 9):   # label index of a gather or amplitude-only pass
         return float(lb * n_in)
+    if k == 11:   # an attempted run's d passes (none when the attempt took it: n_in 0)
+        return float(B * (n_in + n_out) * d) if n_in > 0 else 0.0
     if k == 2:
         return float(B * n_in)
     if k == 3:
@@ -278,7 +280,7 @@ def moved_bytes(r) -> float:
         return float((lb + (lb if r["flags"] & 1 else 0) + (32 if r["flags"] & 2 else 0)) * n_in)
     if k == 10:   # labels stay: amplitudes read and written, labels read by the lookups
         return float((32 + lb) * n_out)
-    return algorithmic_bytes(r) if k in (2, 3, 5, 9) else float(B * (n_in + n_out))
+    return algorithmic_bytes(r) if k in (2, 3, 5, 9, 11) else float(B * (n_in + n_out))
 
 
 def kernel_source_hash() -> str:
@@ -420,12 +422,16 @@ def run_ours(args, dist, rank, world, local_rank):
     c0 = st.counters().kernel_launches
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    if args.profile_range:   # a profiler started with capture off records the timed steps only
+        torch.cuda.profiler.start()
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     launches = st.counters().kernel_launches - c0
     st.sync()   # raises if any timed step failed on the device
     p = probs[:slot[0]].numpy()
@@ -933,6 +939,9 @@ def main():
                     help="all-core oracle baseline on every k-th batched circuit (0: skip)")
     ap.add_argument("--dump-profile", default=None,
                     help="write the per-launch records of one profiled step to this JSON file")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for a profiler "
+                         "started with capture off, e.g. ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -46,7 +46,9 @@ typedef enum sps_status {
   SPS_ERR_TABLE_FULL = 3,  /* the branching hash table hit its probe limit */
   SPS_ERR_CUDA = 4,        /* a CUDA runtime call failed */
   SPS_ERR_OOM = 5,         /* device allocation failed */
-  SPS_ERR_NO_DEVICE = 6    /* no usable CUDA device */
+  SPS_ERR_NO_DEVICE = 6,   /* no usable CUDA device */
+  SPS_ERR_TIMEOUT = 7      /* a device-side wait gave up (a grid barrier that
+                              not every block reached within seconds) */
 } sps_status;
 
 /* Gate codes (sps_gate.op). Every gate takes any number of controls in
@@ -320,7 +322,14 @@ typedef enum sps_option {
                                   starting knowledge, nonzero bound) reuses its
                                   compiled plan and the device copy of it; 0:
                                   every sps_apply compiles its gates and uploads
-                                  the plan */
+                                  the plan */,
+  SPS_OPT_FALLBACK_CHAIN = 21  /* 1 (default): the passes an amplitude-only
+                                  attempt stands in for are enqueued as one
+                                  cooperative launch that returns at once when
+                                  the attempt took the run and otherwise runs
+                                  them in order with grid barriers (the same
+                                  state as their separate launches); 0: each
+                                  pass as its own launches */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:
@@ -344,7 +353,9 @@ sps_status sps_get_counters(sps_state* s, sps_counters* out);
  * collapse, timed together), 9 label index of amplitude-only passes
  * (SPS_OPT_AMP_ONLY; n_in 0 when the index was still valid or the attempt is
  * skipped), 10 amplitude-only attempt (n_out 0 when it did not take the pass;
- * then kinds 5 and 6 follow with n_in > 0; they show n_in 0 when skipped).
+ * then kinds 5 and 6 follow with n_in > 0; they show n_in 0 when skipped),
+ * 11 the attempted run's passes in one launch (SPS_OPT_FALLBACK_CHAIN; nops =
+ * passes; n_in 0 when the attempt took the run).
  * n_in: entries the kernel read; n_out: entries in the state after it. flags: bit 0 the
  * pass permutes labels, bit 1 it changes amplitudes, bit 2 (kinds 7 and 10) the
  * launch also applied the phase/permutation run after the branching gates,

@@ -123,6 +123,7 @@ struct sps_state {
   uint32_t bs_groups = 0;                  // bit-sliced tile groups, 0 = heuristic
   int bs_jit = 1;                          // SPS_OPT_BITSLICE_JIT
   bool plan_cache = true;                  // SPS_OPT_PLAN_CACHE
+  bool chain = true;                       // SPS_OPT_FALLBACK_CHAIN
   uint32_t small_cap = kSmallCap;   // 0 disables small-state runs
   // plan arena: op streams, factors and tables of the current sps_apply
   unsigned char* arena = nullptr;
@@ -460,6 +461,7 @@ const char* sps_status_str(sps_status st) {
     case SPS_ERR_CUDA: return "CUDA error";
     case SPS_ERR_OOM: return "out of device memory";
     case SPS_ERR_NO_DEVICE: return "no CUDA device";
+    case SPS_ERR_TIMEOUT: return "device-side wait timed out";
   }
   return "unknown status";
 }
@@ -744,6 +746,99 @@ static sps_status launch_branch_pass(sps_state* s, const LaunchCfg& lc, const Br
   const uint64_t nb = s->nnz_bound * 2;
   s->nnz_bound = nb < s->capacity ? nb : s->capacity;
   return SPS_OK;
+}
+
+// The passes [pi, end) of a run whose amplitude-only attempt was just enqueued
+// (its branching and layer passes, then the phase-only pass it walks, if any),
+// as one cooperative launch. Returns false, with nothing enqueued or changed,
+// when the run does not fit that launch; the host bookkeeping (serials,
+// epochs, label-mask buffers, bounds, counters) is that of the separate
+// launches.
+static bool launch_fallback_chain(sps_state* s, const LaunchCfg& lc, const ApplyPlan& P,
+                                  size_t pi, size_t end, double prune_eps, uint32_t limit,
+                                  sps_status* err) {
+  *err = SPS_OK;
+  const std::vector<Pass>& passes = P.passes;
+  const size_t amp_end = P.amp_end[pi];
+  if (amp_end - pi > kChainSteps) return false;
+  for (size_t k = pi; k < amp_end; ++k)
+    if (!(passes[k].kind == PASS_LAYER || (passes[k].kind == PASS_BRANCH && !passes[k].br.pauli)))
+      return false;
+  const bool has_walk = end > amp_end;
+  if (has_walk && !P.amp_walk[pi] && P.amp_par[pi].empty()) return false;
+  if (P.amp_par[pi].size() > 2 * kMaxAmpParity) return false;
+  ChainStepDesc steps[kChainSteps];
+  uint32_t nsteps = 0;
+  const uint32_t first_serial = s->pass_serial + 1;
+  for (size_t k = pi; k < amp_end; ++k) {
+    const Pass& q = passes[k];
+    ChainStepDesc& d = steps[nsteps++];
+    std::memset(&d, 0, sizeof(d));
+    const uint32_t serial = ++s->pass_serial;
+    const uint64_t tag = ((uint64_t)s->apply_serial << 32) | (q.first_gate & 0xFFFFFFFFull);
+    const sps_status es = next_epoch(s, lc);   // a wrap clears the table before the launch
+    if (es != SPS_OK) {
+      *err = es;
+      return true;
+    }
+    d.kind = q.kind;
+    d.epoch = s->epoch;
+    if (q.kind == PASS_LAYER) {
+      LayerLaunch& l = d.lay;
+      l.fallback = 1;
+      l.d = (uint32_t)q.lay.size();
+      for (uint32_t j = 0; j < l.d; ++j) l.ops[j] = q.lay[j];
+      l.eps = prune_eps;
+      l.load_pct = s->load_pct;
+      l.max_log2 = s->itab_log2;
+      l.pass_serial = serial;
+      l.mg = s->masks.writer();
+      l.capacity = s->capacity;
+      l.fail_tag = tag;
+      s->nnz_bound = bound_after(q, s->nnz_bound, s->capacity);
+    } else {
+      BranchLaunch& b = d.br;
+      b.op = q.br;
+      b.eps = prune_eps;
+      b.load_pct = s->load_pct;
+      b.max_log2 = s->itab_log2;
+      b.probe_limit = limit;
+      b.pass_serial = serial;
+      b.coop = s->coop;
+      b.capacity = s->capacity;
+      b.fail_tag = tag;
+      b.mg = s->masks.writer();
+      b.fallback = 1;
+      const uint64_t nb = s->nnz_bound * 2;
+      s->nnz_bound = nb < s->capacity ? nb : s->capacity;
+    }
+    s->counters.branch_passes++;
+  }
+  ChainWalk w;
+  std::memset(&w, 0, sizeof(w));
+  if (has_walk) {
+    const Pass& f = passes[amp_end];
+    ++s->pass_serial;
+    w.ngates = f.ngates;
+    if (P.amp_walk[pi]) {
+      w.words = reinterpret_cast<const OpWord*>(s->arena + P.run_off[amp_end]);
+      w.ftab = reinterpret_cast<const double*>(s->arena + P.ph_off[amp_end]);
+      w.nwords = (uint32_t)f.words.size();
+      w.has_phase = f.has_phase ? 1u : 0u;
+    } else {
+      w.par = P.amp_par[pi].data();
+      w.npar = (uint32_t)(P.amp_par[pi].size() / 2);
+    }
+    s->counters.fused_passes++;
+  }
+  ProfScope ps(s, 11, first_serial, nsteps, 3u);
+  const int n = launch_chain(lc, s->kw, s->ctl, s->bufs, s->itab, steps, nsteps, w, s->nnz_bound,
+                             ps.slot);
+  ps.done();
+  // (0, a run too large for the launch, was ruled out above)
+  if (n <= 0) *err = SPS_ERR_CUDA;
+  s->counters.kernel_launches += 1;
+  return true;
 }
 
 static uint32_t probe_limit_of(const sps_state* s) {
@@ -1164,6 +1259,12 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
                                                walk, words, ftab, par);
       if (as != SPS_OK) return as;
       amp_run_end = P.amp_end[pi] + (walk ? 1 : 0);
+      sps_status cs = SPS_OK;
+      if (s->chain && launch_fallback_chain(s, lc, P, pi, amp_run_end, prune_eps, limit, &cs)) {
+        if (cs != SPS_OK) return cs;
+        pi = amp_run_end - 1;
+        continue;
+      }
     }
     const uint32_t fb = pi < amp_run_end ? 1u : 0u;   // a fallback pass of an attempted run
     if (!fb && (p.kind == PASS_BRANCH || p.kind == PASS_LAYER)) s->amp_force = true;
@@ -1641,6 +1742,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_PLAN_CACHE:
       if (v != 0 && v != 1) return SPS_ERR_ARG;
       s->plan_cache = v == 1;
+      return SPS_OK;
+    case SPS_OPT_FALLBACK_CHAIN:
+      if (v != 0 && v != 1) return SPS_ERR_ARG;
+      s->chain = v == 1;
       return SPS_OK;
     case SPS_OPT_FUSED_LABELS:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return SPS_ERR_ARG;

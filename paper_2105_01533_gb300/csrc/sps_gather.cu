@@ -60,9 +60,8 @@ __device__ __forceinline__ uint64_t itab_mask(uint64_t n, uint32_t load_pct, uin
 }
 
 template <int KW>
-__global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsigned long long* itab,
-                                                      const __grid_constant__ GatherArgs a,
-                                                      unsigned long long* plog) {
+__device__ __forceinline__ void gather_build(Ctl* ctl, Bufs bufs, unsigned long long* itab,
+                                             const GatherArgs& a, unsigned long long* plog) {
   const uint64_t n = ctl->nnz;
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
     plog[0] = amp_took(ctl, a.fallback) ? 0ull : n;
@@ -125,10 +124,8 @@ __device__ __forceinline__ uint64_t find_label(const unsigned long long* itab, u
 }
 
 template <int KW>
-__global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
-                                                     const unsigned long long* itab,
-                                                     const __grid_constant__ GatherArgs a,
-                                                     unsigned long long* plog) {
+__device__ __forceinline__ void gather_emit(Ctl* ctl, Bufs bufs, const unsigned long long* itab,
+                                            const GatherArgs& a, unsigned long long* plog) {
   __shared__ unsigned warp_cnt[32];
   __shared__ unsigned long long block_base;
   if (__syncthreads_or(ctl->status != 0u)) return;
@@ -263,6 +260,21 @@ __global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
       __threadfence();
     }
   }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsigned long long* itab,
+                                                      const __grid_constant__ GatherArgs a,
+                                                      unsigned long long* plog) {
+  gather_build<KW>(ctl, bufs, itab, a, plog);
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_gather_emit(Ctl* ctl, Bufs bufs,
+                                                     const unsigned long long* itab,
+                                                     const __grid_constant__ GatherArgs a,
+                                                     unsigned long long* plog) {
+  gather_emit<KW>(ctl, bufs, itab, a, plog);
 }
 
 // ---------------------------------------------------------------------------
@@ -541,9 +553,8 @@ __device__ __forceinline__ uint32_t layer_pairable(const LayerArgs& a, const Lab
 }
 
 template <int KW>
-__global__ void __launch_bounds__(256) k_layer_build(Ctl* ctl, Bufs bufs, unsigned long long* itab,
-                                                     const __grid_constant__ LayerArgs a,
-                                                     unsigned long long* plog) {
+__device__ __forceinline__ void layer_build(Ctl* ctl, Bufs bufs, unsigned long long* itab,
+                                            const LayerArgs& a, unsigned long long* plog) {
   const uint64_t n = ctl->nnz;
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
     plog[0] = amp_took(ctl, a.fallback) ? 0ull : n;
@@ -581,10 +592,8 @@ __global__ void __launch_bounds__(256) k_layer_build(Ctl* ctl, Bufs bufs, unsign
 }
 
 template <int KW>
-__global__ void __launch_bounds__(256) k_layer_emit(Ctl* ctl, Bufs bufs,
-                                                    const unsigned long long* itab,
-                                                    const __grid_constant__ LayerArgs a,
-                                                    unsigned long long* plog) {
+__device__ __forceinline__ void layer_emit(Ctl* ctl, Bufs bufs, const unsigned long long* itab,
+                                           const LayerArgs& a, unsigned long long* plog) {
   __shared__ unsigned warp_cnt[32];
   __shared__ unsigned long long block_base;
   if (__syncthreads_or(ctl->status != 0u)) return;
@@ -781,6 +790,21 @@ __global__ void __launch_bounds__(256) k_layer_emit(Ctl* ctl, Bufs bufs,
       __threadfence();
     }
   }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_layer_build(Ctl* ctl, Bufs bufs, unsigned long long* itab,
+                                                     const __grid_constant__ LayerArgs a,
+                                                     unsigned long long* plog) {
+  layer_build<KW>(ctl, bufs, itab, a, plog);
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_layer_emit(Ctl* ctl, Bufs bufs,
+                                                    const unsigned long long* itab,
+                                                    const __grid_constant__ LayerArgs a,
+                                                    unsigned long long* plog) {
+  layer_emit<KW>(ctl, bufs, itab, a, plog);
 }
 
 // ---------------------------------------------------------------------------
@@ -1152,6 +1176,160 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
   }
 }
 
+// ---------------------------------------------------------------------------
+// The passes an amplitude-only attempt stands in for, in one cooperative
+// launch. When the attempt took the run, block 0 carries the label masks
+// through the passes' buffers (what each skipped emit does) and every block
+// returns. Otherwise the passes run in order, each branching or layer pass as
+// its index build, a grid barrier, its emit, and the phase-only run after them
+// (walked or as a sign parity), with a grid barrier between passes. Every step
+// is the body of the kernel that runs it alone, so the state equals that of
+// the separate launches.
+struct WalkArgs {
+  const uint4* words;     // direct op stream (nwords > 0), or
+  const double2* ftab;
+  uint32_t nwords, has_phase;
+  uint32_t npar;          // a sign parity: npar conditions (c0, c1) in par
+  uint32_t ngates;        // gates of the run; 0: no run after the passes
+  uint64_t par[2 * kMaxAmpParity];
+};
+
+struct ChainStep {
+  uint32_t kind;   // PASS_BRANCH or PASS_LAYER
+  union {
+    GatherArgs g;
+    LayerArgs l;
+  };
+};
+
+struct ChainArgs {
+  uint32_t nsteps;
+  ChainStep steps[kChainSteps];
+  WalkArgs w;
+};
+static_assert(sizeof(ChainArgs) <= 32000, "kernel parameter space");
+
+// Barrier of every block of a cooperative launch (all resident). Thread 0
+// arrives on Ctl::grid_bar (generation << 16 | broken << 15 | arrivals; the
+// last arrival opens the next generation) and polls it with acquire loads. A
+// wait that lasts more than a few seconds marks the barrier broken and records
+// SPS_ERR_TIMEOUT; a broken barrier lets every later wait through at once, so
+// the launch always ends (later steps see the status and do nothing).
+constexpr uint32_t kBarrierSpins = 1u << 24;   // x ~256 ns sleep: ~4 s
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void grid_barrier(Ctl* ctl, uint32_t pass_serial, uint64_t fail_tag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();   // the block's writes before its arrival
+    const unsigned old = atomicAdd(&ctl->grid_bar, 1u);
+    if ((old & 0x7FFFu) + 1u == gridDim.x) {
+      atomicAdd(&ctl->grid_bar, 0x10000u - gridDim.x);   // next generation, none arrived
+    } else {
+      const unsigned gen = old >> 16;
+      for (uint32_t spin = 0;; ++spin) {
+        const unsigned v = ld_acquire(&ctl->grid_bar);
+        if ((v >> 16) != gen || (v & 0x8000u)) break;
+        if (spin >= kBarrierSpins) {
+          atomicOr(&ctl->grid_bar, 0x8000u);
+          fail(ctl, SPS_ERR_TIMEOUT, pass_serial, fail_tag);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// The phase-only run after the passes, as the direct fused pass applies it.
+template <int KW>
+__device__ __forceinline__ void chain_walk(Ctl* ctl, Bufs bufs, const WalkArgs& w) {
+  if (ctl->status != 0u) return;
+  const uint64_t n = ctl->nnz;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->updates += n * w.ngates;
+  if (w.npar == 0u && (w.nwords == 0u || !w.has_phase)) return;   // labels stay: nothing to write
+  const SoA s = pick(bufs, ctl->cur);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k0 = s.lo[i];
+    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+    if (w.npar) {
+      uint32_t odd = 0u;
+      for (uint32_t c = 0; c < w.npar; ++c)
+        odd ^= ((k0 & w.par[2 * c]) == w.par[2 * c] &&
+                (k1 & w.par[2 * c + 1]) == w.par[2 * c + 1]) ? 1u : 0u;
+      if (odd) {   // times e^{i pi}, as apply_pi4 multiplies it
+        s.re[i] = -s.re[i];
+        s.im[i] = -s.im[i];
+      }
+      continue;
+    }
+    uint64_t l0 = k0, l1 = k1;
+    uint32_t cnt = 0;
+    uint64_t fire = 0ull;
+    walk_ops<KW>(w.words, w.nwords, l0, l1, cnt, fire);
+    cnt &= 7u;
+    if (cnt != 0u || fire != 0ull) {
+      double re = s.re[i], im = s.im[i];
+      apply_fire(fire, w.ftab, re, im);
+      apply_pi4(cnt, re, im);
+      s.re[i] = re;
+      s.im[i] = im;
+    }
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_chain(Ctl* ctl, Bufs bufs, unsigned long long* itab,
+                                               const __grid_constant__ ChainArgs a,
+                                               unsigned long long* plog) {
+  const uint64_t n0 = ctl->nnz;
+  if (amp_took(ctl, 1u)) {
+    if (blockIdx.x == 0 && threadIdx.x < 32 && ctl->status == 0u) {
+      for (uint32_t k = 0; k < a.nsteps; ++k) {
+        const ChainStep& st = a.steps[k];
+        carry_label_masks(ctl, st.kind == PASS_LAYER ? st.l.mg : st.g.mg);
+        __syncwarp();
+      }
+      if (plog && threadIdx.x == 0) {
+        plog[0] = 0ull;
+        plog[1] = n0;
+      }
+    }
+    return;
+  }
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) plog[0] = n0;
+  uint32_t serial = 0;
+  uint64_t tag = 0;
+  for (uint32_t k = 0; k < a.nsteps; ++k) {
+    const ChainStep& st = a.steps[k];
+    serial = st.kind == PASS_LAYER ? st.l.pass_serial : st.g.pass_serial;
+    tag = st.kind == PASS_LAYER ? st.l.fail_tag : st.g.fail_tag;
+    if (st.kind == PASS_LAYER) {
+      layer_build<KW>(ctl, bufs, itab, st.l, nullptr);
+      grid_barrier(ctl, serial, tag);
+      layer_emit<KW>(ctl, bufs, itab, st.l, nullptr);
+    } else {
+      gather_build<KW>(ctl, bufs, itab, st.g, nullptr);
+      grid_barrier(ctl, serial, tag);
+      gather_emit<KW>(ctl, bufs, itab, st.g, nullptr);
+    }
+    grid_barrier(ctl, serial, tag);
+  }
+  if (a.w.ngates) {
+    chain_walk<KW>(ctl, bufs, a.w);
+    grid_barrier(ctl, serial + 1u, tag);
+  }
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) plog[1] = ctl->nnz;
+}
+
 int grid_of(uint64_t work, int threads, int max_blocks) {
   uint64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -1161,9 +1339,7 @@ int grid_of(uint64_t work, int threads, int max_blocks) {
 
 }  // namespace
 
-int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
-                      unsigned long long* itab, uint32_t epoch, const LayerLaunch& l,
-                      uint64_t nnz_bound, int part, unsigned long long* plog) {
+static LayerArgs layer_args(const LayerLaunch& l, uint32_t epoch) {
   LayerArgs a;
   std::memset(&a, 0, sizeof(a));
   for (uint32_t j = 0; j < l.d; ++j) a.ops[j] = l.ops[j];
@@ -1178,6 +1354,30 @@ int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   a.epoch = epoch;
   a.mg = l.mg;
   a.fallback = l.fallback;
+  return a;
+}
+
+static GatherArgs gather_args(const BranchLaunch& b, uint32_t epoch) {
+  GatherArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.op = b.op;
+  a.eps2 = b.eps * b.eps;
+  a.eps = b.eps;
+  a.capacity = b.capacity;
+  a.fail_tag = b.fail_tag;
+  a.load_pct = b.load_pct;
+  a.max_log2 = b.max_log2;
+  a.pass_serial = b.pass_serial;
+  a.epoch = epoch;
+  a.mg = b.mg;
+  a.fallback = b.fallback;
+  return a;
+}
+
+int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                      unsigned long long* itab, uint32_t epoch, const LayerLaunch& l,
+                      uint64_t nnz_bound, int part, unsigned long long* plog) {
+  const LayerArgs a = layer_args(l, epoch);
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {
@@ -1192,6 +1392,61 @@ int launch_layer_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
       k_layer_emit<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// Resident blocks of k_chain per SM at `threads` (0 if the query fails).
+template <int KW>
+static int chain_blocks_per_sm(int threads) {
+  static int cached[5] = {-1, -1, -1, -1, -1};   // threads 32 << k, k = 0..3
+  int k = 0;
+  while (k < 4 && (32 << k) < threads) ++k;
+  if (cached[k] < 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chain<KW>, threads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      nb = 0;
+    }
+    cached[k] = nb;
+  }
+  return cached[k];
+}
+
+int launch_chain(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                 unsigned long long* itab, const ChainStepDesc* steps, uint32_t nsteps,
+                 const ChainWalk& w, uint64_t nnz_bound, unsigned long long* plog) {
+  if (nsteps > kChainSteps || w.npar > kMaxAmpParity) return 0;
+  thread_local ChainArgs a;   // ~21 KB: kept off the stack
+  std::memset(&a, 0, sizeof(a));
+  a.nsteps = nsteps;
+  for (uint32_t k = 0; k < nsteps; ++k) {
+    a.steps[k].kind = steps[k].kind;
+    if (steps[k].kind == PASS_LAYER) a.steps[k].l = layer_args(steps[k].lay, steps[k].epoch);
+    else a.steps[k].g = gather_args(steps[k].br, steps[k].epoch);
+  }
+  a.w.words = reinterpret_cast<const uint4*>(w.words);
+  a.w.ftab = reinterpret_cast<const double2*>(w.ftab);
+  a.w.nwords = w.nwords;
+  a.w.has_phase = w.has_phase;
+  a.w.npar = w.npar;
+  a.w.ngates = w.ngates;
+  for (uint32_t c = 0; c < 2 * w.npar; ++c) a.w.par[c] = w.par[c];
+  const int threads = lc.threads < 256 ? lc.threads : 256;
+  const int sms = lc.max_blocks * lc.threads / 2048;
+  const int per_sm = key_words == 1 ? chain_blocks_per_sm<1>(threads) : chain_blocks_per_sm<2>(threads);
+  if (per_sm <= 0 || sms <= 0) return 0;
+  const int blocks = grid_of(nnz_bound, threads, per_sm * sms < 0x7FFF ? per_sm * sms : 0x7FFF);
+  void* args[] = {&ctl, &bufs, &itab, &a, &plog};
+  const cudaError_t e =
+      key_words == 1
+          ? cudaLaunchCooperativeKernel((const void*)k_chain<1>, dim3(blocks), dim3(threads), args, 0,
+                                        (cudaStream_t)lc.stream)
+          : cudaLaunchCooperativeKernel((const void*)k_chain<2>, dim3(blocks), dim3(threads), args, 0,
+                                        (cudaStream_t)lc.stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return 1;
 }
 
 template <int KW, int POST>
@@ -1268,18 +1523,7 @@ int launch_itab_clear(const LaunchCfg& lc, unsigned long long* itab, uint64_t ns
 int launch_gather_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        unsigned long long* itab, uint32_t epoch, const BranchLaunch& b,
                        uint64_t nnz_bound, int part, unsigned long long* plog) {
-  GatherArgs a;
-  a.op = b.op;
-  a.eps2 = b.eps * b.eps;
-  a.eps = b.eps;
-  a.capacity = b.capacity;
-  a.fail_tag = b.fail_tag;
-  a.load_pct = b.load_pct;
-  a.max_log2 = b.max_log2;
-  a.pass_serial = b.pass_serial;
-  a.epoch = epoch;
-  a.mg = b.mg;
-  a.fallback = b.fallback;
+  const GatherArgs a = gather_args(b, epoch);
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {

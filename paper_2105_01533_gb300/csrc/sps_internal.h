@@ -319,7 +319,8 @@ struct Ctl {
   unsigned int amp_fail;         // set by threads that find the form not applicable
   unsigned int amp_backoff;      // passes still to skip after failed attempts
   unsigned int amp_streak;       // failed attempts in a row
-  unsigned int amp_pad;
+  // grid barrier of cooperative launches: generation << 16 | blocks arrived
+  unsigned int grid_bar;
 };
 
 // Mask buffer indices of one label-writing launch, packed rd | wr << 8 | rs << 16.
@@ -473,6 +474,31 @@ struct AmpLaunch {
 int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                     unsigned long long* itab, uint32_t epoch, uint32_t force, const AmpLaunch& l,
                     uint64_t nnz_bound, int part, unsigned long long* plog);
+// The passes of a run an amplitude-only attempt stands in for (its fallback),
+// in one cooperative launch: at once done if the attempt took the run, else
+// each pass as its separate kernels would run it, with grid barriers between
+// them, then the phase-only run after them (a direct op stream, or a sign
+// parity as the attempt applies it). Returns 1 when enqueued, 0 when the
+// chain does not fit one launch (launch the passes one by one), -1 on a
+// launch error.
+constexpr uint32_t kChainSteps = kMaxAmpGates;
+struct ChainStepDesc {
+  uint32_t kind;    // PASS_BRANCH (gather form) or PASS_LAYER
+  uint32_t epoch;   // its index-table epoch
+  BranchLaunch br;  // PASS_BRANCH
+  LayerLaunch lay;  // PASS_LAYER
+};
+struct ChainWalk {
+  const OpWord* words;   // direct op stream (nwords > 0), or
+  const double* ftab;
+  uint32_t nwords, has_phase;
+  const uint64_t* par;   // npar sign conditions (c0, c1 pairs)
+  uint32_t npar;
+  uint32_t ngates;       // gates of the run; 0: none after the passes
+};
+int launch_chain(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
+                 unsigned long long* itab, const ChainStepDesc* steps, uint32_t nsteps,
+                 const ChainWalk& w, uint64_t nnz_bound, unsigned long long* plog);
 // Expansion pass (PASS_EXPAND); f, m: its tables in device memory.
 struct ExpandLaunch {
   const double* f;

@@ -1021,6 +1021,7 @@ __global__ void k_reset_status(Ctl* ctl) {
   ctl->fail_gate = 0ull;
   ctl->out_count = 0ull;
   ctl->blocks_done = 0u;
+  ctl->grid_bar = 0u;   // a barrier that timed out left blocks counted
   for (uint32_t b = 0; b < 3; ++b) unknown_label_masks(ctl, b);
 }
 

@@ -23,13 +23,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsps.so")
 
 SPS_OK, SPS_ERR_ARG, SPS_ERR_CAPACITY, SPS_ERR_TABLE_FULL = 0, 1, 2, 3
-SPS_ERR_CUDA, SPS_ERR_OOM, SPS_ERR_NO_DEVICE = 4, 5, 6
+SPS_ERR_CUDA, SPS_ERR_OOM, SPS_ERR_NO_DEVICE, SPS_ERR_TIMEOUT = 4, 5, 6, 7
 SPS_OPT_LOAD_FACTOR_PCT, SPS_OPT_PROBE_LIMIT, SPS_OPT_BLOCK_THREADS = 1, 2, 3
 SPS_OPT_MAX_FUSED_OPS, SPS_OPT_COOP_WIDTH, SPS_OPT_PROFILE = 4, 5, 6
 SPS_OPT_BITSLICE_MIN_OPS, SPS_OPT_SMALL_RUN_CAP, SPS_OPT_BITSLICE_MIN_NNZ = 7, 8, 9
 SPS_OPT_BRANCH_FORM, SPS_OPT_BITSLICE_GROUPS, SPS_OPT_EXPAND, SPS_OPT_FOLD = 10, 11, 12, 13
 SPS_OPT_COMMUTE, SPS_OPT_LAYER_GATES, SPS_OPT_EXPAND_WALK, SPS_OPT_FUSED_LABELS = 14, 15, 16, 17
 SPS_OPT_AMP_ONLY, SPS_OPT_BITSLICE_JIT, SPS_OPT_PLAN_CACHE = 18, 19, 20
+SPS_OPT_FALLBACK_CHAIN = 21
 KIND_SMALL_RUN, KIND_GATHER_BUILD, KIND_GATHER_EMIT = 4, 5, 6
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 

@@ -92,3 +92,13 @@ def test_roofline_picks_the_dominant_kernel_and_scales_traffic(bench, monkeypatc
     assert abs(r["method_passes"]["rate"] - round(work, 2)) < 0.01
     assert r["traffic"] == 3.0 * 65536      # expansions count their outputs
     assert set(r["time_share"]) == {"k_expand", "k_measure"}
+
+
+def test_chain_launch_is_credited_only_when_it_ran(bench):
+    """An attempted run's passes in one launch (kind 11): nothing when the
+    attempt took the run (n_in 0), else each of its d passes reads and writes
+    the state once."""
+    assert bench.algorithmic_bytes(rec(11, 0, 50, nops=8)) == 0.0
+    assert bench.moved_bytes(rec(11, 0, 50, nops=8)) == 0.0
+    assert bench.algorithmic_bytes(rec(11, 40, 50, nops=8)) == 32 * (40 + 50) * 8
+    assert bench.kernel_name(rec(11, 40, 50)) == "k_chain"

@@ -212,3 +212,98 @@ def test_sign_runs_taken_by_parity(phases):
     identical(got, ref)
     assert upd == upd0 and took > 0
     compare_states(got, oracle(n, parts, 1e-14), 1e-14)
+
+
+CHAIN_KIND = 11
+
+
+def run_counted(n, parts, eps, cap, opts):
+    """As run(), also returning the kernel launches and the chain records
+    (kind 11) seen."""
+    st = sps.SparseState(n, cap)
+    st.set_option(sps.SPS_OPT_PROFILE, 1)
+    for o, v in opts:
+        st.set_option(o, v)
+    c0 = st.counters().kernel_launches
+    chains = []
+    for gates in parts:
+        st.apply(W.to_array(gates), eps)
+        chains += [r for r in st.profile_read() if r["kind"] == CHAIN_KIND]
+    launches = st.counters().kernel_launches - c0
+    got = st.get_amplitudes()
+    upd = st.updates()
+    st.close()
+    return got, upd, launches, chains
+
+
+@pytest.mark.parametrize("n,modes,layers,lay", [(16, 3, 24, 4), (24, 2, 16, 1), (40, 3, 8, 4)])
+def test_fallback_chain_equals_separate_launches(n, modes, layers, lay):
+    """The passes an attempt stands in for, as one cooperative launch: while
+    the sector fills (attempts fail) the launch runs the layer or gather passes
+    and the phase run; once it is full the launch returns at once. The state
+    and update count equal the separate launches' bit for bit, and the oracle's."""
+    parts = givens_parts(n, modes, layers, seed=3 * n + modes, per_part=2)
+    base = [(sps.SPS_OPT_LAYER_GATES, lay), (sps.SPS_OPT_SMALL_RUN_CAP, 0),
+            (sps.SPS_OPT_AMP_ONLY, 1)]
+    got, upd, nl, chains = run_counted(n, parts, 1e-14, 1 << 16, base)
+    ref, upd0, nl0, chains0 = run_counted(n, parts, 1e-14, 1 << 16,
+                                          base + [(sps.SPS_OPT_FALLBACK_CHAIN, 0)])
+    identical(got, ref)
+    assert upd == upd0
+    assert not chains0 and len(chains) > 0
+    assert any(r["n_in"] > 0 for r in chains), "no chain ran its passes"
+    assert any(r["n_in"] == 0 for r in chains), "no attempt took a run"
+    assert nl < nl0
+    compare_states(got, oracle(n, parts, 1e-14), 1e-14)
+
+
+def test_givens_layer_is_three_launches():
+    """Steady state of the Givens workload (every label of the sector present):
+    each layer of n/2 Givens and n/2 CZ is the index check, the attempt and the
+    chain, whatever the layer size of the fallback passes."""
+    n, modes = 32, 3
+    g = W.givens_workload(seed=5, nqubits=n, modes=modes, layers=40)
+    prep, rest = g[:modes + 20 * n], g[modes + 20 * n:]
+    st = sps.SparseState(n, 1 << 14)
+    st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)
+    st.apply(prep, 1e-14)
+    st.sync()
+    c0 = st.counters().kernel_launches
+    st.apply(rest, 1e-14)
+    st.sync()
+    per_layer = (st.counters().kernel_launches - c0) / 20
+    assert per_layer <= 3.0, per_layer
+    orc = OracleState(n)
+    orc.apply(g, eps=1e-14)
+    compare_states(st.get_amplitudes(), orc.get(), 1e-14)
+    st.close()
+
+
+def test_mixed_circuits_chain_on_and_off():
+    """Runs with gather-form single gates, layers and failed attempts that
+    create and prune labels: chain on and off agree bit for bit."""
+    n = 30
+    rng = W.SplitMix64(901)
+    parts = [[W.H(q) for q in range(8)]]
+    for k in range(10):
+        recs = []
+        for _ in range(8):
+            q = rng.distinct(14, 3)
+            c = rng.below(4)
+            if c == 0:
+                recs.append(W.H(q[0]))
+            elif c == 1:
+                recs.append(W.Ry(q[0], rng.angle()))
+            elif c == 2:
+                recs.append(W.Givens(q[0], q[1], rng.angle()))
+            else:
+                recs.append(W.CZ(q[0], q[1]))
+        parts.append(recs)
+    for eps in (0.0, 1e-3):
+        base = [(sps.SPS_OPT_SMALL_RUN_CAP, 0), (sps.SPS_OPT_AMP_ONLY, 1)]
+        got, upd, _, chains = run_counted(n, parts, eps, 1 << 14, base)
+        ref, upd0, _, _ = run_counted(n, parts, eps, 1 << 14,
+                                      base + [(sps.SPS_OPT_FALLBACK_CHAIN, 0)])
+        identical(got, ref)
+        assert upd == upd0 and chains
+        compare_states(got, oracle(n, parts, eps), eps)

@@ -326,9 +326,19 @@ def test_counters_count_launches():
     st.apply(gates, 0.0)
     c = st.counters()
     assert c.fused_passes == 2 and c.branch_passes == 2
-    # a branching pass: the amplitude-only attempt (index, attempt) and the
-    # gather kernels (build, emit), which return at once if the attempt took it
-    assert c.kernel_launches - c0 == 2 * 1 + 2 * 4
+    # a branching pass: the amplitude-only attempt (index, attempt) and its
+    # gather kernels (build, emit) in one cooperative launch, which returns at
+    # once if the attempt took the pass
+    assert c.kernel_launches - c0 == 2 * 1 + 2 * 3
+    st.close()
+    st = sps.SparseState(24, 4096)        # the gather kernels as separate launches
+    st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)
+    st.set_option(sps.SPS_OPT_EXPAND, 0)
+    st.set_option(sps.SPS_OPT_FALLBACK_CHAIN, 0)
+    st.sync()
+    c0 = st.counters().kernel_launches
+    st.apply(gates, 0.0)
+    assert st.counters().kernel_launches - c0 == 2 * 1 + 2 * 4
     st.close()
     st = sps.SparseState(24, 4096)
     st.set_option(sps.SPS_OPT_SMALL_RUN_CAP, 0)
