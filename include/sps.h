@@ -336,6 +336,43 @@ typedef enum sps_option {
  * SPS_ERR_ARG for an unknown option or out-of-range value. */
 sps_status sps_set_option(sps_state* s, sps_option opt, int64_t value);
 
+/* ---- Autotuner of the plain path ---------------------------------------------
+ * sps_tune times whole steps of a circuit on the state (sps_reset, sps_apply,
+ * sps_sync; wall clock, mean of `repeats` after one untimed step per setting)
+ * and searches, one option at a time from the state's current settings:
+ * SPS_OPT_LOAD_FACTOR_PCT (index-table load: 30, 50, 70), SPS_OPT_BITSLICE_GROUPS
+ * (bit-sliced tile: 0, 8, 16, 32), SPS_OPT_FUSED_LABELS (0, 2, 4, 8) and
+ * SPS_OPT_MAX_FUSED_OPS (fusion length: 128, 256, 512). The first three
+ * change no result bit; the fusion length changes how phases of a run are
+ * combined, so results agree to rounding. The best setting is left on the
+ * state, which is left reset. A choice belongs to a size class: label words
+ * kw (1 or 2) and log2peak = ceil(log2(projected peak nonzeros)), the peak
+ * being min(capacity, the bound after the circuit's passes, doubling at every
+ * branching gate). With cache_path non-null, a class already in that text file
+ * takes its recorded choice without timing (from_cache = 1), and a newly timed
+ * choice is appended as one line "sps-tune 1 kw=.. log2peak=.. load_factor_pct=..
+ * bitslice_groups=.. fused_labels=.. max_fused_ops=.. ms=..". Errors:
+ * SPS_ERR_ARG (bad record: as sps_apply; repeats outside 1..1000), or the
+ * status of a failing step. */
+typedef struct sps_tune_choice {
+  uint32_t kw, log2peak;       /* the size class */
+  uint32_t load_factor_pct;
+  uint32_t bitslice_groups;
+  uint32_t fused_labels;
+  uint32_t max_fused_ops;
+  uint32_t from_cache;         /* 1: taken from the cache file, not timed */
+  float ms;                    /* mean step time of the choice (as recorded) */
+} sps_tune_choice;
+
+sps_status sps_tune(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
+                    uint32_t repeats, const char* cache_path, sps_tune_choice* out);
+
+/* Host-only: the choice recorded for size class (kw, log2peak) in a tuning
+ * cache file (the last valid line of the class). SPS_ERR_ARG if the file
+ * cannot be read or holds no valid line for the class. */
+sps_status sps_tune_cache_lookup(const char* path, uint32_t kw, uint32_t log2peak,
+                                 sps_tune_choice* out);
+
 /* Per-state counters since creation (host-side bookkeeping, no sync). */
 typedef struct sps_counters {
   uint64_t gates;            /* gates accepted by sps_apply */
@@ -435,6 +472,16 @@ sps_status sps_batch_add(sps_batch* b, uint32_t nqubits, uint64_t capacity,
  * passes (0 = to completion). The first call allocates device memory. */
 sps_status sps_batch_run(sps_batch* b, uint32_t max_passes);
 
+/* One step of the batch as a captured CUDA graph: every circuit reset to
+ * |0...0>, then the persistent launch advancing each by up to max_passes
+ * passes (0 = to completion), as sps_batch_reset + sps_batch_run enqueue
+ * them. The first call (and the first after max_passes or the launch
+ * configuration changed) captures the step on a private stream and
+ * instantiates it; every call launches the graph on the batch's stream (one
+ * graph launch per step). The results equal those of the two calls. Errors:
+ * SPS_ERR_CUDA if the capture or the instantiation fails (nothing enqueued). */
+sps_status sps_batch_run_graph(sps_batch* b, uint32_t max_passes);
+
 /* Waits for the batch's stream and reads back every circuit's progress;
  * *unfinished (nullable) receives the number still to run. */
 sps_status sps_batch_sync(sps_batch* b, uint32_t* unfinished);
@@ -472,10 +519,14 @@ sps_status sps_batch_counts(sps_batch* b, uint32_t* ncircuits, uint64_t* launche
 sps_status sps_batch_updates(sps_batch* b, uint64_t* total);
 
 /* ---- Serving: continuous batching of requests ---------------------------------
- * A request is a circuit from |0...0> with a capacity (its projected peak
- * nonzero count). Requests are admitted in arrival order while an active slot
- * and enough of the memory budget are free (small requests: 64 B per capacity
- * entry; large ones, capacity > 65,536: 96 B per entry plus 4 MiB). Each
+ * A request is a circuit from |0...0> with a capacity (the most nonzeros its
+ * state may hold). The server charges it for its projected peak instead when
+ * that is smaller: min(capacity, the nonzero bound after its passes, starting
+ * from 1 and doubling at every branching gate), which no state of the circuit
+ * can exceed, so the result and any capacity error are those of the declared
+ * capacity. Requests are admitted in arrival order while an active slot and
+ * enough of the memory budget are free (small requests, projected peak <=
+ * 65,536: 64 B per entry; large ones: 96 B per entry plus 4 MiB). Each
  * sps_server_tick admits what fits, advances every active request by at most
  * passes_per_tick passes (0 = to completion) - small requests together in one
  * batched launch on the server's stream, large ones each as a whole-GPU state
@@ -540,7 +591,7 @@ sps_status sps_server_stats(sps_server* s, uint64_t* ticks, uint64_t* launches,
  * qubits in_hi/out_hi are ignored and may be NULL. Input labels must be
  * distinct and use only qubits below nqubits.
  * Scratch: a fixed array inside the library image, 8,391,776 bytes (262,144
- * table slots of 32 B and a 3,160-byte control block), held by every GPU that
+ * table slots of 32 B and a 3,168-byte control block), held by every GPU that
  * loads the library until the process exits. It allocates nothing: no
  * cudaMalloc, cudaFree or allocating library call. Limit: n_in <= 65,536,
  * else SPS_ERR_CAPACITY before anything is launched.

@@ -3,6 +3,7 @@
 // the gate application runs in the kernels of sps_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1777,6 +1778,148 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
       return SPS_OK;
   }
   return SPS_ERR_ARG;
+}
+
+// ---- autotuner of the plain path --------------------------------------------------
+// Options that shape how the path runs but not what it computes, plus the
+// fusion length, chosen per size class (label width, log2 of the projected
+// peak nonzeros) by timing whole steps; the choice can be kept in a text file,
+// one line per class: "sps-tune 1 kw=K log2peak=P load_factor_pct=.. ...".
+static bool tune_choice_ok(const sps_tune_choice& c) {
+  return c.load_factor_pct >= 10 && c.load_factor_pct <= 90 && c.bitslice_groups <= 32 &&
+         (c.bitslice_groups & 1u) == 0 &&
+         (c.fused_labels == 0 || c.fused_labels == 1 || c.fused_labels == 2 ||
+          c.fused_labels == 4 || c.fused_labels == 8) &&
+         c.max_fused_ops >= 1 && c.max_fused_ops <= kMaxFusedOps;
+}
+
+sps_status sps_tune_cache_lookup(const char* path, uint32_t kw, uint32_t log2peak,
+                                 sps_tune_choice* out) {
+  if (!path || !out || (kw != 1 && kw != 2)) return SPS_ERR_ARG;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return SPS_ERR_ARG;
+  char line[512];
+  bool found = false;
+  sps_tune_choice best;
+  std::memset(&best, 0, sizeof(best));
+  while (std::fgets(line, sizeof(line), f)) {
+    sps_tune_choice c;
+    std::memset(&c, 0, sizeof(c));
+    float ms = 0.f;
+    if (std::sscanf(line,
+                    "sps-tune 1 kw=%u log2peak=%u load_factor_pct=%u bitslice_groups=%u "
+                    "fused_labels=%u max_fused_ops=%u ms=%f",
+                    &c.kw, &c.log2peak, &c.load_factor_pct, &c.bitslice_groups, &c.fused_labels,
+                    &c.max_fused_ops, &ms) != 7)
+      continue;
+    if (c.kw != kw || c.log2peak != log2peak || !tune_choice_ok(c)) continue;
+    c.ms = ms;
+    c.from_cache = 1;
+    best = c;   // a later line of the class replaces an earlier one
+    found = true;
+  }
+  std::fclose(f);
+  if (!found) return SPS_ERR_ARG;
+  *out = best;
+  return SPS_OK;
+}
+
+static void tune_set(sps_state* s, const sps_tune_choice& c) {
+  s->load_pct = c.load_factor_pct;
+  s->bs_groups = c.bitslice_groups;
+  s->fused_labels = (int)c.fused_labels;
+  s->max_fused_ops = c.max_fused_ops;
+}
+
+// Mean wall time of `repeats` whole steps (reset, apply, sync) under choice c,
+// after one untimed step that compiles and uploads the plan for it.
+static sps_status tune_time(sps_state* s, const sps_gate* gates, size_t ngates, double eps,
+                            uint32_t repeats, const sps_tune_choice& c, float* ms) {
+  tune_set(s, c);
+  double total = 0.0;
+  for (uint32_t r = 0; r <= repeats; ++r) {
+    const auto t0 = std::chrono::steady_clock::now();
+    sps_status st = sps_reset(s);
+    if (st == SPS_OK) st = sps_apply(s, gates, ngates, eps, nullptr);
+    if (st == SPS_OK) st = sps_sync(s, nullptr);
+    if (st != SPS_OK) return st;
+    const auto t1 = std::chrono::steady_clock::now();
+    if (r > 0) total += std::chrono::duration<double, std::milli>(t1 - t0).count();
+  }
+  *ms = (float)(total / repeats);
+  return SPS_OK;
+}
+
+sps_status sps_tune(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
+                    uint32_t repeats, const char* cache_path, sps_tune_choice* out) {
+  if (!s || !out || (ngates && !gates) || !(prune_eps >= 0.0) || repeats < 1 || repeats > 1000)
+    return SPS_ERR_ARG;
+  std::vector<Pass> passes;
+  size_t bad = 0;
+  const sps_status cs = compile(gates, ngates, s->nqubits, 0, &passes, &bad);
+  if (cs != SPS_OK) return cs;
+  const uint64_t peak = projected_peak(passes, s->capacity);
+  uint32_t lg = 0;
+  while (lg < 63 && (1ull << lg) < peak) ++lg;
+  const uint32_t kw = (uint32_t)s->kw;
+  if (cache_path) {
+    sps_tune_choice c;
+    if (sps_tune_cache_lookup(cache_path, kw, lg, &c) == SPS_OK) {
+      tune_set(s, c);
+      const sps_status rs = sps_reset(s);
+      if (rs != SPS_OK) return rs;
+      *out = c;
+      return SPS_OK;
+    }
+  }
+  sps_tune_choice best;
+  std::memset(&best, 0, sizeof(best));
+  best.kw = kw;
+  best.log2peak = lg;
+  best.load_factor_pct = s->load_pct;
+  best.bitslice_groups = s->bs_groups;
+  best.fused_labels = (uint32_t)s->fused_labels;
+  best.max_fused_ops = s->max_fused_ops;
+  sps_status st = tune_time(s, gates, ngates, prune_eps, repeats, best, &best.ms);
+  if (st != SPS_OK) return st;
+  // one option at a time, from the best so far
+  static const uint32_t kLoad[] = {30, 50, 70};
+  static const uint32_t kGroups[] = {0, 8, 16, 32};
+  static const uint32_t kLabels[] = {0, 2, 4, 8};
+  static const uint32_t kFused[] = {128, 256, 512};
+  for (int dim = 0; dim < 4; ++dim) {
+    const uint32_t* vals = dim == 0 ? kLoad : dim == 1 ? kGroups : dim == 2 ? kLabels : kFused;
+    const int nv = dim == 0 || dim == 3 ? 3 : 4;
+    const sps_tune_choice base = best;
+    for (int k = 0; k < nv; ++k) {
+      sps_tune_choice c = base;
+      uint32_t* field = dim == 0 ? &c.load_factor_pct : dim == 1 ? &c.bitslice_groups
+                        : dim == 2 ? &c.fused_labels : &c.max_fused_ops;
+      if (*field == vals[k]) continue;
+      *field = vals[k];
+      if (!tune_choice_ok(c)) continue;
+      st = tune_time(s, gates, ngates, prune_eps, repeats, c, &c.ms);
+      if (st != SPS_OK) return st;
+      if (c.ms < best.ms) best = c;
+    }
+  }
+  tune_set(s, best);
+  st = sps_reset(s);
+  if (st != SPS_OK) return st;
+  if (cache_path) {
+    FILE* f = std::fopen(cache_path, "a");
+    if (f) {
+      std::fprintf(f,
+                   "sps-tune 1 kw=%u log2peak=%u load_factor_pct=%u bitslice_groups=%u "
+                   "fused_labels=%u max_fused_ops=%u ms=%.4f\n",
+                   best.kw, best.log2peak, best.load_factor_pct, best.bitslice_groups,
+                   best.fused_labels, best.max_fused_ops, best.ms);
+      std::fclose(f);
+    }
+  }
+  best.from_cache = 0;
+  *out = best;
+  return SPS_OK;
 }
 
 sps_status sps_get_counters(sps_state* s, sps_counters* out) {

@@ -147,31 +147,31 @@ int launch_batch_reset(void* stream, BatchDesc* desc, uint32_t ncirc) {
 
 size_t batch_smem_bytes(uint32_t smem_cap) { return (size_t)smem_cap * (64 + 16); }
 
+int batch_kernel_attr(const BatchConfig& cfg) {
+  const int smem = (int)batch_smem_bytes(cfg.smem_cap);
+  const cudaError_t e =
+      cfg.threads <= 256   ? cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+      : cfg.threads <= 512 ? cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                           : cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e == cudaSuccess ? 0 : -1;
+}
+
 int launch_batch(void* stream, int sms, const BatchConfig& cfg, BatchDesc* desc,
                  const uint32_t* order, uint32_t ncirc, uint32_t* head, uint32_t* gtabs,
-                 uint32_t gtab_slots, uint32_t max_passes) {
+                 uint32_t gtab_slots, uint32_t max_passes, bool set_attr) {
   const size_t smem = batch_smem_bytes(cfg.smem_cap);
   const int blocks = sms * (int)cfg.blocks_per_sm;
   cudaStream_t st = (cudaStream_t)stream;
-  if (cfg.threads <= 256) {
-    if (cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return -1;
+  if (set_attr && batch_kernel_attr(cfg) < 0) return -1;
+  if (cfg.threads <= 256)
     k_batch<256><<<blocks, cfg.threads, smem, st>>>(desc, order, ncirc, head, gtabs, gtab_slots,
                                                     max_passes, cfg.smem_cap);
-  } else if (cfg.threads <= 512) {
-    if (cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return -1;
+  else if (cfg.threads <= 512)
     k_batch<512><<<blocks, cfg.threads, smem, st>>>(desc, order, ncirc, head, gtabs, gtab_slots,
                                                     max_passes, cfg.smem_cap);
-  } else {
-    if (cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return -1;
+  else
     k_batch<1024><<<blocks, cfg.threads, smem, st>>>(desc, order, ncirc, head, gtabs, gtab_slots,
                                                      max_passes, cfg.smem_cap);
-  }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -259,12 +259,27 @@ struct sps_batch {
   std::vector<BatchDesc> host_desc;   // descriptors as uploaded
   std::vector<BatchDesc> result;      // after sync
   uint64_t launches = 0;
+  // one step (reset + persistent launch) captured as a CUDA graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  uint32_t g_passes = 0;
+  BatchConfig g_cfg{0, 0, 0, 0};
 };
 
 namespace {
 
+void drop_graph(sps_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  cudaGetLastError();
+}
+
 void batch_free(sps_batch* b) {
   cudaStreamSynchronize(b->stream);
+  drop_graph(b);
   for (auto& a : b->allocs) hook_free(a.p, a.bytes, b->stream);
   b->allocs.clear();
   cudaStreamSynchronize(b->stream);
@@ -408,6 +423,7 @@ sps_status sps_batch_create(void* cuda_stream, sps_batch** out) {
 void sps_batch_destroy(sps_batch* b) {
   if (!b) return;
   batch_free(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
 }
 
@@ -451,6 +467,45 @@ sps_status sps_batch_run(sps_batch* b, uint32_t max_passes) {
   if (launch_batch(b->stream, b->sms, b->cfg, b->desc, b->order, (uint32_t)b->circs.size(), b->head,
                    b->gtabs, b->gtab_slots, max_passes) < 0)
     return cuda_st(cudaGetLastError());
+  ++b->launches;
+  return SPS_OK;
+}
+
+sps_status sps_batch_run_graph(sps_batch* b, uint32_t max_passes) {
+  if (!b) return SPS_ERR_ARG;
+  if (!b->built) {
+    const sps_status st = batch_build(b);
+    if (st != SPS_OK) return st;
+  }
+  if (b->circs.empty()) return SPS_OK;
+  const BatchConfig& c = b->cfg;
+  if (b->gexec && (max_passes != b->g_passes || c.threads != b->g_cfg.threads ||
+                   c.blocks_per_sm != b->g_cfg.blocks_per_sm || c.smem_cap != b->g_cfg.smem_cap))
+    drop_graph(b);
+  if (!b->gexec) {
+    if (!b->cap_stream &&
+        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cuda_st(cudaGetLastError());
+    if (batch_kernel_attr(c) < 0) return cuda_st(cudaGetLastError());
+    const uint32_t n = (uint32_t)b->circs.size();
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return cuda_st(cudaGetLastError());
+    bool ok = launch_batch_reset(b->cap_stream, b->desc, n) >= 0 &&
+              cudaMemsetAsync(b->head, 0, sizeof(uint32_t), b->cap_stream) == cudaSuccess &&
+              launch_batch(b->cap_stream, b->sms, c, b->desc, b->order, n, b->head, b->gtabs,
+                           b->gtab_slots, max_passes, false) >= 0;
+    cudaGraph_t g = nullptr;
+    ok = cudaStreamEndCapture(b->cap_stream, &g) == cudaSuccess && ok;
+    if (ok && cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) ok = false;
+    b->graph = g;
+    if (!ok) {
+      drop_graph(b);
+      return SPS_ERR_CUDA;
+    }
+    b->g_passes = max_passes;
+    b->g_cfg = c;
+  }
+  if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) return cuda_st(cudaGetLastError());
   ++b->launches;
   return SPS_OK;
 }

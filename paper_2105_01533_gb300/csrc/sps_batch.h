@@ -37,9 +37,12 @@ struct BatchConfig {
 
 size_t batch_smem_bytes(uint32_t smem_cap);
 bool batch_config_ok(const BatchConfig& c);
+// set_attr: set the kernel's shared-memory attribute first (else the caller
+// did, with batch_kernel_attr: not a stream operation, kept out of captures).
 int launch_batch(void* stream, int sms, const BatchConfig& cfg, BatchDesc* desc,
                  const uint32_t* order, uint32_t ncirc, uint32_t* head, uint32_t* gtabs,
-                 uint32_t gtab_slots, uint32_t max_passes);
+                 uint32_t gtab_slots, uint32_t max_passes, bool set_attr = true);
+int batch_kernel_attr(const BatchConfig& cfg);
 // Sets every listed circuit to |0...0> with no progress (one thread per circuit).
 int launch_batch_reset(void* stream, BatchDesc* desc, uint32_t ncirc);
 // Packs a compiled circuit's passes into blob; *pass_off locates its RunPass

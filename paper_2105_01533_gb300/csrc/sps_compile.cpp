@@ -867,4 +867,22 @@ void build_bitslice_rows(const Pass& p, uint32_t nqubits, const uint64_t extra[2
 
 }  // namespace
 
+// The most nonzeros a state can reach from |0...0> through these passes: every
+// branching gate at most doubles the count (an expansion of d gates, d
+// doublings; a layer, one per gate), never above the capacity.
+uint64_t projected_peak(const std::vector<Pass>& passes, uint64_t capacity) {
+  uint64_t b = 1, peak = 1;
+  for (const Pass& p : passes) {
+    uint32_t doublings = 0;
+    if (p.kind == PASS_BRANCH) doublings = 1;
+    if (p.kind == PASS_EXPAND) doublings = p.ex_d;
+    if (p.kind == PASS_LAYER) doublings = (uint32_t)p.lay.size();
+    for (uint32_t k = 0; k < doublings && b < capacity; ++k) b *= 2;
+    if (b > capacity) b = capacity;
+    if (b > peak) peak = b;
+    if (peak == capacity) break;
+  }
+  return peak < capacity ? peak : capacity;
+}
+
 }  // namespace sps

@@ -45,13 +45,22 @@ struct GatherArgs {
 
 // A skipped emit still advances the label masks: the labels are those of its
 // input, so buffer wr gets buffer rd's masks and rs is emptied (block 0).
+// Buffer b set to masks m by the calling warp, one stripe per lane.
+__device__ __forceinline__ void warp_set_label_masks(Ctl* ctl, uint32_t b, const LabelMasks& m) {
+  static_assert(kMaskStripes == 32, "one stripe per lane");
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned long long* p = ctl->lm[b][lane];
+  p[0] = lane == 0 ? m.or0 : 0ull;
+  p[1] = lane == 0 ? m.or1 : 0ull;
+  p[2] = lane == 0 ? m.and0 : ~0ull;
+  p[3] = lane == 0 ? m.and1 : ~0ull;
+}
+
 __device__ __forceinline__ void carry_label_masks(Ctl* ctl, uint32_t mg) {
   if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   const LabelMasks m = read_label_masks(ctl, mg_rd(mg));
-  if (threadIdx.x == 0) {
-    set_label_masks(ctl, mg_wr(mg), m.or0, m.or1, m.and0, m.and1);
-    reset_label_masks(ctl, mg_rs(mg));
-  }
+  warp_set_label_masks(ctl, mg_wr(mg), m);
+  warp_set_label_masks(ctl, mg_rs(mg), LabelMasks{0ull, 0ull, ~0ull, ~0ull});
 }
 
 // The table holds n_in labels at the load factor: size for n_in, not 2 n_in.
@@ -267,6 +276,59 @@ __global__ void __launch_bounds__(256) k_gather_build(Ctl* ctl, Bufs bufs, unsig
                                                       const __grid_constant__ GatherArgs a,
                                                       unsigned long long* plog) {
   gather_build<KW>(ctl, bufs, itab, a, plog);
+}
+
+// find_label for a lookup that also wants the entry's amplitude: the probe
+// reads the index four slots (one 32-byte sector) at a time from the slot the
+// hash names, and on a fingerprint match loads the candidate's label and
+// amplitude together (the amplitude is kept if the label matches). The slots
+// are scanned in the order the build claimed them, so the result is
+// find_label's. Returns ~0 if the label is not indexed.
+template <int KW>
+__device__ __forceinline__ uint64_t find_entry(const unsigned long long* itab, uint64_t mask,
+                                               unsigned long long ep, const SoA& s, uint64_t lo,
+                                               uint64_t hi, double* re, double* im) {
+  const uint64_t hv = hash_label<KW>(lo, hi);
+  const unsigned long long fp = (hv >> 48) << 32;
+  uint64_t h = hv & mask;
+  uint64_t seen = 0;
+  if (mask < 3) {   // a table of fewer than 4 slots: one at a time
+    for (uint64_t p = 0; p <= mask; ++p, h = (h + 1) & mask) {
+      const unsigned long long v = __ldcg(itab + h);
+      if ((v & 0xFFFF000000000000ull) != ep) return ~0ull;
+      if ((v & 0x0000FFFF00000000ull) != fp) continue;
+      const uint64_t j = v & 0xFFFFFFFFull;
+      if (s.lo[j] == lo && (KW == 1 || s.hi[j] == hi)) {
+        *re = s.re[j];
+        *im = s.im[j];
+        return j;
+      }
+    }
+    return ~0ull;
+  }
+  while (seen <= mask) {
+    const uint64_t b = h & ~3ull;
+    const ulonglong2 q0 = __ldcg(reinterpret_cast<const ulonglong2*>(itab + b));
+    const ulonglong2 q1 = __ldcg(reinterpret_cast<const ulonglong2*>(itab + b + 2));
+    const unsigned long long v4[4] = {q0.x, q0.y, q1.x, q1.y};
+    for (uint32_t k = (uint32_t)(h & 3ull); k < 4u; ++k) {
+      const unsigned long long v = v4[k];
+      ++seen;
+      if ((v & 0xFFFF000000000000ull) != ep) return ~0ull;   // a free slot ends the probe
+      if ((v & 0x0000FFFF00000000ull) != fp) continue;
+      const uint64_t j = v & 0xFFFFFFFFull;
+      const uint64_t l0 = s.lo[j];
+      const uint64_t l1 = KW == 2 ? s.hi[j] : 0ull;
+      const double r = s.re[j], i = s.im[j];
+      if (l0 == lo && (KW == 1 || l1 == hi)) {
+        *re = r;
+        *im = i;
+        return j;
+      }
+    }
+    h = (b + 4) & mask;
+  }
+  return ~0ull;
 }
 
 template <int KW>
@@ -818,11 +880,12 @@ __global__ void __launch_bounds__(256) k_layer_emit(Ctl* ctl, Bufs bufs,
 // takes the group: one lane looks up the partner of a pair; a group of 4, 8 or
 // 16 members takes 16 lanes, one per member, that look up their members in
 // parallel and run the gates in order as butterflies over shuffles (each lane
-// its own row of each pair action, pruned after every gate as a pass would).
-// The lookups use an index of every label that stays valid while passes keep
-// labels in place. Every entry written once means every group had its writer;
-// anything else (a member absent, a value pruned, a group of more than 16)
-// leaves the run to the usual kernels launched after it (fallback = 1), and a
+// its own row of each pair action, pruned after every gate as a pass would);
+// a group of 32 or 64 takes a warp, two members per lane for 64 (the sixth
+// gate pairs a lane's own two). The lookups use an index of every label that
+// stays valid while passes keep labels in place. Every entry written once
+// means every group had its writer; anything else (a member absent, a value
+// pruned, a group of more than 64) leaves the run to the usual kernels launched after it (fallback = 1), and a
 // failed attempt makes the following runs skip the attempt for a while (1, 2,
 // 4 ... up to 64 runs), so states that keep changing do not pay for it.
 struct AmpArgs {
@@ -840,25 +903,110 @@ struct AmpArgs {
   // count of holding ones decides the sign (pi steps: 4 + 4 = a full turn)
   uint64_t par[2 * kMaxAmpParity];
   uint32_t npar;
+  // 32-bit label words (bit w: label bits 32 w ..) the gates' conditions and
+  // selectors read, and those the sign conditions read
+  uint32_t words_act, words_par;
 };
 
 constexpr int AMP_PLAIN = 0, AMP_WALK = 1, AMP_PARITY = 2;
+constexpr uint32_t kAmpMaxActive = 6;   // most active gates of a group (64 members)
+#ifndef SPS_AMP_MIN_BLOCKS
+#define SPS_AMP_MIN_BLOCKS 2   // resident blocks per SM the register budget allows
+#endif
+constexpr uint32_t kAmpRing = 64;        // per-warp queue of a size class (>= 31 + 32)
 
-// Stores one output of an amplitude-only run (POST: after the phase run that
-// follows it, walked or as a sign parity).
+// A gate of the run as the kernel reads it, staged in shared memory: lanes
+// read different gates, which from the constant bank would be serialised.
+struct AmpGate {
+  uint64_t c[2], m[2];
+  double mre[4], mim[4];   // M[r][x] at 2 r + x
+  uint32_t sbit, qbit, givens, real;
+};
+
+// 32 x 32 bit transpose over a warp: lane r passes row r (bit c = M[r][c])
+// and gets column `lane` back (bit r = M[r][lane]); block swaps of 16, 8, 4,
+// 2 and 1 over shuffles.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, unsigned lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const uint32_t low = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                       : s == 2 ? 0x33333333u : 0x55555555u;   // columns with bit s clear
+    const uint32_t y = __shfl_xor_sync(FULL, x, s);
+    x = (lane & s) ? ((x & ~low) | ((y >> s) & low)) : ((x & low) | ((y & low) << s));
+  }
+  return x;
+}
+
+// Bit-planes of the 32 labels the warp's lanes hold: pl[q] bit i = bit q of
+// lane i's label, for the 32-bit label words flagged in `words` (bit w: label
+// bits 32 w .. 32 w + 31). Every lane calls it.
+template <int KW>
+__device__ __forceinline__ void label_planes(uint32_t* pl, uint64_t k0, uint64_t k1,
+                                             uint32_t words, unsigned lane) {
+  __syncwarp();   // the previous planes are read
+  const uint32_t w[4] = {(uint32_t)k0, (uint32_t)(k0 >> 32), (uint32_t)k1, (uint32_t)(k1 >> 32)};
+#pragma unroll
+  for (int q = 0; q < 2 * KW; ++q)
+    if ((words >> q) & 1u) pl[32 * q + lane] = warp_transpose32(w[q], lane);
+  __syncwarp();
+}
+
+// The 32 labels on which every bit of a mask (c0, c1) is set, from planes.
+__device__ __forceinline__ uint32_t all_set_plane(const uint32_t* pl, uint64_t c0, uint64_t c1) {
+  uint32_t A = ~0u;
+  for (uint64_t m = c0; m; m &= m - 1) A &= pl[__ffsll((long long)m) - 1];
+  for (uint64_t m = c1; m; m &= m - 1) A &= pl[64 + __ffsll((long long)m) - 1];
+  return A;
+}
+
+// The labels that activate gate g: controls set and, for a Givens gate,
+// bits p and q different.
+__device__ __forceinline__ uint32_t gate_plane(const AmpGate& g, const uint32_t* pl) {
+  uint32_t A = all_set_plane(pl, g.c[0], g.c[1]);
+  if (g.givens) A &= pl[g.sbit] ^ pl[g.qbit];
+  return A;
+}
+
+// Bit i: an odd number of the sign conditions (all bits set) hold for label
+// i; lane c evaluates conditions c, c + 32 (every lane calls it).
+__device__ __forceinline__ uint32_t parity_plane(const uint32_t* pl, const uint64_t* par,
+                                                 uint32_t npar, unsigned lane) {
+  uint32_t P = 0u;
+  for (uint32_t c = lane; c < npar; c += 32) P ^= all_set_plane(pl, par[2 * c], par[2 * c + 1]);
+  return __reduce_xor_sync(FULL, P);
+}
+
+// Row r of gate g's action on the pair (a0, a1) (selector bit 0, 1): M[r][0]
+// a0 + M[r][1] a1 with each product and sum rounded once, as pair_action
+// rounds it; REAL: every gate of the run is real (only its own products are
+// issued: the FP64 pipe is scarce).
+template <bool REAL>
+__device__ __forceinline__ void gate_row(const AmpGate& g, int r, double a0r, double a0i,
+                                         double a1r, double a1i, double* nr, double* ni) {
+  const double m0 = g.mre[2 * r], m1 = g.mre[2 * r + 1];
+  if (REAL || g.real) {
+    *nr = __dadd_rn(__dmul_rn(m0, a0r), __dmul_rn(m1, a1r));
+    *ni = __dadd_rn(__dmul_rn(m0, a0i), __dmul_rn(m1, a1i));
+  } else {
+    const double i0 = g.mim[2 * r], i1 = g.mim[2 * r + 1];
+    const double t0r = __dsub_rn(__dmul_rn(m0, a0r), __dmul_rn(i0, a0i));
+    const double t0i = __dadd_rn(__dmul_rn(m0, a0i), __dmul_rn(i0, a0r));
+    const double t1r = __dsub_rn(__dmul_rn(m1, a1r), __dmul_rn(i1, a1i));
+    const double t1i = __dadd_rn(__dmul_rn(m1, a1i), __dmul_rn(i1, a1r));
+    *nr = __dadd_rn(t0r, t1r);
+    *ni = __dadd_rn(t0i, t1i);
+  }
+}
+
+// Stores one output of an amplitude-only run; POST: the phase run after it,
+// walked here, or as a sign parity already decided (odd).
 template <int KW, int POST>
 __device__ __forceinline__ void amp_store(const AmpArgs& a, const uint4* fsm, const SoA& out,
                                           uint64_t j, uint64_t k0, uint64_t k1, double re,
-                                          double im) {
-  if (POST == AMP_PARITY) {
-    uint32_t odd = 0u;
-    for (uint32_t c = 0; c < a.npar; ++c)
-      odd ^= ((k0 & a.par[2 * c]) == a.par[2 * c] && (k1 & a.par[2 * c + 1]) == a.par[2 * c + 1])
-                 ? 1u : 0u;
-    if (odd) {   // times e^{i pi}, as apply_pi4 multiplies it
-      re = -re;
-      im = -im;
-    }
+                                          double im, bool odd) {
+  if (POST == AMP_PARITY && odd) {   // times e^{i pi}, as apply_pi4 multiplies it
+    re = -re;
+    im = -im;
   }
   if (POST == AMP_WALK) {
     uint64_t l0 = k0, l1 = k1;   // a phase-only run leaves the label as it is
@@ -875,18 +1023,6 @@ __device__ __forceinline__ void amp_store(const AmpArgs& a, const uint4* fsm, co
   if (KW == 2) out.hi[j] = k1;
   out.re[j] = re;
   out.im[j] = im;
-}
-
-template <int KW>
-__device__ __forceinline__ uint32_t amp_active(const AmpArgs& a, uint64_t k0, uint64_t k1) {
-  uint32_t act = 0;
-  for (uint32_t j = 0; j < a.d; ++j) {
-    const BranchOp& op = a.ops[j];
-    bool on = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
-    if (op.givens) on = on && (label_bit(k0, k1, op.sbit) != label_bit(k0, k1, op.qbit));
-    act |= on ? (1u << j) : 0u;
-  }
-  return act;
 }
 
 template <int KW>
@@ -944,6 +1080,7 @@ __global__ void __launch_bounds__(256) k_amp_index(Ctl* ctl, Bufs bufs, unsigned
       ctl->amp_state = 0u;
       ctl->amp_fail = 0u;
       ctl->out_count = 0ull;
+      ctl->chunk_next = 0ull;
       if (backoff) ctl->amp_backoff = backoff - 1u;
       ctl->blocks_done = 0u;
       __threadfence();
@@ -951,200 +1088,262 @@ __global__ void __launch_bounds__(256) k_amp_index(Ctl* ctl, Bufs bufs, unsigned
   }
 }
 
-// Output row r of a pair action with both members present, rounded as
-// pair_action rounds it (each product and the sum once).
-__device__ __forceinline__ void row_action(const BranchOp& op, int r, double a0r, double a0i,
-                                           double a1r, double a1i, double* nr, double* ni) {
-  double t0r, t0i, t1r, t1i;
-  mat_times(op, r, 0, a0r, a0i, &t0r, &t0i);
-  mat_times(op, r, 1, a1r, a1i, &t1r, &t1i);
-  *nr = __dadd_rn(t0r, t1r);
-  *ni = __dadd_rn(t0i, t1i);
-}
-
-// Row r of a pair action whose matrix is real (REAL) or general, with the
-// rounding of pair_action; the real form issues only its own FP64 products
-// (a run-time choice between the two forms is compiled as both, predicated,
-// and the FP64 pipe is scarce).
-template <bool REAL>
-__device__ __forceinline__ void row_of(const BranchOp& op, int r, double a0r, double a0i,
-                                       double a1r, double a1i, double* nr, double* ni) {
-  if (REAL) {
-    const double m0 = r == 0 ? op.m_re[0][0] : op.m_re[1][0];
-    const double m1 = r == 0 ? op.m_re[0][1] : op.m_re[1][1];
-    *nr = __dadd_rn(__dmul_rn(m0, a0r), __dmul_rn(m1, a1r));
-    *ni = __dadd_rn(__dmul_rn(m0, a0i), __dmul_rn(m1, a1i));
-  } else {
-    row_action(op, r, a0r, a0i, a1r, a1i, nr, ni);
+// One round of groups of 2^c members taken from a warp's queue of writers
+// (entry index, active gates): 32 >> c groups of the queue's head in aligned
+// lane segments (64 members: one group, two per lane), each lane looking up
+// its member and running the group's gates in order as butterflies over
+// shuffles; a sign-only phase run after them is a parity, bit-sliced over
+// the round's 32 labels. Every lane of the warp calls it.
+template <int KW, bool REAL, int POST>
+__device__ __forceinline__ void amp_round(const AmpArgs& a, const AmpGate* sg, const uint64_t* spar,
+                                          uint32_t* pl, const uint4* fsm, const SoA& s,
+                                          const SoA& out, const unsigned long long* itab,
+                                          uint64_t mask, unsigned long long ep, uint64_t eps_bits,
+                                          uint32_t c, const uint32_t* qidx, const uint32_t* qact,
+                                          uint32_t head, uint32_t ng, unsigned lane, bool& bad,
+                                          unsigned long long& written) {
+  const uint32_t lg = c < 5u ? c : 5u;   // a group takes 2^lg lanes
+  const bool two = c > 5u;               // 64 members: u and u + 32 on one lane
+  const uint32_t gi = lane >> lg;
+  const bool have = gi < ng;
+  uint64_t wi = 0ull, w0 = 0ull, w1 = 0ull;
+  uint32_t wact = 0u;
+  if (have) {
+    const uint32_t slot = (head + gi) % kAmpRing;
+    wi = qidx[slot];
+    wact = qact[slot];
+    w0 = s.lo[wi];
+    w1 = KW == 2 ? s.hi[wi] : 0ull;
+  }
+  uint32_t gidx[kAmpMaxActive];   // the group's gates, in run order
+  {
+    uint32_t rem = wact;
+#pragma unroll
+    for (uint32_t b = 0; b < kAmpMaxActive; ++b) {
+      gidx[b] = rem ? (uint32_t)(__ffs(rem) - 1) : 0u;
+      rem &= rem - 1u;
+    }
+  }
+  const uint32_t u0 = lane & ((1u << lg) - 1u);
+  double vr[2] = {0.0, 0.0}, vi[2] = {0.0, 0.0};
+  uint64_t m0[2] = {0ull, 0ull}, m1[2] = {0ull, 0ull}, jx[2] = {~0ull, ~0ull};
+  bool ok = have;
+#pragma unroll
+  for (uint32_t r = 0; r < 2; ++r) {
+    if (!have || (r == 1 && !two)) continue;
+    const uint32_t u = u0 + 32u * r;
+    uint64_t l0 = w0, l1 = w1;
+#pragma unroll
+    for (uint32_t b = 0; b < kAmpMaxActive; ++b)
+      if (b < c && ((u >> b) & 1u)) {
+        const AmpGate& g = sg[gidx[b]];
+        l0 ^= g.m[0];
+        l1 ^= g.m[1];
+      }
+    m0[r] = l0;
+    m1[r] = l1;
+    if (u == 0u) {
+      jx[r] = wi;
+      vr[r] = s.re[wi];
+      vi[r] = s.im[wi];
+    } else {
+      jx[r] = find_entry<KW>(itab, mask, ep, s, l0, l1, &vr[r], &vi[r]);
+    }
+    if (jx[r] == ~0ull) {
+      ok = false;
+    } else if ((wact & 1u) == 0u && !keep_amp(vr[r], vi[r], a.eps2, eps_bits)) {
+      ok = false;   // gates before the first active one prune the inputs
+    }
+  }
+#pragma unroll
+  for (uint32_t b = 0; b < kAmpMaxActive; ++b) {
+    if (b >= c) break;
+    const AmpGate& g = sg[gidx[b]];
+    if (b < 5u) {
+      const bool x = (lane >> b) & 1u;
+#pragma unroll
+      for (uint32_t r = 0; r < 2; ++r) {
+        if (r == 1 && !two) continue;
+        const double pr = __shfl_xor_sync(FULL, vr[r], 1u << b);
+        const double pi = __shfl_xor_sync(FULL, vi[r], 1u << b);
+        double nr, ni;
+        gate_row<REAL>(g, x ? 1 : 0, x ? pr : vr[r], x ? pi : vi[r], x ? vr[r] : pr,
+                       x ? vi[r] : pi, &nr, &ni);
+        vr[r] = nr;
+        vi[r] = ni;
+        ok = ok && keep_amp(nr, ni, a.eps2, eps_bits);
+      }
+    } else {   // gate 5 pairs the lane's own two members
+      double n0r, n0i, n1r, n1i;
+      gate_row<REAL>(g, 0, vr[0], vi[0], vr[1], vi[1], &n0r, &n0i);
+      gate_row<REAL>(g, 1, vr[0], vi[0], vr[1], vi[1], &n1r, &n1i);
+      vr[0] = n0r;
+      vi[0] = n0i;
+      vr[1] = n1r;
+      vi[1] = n1i;
+      ok = ok && keep_amp(n0r, n0i, a.eps2, eps_bits) && keep_amp(n1r, n1i, a.eps2, eps_bits);
+    }
+  }
+  if (have && !ok) bad = true;
+#pragma unroll
+  for (uint32_t r = 0; r < 2; ++r) {
+    if (r == 1 && !two) continue;
+    uint32_t odd = 0u;
+    if (POST == AMP_PARITY) {   // the members' signs, bit-sliced over the round
+      label_planes<KW>(pl, m0[r], m1[r], a.words_par, lane);
+      odd = (parity_plane(pl, spar, a.npar, lane) >> lane) & 1u;
+    }
+    if (have && ok) {
+      amp_store<KW, POST>(a, fsm, out, jx[r], m0[r], m1[r], vr[r], vi[r], odd != 0u);
+      ++written;
+    }
   }
 }
 
-// The b-th set bit of act (b < popc(act)).
-__device__ __forceinline__ uint32_t nth_bit(uint32_t act, uint32_t b) {
-  for (uint32_t k = 0; k < b; ++k) act &= act - 1u;
-  return __ffs(act) - 1u;
-}
-
-constexpr uint32_t kAmpQueue = 256;   // >= threads per block
-constexpr uint32_t kAmpWide = 4;      // most active gates of a group (16 members)
-
+// One warp per chunk of 32 entries (chunks handed out by a counter), no block
+// barrier inside the loop:
+//   1. the chunk's labels as bit-planes in the warp's shared rows; lane j
+//      evaluates gate j on all 32 (controls, Givens condition), a transpose
+//      gives each entry its active gates, an OR over lanes its writer flag
+//      (no active gate with the selector bit set);
+//   2. entries no gate touches are copied (each gate only prunes them), with
+//      the chunk's sign parity from the same planes;
+//   3. writers join the warp's queue of their size class (2^c members); a
+//      class runs a round (amp_round) whenever its queue holds a full one,
+//      and what is left runs after the last chunk, so rounds are full.
 template <int KW, bool REAL, int POST>
-__global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
+__global__ void __launch_bounds__(256, SPS_AMP_MIN_BLOCKS) k_amp_layer(Ctl* ctl, Bufs bufs,
                                                    const unsigned long long* itab,
                                                    const __grid_constant__ AmpArgs a,
                                                    unsigned long long* plog) {
-  __shared__ uint32_t q1[kAmpQueue], q2[kAmpQueue];   // writers' entry indices
-  __shared__ uint32_t a1[kAmpQueue], a2[kAmpQueue];   // and their active gates
-  __shared__ unsigned n1, n2;
-  extern __shared__ uint4 fsm[];                      // AMP_WALK: the phase run's op stream
+  __shared__ AmpGate sg[kMaxAmpGates];
+  __shared__ uint32_t splanes[8][128];             // per warp (<= 8 warps): label bit-planes
+  __shared__ uint64_t spar[2 * kMaxAmpParity];     // sign conditions (AMP_PARITY)
+  __shared__ uint32_t sqi[8][kAmpMaxActive][kAmpRing];   // per warp and class: writers' indices
+  __shared__ uint32_t sqa[8][kAmpMaxActive][kAmpRing];   // and their active gates
+  extern __shared__ uint4 fsm[];                   // AMP_WALK: the phase run's op stream
   const bool go = ctl->amp_go != 0u;
-  if (POST == AMP_WALK && go) {
-    for (uint32_t w = threadIdx.x; w < a.nwords; w += blockDim.x) fsm[w] = a.words[w];
-    __syncthreads();
+  if (go) {
+    for (uint32_t j = threadIdx.x; j < a.d; j += blockDim.x) {
+      const BranchOp& op = a.ops[j];
+      AmpGate g;
+      g.c[0] = op.c[0];
+      g.c[1] = op.c[1];
+      g.m[0] = op.m[0];
+      g.m[1] = op.m[1];
+      g.mre[0] = op.m_re[0][0];
+      g.mre[1] = op.m_re[0][1];
+      g.mre[2] = op.m_re[1][0];
+      g.mre[3] = op.m_re[1][1];
+      g.mim[0] = op.m_im[0][0];
+      g.mim[1] = op.m_im[0][1];
+      g.mim[2] = op.m_im[1][0];
+      g.mim[3] = op.m_im[1][1];
+      g.sbit = op.sbit;
+      g.qbit = op.qbit;
+      g.givens = op.givens;
+      g.real = op.real_m;
+      sg[j] = g;
+    }
+    if (POST == AMP_PARITY)
+      for (uint32_t c = threadIdx.x; c < 2 * a.npar; c += blockDim.x) spar[c] = a.par[c];
+    if (POST == AMP_WALK)
+      for (uint32_t w = threadIdx.x; w < a.nwords; w += blockDim.x) fsm[w] = a.words[w];
   }
+  __syncthreads();
   const uint64_t n = ctl->nnz;
   const unsigned cur = ctl->cur;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   bool bad = false;
-  unsigned long long written = 0;   // entries this thread wrote
+  unsigned long long written = 0;   // entries this lane wrote
   if (go) {
     const uint64_t mask = itab_mask(ctl->index_n, a.load_pct, a.max_log2);
     const unsigned long long ep = (unsigned long long)ctl->index_epoch << 48;
     const SoA s = pick(bufs, cur);
     const SoA out = pick(bufs, cur ^ 1u);
     const uint64_t eps_bits = eps_pattern(a.eps);
-    // (no thread polls the others' failures: every iteration would load one
-    // shared address from L2, which costs more than finishing the pass)
-    // A block's warps take chunks of 32 entries spread over the state (chunk
-    // w + W t of the block lies G chunks apart from the next, G blocks, W
-    // warps per block): the writers of large groups can sit in clusters of the
-    // state, and a block whose slice held a cluster would finish long after
-    // the others.
+    uint32_t* pl = splanes[warp];
+    const uint32_t scan_words = a.words_act | (POST == AMP_PARITY ? a.words_par : 0u);
+    uint32_t qhead[kAmpMaxActive], qtail[kAmpMaxActive];   // warp-uniform
+#pragma unroll
+    for (uint32_t c = 0; c < kAmpMaxActive; ++c) qhead[c] = qtail[c] = 0u;
     const uint64_t nchunks = (n + 31) / 32;
-    const uint64_t G = gridDim.x;
-    for (uint64_t t = 0; blockIdx.x + G * nwarps * t < nchunks && !bad; ++t) {
-      if (threadIdx.x == 0) n1 = n2 = 0u;
-      __syncthreads();
-      // 1. scan: untouched entries are copied, writers queued
-      const uint64_t i = (blockIdx.x + G * (warp + nwarps * t)) * 32u + lane;
-      if (i < n) {
-        const uint64_t k0 = s.lo[i];
-        const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
-        const uint32_t act = amp_active<KW>(a, k0, k1);
-        if (act == 0u) {   // every gate only prunes this entry
-          const double re = s.re[i], im = s.im[i];
-          bad = !keep_amp(re, im, a.eps2, eps_bits);
-          amp_store<KW, POST>(a, fsm, out, i, k0, k1, re, im);
-          ++written;
-        } else if (__popc(act) > kAmpWide) {
+    // warps take chunks from a shared counter, so the slower ones take fewer
+    // (the kernel ends with its slowest warp)
+    unsigned long long ch = 0ull;
+    if (lane == 0) ch = atomicAdd(&ctl->chunk_next, 1ull);
+    ch = __shfl_sync(FULL, ch, 0);
+    for (; ch < nchunks;) {
+      unsigned long long next = 0ull;   // the next chunk is claimed before this one is worked
+      if (lane == 0) next = atomicAdd(&ctl->chunk_next, 1ull);
+      const uint64_t i = ch * 32 + lane;
+      const bool valid = i < n;
+      const uint64_t k0 = valid ? s.lo[i] : 0ull;
+      const uint64_t k1 = (KW == 2 && valid) ? s.hi[i] : 0ull;
+      // 1. active gates and writers
+      label_planes<KW>(pl, k0, k1, scan_words, lane);
+      uint32_t A = 0u, S = 0u;
+      if (lane < a.d) {
+        const AmpGate& g = sg[lane];
+        A = gate_plane(g, pl);
+        S = A & pl[g.sbit];   // active with the selector bit set: not the writer
+      }
+      uint32_t act = warp_transpose32(A, lane);
+      const uint32_t nonwriter = __reduce_or_sync(FULL, S);
+      if (!valid) act = 0u;
+      const uint32_t na = __popc(act);
+      const bool writer = act != 0u && !((nonwriter >> lane) & 1u);
+      if (na > kAmpMaxActive) bad = true;
+      // 2. entries no gate touches
+      const uint32_t odd_scan = POST == AMP_PARITY ? parity_plane(pl, spar, a.npar, lane) : 0u;
+      if (valid && act == 0u) {
+        const double re = s.re[i], im = s.im[i];
+        if (!keep_amp(re, im, a.eps2, eps_bits)) {
           bad = true;
         } else {
-          bool writer = true;
-          for (uint32_t rem = act; rem; rem &= rem - 1u)
-            writer = writer && !label_bit(k0, k1, a.ops[__ffs(rem) - 1u].sbit);
-          if (writer) {
-            if ((act & (act - 1u)) == 0u) {
-              const unsigned q = atomicAdd(&n1, 1u);
-              q1[q] = (uint32_t)i;
-              a1[q] = act;
-            } else {
-              const unsigned q = atomicAdd(&n2, 1u);
-              q2[q] = (uint32_t)i;
-              a2[q] = act;
-            }
-          }
-        }
-      }
-      __syncthreads();
-      const unsigned c1 = n1, c2 = n2;
-      // 2. pairs: the writer looks up its partner and writes both
-      for (unsigned t1 = threadIdx.x; t1 < c1; t1 += blockDim.x) {
-        const uint64_t j0 = q1[t1];
-        const uint64_t k0 = s.lo[j0];
-        const uint64_t k1 = KW == 2 ? s.hi[j0] : 0ull;
-        const uint32_t act = a1[t1];
-        const BranchOp& op = a.ops[__ffs(act) - 1u];
-        const uint64_t p0 = k0 ^ op.m[0], p1 = k1 ^ op.m[1];
-        const uint64_t j1 = find_label<KW>(itab, mask, ep, s, p0, p1);
-        if (j1 == ~0ull) {
-          bad = true;
-          continue;
-        }
-        const double a0r = s.re[j0], a0i = s.im[j0], a1r = s.re[j1], a1i = s.im[j1];
-        // gates before it are inactive for the pair: they prune its inputs
-        if ((act & 1u) == 0u && (!keep_amp(a0r, a0i, a.eps2, eps_bits) ||
-                                 !keep_amp(a1r, a1i, a.eps2, eps_bits))) {
-          bad = true;
-          continue;
-        }
-        double n0r, n0i, n1r, n1i;
-        row_of<REAL>(op, 0, a0r, a0i, a1r, a1i, &n0r, &n0i);
-        row_of<REAL>(op, 1, a0r, a0i, a1r, a1i, &n1r, &n1i);
-        // (later gates are inactive for the pair: they prune what this kept)
-        if (!keep_amp(n0r, n0i, a.eps2, eps_bits) || !keep_amp(n1r, n1i, a.eps2, eps_bits)) {
-          bad = true;
-          continue;
-        }
-        amp_store<KW, POST>(a, fsm, out, j0, k0, k1, n0r, n0i);
-        amp_store<KW, POST>(a, fsm, out, j1, p0, p1, n1r, n1i);
-        written += 2;
-      }
-      // 3. groups of 4..16: 16 lanes each, lane u = member u (every lane of
-      //    the warp runs every shuffle; lanes past the group's size idle)
-      for (unsigned g0 = 2u * warp; g0 < c2; g0 += 2u * nwarps) {
-        const unsigned g = g0 + (lane >> 4);
-        const uint32_t u = lane & 15u;
-        const bool have = g < c2;
-        uint64_t k0 = 0, k1 = 0;
-        uint32_t act = 0, na = 0;
-        if (have) {
-          const uint64_t jw = q2[g];
-          k0 = s.lo[jw];
-          k1 = KW == 2 ? s.hi[jw] : 0ull;
-          act = a2[g];
-          na = __popc(act);
-        }
-        const bool mine = have && u < (1u << na);
-        uint64_t l0 = k0, l1 = k1, jx = ~0ull;
-        double re = 0.0, im = 0.0;
-        if (mine) {
-          for (uint32_t b = 0; b < na; ++b)
-            if ((u >> b) & 1u) {
-              const BranchOp& op = a.ops[nth_bit(act, b)];
-              l0 ^= op.m[0];
-              l1 ^= op.m[1];
-            }
-          jx = u == 0u ? (uint64_t)q2[g] : find_label<KW>(itab, mask, ep, s, l0, l1);
-          if (jx == ~0ull) {
-            bad = true;
-          } else {
-            re = s.re[jx];
-            im = s.im[jx];
-            if ((act & 1u) == 0u && !keep_amp(re, im, a.eps2, eps_bits)) bad = true;
-          }
-        }
-        for (uint32_t b = 0; b < kAmpWide; ++b) {
-          const double pr = __shfl_xor_sync(FULL, re, 1u << b);
-          const double pi = __shfl_xor_sync(FULL, im, 1u << b);
-          if (mine && b < na && jx != ~0ull) {
-            const BranchOp& op = a.ops[nth_bit(act, b)];
-            const bool x = (u >> b) & 1u;
-            row_of<REAL>(op, x ? 1 : 0, x ? pr : re, x ? pi : im, x ? re : pr, x ? im : pi, &re,
-                         &im);
-            if (!keep_amp(re, im, a.eps2, eps_bits)) bad = true;
-          }
-        }
-        if (mine && jx != ~0ull) {
-          amp_store<KW, POST>(a, fsm, out, jx, l0, l1, re, im);
+          amp_store<KW, POST>(a, fsm, out, i, k0, k1, re, im, (odd_scan >> lane) & 1u);
           ++written;
         }
       }
-      bad = __syncthreads_or(bad);
+      // 3. writers into their class queues; full rounds run
+#pragma unroll
+      for (uint32_t c = 1; c <= kAmpMaxActive; ++c) {
+        const bool mine = writer && na == c;
+        const uint32_t Mc = __ballot_sync(FULL, mine);
+        if (Mc == 0u) continue;
+        if (mine) {
+          const uint32_t slot = (qtail[c - 1] + __popc(Mc & ((1u << lane) - 1u))) % kAmpRing;
+          sqi[warp][c - 1][slot] = (uint32_t)i;
+          sqa[warp][c - 1][slot] = act;
+        }
+        qtail[c - 1] += __popc(Mc);
+        __syncwarp();
+        const uint32_t per = 32u >> (c < 5u ? c : 5u);   // groups per round
+        while (qtail[c - 1] - qhead[c - 1] >= per) {
+          amp_round<KW, REAL, POST>(a, sg, spar, pl, fsm, s, out, itab, mask, ep, eps_bits, c,
+                                    sqi[warp][c - 1], sqa[warp][c - 1], qhead[c - 1], per, lane,
+                                    bad, written);
+          qhead[c - 1] += per;
+        }
+      }
+      if (__any_sync(FULL, bad)) break;   // the attempt fails: the usual passes run
+      ch = __shfl_sync(FULL, next, 0);
+    }
+    // the partial rounds left in the queues
+    if (!__any_sync(FULL, bad)) {
+#pragma unroll
+      for (uint32_t c = 1; c <= kAmpMaxActive; ++c) {
+        const uint32_t left = qtail[c - 1] - qhead[c - 1];
+        if (left)
+          amp_round<KW, REAL, POST>(a, sg, spar, pl, fsm, s, out, itab, mask, ep, eps_bits, c,
+                                    sqi[warp][c - 1], sqa[warp][c - 1], qhead[c - 1], left, lane,
+                                    bad, written);
+      }
     }
     // every entry written exactly once, or some group had no writer
     for (int dd = 16; dd > 0; dd >>= 1) written += __shfl_xor_sync(FULL, written, dd);
     if (lane == 0 && written) atomicAdd(&ctl->out_count, written);
-    if (bad && threadIdx.x == 0) atomicOr(&ctl->amp_fail, 1u);
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(&ctl->amp_fail, 1u);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1170,6 +1369,7 @@ __global__ void __launch_bounds__(256) k_amp_layer(Ctl* ctl, Bufs bufs,
         plog[1] = took ? n : 0ull;
       }
       ctl->out_count = 0ull;
+      ctl->chunk_next = 0ull;
       ctl->blocks_done = 0u;
       __threadfence();
     }
@@ -1292,12 +1492,20 @@ __global__ void __launch_bounds__(256) k_chain(Ctl* ctl, Bufs bufs, unsigned lon
                                                unsigned long long* plog) {
   const uint64_t n0 = ctl->nnz;
   if (amp_took(ctl, 1u)) {
-    if (blockIdx.x == 0 && threadIdx.x < 32 && ctl->status == 0u) {
-      for (uint32_t k = 0; k < a.nsteps; ++k) {
-        const ChainStep& st = a.steps[k];
-        carry_label_masks(ctl, st.kind == PASS_LAYER ? st.l.mg : st.g.mg);
-        __syncwarp();
-      }
+    // every skipped emit copies its input's masks to its output buffer and
+    // empties the next: after the chain the masks of its first input are in
+    // the last step's input and output buffers, and its third buffer is empty
+    if (blockIdx.x == 0 && threadIdx.x < 32 && ctl->status == 0u && a.nsteps > 0) {
+      const ChainStep& s0 = a.steps[0];
+      const ChainStep& sl = a.steps[a.nsteps - 1];
+      const uint32_t mg0 = s0.kind == PASS_LAYER ? s0.l.mg : s0.g.mg;
+      const uint32_t mgl = sl.kind == PASS_LAYER ? sl.l.mg : sl.g.mg;
+      const LabelMasks m = read_label_masks(ctl, mg_rd(mg0));
+      warp_set_label_masks(ctl, mg_rd(mgl), m);
+      warp_set_label_masks(ctl, mg_wr(mgl), m);
+      warp_set_label_masks(ctl, mg_rs(mgl), LabelMasks{0ull, 0ull, ~0ull, ~0ull});
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
       if (plog && threadIdx.x == 0) {
         plog[0] = 0ull;
         plog[1] = n0;
@@ -1449,21 +1657,45 @@ int launch_chain(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   return 1;
 }
 
-template <int KW, int POST>
-static void amp_go(bool real, int blocks, int threads, size_t smem, cudaStream_t st, Ctl* ctl,
-                   Bufs bufs, const unsigned long long* itab, const AmpArgs& a,
-                   unsigned long long* plog) {
-  if (real) {
-    if (POST == AMP_WALK)
-      cudaFuncSetAttribute(k_amp_layer<KW, true, POST>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_amp_layer<KW, true, POST><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
-  } else {
-    if (POST == AMP_WALK)
-      cudaFuncSetAttribute(k_amp_layer<KW, false, POST>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_amp_layer<KW, false, POST><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
+// Resident blocks per SM of one k_amp_layer instance (cached per block size
+// and dynamic shared memory; 0 if the query fails).
+template <typename K>
+static int amp_per_sm(K kern, int threads, size_t smem) {
+  static int c_threads = -1, c_per = 0;
+  static size_t c_smem = 0;
+  if (threads != c_threads || smem != c_smem) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      per = 0;
+    }
+    c_threads = threads;
+    c_smem = smem;
+    c_per = per;
   }
+  return c_per;
+}
+
+// The attempt as one resident wave (each warp then works through many chunks,
+// so its class queues fill whole rounds).
+template <int KW, bool REAL, int POST>
+static void amp_launch(int blocks, int threads, size_t smem, int sms, cudaStream_t st, Ctl* ctl,
+                       Bufs bufs, const unsigned long long* itab, const AmpArgs& a,
+                       unsigned long long* plog) {
+  if (POST == AMP_WALK)
+    cudaFuncSetAttribute(k_amp_layer<KW, REAL, POST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  const int per = amp_per_sm(k_amp_layer<KW, REAL, POST>, threads, smem);
+  if (per > 0 && blocks > per * sms) blocks = per * sms;
+  k_amp_layer<KW, REAL, POST><<<blocks, threads, smem, st>>>(ctl, bufs, itab, a, plog);
+}
+
+template <int KW, int POST>
+static void amp_go(bool real, int blocks, int threads, size_t smem, int sms, cudaStream_t st,
+                   Ctl* ctl, Bufs bufs, const unsigned long long* itab, const AmpArgs& a,
+                   unsigned long long* plog) {
+  if (real) amp_launch<KW, true, POST>(blocks, threads, smem, sms, st, ctl, bufs, itab, a, plog);
+  else amp_launch<KW, false, POST>(blocks, threads, smem, sms, st, ctl, bufs, itab, a, plog);
 }
 
 int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
@@ -1488,6 +1720,22 @@ int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   a.has_phase = l.has_phase;
   a.npar = l.npar;
   for (uint32_t c = 0; c < 2 * l.npar; ++c) a.par[c] = l.par[c];
+  // the label words the kernel reads as bit-planes
+  auto words_of = [](uint64_t lo, uint64_t hi) {
+    return ((lo & 0xFFFFFFFFull) ? 1u : 0u) | ((lo >> 32) ? 2u : 0u) |
+           ((hi & 0xFFFFFFFFull) ? 4u : 0u) | ((hi >> 32) ? 8u : 0u);
+  };
+  auto bit_words = [&](uint32_t q) {
+    return words_of(q < 64 ? 1ull << q : 0ull, q >= 64 ? 1ull << (q - 64) : 0ull);
+  };
+  a.words_act = 0u;
+  for (uint32_t j = 0; j < l.d; ++j) {
+    const BranchOp& op = l.ops[j];
+    a.words_act |= words_of(op.c[0], op.c[1]) | bit_words(op.sbit);
+    if (op.givens) a.words_act |= bit_words(op.qbit);
+  }
+  a.words_par = 0u;
+  for (uint32_t c = 0; c < l.npar; ++c) a.words_par |= words_of(l.par[2 * c], l.par[2 * c + 1]);
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {
@@ -1501,14 +1749,15 @@ int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
     // (a phase run with no ops left only counts its gates: a walk of no words)
     const int post = l.npar ? AMP_PARITY : l.fused_gates ? AMP_WALK : AMP_PLAIN;
     const size_t smem = post == AMP_WALK ? 16 * (size_t)l.nwords : 0;
+    const int sms = lc.max_blocks * lc.threads / 2048;
     if (key_words == 1) {
-      if (post == AMP_PARITY) amp_go<1, AMP_PARITY>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
-      else if (post == AMP_WALK) amp_go<1, AMP_WALK>(real, blocks, lc.threads, smem, st, ctl, bufs, itab, a, plog);
-      else amp_go<1, AMP_PLAIN>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
+      if (post == AMP_PARITY) amp_go<1, AMP_PARITY>(real, blocks, lc.threads, 0, sms, st, ctl, bufs, itab, a, plog);
+      else if (post == AMP_WALK) amp_go<1, AMP_WALK>(real, blocks, lc.threads, smem, sms, st, ctl, bufs, itab, a, plog);
+      else amp_go<1, AMP_PLAIN>(real, blocks, lc.threads, 0, sms, st, ctl, bufs, itab, a, plog);
     } else {
-      if (post == AMP_PARITY) amp_go<2, AMP_PARITY>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
-      else if (post == AMP_WALK) amp_go<2, AMP_WALK>(real, blocks, lc.threads, smem, st, ctl, bufs, itab, a, plog);
-      else amp_go<2, AMP_PLAIN>(real, blocks, lc.threads, 0, st, ctl, bufs, itab, a, plog);
+      if (post == AMP_PARITY) amp_go<2, AMP_PARITY>(real, blocks, lc.threads, 0, sms, st, ctl, bufs, itab, a, plog);
+      else if (post == AMP_WALK) amp_go<2, AMP_WALK>(real, blocks, lc.threads, smem, sms, st, ctl, bufs, itab, a, plog);
+      else amp_go<2, AMP_PLAIN>(real, blocks, lc.threads, 0, sms, st, ctl, bufs, itab, a, plog);
     }
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

@@ -287,6 +287,9 @@ sps_status compile(const sps_gate* gates, size_t ngates, uint32_t nqubits,
                    uint32_t max_fused_ops, std::vector<Pass>* out, size_t* bad,
                    KnownBits* kb = nullptr, bool expand = false, bool fold = false,
                    uint32_t layer_max = 1);
+// The most nonzeros a state can reach from |0...0> through the passes (every
+// branching gate at most doubles the count), capped at the capacity.
+uint64_t projected_peak(const std::vector<Pass>& passes, uint64_t capacity);
 
 // ---- device-side control block -------------------------------------------------
 constexpr int kMaskStripes = 32;
@@ -321,6 +324,9 @@ struct Ctl {
   unsigned int amp_streak;       // failed attempts in a row
   // grid barrier of cooperative launches: generation << 16 | blocks arrived
   unsigned int grid_bar;
+  // next chunk of 32 entries an amplitude-only attempt's warps take (zeroed
+  // by the index launch before it and by the attempt's last block)
+  unsigned long long chunk_next;
 };
 
 // Mask buffer indices of one label-writing launch, packed rd | wr << 8 | rs << 16.

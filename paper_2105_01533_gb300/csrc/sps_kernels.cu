@@ -613,7 +613,81 @@ __device__ __forceinline__ bool table_add(Slot* table, uint64_t mask, uint32_t l
   return false;
 }
 
-template <int KW>
+// The same inserts with the W lanes of a group (W = 2, 4, 8) probing W
+// consecutive slots at once. The group takes its lanes' inserts in turn
+// (`have`: the lane has one); for each, lane k reads slot h + k, a ballot
+// finds the slots in probe order that hold the label or look free, and they
+// are settled in that order: a slot with the label takes the amplitude, a free
+// one is claimed by CAS (a lost race to another label moves on to the next).
+// Slots only go from free to a label during the pass, so the first slot of
+// the probe sequence holding the label or free is the one a single-lane probe
+// would settle. Every lane of the group calls it; returns false (for the whole
+// group) if an insert probed `limit` slots without a place.
+template <int KW, int W>
+__device__ __forceinline__ bool table_add_coop(Slot* table, uint64_t mask, uint32_t limit, bool have,
+                                               uint64_t lo, uint64_t hi, double re, double im) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned sub = lane & (W - 1u);
+  const unsigned base = lane - sub;
+  const unsigned wm = (1u << W) - 1u;
+  const unsigned gm = wm << base;   // the group's lanes
+  unsigned pending = (__ballot_sync(gm, have) >> base) & wm;
+  bool ok = true;
+  while (pending) {
+    const unsigned src = base + __ffs(pending) - 1u;
+    pending &= pending - 1u;
+    const uint64_t L0 = __shfl_sync(gm, lo, src);
+    const uint64_t L1 = KW == 2 ? __shfl_sync(gm, hi, src) : 0ull;
+    const double R = __shfl_sync(gm, re, src), I = __shfl_sync(gm, im, src);
+    const uint64_t h0 = hash_label<KW>(L0, L1) & mask;
+    bool done = false;
+    for (uint32_t p = 0; p < limit && !done; p += W) {
+      Slot* sl = table + ((h0 + p + sub) & mask);
+      bool match, open;
+      if (KW == 1) {
+        const uint64_t cur = __ldcg(&sl->lo);
+        match = cur == L0;
+        open = cur == EMPTY;
+      } else {
+        // a read with an EMPTY word may be torn: the CAS settles it
+        const ulonglong2 cur = __ldcg(reinterpret_cast<const ulonglong2*>(sl));
+        open = cur.x == EMPTY || cur.y == EMPTY;
+        match = !open && cur.x == L0 && cur.y == L1;
+      }
+      unsigned cand = (__ballot_sync(gm, p + sub < limit && (match || open)) >> base) & wm;
+      while (cand) {
+        const unsigned k = __ffs(cand) - 1u;
+        cand &= cand - 1u;
+        int got = 0;
+        if (sub == k) {
+          if (match) {
+            got = 1;
+          } else if (KW == 1) {
+            const unsigned long long old =
+                atomicCAS(reinterpret_cast<unsigned long long*>(&sl->lo), EMPTY, L0);
+            got = old == EMPTY || old == L0;
+          } else {
+            K128a expect{EMPTY, EMPTY}, want{L0, L1};
+            const K128a old = atomicCAS(reinterpret_cast<K128a*>(sl), expect, want);
+            got = (old.lo == EMPTY && old.hi == EMPTY) || (old.lo == L0 && old.hi == L1);
+          }
+          if (got) {
+            atomicAdd(&sl->re, R);
+            atomicAdd(&sl->im, I);
+          }
+        }
+        if (__shfl_sync(gm, got, base + k)) {
+          done = true;
+          break;
+        }
+      }
+    }
+    ok = ok && done;
+  }
+  return ok;
+}
+
+template <int KW, int W>
 __global__ void __launch_bounds__(256) k_branch_emit(Ctl* ctl, Bufs bufs, Slot* table,
                                                      const __grid_constant__ BranchArgs a,
                                                      unsigned long long* plog) {
@@ -626,36 +700,54 @@ __global__ void __launch_bounds__(256) k_branch_emit(Ctl* ctl, Bufs bufs, Slot* 
   const uint64_t mask = (1ull << table_log2_for(n, a.load_pct, a.max_log2)) - 1;
   const SoA s = pick(bufs, ctl->cur);
   const BranchOp& op = a.op;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t k0 = s.lo[i];
-    const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
-    const double re = s.re[i], im = s.im[i];
-    bool active = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
-    const bool x = label_bit(k0, k1, op.sbit);
-    if (op.givens) active = active && (x != label_bit(k0, k1, op.qbit));
-    bool ok = true;
-    if (!active) {
-      ok = table_add<KW>(table, mask, a.probe_limit, k0, k1, re, im);
-    } else {
-      const int xi = x ? 1 : 0;
-      const uint64_t f0 = k0 ^ op.m[0], f1 = k1 ^ op.m[1];
-      // k0 side: the label whose selector bit is 0
-      const uint64_t a0 = x ? f0 : k0, a1 = x ? f1 : k1;
-      const uint64_t b0 = x ? k0 : f0, b1 = x ? k1 : f1;
-      const BranchOp pm = op.pauli ? pauli_pair(op, a0, a1, b0, b1) : op;
-      if (pm.m_re[0][xi] != 0.0 || pm.m_im[0][xi] != 0.0) {
-        double vr, vi;
-        mat_times(pm, 0, xi, re, im, &vr, &vi);
-        ok = table_add<KW>(table, mask, a.probe_limit, a0, a1, vr, vi);
-      }
-      if (ok && (pm.m_re[1][xi] != 0.0 || pm.m_im[1][xi] != 0.0)) {
-        double vr, vi;
-        mat_times(pm, 1, xi, re, im, &vr, &vi);
-        ok = table_add<KW>(table, mask, a.probe_limit, b0, b1, vr, vi);
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n;
+       base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    // the entry's one or two contributions (label, amplitude)
+    bool h0 = false, h1 = false;
+    uint64_t l0 = 0, m0 = 0, l1 = 0, m1 = 0;
+    double r0 = 0.0, i0 = 0.0, r1 = 0.0, i1 = 0.0;
+    if (i < n) {
+      const uint64_t k0 = s.lo[i];
+      const uint64_t k1 = KW == 2 ? s.hi[i] : 0ull;
+      const double re = s.re[i], im = s.im[i];
+      bool active = (k0 & op.c[0]) == op.c[0] && (k1 & op.c[1]) == op.c[1];
+      const bool x = label_bit(k0, k1, op.sbit);
+      if (op.givens) active = active && (x != label_bit(k0, k1, op.qbit));
+      if (!active) {
+        h0 = true;
+        l0 = k0;
+        m0 = k1;
+        r0 = re;
+        i0 = im;
+      } else {
+        const int xi = x ? 1 : 0;
+        const uint64_t f0 = k0 ^ op.m[0], f1 = k1 ^ op.m[1];
+        // k0 side: the label whose selector bit is 0
+        l0 = x ? f0 : k0;
+        m0 = x ? f1 : k1;
+        l1 = x ? k0 : f0;
+        m1 = x ? k1 : f1;
+        const BranchOp pm = op.pauli ? pauli_pair(op, l0, m0, l1, m1) : op;
+        if (pm.m_re[0][xi] != 0.0 || pm.m_im[0][xi] != 0.0) {
+          h0 = true;
+          mat_times(pm, 0, xi, re, im, &r0, &i0);
+        }
+        if (pm.m_re[1][xi] != 0.0 || pm.m_im[1][xi] != 0.0) {
+          h1 = true;
+          mat_times(pm, 1, xi, re, im, &r1, &i1);
+        }
       }
     }
-    if (!ok) {
+    bool ok;
+    if (W == 1) {
+      ok = !h0 || table_add<KW>(table, mask, a.probe_limit, l0, m0, r0, i0);
+      ok = ok && (!h1 || table_add<KW>(table, mask, a.probe_limit, l1, m1, r1, i1));
+    } else {
+      ok = table_add_coop<KW, W>(table, mask, a.probe_limit, h0, l0, m0, r0, i0);
+      ok = table_add_coop<KW, W>(table, mask, a.probe_limit, h1, l1, m1, r1, i1) && ok;
+    }
+    if (!ok) {   // (W > 1: the whole group)
       fail(ctl, SPS_ERR_TABLE_FULL, a.pass_serial, a.fail_tag);
       return;
     }
@@ -1284,10 +1376,19 @@ int launch_branch_emit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, 
   const BranchArgs a = branch_args(b);
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_for(nnz_bound, lc.threads, lc.max_blocks);
-  if (key_words == 1)
-    k_branch_emit<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, table, a, plog);
-  else
-    k_branch_emit<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, table, a, plog);
+  // lanes probing one insert together (SPS_OPT_COOP_WIDTH)
+  auto go = [&](auto kern) { kern<<<blocks, lc.threads, 0, st>>>(ctl, bufs, table, a, plog); };
+  if (key_words == 1) {
+    if (b.coop == 8) go(k_branch_emit<1, 8>);
+    else if (b.coop == 4) go(k_branch_emit<1, 4>);
+    else if (b.coop == 2) go(k_branch_emit<1, 2>);
+    else go(k_branch_emit<1, 1>);
+  } else {
+    if (b.coop == 8) go(k_branch_emit<2, 8>);
+    else if (b.coop == 4) go(k_branch_emit<2, 4>);
+    else if (b.coop == 2) go(k_branch_emit<2, 2>);
+    else go(k_branch_emit<2, 1>);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -9,7 +9,7 @@
 // allocator callback, where allocating again would re-enter the allocator.
 //
 // The array below is part of the library image: every GPU that loads
-// libsps.so holds it (8 MiB of table slots plus the 3,160-byte control block,
+// libsps.so holds it (8 MiB of table slots plus the 3,168-byte control block,
 // 8,391,776 bytes in all) until the process exits.
 #include <cuda_runtime.h>
 
@@ -29,7 +29,7 @@ struct StaticScratch {
   Ctl ctl;
 };
 // the footprint the header states: keep the two in step
-static_assert(sizeof(Ctl) == 3160, "control block size changed: update sps.h");
+static_assert(sizeof(Ctl) == 3168, "control block size changed: update sps.h");
 static_assert(sizeof(StaticScratch) == 8391776, "scratch size changed: update sps.h");
 
 static __device__ __align__(256) StaticScratch g_static_scratch;

@@ -287,7 +287,9 @@ sps_status sps_server_submit(sps_server* s, uint32_t nqubits, uint64_t capacity,
     return st;
   }
   r.gates.assign(gates, gates + ngates);
-  r.small = capacity <= kServeSmallCap;
+  // the state is sized (and the request charged) for its projected peak
+  r.capacity = projected_peak(r.passes, capacity);
+  r.small = r.capacity <= kServeSmallCap;
   r.id = s->next_id++;
   r.submit_tick = s->tick;
   if (request_bytes(r, 0) > s->budget) return SPS_ERR_CAPACITY;   // could never be admitted

@@ -38,13 +38,13 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_nnz", "sps_get_amplitudes", "sps_set_amplitudes", "sps_probability",
            "sps_set_option", "sps_get_counters", "sps_profile_read", "sps_plan", "sps_status_str",
            "sps_branch_apply_static", "sps_batch_create", "sps_batch_destroy", "sps_batch_add",
-           "sps_batch_run", "sps_batch_sync", "sps_batch_circuit_status",
+           "sps_batch_run", "sps_batch_run_graph", "sps_batch_sync", "sps_batch_circuit_status",
            "sps_batch_get_amplitudes", "sps_batch_reset", "sps_batch_set_config",
            "sps_batch_get_config", "sps_batch_tune", "sps_batch_counts", "sps_batch_updates",
            "sps_get_updates", "sps_server_create", "sps_server_destroy", "sps_server_submit",
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
            "sps_server_completed", "sps_probability_async", "sps_measure", "sps_pauli_exp",
-           "sps_jit_selftest", "sps_device_rates",
+           "sps_jit_selftest", "sps_device_rates", "sps_tune", "sps_tune_cache_lookup",
            "sps_commute")
 
 
@@ -69,6 +69,16 @@ class KernelRecord(ctypes.Structure):
                 ("ms", ctypes.c_float), ("nops", ctypes.c_uint32), ("n_in", ctypes.c_uint64),
                 ("n_out", ctypes.c_uint64), ("flags", ctypes.c_uint32),
                 ("label_bytes", ctypes.c_uint32)]
+
+
+class TuneChoice(ctypes.Structure):
+    _fields_ = [("kw", ctypes.c_uint32), ("log2peak", ctypes.c_uint32),
+                ("load_factor_pct", ctypes.c_uint32), ("bitslice_groups", ctypes.c_uint32),
+                ("fused_labels", ctypes.c_uint32), ("max_fused_ops", ctypes.c_uint32),
+                ("from_cache", ctypes.c_uint32), ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class BatchConfig(ctypes.Structure):
@@ -150,6 +160,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_batch_add.restype = st
     lib.sps_batch_run.argtypes = [vp, u32]
     lib.sps_batch_run.restype = st
+    lib.sps_batch_run_graph.argtypes = [vp, u32]
+    lib.sps_batch_run_graph.restype = st
+    lib.sps_tune.argtypes = [vp, vp, sz, dbl, u32, ctypes.c_char_p, ctypes.POINTER(TuneChoice)]
+    lib.sps_tune.restype = st
+    lib.sps_tune_cache_lookup.argtypes = [ctypes.c_char_p, u32, u32, ctypes.POINTER(TuneChoice)]
+    lib.sps_tune_cache_lookup.restype = st
     lib.sps_batch_sync.argtypes = [vp, ctypes.POINTER(u32)]
     lib.sps_batch_sync.restype = st
     lib.sps_batch_circuit_status.argtypes = [vp, u32, ctypes.POINTER(st), psz, pu64,
@@ -419,6 +435,14 @@ def sps_device_rates() -> dict:
     return {"fp64_fma": out[0], "fp32_fma": out[1], "lop3": out[2], "imad": out[3]}
 
 
+def sps_tune_cache_lookup(path: str, kw: int, log2peak: int):
+    """The choice recorded for a size class in a tuning cache file, or None
+    (host only)."""
+    c = TuneChoice()
+    r = load_library().sps_tune_cache_lookup(path.encode(), kw, log2peak, ctypes.byref(c))
+    return c.as_dict() if r == SPS_OK else None
+
+
 def sps_jit_selftest():
     """(ok, message): whether the runtime compiler builds the specialised
     bit-sliced kernel of a sample run (host only, no GPU needed)."""
@@ -470,6 +494,17 @@ class SparseState:
 
     def apply(self, gates, eps: float = 0.0) -> None:
         sps_apply(self._h, gates, eps)
+
+    def tune(self, gates, eps: float = 0.0, repeats: int = 2, cache: Optional[str] = None) -> dict:
+        """Time whole steps of `gates` under candidate settings of the plain
+        path's tunable options and keep the fastest (sps_tune); with `cache`, a
+        size class already recorded there is taken from the file."""
+        g = gate_array(gates)
+        c = TuneChoice()
+        rc = load_library().sps_tune(self._h, _ptr(g), g.size, float(eps), repeats,
+                                     cache.encode() if cache else None, ctypes.byref(c))
+        _check(rc, "sps_tune")
+        return c.as_dict()
 
     def sync(self) -> None:
         sps_sync(self._h)
@@ -582,6 +617,11 @@ class Batch:
 
     def run(self, max_passes: int = 0) -> None:
         _check(load_library().sps_batch_run(self._h, max_passes), "sps_batch_run")
+
+    def run_graph(self, max_passes: int = 0) -> None:
+        """Reset every circuit and advance it, as one replay of a captured
+        CUDA graph (sps_batch_run_graph)."""
+        _check(load_library().sps_batch_run_graph(self._h, max_passes), "sps_batch_run_graph")
 
     def sync(self) -> int:
         u = ctypes.c_uint32(0)

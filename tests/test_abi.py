@@ -133,3 +133,28 @@ def test_runtime_compiler_builds_the_specialised_kernel(lib):
     generated and compiled for sm_103a on the host; no GPU is needed."""
     ok, msg = sps.sps_jit_selftest()
     assert ok, msg
+
+
+def test_tune_cache_file_lookup(tmp_path):
+    """The tuning cache is a text file, one line per size class; the last valid
+    line of a class wins, lines of other classes and malformed or out-of-range
+    lines are ignored (host only)."""
+    p = tmp_path / "tune.txt"
+    p.write_text(
+        "sps-tune 1 kw=2 log2peak=24 load_factor_pct=50 bitslice_groups=8 fused_labels=0 "
+        "max_fused_ops=512 ms=0.2500\n"
+        "sps-tune 1 kw=1 log2peak=24 load_factor_pct=70 bitslice_groups=16 fused_labels=4 "
+        "max_fused_ops=256 ms=1.0\n"
+        "garbage line\n"
+        "sps-tune 1 kw=2 log2peak=24 load_factor_pct=95 bitslice_groups=8 fused_labels=0 "
+        "max_fused_ops=512 ms=0.1\n"          # load factor out of range: ignored
+        "sps-tune 1 kw=2 log2peak=24 load_factor_pct=30 bitslice_groups=32 fused_labels=2 "
+        "max_fused_ops=128 ms=0.2000\n")
+    c = sps.sps_tune_cache_lookup(str(p), 2, 24)
+    assert c["load_factor_pct"] == 30 and c["bitslice_groups"] == 32
+    assert c["fused_labels"] == 2 and c["max_fused_ops"] == 128 and c["from_cache"] == 1
+    assert abs(c["ms"] - 0.2) < 1e-6
+    c1 = sps.sps_tune_cache_lookup(str(p), 1, 24)
+    assert c1["load_factor_pct"] == 70 and c1["max_fused_ops"] == 256
+    assert sps.sps_tune_cache_lookup(str(p), 2, 23) is None
+    assert sps.sps_tune_cache_lookup(str(tmp_path / "missing.txt"), 2, 24) is None

@@ -76,10 +76,13 @@ def givens_parts(n, modes, layers, seed, per_part=4):
 
 
 @pytest.mark.parametrize("n,modes,layers,lay", [(16, 3, 30, 4), (40, 2, 24, 4), (64, 3, 12, 1),
-                                                (100, 2, 10, 4)])
+                                                (100, 2, 10, 4), (24, 5, 12, 4), (20, 6, 12, 4),
+                                                (18, 6, 12, 1)])
 def test_givens_layers_take_the_amplitude_form(n, modes, layers, lay):
     """Particle-number-conserving circuits: once every label of the sector is
-    present, Givens layers and single Givens gates keep the label set."""
+    present, Givens layers and single Givens gates keep the label set. With 5
+    or 6 occupied modes a label activates up to 5 or 6 Givens of a layer:
+    groups of 32 and 64 members."""
     parts = givens_parts(n, modes, layers, seed=n + modes)
     opts = [(sps.SPS_OPT_LAYER_GATES, lay)]
     got, upd, took = run(n, parts, 1e-14, 1 << 18, 1, opts)

@@ -133,3 +133,46 @@ def test_batch_tune_keeps_results():
     for i, c in enumerate(circs):
         compare_states(b.get_amplitudes(i), oracle_result(c), EPS)
     b.close()
+
+
+def identical(a, b):
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_graph_step_equals_reset_and_run():
+    """One step captured as a CUDA graph (reset, then the persistent launch),
+    replayed several times, with a bounded pass count and after a change of
+    launch configuration: each replay gives what sps_batch_reset +
+    sps_batch_run give, bit for bit, and one launch per step is counted."""
+    circs = small_batch(20, seed0=2600)
+    ref = sps.Batch()
+    for c in circs:
+        ref.add(c.nqubits, c.cap, c.gates, EPS)
+    ref.run()
+    ref.sync()
+    want = [ref.get_amplitudes(i) for i in range(len(circs))]
+    ref.close()
+    b = sps.Batch()
+    for c in circs:
+        b.add(c.nqubits, c.cap, c.gates, EPS)
+    for cfg in (None, (256, 2, 0)):
+        if cfg:
+            b.set_config(*cfg)
+        for _ in range(3):
+            l0 = b.launches()
+            b.run_graph()
+            assert b.sync() == 0
+            assert b.launches() == l0 + 1
+            for i in range(len(circs)):
+                identical(b.get_amplitudes(i), want[i])
+    # a bounded step: every circuit reset and advanced by two passes, as reset + run(2)
+    b.run_graph(max_passes=2)
+    b.sync()
+    two = [b.get_amplitudes(i) for i in range(len(circs))]
+    b.reset()
+    b.run(max_passes=2)
+    b.sync()
+    for i in range(len(circs)):
+        identical(b.get_amplitudes(i), two[i])
+    b.close()

@@ -580,3 +580,54 @@ def test_commuting_queues_on_the_device():
         st.sync()
     assert e.value.status == sps.SPS_ERR_CAPACITY and e.value.failed_gate == 4
     st.close()
+
+
+@pytest.mark.parametrize("coop", [2, 4, 8])
+@pytest.mark.parametrize("n,load", [(30, 50), (70, 90)])
+def test_scatter_cooperative_probing(coop, n, load):
+    """Scatter form with W lanes probing one insert together: bit-identical
+    to single-lane probing (each slot receives at most two contributions, and
+    0 + x and x + y are exact in either order) at a normal and a high table
+    load (long probe runs), and equal to the oracle."""
+    rng = W.SplitMix64(40 + n)
+    recs = [W.H(q) for q in range(9)]
+    branching = 0
+    for _ in range(40):
+        kind = rng.below(4) if branching < 5 else 3   # at most 2^14 nonzeros
+        branching += kind < 3
+        q = rng.distinct(n, 3)
+        if kind == 0:
+            recs.append(W.H(q[0]))
+        elif kind == 1:
+            recs.append(W.Ry(q[0], rng.angle(), q[1]))
+        elif kind == 2:
+            recs.append(W.Givens(q[0], q[1], rng.angle()))
+        else:
+            recs.append(W.CX(q[0], q[1]))
+    gates = W.to_array(recs)
+    base = [(sps.SPS_OPT_BRANCH_FORM, 1), (sps.SPS_OPT_SMALL_RUN_CAP, 0),
+            (sps.SPS_OPT_EXPAND, 0), (sps.SPS_OPT_LOAD_FACTOR_PCT, load)]
+    one, want = run_both(n, gates, eps=1e-14, capacity=1 << 15, options=base)
+    got, _ = run_both(n, gates, eps=1e-14, capacity=1 << 15,
+                      options=base + [(sps.SPS_OPT_COOP_WIDTH, coop)])
+    for a, b in zip(got, one):
+        np.testing.assert_array_equal(a, b)
+    compare_states(got, want, 1e-14)
+
+
+def test_scatter_cooperative_probe_limit():
+    """With a probe limit of one slot and 8 lanes per insert, only the first
+    slot is probed: 4,096 labels hashed into 8,192 slots collide, so the pass
+    fails with SPS_ERR_TABLE_FULL as the single-lane form does."""
+    gates = W.to_array([W.H(q) for q in range(12)])
+    for coop in (1, 8):
+        st = sps.SparseState(20, 1 << 13)
+        for o, v in [(sps.SPS_OPT_BRANCH_FORM, 1), (sps.SPS_OPT_SMALL_RUN_CAP, 0),
+                     (sps.SPS_OPT_EXPAND, 0), (sps.SPS_OPT_LOAD_FACTOR_PCT, 90),
+                     (sps.SPS_OPT_PROBE_LIMIT, 1), (sps.SPS_OPT_COOP_WIDTH, coop)]:
+            st.set_option(o, v)
+        st.apply(gates, 0.0)
+        with pytest.raises(sps.SpsError) as e:
+            st.sync()
+        assert e.value.status == sps.SPS_ERR_TABLE_FULL
+        st.close()

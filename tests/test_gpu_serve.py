@@ -130,8 +130,10 @@ def test_failing_request_is_isolated():
     for i, (nq, cap, g) in zip(ids, reqs):
         assert srv.poll(i)["status"] == 0
         compare_states(srv.result(i), alone(nq, cap, g), EPS)
+    wide = W.to_array([W.H(q) for q in range(30)])   # projected peak 2^30: capped at 10^9
     with pytest.raises(sps.SpsError):
-        srv.submit(30, 10 ** 9, bad, EPS)   # can never fit the budget
+        srv.submit(30, 10 ** 9, wide, EPS)   # can never fit the budget
+    srv.submit(30, 10 ** 9, bad, EPS)        # charged for its peak, 2^9: fits
     srv.close()
 
 
@@ -145,3 +147,41 @@ def test_state_update_counter():
     st.apply(W.to_array([W.H(0), W.H(1), W.H(2), W.X(3), W.Z(4)]), 0.0)
     assert st.updates() == 23
     st.close()
+
+
+def test_admission_charges_the_projected_peak():
+    """A request declared with capacity 2^26 whose circuit can reach only 2^8
+    (or 2^20) nonzeros is charged and sized for that peak: it fits a 256 MiB
+    budget that the declared capacity (6 GB at 96 B per entry) would not, the
+    small one takes the batched route, and both equal sps_apply alone. A
+    2^22-nonzero adder runs beside small requests in the same ticks."""
+    small = W.to_array([W.H(q) for q in range(8)] + [W.CX(0, 9), W.T(3), W.Ry(9, 0.4)])
+    ad20 = W.adder_workload(seed=20, nbits=32, width=20, n_cp=4)
+    srv = sps.Server(mem_budget_bytes=256 << 20, max_active=16, passes_per_tick=0)
+    a = srv.submit(40, 1 << 26, small, EPS)
+    b = srv.submit(ad20.layout.nqubits, 1 << 26, ad20.gates, EPS)
+    while any(srv.poll(i)["state"] != 2 for i in (a, b)):
+        srv.tick()
+        assert srv.stats()["bytes_in_use"] <= 256 << 20
+    ia, ib = srv.poll(a), srv.poll(b)
+    assert ia["status"] == 0 and ib["status"] == 0
+    assert ia["large"] == 0 and ib["large"] == 1
+    compare_states(srv.result(a), alone(40, 1 << 26, small), EPS)
+    compare_states(srv.result(b), alone(ad20.layout.nqubits, 1 << 20, ad20.gates), EPS)
+    srv.close()
+    # a large request among small ones, served in the same ticks
+    reqs = request_mix()[:8]
+    ad22 = W.adder_workload(seed=22, nbits=32, width=22, n_cp=4)
+    srv = sps.Server(mem_budget_bytes=8 << 30, max_active=64, passes_per_tick=4)
+    big = srv.submit(ad22.layout.nqubits, 1 << 22, ad22.gates, EPS)
+    ids = [srv.submit(nq, cap, g, EPS) for nq, cap, g in reqs]
+    overlap = False
+    while any(srv.poll(i)["state"] != 2 for i in ids + [big]):
+        srv.tick()
+        if srv.poll(big)["state"] == 1 and any(srv.poll(i)["state"] == 1 for i in ids):
+            overlap = True   # small requests advanced in the ticks the large one did
+    assert overlap and srv.poll(big)["large"] == 1
+    compare_states(srv.result(big), alone(ad22.layout.nqubits, 1 << 22, ad22.gates), EPS)
+    for i, (nq, cap, g) in zip(ids, reqs):
+        compare_states(srv.result(i), alone(nq, cap, g), EPS)
+    srv.close()
