@@ -485,6 +485,10 @@ def run_ours(args, dist, rank, world, local_rank):
                 subs[name] = run_sub(args, sps, torch, name)
         if res is not None:
             res["sublines"] = subs
+    if args.branch_forms and rank == 0:
+        bf = branch_forms(args, sps, torch)
+        if res is not None:
+            res["branch_forms"] = bf
     if args.batched:
         bres = run_batched(args, sps, torch, args.batch_count, steps=args.batch_steps,
                            warmup=1, dist=dist, rank=rank, world=world)
@@ -505,6 +509,57 @@ def device_rates(sps) -> dict:
     except Exception as e:   # a measurement aid: never fail the bench line for it
         return {"error": str(e)}
     return {k: round(v / 1e9, 1) for k, v in r.items()} | {"unit": "G lane-ops/s"}
+
+
+def branch_forms(args, sps, torch):
+    """One branching-heavy workload under the gather form (the paper's
+    insert-once rule: index, look up, write each pair once) and the scatter form
+    (atomic accumulation into a 128-bit open-addressing table) with 1 and 4
+    lanes probing each insert: 40 qubits, H on 20 of them (1,048,576 nonzeros),
+    then 24 Ry / controlled-Ry / Givens gates on the same qubits (labels meet
+    partners; nothing grows), one pass per gate (no layers, no amplitude-only
+    runs). Per-pass time by CUDA events over whole applies."""
+    from paper_2105_01533_gb300 import workloads as W
+    rng = W.SplitMix64(31)
+    recs = [W.H(q) for q in range(20)]
+    for _ in range(24):
+        q = rng.distinct(20, 3)
+        k = rng.below(3)
+        if k == 0:
+            recs.append(W.Ry(q[0], rng.angle()))
+        elif k == 1:
+            recs.append(W.Ry(q[0], rng.angle(), q[1]))
+        else:
+            recs.append(W.Givens(q[0], q[1], rng.angle()))
+    gates = W.to_array(recs)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, opts in (("gather", [(sps.SPS_OPT_BRANCH_FORM, 2)]),
+                       ("scatter_w1", [(sps.SPS_OPT_BRANCH_FORM, 1), (sps.SPS_OPT_COOP_WIDTH, 1)]),
+                       ("scatter_w4", [(sps.SPS_OPT_BRANCH_FORM, 1), (sps.SPS_OPT_COOP_WIDTH, 4)])):
+        st = sps.SparseState(40, 1 << 21)
+        for o, v in opts + [(sps.SPS_OPT_LAYER_GATES, 1), (sps.SPS_OPT_AMP_ONLY, 0)]:
+            st.set_option(o, v)
+        prep = gates[:20]
+        body = gates[20:]
+        times = []
+        for rep_i in range(4):
+            st.reset()
+            st.apply(prep, EPS)
+            st.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st.apply(body, EPS)
+            e1.record(stream)
+            st.sync()
+            if rep_i:
+                times.append(e0.elapsed_time(e1))
+        n = st.nnz()
+        st.close()
+        out[name] = {"ms_per_pass": round(float(np.median(times)) / len(body), 4), "nnz": int(n)}
+    out["workload"] = ("40 qubits, H on 20 (1,048,576 nonzeros), 24 Ry / CRy / Givens on those "
+                       "qubits, one pass per gate; FP64, eps 1e-14")
+    return out
 
 
 def run_sub(args, sps, torch, name: str):
@@ -805,13 +860,16 @@ def run_served(args, sps, torch, count: int, arrive_s: float):
                     "p50_latency_ms": round(1e3 * float(np.percentile(lat2, 50)), 3),
                     "p99_latency_ms": round(1e3 * float(np.percentile(lat2, 99)), 3),
                     "ticks": st2["ticks"], "batched_launches": st2["launches"]}
-    # the plain path, one request at a time, on the saturation set
+    # the plain path, one request at a time, on the saturation set: each
+    # request's state created, the circuit applied, the result copied to the
+    # host (what the server hands back)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pu = 0
     for (nm, nq, cap, g) in reqs[:sat_n]:
         s1 = sps.SparseState(nq, cap)
         s1.apply(g, EPS)
+        s1.get_amplitudes(sort=False)
         pu += s1.updates()
         s1.close()
     plain_s = time.perf_counter() - t0
@@ -830,7 +888,8 @@ def run_served(args, sps, torch, count: int, arrive_s: float):
             "loads": {"%.1fx" % f: v for f, v in loads.items()},
             "plain_value": round(pu / plain_s, 1),
             "served_vs_plain": round(sat_rate / (pu / plain_s), 2),
-            "served_vs_plain_set": "the same %d requests, one sps_apply each" % sat_n,
+            "served_vs_plain_set": "the same %d requests, one state, sps_apply and result "
+                                   "read-back each" % sat_n,
             "memory_budget_gb": round(budget / 2 ** 30, 1)}
 
 
@@ -945,6 +1004,8 @@ def main():
     ap.add_argument("--served", type=int, default=1,
                     help="also measure the served form (1) or not (0)")
     ap.add_argument("--serve-count", type=int, default=2000)
+    ap.add_argument("--branch-forms", type=int, default=1,
+                    help="1: time one branching workload under the gather and scatter forms")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--batch-cpu-every", type=int, default=8,

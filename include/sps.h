@@ -88,7 +88,9 @@ typedef struct sps_gate {
 typedef struct sps_state sps_state; /* opaque, owned by the library */
 
 /* Device memory hook. alloc(ctx, bytes, stream) returns a device pointer
- * aligned to >= 256 bytes or NULL; release(ctx, ptr, bytes, stream) frees it.
+ * aligned to >= 256 bytes or NULL (a pointer that is not so aligned is
+ * released at once and counts as a failed allocation: SPS_ERR_OOM);
+ * release(ctx, ptr, bytes, stream) frees it.
  * Both are called on the thread that calls into the library, with the
  * state's stream. Passing NULL for both restores the built-in allocator
  * (cudaMallocAsync on the state's stream). Affects states created afterwards. */
@@ -373,6 +375,16 @@ sps_status sps_tune(sps_state* s, const sps_gate* gates, size_t ngates, double p
 sps_status sps_tune_cache_lookup(const char* path, uint32_t kw, uint32_t log2peak,
                                  sps_tune_choice* out);
 
+/* Exercises the grid barrier that the cooperative fallback launch uses
+ * between passes: 8 blocks meet at three barriers whose waits give up after
+ * `spins` polls (about 256 ns each); block skip_block (>= 8: none) does not
+ * arrive at the first, so the other blocks' waits run out. *result receives
+ * the status the launch recorded: SPS_OK when every block arrived,
+ * SPS_ERR_TIMEOUT when a wait ran out (the launch still ends; later barriers
+ * pass at once). Uses its own scratch control block and stream. Errors:
+ * SPS_ERR_ARG (spins 0, result NULL), SPS_ERR_NO_DEVICE, SPS_ERR_CUDA. */
+sps_status sps_barrier_selftest(uint32_t skip_block, uint32_t spins, sps_status* result);
+
 /* Per-state counters since creation (host-side bookkeeping, no sync). */
 typedef struct sps_counters {
   uint64_t gates;            /* gates accepted by sps_apply */
@@ -532,7 +544,9 @@ sps_status sps_batch_updates(sps_batch* b, uint64_t* total);
  * batched launch on the server's stream, large ones each as a whole-GPU state
  * on its own stream, so their work overlaps on the device - waits for them,
  * and copies finished requests to host memory, releasing their device memory.
- * Results equal sps_apply's for the same circuit. */
+ * Large requests' states run without SPS_OPT_BITSLICE_JIT (their passes
+ * arrive a tick at a time; a run-time compile per slice would cost more than
+ * most requests). Results equal sps_apply's for the same circuit. */
 typedef struct sps_server sps_server;
 
 typedef struct sps_server_request_info {

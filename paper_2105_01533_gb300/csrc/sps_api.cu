@@ -214,13 +214,22 @@ void release_all(sps_state* s) {
 
 void* sps::hook_alloc(size_t bytes, void* stream) {
   sps_alloc_fn a;
+  sps_free_fn f;
   void* ctx;
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     a = g_alloc ? g_alloc : default_alloc;
+    f = g_alloc ? g_free : default_free;
     ctx = g_alloc ? g_alloc_ctx : nullptr;
   }
-  return a(ctx, (bytes + 255) & ~size_t(255), stream);
+  const size_t rounded = (bytes + 255) & ~size_t(255);
+  void* p = a(ctx, rounded, stream);
+  // the kernels' vector loads rely on the alignment the hook promises
+  if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0u) {
+    f(ctx, p, rounded, stream);
+    return nullptr;
+  }
+  return p;
 }
 
 void sps::hook_free(void* p, size_t bytes, void* stream) {
@@ -1919,6 +1928,19 @@ sps_status sps_tune(sps_state* s, const sps_gate* gates, size_t ngates, double p
   }
   best.from_cache = 0;
   *out = best;
+  return SPS_OK;
+}
+
+sps_status sps_barrier_selftest(uint32_t skip_block, uint32_t spins, sps_status* result) {
+  if (!result || spins < 1) return SPS_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SPS_ERR_NO_DEVICE;
+  }
+  int st = 0;
+  if (barrier_selftest(skip_block, spins, &st) < 0) return SPS_ERR_CUDA;
+  *result = (sps_status)st;
   return SPS_OK;
 }
 

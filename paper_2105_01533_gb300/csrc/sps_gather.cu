@@ -307,10 +307,11 @@ __device__ __forceinline__ uint64_t find_entry(const unsigned long long* itab, u
     return ~0ull;
   }
   while (seen <= mask) {
-    const uint64_t b = h & ~3ull;
-    const ulonglong2 q0 = __ldcg(reinterpret_cast<const ulonglong2*>(itab + b));
-    const ulonglong2 q1 = __ldcg(reinterpret_cast<const ulonglong2*>(itab + b + 2));
-    const unsigned long long v4[4] = {q0.x, q0.y, q1.x, q1.y};
+    const uint64_t b = h & ~3ull;   // the table is 256-byte aligned: a 32-byte sector
+    unsigned long long v4[4];
+    asm("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(v4[0]), "=l"(v4[1]), "=l"(v4[2]), "=l"(v4[3])
+        : "l"(itab + b));
     for (uint32_t k = (uint32_t)(h & 3ull); k < 4u; ++k) {
       const unsigned long long v = v4[k];
       ++seen;
@@ -1253,7 +1254,7 @@ __global__ void __launch_bounds__(256, SPS_AMP_MIN_BLOCKS) k_amp_layer(Ctl* ctl,
   __syncthreads();
   const uint64_t n = ctl->nnz;
   const unsigned cur = ctl->cur;
-  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   bool bad = false;
   unsigned long long written = 0;   // entries this lane wrote
   if (go) {
@@ -1423,7 +1424,8 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ void grid_barrier(Ctl* ctl, uint32_t pass_serial, uint64_t fail_tag) {
+__device__ __forceinline__ void grid_barrier(Ctl* ctl, uint32_t pass_serial, uint64_t fail_tag,
+                                             uint32_t spins = kBarrierSpins) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();   // the block's writes before its arrival
@@ -1435,7 +1437,7 @@ __device__ __forceinline__ void grid_barrier(Ctl* ctl, uint32_t pass_serial, uin
       for (uint32_t spin = 0;; ++spin) {
         const unsigned v = ld_acquire(&ctl->grid_bar);
         if ((v >> 16) != gen || (v & 0x8000u)) break;
-        if (spin >= kBarrierSpins) {
+        if (spin >= spins) {
           atomicOr(&ctl->grid_bar, 0x8000u);
           fail(ctl, SPS_ERR_TIMEOUT, pass_serial, fail_tag);
           break;
@@ -1536,6 +1538,16 @@ __global__ void __launch_bounds__(256) k_chain(Ctl* ctl, Bufs bufs, unsigned lon
     grid_barrier(ctl, serial + 1u, tag);
   }
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) plog[1] = ctl->nnz;
+}
+
+// The barrier's bounded wait, exercised: `rounds` barriers over the grid; block
+// `skip` (if in the grid) does not arrive at the first one, so the others
+// give up after `spins` polls and the status reads SPS_ERR_TIMEOUT.
+__global__ void k_barrier_test(Ctl* ctl, uint32_t skip, uint32_t spins, uint32_t rounds) {
+  for (uint32_t r = 0; r < rounds; ++r) {
+    if (r == 0 && blockIdx.x == skip) continue;
+    grid_barrier(ctl, r, 0ull, spins);
+  }
 }
 
 int grid_of(uint64_t work, int threads, int max_blocks) {
@@ -1739,10 +1751,13 @@ int launch_amp_part(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   cudaStream_t st = (cudaStream_t)lc.stream;
   const int blocks = grid_of(nnz_bound, lc.threads, lc.max_blocks);
   if (part == 0) {
+    // mostly the index is still valid and the launch only decides: a quarter
+    // of the resident blocks (a rebuild loops over the labels)
+    const int ib = grid_of(nnz_bound, lc.threads, lc.max_blocks / 4 > 0 ? lc.max_blocks / 4 : 1);
     if (key_words == 1)
-      k_amp_index<1><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+      k_amp_index<1><<<ib, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
     else
-      k_amp_index<2><<<blocks, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
+      k_amp_index<2><<<ib, lc.threads, 0, st>>>(ctl, bufs, itab, a, plog);
   } else {
     bool real = true;
     for (uint32_t j = 0; j < l.d; ++j) real = real && l.ops[j].real_m && !l.ops[j].pauli;
@@ -1857,6 +1872,34 @@ int launch_expand(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const
   else
     expand_kw<2>(e_log2, walk, blocks, lc.threads, smem, st, ctl, bufs, a, plog);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int barrier_selftest(uint32_t skip_block, uint32_t spins, int* status) {
+  Ctl* ctl = nullptr;
+  if (cudaMalloc(&ctl, sizeof(Ctl)) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int rc = -1;
+  cudaStream_t st = nullptr;
+  if (cudaMemset(ctl, 0, sizeof(Ctl)) == cudaSuccess &&
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) {
+    uint32_t rounds = 3;
+    void* args[] = {&ctl, &skip_block, &spins, &rounds};
+    if (cudaLaunchCooperativeKernel((const void*)k_barrier_test, dim3(8), dim3(64), args, 0, st) ==
+            cudaSuccess &&
+        cudaStreamSynchronize(st) == cudaSuccess) {
+      Ctl h;
+      if (cudaMemcpy(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        *status = (int)h.status;
+        rc = 0;
+      }
+    }
+  }
+  if (st) cudaStreamDestroy(st);
+  cudaFree(ctl);
+  cudaGetLastError();
+  return rc;
 }
 
 }  // namespace sps

@@ -117,6 +117,13 @@ constexpr uint64_t kBsJitMinNnz = 1ull << 20;   // SPS_OPT_BITSLICE_JIT = 1: fro
 constexpr uint32_t kBsDirectBits = 22;
 
 struct BsPass {
+  // the kernel compiled for this pass (sps_jit.cu), kept with the plan so a
+  // reused plan launches it without generating its source again: the launch
+  // form it was built for (jit_form, 0 = none), the kernel, its resident
+  // blocks per SM at its shared memory
+  mutable uint32_t jit_form = 0;
+  mutable const void* jit_fn = nullptr;
+  mutable int jit_bps = 0;
   uint32_t nw = 0;            // 32-bit words of a label (nqubits / 32 rounded up)
   uint32_t nrows = 0;         // rows per tile column: label + aux + scratch + ones
   uint32_t label_rows = 0;
@@ -505,6 +512,10 @@ struct ChainWalk {
 int launch_chain(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                  unsigned long long* itab, const ChainStepDesc* steps, uint32_t nsteps,
                  const ChainWalk& w, uint64_t nnz_bound, unsigned long long* plog);
+// Runs the grid barrier of k_chain on a scratch control block (8 blocks, three
+// barriers; block skip_block misses the first); *status receives the block's
+// status word. Returns 0, or -1 on a CUDA error.
+int barrier_selftest(uint32_t skip_block, uint32_t spins, int* status);
 // Expansion pass (PASS_EXPAND); f, m: its tables in device memory.
 struct ExpandLaunch {
   const double* f;

@@ -695,20 +695,37 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   // extra resident blocks made the walk spill (SPS_OPT_BITSLICE_GROUPS 2..16
   // still asks for 16)
   const uint32_t G = (b.groups == 0 || b.groups >= 32) ? 32u : 16u;
-  const std::string src = make_source(P, key_words, b.has_perm != 0, b.has_phase != 0, G);
-  const JitEntry* e = jit_kernel(src);
-  if (!e) return 0;
-  const void* fn = reinterpret_cast<const void*>(e->kernel);
   const size_t smem = (size_t)kJitWarps * P.nrows * (G + 1) * 4;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kJitWarps * 32, smem) != cudaSuccess ||
-      bps < 1) {
-    cudaGetLastError();
-    return 0;
+  // the form: device, label words, permutes, phases, tile groups
+  const uint32_t form = 1u | ((uint32_t)dev << 8) | ((uint32_t)key_words << 16) |
+                        (b.has_perm ? 1u << 20 : 0u) | (b.has_phase ? 1u << 21 : 0u) | (G << 24);
+  const void* fn = P.jit_form == form ? P.jit_fn : nullptr;
+  int bps = P.jit_bps;
+  if (!fn) {
+    const std::string src = make_source(P, key_words, b.has_perm != 0, b.has_phase != 0, G);
+    const JitEntry* e = jit_kernel(src);
+    if (!e) return 0;
+    fn = reinterpret_cast<const void*>(e->kernel);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kJitWarps * 32, smem) !=
+            cudaSuccess ||
+        bps < 1) {
+      cudaGetLastError();
+      return 0;
+    }
+    P.jit_form = form;
+    P.jit_fn = fn;
+    P.jit_bps = bps;
   }
   const int launched = b.build_tables ? launch_bs_tables(lc, b) : 0;
   if (launched < 0) return -1;

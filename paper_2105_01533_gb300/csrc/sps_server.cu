@@ -165,6 +165,13 @@ sps_status admit(sps_server* s, Request& r) {
       release_request(s, r);
       return st;
     }
+    // a request's passes reach the state a tick at a time, so its long runs
+    // are compiled per slice: the general bit-sliced kernel, not one compiled
+    // at run time for each run (a compile costs more than most requests)
+    if ((st = sps_set_option(r.st, SPS_OPT_BITSLICE_JIT, 0)) != SPS_OK) {
+      release_request(s, r);
+      return st;
+    }
     r.next_pass = 0;
   }
   return SPS_OK;

@@ -45,6 +45,7 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
            "sps_server_completed", "sps_probability_async", "sps_measure", "sps_pauli_exp",
            "sps_jit_selftest", "sps_device_rates", "sps_tune", "sps_tune_cache_lookup",
+           "sps_barrier_selftest",
            "sps_commute")
 
 
@@ -166,6 +167,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_tune.restype = st
     lib.sps_tune_cache_lookup.argtypes = [ctypes.c_char_p, u32, u32, ctypes.POINTER(TuneChoice)]
     lib.sps_tune_cache_lookup.restype = st
+    lib.sps_barrier_selftest.argtypes = [u32, u32, ctypes.POINTER(ctypes.c_int)]
+    lib.sps_barrier_selftest.restype = st
     lib.sps_batch_sync.argtypes = [vp, ctypes.POINTER(u32)]
     lib.sps_batch_sync.restype = st
     lib.sps_batch_circuit_status.argtypes = [vp, u32, ctypes.POINTER(st), psz, pu64,
@@ -441,6 +444,15 @@ def sps_tune_cache_lookup(path: str, kw: int, log2peak: int):
     c = TuneChoice()
     r = load_library().sps_tune_cache_lookup(path.encode(), kw, log2peak, ctypes.byref(c))
     return c.as_dict() if r == SPS_OK else None
+
+
+def sps_barrier_selftest(skip_block: int, spins: int) -> int:
+    """Status recorded by the cooperative launch's grid barrier with block
+    skip_block missing its first arrival (>= 8: none misses)."""
+    r = ctypes.c_int(-1)
+    _check(load_library().sps_barrier_selftest(skip_block, spins, ctypes.byref(r)),
+           "sps_barrier_selftest")
+    return r.value
 
 
 def sps_jit_selftest():

@@ -310,3 +310,19 @@ def test_mixed_circuits_chain_on_and_off():
         identical(got, ref)
         assert upd == upd0 and chains
         compare_states(got, oracle(n, parts, eps), eps)
+
+
+def test_grid_barrier_wait_is_bounded():
+    """The cooperative fallback launch's grid barrier: with every block
+    arriving, three barriers pass and nothing is recorded; with one block
+    missing its first arrival (a wait that nothing completes) the others give
+    up after their poll limit, the launch ends and SPS_ERR_TIMEOUT is recorded
+    for the host to read; the device stays usable."""
+    assert sps.sps_barrier_selftest(99, 1 << 14) == sps.SPS_OK
+    assert sps.sps_barrier_selftest(3, 1 << 14) == sps.SPS_ERR_TIMEOUT
+    assert sps.sps_barrier_selftest(0, 1 << 14) == sps.SPS_ERR_TIMEOUT
+    assert sps.sps_barrier_selftest(99, 1 << 14) == sps.SPS_OK
+    st = sps.SparseState(20, 1 << 10)   # the context still serves new work
+    st.apply(W.to_array([W.H(q) for q in range(6)]), 0.0)
+    assert st.nnz() == 64
+    st.close()
