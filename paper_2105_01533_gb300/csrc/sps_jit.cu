@@ -684,6 +684,62 @@ const JitEntry* jit_kernel(const std::string& src) {
   return ins->second.ok ? &ins->second : nullptr;
 }
 
+// The fields of a pass that decide its kernel's source (everything make_source
+// reads: all but the phase factors, which reach the kernel as device tables),
+// with the launch form and the architecture: the key of a second cache level
+// that costs a copy of the fields instead of a source generation.
+static_assert(sizeof(SOp) == 10, "SOp is ten bytes of rows and steps");
+std::string content_key(const BsPass& P, int kw, bool has_perm, bool has_phase, uint32_t G,
+                        int major, int minor) {
+  std::string k;
+  k.reserve(256 + P.ops.size() * sizeof(SOp) + P.row_choice.size());
+  auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+  const int32_t hdr[6] = {major, minor, kw, has_perm ? 1 : 0, has_phase ? 1 : 0, (int32_t)G};
+  put(hdr, sizeof(hdr));
+  const uint32_t f[8] = {P.nw, P.nrows, P.label_rows, P.aux_row0, P.aux_bits, P.ones_row,
+                         P.word_out, P.nchunks};
+  put(f, sizeof(f));
+  const uint8_t flags[3] = {(uint8_t)P.has_cnt, (uint8_t)P.expand, (uint8_t)P.direct};
+  put(flags, sizeof(flags));
+  put(P.word_bits, sizeof(P.word_bits));
+  put(P.row_of, sizeof(P.row_of));
+  put(P.chunk_shift, sizeof(P.chunk_shift));
+  put(P.chunk_bits, sizeof(P.chunk_bits));
+  put(&P.c_re, sizeof(double));
+  put(&P.c_im, sizeof(double));
+  put(&P.ex_d, sizeof(P.ex_d));
+  const uint32_t counts[2] = {(uint32_t)P.ops.size(), (uint32_t)P.row_choice.size()};
+  put(counts, sizeof(counts));
+  if (!P.ops.empty()) put(P.ops.data(), P.ops.size() * sizeof(SOp));
+  if (!P.row_choice.empty()) put(P.row_choice.data(), P.row_choice.size());
+  return k;
+}
+
+std::unordered_map<std::string, const JitEntry*>* g_jit_content = nullptr;
+
+// The compiled kernel of a pass: from the cache of pass contents, else its
+// source is generated and compiled (or found in the cache of sources).
+const JitEntry* jit_kernel_for(const BsPass& P, int kw, bool has_perm, bool has_phase, uint32_t G) {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const std::string key = content_key(P, kw, has_perm, has_phase, G, major, minor);
+  {
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    if (!g_jit_content) g_jit_content = new std::unordered_map<std::string, const JitEntry*>();
+    auto it = g_jit_content->find(key);
+    if (it != g_jit_content->end()) return it->second;
+  }
+  const JitEntry* e = jit_kernel(make_source(P, kw, has_perm, has_phase, G));
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  g_jit_content->emplace(key, e);
+  return e;
+}
+
 }  // namespace
 
 int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, const BsLaunch& b,
@@ -707,8 +763,7 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   const void* fn = P.jit_form == form ? P.jit_fn : nullptr;
   int bps = P.jit_bps;
   if (!fn) {
-    const std::string src = make_source(P, key_words, b.has_perm != 0, b.has_phase != 0, G);
-    const JitEntry* e = jit_kernel(src);
+    const JitEntry* e = jit_kernel_for(P, key_words, b.has_perm != 0, b.has_phase != 0, G);
     if (!e) return 0;
     fn = reinterpret_cast<const void*>(e->kernel);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
