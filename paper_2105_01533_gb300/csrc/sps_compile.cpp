@@ -723,6 +723,7 @@ void build_bitslice_rows(const Pass& p, uint32_t nqubits, const uint64_t extra[2
                          BsPass* out) {
   *out = BsPass();
   BsPass& b = *out;
+  b.ops.reserve(p.ops.size() + p.ops.size() / 4 + 8);
   b.nw = (nqubits + 31) / 32;
   std::memset(b.row_of, kNoRow, sizeof(b.row_of));
   // qubits the ops read (conditions, selectors) and flip
@@ -784,35 +785,37 @@ void build_bitslice_rows(const Pass& p, uint32_t nqubits, const uint64_t extra[2
     std::memset(&so, 0, sizeof(so));
     so.c[0] = so.c[1] = so.c[2] = ones;
     so.t = so.s = so.f0 = so.f1 = kNoRow;
-    std::vector<uint8_t> conds;
+    uint8_t conds[130];   // at most 128 condition qubits, then the scratch row
+    size_t nconds = 0;
     for (uint32_t w = 0; w < 2; ++w)
-      for (uint32_t q = 0; q < 64; ++q)
-        if ((o.c[w] >> q) & 1ull) conds.push_back(row_q(64 * w + q));
-    if (conds.size() > 3) {
+      for (uint64_t m = o.c[w]; m; m &= m - 1)
+        conds[nconds++] = row_q(64 * w + (uint32_t)__builtin_ctzll(m));
+    if (nconds > 3) {
       // AND the conditions past the second into the scratch row, three at a time
       size_t k = 2;
       bool first = true;
-      while (k < conds.size()) {
+      while (k < nconds) {
         SOp a;
         std::memset(&a, 0, sizeof(a));
         a.kind = SOP_AND;
         a.t = scratch;
         a.s = a.f0 = a.f1 = kNoRow;
         a.c[0] = first ? conds[k++] : scratch;
-        a.c[1] = k < conds.size() ? conds[k++] : ones;
-        a.c[2] = k < conds.size() ? conds[k++] : ones;
+        a.c[1] = k < nconds ? conds[k++] : ones;
+        a.c[2] = k < nconds ? conds[k++] : ones;
         first = false;
         b.ops.push_back(a);
       }
-      conds.resize(2);
-      conds.push_back(scratch);
+      nconds = 3;
+      conds[2] = scratch;
     }
-    for (size_t k = 0; k < conds.size(); ++k) so.c[k] = conds[k];
-    std::vector<uint8_t> tbits;   // a merged flip has several targets, one condition
+    for (size_t k = 0; k < nconds; ++k) so.c[k] = conds[k];
+    uint8_t tbits[128];   // a merged flip has several targets, one condition
+    size_t ntbits = 0;
     for (uint32_t w = 0; w < 2; ++w)
-      for (uint32_t q = 0; q < 64; ++q)
-        if ((o.t[w] >> q) & 1ull) tbits.push_back(row_q(64 * w + q));
-    if (!tbits.empty()) {
+      for (uint64_t m = o.t[w]; m; m &= m - 1)
+        tbits[ntbits++] = row_q(64 * w + (uint32_t)__builtin_ctzll(m));
+    if (ntbits > 0) {
       so.kind |= SOP_FLIP;
       so.t = tbits[0];
     }
@@ -837,7 +840,7 @@ void build_bitslice_rows(const Pass& p, uint32_t nqubits, const uint64_t extra[2
     }
     b.ops.push_back(so);
     // further targets: the same condition (no target is in it), flip only
-    for (size_t k = 1; k < tbits.size(); ++k) {
+    for (size_t k = 1; k < ntbits; ++k) {
       SOp x = so;
       x.kind = SOP_FLIP;
       x.t = tbits[k];
