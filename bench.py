@@ -214,7 +214,7 @@ def measured_peaks():
 
 KIND_NAMES = {1: "k_fused", 2: "k_branch_emit", 3: "k_branch_compact", 4: "k_small_run",
               5: "k_gather_build", 6: "k_gather_emit", 7: "k_expand", 8: "k_measure",
-              9: "k_amp_index", 10: "k_amp_layer", 11: "k_chain"}
+              9: "k_amp_index", 10: "k_amp_layer", 11: "k_chain", 12: "k_probability"}
 MOVED_ACCOUNTING = ("bytes the launch must move: B*n read and written by a fused pass that "
                     "permutes and changes phases (labels only or amplitudes only when it does "
                     "one of the two), B*(n_in + n_out) by a branching pass or an expansion, "
@@ -263,6 +263,8 @@ def algorithmic_bytes(r) -> float:
         return float(lb * n_in)
     if k == 11:   # an attempted run's d passes (none when the attempt took it: n_in 0)
         return float(B * (n_in + n_out) * d) if n_in > 0 else 0.0
+    if k == 12:   # readout: the labels (and the matching entries' amplitudes) read
+        return float(lb * n_in)
     if k == 2:
         return float(B * n_in)
     if k == 3:
@@ -280,7 +282,7 @@ def moved_bytes(r) -> float:
         return float((lb + (lb if r["flags"] & 1 else 0) + (32 if r["flags"] & 2 else 0)) * n_in)
     if k == 10:   # labels stay: amplitudes read and written, labels read by the lookups
         return float((32 + lb) * n_out)
-    return algorithmic_bytes(r) if k in (2, 3, 5, 9, 11) else float(B * (n_in + n_out))
+    return algorithmic_bytes(r) if k in (2, 3, 5, 9, 11, 12) else float(B * (n_in + n_out))
 
 
 def kernel_source_hash() -> str:

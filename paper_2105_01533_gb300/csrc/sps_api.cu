@@ -1575,9 +1575,11 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
   sps_status st = sps_sync(s, nullptr);
   if (st != SPS_OK) return st;
   const LaunchCfg lc = cfg_of(s);
-  if (launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0], value[1],
-                         s->partials, prob_grid(s), s->dresult) < 0)
-    return cuda_ok(cudaGetLastError());
+  ProfScope ps(s, 12, s->pass_serial, 0, 0u);
+  const int pn = launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0],
+                                    value[1], s->partials, prob_grid(s), s->dresult, ps.slot);
+  ps.done();
+  if (pn < 0) return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 1;
   if (cudaMemcpyAsync(s->hresult, s->dresult, sizeof(double), cudaMemcpyDeviceToHost, s->stream) !=
       cudaSuccess)
@@ -1594,9 +1596,11 @@ sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uin
   const sps_status fs = flush_reset(s);
   if (fs != SPS_OK) return fs;
   const LaunchCfg lc = cfg_of(s);
-  if (launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0], value[1],
-                         s->partials, prob_grid(s), s->dresult) < 0)
-    return cuda_ok(cudaGetLastError());
+  ProfScope ps(s, 12, s->pass_serial, 0, 0u);
+  const int pn = launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0],
+                                    value[1], s->partials, prob_grid(s), s->dresult, ps.slot);
+  ps.done();
+  if (pn < 0) return cuda_ok(cudaGetLastError());
   s->counters.kernel_launches += 1;
   if (cudaMemcpyAsync(out, s->dresult, sizeof(double), cudaMemcpyDefault, s->stream) != cudaSuccess)
     return cuda_ok(cudaGetLastError());

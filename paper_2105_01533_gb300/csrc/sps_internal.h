@@ -541,7 +541,8 @@ int launch_measure(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs, uint
                    uint32_t mg, unsigned long long* plog);
 int launch_probability(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
-                       double* partials, int nblocks, double* result);
+                       double* partials, int nblocks, double* result,
+                       unsigned long long* plog = nullptr);
 // mg: label-mask buffers of a launch that writes labels (MaskRing::writer)
 int launch_set_nnz(void* stream, Ctl* ctl, unsigned long long nnz, uint32_t mg);
 int launch_reset_state(void* stream, int key_words, Ctl* ctl, Bufs bufs, uint32_t mg);

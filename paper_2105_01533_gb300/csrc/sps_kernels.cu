@@ -874,11 +874,16 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 template <int KW>
 __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64_t m0,
                                                      uint64_t m1, uint64_t v0, uint64_t v1,
-                                                     double* partials, double* result) {
+                                                     double* partials, double* result,
+                                                     unsigned long long* plog) {
   __shared__ double sh[32];
   __shared__ bool last;
   constexpr int U = 8;
   const uint64_t n = ctl->nnz;
+  if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
+    plog[0] = n;
+    plog[1] = n;
+  }
   const SoA s = pick(bufs, ctl->cur);
   const bool use0 = (m0 | v0) != 0ull, use1 = KW == 2 && (m1 | v1) != 0ull;
   double acc = 0.0;
@@ -1407,14 +1412,15 @@ int launch_branch_compact(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs buf
 
 int launch_probability(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        uint64_t mask_lo, uint64_t mask_hi, uint64_t val_lo, uint64_t val_hi,
-                       double* partials, int nblocks, double* result) {
+                       double* partials, int nblocks, double* result,
+                       unsigned long long* plog) {
   cudaStream_t st = (cudaStream_t)lc.stream;
   if (key_words == 1)
     k_probability<1><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
-                                              partials, result);
+                                              partials, result, plog);
   else
     k_probability<2><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
-                                              partials, result);
+                                              partials, result, plog);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -102,3 +102,10 @@ def test_chain_launch_is_credited_only_when_it_ran(bench):
     assert bench.moved_bytes(rec(11, 0, 50, nops=8)) == 0.0
     assert bench.algorithmic_bytes(rec(11, 40, 50, nops=8)) == 32 * (40 + 50) * 8
     assert bench.kernel_name(rec(11, 40, 50)) == "k_chain"
+
+
+def test_readout_records(bench):
+    """The probability readout (kind 12) reads the labels of every entry."""
+    assert bench.algorithmic_bytes(rec(12, 1000, 1000, lb=16)) == 16 * 1000
+    assert bench.moved_bytes(rec(12, 1000, 1000, lb=8)) == 8 * 1000
+    assert bench.kernel_name(rec(12, 10, 10)) == "k_probability"
