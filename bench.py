@@ -620,6 +620,8 @@ def run_sub(args, sps, torch, name: str):
             "ms_per_step": round(total / steps, 5), "steps": steps,
             "updates_per_step": int(U // steps), "nnz": int(nnz),
             "gpu_launches_per_step": round(launches / steps, 1), "roofline": rl,
+            "p50_step_ms": round(float(np.median(ms)), 5),
+            "min_step_ms": round(float(np.min(ms)), 5), "max_step_ms": round(float(np.max(ms)), 5),
             "prepare_s": round(prep_s, 2)}
 
 
