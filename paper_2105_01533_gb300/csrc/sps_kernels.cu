@@ -871,63 +871,74 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // Each thread takes 8 consecutive entries per step (four 16-byte label loads
 // in flight); a label word the mask does not test is not read at all, and
 // amplitudes are read only for matching labels.
-template <int KW>
+// HI: the condition reads the high label words (128-bit labels, a mask or
+// value there); else only the low words are loaded.
+template <int KW, bool HI>
 __global__ void __launch_bounds__(256) k_probability(Ctl* ctl, Bufs bufs, uint64_t m0,
                                                      uint64_t m1, uint64_t v0, uint64_t v1,
                                                      double* partials, double* result,
                                                      unsigned long long* plog) {
   __shared__ double sh[32];
   __shared__ bool last;
-  constexpr int U = 8;
+  constexpr int U = HI ? 8 : 16;   // entries per lane and iteration (loads in flight)
   const uint64_t n = ctl->nnz;
   if (plog && blockIdx.x == 0 && threadIdx.x == 0) {
     plog[0] = n;
     plog[1] = n;
   }
   const SoA s = pick(bufs, ctl->cur);
-  const bool use0 = (m0 | v0) != 0ull, use1 = KW == 2 && (m1 | v1) != 0ull;
+  const bool use0 = (m0 | v0) != 0ull;
+  constexpr bool use1 = HI;
   double acc = 0.0;
   const uint64_t stride = (uint64_t)U * gridDim.x * blockDim.x;
-  // warps iterate together (the loop bound is taken at the warp's first lane)
-  const uint64_t lane_off = (uint64_t)U * (threadIdx.x & 31u);
+  // A warp reads U * 32 consecutive entries per iteration, 64 per load: load h
+  // takes entries w0 + 64 h + 2 lane and the next (one contiguous 512-byte
+  // span per instruction). Warps iterate together (the bound is the warp's).
+  const uint64_t lane2 = 2ull * (threadIdx.x & 31u);
   for (uint64_t w0 = (uint64_t)U * (blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u));
        w0 < n; w0 += stride) {
-    const uint64_t i = w0 + lane_off;
     uint64_t k0[U], k1[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) k0[j] = k1[j] = 0ull;
-    if (i + U <= n) {   // the buffers are 256-byte aligned and i is a multiple of 8
+    if (w0 + 32u * U <= n) {   // the buffers are 256-byte aligned and w0 a multiple of 256
 #pragma unroll
       for (int h = 0; h < U / 2; ++h) {
+        const uint64_t e = w0 + 64u * h + lane2;
         if (use0) {
-          const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + i) + h);
+          const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.lo + e));
           k0[2 * h] = a.x;
           k0[2 * h + 1] = a.y;
         }
         if (use1) {
-          const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.hi + i) + h);
+          const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(s.hi + e));
           k1[2 * h] = a.x;
           k1[2 * h + 1] = a.y;
         }
       }
-    } else if (i < n) {
-      for (int j = 0; j < U; ++j)
-        if (i + j < n) {
-          if (use0) k0[j] = s.lo[i + j];
-          if (use1) k1[j] = s.hi[i + j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const uint64_t e = w0 + 64u * (j >> 1) + lane2 + (j & 1);
+        if (e < n) {
+          if (use0) k0[j] = s.lo[e];
+          if (use1) k1[j] = s.hi[e];
         }
+      }
     }
     uint32_t hit = 0;
 #pragma unroll
-    for (int j = 0; j < U; ++j)
-      if (i + j < n && (k0[j] & m0) == v0 && (k1[j] & m1) == v1) hit |= 1u << j;
+    for (int j = 0; j < U; ++j) {
+      const uint64_t e = w0 + 64u * (j >> 1) + lane2 + (j & 1);
+      if (e < n && (k0[j] & m0) == v0 && (k1[j] & m1) == v1) hit |= 1u << j;
+    }
     // FP64 is scarce on this part: only warps with a matching label run the
     // products (a predicated product still occupies the FP64 pipe)
     if (__any_sync(FULL, hit != 0u)) {
 #pragma unroll
       for (int j = 0; j < U; ++j) {
         if ((hit >> j) & 1u) {
-          const double re = s.re[i + j], im = s.im[i + j];
+          const uint64_t e = w0 + 64u * (j >> 1) + lane2 + (j & 1);
+          const double re = s.re[e], im = s.im[e];
           acc += re * re + im * im;
         }
       }
@@ -1415,12 +1426,16 @@ int launch_probability(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
                        double* partials, int nblocks, double* result,
                        unsigned long long* plog) {
   cudaStream_t st = (cudaStream_t)lc.stream;
+  const bool hi = key_words == 2 && (mask_hi | val_hi) != 0ull;
   if (key_words == 1)
-    k_probability<1><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
-                                              partials, result, plog);
+    k_probability<1, false><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
+                                                     partials, result, plog);
+  else if (hi)
+    k_probability<2, true><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
+                                                    partials, result, plog);
   else
-    k_probability<2><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
-                                              partials, result, plog);
+    k_probability<2, false><<<nblocks, 256, 0, st>>>(ctl, bufs, mask_lo, mask_hi, val_lo, val_hi,
+                                                     partials, result, plog);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

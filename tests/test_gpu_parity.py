@@ -631,3 +631,28 @@ def test_scatter_cooperative_probe_limit():
             st.sync()
         assert e.value.status == sps.SPS_ERR_TABLE_FULL
         st.close()
+
+
+@pytest.mark.parametrize("n_entries", [1, 255, 256, 257, 4095, 70001, 200001])
+@pytest.mark.parametrize("nq", [40, 90])
+def test_probability_ragged_sizes(n_entries, nq):
+    """The readout over states whose size is not a multiple of a warp's 256
+    entries (full spans and the ragged tail), 64- and 128-bit labels: equal to
+    the sum of |a|^2 over the matching labels of the state itself."""
+    rng = np.random.default_rng(n_entries + nq)
+    lo = rng.choice(1 << 38, size=n_entries, replace=False).astype(np.uint64)
+    hi = (rng.integers(0, 1 << 20, size=n_entries).astype(np.uint64) if nq > 64
+          else np.zeros(n_entries, np.uint64))
+    re = rng.normal(size=n_entries)
+    im = rng.normal(size=n_entries)
+    st = sps.SparseState(nq, max(n_entries, 16))
+    st.set_amplitudes(hi if nq > 64 else None, lo, re, im)
+    mag = re * re + im * im
+    for mask, val in [((0, 0), (0, 0)), ((0b1011, 0), (0b0010, 0)),
+                      ((1 << 37, 1 if nq > 64 else 0), (0, 1 if nq > 64 else 0))]:
+        sel = ((lo & np.uint64(mask[0])) == np.uint64(val[0])) & \
+              ((hi & np.uint64(mask[1])) == np.uint64(val[1]))
+        want = float(np.sum(mag[sel]))
+        got = st.probability(mask, val)
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (mask, got, want)
+    st.close()
