@@ -12,7 +12,9 @@ layers), ``givens64-m5`` / ``givens64-m6`` (5 / 6 occupied modes, the
 
 A step = reset to |0...0>, apply the whole gate stream (every branching pass
 and fused phase/permutation pass), read the probability of one register value
-back (the readout kernel). Updates per step U = sum over gates of the nonzero
+back (registered with sps_set_readout: summed by the compiled expansion launch
+when that launch ends the apply, else by the readout kernel; ``--fused-readout
+0`` always takes the kernel). Updates per step U = sum over gates of the nonzero
 count before the gate. ``value`` = U * steps / (sum of per-step device times);
 L2 is flushed (a 512 MB write) between timed steps, outside the timed events.
 The default run adds sub-lines for the other configs, the batched and the
@@ -400,6 +402,8 @@ def run_ours(args, dist, rank, world, local_rank):
     U, nnz_final = updates_per_step(sps, wl, st)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     mask, val = wl["readout"]
+    if args.fused_readout:   # summed by the launch that ends the apply, where it can be
+        st.set_readout(mask, val)
     # each step's readout lands in its own pinned slot, in stream order: the host
     # does not wait for step i before enqueueing step i + 1
     nslots = args.warmup + args.steps + min(args.steps, 20)
@@ -422,6 +426,7 @@ def run_ours(args, dist, rank, world, local_rank):
         sampler.start()
         time.sleep(0.3)
     c0 = st.counters().kernel_launches
+    f0 = st.counters().fused_readouts
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     if args.profile_range:   # a profiler started with capture off records the timed steps only
@@ -435,10 +440,23 @@ def run_ours(args, dist, rank, world, local_rank):
     if args.profile_range:
         torch.cuda.profiler.stop()
     launches = st.counters().kernel_launches - c0
+    fused = st.counters().fused_readouts - f0
     st.sync()   # raises if any timed step failed on the device
     p = probs[:slot[0]].numpy()
     if not np.all(np.abs(p - p[0]) <= 1e-9):
         raise SystemExit("readouts of identical steps differ: %r" % p[:8])
+    # the same state read by the readout kernel
+    st.set_readout(None, None)
+    p_kernel = st.probability(mask, val)
+    if abs(p_kernel - p[0]) > 1e-13:
+        raise SystemExit("fused readout %r differs from the readout kernel's %r" % (p[0], p_kernel))
+    readout = {"probability": float(p[0]), "kernel_probability": p_kernel,
+               "fused_per_step": round(fused / args.steps, 3),
+               "what": "sum of |a|^2 over labels with (label & mask) == value; fused: formed by "
+                       "the compiled expansion launch as it stores the outputs "
+                       "(sps_set_readout), else the readout kernel"}
+    if args.fused_readout:
+        st.set_readout(mask, val)
     barrier(dist)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
@@ -473,6 +491,7 @@ def run_ours(args, dist, rank, world, local_rank):
                           "l2": "flushed between timed steps (512 MB write)",
                           "parallelism": "replicas" if world > 1 else "single"},
                "roofline": rl, "e2e": e2e, "gpu_launches": int(launches * world),
+               "readout": readout,
                "device_rates": device_rates(sps),
                "clocks": clocks, "p50_step_ms": round(float(np.median(step_ms)), 5),
                "p99_step_ms": round(float(np.percentile(step_ms, 99)), 5)}
@@ -572,6 +591,8 @@ def run_sub(args, sps, torch, name: str):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     mask, val = wl["readout"]
+    if args.fused_readout:
+        st.set_readout(mask, val)
     out = torch.zeros(4096, dtype=torch.float64, device="cuda")
     slot = [0]
     block = wl.get("block", False)
@@ -1000,6 +1021,9 @@ def main():
     ap.add_argument("--sub-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused-readout", type=int, default=1,
+                    help="register the step's readout so that a compiled expansion launch "
+                         "ending the apply sums it (0: the readout kernel every step)")
     ap.add_argument("--opt", action="append", default=[],
                     help="library option NAME=VALUE (e.g. bitslice_min_ops=0), repeatable")
     ap.add_argument("--batched", type=int, default=1,

@@ -177,6 +177,22 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
 sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
                                  double* out);
 
+/* Registers a readout condition (mask, value as in sps_probability), or
+ * clears it (both NULL). While it is set, an sps_apply whose last launch is
+ * the compiled expansion form (a circuit that starts from a reset with an
+ * expansion and a compiled phase/permutation run, SPS_OPT_BITSLICE_JIT) also
+ * forms that condition's probability in the same launch, as the outputs are
+ * stored; a later sps_probability or sps_probability_async with the same
+ * condition, before any call that changes the state, then copies that sum
+ * instead of launching the readout (counted in sps_counters.fused_readouts).
+ * Other conditions, and states changed by other launches, take the readout
+ * kernel as before. The fused sum is formed in a fixed order too (per block
+ * of the launch, then over blocks in block order), which differs from the
+ * readout kernel's, so the two may differ in the last bits. Allocates a few
+ * KB of device memory on first use. Errors: SPS_ERR_ARG (one of mask, value
+ * NULL), SPS_ERR_OOM. */
+sps_status sps_set_readout(sps_state* s, const uint64_t mask[2], const uint64_t value[2]);
+
 /* Applies exp(-i theta/2 P) for a Pauli string P (Sec. 3 lists Pauli
  * exponentials among the simulator's operations; Sec. 2.1 defines X, Y, Z and
  * R_P(theta) = exp(-i theta P / 2)). x[2] marks the qubits whose factor is X or
@@ -331,7 +347,15 @@ typedef enum sps_option {
                                   the attempt took the run and otherwise runs
                                   them in order with grid barriers (the same
                                   state as their separate launches); 0: each
-                                  pass as its own launches */
+                                  pass as its own launches */,
+  SPS_OPT_READOUT_MIN_PLANES = 22 /* 8 (default): a registered readout
+                                  (sps_set_readout) is summed by the compiled
+                                  expansion launch only when it tests at least
+                                  this many of the launch's label bits (or no
+                                  label can match): a broad condition matches
+                                  many outputs, whose amplitudes the launch
+                                  would read back, and the readout kernel
+                                  serves it better; 0..128 */
 } sps_option;
 
 /* Sets an option for subsequent sps_apply calls on this state. Errors:
@@ -392,6 +416,8 @@ typedef struct sps_counters {
   uint64_t branch_passes;    /* branching passes enqueued */
   uint64_t kernel_launches;  /* kernels enqueued by this state */
   uint64_t upload_bytes;     /* compiled plans copied host -> device by sps_apply */
+  uint64_t fused_readouts;   /* probability readouts answered from a registered
+                                readout's sum (sps_set_readout), no launch */
 } sps_counters;
 sps_status sps_get_counters(sps_state* s, sps_counters* out);
 
@@ -410,7 +436,8 @@ sps_status sps_get_counters(sps_state* s, sps_counters* out);
  * pass permutes labels, bit 1 it changes amplitudes, bit 2 (kinds 7 and 10) the
  * launch also applied the phase/permutation run after the branching gates,
  * bit 3 (kind 1) bit-sliced form, bit 4 (kind 1) the form compiled for this
- * run (SPS_OPT_BITSLICE_JIT). label_bytes: 8 or 16. */
+ * run (SPS_OPT_BITSLICE_JIT), bit 5 (kind 7) the launch also summed the
+ * registered readout (sps_set_readout). label_bytes: 8 or 16. */
 typedef struct sps_kernel_record {
   uint32_t kind;
   uint32_t pass_serial;

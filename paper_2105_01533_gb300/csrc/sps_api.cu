@@ -113,6 +113,14 @@ struct sps_state {
   unsigned* dflag = nullptr;
   unsigned* hflag = nullptr;  // pinned
   int prob_blocks = 0;
+  // a registered readout (sps_set_readout): summed by a compiled expansion
+  // launch that ends an sps_apply; valid while version == rd_version
+  bool rd_on = false;
+  uint64_t rd_mask[2] = {0ull, 0ull}, rd_value[2] = {0ull, 0ull};
+  double* rd_buf = nullptr;    // rd_cap block sums, then the sum
+  uint32_t rd_cap = 0;
+  uint64_t version = 1;        // bumped by every call that changes the state
+  uint64_t rd_version = 0;     // version whose readout sum is in rd_buf[rd_cap]
   // options
   uint32_t load_pct = 50;
   uint32_t probe_limit = 0;   // 0 = table size
@@ -125,6 +133,7 @@ struct sps_state {
   int bs_jit = 1;                          // SPS_OPT_BITSLICE_JIT
   bool plan_cache = true;                  // SPS_OPT_PLAN_CACHE
   bool chain = true;                       // SPS_OPT_FALLBACK_CHAIN
+  uint32_t rd_min_planes = 8;              // SPS_OPT_READOUT_MIN_PLANES
   uint32_t small_cap = kSmallCap;   // 0 disables small-state runs
   // plan arena: op streams, factors and tables of the current sps_apply
   unsigned char* arena = nullptr;
@@ -579,6 +588,7 @@ sps_status sps_create(uint32_t nqubits, uint64_t capacity, void* cuda_stream, sp
 
 sps_status sps_reset(sps_state* s) {
   if (!s) return SPS_ERR_ARG;
+  ++s->version;
   s->amp_force = true;
   s->reset_pending = true;   // enqueued by the next use of the state (flush_reset)
   s->nnz_bound = 1;
@@ -1154,6 +1164,7 @@ static sps_status build_plan(sps_state* s, const sps_gate* gates, size_t ngates,
 sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double prune_eps,
                      size_t* failed_gate) {
   if (!s || (ngates && !gates) || !(prune_eps >= 0.0)) return SPS_ERR_ARG;
+  ++s->version;
   uint64_t eps_bits;
   std::memcpy(&eps_bits, &prune_eps, sizeof(eps_bits));
   std::vector<uint64_t> opts = plan_options(s);
@@ -1295,11 +1306,25 @@ sps_status sps_apply(sps_state* s, const sps_gate* gates, size_t ngates, double 
       MaskRing ring = s->masks;   // taken only if the launch happens
       bl.mg = ring.writer();
       bl.fallback = 0;
+      ReadoutFuse rf;
+      uint32_t rd_done = 0;
+      if (s->rd_on && passes.size() == 2) {   // the launch ends the apply
+        std::memcpy(rf.mask, s->rd_mask, sizeof(rf.mask));
+        std::memcpy(rf.value, s->rd_value, sizeof(rf.value));
+        rf.part = s->rd_buf;
+        rf.out = s->rd_buf + s->rd_cap;
+        rf.cap = s->rd_cap;
+        rf.min_planes = s->rd_min_planes;
+        bl.rd = &rf;
+        bl.rd_done = &rd_done;
+      }
       const uint64_t nout = 1ull << p.ex_d;
       ProfScope ps(s, 7, serial, p.ex_d, 3u | 4u | 8u | 16u);
       const int n = launch_fused_bs_jit(lc, s->kw, s->ctl, s->bufs, bl, nout, ps.slot);
+      if (rd_done) ps.rec.flags |= 32u;
       ps.done();
       if (n < 0) return cuda_ok(cudaGetLastError());
+      if (n > 0 && rd_done) s->rd_version = s->version;
       if (n > 0) {
         s->masks = ring;
         s->amp_force = true;
@@ -1502,6 +1527,7 @@ sps_status sps_set_amplitudes(sps_state* s, const uint64_t* key_hi, const uint64
                               const double* re, const double* im, uint64_t n) {
   if (!s || (n && (!key_lo || !re || !im))) return SPS_ERR_ARG;
   if (n > s->capacity) return SPS_ERR_CAPACITY;
+  ++s->version;
   s->amp_force = true;
   sps_status st = sps_sync(s, nullptr);
   if (st != SPS_OK) return st;
@@ -1570,10 +1596,51 @@ static int prob_grid(const sps_state* s) {
   return b < 1 ? 1 : b > (uint64_t)s->prob_blocks ? s->prob_blocks : (int)b;
 }
 
+// The registered readout's sum holds for the state now and this condition.
+static bool readout_fused(const sps_state* s, const uint64_t mask[2], const uint64_t value[2]) {
+  return s->rd_on && s->rd_version == s->version && !s->reset_pending &&
+         s->rd_mask[0] == mask[0] && s->rd_mask[1] == mask[1] && s->rd_value[0] == value[0] &&
+         s->rd_value[1] == value[1];
+}
+
+sps_status sps_set_readout(sps_state* s, const uint64_t mask[2], const uint64_t value[2]) {
+  if (!s || (!mask) != (!value)) return SPS_ERR_ARG;
+  if (!mask) {
+    s->rd_on = false;
+    return SPS_OK;
+  }
+  if (!s->rd_buf) {
+    // one sum per block of the compiled launch: at most 16 resident per SM
+    void* p = nullptr;
+    const uint32_t cap = (uint32_t)(s->sms > 0 ? s->sms : 1) * 16u;
+    const sps_status st = dev_alloc(s, sizeof(double) * (cap + 1), &p);
+    if (st != SPS_OK) return st;
+    s->rd_buf = (double*)p;
+    s->rd_cap = cap;
+  }
+  const bool same = s->rd_on && s->rd_mask[0] == mask[0] && s->rd_mask[1] == mask[1] &&
+                    s->rd_value[0] == value[0] && s->rd_value[1] == value[1];
+  if (!same) s->rd_version = 0;   // the sum in rd_buf is for another condition
+  std::memcpy(s->rd_mask, mask, sizeof(s->rd_mask));
+  std::memcpy(s->rd_value, value, sizeof(s->rd_value));
+  s->rd_on = true;
+  return SPS_OK;
+}
+
 sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t value[2], double* p) {
   if (!s || !mask || !value || !p) return SPS_ERR_ARG;
   sps_status st = sps_sync(s, nullptr);
   if (st != SPS_OK) return st;
+  if (readout_fused(s, mask, value)) {
+    s->counters.fused_readouts += 1;
+    if (cudaMemcpyAsync(s->hresult, s->rd_buf + s->rd_cap, sizeof(double), cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess)
+      return cuda_ok(cudaGetLastError());
+    st = cuda_ok(cudaStreamSynchronize(s->stream));
+    if (st != SPS_OK) return st;
+    *p = *s->hresult;
+    return SPS_OK;
+  }
   const LaunchCfg lc = cfg_of(s);
   ProfScope ps(s, 12, s->pass_serial, 0, 0u);
   const int pn = launch_probability(lc, s->kw, s->ctl, s->bufs, mask[0], mask[1], value[0],
@@ -1593,6 +1660,13 @@ sps_status sps_probability(sps_state* s, const uint64_t mask[2], const uint64_t 
 sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uint64_t value[2],
                                  double* out) {
   if (!s || !mask || !value || !out) return SPS_ERR_ARG;
+  if (readout_fused(s, mask, value)) {
+    s->counters.fused_readouts += 1;
+    if (cudaMemcpyAsync(out, s->rd_buf + s->rd_cap, sizeof(double), cudaMemcpyDefault, s->stream) !=
+        cudaSuccess)
+      return cuda_ok(cudaGetLastError());
+    return SPS_OK;
+  }
   const sps_status fs = flush_reset(s);
   if (fs != SPS_OK) return fs;
   const LaunchCfg lc = cfg_of(s);
@@ -1610,6 +1684,7 @@ sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uin
 sps_status sps_pauli_exp(sps_state* s, const uint64_t x[2], const uint64_t z[2],
                          const uint64_t cmask[2], double theta, double prune_eps) {
   if (!s || !x || !z || !cmask || !(prune_eps >= 0.0) || !std::isfinite(theta)) return SPS_ERR_ARG;
+  ++s->version;
   uint64_t lim[2];
   label_limits(s->nqubits, &lim[0], &lim[1]);
   for (int w = 0; w < 2; ++w)
@@ -1684,6 +1759,7 @@ sps_status sps_pauli_exp(sps_state* s, const uint64_t x[2], const uint64_t z[2],
 
 sps_status sps_measure(sps_state* s, uint32_t qubit, double r, double* out) {
   if (!s || !out || qubit >= s->nqubits || !(r >= 0.0 && r < 1.0)) return SPS_ERR_ARG;
+  ++s->version;
   const sps_status fs = flush_reset(s);
   if (fs != SPS_OK) return fs;
   const LaunchCfg lc = cfg_of(s);
@@ -1760,6 +1836,10 @@ sps_status sps_set_option(sps_state* s, sps_option opt, int64_t v) {
     case SPS_OPT_FALLBACK_CHAIN:
       if (v != 0 && v != 1) return SPS_ERR_ARG;
       s->chain = v == 1;
+      return SPS_OK;
+    case SPS_OPT_READOUT_MIN_PLANES:
+      if (v < 0 || v > 128) return SPS_ERR_ARG;
+      s->rd_min_planes = (uint32_t)v;
       return SPS_OK;
     case SPS_OPT_FUSED_LABELS:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return SPS_ERR_ARG;

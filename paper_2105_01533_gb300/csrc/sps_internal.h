@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "sps.h"
@@ -124,6 +125,11 @@ struct BsPass {
   mutable uint32_t jit_form = 0;
   mutable const void* jit_fn = nullptr;
   mutable int jit_bps = 0;
+  // the same with a readout compiled in (jit_rd_key: the readout's form)
+  mutable uint32_t jit_rd_form = 0;
+  mutable std::string jit_rd_key;
+  mutable const void* jit_rd_fn = nullptr;
+  mutable int jit_rd_bps = 0;
   uint32_t nw = 0;            // 32-bit words of a label (nqubits / 32 rounded up)
   uint32_t nrows = 0;         // rows per tile column: label + aux + scratch + ones
   uint32_t label_rows = 0;
@@ -416,6 +422,19 @@ struct BsLaunch {
   uint32_t groups;           // groups of 32 entries per warp tile (2..32), 0 = choose
   uint32_t mg;               // label-mask buffers (MaskRing)
   uint32_t fallback = 0;     // as in launch_fused
+  // A probability readout summed by the expansion form as it stores (see
+  // ReadoutFuse); nullptr: none. *rd_done is set to 1 if the launch sums it.
+  const struct ReadoutFuse* rd = nullptr;
+  uint32_t* rd_done = nullptr;
+};
+// sum |a|^2 over output labels k with (k & mask) == value, formed by a
+// compiled expansion launch: per-block sums in part[0 .. cap), the total in *out
+struct ReadoutFuse {
+  uint64_t mask[2], value[2];
+  double* part;
+  double* out;
+  uint32_t cap;
+  uint32_t min_planes;   // summed only if it tests this many planes (or none can match)
 };
 // Returns the kernels enqueued (1 or more), 0 if the plan does not fit one
 // launch (then the pass must take the direct form), -1 on a launch error.

@@ -114,6 +114,9 @@ struct JArgs {
   const double2* direct;
   u64* plog;
   u32 fallback, mg_wr, mg_rs, ngates;
+  // with RD: the readout's block sums and its total
+  double* rd_part;
+  double* rd_out;
 };
 
 struct Transposer {
@@ -187,6 +190,11 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
   extern __shared__ __align__(16) u32 bsm[];
   __shared__ u64 part[4][32];
   unsigned char* ctl = a.ctl;
+#if EXPAND && RD
+  __shared__ double rsum[32];
+  __shared__ u32 am_last;
+  double racc = 0.0;   // this lane's readout sum
+#endif
 #if EXPAND
   // the expansion's 2^EX_D outputs from |0...0> (a reset not yet carried out):
   // nothing is read, the outputs go to buffer 1, the last block publishes them
@@ -284,6 +292,16 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
     // 2. the walk, lane g on group g (in an expansion: from the generated planes)
     if (lane < GG) walk(pl + lane, base + 32ull * lane);
     __syncwarp();
+#if EXPAND && RD
+    // the readout's matches among lane g's group: the tested output planes
+    // (bit e: entry base + 32 g + e), as stored by the walk
+    u32 rmatch = 0u;
+    if (!RD_NONE && lane < GG) {
+      const u64 g0e = base + 32ull * lane;
+      rmatch = g0e >= n ? 0u : n - g0e >= 32ull ? FULL : (1u << (u32)(n - g0e)) - 1u;
+      rmatch &= rd_match(pl + lane);
+    }
+#endif
     // 3. transpose back and store, 4 groups at a time
 #pragma unroll 1
     for (u32 g0 = 0; g0 < GG; g0 += STORE_BATCH) {
@@ -430,6 +448,20 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
         }
       }
     }
+#if EXPAND && RD
+    // the matching entries' amplitudes, each read back by the lane that stored
+    // it (rare: FP64 products only in warps with a match)
+    if (__any_sync(FULL, rmatch != 0u)) {
+      for (u32 g = 0; g < GG; ++g) {
+        const u32 mw = __shfl_sync(FULL, rmatch, g);
+        if ((mw >> lane) & 1u) {
+          const u64 e = base + 32ull * g + lane;
+          const double re = s.re[e], im = s.im[e];
+          racc += re * re + im * im;
+        }
+      }
+    }
+#endif
     __syncwarp();
   }
   if (HAS_PERM) {
@@ -465,10 +497,43 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
   // the last block publishes the outputs and does the reset's work on the
   // control block (no status, no failure record; the updates of the expansion,
   // 2^EX_D - 1, and of the run, 2^EX_D per gate)
+  // (with RD, first the readout: block sums in a fixed order, which the last
+  // block adds in block order)
+#if RD
+  for (int d = 16; d > 0; d >>= 1) racc += __shfl_down_sync(FULL, racc, d);
+  if (lane == 0) rsum[warp] = racc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned w = 0; w < (blockDim.x >> 5); ++w) t += rsum[w];
+    a.rd_part[blockIdx.x] = t;
+    __threadfence();
+    const u32 done = atomicAdd(reinterpret_cast<u32*>(ctl + OFF_BLOCKS_DONE), 1u);
+    am_last = done == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    double t = 0.0;
+    for (u32 b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(a.rd_part + b);
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(FULL, t, d);
+    __syncthreads();
+    if (lane == 0) rsum[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = 0.0;
+      for (unsigned w = 0; w < (blockDim.x >> 5); ++w) r += rsum[w];
+      *a.rd_out = r;
+    }
+  }
+  if (threadIdx.x == 0 && am_last) {
+    {
+#else
   if (threadIdx.x == 0) {
     __threadfence();
     const u32 done = atomicAdd(reinterpret_cast<u32*>(ctl + OFF_BLOCKS_DONE), 1u);
     if (done == gridDim.x - 1) {
+#endif
       __threadfence();
       *reinterpret_cast<volatile u32*>(ctl + OFF_STATUS) = 0u;
       *reinterpret_cast<volatile u32*>(ctl + OFF_FAIL_PASS) = 0u;
@@ -487,10 +552,51 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
 
 constexpr int kJitWarps = 4;
 
+// A readout compiled into the expansion form: the output planes it tests
+// (row offsets in words) and the wanted value of each; none: no output label
+// can match. key(): its bytes, for the caches.
+struct RdForm {
+  bool none = false;
+  std::vector<uint16_t> row;
+  std::vector<uint8_t> want;
+  std::string key() const {
+    std::string k(1, none ? '\1' : '\0');
+    k.append(reinterpret_cast<const char*>(row.data()), row.size() * sizeof(uint16_t));
+    k.append(reinterpret_cast<const char*>(want.data()), want.size());
+    return k;
+  }
+};
+
+// The readout (mask, value) on the outputs of expansion plan P in tiles of G
+// groups: a tested bit with a row is a plane; one without is 0 in every output
+// label (the launch writes every word, and a bit without a row stays 0).
+RdForm readout_form(const BsPass& P, int kw, uint32_t G, const uint64_t mask[2],
+                    const uint64_t value[2]) {
+  RdForm f;
+  for (int i = 0; i < 128; ++i) {
+    const uint64_t bit = 1ull << (i & 63);
+    const bool m = (mask[i >> 6] & bit) != 0ull, v = (value[i >> 6] & bit) != 0ull;
+    if (!m || i >= 64 * kw) {
+      f.none = f.none || v;   // a wanted bit outside the mask or the label
+      continue;
+    }
+    const int w = i >> 5;
+    const uint8_t r = ((P.word_out >> w) & 1u) ? P.row_of[w][i & 31] : kNoRow;
+    if (r == kNoRow) {
+      f.none = f.none || v;
+      continue;
+    }
+    f.row.push_back((uint16_t)(r * (G + 1)));
+    f.want.push_back(v ? 1u : 0u);
+  }
+  return f;
+}
+
 // The constants and the walk of one plan for tiles of G groups (16 or 32),
 // then the template. Tiles of 16 groups leave half the lanes idle in the walk
 // and load and store in smaller batches.
-std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, uint32_t G) {
+std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, uint32_t G,
+                        const RdForm* rd) {
   const uint32_t S = G + 1;
   std::string o;
   char buf[256];
@@ -511,6 +617,8 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, 
   def("HAS_PERM", (has_perm || P.expand) ? 1 : 0);
   def("EXPAND", P.expand ? 1 : 0);
   def("EX_D", P.ex_d);
+  def("RD", rd && P.expand ? 1 : 0);
+  def("RD_NONE", rd && rd->none ? 1 : 0);
   def("OFF_FAIL_PASS", offsetof(Ctl, fail_pass));
   def("OFF_FAIL_GATE", offsetof(Ctl, fail_gate));
   def("OFF_BLOCKS_DONE", offsetof(Ctl, blocks_done));
@@ -552,8 +660,19 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, 
     o += "}";
   }
   o += "};\n";
-  // forward declaration; the walk follows the template
+  // forward declarations; the walk follows the template
   o += "__device__ __forceinline__ void walk(unsigned int* col, unsigned long long tb);\n";
+  // the readout's test of 32 outputs: the AND of the tested planes, each
+  // taken as is (wanted 1) or inverted (wanted 0)
+  o += "__device__ __forceinline__ unsigned int rd_match(const unsigned int* col) {\n";
+  o += "  unsigned int m = 0xFFFFFFFFu;\n";
+  if (rd)
+    for (size_t i = 0; i < rd->row.size(); ++i) {
+      std::snprintf(buf, sizeof(buf), "  m &= %scol[%u];\n", rd->want[i] ? "" : "~",
+                    (unsigned)rd->row[i]);
+      o += buf;
+    }
+  o += "  return m;\n}\n";
   o += kTemplate;
   // ---- the walk: straight-line code on registers
   std::vector<uint8_t> read(256, 0), written(256, 0);
@@ -719,7 +838,8 @@ std::unordered_map<std::string, const JitEntry*>* g_jit_content = nullptr;
 
 // The compiled kernel of a pass: from the cache of pass contents, else its
 // source is generated and compiled (or found in the cache of sources).
-const JitEntry* jit_kernel_for(const BsPass& P, int kw, bool has_perm, bool has_phase, uint32_t G) {
+const JitEntry* jit_kernel_for(const BsPass& P, int kw, bool has_perm, bool has_phase, uint32_t G,
+                               const RdForm* rd) {
   int dev = 0, major = 0, minor = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
@@ -727,14 +847,15 @@ const JitEntry* jit_kernel_for(const BsPass& P, int kw, bool has_perm, bool has_
     cudaGetLastError();
     return nullptr;
   }
-  const std::string key = content_key(P, kw, has_perm, has_phase, G, major, minor);
+  std::string key = content_key(P, kw, has_perm, has_phase, G, major, minor);
+  if (rd) key += "rd" + rd->key();
   {
     std::lock_guard<std::mutex> lk(g_jit_mu);
     if (!g_jit_content) g_jit_content = new std::unordered_map<std::string, const JitEntry*>();
     auto it = g_jit_content->find(key);
     if (it != g_jit_content->end()) return it->second;
   }
-  const JitEntry* e = jit_kernel(make_source(P, kw, has_perm, has_phase, G));
+  const JitEntry* e = jit_kernel(make_source(P, kw, has_perm, has_phase, G, rd));
   std::lock_guard<std::mutex> lk(g_jit_mu);
   g_jit_content->emplace(key, e);
   return e;
@@ -760,10 +881,27 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   // the form: device, label words, permutes, phases, tile groups
   const uint32_t form = 1u | ((uint32_t)dev << 8) | ((uint32_t)key_words << 16) |
                         (b.has_perm ? 1u << 20 : 0u) | (b.has_phase ? 1u << 21 : 0u) | (G << 24);
-  const void* fn = P.jit_form == form ? P.jit_fn : nullptr;
-  int bps = P.jit_bps;
+  // a readout is compiled into the expansion form (a kernel of its own)
+  RdForm rdf;
+  bool rd = b.rd && P.expand;
+  std::string rkey;
+  if (rd) {
+    rdf = readout_form(P, key_words, G, b.rd->mask, b.rd->value);
+    if (!rdf.none && rdf.row.size() < b.rd->min_planes) rd = false;   // a broad condition
+    rkey = rdf.key();
+  }
+  const void* fn = nullptr;
+  int bps = 0;
+  if (!rd && P.jit_form == form) {
+    fn = P.jit_fn;
+    bps = P.jit_bps;
+  } else if (rd && P.jit_rd_form == form && P.jit_rd_key == rkey) {
+    fn = P.jit_rd_fn;
+    bps = P.jit_rd_bps;
+  }
   if (!fn) {
-    const JitEntry* e = jit_kernel_for(P, key_words, b.has_perm != 0, b.has_phase != 0, G);
+    const JitEntry* e =
+        jit_kernel_for(P, key_words, b.has_perm != 0, b.has_phase != 0, G, rd ? &rdf : nullptr);
     if (!e) return 0;
     fn = reinterpret_cast<const void*>(e->kernel);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -778,9 +916,16 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
       cudaGetLastError();
       return 0;
     }
-    P.jit_form = form;
-    P.jit_fn = fn;
-    P.jit_bps = bps;
+    if (rd) {
+      P.jit_rd_form = form;
+      P.jit_rd_key = rkey;
+      P.jit_rd_fn = fn;
+      P.jit_rd_bps = bps;
+    } else {
+      P.jit_form = form;
+      P.jit_fn = fn;
+      P.jit_bps = bps;
+    }
   }
   const int launched = b.build_tables ? launch_bs_tables(lc, b) : 0;
   if (launched < 0) return -1;
@@ -792,6 +937,8 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
     const void* direct;
     unsigned long long* plog;
     uint32_t fallback, mg_wr, mg_rs, ngates;
+    double* rd_part;
+    double* rd_out;
   } args;
   std::memset(&args, 0, sizeof(args));
   args.ctl = reinterpret_cast<unsigned char*>(ctl);
@@ -812,6 +959,12 @@ int launch_fused_bs_jit(const LaunchCfg& lc, int key_words, Ctl* ctl, Bufs bufs,
   const uint64_t max_blocks = (uint64_t)sms * bps;
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
+  if (rd) {   // one block sum each: at most cap blocks (the tiles are grid-strided)
+    if (blocks > b.rd->cap) blocks = b.rd->cap;
+    args.rd_part = b.rd->part;
+    args.rd_out = b.rd->out;
+    if (b.rd_done) *b.rd_done = 1u;
+  }
   void* params[] = {&args};
   if (cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kJitWarps * 32), params, smem,
                        (cudaStream_t)lc.stream) != cudaSuccess)
@@ -858,7 +1011,7 @@ int bs_jit_selftest(char* log, size_t cap) {
   p.has_phase = true;
   BsPass b;
   build_bitslice(p, 70, &b);
-  const std::string src = make_source(b, 2, true, true, 32);
+  const std::string src = make_source(b, 2, true, true, 32, nullptr);
   std::string msg;
   const std::string cubin = compile_cubin(src, 10, 3, &msg);
   if (log && cap) {

@@ -31,6 +31,7 @@ SPS_OPT_BRANCH_FORM, SPS_OPT_BITSLICE_GROUPS, SPS_OPT_EXPAND, SPS_OPT_FOLD = 10,
 SPS_OPT_COMMUTE, SPS_OPT_LAYER_GATES, SPS_OPT_EXPAND_WALK, SPS_OPT_FUSED_LABELS = 14, 15, 16, 17
 SPS_OPT_AMP_ONLY, SPS_OPT_BITSLICE_JIT, SPS_OPT_PLAN_CACHE = 18, 19, 20
 SPS_OPT_FALLBACK_CHAIN = 21
+SPS_OPT_READOUT_MIN_PLANES = 22
 KIND_SMALL_RUN, KIND_GATHER_BUILD, KIND_GATHER_EMIT = 4, 5, 6
 KIND_FUSED, KIND_EMIT, KIND_COMPACT = 1, 2, 3
 
@@ -45,7 +46,7 @@ EXPORTS = ("sps_set_allocator", "sps_create", "sps_reset", "sps_destroy", "sps_a
            "sps_server_tick", "sps_server_poll", "sps_server_result", "sps_server_stats",
            "sps_server_completed", "sps_probability_async", "sps_measure", "sps_pauli_exp",
            "sps_jit_selftest", "sps_device_rates", "sps_tune", "sps_tune_cache_lookup",
-           "sps_barrier_selftest",
+           "sps_barrier_selftest", "sps_set_readout",
            "sps_commute")
 
 
@@ -62,7 +63,7 @@ class SpsError(RuntimeError):
 class Counters(ctypes.Structure):
     _fields_ = [("gates", ctypes.c_uint64), ("fused_passes", ctypes.c_uint64),
                 ("branch_passes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("upload_bytes", ctypes.c_uint64)]
+                ("upload_bytes", ctypes.c_uint64), ("fused_readouts", ctypes.c_uint64)]
 
 
 class KernelRecord(ctypes.Structure):
@@ -138,6 +139,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sps_probability.restype = st
     lib.sps_probability_async.argtypes = [vp, vp, vp, vp]
     lib.sps_probability_async.restype = st
+    lib.sps_set_readout.argtypes = [vp, vp, vp]
+    lib.sps_set_readout.restype = st
     lib.sps_measure.argtypes = [vp, u32, dbl, vp]
     lib.sps_measure.restype = st
     lib.sps_pauli_exp.argtypes = [vp, vp, vp, vp, dbl, dbl]
@@ -349,6 +352,16 @@ def sps_probability(h: int, mask: Sequence[int], value: Sequence[int]) -> float:
     return p.value
 
 
+def sps_set_readout(h: int, mask: Optional[Sequence[int]], value: Optional[Sequence[int]]) -> None:
+    """Register (mask, value) as the state's readout (None, None: clear it)."""
+    if mask is None or value is None:
+        _check(load_library().sps_set_readout(h, None, None), "sps_set_readout")
+        return
+    m = np.array([int(mask[0]), int(mask[1])], np.uint64)
+    v = np.array([int(value[0]), int(value[1])], np.uint64)
+    _check(load_library().sps_set_readout(h, _ptr(m), _ptr(v)), "sps_set_readout")
+
+
 def sps_probability_async(h: int, mask: Sequence[int], value: Sequence[int], out_ptr: int) -> None:
     """Enqueue the probability; the double lands at out_ptr (pinned host or
     device memory) in stream order."""
@@ -547,6 +560,11 @@ class SparseState:
     def probability_async(self, mask, value, out_ptr: int) -> None:
         """Enqueue the probability into out_ptr (pinned host or device memory)."""
         sps_probability_async(self._h, mask, value, out_ptr)
+
+    def set_readout(self, mask=None, value=None) -> None:
+        """Register a readout condition summed by a compiled expansion launch
+        that ends an apply (None: clear it)."""
+        sps_set_readout(self._h, mask, value)
 
     def pauli_exp(self, x, z, controls, theta: float, eps: float = 0.0) -> None:
         """exp(-i theta/2 P): x / z are the X-or-Y and Z-or-Y masks (two words)."""

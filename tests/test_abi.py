@@ -158,3 +158,16 @@ def test_tune_cache_file_lookup(tmp_path):
     assert c1["load_factor_pct"] == 70 and c1["max_fused_ops"] == 256
     assert sps.sps_tune_cache_lookup(str(p), 2, 23) is None
     assert sps.sps_tune_cache_lookup(str(tmp_path / "missing.txt"), 2, 24) is None
+
+
+def test_option_and_status_constants_match_the_header():
+    """Every SPS_OPT_* and SPS_ERR_* value of the binding is the one the header
+    declares (the enum's explicit initialisers)."""
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "sps.h")).read()
+    declared = {m.group(1): int(m.group(2))
+                for m in re.finditer(r"\b(SPS_(?:OPT|ERR)_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)}
+    assert len(declared) >= 20
+    bound = {k: getattr(sps, k) for k in dir(sps) if re.match(r"SPS_(OPT|ERR)_", k)}
+    for k, v in declared.items():
+        assert k in bound, k
+        assert bound[k] == v, (k, bound[k], v)
