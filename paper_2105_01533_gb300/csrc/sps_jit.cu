@@ -318,7 +318,9 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
 #pragma unroll
           for (int w = 0; w < NW; ++w) {
             if (!((WORD_OUT >> w) & 1u)) continue;
-            const u64 x = tr(my_row[w] >= 0 ? pl[my_row[w] + g] : 0u);
+            const u64 x = ((SPARSE_W >> w) & 1u)
+                              ? (u64)sparse_word(w, pl, g, lane)
+                              : (u64)tr(my_row[w] >= 0 ? pl[my_row[w] + g] : 0u);
             if (w < 2) lo |= x << (32 * w);
             else hi |= x << (32 * (w - 2));
           }
@@ -370,6 +372,15 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
 #endif
           ph[k] = __ldg(a.direct + aux[k]);
         }
+#if EXPAND
+        // the expansion's table holds the common factor times each phase
+#pragma unroll
+        for (u32 k = 0; k < STORE_BATCH; ++k) {
+          if (aux[k] == 0ull) continue;
+          s.re[ent[k]] = ph[k].x;
+          s.im[ent[k]] = ph[k].y;
+        }
+#else
         bool real = true;
 #pragma unroll
         for (u32 k = 0; k < STORE_BATCH; ++k) real = real && (__double_as_longlong(im[k]) << 1) == 0;
@@ -385,6 +396,7 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
             s.im[ent[k]] = fma(re[k], ph[k].y, im[k] * ph[k].x);
           }
         }
+#endif
       } else if (HAS_PHASE) {
         double re[STORE_BATCH], im[STORE_BATCH];
         longlong2 t0[STORE_BATCH], t1[STORE_BATCH];
@@ -673,6 +685,28 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, 
       o += buf;
     }
   o += "  return m;\n}\n";
+  // words with at most 4 rows: each output bit read from its plane (one
+  // broadcast load per row) instead of a 32 x 32 transpose
+  uint32_t sparse = 0;
+  for (uint32_t w = 0; w < 4; ++w)
+    if (__builtin_popcount(P.word_bits[w]) <= 4) sparse |= 1u << w;
+  def("SPARSE_W", sparse);
+  o += "__device__ __forceinline__ unsigned int sparse_word(int w, const unsigned int* pl, "
+       "unsigned int g, unsigned int lane) {\n  unsigned int x = 0u;\n";
+  for (uint32_t w = 0; w < 4; ++w) {
+    if (!((sparse >> w) & 1u) || P.word_bits[w] == 0u) continue;
+    std::snprintf(buf, sizeof(buf), "  if (w == %u) {\n", w);
+    o += buf;
+    for (uint32_t j = 0; j < 32; ++j) {
+      const uint8_t r = P.row_of[w][j];
+      if (!((P.word_bits[w] >> j) & 1u) || r == kNoRow) continue;
+      std::snprintf(buf, sizeof(buf), "    x |= ((pl[%u + g] >> lane) & 1u) << %u;\n",
+                    (unsigned)(r * S), j);
+      o += buf;
+    }
+    o += "  }\n";
+  }
+  o += "  return x;\n}\n";
   o += kTemplate;
   // ---- the walk: straight-line code on registers
   std::vector<uint8_t> read(256, 0), written(256, 0);

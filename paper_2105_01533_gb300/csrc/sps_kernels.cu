@@ -528,9 +528,12 @@ __global__ void k_bs_tables(const longlong2* factors, longlong2* out, uint32_t b
 }
 
 // The direct phase table: entry idx = chunk0[low bits] * chunk1[high bits]
-// (fixed point, rounded once more) as doubles.
+// (fixed point, rounded once more) as doubles; with premul, times the common
+// factor (c_re, c_im), in the same operations the compiled expansion applied
+// to each output before (so its outputs are the same to the bit).
 __global__ void k_bs_direct_table(const longlong2* c0, const longlong2* c1, uint32_t bits0,
-                                  uint32_t bits, double2* out) {
+                                  uint32_t bits, double2* out, uint32_t premul, double c_re,
+                                  double c_im) {
   const uint32_t size = 1u << bits;
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < size;
        idx += gridDim.x * blockDim.x) {
@@ -542,7 +545,14 @@ __global__ void k_bs_direct_table(const longlong2* c0, const longlong2* c1, uint
       qmul(re, im, t.x, t.y);
       q -= 2;
     }
-    out[idx] = make_double2(q_to_double(re, q), q_to_double(im, q));
+    double2 v = make_double2(q_to_double(re, q), q_to_double(im, q));
+    if (premul) {
+      if ((__double_as_longlong(c_im) << 1) == 0)
+        v = make_double2(c_re * v.x, c_re * v.y);
+      else
+        v = make_double2(fma(c_re, v.x, -(c_im * v.y)), fma(c_re, v.y, c_im * v.x));
+    }
+    out[idx] = v;
   }
 }
 
@@ -1369,7 +1379,8 @@ int launch_bs_tables(const LaunchCfg& lc, const BsLaunch& b) {
     const longlong2* t = reinterpret_cast<const longlong2*>(b.tables);
     k_bs_direct_table<<<(int)((size + 255) / 256), 256, 0, (cudaStream_t)lc.stream>>>(
         t, P.nchunks > 1 ? t + (1ull << P.chunk_bits[0]) : t, P.chunk_bits[0], P.aux_bits,
-        reinterpret_cast<double2*>(b.tables) + P.direct_offset());
+        reinterpret_cast<double2*>(b.tables) + P.direct_offset(), P.expand ? 1u : 0u, P.c_re,
+        P.c_im);
     ++launched;
   }
   return cudaPeekAtLastError() == cudaSuccess ? launched : -1;
