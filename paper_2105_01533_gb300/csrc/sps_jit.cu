@@ -298,7 +298,8 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
     u32 rmatch = 0u;
     if (!RD_NONE && lane < GG) {
       const u64 g0e = base + 32ull * lane;
-      rmatch = g0e >= n ? 0u : n - g0e >= 32ull ? FULL : (1u << (u32)(n - g0e)) - 1u;
+      rmatch = FULL_TILES ? FULL
+             : g0e >= n ? 0u : n - g0e >= 32ull ? FULL : (1u << (u32)(n - g0e)) - 1u;
       rmatch &= rd_match(pl + lane);
     }
 #endif
@@ -312,7 +313,7 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
         const u32 g = g0 + k;
         aux[k] = 0ull;
         ent[k] = base + 32ull * g + lane;
-        const bool valid = ent[k] < n;
+        const bool valid = FULL_TILES || ent[k] < n;
         if (HAS_PERM) {
           u64 lo = 0ull, hi = 0ull;
 #pragma unroll
@@ -356,14 +357,10 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
         for (u32 k = 0; k < STORE_BATCH; ++k) {
           ph[k] = make_double2(1.0, 0.0);
 #if EXPAND
+          // every output from the table (entry 0: the common factor itself)
           re[k] = C_RE;
           im[k] = C_IM;
-          if (ent[k] >= n) continue;
-          if (aux[k] == 0ull) {   // no phase: the common factor
-            s.re[ent[k]] = C_RE;
-            s.im[ent[k]] = C_IM;
-            continue;
-          }
+          if (!FULL_TILES && ent[k] >= n) continue;
 #else
           re[k] = im[k] = 0.0;
           if (aux[k] == 0ull) continue;
@@ -376,7 +373,7 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
         // the expansion's table holds the common factor times each phase
 #pragma unroll
         for (u32 k = 0; k < STORE_BATCH; ++k) {
-          if (aux[k] == 0ull) continue;
+          if (!FULL_TILES && ent[k] >= n) continue;
           s.re[ent[k]] = ph[k].x;
           s.im[ent[k]] = ph[k].y;
         }
@@ -630,6 +627,8 @@ std::string make_source(const BsPass& P, int kw, bool has_perm, bool has_phase, 
   def("EXPAND", P.expand ? 1 : 0);
   def("EX_D", P.ex_d);
   def("RD", rd && P.expand ? 1 : 0);
+  // an expansion whose 2^EX_D outputs fill every tile: no entry test
+  def("FULL_TILES", P.expand && P.ex_d < 64 && ((1ull << P.ex_d) % (32ull * G)) == 0 ? 1 : 0);
   def("RD_NONE", rd && rd->none ? 1 : 0);
   def("OFF_FAIL_PASS", offsetof(Ctl, fail_pass));
   def("OFF_FAIL_GATE", offsetof(Ctl, fail_gate));

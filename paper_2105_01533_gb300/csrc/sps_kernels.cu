@@ -546,8 +546,10 @@ __global__ void k_bs_direct_table(const longlong2* c0, const longlong2* c1, uint
       q -= 2;
     }
     double2 v = make_double2(q_to_double(re, q), q_to_double(im, q));
-    if (premul) {
-      if ((__double_as_longlong(c_im) << 1) == 0)
+    if (premul) {   // entry 0 (no phase) is the factor itself
+      if (idx == 0u)
+        v = make_double2(c_re, c_im);
+      else if ((__double_as_longlong(c_im) << 1) == 0)
         v = make_double2(c_re * v.x, c_re * v.y);
       else
         v = make_double2(fma(c_re, v.x, -(c_im * v.y)), fma(c_re, v.y, c_im * v.x));
