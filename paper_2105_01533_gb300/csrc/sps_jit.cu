@@ -459,15 +459,15 @@ extern "C" __global__ void __launch_bounds__(128, LB_MIN) k_bs_jit(const JArgs a
     }
 #if EXPAND && RD
     // the matching entries' amplitudes, each read back by the lane that stored
-    // it (rare: FP64 products only in warps with a match)
-    if (__any_sync(FULL, rmatch != 0u)) {
-      for (u32 g = 0; g < GG; ++g) {
-        const u32 mw = __shfl_sync(FULL, rmatch, g);
-        if ((mw >> lane) & 1u) {
-          const u64 e = base + 32ull * g + lane;
-          const double re = s.re[e], im = s.im[e];
-          racc += re * re + im * im;
-        }
+    // it, over the groups with a match only, in group order (rare: FP64
+    // products only in warps with a match)
+    for (u32 gm = __ballot_sync(FULL, rmatch != 0u); gm != 0u; gm &= gm - 1u) {
+      const u32 g = (u32)__ffs((int)gm) - 1u;
+      const u32 mw = __shfl_sync(FULL, rmatch, g);
+      if ((mw >> lane) & 1u) {
+        const u64 e = base + 32ull * g + lane;
+        const double re = s.re[e], im = s.im[e];
+        racc += re * re + im * im;
       }
     }
 #endif
