@@ -185,8 +185,9 @@ sps_status sps_probability_async(sps_state* s, const uint64_t mask[2], const uin
  * stored; a later sps_probability or sps_probability_async with the same
  * condition, before any call that changes the state, then copies that sum
  * instead of launching the readout (counted in sps_counters.fused_readouts).
- * Other conditions, and states changed by other launches, take the readout
- * kernel as before. The fused sum is formed in a fixed order too (per block
+ * Other conditions, conditions testing fewer of the launch's label bits than
+ * SPS_OPT_READOUT_MIN_PLANES (default 8, unless no label can match), and states
+ * changed by other launches take the readout kernel as before. The fused sum is formed in a fixed order too (per block
  * of the launch, then over blocks in block order), which differs from the
  * readout kernel's, so the two may differ in the last bits. Allocates a few
  * KB of device memory on first use. Errors: SPS_ERR_ARG (one of mask, value
