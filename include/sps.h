@@ -432,7 +432,8 @@ sps_status sps_get_counters(sps_state* s, sps_counters* out);
  * then kinds 5 and 6 follow with n_in > 0; they show n_in 0 when skipped),
  * 11 the attempted run's passes in one launch (SPS_OPT_FALLBACK_CHAIN; nops =
  * passes; n_in 0 when the attempt took the run), 12 probability readout
- * (sps_probability and sps_probability_async; n_in = n_out = entries read).
+ * (sps_probability and sps_probability_async; n_in = n_out = entries read;
+ * none when a registered readout's sum is copied instead).
  * n_in: entries the kernel read; n_out: entries in the state after it. flags: bit 0 the
  * pass permutes labels, bit 1 it changes amplitudes, bit 2 (kinds 7 and 10) the
  * launch also applied the phase/permutation run after the branching gates,
